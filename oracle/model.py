@@ -1,0 +1,548 @@
+"""FP64 oracle of the 3DSS renderer (forward values and gradients).
+
+TEST INFRASTRUCTURE ONLY: only tests/, ``__graft_entry__.smoke()`` and the
+cpu_baseline / reference arm of ``bench.py`` may import this module.  It
+shares no code with the CUDA path (``paper_2605_05876_gb300``) and imports
+nothing from it; both sides read the same seeded inputs.
+
+The oracle is the method written out plainly, in double precision:
+
+* per surfel and view (``records``): the T-matrix rows (Sec. 3.1), the depth
+  interval (Sec. 3.1, Sec. 3.2.1), the centre-precomputed MIP covariance of
+  Eq. mip_cov with n_f of Eq. mip_eval (Sec. 3.3.2 applies them at the
+  centre), and the forward-shaded split-sum colour of Eq. ibl (Sec. 3.4);
+* per pixel: the discrete decisions of Algorithm 1 (which surfels cover it,
+  the order by z_start, the layer of each, the K_max cap) come from the C
+  half (``ss3d_oracle.c``);
+* the values -- weights (Eq. mip_weight), Shepard sums (Eq. shepard),
+  coverage opacity (Eq. alpha), front-to-back compositing and residual
+  transmittance (Eq. compositing) -- are PyTorch FP64 ops, so the gradient
+  of any loss is PyTorch autograd with every discrete decision held fixed
+  (which is the definition of the gradient used here).
+
+Readings where the paper is silent are listed in the design doc; each is restated
+at the function that applies it.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import os
+import subprocess
+from functools import lru_cache
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ss3d_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libss3d_oracle.so")
+
+F64 = torch.float64
+
+# channel layout of the per-surfel payload that layers average
+# 0..2 shaded RGB, 3..5 albedo, 6 roughness, 7 metallic, 8..10 normal, 11 depth
+N_CH = 12
+NORMAL = slice(8, 11)
+
+
+@dataclasses.dataclass
+class Params:
+    """Renderer constants.  r_cut = 3 (App. A "Cutoff radius"),
+    gamma = 2 pi (Sec. 3.5.1), K_max = 16 (App. A "Maximum layer count").
+    sigma_f (the screen prefilter variance of Eq. mip_cov) is not given by
+    the paper; 0.5 px^2 is this build's default.  z_near and the background
+    are not given either."""
+    r_cut: float = 3.0
+    sigma_f: float = 0.5
+    gamma: float = 2.0 * math.pi
+    k_max: int = 16
+    z_near: float = 0.01
+    bg: tuple = (0.0, 0.0, 0.0)
+    env_levels: int = 6
+    irr_w: int = 32
+    irr_h: int = 16
+    lut_n: int = 128
+
+
+# ---------------------------------------------------------------------------
+# the C half
+
+
+def build(force: bool = False) -> str:
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+@lru_cache(maxsize=1)
+def lib():
+    L = ctypes.CDLL(build())
+    dp = ctypes.POINTER(ctypes.c_double)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    u8p = ctypes.POINTER(ctypes.c_uint8)
+    L.oref_brdf_lut.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp]
+    L.oref_brdf_eval.argtypes = [ctypes.c_int, dp, dp, ctypes.c_int, dp, dp, dp]
+    L.oref_spec_levels_size.argtypes = [ctypes.c_int] * 3
+    L.oref_spec_levels_size.restype = ctypes.c_longlong
+    L.oref_env_prefilter.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, dp, dp]
+    L.oref_env_adjoint.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_int, dp]
+    L.oref_fragments.argtypes = [ctypes.c_int, dp, dp, dp, u8p, dp, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_double, ctypes.c_int, ctypes.c_int, i32p, i32p, dp, i64p,
+                                 i64p, i32p, i32p, i32p]
+    L.oref_fragments.restype = ctypes.c_longlong
+    return L
+
+
+def _p(a: np.ndarray, t):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+# ---------------------------------------------------------------------------
+# BRDF table and environment levels
+
+
+@lru_cache(maxsize=4)
+def _brdf_lut_np(n: int, nq: int) -> np.ndarray:
+    x, w = np.polynomial.legendre.leggauss(nq)
+    x = np.ascontiguousarray(x, np.float64)
+    w = np.ascontiguousarray(w, np.float64)
+    out = np.zeros(n * n * 2, np.float64)
+    lib().oref_brdf_lut(n, nq, _p(x, ctypes.c_double), _p(w, ctypes.c_double), _p(out, ctypes.c_double))
+    return out.reshape(n, n, 2)
+
+
+def brdf_lut(n: int = 128, nq: int = 128) -> np.ndarray:
+    """(beta1, beta2) at cell centres, indexed [roughness][n.v][2]."""
+    return _brdf_lut_np(n, nq).copy()
+
+
+def brdf_eval(mu, r, nq: int = 128) -> np.ndarray:
+    """(beta1, beta2) of the split-sum integral at arbitrary (n.v, r)."""
+    mu = np.ascontiguousarray(np.atleast_1d(mu), np.float64)
+    r = np.ascontiguousarray(np.broadcast_to(np.atleast_1d(r), mu.shape), np.float64)
+    x, w = np.polynomial.legendre.leggauss(nq)
+    x = np.ascontiguousarray(x)
+    w = np.ascontiguousarray(w)
+    out = np.zeros((mu.shape[0], 2))
+    lib().oref_brdf_eval(mu.shape[0], _p(mu, ctypes.c_double), _p(r, ctypes.c_double), nq,
+                         _p(x, ctypes.c_double), _p(w, ctypes.c_double), _p(out, ctypes.c_double))
+    return out
+
+
+def level_sizes(We: int, He: int, L: int):
+    return [(max(We >> i, 8), max(He >> i, 4)) for i in range(L)]
+
+
+def env_prefilter(env: np.ndarray, L: int = 6, Wi: int = 32, Hi: int = 16):
+    """Irradiance map [Hi][Wi][3] and the L specular levels (list of
+    [H_i][W_i][3]) of an equirect env [He][We][3] (see ss3d_oracle.c)."""
+    env = np.ascontiguousarray(env, np.float64)
+    He, We, _ = env.shape
+    irr = np.zeros((Hi, Wi, 3))
+    spec = np.zeros(lib().oref_spec_levels_size(We, He, L))
+    lib().oref_env_prefilter(_p(env, ctypes.c_double), We, He, Wi, Hi, L,
+                             _p(irr, ctypes.c_double), _p(spec, ctypes.c_double))
+    levels, off = [], 0
+    for (W, H) in level_sizes(We, He, L):
+        levels.append(spec[off:off + W * H * 3].reshape(H, W, 3))
+        off += W * H * 3
+    return irr, levels
+
+
+def env_adjoint(d_irr: np.ndarray, d_levels, We: int, He: int):
+    """Transpose of env_prefilter: gradient w.r.t. the base env texels."""
+    Hi, Wi, _ = d_irr.shape
+    L = len(d_levels)
+    d_irr = np.ascontiguousarray(d_irr, np.float64)
+    d_spec = np.ascontiguousarray(np.concatenate([np.asarray(d, np.float64).ravel() for d in d_levels]))
+    out = np.zeros((He, We, 3))
+    lib().oref_env_adjoint(_p(d_irr, ctypes.c_double), _p(d_spec, ctypes.c_double), We, He, Wi, Hi, L,
+                           _p(out, ctypes.c_double))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# texture lookups (bilinear, equirect convention of ss3d_oracle.c)
+
+
+def dir_to_uv(d: torch.Tensor):
+    """phi = atan2(d_x, -d_z), theta = acos(d_y); u = phi / 2 pi + 1/2,
+    v = theta / pi."""
+    d = d / torch.linalg.norm(d, dim=-1, keepdim=True)
+    phi = torch.atan2(d[..., 0], -d[..., 2])
+    th = torch.acos(torch.clamp(d[..., 1], -1.0, 1.0))
+    return phi / (2.0 * math.pi) + 0.5, th / math.pi
+
+
+def bilinear_wrap(tex: torch.Tensor, u: torch.Tensor, v: torch.Tensor):
+    """Bilinear lookup of tex [H][W][C] at texel-centre coordinates
+    (u W - 1/2, v H - 1/2), wrapping in u and clamping in v."""
+    H, W, _ = tex.shape
+    X = u * W - 0.5
+    Y = v * H - 0.5
+    x0 = torch.floor(X)
+    y0 = torch.floor(Y)
+    fx = (X - x0)[..., None]
+    fy = (Y - y0)[..., None]
+    x0 = x0.long()
+    y0 = y0.long()
+    xa = torch.remainder(x0, W)
+    xb = torch.remainder(x0 + 1, W)
+    ya = torch.clamp(y0, 0, H - 1)
+    yb = torch.clamp(y0 + 1, 0, H - 1)
+    return ((1 - fy) * ((1 - fx) * tex[ya, xa] + fx * tex[ya, xb])
+            + fy * ((1 - fx) * tex[yb, xa] + fx * tex[yb, xb]))
+
+
+def bilinear_clamp(tex: torch.Tensor, u: torch.Tensor, v: torch.Tensor):
+    """Bilinear lookup of tex [H][W][C] with u along W, v along H, both in
+    [0,1] at cell centres, clamped at the borders."""
+    H, W, _ = tex.shape
+    X = u * W - 0.5
+    Y = v * H - 0.5
+    x0 = torch.floor(X)
+    y0 = torch.floor(Y)
+    fx = (X - x0)[..., None]
+    fy = (Y - y0)[..., None]
+    x0 = x0.long()
+    y0 = y0.long()
+    xa = torch.clamp(x0, 0, W - 1)
+    xb = torch.clamp(x0 + 1, 0, W - 1)
+    ya = torch.clamp(y0, 0, H - 1)
+    yb = torch.clamp(y0 + 1, 0, H - 1)
+    return ((1 - fy) * ((1 - fx) * tex[ya, xa] + fx * tex[ya, xb])
+            + fy * ((1 - fx) * tex[yb, xa] + fx * tex[yb, xb]))
+
+
+def specular_lookup(levels, d: torch.Tensor, r: torch.Tensor):
+    """Roughness-indexed level lookup: level coordinate r (L-1), linear
+    between the two nearest levels, bilinear within each."""
+    L = len(levels)
+    u, v = dir_to_uv(d)
+    lc = torch.clamp(r, 0.0, 1.0) * (L - 1)
+    i0 = torch.clamp(torch.floor(lc).long(), 0, L - 1)
+    f = (lc - i0.to(lc.dtype))[..., None]
+    i1 = torch.clamp(i0 + 1, max=L - 1)
+    out = torch.zeros(d.shape[:-1] + (3,), dtype=d.dtype)
+    for i in range(L):
+        w = (1.0 - f) * (i0 == i)[..., None] + f * (i1 == i)[..., None]
+        out = out + w * bilinear_wrap(levels[i], u, v)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# per surfel and view
+
+
+def quat_to_rot(q: torch.Tensor):
+    q = q / torch.linalg.norm(q, dim=-1, keepdim=True)
+    w, x, y, z = q.unbind(-1)
+    return torch.stack([
+        torch.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], -1),
+        torch.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], -1),
+        torch.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)], -2)
+
+
+def records(S: dict, cam: dict, irr, levels, lut, prm: Params):
+    """Everything the rasteriser needs for one view, as FP64 tensors that
+    stay differentiable w.r.t. the surfel parameters in S and the env
+    levels.
+
+    S: pos [N,3], quat [N,4], log_scale [N,2], albedo [N,3], roughness [N],
+    metallic [N].  cam: R [3,3], t [3], fx, fy, cx, cy, width, height.
+    """
+    R = quat_to_rot(S["quat"])
+    scale = torch.exp(S["log_scale"])
+    t_u = scale[:, 0:1] * R[:, :, 0]          # Sec. 3.6: quaternion + log scales
+    t_v = scale[:, 1:2] * R[:, :, 1]
+    n = R[:, :, 2]                            # = t_u x t_v / |.| (Sec. 3.1)
+    Rc, tc = cam["R"], cam["t"]
+    c_cam = S["pos"] @ Rc.T + tc              # camera-space centre c'
+    tu_c = t_u @ Rc.T
+    tv_c = t_v @ Rc.T
+    fx, fy, cx, cy = cam["fx"], cam["fy"], cam["cx"], cam["cy"]
+    # T = P S with S = [t'_u t'_v 0 c'] (Sec. 3.1).  P is the pinhole that
+    # maps camera space to homogeneous pixel coordinates; its rows x, y and w
+    # give T1, T2, T4 (the depth row T3 is unused, App. A).
+    row_x = torch.stack([tu_c[:, 0], tv_c[:, 0], c_cam[:, 0]], -1)
+    row_y = torch.stack([tu_c[:, 1], tv_c[:, 1], c_cam[:, 1]], -1)
+    row_z = torch.stack([tu_c[:, 2], tv_c[:, 2], c_cam[:, 2]], -1)
+    T1 = fx * row_x + cx * row_z
+    T2 = fy * row_y + cy * row_z
+    T4 = row_z
+    # depth interval (Sec. 3.1): eps_z = r_cut sqrt(t'_uz^2 + t'_vz^2)
+    z = c_cam[:, 2]
+    eps = prm.r_cut * torch.sqrt(tu_c[:, 2] ** 2 + tv_c[:, 2] ** 2)
+    zs, ze = z - eps, z + eps
+    # centre-precomputed MIP filter (Sec. 3.3.2): J = d(u,v)/d(x,y) at the
+    # centre is the inverse of M = d(x,y)/d(u,v) there, with x = T1.u/T4.u.
+    px = T1[:, 2] / T4[:, 2]
+    py = T2[:, 2] / T4[:, 2]
+    M = torch.stack([
+        torch.stack([T1[:, 0] - px * T4[:, 0], T1[:, 1] - px * T4[:, 1]], -1),
+        torch.stack([T2[:, 0] - py * T4[:, 0], T2[:, 1] - py * T4[:, 1]], -1)], -2) / T4[:, 2, None, None]
+    detM = M[:, 0, 0] * M[:, 1, 1] - M[:, 0, 1] * M[:, 1, 0]
+    valid = (zs > prm.z_near) & (detM != 0)
+    Msafe = torch.where(valid[:, None, None], M, torch.eye(2, dtype=F64).expand_as(M))
+    J = torch.linalg.inv(Msafe)
+    Sigma = torch.eye(2, dtype=F64) + prm.sigma_f * (J @ J.transpose(1, 2))   # Eq. mip_cov
+    Sinv = torch.linalg.inv(Sigma)
+    n_f = torch.rsqrt(torch.linalg.det(Sigma))                                # sqrt(|I| / |Sigma|)
+
+    # forward shading (Sec. 3.4, Eq. ibl), one colour per surfel and view
+    o = -(Rc.T @ tc)                                   # camera centre
+    w_o = o[None, :] - S["pos"]
+    w_o = w_o / torch.linalg.norm(w_o, dim=-1, keepdim=True)
+    facing = (n * w_o).sum(-1, keepdim=True)
+    n_s = torch.where(facing < 0, -n, n)                # two-sided surfels
+    mu = torch.clamp((n_s * w_o).sum(-1), 0.0, 1.0)
+    refl = 2.0 * (w_o * n_s).sum(-1, keepdim=True) * n_s - w_o
+    rho, m, r = S["albedo"], S["metallic"][:, None], S["roughness"]
+    F0 = 0.04 * (1.0 - m) + rho * m
+    k_d = (1.0 - F0) * (1.0 - m)
+    u_n, v_n = dir_to_uv(n_s)
+    L_d = bilinear_wrap(irr, u_n, v_n)
+    L_s = specular_lookup(levels, refl, r)
+    beta = bilinear_clamp(lut, mu, torch.clamp(r, 0.0, 1.0))   # [n.v along W, r along H]
+    colour = k_d * rho * L_d + L_s * (F0 * beta[:, 0:1] + beta[:, 1:2])
+
+    ch = torch.cat([colour, rho, r[:, None], m, n_s, z[:, None]], -1)   # [N, 12]
+    T = torch.stack([T1, T2, T4], 1)                                     # [N, 3, 3]
+    return dict(T=T, Sinv=Sinv, n_f=n_f, zs=zs, ze=ze, valid=valid, ch=ch, M=M)
+
+
+def support_rect(rec: dict, prm: Params) -> np.ndarray:
+    """Support rectangle [x_lo, x_hi, y_lo, y_hi] (continuous pixel
+    coordinates) of every surfel: the union of
+      (a) the exact bounds of the projected disc of radius r_cut -- the
+          bounding-rectangle construction of App. A: tangent lines of the
+          image of the disc, from the dual conic C* = H Q* H^T with
+          H = [T1; T2; T4] and Q* = diag(1, 1, -1/r_cut^2);
+      (b) the r_cut bounds of the screen-space EWA resampling ellipse at the
+          centre, covariance M M^T + sigma_f I (M = d(x,y)/d(u,v), so this is
+          the screen image of Sigma_mip of Eq. mip_cov under the local affine
+          map), i.e. p +- r_cut sqrt((M M^T)_aa + sigma_f);
+    padded by one pixel.  A pixel is a candidate only if its centre lies in
+    the rectangle.  For ordinary surfels the rectangle contains the whole
+    filtered support; for nearly edge-on surfels, whose centre-precomputed
+    filtered support is an unbounded strip, it bounds the footprint."""
+    T = rec["T"].detach().numpy()
+    N = T.shape[0]
+    Q = np.diag([1.0, 1.0, -1.0 / prm.r_cut ** 2])
+    C = np.einsum("nij,jk,nlk->nil", T, Q, T)
+    c22 = C[:, 2, 2]
+    M = rec["M"].detach().numpy()
+    MMt = np.einsum("nij,nkj->nik", M, M)
+    p = np.stack([T[:, 0, 2] / T[:, 2, 2], T[:, 1, 2] / T[:, 2, 2]], 1)
+    out = np.zeros((N, 4))
+    with np.errstate(invalid="ignore", divide="ignore"):
+        for a in range(2):
+            ca, cb = C[:, a, a], C[:, a, 2]
+            disc = np.sqrt(np.maximum(cb * cb - ca * c22, 0.0))
+            r0, r1 = (cb + disc) / c22, (cb - disc) / c22
+            ext = prm.r_cut * np.sqrt(MMt[:, a, a] + prm.sigma_f)
+            lo = np.minimum(np.minimum(r0, r1), p[:, a] - ext) - 1.0
+            hi = np.maximum(np.maximum(r0, r1), p[:, a] + ext) + 1.0
+            bad = ~(c22 < 0)
+            lo[bad] = -np.inf
+            hi[bad] = np.inf
+            out[:, 2 * a], out[:, 2 * a + 1] = lo, hi
+    return out
+
+
+# ---------------------------------------------------------------------------
+# decisions (C) and values (torch)
+
+
+@dataclasses.dataclass
+class Fragments:
+    pix: np.ndarray        # [F] pixel id (y * W + x) of each kept fragment
+    sid: np.ndarray        # [F] surfel index
+    layer: np.ndarray      # [F] layer index (< k_max)
+    q_pix: np.ndarray      # [P] queried pixel ids
+    n_layers: np.ndarray   # [P] kept layers per queried pixel
+    margin: np.ndarray     # [P, 3] rho2 cutoff (rel), gap (rel), rectangle edge (px)
+    count: np.ndarray      # [P] fragments per queried pixel
+
+
+def fragments(rec: dict, rect: np.ndarray, W: int, H: int, prm: Params, pix=None) -> Fragments:
+    T = np.ascontiguousarray(rec["T"].detach().numpy().reshape(-1, 9))
+    Sinv = rec["Sinv"].detach().numpy()
+    Sv = np.ascontiguousarray(np.stack([Sinv[:, 0, 0], Sinv[:, 0, 1], Sinv[:, 1, 1]], 1))
+    zse = np.ascontiguousarray(np.stack([rec["zs"].detach().numpy(), rec["ze"].detach().numpy()], 1))
+    valid = np.ascontiguousarray(rec["valid"].numpy().astype(np.uint8))
+    rect = np.ascontiguousarray(rect, np.float64)
+    N = T.shape[0]
+    if pix is None:
+        q = np.arange(W * H, dtype=np.int32)
+        pix_ptr = None
+    else:
+        q = np.ascontiguousarray(pix, np.int32)
+        pix_ptr = _p(q, ctypes.c_int32)
+    P = q.shape[0]
+    nl = np.zeros(P, np.int32)
+    mg = np.zeros((P, 3), np.float64)
+    cnt = np.zeros(P, np.int64)
+    L = lib()
+    args = (N, _p(T, ctypes.c_double), _p(Sv, ctypes.c_double), _p(zse, ctypes.c_double),
+            _p(valid, ctypes.c_uint8), _p(rect, ctypes.c_double), W, H, prm.r_cut ** 2, prm.k_max,
+            P, pix_ptr, _p(nl, ctypes.c_int32), _p(mg, ctypes.c_double), _p(cnt, ctypes.c_int64))
+    total = L.oref_fragments(*args, None, None, None, None)
+    off = np.zeros(P, np.int64)
+    off[1:] = np.cumsum(cnt)[:-1]
+    fp = np.zeros(total, np.int32)
+    fs = np.zeros(total, np.int32)
+    fl = np.zeros(total, np.int32)
+    L.oref_fragments(*args, _p(off, ctypes.c_int64), _p(fp, ctypes.c_int32), _p(fs, ctypes.c_int32),
+                     _p(fl, ctypes.c_int32))
+    return Fragments(fp, fs, fl, q, nl, mg, cnt)
+
+
+def composite(rec: dict, fr: Fragments, W: int, prm: Params):
+    """Layer sums, Shepard normalisation, coverage opacity and compositing
+    for the queried pixels.  Returns (rgba [P,4], aov [P,9]) as FP64
+    tensors, differentiable w.r.t. the record tensors."""
+    P = fr.q_pix.shape[0]
+    Kq = max(1, int(fr.n_layers.max()) if P else 1)
+    # row of each fragment within the query
+    q_index = {int(p): i for i, p in enumerate(fr.q_pix)} if P < 4096 else None
+    if q_index is not None:
+        row = np.array([q_index[int(p)] for p in fr.pix], np.int64)
+    else:
+        lookup = np.full(int(fr.q_pix.max()) + 1, -1, np.int64)
+        lookup[fr.q_pix] = np.arange(P)
+        row = lookup[fr.pix]
+    row_t = torch.from_numpy(row)
+    sid = torch.from_numpy(fr.sid.astype(np.int64))
+    layer = torch.from_numpy(fr.layer.astype(np.int64))
+    x = torch.from_numpy((fr.pix % W).astype(np.float64)) + 0.5
+    y = torch.from_numpy((fr.pix // W).astype(np.float64)) + 0.5
+    T = rec["T"][sid]
+    T1, T2, T4 = T[:, 0], T[:, 1], T[:, 2]
+    # ray planes pulled back through T (Sec. 3.1) and their common zero
+    k = x[:, None] * T4 - T1
+    l = y[:, None] * T4 - T2
+    s = torch.linalg.cross(k, l, dim=-1)
+    u = s[:, 0] / s[:, 2]
+    v = s[:, 1] / s[:, 2]
+    Si = rec["Sinv"][sid]
+    rho2 = Si[:, 0, 0] * u * u + 2.0 * Si[:, 0, 1] * u * v + Si[:, 1, 1] * v * v   # Eq. mip_weight
+    w = rec["n_f"][sid] * torch.exp(-0.5 * rho2)
+    key = row_t * Kq + layer
+    Wk = torch.zeros(P * Kq, dtype=F64).index_add(0, key, w).reshape(P, Kq)
+    Ck = torch.zeros(P * Kq, N_CH, dtype=F64).index_add(0, key, w[:, None] * rec["ch"][sid]).reshape(P, Kq, N_CH)
+    present = torch.arange(Kq)[None, :] < torch.from_numpy(fr.n_layers.astype(np.int64))[:, None]
+    Wsafe = torch.where(present, Wk, torch.ones_like(Wk))
+    Chat = Ck / Wsafe[..., None]                                   # Eq. shepard
+    nrm = Ck[..., NORMAL]
+    nlen = torch.linalg.norm(nrm, dim=-1, keepdim=True)
+    nlen = torch.where(present[..., None], nlen, torch.ones_like(nlen))
+    Chat = torch.cat([Chat[..., :8], nrm / nlen, Chat[..., 11:]], -1)   # normals renormalised per layer
+    alpha = 1.0 - torch.exp(-prm.gamma * Wk / (2.0 * math.pi))         # Eq. alpha
+    alpha = torch.where(present, alpha, torch.zeros_like(alpha))
+    one_minus = 1.0 - alpha
+    Tbar = torch.cumprod(torch.cat([torch.ones(P, 1, dtype=F64), one_minus], 1), 1)   # [P, Kq+1]
+    wgt = Tbar[:, :Kq] * alpha                                         # Eq. compositing
+    out = (wgt[..., None] * torch.where(present[..., None], Chat, torch.zeros_like(Chat))).sum(1)
+    T_end = Tbar[:, Kq]
+    bg = torch.tensor(prm.bg, dtype=F64)
+    rgb = out[:, :3] + T_end[:, None] * bg
+    rgba = torch.cat([rgb, (1.0 - T_end)[:, None]], 1)                # soft silhouette (Sec. 3.5.2)
+    return rgba, out[:, 3:]
+
+
+# ---------------------------------------------------------------------------
+# convenience: a whole view
+
+
+def to_torch_surfels(surf, requires_grad=False) -> dict:
+    d = {k: torch.from_numpy(np.asarray(getattr(surf, k), np.float64).copy())
+         for k in ("pos", "quat", "log_scale", "albedo", "roughness", "metallic")}
+    if requires_grad:
+        for v in d.values():
+            v.requires_grad_(True)
+    return d
+
+
+def cam_dict(cam) -> dict:
+    """Camera values rounded to float32 first (the CUDA path receives
+    float32), then held in FP64."""
+    f32 = lambda a: float(np.float32(a))
+    return dict(R=torch.from_numpy(np.asarray(cam.R, np.float32).astype(np.float64)),
+                t=torch.from_numpy(np.asarray(cam.t, np.float32).astype(np.float64)),
+                fx=f32(cam.fx), fy=f32(cam.fy), cx=f32(cam.cx), cy=f32(cam.cy),
+                width=int(cam.width), height=int(cam.height))
+
+
+@dataclasses.dataclass
+class EnvState:
+    irr: np.ndarray
+    levels: list
+    lut: np.ndarray
+    shape: tuple
+
+
+def prepare_env(env: np.ndarray, prm: Params, lut_nq: int = 128) -> EnvState:
+    env32 = np.asarray(env, np.float32).astype(np.float64)
+    irr, levels = env_prefilter(env32, prm.env_levels, prm.irr_w, prm.irr_h)
+    return EnvState(irr, levels, brdf_lut(prm.lut_n, lut_nq), env32.shape)
+
+
+def render_view(surf, cam, env: EnvState, prm: Params = Params(), pix=None, G=None,
+                chunk: int = 1 << 16):
+    """Render one view (all pixels, or the pixel ids in `pix`).
+
+    Returns a dict with rgba [P,4], aov [P,9], n_layers, margins and, if G
+    (upstream gradient, [P,13] = rgba then aov) is given, the gradients of
+    sum(G * [rgba, aov]) w.r.t. the surfel parameters and the base env.
+    """
+    need_grad = G is not None
+    S = to_torch_surfels(surf, requires_grad=need_grad)
+    cd = cam_dict(cam)
+    irr = torch.from_numpy(env.irr.copy()).requires_grad_(need_grad)
+    levels = [torch.from_numpy(l.copy()).requires_grad_(need_grad) for l in env.levels]
+    lut = torch.from_numpy(env.lut.copy())
+    W, H = cd["width"], cd["height"]
+    with torch.set_grad_enabled(need_grad):
+        rec = records(S, cd, irr, levels, lut, prm)
+    rect = support_rect(rec, prm)
+    q_all = np.arange(W * H, dtype=np.int32) if pix is None else np.asarray(pix, np.int32)
+    # leaves for the per-pixel part, so pixel chunks can be back-propagated one at a time
+    leaf = {k: rec[k].detach().clone().requires_grad_(need_grad) for k in ("T", "Sinv", "n_f", "ch")}
+    leaf.update(zs=rec["zs"].detach(), ze=rec["ze"].detach(), valid=rec["valid"])
+    rgba_parts, aov_parts, nl_parts, mg_parts = [], [], [], []
+    for c0 in range(0, q_all.shape[0], chunk):
+        q = q_all[c0:c0 + chunk]
+        fr = fragments(leaf, rect, W, H, prm, pix=q)
+        with torch.set_grad_enabled(need_grad):
+            rgba, aov = composite(leaf, fr, W, prm)
+            if need_grad:
+                Gc = torch.from_numpy(np.asarray(G[c0:c0 + chunk], np.float64))
+                (torch.cat([rgba, aov], 1) * Gc).sum().backward()
+        rgba_parts.append(rgba.detach().numpy())
+        aov_parts.append(aov.detach().numpy())
+        nl_parts.append(fr.n_layers)
+        mg_parts.append(fr.margin)
+    out = dict(rgba=np.concatenate(rgba_parts), aov=np.concatenate(aov_parts),
+               n_layers=np.concatenate(nl_parts), margin=np.concatenate(mg_parts), rect=rect,
+               valid=rec["valid"].numpy())
+    if need_grad:
+        tens = [rec[k] for k in ("T", "Sinv", "n_f", "ch")]
+        grads = [leaf[k].grad if leaf[k].grad is not None else torch.zeros_like(leaf[k]) for k in
+                 ("T", "Sinv", "n_f", "ch")]
+        torch.autograd.backward(tens, grads)
+        out["grad"] = {k: (v.grad.numpy() if v.grad is not None else np.zeros(v.shape)) for k, v in S.items()}
+        d_irr = irr.grad.numpy() if irr.grad is not None else np.zeros(irr.shape)
+        d_lv = [lv.grad.numpy() if lv.grad is not None else np.zeros(lv.shape) for lv in levels]
+        He, We, _ = env.shape
+        out["grad"]["env"] = env_adjoint(d_irr, d_lv, We, He)
+    return out

@@ -1,0 +1,535 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+Each test is chosen so that a plausible slip in the oracle (a dropped term,
+a wrong sign or index, a transposed operand) fails it.  Nothing here uses the
+CUDA path.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import model as M
+from paper_2605_05876_gb300 import scenes as S
+from tests import _tiny
+
+GOLDEN = {}
+with open(__file__.replace("test_oracle_pins.py", "golden/paper_constants.txt")) as fh:
+    for line in fh:
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()[:2]
+            GOLDEN[k] = float(v)
+
+
+def env_state(env, prm, nq=96):
+    env = np.asarray(env, np.float64)
+    irr, levels = M.env_prefilter(env, prm.env_levels, prm.irr_w, prm.irr_h)
+    return M.EnvState(irr, levels, M.brdf_lut(prm.lut_n, nq), env.shape)
+
+
+# --------------------------------------------------------------------------
+# paper constants
+
+
+def test_paper_constants_match_defaults():
+    prm = M.Params()
+    assert prm.r_cut == GOLDEN["r_cut"]
+    assert prm.k_max == GOLDEN["k_max"]
+    assert abs(prm.gamma - GOLDEN["gamma"]) < 1e-8
+    # Eq. alpha at W = 2 pi with gamma = 2 pi (the paper prints 0.998)
+    a = 1.0 - math.exp(-prm.gamma * 2 * math.pi / (2 * math.pi))
+    assert round(a, 3) == GOLDEN["alpha_at_W_2pi_gamma_2pi"]
+
+
+# --------------------------------------------------------------------------
+# BRDF table
+
+
+def test_brdf_r_to_zero_limit():
+    """As r -> 0 the GGX lobe is a mirror and G -> 1, so beta1 -> 1 - Fc(mu)
+    and beta2 -> Fc(mu) with Fc = (1 - mu)^5 (Schlick)."""
+    mu = np.array([0.1, 0.3, 0.5, 0.7, 0.95])
+    b = M.brdf_eval(mu, 1e-4 * np.ones_like(mu), nq=128)
+    Fc = (1 - mu) ** 5
+    np.testing.assert_allclose(b[:, 0], 1 - Fc, atol=2e-6)
+    np.testing.assert_allclose(b[:, 1], Fc, atol=2e-6)
+
+
+def test_brdf_energy_bound():
+    lut = M.brdf_lut(32, 96)
+    s = lut.sum(-1)
+    assert np.all(s <= 1.0 + 1e-9) and np.all(s > 0.0)
+    # rougher surfaces lose energy to shadowing-masking at grazing angles
+    assert s[-1, 0] < s[0, -1]
+
+
+def test_brdf_quadrature_converged():
+    mu = np.array([0.02, 0.2, 0.6, 0.98, 0.5])
+    r = np.array([0.05, 0.5, 0.9, 0.3, 1.0])
+    a = M.brdf_eval(mu, r, nq=128)
+    b = M.brdf_eval(mu, r, nq=384)
+    assert np.abs(a - b).max() < 1e-7
+
+
+def test_brdf_against_monte_carlo():
+    """Independent estimate: integrate the Cook-Torrance specular term
+    f (n.l) over l directly, uniform on the hemisphere (no half-vector
+    change of variables)."""
+    rng = np.random.default_rng(7)
+    for mu, r in [(0.5, 0.5), (0.8, 0.35), (0.25, 0.8)]:
+        n_s = 2_000_000
+        z = rng.uniform(0, 1, n_s)
+        phi = rng.uniform(0, 2 * math.pi, n_s)
+        st = np.sqrt(1 - z * z)
+        l = np.stack([st * np.cos(phi), st * np.sin(phi), z], 1)
+        v = np.array([math.sqrt(1 - mu * mu), 0.0, mu])
+        h = l + v
+        h /= np.linalg.norm(h, axis=1, keepdims=True)
+        nh, vh, nl = h[:, 2], h @ v, l[:, 2]
+        a = r * r
+        D = a * a / (math.pi * (nh * nh * (a * a - 1) + 1) ** 2)
+        k = a / 2
+        G = (mu / (mu * (1 - k) + k)) * (nl / (nl * (1 - k) + k))
+        Fc = (1 - vh) ** 5
+        f = D * G / (4 * mu * nl)                  # specular BRDF without F
+        est = 2 * math.pi * f * nl                 # / pdf (1 / 2pi)
+        e1, e2 = est * (1 - Fc), est * Fc
+        ref = M.brdf_eval([mu], [r], nq=192)[0]
+        for val, e in ((ref[0], e1), (ref[1], e2)):
+            se = e.std() / math.sqrt(n_s)
+            assert abs(val - e.mean()) < 4 * se + 1e-4, (mu, r, val, e.mean(), se)
+
+
+# --------------------------------------------------------------------------
+# environment prefilter
+
+
+def test_env_constant_is_fixed_point():
+    env = np.full((32, 64, 3), 0.7)
+    irr, levels = M.env_prefilter(env, 6, 32, 16)
+    assert np.abs(irr - 0.7).max() < 1e-12
+    for lv in levels:
+        assert np.abs(lv - 0.7).max() < 1e-12
+
+
+def test_env_adjoint_dot_product():
+    rng = np.random.default_rng(3)
+    We, He = 32, 16
+    x = rng.normal(size=(He, We, 3))
+    irr, levels = M.env_prefilter(x, 4, 16, 8)
+    y_irr = rng.normal(size=irr.shape)
+    y_lv = [rng.normal(size=lv.shape) for lv in levels]
+    lhs = (irr * y_irr).sum() + sum((a * b).sum() for a, b in zip(levels, y_lv))
+    rhs = (x * M.env_adjoint(y_irr, y_lv, We, He)).sum()
+    assert abs(lhs - rhs) < 1e-10 * max(1.0, abs(lhs))
+
+
+def _dir(a, b, W, H):
+    phi = 2 * math.pi * ((a + 0.5) / W - 0.5)
+    th = math.pi * (b + 0.5) / H
+    return np.array([math.sin(th) * math.sin(phi), math.cos(th), -math.sin(th) * math.cos(phi)])
+
+
+def test_irradiance_of_cosine_lobe():
+    """Env L(w) = max(0, w.a): the cosine-weighted mean over the hemisphere
+    around a is (1/pi) Int cos^2 = 2/3; around -a it is exactly 0."""
+    We, He = 256, 128
+    Wi, Hi = 32, 16
+    ta, tb = 5, 4
+    a = _dir(ta, tb, Wi, Hi)
+    env = np.zeros((He, We, 3))
+    for b in range(He):
+        for c in range(We):
+            env[b, c, :] = max(0.0, float(_dir(c, b, We, He) @ a))
+    irr, _ = M.env_prefilter(env, 2, Wi, Hi)
+    assert abs(irr[tb, ta, 0] - 2.0 / 3.0) < 2e-3
+    # antipode of texel (ta, tb) is texel (ta + Wi/2, Hi - 1 - tb)
+    assert abs(irr[Hi - 1 - tb, (ta + Wi // 2) % Wi, 1]) < 1e-12
+
+
+def test_specular_level_sharp_limit():
+    """With many levels, level 1 has r = 1/(L-1) -> alpha = r^2 tiny and the
+    GGX-weighted average collapses onto the texel itself, i.e. the level
+    equals its box-averaged source."""
+    rng = np.random.default_rng(5)
+    env = rng.uniform(0.1, 2.0, size=(32, 64, 3))
+    _, levels = M.env_prefilter(env, 1001, 8, 4)
+    src = env.reshape(16, 2, 32, 2, 3).mean(axis=(1, 3))
+    assert np.abs(levels[1] - src).max() < 1e-9 * np.abs(src).max()
+    assert np.array_equal(levels[0], env)
+
+
+def test_specular_level_explicit_half_vector():
+    """One output texel of a rough level recomputed with the half vector
+    formed explicitly, D(n.h) with n = v = r = w_t."""
+    rng = np.random.default_rng(6)
+    env = rng.uniform(0.1, 2.0, size=(16, 32, 3))
+    L = 4
+    _, levels = M.env_prefilter(env, L, 8, 4)
+    i = 2
+    W, H = 8, 4
+    src = env.reshape(4, 4, 8, 4, 3).mean(axis=(1, 3))
+    alpha = (i / (L - 1)) ** 2
+    for (ta, tb) in [(1, 1), (6, 2)]:
+        wt = _dir(ta, tb, W, H)
+        num = np.zeros(3)
+        den = 0.0
+        for b in range(H):
+            dW = 2 * math.pi / W * (math.cos(math.pi * b / H) - math.cos(math.pi * (b + 1) / H))
+            for a in range(W):
+                wj = _dir(a, b, W, H)
+                if wt @ wj <= 0:
+                    continue
+                h = (wt + wj) / np.linalg.norm(wt + wj)
+                nh = wt @ h
+                D = alpha ** 2 / (math.pi * (nh * nh * (alpha ** 2 - 1) + 1) ** 2)
+                wgt = D * (wt @ wj) * dW
+                num += wgt * src[b, a]
+                den += wgt
+        np.testing.assert_allclose(levels[i][tb, ta], num / den, rtol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# single surfels, footprints, partition of unity
+
+
+def _render(surf, cam, env, prm, **kw):
+    return M.render_view(surf, cam, env, prm, **kw)
+
+
+def test_single_surfel_normalises_to_itself():
+    """A single-surfel layer reconstructs the surfel's own value wherever
+    its weight is nonzero (Sec. 3.5.3: C_hat = w c / w = c)."""
+    prm = M.Params()
+    surf = _tiny.surfels([[0.02, -0.01, 0.0]], normals=[[0.2, 0.1, 1.0]], scale=0.12,
+                         albedo=[[0.9, 0.3, 0.6]], rough=0.4, metal=0.3)
+    cam = _tiny.front_camera(res=48)
+    env = env_state(_tiny.lognormal_env(np.random.default_rng(1)), prm)
+    out = _render(surf, cam, env, prm)
+    a = out["rgba"][:, 3]
+    cov = a > 0
+    assert cov.sum() > 50
+    assert out["n_layers"].max() == 1
+    # shaded colour: the same for every covered pixel
+    col = out["rgba"][cov, :3] / a[cov, None]
+    assert np.abs(col - col[0]).max() < 1e-12
+    alb = out["aov"][cov, 0:3] / a[cov, None]
+    np.testing.assert_allclose(alb, np.broadcast_to([0.9, 0.3, 0.6], alb.shape), rtol=1e-6)
+    nrm = out["aov"][cov, 5:8] / a[cov, None]
+    assert np.abs(np.linalg.norm(nrm, axis=1) - 1).max() < 1e-12
+
+
+@pytest.mark.parametrize("sigma_f", [0.0, 0.5, 2.0])
+def test_footprint_integral(sigma_f):
+    """A fronto-parallel surfel of scale s at depth z maps its unit-variance
+    kernel to a screen Gaussian of std f s / z; summed over pixels the
+    weights give 2 pi (f s / z)^2, independent of sigma_f because n_f
+    preserves the kernel integral (Eq. mip_eval)."""
+    prm = M.Params(sigma_f=sigma_f, r_cut=6.0)
+    cam = _tiny.front_camera(dist=3.0, res=64)
+    f = cam.fx
+    s = 2.5 * 3.0 / f     # 2.5 px std
+    surf = _tiny.surfels([[0.0, 0.0, 0.0]], scale=s)
+    env = env_state(_tiny.const_env(), prm)
+    out = _render(surf, cam, env, prm)
+    w = -np.log1p(-out["rgba"][:, 3])            # alpha = 1 - exp(-W) (gamma = 2 pi)
+    s_px = float(np.float32(s)) * f / 3.0
+    expect = 2 * math.pi * s_px ** 2
+    assert abs(w.sum() / expect - 1) < 1e-6
+
+
+@pytest.mark.parametrize("h", [1.0, 0.5])
+def test_partition_of_unity(h):
+    """A regular grid of unit-variance kernels with spacing h (in kernel
+    units) sums to 2 pi / h^2 away from its border (Poisson summation), so
+    a densely sampled plane has layer opacity 1 - exp(-2 pi / h^2)
+    (0.998 at h = 1, Sec. 3.5.1)."""
+    prm = M.Params(r_cut=6.0)
+    cam = _tiny.front_camera(dist=3.0, res=33)
+    s = 1.5 * 3.0 / cam.fx
+    surf = _tiny.grid_plane(int(40 / h), h * s, scale=s)
+    env = env_state(_tiny.const_env(), prm)
+    out = _render(surf, cam, env, prm, pix=[16 * 33 + 16])
+    assert out["n_layers"][0] == 1
+    expect = 1 - math.exp(-2 * math.pi / h ** 2)
+    assert abs(out["rgba"][0, 3] - expect) < 1e-7
+    if h == 1.0:
+        assert round(out["rgba"][0, 3], 3) == GOLDEN["alpha_at_W_2pi_gamma_2pi"]
+
+
+def _tilt(surf, angle):
+    """Rotate every surfel's frame about the x axis (tilts the normal)."""
+    c, s = math.cos(angle / 2), math.sin(angle / 2)
+    q = surf.quat.astype(np.float64)
+    rx = np.array([c, s, 0.0, 0.0])
+    w1, x1, y1, z1 = rx
+    w2, x2, y2, z2 = q.T
+    prod = np.stack([w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2, w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+                     w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2, w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2], 1)
+    return S.Surfels(surf.pos, prod.astype(np.float32), surf.log_scale, surf.albedo, surf.roughness,
+                     surf.metallic)
+
+
+def test_two_separated_planes_make_two_layers():
+    """Two well separated planes form two layers composited front to back:
+    A = a1 + (1 - a1) a2 and the albedo channel is
+    a1 rho1 + (1 - a1) a2 rho2 (Eq. compositing)."""
+    prm = M.Params()
+    cam = _tiny.front_camera(dist=3.0, res=33)
+    s = 1.2 * 3.0 / cam.fx
+    p1 = _tiny.grid_plane(30, 1.3 * s, z=0.1, scale=s, albedo=(0.9, 0.2, 0.1))
+    p2 = _tiny.grid_plane(30, 1.3 * s, z=-0.2, scale=s, albedo=(0.1, 0.4, 0.8), center=(0.3 * s, 0.2 * s))
+    env = env_state(_tiny.const_env(), prm)
+    pix = [16 * 33 + 16, 14 * 33 + 17]
+    o1 = _render(p1, cam, env, prm, pix=pix)
+    o2 = _render(p2, cam, env, prm, pix=pix)
+    o = _render(S.Surfels.concat([p2, p1]), cam, env, prm, pix=pix)
+    a1, a2 = o1["rgba"][:, 3], o2["rgba"][:, 3]
+    assert np.all(o["n_layers"] == 2)
+    np.testing.assert_allclose(o["rgba"][:, 3], a1 + (1 - a1) * a2, rtol=1e-12)
+    expect = a1[:, None] * np.array([0.9, 0.2, 0.1]) + ((1 - a1) * a2)[:, None] * np.array([0.1, 0.4, 0.8])
+    np.testing.assert_allclose(o["aov"][:, 0:3], expect, rtol=1e-6)
+
+
+def test_thin_shell_merges():
+    """Tilted planes closer than their depth extents merge into one layer
+    (the thin-shell failure mode of Sec. 6)."""
+    prm = M.Params()
+    cam = _tiny.front_camera(dist=3.0, res=33)
+    s = 1.2 * 3.0 / cam.fx
+    p1 = _tilt(_tiny.grid_plane(30, 1.3 * s, z=0.0, scale=s), 0.6)
+    p2 = _tilt(_tiny.grid_plane(30, 1.3 * s, z=0.5 * s, scale=s, center=(0.4 * s, 0.1 * s)), 0.6)
+    env = env_state(_tiny.const_env(), prm)
+    o = _render(S.Surfels.concat([p1, p2]), cam, env, prm, pix=[16 * 33 + 16])
+    assert o["n_layers"][0] == 1
+
+
+# --------------------------------------------------------------------------
+# grouping and brute force
+
+
+def _frag_sets(surf, cam, prm, env):
+    Sd = M.to_torch_surfels(surf)
+    cd = M.cam_dict(cam)
+    rec = M.records(Sd, cd, torch.from_numpy(env.irr), [torch.from_numpy(l) for l in env.levels],
+                    torch.from_numpy(env.lut), prm)
+    rect = M.support_rect(rec, prm)
+    fr = M.fragments(rec, rect, cd["width"], cd["height"], prm)
+    return rec, rect, fr
+
+
+def test_grouping_is_connected_components():
+    """Layers of Algorithm 1 over z_start-sorted fragments are the connected
+    components of the union of the covering depth intervals (Sec. 3.2.1)."""
+    rng = np.random.default_rng(11)
+    prm = M.Params(k_max=64)
+    surf = _tiny.random_scene(rng, n=120, spread=0.4, scale=(0.02, 0.06))
+    env = env_state(_tiny.const_env(), prm)
+    rec, _, fr = _frag_sets(surf, _tiny.front_camera(res=48), prm, env)
+    zs, ze = rec["zs"].numpy(), rec["ze"].numpy()
+    n_multi = 0
+    for p in np.unique(fr.pix):
+        sel = fr.pix == p
+        sids, layers = fr.sid[sel], fr.layer[sel]
+        # union-find on interval overlap
+        parent = list(range(len(sids)))
+
+        def find(a):
+            while parent[a] != a:
+                parent[a] = parent[parent[a]]
+                a = parent[a]
+            return a
+        for i in range(len(sids)):
+            for j in range(i + 1, len(sids)):
+                a, b = sids[i], sids[j]
+                if zs[a] <= ze[b] and zs[b] <= ze[a]:
+                    parent[find(i)] = find(j)
+        roots = [find(i) for i in range(len(sids))]
+        order = sorted(set(roots), key=lambda r: min(zs[sids[i]] for i in range(len(sids)) if roots[i] == r))
+        comp = np.array([order.index(r) for r in roots])
+        assert np.array_equal(comp, layers), p
+        n_multi += layers.max() > 0
+    assert n_multi > 50
+
+
+def test_permutation_invariance():
+    rng = np.random.default_rng(12)
+    prm = M.Params()
+    surf = _tiny.random_scene(rng, n=60)
+    perm = rng.permutation(60)
+    env = env_state(_tiny.lognormal_env(rng), prm)
+    cam = _tiny.front_camera(res=24)
+    a = _render(surf, cam, env, prm)
+    b = _render(surf.subset(perm), cam, env, prm)
+    np.testing.assert_allclose(a["rgba"], b["rgba"], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(a["aov"], b["aov"], rtol=1e-12, atol=1e-14)
+
+
+def _quat_rot(q):
+    q = q / np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def brute_force(surf, cam, prm, ch):
+    """Independent tiny renderer: per pixel and surfel, intersect the pixel
+    ray with the surfel plane by a 3x3 solve, build J by differentiating
+    that intersection numerically at the surfel centre, then group by
+    connected components of depth intervals and composite."""
+    R = np.asarray(cam.R, np.float32).astype(np.float64)
+    t = np.asarray(cam.t, np.float32).astype(np.float64)
+    fx, fy, cx, cy = (float(np.float32(v)) for v in (cam.fx, cam.fy, cam.cx, cam.cy))
+    W, H = cam.width, cam.height
+    N = surf.n
+    geo = []
+    for i in range(N):
+        Rs = _quat_rot(surf.quat[i].astype(np.float64))
+        sc = np.exp(surf.log_scale[i].astype(np.float64))
+        tu, tv = R @ (sc[0] * Rs[:, 0]), R @ (sc[1] * Rs[:, 1])
+        c = R @ surf.pos[i].astype(np.float64) + t
+
+        def hit(x, y, tu=tu, tv=tv, c=c):
+            d = np.array([(x - cx) / fx, (y - cy) / fy, 1.0])
+            A = np.stack([tu, tv, -d], 1)
+            u, v, lam = np.linalg.solve(A, -c)
+            return u, v, lam
+        px, py = fx * c[0] / c[2] + cx, fy * c[1] / c[2] + cy
+        e = 1e-4
+        J = np.array([[(hit(px + e, py)[k] - hit(px - e, py)[k]) / (2 * e) for k in (0, 1)],
+                      [(hit(px, py + e)[k] - hit(px, py - e)[k]) / (2 * e) for k in (0, 1)]]).T
+        Sig = np.eye(2) + prm.sigma_f * J @ J.T
+        eps = prm.r_cut * math.hypot(tu[2], tv[2])
+        # support rectangle: sampled disc boundary U affine EWA ellipse, +1 px
+        th = np.linspace(0, 2 * math.pi, 20001)
+        P = c[None] + prm.r_cut * (np.cos(th)[:, None] * tu + np.sin(th)[:, None] * tv)
+        bx, by = fx * P[:, 0] / P[:, 2] + cx, fy * P[:, 1] / P[:, 2] + cy
+        Mj = np.linalg.inv(J)
+        MMt = Mj @ Mj.T
+        ex = prm.r_cut * np.sqrt(np.diag(MMt) + prm.sigma_f)
+        rect = (min(bx.min(), px - ex[0]) - 1, max(bx.max(), px + ex[0]) + 1,
+                min(by.min(), py - ex[1]) - 1, max(by.max(), py + ex[1]) + 1)
+        geo.append(dict(hit=hit, Sinv=np.linalg.inv(Sig), nf=1 / math.sqrt(np.linalg.det(Sig)),
+                        zs=c[2] - eps, ze=c[2] + eps, valid=(c[2] - eps) > prm.z_near, rect=rect))
+    rgba = np.zeros((W * H, 4))
+    aov = np.zeros((W * H, 9))
+    unsure = np.zeros(W * H, bool)
+    for y in range(H):
+        for x in range(W):
+            X, Y = x + 0.5, y + 0.5
+            frs = []
+            for i, g in enumerate(geo):
+                if not g["valid"]:
+                    continue
+                r = g["rect"]
+                if not (r[0] <= X <= r[1] and r[2] <= Y <= r[3]):
+                    continue
+                u, v, lam = g["hit"](X, Y)
+                if lam <= 0:
+                    continue
+                uv = np.array([u, v])
+                rho2 = uv @ g["Sinv"] @ uv
+                if abs(rho2 - prm.r_cut ** 2) < 1e-6 or min(X - r[0], r[1] - X, Y - r[2], r[3] - Y) < 1e-3:
+                    unsure[y * W + x] = True
+                if rho2 < prm.r_cut ** 2:
+                    frs.append((g["zs"], g["ze"], i, g["nf"] * math.exp(-0.5 * rho2)))
+            frs.sort(key=lambda f: (f[0], f[2]))
+            # connected components of the union of intervals, front to back
+            layers = []
+            for f in frs:
+                if layers and f[0] <= layers[-1]["zmax"]:
+                    layers[-1]["zmax"] = max(layers[-1]["zmax"], f[1])
+                    layers[-1]["f"].append(f)
+                else:
+                    layers.append(dict(zmax=f[1], f=[f]))
+            Tb = 1.0
+            out = np.zeros(12)
+            for L in layers[:prm.k_max]:
+                Wk = sum(f[3] for f in L["f"])
+                C = sum(f[3] * ch[f[2]] for f in L["f"])
+                Ch = C / Wk
+                Ch[8:11] = C[8:11] / np.linalg.norm(C[8:11])
+                al = 1 - math.exp(-prm.gamma * Wk / (2 * math.pi))
+                out += Tb * al * Ch
+                Tb *= 1 - al
+            rgba[y * W + x, :3] = out[:3] + Tb * np.asarray(prm.bg)
+            rgba[y * W + x, 3] = 1 - Tb
+            aov[y * W + x] = out[3:]
+    return rgba, aov, unsure
+
+
+@pytest.mark.parametrize("seed", [21, 22])
+def test_oracle_matches_brute_force(seed):
+    rng = np.random.default_rng(seed)
+    prm = M.Params(sigma_f=0.5 if seed == 21 else 1.5)
+    surf = _tiny.random_scene(rng, n=40, spread=0.35, scale=(0.08, 0.2))
+    cam = _tiny.front_camera(res=28)
+    env = env_state(_tiny.lognormal_env(rng), prm)
+    out = _render(surf, cam, env, prm)
+    Sd = M.to_torch_surfels(surf)
+    rec = M.records(Sd, M.cam_dict(cam), torch.from_numpy(env.irr),
+                    [torch.from_numpy(l) for l in env.levels], torch.from_numpy(env.lut), prm)
+    rgba, aov, unsure = brute_force(surf, cam, prm, rec["ch"].detach().numpy())
+    ok = ~unsure
+    assert ok.sum() > 0.95 * ok.size and (rgba[:, 3] > 0).sum() > 150
+    np.testing.assert_allclose(out["rgba"][ok], rgba[ok], rtol=1e-6, atol=1e-9)
+    np.testing.assert_allclose(out["aov"][ok], aov[ok], rtol=1e-6, atol=1e-9)
+
+
+# --------------------------------------------------------------------------
+# gradients: autograd of the oracle vs central finite differences
+
+
+def _decisions(surf, cam, env, prm):
+    rec, rect, fr = _frag_sets(surf, cam, prm, env)
+    return fr.pix.tobytes() + fr.sid.tobytes() + fr.layer.tobytes()
+
+
+def _f64(surf):
+    return S.Surfels(*(np.asarray(getattr(surf, k), np.float64).copy() for k in
+                       ("pos", "quat", "log_scale", "albedo", "roughness", "metallic")))
+
+
+def test_gradients_match_finite_differences():
+    rng = np.random.default_rng(31)
+    prm = M.Params()
+    surf = _f64(_tiny.random_scene(rng, n=24, spread=0.3, scale=(0.06, 0.16)))
+    cam = _tiny.front_camera(res=20)
+    env_base = _tiny.lognormal_env(rng).astype(np.float64)
+    env = env_state(env_base, prm)
+    P = cam.width * cam.height
+    G = rng.normal(size=(P, 13))
+    out = M.render_view(surf, cam, env, prm, G=G)
+    grads = out["grad"]
+    base_dec = _decisions(surf, cam, env, prm)
+
+    def loss(s, e):
+        o = M.render_view(s, cam, e, prm)
+        return float((np.concatenate([o["rgba"], o["aov"]], 1) * G).sum())
+
+    checked = 0
+    for name, h in [("pos", 1e-6), ("quat", 1e-6), ("log_scale", 1e-6), ("albedo", 1e-6),
+                    ("roughness", 1e-6), ("metallic", 1e-6)]:
+        arr = getattr(surf, name)
+        flat = arr.reshape(-1)
+        for idx in rng.choice(flat.size, size=min(6, flat.size), replace=False):
+            plus, minus = _f64(surf), _f64(surf)
+            getattr(plus, name).reshape(-1)[idx] += h
+            getattr(minus, name).reshape(-1)[idx] -= h
+            if _decisions(plus, cam, env, prm) != base_dec or _decisions(minus, cam, env, prm) != base_dec:
+                continue
+            fd = (loss(plus, env) - loss(minus, env)) / (2 * h)
+            an = grads[name].reshape(-1)[idx]
+            assert abs(fd - an) <= 2e-5 * max(1.0, abs(an)), (name, idx, fd, an)
+            checked += 1
+    assert checked >= 25
+    # environment texels: decisions do not depend on them
+    for idx in rng.choice(env_base.size, size=6, replace=False):
+        ep, em = env_base.copy(), env_base.copy()
+        ep.reshape(-1)[idx] += 1e-5
+        em.reshape(-1)[idx] -= 1e-5
+        fd = (loss(surf, env_state(ep, prm)) - loss(surf, env_state(em, prm))) / 2e-5
+        an = grads["env"].reshape(-1)[idx]
+        assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (idx, fd, an)
