@@ -1,0 +1,238 @@
+/*
+ * ss3d.h -- C ABI of a GB300 (sm_103a) implementation of the differentiable
+ * surfel rasteriser of "3D Surface Splatting" (3DSS, arxiv 2605.05876).
+ *
+ * Conventions for every entry point
+ *  - All pointers named *_dev are device pointers; *_host are host pointers.
+ *    The caller owns all memory.  Unless an entry point says otherwise, no
+ *    entry point allocates device memory: scratch space is the caller's
+ *    workspace (see ss_workspace_size).
+ *  - All work is enqueued on the given cudaStream_t (passed as void*; NULL is
+ *    the legacy default stream) and is asynchronous.  Entry points return
+ *    after enqueueing.
+ *  - Host-detectable errors (bad sizes, NULL pointers, a workspace that is
+ *    too small, unsupported shapes) are returned immediately and nothing is
+ *    enqueued.  Errors found on the device (instance-capacity overflow,
+ *    non-finite inputs) are OR-ed into a status word inside the workspace;
+ *    ss_read_status synchronises the stream and returns them.  No kernel
+ *    traps.
+ *  - Gradient outputs accumulate (+=); zeroing them is the caller's job.
+ *  - Float data are IEEE binary32, little-endian, C-contiguous.
+ *
+ * Geometry conventions (shared with the oracle as a specification)
+ *  - Surfel i: centre pos[i], unit quaternion quat[i] = (w, x, y, z) (it is
+ *    normalised inside), log-scales (s_u, s_v); the tangent vectors are
+ *    t_u = exp(s_u) R(q) e_x, t_v = exp(s_v) R(q) e_y and the normal is
+ *    R(q) e_z (Sec. 3.1, Sec. 3.6).  Albedo, roughness and metallic are
+ *    activated values in [0, 1].
+ *  - Camera: OpenCV pinhole, x_cam = R x_world + t, pixel (i, j) has its
+ *    centre at (i + 0.5, j + 0.5), x_pix = fx X/Z + cx.
+ *  - Environment maps are equirectangular: direction d <-> (phi, theta) with
+ *    phi = atan2(d_x, -d_z), theta = acos(d_y); texel (a, b) of a W x H map
+ *    is centred at u = (a + 0.5)/W = phi/(2 pi) + 1/2, v = (b + 0.5)/H =
+ *    theta/pi; bilinear lookups wrap in u and clamp in v.
+ */
+#ifndef SS3D_H
+#define SS3D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int ss_status;
+#define SS_OK 0
+#define SS_ERR_INVALID_ARG 1  /* bad argument; nothing was enqueued */
+#define SS_ERR_WORKSPACE 2    /* workspace smaller than ss_workspace_size */
+#define SS_ERR_CAPACITY 4     /* device: more (tile, surfel) instances than
+                                 ss_render_params.max_instances; the affected
+                                 outputs are incomplete */
+#define SS_ERR_TIMEOUT 8      /* device: a bounded wait gave up */
+#define SS_ERR_NONFINITE 16   /* device: a non-finite surfel parameter was seen
+                                 (that surfel is skipped) */
+#define SS_ERR_CUDA 32        /* a CUDA runtime call failed */
+
+#define SS_MAX_VIEWS 256
+#define SS_MAX_SCENES 64
+#define SS_KMAX_LIMIT 16      /* App. A: at most 16 composited layers */
+#define SS_N_AOV 9            /* albedo(3), roughness, metallic, normal(3), depth */
+
+/* One view.  80 bytes; arrays of it are read by both host and device. */
+typedef struct ss_camera {
+    float R[9];        /* world->camera rotation, row-major */
+    float t[3];        /* world->camera translation */
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    int32_t scene;     /* index of the scene (surfel set + env map) it shows */
+    int32_t pad_;
+} ss_camera;
+
+/* Surfel parameters of all scenes, concatenated (device, SoA). */
+typedef struct ss_surfels {
+    const float* pos;        /* [N][3] */
+    const float* quat;       /* [N][4] (w, x, y, z) */
+    const float* log_scale;  /* [N][2] (s_u, s_v) */
+    const float* albedo;     /* [N][3] */
+    const float* roughness;  /* [N] */
+    const float* metallic;   /* [N] */
+} ss_surfels;
+
+/* Gradients w.r.t. ss_surfels (device, same layout, accumulated +=).
+ * Any member may be NULL to skip it. */
+typedef struct ss_surfel_grads {
+    float* pos;
+    float* quat;
+    float* log_scale;
+    float* albedo;
+    float* roughness;
+    float* metallic;
+} ss_surfel_grads;
+
+/* A batch: several scenes, each with its surfels and views.
+ * Views must be ordered by scene (all views of scene 0 first, ...). */
+typedef struct ss_batch_desc {
+    int32_t n_scenes;                 /* 1 .. SS_MAX_SCENES */
+    int32_t n_views;                  /* 1 .. SS_MAX_VIEWS */
+    const int64_t* scene_offsets_host;/* [n_scenes + 1] surfel ranges */
+    const ss_camera* cams_host;       /* [n_views]: sizes and scene indices */
+    const ss_camera* cams_dev;        /* [n_views]: poses/intrinsics read by the
+                                         kernels (same sizes and scenes as
+                                         cams_host; may change between calls,
+                                         e.g. between CUDA-graph replays) */
+} ss_batch_desc;
+
+/* Renderer constants.  ss_default_params fills the paper's values. */
+typedef struct ss_render_params {
+    float r_cut;             /* kernel cutoff, 3 (App. A) */
+    float sigma_f;           /* screen prefilter variance of Eq. mip_cov, px^2 */
+    float gamma;             /* coverage gain of Eq. alpha, 2 pi (Sec. 3.5.1) */
+    int32_t k_max;           /* max composited layers, 16 (App. A) */
+    float z_near;            /* surfels with z_start <= z_near are culled */
+    float bg[3];             /* background radiance behind the last layer */
+    int32_t write_aov;       /* 1: also write the 9 AOV channels */
+    int32_t lut_n;           /* BRDF table resolution (n x n) */
+    int64_t max_instances;   /* capacity of the (tile, surfel) instance list */
+} ss_render_params;
+
+/* Environment map shape.  Every scene has one map of this shape. */
+typedef struct ss_env_desc {
+    int32_t width, height;   /* base map, width = 2 height, both powers of two */
+    int32_t n_levels;        /* specular levels (roughness i/(n_levels-1)) */
+    int32_t irr_width, irr_height; /* diffuse irradiance map size */
+} ss_env_desc;
+
+/* Prefiltered environment of every scene plus the BRDF table (device). */
+typedef struct ss_env_maps {
+    const float* irr;        /* [S][irr_h][irr_w][3] */
+    const float* spec;       /* [S][spec_floats]: levels back to back, each [H_i][W_i][3] */
+    const float* lut;        /* [lut_n][lut_n][2]: (beta1, beta2) at
+                                (roughness row, n.v column) cell centres */
+} ss_env_maps;
+
+/* Gradients w.r.t. the prefiltered maps (device, accumulated +=). */
+typedef struct ss_env_map_grads {
+    float* irr;              /* [S][irr_h][irr_w][3] or NULL */
+    float* spec;             /* [S][spec_floats] or NULL */
+} ss_env_map_grads;
+
+/* ---------------------------------------------------------------------- */
+
+/* Fill p with the paper's constants (r_cut 3, gamma 2 pi, K_max 16) and this
+ * library's defaults for what the paper leaves open (sigma_f 0.5 px^2,
+ * z_near 0.01, black background, AOVs on, 128 x 128 BRDF table).
+ * max_instances is set to 0; size it with ss_count_instances or a bound. */
+void ss_default_params(ss_render_params* p);
+
+/* Human-readable text for the lowest set bit of a status. */
+const char* ss_error_string(ss_status s);
+
+/* Split-sum BRDF table of Eq. ibl: (beta1, beta2) with F0 beta1 + beta2 the
+ * specular factor (Sec. 3.4.2), for isotropic GGX (alpha = r^2) with the
+ * Smith-Schlick G (k = alpha/2) and Schlick Fresnel:
+ *   beta1 = Int D G (v.h) (1 - (1 - v.h)^5) / (n.v) dh,
+ *   beta2 = Int D G (v.h) (1 - v.h)^5 / (n.v) dh   over n.l > 0,
+ * evaluated at cell centres r = (row + 0.5)/n, n.v = (col + 0.5)/n.
+ * lut_dev: [n][n][2] floats.  n in [4, 1024].  Deterministic. */
+ss_status ss_brdf_lut(float* lut_dev, int32_t n, void* stream);
+
+/* Sizes (in floats) of the prefiltered maps of ONE scene, and of the
+ * scratch that ss_env_prefilter keeps for the backward pass. */
+ss_status ss_env_sizes(const ss_env_desc* d, int64_t* irr_floats, int64_t* spec_floats,
+                       int64_t* aux_floats);
+
+/* Environment prefilter (Sec. 3.4.2: "pre-convolved diffuse environment
+ * map" queried along n; specular radiance "pre-filtered ... at a MIP level
+ * determined by the roughness"):
+ *   irradiance  L_d(n_t) = sum_j L_j max(0, n_t.w_j) dW_j / sum_j max(0, n_t.w_j) dW_j
+ *               over all base texels j;
+ *   level 0     the base map;
+ *   level i>=1  roughness r_i = i/(n_levels-1), size (max(W>>i,8), max(H>>i,4)),
+ *               source S = base box-averaged to that size,
+ *               L_i(w_t) = sum_j S_j D(h_j) max(0, w_t.w_j) dW_j / sum_j D(h_j) max(0, w_t.w_j) dW_j
+ *               with GGX D at alpha = r_i^2 and (n.h_j)^2 = (1 + w_t.w_j)/2.
+ * env_dev: [n_envs][H][W][3].  Writes irr, spec and aux (normalisers and
+ * box-averaged sources, read by ss_env_prefilter_backward). */
+ss_status ss_env_prefilter(const ss_env_desc* d, int32_t n_envs, const float* env_dev,
+                           float* irr_dev, float* spec_dev, float* aux_dev, void* stream);
+
+/* Transpose of ss_env_prefilter: d_env += P^T (d_irr, d_spec).  aux_dev is
+ * the scratch written by the forward call for the same env maps. */
+ss_status ss_env_prefilter_backward(const ss_env_desc* d, int32_t n_envs, const float* d_irr_dev,
+                                    const float* d_spec_dev, const float* aux_dev, float* d_env_dev,
+                                    void* stream);
+
+/* Workspace bytes for a render of this batch.  with_backward != 0 adds the
+ * per-pixel layer state that ss_render_backward reads.  Requires
+ * p->max_instances > 0. */
+ss_status ss_workspace_size(const ss_batch_desc* b, const ss_render_params* p, int32_t with_backward,
+                            size_t* bytes);
+
+/* Exact number of (tile, surfel) instances of a batch: runs the projection
+ * step into `ws` and reads the count back (synchronises the stream).  Use it
+ * to size max_instances.  `ws` must be at least ss_workspace_size bytes for
+ * the same batch with max_instances = 1. */
+ss_status ss_count_instances(const ss_batch_desc* b, const ss_surfels* s, const ss_render_params* p,
+                             const ss_env_desc* ed, const ss_env_maps* env, void* ws, size_t ws_bytes,
+                             int64_t* count, void* stream);
+
+/* Forward render (Sec. 3, Fig. 2 stages 1-5 without tone mapping):
+ * per surfel and view the T-matrix (Sec. 3.1), depth interval, centre-
+ * precomputed MIP filter (Eq. mip_weight) and forward split-sum shading
+ * (Eq. ibl); binning into 16 x 16 tiles sorted by z_start (Sec. 3.2.1);
+ * per pixel Algorithm 1 with Eq. alpha coverage and Eq. compositing, at most
+ * K_max layers.  Surfel i covers pixel x iff x lies in its support rectangle
+ * (the projected r_cut disc of App. A united with the r_cut bounds of the
+ * screen-space EWA ellipse M M^T + sigma_f I, padded 1 px) and
+ * rho2_mip(x) < r_cut^2.
+ * Outputs (device): out_rgba [P][4] (linear radiance composited over bg, and
+ * coverage 1 - T_{K+1}), out_aov [9][P] planar (may be NULL if
+ * p->write_aov == 0), where P = sum over views of width*height and view v's
+ * pixels start at the running sum over earlier views, row-major.
+ * The workspace keeps what ss_render_backward needs. */
+ss_status ss_render_forward(const ss_batch_desc* b, const ss_surfels* s, const ss_render_params* p,
+                            const ss_env_desc* ed, const ss_env_maps* env, float* out_rgba_dev,
+                            float* out_aov_dev, void* ws, size_t ws_bytes, void* stream);
+
+/* Backward of ss_render_forward (App. A "Backward Pass"): replays each
+ * pixel's grouping front to back against the layer totals kept by the
+ * forward call and accumulates the gradient of L = sum(d_rgba * rgba) +
+ * sum(d_aov * aov) w.r.t. the surfel parameters and the prefiltered maps.
+ * All discrete decisions (support, cutoff, grouping, K_max) are held fixed.
+ * d_aov may be NULL.  out_rgba/out_aov are the forward outputs.  Must follow
+ * a ss_render_forward with with_backward workspace and the same inputs. */
+ss_status ss_render_backward(const ss_batch_desc* b, const ss_surfels* s, const ss_render_params* p,
+                             const ss_env_desc* ed, const ss_env_maps* env, const float* out_rgba_dev,
+                             const float* out_aov_dev, const float* d_rgba_dev, const float* d_aov_dev,
+                             ss_surfel_grads* g, ss_env_map_grads* genv, void* ws, size_t ws_bytes,
+                             void* stream);
+
+/* Synchronise the stream and return (and clear) the device status word in
+ * ws: SS_OK or an OR of SS_ERR_CAPACITY / SS_ERR_TIMEOUT / SS_ERR_NONFINITE. */
+ss_status ss_read_status(void* ws, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SS3D_H */

@@ -1,0 +1,114 @@
+"""ctypes binding of libss3d.so (include/ss3d.h).  Argument marshalling only:
+every step of the renderer runs in the library's CUDA kernels.  Loading fails
+loudly when the library is missing; there is no CPU fallback."""
+from __future__ import annotations
+
+import ctypes
+import os
+from functools import lru_cache
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libss3d.so")
+
+c_f = ctypes.c_float
+c_i32 = ctypes.c_int32
+c_i64 = ctypes.c_int64
+c_vp = ctypes.c_void_p
+fp = ctypes.POINTER(ctypes.c_float)
+
+SS_OK = 0
+SS_ERR_INVALID_ARG = 1
+SS_ERR_WORKSPACE = 2
+SS_ERR_CAPACITY = 4
+SS_ERR_TIMEOUT = 8
+SS_ERR_NONFINITE = 16
+SS_ERR_CUDA = 32
+SS_MAX_VIEWS = 256
+SS_MAX_SCENES = 64
+SS_N_AOV = 9
+
+
+class ss_camera(ctypes.Structure):
+    _fields_ = [("R", c_f * 9), ("t", c_f * 3), ("fx", c_f), ("fy", c_f), ("cx", c_f), ("cy", c_f),
+                ("width", c_i32), ("height", c_i32), ("scene", c_i32), ("pad_", c_i32)]
+
+
+class ss_surfels(ctypes.Structure):
+    _fields_ = [("pos", c_vp), ("quat", c_vp), ("log_scale", c_vp), ("albedo", c_vp), ("roughness", c_vp),
+                ("metallic", c_vp)]
+
+
+class ss_surfel_grads(ctypes.Structure):
+    _fields_ = [("pos", c_vp), ("quat", c_vp), ("log_scale", c_vp), ("albedo", c_vp), ("roughness", c_vp),
+                ("metallic", c_vp)]
+
+
+class ss_batch_desc(ctypes.Structure):
+    _fields_ = [("n_scenes", c_i32), ("n_views", c_i32), ("scene_offsets_host", ctypes.POINTER(c_i64)),
+                ("cams_host", ctypes.POINTER(ss_camera)), ("cams_dev", c_vp)]
+
+
+class ss_render_params(ctypes.Structure):
+    _fields_ = [("r_cut", c_f), ("sigma_f", c_f), ("gamma", c_f), ("k_max", c_i32), ("z_near", c_f),
+                ("bg", c_f * 3), ("write_aov", c_i32), ("lut_n", c_i32), ("max_instances", c_i64)]
+
+
+class ss_env_desc(ctypes.Structure):
+    _fields_ = [("width", c_i32), ("height", c_i32), ("n_levels", c_i32), ("irr_width", c_i32),
+                ("irr_height", c_i32)]
+
+
+class ss_env_maps(ctypes.Structure):
+    _fields_ = [("irr", c_vp), ("spec", c_vp), ("lut", c_vp)]
+
+
+class ss_env_map_grads(ctypes.Structure):
+    _fields_ = [("irr", c_vp), ("spec", c_vp)]
+
+
+EXPORTS = {
+    "ss_default_params": (None, [ctypes.POINTER(ss_render_params)]),
+    "ss_error_string": (ctypes.c_char_p, [c_i32]),
+    "ss_brdf_lut": (c_i32, [c_vp, c_i32, c_vp]),
+    "ss_env_sizes": (c_i32, [ctypes.POINTER(ss_env_desc), ctypes.POINTER(c_i64), ctypes.POINTER(c_i64),
+                             ctypes.POINTER(c_i64)]),
+    "ss_env_prefilter": (c_i32, [ctypes.POINTER(ss_env_desc), c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "ss_env_prefilter_backward": (c_i32, [ctypes.POINTER(ss_env_desc), c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "ss_workspace_size": (c_i32, [ctypes.POINTER(ss_batch_desc), ctypes.POINTER(ss_render_params), c_i32,
+                                  ctypes.POINTER(ctypes.c_size_t)]),
+    "ss_count_instances": (c_i32, [ctypes.POINTER(ss_batch_desc), ctypes.POINTER(ss_surfels),
+                                   ctypes.POINTER(ss_render_params), ctypes.POINTER(ss_env_desc),
+                                   ctypes.POINTER(ss_env_maps), c_vp, ctypes.c_size_t, ctypes.POINTER(c_i64),
+                                   c_vp]),
+    "ss_render_forward": (c_i32, [ctypes.POINTER(ss_batch_desc), ctypes.POINTER(ss_surfels),
+                                  ctypes.POINTER(ss_render_params), ctypes.POINTER(ss_env_desc),
+                                  ctypes.POINTER(ss_env_maps), c_vp, c_vp, c_vp, ctypes.c_size_t, c_vp]),
+    "ss_render_backward": (c_i32, [ctypes.POINTER(ss_batch_desc), ctypes.POINTER(ss_surfels),
+                                   ctypes.POINTER(ss_render_params), ctypes.POINTER(ss_env_desc),
+                                   ctypes.POINTER(ss_env_maps), c_vp, c_vp, c_vp, c_vp,
+                                   ctypes.POINTER(ss_surfel_grads), ctypes.POINTER(ss_env_map_grads), c_vp,
+                                   ctypes.c_size_t, c_vp]),
+    "ss_read_status": (c_i32, [c_vp, c_vp]),
+}
+
+
+class SS3DError(RuntimeError):
+    pass
+
+
+@lru_cache(maxsize=1)
+def lib() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise SS3DError(f"libss3d.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    return L
+
+
+def check(status: int, what: str = ""):
+    if status != SS_OK:
+        msg = lib().ss_error_string(status).decode()
+        raise SS3DError(f"{what}: {msg} (status {status})")

@@ -1,0 +1,192 @@
+"""Device-resident front end over the C ABI.
+
+``Renderer`` keeps one batch (surfels of one or more scenes, their views,
+one environment map per scene) in HBM as torch tensors and calls the
+library's entry points on torch's current CUDA stream.  PyTorch provides the
+memory and the stream; all arithmetic runs in libss3d.so.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import numpy as np
+
+from . import _lib as C
+from ._lib import check, lib
+
+SURFEL_FIELDS = ("pos", "quat", "log_scale", "albedo", "roughness", "metallic")
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def make_cameras(cams) -> ctypes.Array:
+    arr = (C.ss_camera * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i].R[:] = [float(v) for v in np.asarray(c.R, np.float32).ravel()]
+        arr[i].t[:] = [float(v) for v in np.asarray(c.t, np.float32).ravel()]
+        arr[i].fx, arr[i].fy, arr[i].cx, arr[i].cy = (float(np.float32(v)) for v in (c.fx, c.fy, c.cx, c.cy))
+        arr[i].width, arr[i].height, arr[i].scene = int(c.width), int(c.height), int(c.scene)
+    return arr
+
+
+def default_params(**overrides) -> C.ss_render_params:
+    p = C.ss_render_params()
+    lib().ss_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if k == "bg":
+            p.bg[:] = list(v)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class Renderer:
+    """One batch resident on the GPU.
+
+    scene: ``paper_2605_05876_gb300.scenes.Scene`` (numpy inputs).
+    params: overrides of ss_render_params fields (r_cut, sigma_f, ...).
+    """
+
+    def __init__(self, scene, params: dict | None = None, env_levels: int = 6, irr_size=(32, 16),
+                 with_backward: bool = True, capacity_slack: float = 1.3, device: str = "cuda"):
+        import torch
+        self.torch = torch
+        self.dev = torch.device(device)
+        self.scene = scene
+        s = scene.surfels
+        f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(self.dev)
+        self.params_t = {k: f32(getattr(s, k)) for k in SURFEL_FIELDS}
+        self.n_surfels = s.n
+        self.n_views = len(scene.cameras)
+        self.n_scenes = scene.n_scenes
+        self._cams_host = make_cameras(scene.cameras)
+        self.cams_dev = torch.frombuffer(bytearray(bytes(self._cams_host)), dtype=torch.uint8).to(self.dev)
+        self._offsets = (ctypes.c_int64 * (self.n_scenes + 1))(*[int(v) for v in scene.scene_offsets])
+        self.desc = C.ss_batch_desc(self.n_scenes, self.n_views, self._offsets, self._cams_host,
+                                    ctypes.c_void_p(self.cams_dev.data_ptr()))
+        self.sizes = [(int(c.width), int(c.height)) for c in scene.cameras]
+        self.pixel_offsets = np.concatenate([[0], np.cumsum([w * h for w, h in self.sizes])]).astype(np.int64)
+        self.n_pixels = int(self.pixel_offsets[-1])
+        # environment
+        He, We, _ = scene.envs[0].shape
+        self.ed = C.ss_env_desc(We, He, env_levels, irr_size[0], irr_size[1])
+        ni, ns, na = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        check(lib().ss_env_sizes(ctypes.byref(self.ed), ctypes.byref(ni), ctypes.byref(ns), ctypes.byref(na)),
+              "ss_env_sizes")
+        S = self.n_scenes
+        self.env = torch.from_numpy(np.stack([np.asarray(e, np.float32) for e in scene.envs])).to(self.dev)
+        self.irr = torch.zeros(S, ni.value, device=self.dev)
+        self.spec = torch.zeros(S, ns.value, device=self.dev)
+        self.aux = torch.zeros(S, na.value, device=self.dev)
+        self.prm = default_params(**(params or {}))
+        self.lut = torch.zeros(self.prm.lut_n, self.prm.lut_n, 2, device=self.dev)
+        check(lib().ss_brdf_lut(_ptr(self.lut), self.prm.lut_n, _stream()), "ss_brdf_lut")
+        self.prefilter_env()
+        self.maps = C.ss_env_maps(_ptr(self.irr), _ptr(self.spec), _ptr(self.lut))
+        # outputs
+        self.rgba = torch.zeros(self.n_pixels, 4, device=self.dev)
+        self.aov = torch.zeros(C.SS_N_AOV, self.n_pixels, device=self.dev)
+        self.with_backward = with_backward
+        self.capacity_slack = capacity_slack
+        self.ws = None
+        self.plan_capacity()
+
+    # -- surfel parameters as the ABI struct
+    def surfels_struct(self) -> C.ss_surfels:
+        p = self.params_t
+        return C.ss_surfels(*(ctypes.c_void_p(p[k].data_ptr()) for k in SURFEL_FIELDS))
+
+    def prefilter_env(self):
+        check(lib().ss_env_prefilter(ctypes.byref(self.ed), self.n_scenes, _ptr(self.env), _ptr(self.irr),
+                                     _ptr(self.spec), _ptr(self.aux), _stream()), "ss_env_prefilter")
+
+    def plan_capacity(self, max_instances: int | None = None):
+        torch = self.torch
+        if max_instances is None:
+            probe = default_params()
+            ctypes.memmove(ctypes.byref(probe), ctypes.byref(self.prm), ctypes.sizeof(probe))
+            probe.max_instances = 1
+            nb = ctypes.c_size_t()
+            check(lib().ss_workspace_size(ctypes.byref(self.desc), ctypes.byref(probe), 0, ctypes.byref(nb)),
+                  "ss_workspace_size")
+            ws = torch.empty(nb.value + 256, dtype=torch.uint8, device=self.dev)
+            cnt = ctypes.c_int64()
+            check(lib().ss_count_instances(ctypes.byref(self.desc), ctypes.byref(self.surfels_struct()),
+                                           ctypes.byref(self.prm), ctypes.byref(self.ed), ctypes.byref(self.maps),
+                                           _ptr(ws), nb.value, ctypes.byref(cnt), _stream()), "ss_count_instances")
+            self.counted_instances = int(cnt.value)
+            max_instances = int(math.ceil(cnt.value * self.capacity_slack)) + 4096
+            del ws
+        self.prm.max_instances = max_instances
+        nb = ctypes.c_size_t()
+        check(lib().ss_workspace_size(ctypes.byref(self.desc), ctypes.byref(self.prm), int(self.with_backward),
+                                      ctypes.byref(nb)), "ss_workspace_size")
+        self.ws_bytes = nb.value
+        self.ws = torch.empty(nb.value, dtype=torch.uint8, device=self.dev)
+
+    def forward(self):
+        check(lib().ss_render_forward(ctypes.byref(self.desc), ctypes.byref(self.surfels_struct()),
+                                      ctypes.byref(self.prm), ctypes.byref(self.ed), ctypes.byref(self.maps),
+                                      _ptr(self.rgba), _ptr(self.aov), _ptr(self.ws), self.ws_bytes, _stream()),
+              "ss_render_forward")
+        return self.rgba, self.aov
+
+    def zero_grads(self):
+        torch = self.torch
+        self.grads = {k: torch.zeros_like(v) for k, v in self.params_t.items()}
+        self.d_irr = torch.zeros_like(self.irr)
+        self.d_spec = torch.zeros_like(self.spec)
+        self.d_env = torch.zeros_like(self.env)
+
+    def backward(self, d_rgba, d_aov=None, env_grad: bool = True):
+        """Accumulate gradients of sum(d_rgba * rgba) + sum(d_aov * aov) into
+        self.grads (surfel params) and self.d_env (base env texels)."""
+        if not hasattr(self, "grads"):
+            self.zero_grads()
+        g = C.ss_surfel_grads(*(ctypes.c_void_p(self.grads[k].data_ptr()) for k in SURFEL_FIELDS))
+        ge = C.ss_env_map_grads(_ptr(self.d_irr), _ptr(self.d_spec))
+        check(lib().ss_render_backward(ctypes.byref(self.desc), ctypes.byref(self.surfels_struct()),
+                                       ctypes.byref(self.prm), ctypes.byref(self.ed), ctypes.byref(self.maps),
+                                       _ptr(self.rgba), _ptr(self.aov), _ptr(d_rgba.contiguous()),
+                                       _ptr(d_aov.contiguous() if d_aov is not None else None), ctypes.byref(g),
+                                       ctypes.byref(ge), _ptr(self.ws), self.ws_bytes, _stream()),
+              "ss_render_backward")
+        if env_grad:
+            check(lib().ss_env_prefilter_backward(ctypes.byref(self.ed), self.n_scenes, _ptr(self.d_irr),
+                                                  _ptr(self.d_spec), _ptr(self.aux), _ptr(self.d_env), _stream()),
+                  "ss_env_prefilter_backward")
+        return self.grads
+
+    def read_status(self) -> int:
+        return int(lib().ss_read_status(_ptr(self.ws), _stream()))
+
+    def set_cameras(self, cams):
+        """Replace the views' poses/intrinsics (same sizes and scenes)."""
+        arr = make_cameras(cams)
+        for i, c in enumerate(cams):
+            if (c.width, c.height, c.scene) != (self._cams_host[i].width, self._cams_host[i].height,
+                                                 self._cams_host[i].scene):
+                raise ValueError("set_cameras keeps sizes and scenes")
+        src = self.torch.frombuffer(bytearray(bytes(arr)), dtype=self.torch.uint8)
+        self.cams_dev.copy_(src, non_blocking=False)
+        ctypes.memmove(self._cams_host, arr, ctypes.sizeof(arr))
+
+    # -- views of the outputs
+    def view_slice(self, v: int) -> slice:
+        return slice(int(self.pixel_offsets[v]), int(self.pixel_offsets[v + 1]))
+
+    def view_rgba(self, v: int):
+        w, h = self.sizes[v]
+        return self.rgba[self.view_slice(v)].reshape(h, w, 4)
+
+    def view_aov(self, v: int):
+        w, h = self.sizes[v]
+        return self.aov[:, self.view_slice(v)].reshape(C.SS_N_AOV, h, w)

@@ -1,0 +1,332 @@
+// C ABI entry points (include/ss3d.h): argument checks, batch layout,
+// workspace carving and the launch sequences.
+#include <math.h>
+#include <string.h>
+
+#include "ss3d_internal.cuh"
+
+#define CK(x)                                      \
+    do {                                           \
+        if ((x) != cudaSuccess) return SS_ERR_CUDA; \
+    } while (0)
+
+static inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+extern "C" void ss_default_params(ss_render_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->r_cut = 3.f;
+    p->sigma_f = 0.5f;
+    p->gamma = 6.28318530717958647692f;
+    p->k_max = 16;
+    p->z_near = 0.01f;
+    p->write_aov = 1;
+    p->lut_n = 128;
+    p->max_instances = 0;
+}
+
+extern "C" const char* ss_error_string(ss_status s) {
+    if (s == SS_OK) return "ok";
+    if (s & SS_ERR_INVALID_ARG) return "invalid argument";
+    if (s & SS_ERR_WORKSPACE) return "workspace too small";
+    if (s & SS_ERR_CAPACITY) return "instance capacity exceeded";
+    if (s & SS_ERR_TIMEOUT) return "device wait timed out";
+    if (s & SS_ERR_NONFINITE) return "non-finite surfel parameter";
+    if (s & SS_ERR_CUDA) return "CUDA runtime error";
+    return "unknown status";
+}
+
+// ------------------------------------------------------------------------
+// batch layout
+
+static ss_status build_layout(const ss_batch_desc* b, const ss_render_params* p, ss_layout* L) {
+    if (!b || !p || !L) return SS_ERR_INVALID_ARG;
+    if (b->n_scenes < 1 || b->n_scenes > SS_MAX_SCENES) return SS_ERR_INVALID_ARG;
+    if (b->n_views < 1 || b->n_views > SS_MAX_VIEWS) return SS_ERR_INVALID_ARG;
+    if (!b->scene_offsets_host || !b->cams_host) return SS_ERR_INVALID_ARG;
+    if (p->k_max < 1 || p->k_max > SS_KMAX_LIMIT) return SS_ERR_INVALID_ARG;
+    if (!(p->r_cut > 0.f) || !(p->sigma_f >= 0.f) || !(p->gamma > 0.f) || p->lut_n < 2) return SS_ERR_INVALID_ARG;
+    memset(L, 0, sizeof(*L));
+    L->n_views = b->n_views;
+    L->n_scenes = b->n_scenes;
+    L->k_max = p->k_max;
+    for (int s = 0; s <= b->n_scenes; ++s) {
+        L->scene_begin[s] = b->scene_offsets_host[s];
+        if (s > 0 && L->scene_begin[s] < L->scene_begin[s - 1]) return SS_ERR_INVALID_ARG;
+    }
+    if (L->scene_begin[0] != 0) return SS_ERR_INVALID_ARG;
+    for (int s = 0; s <= SS_MAX_SCENES; ++s) L->scene_view_begin[s] = b->n_views;
+    int prev_scene = -1;
+    int64_t pix = 0, rec = 0;
+    int tiles = 0;
+    for (int v = 0; v < b->n_views; ++v) {
+        const ss_camera& c = b->cams_host[v];
+        if (c.scene < 0 || c.scene >= b->n_scenes || c.scene < prev_scene) return SS_ERR_INVALID_ARG;
+        if (c.width < 1 || c.height < 1 || c.width > 32768 || c.height > 32768) return SS_ERR_INVALID_ARG;
+        if (!(c.fx > 0.f) || !(c.fy > 0.f)) return SS_ERR_INVALID_ARG;
+        for (int s = prev_scene + 1; s <= c.scene; ++s) L->scene_view_begin[s] = v;
+        prev_scene = c.scene;
+        ss_view_layout& vl = L->v[v];
+        vl.scene = c.scene;
+        vl.width = c.width;
+        vl.height = c.height;
+        vl.tiles_x = (c.width + SS_TILE - 1) / SS_TILE;
+        vl.tiles_y = (c.height + SS_TILE - 1) / SS_TILE;
+        vl.tile_off = tiles;
+        vl.pixel_off = pix;
+        vl.rec_off = rec;
+        vl.surfel_begin = L->scene_begin[c.scene];
+        int64_t ns = L->scene_begin[c.scene + 1] - L->scene_begin[c.scene];
+        if (ns > 0x7fffffffll) return SS_ERR_INVALID_ARG;
+        vl.n_surfels = (int32_t)ns;
+        tiles += vl.tiles_x * vl.tiles_y;
+        pix += (int64_t)c.width * c.height;
+        rec += ns;
+    }
+    for (int s = prev_scene + 1; s <= SS_MAX_SCENES; ++s) L->scene_view_begin[s] = b->n_views;
+    L->total_tiles = tiles;
+    L->total_pixels = pix;
+    L->total_records = rec;
+    return SS_OK;
+}
+
+struct ws_plan {
+    size_t status, layout, rec, tc, ts, tcur, keys, keys_alt, layer, pix, grad, total;
+};
+
+static ws_plan plan_ws(const ss_layout& L, const ss_render_params& p, int with_bwd) {
+    ws_plan w;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes, 256);
+        return at;
+    };
+    w.status = take(256);
+    w.layout = take(sizeof(ss_layout));
+    w.rec = take(sizeof(ss_rec) * (size_t)L.total_records);
+    w.tc = take(sizeof(uint32_t) * (size_t)L.total_tiles);
+    w.ts = take(sizeof(uint32_t) * ((size_t)L.total_tiles + 1));
+    w.tcur = take(sizeof(uint32_t) * (size_t)L.total_tiles);
+    w.keys = take(sizeof(unsigned long long) * (size_t)p.max_instances);
+    w.keys_alt = take(sizeof(unsigned long long) * (size_t)p.max_instances);
+    if (with_bwd) {
+        w.layer = take(sizeof(float) * (size_t)p.k_max * 13 * (size_t)L.total_pixels);
+        w.pix = take(sizeof(float) * 2 * (size_t)L.total_pixels);
+        w.grad = take(sizeof(float) * SS_NGRAD * (size_t)L.total_records);
+    } else {
+        w.layer = w.pix = w.grad = 0;
+    }
+    w.total = o;
+    return w;
+}
+
+static ss_ws_view carve(void* ws, const ws_plan& w, const ss_render_params& p, int with_bwd) {
+    char* b = (char*)ws;
+    ss_ws_view v;
+    v.status = (int*)(b + w.status);
+    v.layout = (ss_layout*)(b + w.layout);
+    v.rec = (ss_rec*)(b + w.rec);
+    v.tile_count = (uint32_t*)(b + w.tc);
+    v.tile_start = (uint32_t*)(b + w.ts);
+    v.tile_cursor = (uint32_t*)(b + w.tcur);
+    v.keys = (unsigned long long*)(b + w.keys);
+    v.keys_alt = (unsigned long long*)(b + w.keys_alt);
+    v.layer_state = with_bwd ? (float*)(b + w.layer) : nullptr;
+    v.pix_state = with_bwd ? (float*)(b + w.pix) : nullptr;
+    v.grad_rec = with_bwd ? (float*)(b + w.grad) : nullptr;
+    v.max_instances = p.max_instances;
+    return v;
+}
+
+__global__ void set_layout_kernel(ss_layout* dst, ss_layout src) {
+    const int* s = reinterpret_cast<const int*>(&src);
+    int* d = reinterpret_cast<int*>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(ss_layout) / sizeof(int)); i += blockDim.x) d[i] = s[i];
+}
+
+extern "C" ss_status ss_workspace_size(const ss_batch_desc* b, const ss_render_params* p, int32_t with_backward,
+                                       size_t* bytes) {
+    if (!bytes || !p || p->max_instances <= 0 || p->max_instances > 0xffffffffll) return SS_ERR_INVALID_ARG;
+    static ss_layout L;
+    ss_status st = build_layout(b, p, &L);
+    if (st) return st;
+    *bytes = plan_ws(L, *p, with_backward).total;
+    return SS_OK;
+}
+
+// ------------------------------------------------------------------------
+// BRDF table and environment
+
+extern "C" ss_status ss_brdf_lut(float* lut_dev, int32_t n, void* stream) {
+    if (!lut_dev || n < 4 || n > 1024) return SS_ERR_INVALID_ARG;
+    ss_launch_brdf_lut(lut_dev, n, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return SS_OK;
+}
+
+static bool env_desc_ok(const ss_env_desc* d) {
+    if (!d) return false;
+    auto pow2 = [](int x) { return x > 0 && (x & (x - 1)) == 0; };
+    return pow2(d->width) && pow2(d->height) && d->width >= 8 && d->height >= 4 && d->width <= 16384 &&
+           d->height <= 8192 && d->n_levels >= 1 && d->n_levels <= 16 && d->irr_width >= 1 && d->irr_height >= 1 &&
+           d->irr_width <= 1024 && d->irr_height <= 512;
+}
+
+extern "C" ss_status ss_env_sizes(const ss_env_desc* d, int64_t* irr_floats, int64_t* spec_floats,
+                                  int64_t* aux_floats) {
+    if (!env_desc_ok(d)) return SS_ERR_INVALID_ARG;
+    if (irr_floats) *irr_floats = ss_env_irr_floats(d);
+    if (spec_floats) *spec_floats = ss_env_spec_floats(d);
+    if (aux_floats) *aux_floats = ss_env_aux_floats(d);
+    return SS_OK;
+}
+
+extern "C" ss_status ss_env_prefilter(const ss_env_desc* d, int32_t n_envs, const float* env_dev, float* irr_dev,
+                                      float* spec_dev, float* aux_dev, void* stream) {
+    if (!env_desc_ok(d) || n_envs < 1 || !env_dev || !irr_dev || !spec_dev || !aux_dev) return SS_ERR_INVALID_ARG;
+    if (d->n_levels < 2 && d->n_levels != 1) return SS_ERR_INVALID_ARG;
+    ss_launch_env_prefilter(d, n_envs, env_dev, irr_dev, spec_dev, aux_dev, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return SS_OK;
+}
+
+extern "C" ss_status ss_env_prefilter_backward(const ss_env_desc* d, int32_t n_envs, const float* d_irr_dev,
+                                               const float* d_spec_dev, const float* aux_dev, float* d_env_dev,
+                                               void* stream) {
+    if (!env_desc_ok(d) || n_envs < 1 || !aux_dev || !d_env_dev) return SS_ERR_INVALID_ARG;
+    ss_launch_env_prefilter_bwd(d, n_envs, d_irr_dev, d_spec_dev, aux_dev, d_env_dev, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    return SS_OK;
+}
+
+// ------------------------------------------------------------------------
+// render
+
+static ss_status check_render_args(const ss_batch_desc* b, const ss_surfels* s, const ss_render_params* p,
+                                   const ss_env_desc* ed, const ss_env_maps* env, void* ws) {
+    if (!b || !s || !p || !ed || !env || !ws || !b->cams_dev) return SS_ERR_INVALID_ARG;
+    if (!s->pos || !s->quat || !s->log_scale || !s->albedo || !s->roughness || !s->metallic) return SS_ERR_INVALID_ARG;
+    if (!env->irr || !env->spec || !env->lut || !env_desc_ok(ed)) return SS_ERR_INVALID_ARG;
+    if (((uintptr_t)s->quat & 15) || ((uintptr_t)s->log_scale & 7) || ((uintptr_t)ws & 255)) return SS_ERR_INVALID_ARG;
+    if (p->max_instances <= 0 || p->max_instances > 0xffffffffll) return SS_ERR_INVALID_ARG;
+    return SS_OK;
+}
+
+static ss_status forward_core(const ss_batch_desc* b, const ss_surfels* s, const ss_render_params* p,
+                              const ss_env_desc* ed, const ss_env_maps* env, float* out_rgba, float* out_aov,
+                              void* ws, size_t ws_bytes, int with_bwd, int stop_after_count, cudaStream_t st,
+                              ss_layout& L, ss_ws_view& W) {
+    ss_status e = check_render_args(b, s, p, ed, env, ws);
+    if (e) return e;
+    e = build_layout(b, p, &L);
+    if (e) return e;
+    ws_plan plan = plan_ws(L, *p, with_bwd);
+    if (ws_bytes < plan.total) return SS_ERR_WORKSPACE;
+    W = carve(ws, plan, *p, with_bwd);
+    ss_fwd_args a;
+    a.s = *s;
+    a.p = *p;
+    a.ed = *ed;
+    a.env = *env;
+    a.cams = b->cams_dev;
+    a.out_rgba = out_rgba;
+    a.out_aov = p->write_aov ? out_aov : nullptr;
+    a.with_backward = with_bwd;
+    CK(cudaMemsetAsync(W.status, 0, sizeof(int), st));
+    set_layout_kernel<<<1, 256, 0, st>>>(W.layout, L);
+    CK(cudaMemsetAsync(W.tile_count, 0, sizeof(uint32_t) * (size_t)L.total_tiles, st));
+    CK(cudaMemsetAsync(W.tile_cursor, 0, sizeof(uint32_t) * (size_t)L.total_tiles, st));
+    ss_launch_project(W, L, a, st);
+    if (stop_after_count) {
+        ss_launch_bin_sort(W, L, a, st);  // scan gives the total; scatter is bounded by capacity
+        CK(cudaGetLastError());
+        return SS_OK;
+    }
+    ss_launch_bin_sort(W, L, a, st);
+    ss_launch_raster_fwd(W, L, a, st);
+    CK(cudaGetLastError());
+    return SS_OK;
+}
+
+extern "C" ss_status ss_render_forward(const ss_batch_desc* b, const ss_surfels* s, const ss_render_params* p,
+                                       const ss_env_desc* ed, const ss_env_maps* env, float* out_rgba_dev,
+                                       float* out_aov_dev, void* ws, size_t ws_bytes, void* stream) {
+    if (!out_rgba_dev || (p && p->write_aov && !out_aov_dev)) return SS_ERR_INVALID_ARG;
+    ss_layout L;
+    ss_ws_view W;
+    // the workspace decides whether backward state is kept: use the larger plan if it fits
+    int with_bwd = 0;
+    if (b && p && p->max_instances > 0) {
+        static ss_layout Lt;
+        if (build_layout(b, p, &Lt) == SS_OK && ws_bytes >= plan_ws(Lt, *p, 1).total) with_bwd = 1;
+    }
+    return forward_core(b, s, p, ed, env, out_rgba_dev, out_aov_dev, ws, ws_bytes, with_bwd, 0,
+                        (cudaStream_t)stream, L, W);
+}
+
+extern "C" ss_status ss_count_instances(const ss_batch_desc* b, const ss_surfels* s, const ss_render_params* p,
+                                        const ss_env_desc* ed, const ss_env_maps* env, void* ws, size_t ws_bytes,
+                                        int64_t* count, void* stream) {
+    if (!count || !p) return SS_ERR_INVALID_ARG;
+    ss_render_params q = *p;
+    q.max_instances = 1;
+    ss_layout L;
+    ss_ws_view W;
+    cudaStream_t st = (cudaStream_t)stream;
+    ss_status e = forward_core(b, s, &q, ed, env, nullptr, nullptr, ws, ws_bytes, 0, 1, st, L, W);
+    if (e) return e;
+    uint32_t total = 0;
+    CK(cudaMemcpyAsync(&total, W.tile_start + L.total_tiles, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *count = (int64_t)total;
+    return SS_OK;
+}
+
+extern "C" ss_status ss_render_backward(const ss_batch_desc* b, const ss_surfels* s, const ss_render_params* p,
+                                        const ss_env_desc* ed, const ss_env_maps* env, const float* out_rgba_dev,
+                                        const float* out_aov_dev, const float* d_rgba_dev, const float* d_aov_dev,
+                                        ss_surfel_grads* g, ss_env_map_grads* genv, void* ws, size_t ws_bytes,
+                                        void* stream) {
+    ss_status e = check_render_args(b, s, p, ed, env, ws);
+    if (e) return e;
+    if (!out_rgba_dev || !d_rgba_dev || !g) return SS_ERR_INVALID_ARG;
+    if (p->write_aov && d_aov_dev && !out_aov_dev) return SS_ERR_INVALID_ARG;
+    static ss_layout L;
+    e = build_layout(b, p, &L);
+    if (e) return e;
+    ws_plan plan = plan_ws(L, *p, 1);
+    if (ws_bytes < plan.total) return SS_ERR_WORKSPACE;
+    ss_ws_view W = carve(ws, plan, *p, 1);
+    cudaStream_t st = (cudaStream_t)stream;
+    ss_bwd_args a;
+    a.f.s = *s;
+    a.f.p = *p;
+    a.f.ed = *ed;
+    a.f.env = *env;
+    a.f.cams = b->cams_dev;
+    a.f.out_rgba = nullptr;
+    a.f.out_aov = nullptr;
+    a.f.with_backward = 1;
+    a.out_rgba = out_rgba_dev;
+    a.out_aov = p->write_aov ? out_aov_dev : nullptr;
+    a.d_rgba = d_rgba_dev;
+    a.d_aov = p->write_aov ? d_aov_dev : nullptr;
+    a.g = *g;
+    ss_env_map_grads ge = {nullptr, nullptr};
+    a.genv = genv ? *genv : ge;
+    CK(cudaMemsetAsync(W.grad_rec, 0, sizeof(float) * SS_NGRAD * (size_t)L.total_records, st));
+    ss_launch_raster_bwd(W, L, a, st);
+    ss_launch_project_bwd(W, L, a, st);
+    CK(cudaGetLastError());
+    return SS_OK;
+}
+
+extern "C" ss_status ss_read_status(void* ws, void* stream) {
+    if (!ws) return SS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int v = 0;
+    CK(cudaMemcpyAsync(&v, ws, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return (ss_status)v;
+}

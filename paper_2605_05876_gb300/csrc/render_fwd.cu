@@ -1,0 +1,587 @@
+// Forward render: projection + shading, tile binning, per-tile depth sort and
+// the fused per-pixel rasteriser (Algorithm 1 with coverage compositing).
+#include <math.h>
+
+#include "ss3d_internal.cuh"
+
+// ------------------------------------------------------------------------
+// projection (Sec. 3.1), centre-precomputed MIP filter (Sec. 3.3.2) and
+// forward split-sum shading (Sec. 3.4.2) for one surfel and every view of its
+// scene.  One thread per surfel: the 64 B of parameters are read once per
+// batch and one 112 B record is written per view.
+
+struct ss_env_ptrs {
+    const float* irr;
+    const float* spec;
+    const float* lut;
+};
+
+__device__ __forceinline__ float3 tex3(const float* T, int i) { return make_float3(T[i * 3], T[i * 3 + 1], T[i * 3 + 2]); }
+
+__device__ __forceinline__ float3 bilerp3(const float* T, ss_taps t) {
+    float3 a = tex3(T, t.i00), b = tex3(T, t.i01), c = tex3(T, t.i10), d = tex3(T, t.i11);
+    float w00 = (1.f - t.fx) * (1.f - t.fy), w01 = t.fx * (1.f - t.fy), w10 = (1.f - t.fx) * t.fy, w11 = t.fx * t.fy;
+    return make_float3(w00 * a.x + w01 * b.x + w10 * c.x + w11 * d.x, w00 * a.y + w01 * b.y + w10 * c.y + w11 * d.y,
+                       w00 * a.z + w01 * b.z + w10 * c.z + w11 * d.z);
+}
+
+// level offsets of the specular stack (floats)
+__device__ __forceinline__ int64_t spec_level_off(const ss_env_desc& ed, int i, int& W, int& H) {
+    int64_t off = 0;
+    for (int k = 0; k < i; ++k) {
+        int w = max(ed.width >> k, 8), h = max(ed.height >> k, 4);
+        off += (int64_t)w * h * 3;
+    }
+    W = max(ed.width >> i, 8);
+    H = max(ed.height >> i, 4);
+    return off;
+}
+
+__global__ void __launch_bounds__(256) project_kernel(ss_ws_view ws, ss_fwd_args a, int64_t n_total) {
+    const ss_layout* L = ws.layout;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_total) return;
+    int scene = 0;
+    while (scene + 1 < L->n_scenes && i >= L->scene_begin[scene + 1]) ++scene;
+    const float* P = a.s.pos + i * 3;
+    float c0 = P[0], c1 = P[1], c2 = P[2];
+    float4 q = *reinterpret_cast<const float4*>(a.s.quat + i * 4);
+    float2 ls = *reinterpret_cast<const float2*>(a.s.log_scale + i * 2);
+    float rho0 = a.s.albedo[i * 3], rho1 = a.s.albedo[i * 3 + 1], rho2 = a.s.albedo[i * 3 + 2];
+    float rough = a.s.roughness[i], metal = a.s.metallic[i];
+    bool finite = isfinite(c0) && isfinite(c1) && isfinite(c2) && isfinite(q.x) && isfinite(q.y) && isfinite(q.z) &&
+                  isfinite(q.w) && isfinite(ls.x) && isfinite(ls.y) && isfinite(rho0) && isfinite(rho1) &&
+                  isfinite(rho2) && isfinite(rough) && isfinite(metal) &&
+                  (q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w) > 0.f;
+    if (!finite) atomicOr(ws.status, SS_ERR_NONFINITE);
+    float Rq[9];
+    quat_rot(q.x, q.y, q.z, q.w, Rq);
+    const float su = expf(ls.x), sv = expf(ls.y);
+    const float tu[3] = {su * Rq[0], su * Rq[3], su * Rq[6]};
+    const float tv[3] = {sv * Rq[1], sv * Rq[4], sv * Rq[7]};
+    const float nrm[3] = {Rq[2], Rq[5], Rq[8]};
+    const float rc = a.p.r_cut, rc2 = rc * rc, sig = a.p.sigma_f;
+    const int nL = a.ed.n_levels;
+    const int64_t irr_stride = (int64_t)a.ed.irr_width * a.ed.irr_height * 3;
+    int64_t spec_stride = 0;
+    {
+        int W, H;
+        spec_stride = spec_level_off(a.ed, nL, W, H);
+    }
+    const float* irr = a.env.irr + scene * irr_stride;
+    const float* spec = a.env.spec + scene * spec_stride;
+    const int lutn = a.p.lut_n;
+
+    for (int v = L->scene_view_begin[scene]; v < L->scene_view_begin[scene + 1]; ++v) {
+        const ss_view_layout& vl = L->v[v];
+        const ss_camera& cam = a.cams[v];
+        const int64_t local = i - vl.surfel_begin;
+        ss_rec rec;
+        uint32_t flags = 0;
+        // camera-space centre in double-float, camera-space tangents in FP32
+        dfl cx_ = df_dot3_add(cam.R[0], cam.R[1], cam.R[2], c0, c1, c2, cam.t[0]);
+        dfl cy_ = df_dot3_add(cam.R[3], cam.R[4], cam.R[5], c0, c1, c2, cam.t[1]);
+        dfl cz_ = df_dot3_add(cam.R[6], cam.R[7], cam.R[8], c0, c1, c2, cam.t[2]);
+        float tuc[3], tvc[3];
+        for (int r = 0; r < 3; ++r) {
+            tuc[r] = cam.R[r * 3] * tu[0] + cam.R[r * 3 + 1] * tu[1] + cam.R[r * 3 + 2] * tu[2];
+            tvc[r] = cam.R[r * 3] * tv[0] + cam.R[r * 3 + 1] * tv[1] + cam.R[r * 3 + 2] * tv[2];
+        }
+        const float cz = cz_.hi + cz_.lo;
+        const float eps = rc * sqrtf(tuc[2] * tuc[2] + tvc[2] * tvc[2]);   // Sec. 3.1 depth extent
+        const float zs = __fadd_rn(__fsub_rn(cz_.hi, eps), cz_.lo);
+        const float ze = __fadd_rn(__fadd_rn(cz_.hi, eps), cz_.lo);
+        // centre in pixels (double-float): p = f c'_xy / c'_z + c
+        dfl mx = df_div(cx_, cz_), my = df_div(cy_, cz_);
+        dfl px = df_add_f(df_mul_f(mx, cam.fx), cam.cx);
+        dfl py = df_add_f(df_mul_f(my, cam.fy), cam.cy);
+        const float mxf = mx.hi, myf = my.hi;
+        // screen-plane derivatives of the tangents: a = t'_u - m t'_uz, b = t'_v - m t'_vz
+        const float ax = tuc[0] - mxf * tuc[2], ay = tuc[1] - myf * tuc[2];
+        const float bx = tvc[0] - mxf * tvc[2], by = tvc[1] - myf * tvc[2];
+        const float det0 = ax * by - bx * ay;
+        bool valid = finite && (zs > a.p.z_near) && (det0 != 0.f) && isfinite(det0);
+        const float fx = cam.fx, fy = cam.fy;
+        // normalised homogeneous ray coefficients (s / C2):  u = s0/s2, v = s1/s2 with
+        // s0 = J00 dx + J01 dy, s1 = J10 dx + J11 dy, s2 = A2 dx + B2 dy + 1, J = d(u,v)/d(x,y) at the centre
+        const float id = 1.f / det0;
+        const float J00 = by * cz * id / fx, J01 = -bx * cz * id / fy;
+        const float J10 = -ay * cz * id / fx, J11 = ax * cz * id / fy;
+        const float A2 = (tvc[2] * ay - tuc[2] * by) * id / fx;
+        const float B2 = (tuc[2] * bx - tvc[2] * ax) * id / fy;
+        // MIP filter at the centre (Eq. mip_cov) in the stable form
+        // Sigma^-1 = G (G + sig I)^-1, n_f = sqrt(det G / det(G + sig I)), G = M^T M, M = J^-1
+        const float icz = 1.f / cz;
+        const float fx2 = fx * fx, fy2 = fy * fy, icz2 = icz * icz;
+        const float Guu = (fx2 * ax * ax + fy2 * ay * ay) * icz2;
+        const float Guv = (fx2 * ax * bx + fy2 * ay * by) * icz2;
+        const float Gvv = (fx2 * bx * bx + fy2 * by * by) * icz2;
+        const float sdg = fx * fy * det0 * icz2;
+        const float detG = sdg * sdg;
+        const float Dn = detG + sig * (Guu + Gvv) + sig * sig;
+        const float iD = 1.f / Dn;
+        const float Sa = (detG + sig * Guu) * iD, Sb = sig * Guv * iD, Sc = (detG + sig * Gvv) * iD;
+        const float nf = sqrtf(detG * iD);
+        // whitening factor F with F^T F = Sigma^-1 (pivoted Cholesky; det Sigma^-1 = n_f^2)
+        float P00, P01, P10, P11;
+        if (Sa >= Sc) {
+            float f00 = sqrtf(Sa), f01 = Sb / f00, f11 = nf / f00;
+            P00 = f00 * J00 + f01 * J10; P01 = f00 * J01 + f01 * J11;
+            P10 = f11 * J10; P11 = f11 * J11;
+        } else {
+            float g11 = sqrtf(Sc), g10 = Sb / g11, g00 = nf / g11;
+            P00 = g11 * J10 + g10 * J00; P01 = g11 * J11 + g10 * J01;
+            P10 = g00 * J00; P11 = g00 * J01;
+        }
+        // support rectangle (centred pixel offsets): exact bounds of the projected r_cut
+        // disc (dual conic, App. A) U r_cut bounds of the EWA ellipse M M^T + sig I, +1 px
+        const float C00 = fx2 * (ax * ax + bx * bx), C02 = fx * (ax * tuc[2] + bx * tvc[2]);
+        const float C11 = fy2 * (ay * ay + by * by), C12 = fy * (ay * tuc[2] + by * tvc[2]);
+        const float C22 = tuc[2] * tuc[2] + tvc[2] * tvc[2] - cz * cz / rc2;
+        float lo[2], hi[2];
+        {
+            const float Caa[2] = {C00, C11}, Ca2[2] = {C02, C12};
+            for (int ax_ = 0; ax_ < 2; ++ax_) {
+                float dsc = sqrtf(fmaxf(Ca2[ax_] * Ca2[ax_] - Caa[ax_] * C22, 0.f));
+                float r0 = (Ca2[ax_] + dsc) / C22, r1 = (Ca2[ax_] - dsc) / C22;
+                float ext = rc * sqrtf(Caa[ax_] * icz2 + sig);
+                lo[ax_] = fminf(fminf(r0, r1), -ext) - 1.f;
+                hi[ax_] = fmaxf(fmaxf(r0, r1), ext) + 1.f;
+            }
+        }
+        valid = valid && (C22 < 0.f);
+        int i0 = (int)ceilf(px.hi + lo[0] - 0.5f), i1 = (int)floorf(px.hi + hi[0] - 0.5f);
+        int j0 = (int)ceilf(py.hi + lo[1] - 0.5f), j1 = (int)floorf(py.hi + hi[1] - 0.5f);
+        i0 = max(i0, 0); j0 = max(j0, 0);
+        i1 = min(i1, vl.width - 1); j1 = min(j1, vl.height - 1);
+        valid = valid && (i0 <= i1) && (j0 <= j1) && isfinite(px.hi) && isfinite(py.hi);
+        if (valid) {
+            // does the exact filtered support {u^T Sigma^-1 u < r^2} stay inside the rectangle?
+            // dual conic H adj(Q_f) H^T with adj(Q_f) ~ [[r^2 Sc, -r^2 Sb, 0], [-r^2 Sb, r^2 Sa, 0], [0, 0, -n_f^2]]
+            const float h[3][3] = {{fx * ax, fx * bx, 0.f}, {fy * ay, fy * by, 0.f}, {tuc[2], tvc[2], cz}};
+            float Cf[3][3];
+            for (int r = 0; r < 3; ++r)
+                for (int c = r; c < 3; ++c) {
+                    float val = rc2 * (Sc * h[r][0] * h[c][0] - Sb * (h[r][0] * h[c][1] + h[r][1] * h[c][0]) +
+                                       Sa * h[r][1] * h[c][1]) -
+                                nf * nf * h[r][2] * h[c][2];
+                    Cf[r][c] = val;
+                }
+            bool inside = Cf[2][2] < 0.f;
+            for (int ax_ = 0; ax_ < 2 && inside; ++ax_) {
+                float caa = Cf[ax_][ax_], ca2 = Cf[ax_][2], c22 = Cf[2][2];
+                float dsc = sqrtf(fmaxf(ca2 * ca2 - caa * c22, 0.f));
+                float r0 = (ca2 + dsc) / c22, r1 = (ca2 - dsc) / c22;
+                inside = (fminf(r0, r1) > lo[ax_] + 0.25f) && (fmaxf(r0, r1) < hi[ax_] - 0.25f);
+            }
+            if (!inside) flags |= SS_FLAG_RECT_TEST;
+            flags |= SS_FLAG_VALID;
+        }
+        // forward shading (Eq. ibl): one pre-shaded colour per surfel and view
+        const float ox = -(cam.R[0] * cam.t[0] + cam.R[3] * cam.t[1] + cam.R[6] * cam.t[2]);
+        const float oy = -(cam.R[1] * cam.t[0] + cam.R[4] * cam.t[1] + cam.R[7] * cam.t[2]);
+        const float oz = -(cam.R[2] * cam.t[0] + cam.R[5] * cam.t[1] + cam.R[8] * cam.t[2]);
+        float wo[3] = {ox - c0, oy - c1, oz - c2};
+        {
+            float inv = rsqrtf(wo[0] * wo[0] + wo[1] * wo[1] + wo[2] * wo[2]);
+            wo[0] *= inv; wo[1] *= inv; wo[2] *= inv;
+        }
+        float ns[3] = {nrm[0], nrm[1], nrm[2]};
+        float facing = ns[0] * wo[0] + ns[1] * wo[1] + ns[2] * wo[2];
+        if (facing < 0.f) {
+            ns[0] = -ns[0]; ns[1] = -ns[1]; ns[2] = -ns[2];
+            facing = -facing;
+            flags |= SS_FLAG_FLIPPED;
+        }
+        const float mu = fminf(fmaxf(facing, 0.f), 1.f);
+        const float refl[3] = {2.f * facing * ns[0] - wo[0], 2.f * facing * ns[1] - wo[1], 2.f * facing * ns[2] - wo[2]};
+        float3 col = make_float3(0.f, 0.f, 0.f);
+        if (valid) {
+            float u, vv;
+            dir_to_uv(ns[0], ns[1], ns[2], u, vv);
+            float3 Ld = bilerp3(irr, bilinear_taps(u, vv, a.ed.irr_width, a.ed.irr_height, true));
+            dir_to_uv(refl[0], refl[1], refl[2], u, vv);
+            float lc = fminf(fmaxf(rough, 0.f), 1.f) * (float)(nL - 1);
+            int l0 = min((int)floorf(lc), nL - 1), l1 = min(l0 + 1, nL - 1);
+            float lf = lc - (float)l0;
+            int W0, H0, W1, H1;
+            int64_t o0 = spec_level_off(a.ed, l0, W0, H0), o1 = spec_level_off(a.ed, l1, W1, H1);
+            float3 s0 = bilerp3(spec + o0, bilinear_taps(u, vv, W0, H0, true));
+            float3 s1 = bilerp3(spec + o1, bilinear_taps(u, vv, W1, H1, true));
+            float3 Ls = make_float3((1.f - lf) * s0.x + lf * s1.x, (1.f - lf) * s0.y + lf * s1.y,
+                                    (1.f - lf) * s0.z + lf * s1.z);
+            ss_taps lt = bilinear_taps(mu, fminf(fmaxf(rough, 0.f), 1.f), lutn, lutn, false);
+            const float* LUT = a.env.lut;
+            float w00 = (1.f - lt.fx) * (1.f - lt.fy), w01 = lt.fx * (1.f - lt.fy), w10 = (1.f - lt.fx) * lt.fy,
+                  w11 = lt.fx * lt.fy;
+            float be1 = w00 * LUT[lt.i00 * 2] + w01 * LUT[lt.i01 * 2] + w10 * LUT[lt.i10 * 2] + w11 * LUT[lt.i11 * 2];
+            float be2 = w00 * LUT[lt.i00 * 2 + 1] + w01 * LUT[lt.i01 * 2 + 1] + w10 * LUT[lt.i10 * 2 + 1] +
+                        w11 * LUT[lt.i11 * 2 + 1];
+            const float rho[3] = {rho0, rho1, rho2};
+            float cc[3];
+            const float Lda[3] = {Ld.x, Ld.y, Ld.z}, Lsa[3] = {Ls.x, Ls.y, Ls.z};
+            for (int k = 0; k < 3; ++k) {
+                float F0 = 0.04f * (1.f - metal) + rho[k] * metal;
+                float kd = (1.f - F0) * (1.f - metal);
+                cc[k] = kd * rho[k] * Lda[k] + Lsa[k] * (F0 * be1 + be2);
+            }
+            col = make_float3(cc[0], cc[1], cc[2]);
+        }
+        rec.r0 = make_float4(P00, P01, P10, P11);
+        rec.r1 = make_float4(A2, B2, 1.f, nf);
+        rec.r2 = make_float4(px.hi, py.hi, px.lo, py.lo);
+        rec.r3 = make_float4(zs, ze, __uint_as_float(valid ? pack16(i0, i1) : 0xffffu),
+                             __uint_as_float(valid ? pack16(j0, j1) : 0xffffu));
+        rec.r4 = make_float4(col.x, col.y, col.z, __uint_as_float(flags));
+        rec.r5 = make_float4(rho0, rho1, rho2, rough);
+        rec.r6 = make_float4(metal, ns[0], ns[1], ns[2]);
+        ws.rec[vl.rec_off + local] = rec;
+        if (valid) {
+            int tx0 = i0 / SS_TILE, tx1 = i1 / SS_TILE, ty0 = j0 / SS_TILE, ty1 = j1 / SS_TILE;
+            for (int ty = ty0; ty <= ty1; ++ty)
+                for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&ws.tile_count[vl.tile_off + ty * vl.tiles_x + tx], 1u);
+        }
+    }
+}
+
+void ss_launch_project(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st) {
+    int64_t n = L.scene_begin[L.n_scenes];
+    if (n <= 0) return;
+    project_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ws, a, n);
+}
+
+// ------------------------------------------------------------------------
+// binning: exclusive scan of tile counts, scatter of (z_start, id) keys,
+// per-tile sort by (z_start, id) (Sec. 3.2.1: sort key z_start; ties by id)
+
+__global__ void __launch_bounds__(1024) scan_kernel(const uint32_t* cnt, uint32_t* start, int n, int* status,
+                                                    int64_t cap) {
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int base = 0; base < n; base += blockDim.x) {
+        int i = base + threadIdx.x;
+        uint32_t v = i < n ? cnt[i] : 0u;
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            uint32_t s = wsum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            wsum[lane] = s;
+        }
+        __syncthreads();
+        uint32_t excl = carry + (w > 0 ? wsum[w - 1] : 0u) + x - v;
+        if (i < n) start[i] = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        start[n] = carry;
+        if ((int64_t)carry > cap) atomicOr(status, SS_ERR_CAPACITY);
+    }
+}
+
+__global__ void __launch_bounds__(256) scatter_kernel(ss_ws_view ws, int64_t total_records) {
+    const ss_layout* L = ws.layout;
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= total_records) return;
+    int v = 0;
+    while (v + 1 < L->n_views && r >= L->v[v + 1].rec_off) ++v;
+    const ss_view_layout& vl = L->v[v];
+    float4 r3 = ws.rec[r].r3;
+    uint32_t flags = __float_as_uint(ws.rec[r].r4.w);
+    if (!(flags & SS_FLAG_VALID)) return;
+    uint32_t rx = __float_as_uint(r3.z), ry = __float_as_uint(r3.w);
+    int i0 = rx & 0xffff, i1 = rx >> 16, j0 = ry & 0xffff, j1 = ry >> 16;
+    unsigned long long key = ((unsigned long long)__float_as_uint(r3.x) << 32) | (uint32_t)(r - vl.rec_off);
+    for (int ty = j0 / SS_TILE; ty <= j1 / SS_TILE; ++ty)
+        for (int tx = i0 / SS_TILE; tx <= i1 / SS_TILE; ++tx) {
+            int t = vl.tile_off + ty * vl.tiles_x + tx;
+            uint32_t pos = ws.tile_start[t] + atomicAdd(&ws.tile_cursor[t], 1u);
+            if ((int64_t)pos < ws.max_instances) ws.keys[pos] = key;
+        }
+}
+
+#define SORT_THREADS 512
+#define SORT_CAP 8192  // keys sorted in shared memory at once (64 KB)
+
+__device__ void bitonic_smem(unsigned long long* s, int npow2) {
+    for (int k = 2; k <= npow2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < npow2; i += blockDim.x) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    unsigned long long a = s[i], b = s[ixj];
+                    bool up = (i & k) == 0;
+                    if ((a > b) == up) {
+                        s[i] = b;
+                        s[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// merge two sorted runs A[0,na) and B[0,nb) into out, all threads of the CTA
+__device__ void merge_runs(const unsigned long long* A, int na, const unsigned long long* B, int nb,
+                           unsigned long long* out) {
+    const int n = na + nb;
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    int d0 = min(n, (int)threadIdx.x * per), d1 = min(n, d0 + per);
+    if (d0 >= d1) return;
+    // merge path: find i in A with i + j = d0
+    int lo = max(0, d0 - nb), hi = min(d0, na);
+    while (lo < hi) {
+        int m = (lo + hi) >> 1;
+        if (A[m] < B[d0 - 1 - m]) lo = m + 1;
+        else hi = m;
+    }
+    int ia = lo, ib = d0 - lo;
+    for (int d = d0; d < d1; ++d) {
+        bool takeA = ib >= nb || (ia < na && A[ia] < B[ib]);
+        out[d] = takeA ? A[ia++] : B[ib++];
+    }
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) tile_sort_kernel(ss_ws_view ws, int total_tiles) {
+    extern __shared__ unsigned long long sk[];
+    const int t = blockIdx.x;
+    const int64_t cap = ws.max_instances;
+    int64_t b = ws.tile_start[t], e = ws.tile_start[t + 1];
+    if (e > cap) e = cap;
+    if (b >= e) return;
+    const int n = (int)(e - b);
+    if (n == 1) return;
+    unsigned long long* K = ws.keys + b;
+    unsigned long long* Alt = ws.keys_alt + b;
+    // chunks of SORT_CAP sorted in shared memory
+    for (int c0 = 0; c0 < n; c0 += SORT_CAP) {
+        int m = min(SORT_CAP, n - c0);
+        int p2 = 1;
+        while (p2 < m) p2 <<= 1;
+        for (int i = threadIdx.x; i < p2; i += blockDim.x) sk[i] = i < m ? K[c0 + i] : ~0ull;
+        __syncthreads();
+        bitonic_smem(sk, p2);
+        for (int i = threadIdx.x; i < m; i += blockDim.x) K[c0 + i] = sk[i];
+        __syncthreads();
+    }
+    if (n <= SORT_CAP) return;
+    // pairwise merges in global memory, ping-pong between K and Alt
+    unsigned long long *src = K, *dst = Alt;
+    for (int w = SORT_CAP; w < n; w <<= 1) {
+        for (int lo = 0; lo < n; lo += 2 * w) {
+            int na = min(w, n - lo), nb = min(w, max(0, n - lo - w));
+            if (nb == 0) {
+                for (int i = threadIdx.x; i < na; i += blockDim.x) dst[lo + i] = src[lo + i];
+            } else {
+                merge_runs(src + lo, na, src + lo + w, nb, dst + lo);
+            }
+        }
+        __syncthreads();
+        unsigned long long* tmp = src;
+        src = dst;
+        dst = tmp;
+    }
+    if (src != K) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) K[i] = src[i];
+    }
+}
+
+void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st) {
+    (void)a;
+    scan_kernel<<<1, 1024, 0, st>>>(ws.tile_count, ws.tile_start, L.total_tiles, ws.status, ws.max_instances);
+    if (L.total_records > 0)
+        scatter_kernel<<<(unsigned)((L.total_records + 255) / 256), 256, 0, st>>>(ws, L.total_records);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(tile_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             SORT_CAP * (int)sizeof(unsigned long long));
+        attr = true;
+    }
+    tile_sort_kernel<<<L.total_tiles, SORT_THREADS, SORT_CAP * sizeof(unsigned long long), st>>>(ws, L.total_tiles);
+}
+
+// ------------------------------------------------------------------------
+// per-pixel rasteriser (Algorithm 1, Eq. alpha, Eq. compositing)
+
+#define RB 256  // instances staged per batch (one per thread)
+
+struct ss_stage {
+    float4 r0[RB];   // primed J rows
+    float4 r1[RB];   // A2, B2, 1, n_f
+    float4 pz[RB];   // centre relative to the tile origin (x, y), z_start, z_end
+    uint4 meta[RB];  // rect_x, rect_y, flags, -
+    float4 c0[RB];   // rgb, albedo r
+    float4 c1[RB];   // albedo g, b, roughness, metallic
+    float4 c2[RB];   // normal xyz, depth
+};
+
+__device__ __forceinline__ int find_view(const ss_layout* L, int tile) {
+    int lo = 0, hi = L->n_views - 1;
+    while (lo < hi) {
+        int m = (lo + hi + 1) >> 1;
+        if (L->v[m].tile_off <= tile) lo = m;
+        else hi = m - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void stage_instance(ss_stage& S, int slot, const ss_rec& rc, float tx0, float ty0) {
+    S.r0[slot] = rc.r0;
+    S.r1[slot] = rc.r1;
+    // centre relative to the tile origin, from the double-float centre
+    float prx = __fadd_rn(__fsub_rn(rc.r2.x, tx0), rc.r2.z);
+    float pry = __fadd_rn(__fsub_rn(rc.r2.y, ty0), rc.r2.w);
+    S.pz[slot] = make_float4(prx, pry, rc.r3.x, rc.r3.y);
+    S.meta[slot] = make_uint4(__float_as_uint(rc.r3.z), __float_as_uint(rc.r3.w), __float_as_uint(rc.r4.w), 0u);
+    S.c0[slot] = make_float4(rc.r4.x, rc.r4.y, rc.r4.z, rc.r5.x);
+    S.c1[slot] = make_float4(rc.r5.y, rc.r5.z, rc.r5.w, rc.r6.x);
+    S.c2[slot] = make_float4(rc.r6.y, rc.r6.z, rc.r6.w, 0.5f * (rc.r3.x + rc.r3.y));
+}
+
+__global__ void __launch_bounds__(256) raster_fwd_kernel(ss_ws_view ws, ss_fwd_args a) {
+    __shared__ ss_stage S;
+    const ss_layout* L = ws.layout;
+    const int tile = blockIdx.x;
+    const int view = find_view(L, tile);
+    const ss_view_layout& vl = L->v[view];
+    const int lt = tile - vl.tile_off;
+    const int tx = lt % vl.tiles_x, ty = lt / vl.tiles_x;
+    const int x0 = tx * SS_TILE, y0 = ty * SS_TILE;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wx0 = 8 * (warp & 1), wy0 = 4 * (warp >> 1);         // 8 x 4 pixel block per warp
+    const int lx = wx0 + (lane & 7), ly = wy0 + (lane >> 3);
+    const int px = x0 + lx, py = y0 + ly;
+    const bool inside = px < vl.width && py < vl.height;
+    const int gx0 = x0 + wx0, gx1 = gx0 + 7, gy0 = y0 + wy0, gy1 = gy0 + 3;
+    const float xl = (float)lx + 0.5f, yl = (float)ly + 0.5f;
+    const float rc2 = a.p.r_cut * a.p.r_cut;
+    const float kw = a.p.gamma * (0.5f / SS_PI_F);
+    const int kmax = a.p.k_max;
+    const int64_t gpix = vl.pixel_off + (int64_t)py * vl.width + px;
+    const int64_t P = L->total_pixels;
+
+    float C[SS_NCH];
+#pragma unroll
+    for (int c = 0; c < SS_NCH; ++c) C[c] = 0.f;
+    float out[SS_NCH];
+#pragma unroll
+    for (int c = 0; c < SS_NCH; ++c) out[c] = 0.f;
+    float Wg = 0.f, zmax = 0.f, Tb = 1.f, Acov = 0.f;
+    int K = 0;
+    bool done = !inside;
+
+    auto flush = [&]() {
+        const float invW = 1.f / Wg;
+        float hat[SS_NCH];
+#pragma unroll
+        for (int c = 0; c < SS_NCH; ++c) hat[c] = C[c] * invW;
+        const float nl = sqrtf(C[8] * C[8] + C[9] * C[9] + C[10] * C[10]);
+        const float inl = nl > 0.f ? 1.f / nl : 0.f;
+        hat[8] = C[8] * inl; hat[9] = C[9] * inl; hat[10] = C[10] * inl;   // renormalised normal
+        const float al = -expm1f(-kw * Wg);                                   // Eq. alpha
+        const float tw = Tb * al;
+#pragma unroll
+        for (int c = 0; c < SS_NCH; ++c) out[c] = fmaf(tw, hat[c], out[c]);  // Eq. compositing
+        if (a.with_backward) {
+            float* ls = ws.layer_state + (int64_t)K * 13 * P + gpix;
+#pragma unroll
+            for (int c = 0; c < SS_NCH; ++c) ls[c * P] = C[c];
+            ls[12 * P] = Wg;
+        }
+        Acov = fmaf(Tb, al, Acov);
+        Tb *= expf(-kw * Wg);
+        ++K;
+#pragma unroll
+        for (int c = 0; c < SS_NCH; ++c) C[c] = 0.f;
+        Wg = 0.f;
+        zmax = 0.f;
+        if (K >= kmax) done = true;
+    };
+
+    const int64_t cap = ws.max_instances;
+    int64_t beg = ws.tile_start[tile], end = ws.tile_start[tile + 1];
+    if (end > cap) end = cap;
+    if (beg > end) beg = end;
+    const ss_rec* recs = ws.rec + vl.rec_off;
+    for (int64_t base = beg; base < end; base += RB) {
+        const int nb = (int)min((int64_t)RB, end - base);
+        __syncthreads();
+        if ((int)threadIdx.x < nb) {
+            uint32_t id = (uint32_t)(ws.keys[base + threadIdx.x] & 0xffffffffull);
+            stage_instance(S, threadIdx.x, recs[id], (float)x0, (float)y0);
+        }
+        __syncthreads();
+        if (__all_sync(0xffffffffu, done)) continue;
+        for (int c0 = 0; c0 < nb; c0 += 32) {
+            const int j = c0 + lane;
+            bool ov = false;
+            if (j < nb) {
+                uint4 m = S.meta[j];
+                int i0 = m.x & 0xffff, i1 = m.x >> 16, j0 = m.y & 0xffff, j1 = m.y >> 16;
+                ov = i0 <= gx1 && i1 >= gx0 && j0 <= gy1 && j1 >= gy0;
+            }
+            uint32_t mask = __ballot_sync(0xffffffffu, ov);
+            while (mask) {
+                const int b = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const int s = c0 + b;
+                const float4 r0 = S.r0[s], r1 = S.r1[s], pz = S.pz[s];
+                ss_hit h = ss_pixel_test(r0, r1, xl - pz.x, yl - pz.y, rc2);
+                bool cov = h.cover && !done;
+                const uint4 m = S.meta[s];
+                if (m.z & SS_FLAG_RECT_TEST) {
+                    int i0 = m.x & 0xffff, i1 = m.x >> 16, j0 = m.y & 0xffff, j1 = m.y >> 16;
+                    cov = cov && px >= i0 && px <= i1 && py >= j0 && py <= j1;
+                }
+                if (cov) {
+                    const float w = r1.w * __expf(-0.5f * __fdividef(h.q, h.t));   // Eq. mip_weight
+                    if (Wg > 0.f && pz.z > zmax) flush();                          // gap: new layer
+                    if (!done) {
+                        zmax = fmaxf(zmax, pz.w);
+                        const float4 c0v = S.c0[s], c1v = S.c1[s], c2v = S.c2[s];
+                        C[0] = fmaf(w, c0v.x, C[0]); C[1] = fmaf(w, c0v.y, C[1]); C[2] = fmaf(w, c0v.z, C[2]);
+                        C[3] = fmaf(w, c0v.w, C[3]); C[4] = fmaf(w, c1v.x, C[4]); C[5] = fmaf(w, c1v.y, C[5]);
+                        C[6] = fmaf(w, c1v.z, C[6]); C[7] = fmaf(w, c1v.w, C[7]); C[8] = fmaf(w, c2v.x, C[8]);
+                        C[9] = fmaf(w, c2v.y, C[9]); C[10] = fmaf(w, c2v.z, C[10]); C[11] = fmaf(w, c2v.w, C[11]);
+                        Wg += w;
+                    }
+                }
+            }
+        }
+    }
+    if (!done && Wg > 0.f) flush();
+    if (!inside) return;
+    float4 o;
+    o.x = fmaf(Tb, a.p.bg[0], out[0]);
+    o.y = fmaf(Tb, a.p.bg[1], out[1]);
+    o.z = fmaf(Tb, a.p.bg[2], out[2]);
+    o.w = Acov;
+    reinterpret_cast<float4*>(a.out_rgba)[gpix] = o;
+    if (a.out_aov) {
+#pragma unroll
+        for (int c = 0; c < SS_N_AOV; ++c) a.out_aov[c * P + gpix] = out[3 + c];
+    }
+    if (a.with_backward) {
+        ws.pix_state[gpix] = __int_as_float(K);
+        ws.pix_state[P + gpix] = Tb;
+    }
+}
+
+void ss_launch_raster_fwd(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st) {
+    if (L.total_tiles <= 0) return;
+    raster_fwd_kernel<<<L.total_tiles, 256, 0, st>>>(ws, a);
+}

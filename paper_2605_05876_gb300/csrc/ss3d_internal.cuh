@@ -1,0 +1,231 @@
+// Internal declarations of the GB300 3DSS rasteriser (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ss3d.h"
+
+#define SS_TILE 16                 // 16 x 16 pixel tiles (App. A)
+#define SS_TILE_PIX (SS_TILE * SS_TILE)
+#define SS_NCH 12                  // averaged channels: rgb, albedo 3, rough, metal, normal 3, depth
+#define SS_NGRAD 24                // floats per (view, surfel) gradient record (22 used)
+#define SS_PI_F 3.14159265358979323846f
+
+// ------------------------------------------------------------------------
+// batch layout, built on the host and copied into the workspace
+
+struct ss_view_layout {
+    int32_t scene;
+    int32_t width, height;
+    int32_t tiles_x, tiles_y;
+    int32_t tile_off;        // first global tile index of this view
+    int64_t pixel_off;       // first pixel of this view in the outputs
+    int64_t rec_off;         // first record of this view
+    int64_t surfel_begin;    // first surfel of the view's scene
+    int32_t n_surfels;       // surfels of the view's scene
+    int32_t pad_;
+};
+
+struct ss_layout {
+    int32_t n_views, n_scenes;
+    int32_t total_tiles;
+    int32_t k_max;
+    int64_t total_pixels;
+    int64_t total_records;
+    int64_t scene_begin[SS_MAX_SCENES + 1];
+    int32_t scene_view_begin[SS_MAX_SCENES + 1];
+    ss_view_layout v[SS_MAX_VIEWS];
+};
+
+// Per (view, surfel) record written by the projection step: 7 x float4.
+//  r0: A0', B0', A1', B1'   primed (filter-whitened) ray coefficients
+//  r1: A2, B2, C2, n_f      homogeneous denominator coefficients, MIP n_f
+//  r2: px_hi, py_hi, px_lo, py_lo   surfel centre in pixels (double-float)
+//  r3: z_start, z_end, rect_x, rect_y (packed u16 lo | hi << 16; empty = 0xffff0000? see below)
+//  r4: r, g, b, flags       forward-shaded colour (Eq. ibl), flags
+//  r5: albedo rgb, roughness
+//  r6: metallic, normal xyz (facing the camera, world space)
+// With dx = x - px, dy = y - py (pixel offsets from the centre):
+//   s0' = A0' dx + B0' dy,  s1' = A1' dx + B1' dy,  s2 = A2 dx + B2 dy + C2,
+//   rho2_mip = (s0'^2 + s1'^2) / s2^2, the hit is in front iff s2 > 0.
+struct __align__(16) ss_rec {
+    float4 r0, r1, r2, r3, r4, r5, r6;
+};
+
+#define SS_FLAG_VALID 1u
+#define SS_FLAG_RECT_TEST 2u        // the support rectangle can clip: test it per pixel
+#define SS_FLAG_FLIPPED 4u          // shading normal is -n
+
+// device status bits live in the first word of the workspace
+struct ss_ws_view {
+    int* status;
+    ss_layout* layout;
+    ss_rec* rec;
+    uint32_t* tile_count;   // [total_tiles]
+    uint32_t* tile_start;   // [total_tiles + 1]
+    uint32_t* tile_cursor;  // [total_tiles]
+    unsigned long long* keys;      // [max_instances]
+    unsigned long long* keys_alt;  // [max_instances]
+    float* layer_state;     // [k_max][13][total_pixels]  (raw C (12), W)
+    float* pix_state;       // [2][total_pixels]  (K as float bits, T_end)
+    float* grad_rec;        // [total_records][SS_NGRAD]
+    int64_t max_instances;
+};
+
+// ------------------------------------------------------------------------
+// double-float helpers (error-free transforms; Dekker / Knuth)
+
+struct dfl {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dfl two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ dfl two_prod(float a, float b) {
+    float p = __fmul_rn(a, b);
+    float e = __fmaf_rn(a, b, -p);
+    return {p, e};
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+    dfl s = two_sum(a.hi, b.hi);
+    float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return two_sum(s.hi, e);
+}
+__device__ __forceinline__ dfl df_add_f(dfl a, float b) {
+    dfl s = two_sum(a.hi, b);
+    return two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+__device__ __forceinline__ dfl df_mul_f(dfl a, float b) {
+    dfl p = two_prod(a.hi, b);
+    return two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
+}
+__device__ __forceinline__ dfl df_div(dfl a, dfl b) {
+    float q1 = __fdiv_rn(a.hi, b.hi);
+    dfl p = df_mul_f(b, q1);
+    dfl r = df_add(a, {-p.hi, -p.lo});
+    float q2 = __fdiv_rn(r.hi, b.hi);
+    return two_sum(q1, q2);
+}
+// a.x + b  with a, x float3 rows, b float, in double-float
+__device__ __forceinline__ dfl df_dot3_add(float a0, float a1, float a2, float x0, float x1, float x2,
+                                           float b) {
+    dfl acc = two_prod(a0, x0);
+    acc = df_add(acc, two_prod(a1, x1));
+    acc = df_add(acc, two_prod(a2, x2));
+    return df_add_f(acc, b);
+}
+
+// ------------------------------------------------------------------------
+// small math
+
+__device__ __forceinline__ void quat_rot(float w, float x, float y, float z, float R[9]) {
+    float n = rsqrtf(w * w + x * x + y * y + z * z);
+    w *= n; x *= n; y *= n; z *= n;
+    R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z); R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z); R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y); R[7] = 2.f * (y * z + w * x); R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+__device__ __forceinline__ uint32_t pack16(int lo, int hi) {
+    return (uint32_t)(lo & 0xffff) | ((uint32_t)(hi & 0xffff) << 16);
+}
+
+// Equirect coordinates (u, v) of a direction (not necessarily unit).
+__device__ __forceinline__ void dir_to_uv(float dx, float dy, float dz, float& u, float& v) {
+    float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+    float y = fminf(fmaxf(dy * inv, -1.f), 1.f);
+    u = atan2f(dx, -dz) * (0.5f / SS_PI_F) + 0.5f;
+    v = acosf(y) * (1.f / SS_PI_F);
+}
+
+// Bilinear texel taps of a [H][W] map at continuous (u, v) in [0,1]:
+// wrap in u (wrap != 0) or clamp, clamp in v.  Returns 4 texel indices and
+// weights; also the derivative weights w.r.t. X = uW - 0.5 and Y = vH - 0.5.
+struct ss_taps {
+    int i00, i01, i10, i11;
+    float fx, fy;
+};
+__device__ __forceinline__ ss_taps bilinear_taps(float u, float v, int W, int H, bool wrap) {
+    float X = u * (float)W - 0.5f, Y = v * (float)H - 0.5f;
+    float x0f = floorf(X), y0f = floorf(Y);
+    int x0 = (int)x0f, y0 = (int)y0f;
+    ss_taps t;
+    t.fx = X - x0f;
+    t.fy = Y - y0f;
+    int xa, xb;
+    if (wrap) {
+        xa = ((x0 % W) + W) % W;
+        xb = (xa + 1) % W;
+    } else {
+        xa = min(max(x0, 0), W - 1);
+        xb = min(max(x0 + 1, 0), W - 1);
+    }
+    int ya = min(max(y0, 0), H - 1), yb = min(max(y0 + 1, 0), H - 1);
+    t.i00 = ya * W + xa;
+    t.i01 = ya * W + xb;
+    t.i10 = yb * W + xa;
+    t.i11 = yb * W + xb;
+    return t;
+}
+
+// ------------------------------------------------------------------------
+// The per-pixel test, identical in the forward and backward kernels (explicit
+// roundings so that both make the same decision bit for bit).
+struct ss_hit {
+    float s0, s1, s2, q, t;  // t = s2^2
+    bool cover;
+};
+__device__ __forceinline__ ss_hit ss_pixel_test(float4 r0, float4 r1, float dx, float dy, float rc2) {
+    ss_hit h;
+    h.s0 = __fmaf_rn(r0.x, dx, __fmul_rn(r0.y, dy));
+    h.s1 = __fmaf_rn(r0.z, dx, __fmul_rn(r0.w, dy));
+    h.s2 = __fmaf_rn(r1.x, dx, __fmaf_rn(r1.y, dy, r1.z));
+    h.q = __fmaf_rn(h.s0, h.s0, __fmul_rn(h.s1, h.s1));
+    h.t = __fmul_rn(h.s2, h.s2);
+    h.cover = (h.s2 > 0.f) && (h.q < __fmul_rn(rc2, h.t));
+    return h;
+}
+
+// ------------------------------------------------------------------------
+// host-side launchers implemented in the .cu files
+
+void ss_launch_brdf_lut(float* lut, int n, cudaStream_t st);
+void ss_launch_env_prefilter(const ss_env_desc* d, int n_envs, const float* env, float* irr, float* spec,
+                             float* aux, cudaStream_t st);
+void ss_launch_env_prefilter_bwd(const ss_env_desc* d, int n_envs, const float* d_irr, const float* d_spec,
+                                 const float* aux, float* d_env, cudaStream_t st);
+int64_t ss_env_irr_floats(const ss_env_desc* d);
+int64_t ss_env_spec_floats(const ss_env_desc* d);
+int64_t ss_env_aux_floats(const ss_env_desc* d);
+void ss_env_level_size(const ss_env_desc* d, int i, int* W, int* H);
+
+struct ss_fwd_args {
+    ss_surfels s;
+    ss_render_params p;
+    ss_env_desc ed;
+    ss_env_maps env;
+    const ss_camera* cams;
+    float* out_rgba;
+    float* out_aov;
+    int with_backward;
+};
+void ss_launch_project(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st);
+void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st);
+void ss_launch_raster_fwd(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st);
+
+struct ss_bwd_args {
+    ss_fwd_args f;
+    const float* out_rgba;
+    const float* out_aov;
+    const float* d_rgba;
+    const float* d_aov;
+    ss_surfel_grads g;
+    ss_env_map_grads genv;
+};
+void ss_launch_raster_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st);
+void ss_launch_project_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st);

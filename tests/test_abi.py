@@ -1,0 +1,72 @@
+"""The C ABI library builds, loads and exports every entry point that
+include/ss3d.h declares (no GPU needed: no compute call is made)."""
+import ctypes
+import os
+import re
+
+from paper_2605_05876_gb300 import _lib, build
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "ss3d.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:ss_status|void|const char\*)\s+(ss_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("ss_render_forward", "ss_render_backward", "ss_env_prefilter", "ss_env_prefilter_backward",
+              "ss_brdf_lut", "ss_workspace_size", "ss_read_status"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    build()
+    lib = ctypes.CDLL(_lib.LIB_PATH)
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+    assert set(_lib.EXPORTS) == set(declared_functions())
+
+
+def test_struct_sizes_match_header():
+    assert ctypes.sizeof(_lib.ss_camera) == 80
+    assert ctypes.sizeof(_lib.ss_render_params) == 48
+
+
+def test_host_side_argument_errors():
+    """Host-detectable errors return SS_ERR_INVALID_ARG without touching a GPU."""
+    lib = _lib.lib()
+    p = _lib.ss_render_params()
+    lib.ss_default_params(ctypes.byref(p))
+    assert abs(p.gamma - 6.2831853) < 1e-6 and p.k_max == 16 and p.r_cut == 3.0
+    nb = ctypes.c_size_t()
+    # max_instances 0 -> invalid
+    cams = (_lib.ss_camera * 1)()
+    cams[0].width = cams[0].height = 16
+    cams[0].fx = cams[0].fy = 10.0
+    off = (ctypes.c_int64 * 2)(0, 10)
+    d = _lib.ss_batch_desc(1, 1, off, cams, None)
+    assert lib.ss_workspace_size(ctypes.byref(d), ctypes.byref(p), 0, ctypes.byref(nb)) == _lib.SS_ERR_INVALID_ARG
+    p.max_instances = 1000
+    assert lib.ss_workspace_size(ctypes.byref(d), ctypes.byref(p), 1, ctypes.byref(nb)) == 0 and nb.value > 0
+    # views out of scene order, bad scene index, zero views
+    d0 = _lib.ss_batch_desc(1, 0, off, cams, None)
+    assert lib.ss_workspace_size(ctypes.byref(d0), ctypes.byref(p), 0, ctypes.byref(nb)) == _lib.SS_ERR_INVALID_ARG
+    cams[0].scene = 3
+    assert lib.ss_workspace_size(ctypes.byref(d), ctypes.byref(p), 0, ctypes.byref(nb)) == _lib.SS_ERR_INVALID_ARG
+    cams[0].scene = 0
+    p.k_max = 17
+    assert lib.ss_workspace_size(ctypes.byref(d), ctypes.byref(p), 0, ctypes.byref(nb)) == _lib.SS_ERR_INVALID_ARG
+    # env descriptor checks
+    ed = _lib.ss_env_desc(100, 50, 6, 32, 16)
+    a = ctypes.c_int64()
+    assert lib.ss_env_sizes(ctypes.byref(ed), ctypes.byref(a), ctypes.byref(a), ctypes.byref(a)) == 1
+    ed = _lib.ss_env_desc(64, 32, 6, 32, 16)
+    b, c = ctypes.c_int64(), ctypes.c_int64()
+    assert lib.ss_env_sizes(ctypes.byref(ed), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)) == 0
+    assert a.value == 32 * 16 * 3
+    assert b.value == 3 * (64 * 32 + 32 * 16 + 16 * 8 + 8 * 4 * 3)
+    assert lib.ss_brdf_lut(None, 128, None) == _lib.SS_ERR_INVALID_ARG
+    assert lib.ss_error_string(_lib.SS_ERR_CAPACITY) == b"instance capacity exceeded"
