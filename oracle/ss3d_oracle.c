@@ -469,8 +469,10 @@ long long oref_fragments(int N, const double* T /* [N][9] */, const double* Sinv
             long long kept = 0;
             for (int f = 0; f < nf; ++f) {
                 if (layer >= 0) {
+                    /* an exact tie (equal interval ends, e.g. coplanar
+                     * fronto-parallel surfels) is not near a flip */
                     double m = fabs(fr[f].zs - zmax) / fabs(zmax);
-                    if (m < m_gap) m_gap = m;
+                    if (m > 0.0 && m < m_gap) m_gap = m;
                 }
                 if (layer < 0 || fr[f].zs > zmax) { /* gap: flush and open a new layer */
                     layer++;

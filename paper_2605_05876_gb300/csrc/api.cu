@@ -91,7 +91,7 @@ static ss_status build_layout(const ss_batch_desc* b, const ss_render_params* p,
 }
 
 struct ws_plan {
-    size_t status, layout, rec, tc, ts, tcur, keys, keys_alt, layer, pix, grad, total;
+    size_t status, layout, vgeo, rec, tc, ts, tcur, keys, keys_alt, layer, pix, grad, total;
 };
 
 static ws_plan plan_ws(const ss_layout& L, const ss_render_params& p, int with_bwd) {
@@ -104,6 +104,7 @@ static ws_plan plan_ws(const ss_layout& L, const ss_render_params& p, int with_b
     };
     w.status = take(256);
     w.layout = take(sizeof(ss_layout));
+    w.vgeo = take(sizeof(ss_view_geo) * SS_MAX_VIEWS);
     w.rec = take(sizeof(ss_rec) * (size_t)L.total_records);
     w.tc = take(sizeof(uint32_t) * (size_t)L.total_tiles);
     w.ts = take(sizeof(uint32_t) * ((size_t)L.total_tiles + 1));
@@ -126,6 +127,7 @@ static ss_ws_view carve(void* ws, const ws_plan& w, const ss_render_params& p, i
     ss_ws_view v;
     v.status = (int*)(b + w.status);
     v.layout = (ss_layout*)(b + w.layout);
+    v.vgeo = (ss_view_geo*)(b + w.vgeo);
     v.rec = (ss_rec*)(b + w.rec);
     v.tile_count = (uint32_t*)(b + w.tc);
     v.tile_start = (uint32_t*)(b + w.ts);
@@ -137,6 +139,29 @@ static ss_ws_view carve(void* ws, const ws_plan& w, const ss_render_params& p, i
     v.grad_rec = with_bwd ? (float*)(b + w.grad) : nullptr;
     v.max_instances = p.max_instances;
     return v;
+}
+
+// camera centre o = -R^-1 t (double-float) and det R of every view, in FP64
+__global__ void view_geo_kernel(const ss_camera* cams, ss_view_geo* out, int n_views) {
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n_views) return;
+    const ss_camera& c = cams[v];
+    double R[9], t[3] = {c.t[0], c.t[1], c.t[2]};
+    for (int k = 0; k < 9; ++k) R[k] = c.R[k];
+    double A[9];  // adjugate
+    A[0] = R[4] * R[8] - R[5] * R[7]; A[1] = R[2] * R[7] - R[1] * R[8]; A[2] = R[1] * R[5] - R[2] * R[4];
+    A[3] = R[5] * R[6] - R[3] * R[8]; A[4] = R[0] * R[8] - R[2] * R[6]; A[5] = R[2] * R[3] - R[0] * R[5];
+    A[6] = R[3] * R[7] - R[4] * R[6]; A[7] = R[1] * R[6] - R[0] * R[7]; A[8] = R[0] * R[4] - R[1] * R[3];
+    double det = R[0] * A[0] + R[1] * A[3] + R[2] * A[6];
+    ss_view_geo g;
+    for (int r = 0; r < 3; ++r) {
+        double o = -(A[r * 3] * t[0] + A[r * 3 + 1] * t[1] + A[r * 3 + 2] * t[2]) / det;
+        g.o_hi[r] = (float)o;
+        g.o_lo[r] = (float)(o - (double)g.o_hi[r]);
+    }
+    g.detR = (float)det;
+    g.pad_ = 0.f;
+    out[v] = g;
 }
 
 __global__ void set_layout_kernel(ss_layout* dst, ss_layout src) {
@@ -235,6 +260,7 @@ static ss_status forward_core(const ss_batch_desc* b, const ss_surfels* s, const
     a.with_backward = with_bwd;
     CK(cudaMemsetAsync(W.status, 0, sizeof(int), st));
     set_layout_kernel<<<1, 256, 0, st>>>(W.layout, L);
+    view_geo_kernel<<<(L.n_views + 63) / 64, 64, 0, st>>>(b->cams_dev, W.vgeo, L.n_views);
     CK(cudaMemsetAsync(W.tile_count, 0, sizeof(uint32_t) * (size_t)L.total_tiles, st));
     CK(cudaMemsetAsync(W.tile_cursor, 0, sizeof(uint32_t) * (size_t)L.total_tiles, st));
     ss_launch_project(W, L, a, st);

@@ -17,15 +17,22 @@
 
 #define LUT_NQ 128
 
+// Quadrature nodes on [0, 1]: Gauss-Legendre abscissae t_i mapped through
+// the endpoint-clustering map s(t) = t^3 (10 - 15 t + 6 t^2); the host keeps
+// them in double so that the nodes next to 0 and 1 keep full relative
+// precision, then rounds s_i and the weights w_i s'(t_i) / 2 to float.
 struct gl_nodes {
-    float x[LUT_NQ];
-    float w[LUT_NQ];
+    double s[LUT_NQ];    // xi nodes (double: for tiny alpha the mass sits within 1e-8 of xi = 1)
+    double sc[LUT_NQ];   // 1 - s, formed as s(1 - t) (the map is symmetric) to keep precision
+    double w[LUT_NQ];
+    float sf[LUT_NQ];    // phi nodes
+    float wf[LUT_NQ];
 };
 
-// Gauss-Legendre nodes on [-1, 1] by Newton iteration on P_n.
 static gl_nodes make_gl_nodes() {
     gl_nodes g;
     const int n = LUT_NQ;
+    double xs[LUT_NQ], ws[LUT_NQ];
     for (int i = 0; i < (n + 1) / 2; ++i) {
         double z = cos(M_PI * (i + 0.75) / (n + 0.5)), pp = 0.0;
         for (int it = 0; it < 100; ++it) {
@@ -41,16 +48,21 @@ static gl_nodes make_gl_nodes() {
             if (fabs(z - z1) < 1e-15) break;
         }
         double w = 2.0 / ((1.0 - z * z) * pp * pp);
-        g.x[i] = (float)(-z);
-        g.x[n - 1 - i] = (float)z;
-        g.w[i] = g.w[n - 1 - i] = (float)w;
+        xs[i] = -z;
+        xs[n - 1 - i] = z;
+        ws[i] = ws[n - 1 - i] = w;
+    }
+    for (int i = 0; i < n; ++i) {
+        // t = (x + 1)/2, written so that nodes next to either end keep precision
+        double t = xs[i] < 0 ? 0.5 * (1.0 + xs[i]) : 1.0 - 0.5 * (1.0 - xs[i]);
+        double u = 1.0 - t;
+        g.s[i] = t * t * t * (10.0 - 15.0 * t + 6.0 * t * t);
+        g.sc[i] = u * u * u * (10.0 - 15.0 * u + 6.0 * u * u);
+        g.w[i] = 0.5 * ws[i] * 30.0 * t * t * u * u;
+        g.sf[i] = (float)g.s[i];
+        g.wf[i] = (float)g.w[i];
     }
     return g;
-}
-
-__device__ __forceinline__ float smoother(float t, float& dt) {
-    dt = 30.f * t * t * (1.f - t) * (1.f - t);
-    return t * t * t * (10.f - 15.f * t + 6.f * t * t);
 }
 
 // beta1 = Int D G (v.h)(1-Fc)/(n.v) dh, beta2 = ... Fc ..., over n.l > 0.
@@ -62,17 +74,20 @@ __global__ void __launch_bounds__(256) brdf_lut_kernel(float* lut, int n, gl_nod
     const int cell = blockIdx.x;
     const int ir = cell / n, im = cell % n;
     const float r = (ir + 0.5f) / n, mu = (im + 0.5f) / n;
-    const float alpha = r * r, k = 0.5f * alpha, a2 = alpha * alpha;
+    const float alpha = r * r, k = 0.5f * alpha;
     const float sv = sqrtf(fmaxf(0.f, 1.f - mu * mu));
     const float thv = acosf(mu);
-    float xi_seg[3];
+    // segment ends in xi, in double (for tiny alpha they sit within 1e-9 of 1)
+    double xi_seg[3], om_seg[3];  // segment ends in xi and 1 - xi
     {
-        float th[2] = {fmaxf(0.f, 0.5f * (0.5f * SS_PI_F - thv)), 0.5f * (0.5f * SS_PI_F + thv)};
-        xi_seg[0] = 0.f;
+        double th[2] = {fmax(0.0, 0.5 * (0.5 * M_PI - (double)thv)), 0.5 * (0.5 * M_PI + (double)thv)};
+        xi_seg[0] = 0.0;
+        om_seg[0] = 1.0;
         for (int s = 0; s < 2; ++s) {
-            float c = cosf(th[s]), c2 = c * c;
-            float sn = sinf(th[s]), s2 = sn * sn;
-            xi_seg[s + 1] = s2 / (s2 + a2 * c2);
+            double c = cos(th[s]), sn = sin(th[s]);
+            double a2c2 = (double)alpha * alpha * c * c;
+            xi_seg[s + 1] = sn * sn / (sn * sn + a2c2);
+            om_seg[s + 1] = a2c2 / (sn * sn + a2c2);
         }
     }
     const float g1v = mu / (mu * (1.f - k) + k);
@@ -80,35 +95,42 @@ __global__ void __launch_bounds__(256) brdf_lut_kernel(float* lut, int n, gl_nod
     // 2 segments x LUT_NQ xi nodes; each thread takes one (segment, xi) node
     for (int idx = threadIdx.x; idx < 2 * LUT_NQ; idx += blockDim.x) {
         int sg = idx / LUT_NQ, i = idx % LUT_NQ;
-        float lo = xi_seg[sg], hi = xi_seg[sg + 1];
+        const double lo = xi_seg[sg], hi = xi_seg[sg + 1], om_lo = om_seg[sg], om_hi = om_seg[sg + 1];
         if (!(hi > lo)) continue;
-        float dti, ti = smoother(0.5f * (g.x[i] + 1.f), dti);
-        float xi = lo + (hi - lo) * ti;
-        float wxi = 0.5f * g.w[i] * (hi - lo) * dti;
-        float c2 = (1.f - xi) / (1.f + (a2 - 1.f) * xi);
-        if (!(c2 > 0.f)) continue;
-        float ct = sqrtf(c2), st = sqrtf(fmaxf(0.f, 1.f - c2));
-        float K = mu / (2.f * ct) - mu * ct;
-        float phimax;
-        if (sv * st <= 0.f) {
-            phimax = K < 0.f ? SS_PI_F : 0.f;
+        // the node's polar angle in double: with alpha^2 ~ 1e-10, (alpha^2 - 1) is
+        // not representable in FP32 next to 1
+        // xi and 1 - xi, each measured from its nearer end
+        const double xi = g.s[i] < 0.5 ? lo + (hi - lo) * g.s[i] : hi - (hi - lo) * g.sc[i];
+        const double one_m_xi = g.s[i] < 0.5 ? om_lo - (hi - lo) * g.s[i] : om_hi + (hi - lo) * g.sc[i];
+        const float wxi = (float)(g.w[i] * (hi - lo));
+        const double a2d = (double)alpha * (double)alpha;
+        const double den = one_m_xi + a2d * xi;
+        const double c2d = one_m_xi / den, s2d = a2d * xi / den;
+        if (!(c2d > 0.0)) continue;
+        const double ctd = sqrt(c2d), std_ = sqrt(s2d);
+        const double Kd = (double)mu / (2.0 * ctd) - (double)mu * ctd;
+        double phimax_d;
+        if ((double)sv * std_ <= 0.0) {
+            phimax_d = Kd < 0.0 ? M_PI : 0.0;
         } else {
-            float kap = K / (sv * st);
-            phimax = kap <= -1.f ? SS_PI_F : (kap >= 1.f ? 0.f : acosf(kap));
+            double kap = Kd / ((double)sv * std_);
+            phimax_d = kap <= -1.0 ? M_PI : (kap >= 1.0 ? 0.0 : acos(kap));
         }
-        if (!(phimax > 0.f)) continue;
+        if (!(phimax_d > 0.0)) continue;
+        const float ct = (float)ctd, st = (float)std_, phimax = (float)phimax_d;
         float acc1 = 0.f, acc2 = 0.f;
         for (int j = 0; j < LUT_NQ; ++j) {
-            float dtj, tj = smoother(0.5f * (g.x[j] + 1.f), dtj);
-            float phi = phimax * tj, wphi = 0.5f * g.w[j] * phimax * dtj;
+            float phi = phimax * g.sf[j], wphi = g.wf[j] * phimax;
             float vh = sv * st * cosf(phi) + mu * ct;
             float nl = 2.f * vh * ct - mu;
             if (nl <= 0.f || vh <= 0.f) continue;
             float G = g1v * (nl / (nl * (1.f - k) + k));
+            // 1 - Fc = 1 - (1 - vh)^5 expanded, so it keeps precision for small vh
+            float one_m_Fc = vh * (5.f + vh * (-10.f + vh * (10.f + vh * (-5.f + vh))));
             float om = 1.f - vh, om2 = om * om;
             float Fc = om2 * om2 * om;
             float common = wphi * G * vh / (mu * ct) * (1.f / SS_PI_F);
-            acc1 += common * (1.f - Fc);
+            acc1 += common * one_m_Fc;
             acc2 += common * Fc;
         }
         b1 += (double)wxi * acc1;

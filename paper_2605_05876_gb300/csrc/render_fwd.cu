@@ -96,42 +96,58 @@ __global__ void __launch_bounds__(256) project_kernel(ss_ws_view ws, ss_fwd_args
         dfl px = df_add_f(df_mul_f(mx, cam.fx), cam.cx);
         dfl py = df_add_f(df_mul_f(my, cam.fy), cam.cy);
         const float mxf = mx.hi, myf = my.hi;
-        // screen-plane derivatives of the tangents: a = t'_u - m t'_uz, b = t'_v - m t'_vz
-        const float ax = tuc[0] - mxf * tuc[2], ay = tuc[1] - myf * tuc[2];
-        const float bx = tvc[0] - mxf * tvc[2], by = tvc[1] - myf * tvc[2];
-        const float det0 = ax * by - bx * ay;
-        bool valid = finite && (zs > a.p.z_near) && (det0 != 0.f) && isfinite(det0);
         const float fx = cam.fx, fy = cam.fy;
-        // normalised homogeneous ray coefficients (s / C2):  u = s0/s2, v = s1/s2 with
-        // s0 = J00 dx + J01 dy, s1 = J10 dx + J11 dy, s2 = A2 dx + B2 dy + 1, J = d(u,v)/d(x,y) at the centre
-        const float id = 1.f / det0;
-        const float J00 = by * cz * id / fx, J01 = -bx * cz * id / fy;
-        const float J10 = -ay * cz * id / fx, J11 = ax * cz * id / fy;
-        const float A2 = (tvc[2] * ay - tuc[2] * by) * id / fx;
-        const float B2 = (tuc[2] * bx - tvc[2] * ax) * id / fy;
-        // MIP filter at the centre (Eq. mip_cov) in the stable form
-        // Sigma^-1 = G (G + sig I)^-1, n_f = sqrt(det G / det(G + sig I)), G = M^T M, M = J^-1
-        const float icz = 1.f / cz;
-        const float fx2 = fx * fx, fy2 = fy * fy, icz2 = icz * icz;
-        const float Guu = (fx2 * ax * ax + fy2 * ay * ay) * icz2;
-        const float Guv = (fx2 * ax * bx + fy2 * ay * by) * icz2;
-        const float Gvv = (fx2 * bx * bx + fy2 * by * by) * icz2;
-        const float sdg = fx * fy * det0 * icz2;
+        // screen-plane parts of the tangents: a = t'_u - m t'_uz, b = t'_v - m t'_vz
+        const float ax = __fmaf_rn(-mxf, tuc[2], tuc[0]), ay = __fmaf_rn(-myf, tuc[2], tuc[1]);
+        const float bx = __fmaf_rn(-mxf, tvc[2], tvc[0]), by = __fmaf_rn(-myf, tvc[2], tvc[1]);
+        // N_d = n . (c - o), o = -R^-1 t the camera centre: the signed distance of the
+        // camera from the surfel plane.  It is the one ill-conditioned quantity for
+        // nearly edge-on surfels, so it is formed in double-float from the quaternion,
+        // n = (2(xz+wy), 2(yz-wx), w^2-x^2-y^2+z^2) / |q|^2.
+        float Nd;
+        {
+            const ss_view_geo& vg = ws.vgeo[v];
+            const float qw = q.x, qx = q.y, qy = q.z, qz = q.w;
+            dfl n0 = df_add(two_prod(qx, qz), two_prod(qw, qy));
+            dfl n1 = df_add(two_prod(qy, qz), two_prod(-qw, qx));
+            dfl n2 = df_add(df_add(two_prod(qw, qw), two_prod(-qx, qx)), df_add(two_prod(-qy, qy), two_prod(qz, qz)));
+            n0 = {2.f * n0.hi, 2.f * n0.lo};
+            n1 = {2.f * n1.hi, 2.f * n1.lo};
+            dfl d0 = df_add_f({-vg.o_hi[0], -vg.o_lo[0]}, c0);
+            dfl d1 = df_add_f({-vg.o_hi[1], -vg.o_lo[1]}, c1);
+            dfl d2 = df_add_f({-vg.o_hi[2], -vg.o_lo[2]}, c2);
+            dfl nd = df_add(df_add(df_mul(n0, d0), df_mul(n1, d1)), df_mul(n2, d2));
+            const float qq = qw * qw + qx * qx + qy * qy + qz * qz;
+            Nd = (nd.hi + nd.lo) / qq;
+        }
+        const float ncx = cam.R[0] * nrm[0] + cam.R[1] * nrm[1] + cam.R[2] * nrm[2];   // n' = R n
+        const float ncy = cam.R[3] * nrm[0] + cam.R[4] * nrm[1] + cam.R[5] * nrm[2];
+        // (t'_u x t'_v) . c'/c'_z = det R s_u s_v N_d / c'_z
+        const float det0 = ws.vgeo[v].detR * su * sv * Nd / cz;
+        bool valid = finite && (zs > a.p.z_near) && (Nd != 0.f) && isfinite(Nd);
+        // perspective denominator: s2 = c'_z / depth(hit) = 1 + (n'_x dx/fx + n'_y dy/fy) c'_z / N_d
+        // (n' = R^-T n is the camera-space plane normal; R n differs from it by rounding only)
+        const float A2 = cz * ncx / (fx * Nd), B2 = cz * ncy / (fy * Nd);
+        // M M^T (M = d(x,y)/d(u,v) at the centre) and the filtered screen covariance
+        const float icz = 1.f / cz, icz2 = icz * icz;
+        const float fx2 = fx * fx, fy2 = fy * fy;
+        const float m11 = fx2 * (ax * ax + bx * bx) * icz2;
+        const float m12 = fx * fy * (ax * ay + bx * by) * icz2;
+        const float m22 = fy2 * (ay * ay + by * by) * icz2;
+        const float sdg = fx * fy * det0 * icz2;     // det M
         const float detG = sdg * sdg;
-        const float Dn = detG + sig * (Guu + Gvv) + sig * sig;
-        const float iD = 1.f / Dn;
-        const float Sa = (detG + sig * Guu) * iD, Sb = sig * Guv * iD, Sc = (detG + sig * Gvv) * iD;
-        const float nf = sqrtf(detG * iD);
-        // whitening factor F with F^T F = Sigma^-1 (pivoted Cholesky; det Sigma^-1 = n_f^2)
+        const float sig = a.p.sigma_f;
+        const float Dn = detG + sig * (m11 + m22) + sig * sig;   // det(M M^T + sig I)
+        const float nf = sqrtf(detG / Dn);                        // Eq. mip_eval: sqrt(|I| / |Sigma_mip|)
+        // Qs = (M M^T + sig I)^-1 = [[m22 + sig, -m12], [-m12, m11 + sig]] / Dn, factor P^T P = Qs
+        const float qa = (m22 + sig) / Dn, qb = -m12 / Dn, qc = (m11 + sig) / Dn;
         float P00, P01, P10, P11;
-        if (Sa >= Sc) {
-            float f00 = sqrtf(Sa), f01 = Sb / f00, f11 = nf / f00;
-            P00 = f00 * J00 + f01 * J10; P01 = f00 * J01 + f01 * J11;
-            P10 = f11 * J10; P11 = f11 * J11;
-        } else {
-            float g11 = sqrtf(Sc), g10 = Sb / g11, g00 = nf / g11;
-            P00 = g11 * J10 + g10 * J00; P01 = g11 * J11 + g10 * J01;
-            P10 = g00 * J00; P11 = g00 * J01;
+        if (qa >= qc) {   // q = (l00 dx + l01 dy)^2 + (l11 dy)^2, det Qs = 1/Dn
+            float l00 = sqrtf(qa);
+            P00 = l00; P01 = qb / l00; P10 = 0.f; P11 = rsqrtf(Dn) / l00;
+        } else {          // q = (l11 dy + l10 dx)^2 + (l00 dx)^2
+            float l11 = sqrtf(qc);
+            P00 = qb / l11; P01 = l11; P10 = rsqrtf(Dn) / l11; P11 = 0.f;
         }
         // support rectangle (centred pixel offsets): exact bounds of the projected r_cut
         // disc (dual conic, App. A) U r_cut bounds of the EWA ellipse M M^T + sig I, +1 px
@@ -140,39 +156,35 @@ __global__ void __launch_bounds__(256) project_kernel(ss_ws_view ws, ss_fwd_args
         const float C22 = tuc[2] * tuc[2] + tvc[2] * tvc[2] - cz * cz / rc2;
         float lo[2], hi[2];
         {
-            const float Caa[2] = {C00, C11}, Ca2[2] = {C02, C12};
+            const float Caa[2] = {C00, C11}, Ca2[2] = {C02, C12}, Maa[2] = {m11, m22};
             for (int ax_ = 0; ax_ < 2; ++ax_) {
                 float dsc = sqrtf(fmaxf(Ca2[ax_] * Ca2[ax_] - Caa[ax_] * C22, 0.f));
                 float r0 = (Ca2[ax_] + dsc) / C22, r1 = (Ca2[ax_] - dsc) / C22;
-                float ext = rc * sqrtf(Caa[ax_] * icz2 + sig);
+                float ext = rc * sqrtf(Maa[ax_] + sig);
                 lo[ax_] = fminf(fminf(r0, r1), -ext) - 1.f;
                 hi[ax_] = fmaxf(fmaxf(r0, r1), ext) + 1.f;
             }
         }
-        valid = valid && (C22 < 0.f);
+        valid = valid && (C22 < 0.f) && isfinite(nf) && isfinite(A2) && isfinite(B2);
         int i0 = (int)ceilf(px.hi + lo[0] - 0.5f), i1 = (int)floorf(px.hi + hi[0] - 0.5f);
         int j0 = (int)ceilf(py.hi + lo[1] - 0.5f), j1 = (int)floorf(py.hi + hi[1] - 0.5f);
         i0 = max(i0, 0); j0 = max(j0, 0);
         i1 = min(i1, vl.width - 1); j1 = min(j1, vl.height - 1);
         valid = valid && (i0 <= i1) && (j0 <= j1) && isfinite(px.hi) && isfinite(py.hi);
         if (valid) {
-            // does the exact filtered support {u^T Sigma^-1 u < r^2} stay inside the rectangle?
-            // dual conic H adj(Q_f) H^T with adj(Q_f) ~ [[r^2 Sc, -r^2 Sb, 0], [-r^2 Sb, r^2 Sa, 0], [0, 0, -n_f^2]]
-            const float h[3][3] = {{fx * ax, fx * bx, 0.f}, {fy * ay, fy * by, 0.f}, {tuc[2], tvc[2], cz}};
-            float Cf[3][3];
-            for (int r = 0; r < 3; ++r)
-                for (int c = r; c < 3; ++c) {
-                    float val = rc2 * (Sc * h[r][0] * h[c][0] - Sb * (h[r][0] * h[c][1] + h[r][1] * h[c][0]) +
-                                       Sa * h[r][1] * h[c][1]) -
-                                nf * nf * h[r][2] * h[c][2];
-                    Cf[r][c] = val;
-                }
-            bool inside = Cf[2][2] < 0.f;
-            for (int ax_ = 0; ax_ < 2 && inside; ++ax_) {
-                float caa = Cf[ax_][ax_], ca2 = Cf[ax_][2], c22 = Cf[2][2];
-                float dsc = sqrtf(fmaxf(ca2 * ca2 - caa * c22, 0.f));
-                float r0 = (ca2 + dsc) / c22, r1 = (ca2 - dsc) / c22;
-                inside = (fminf(r0, r1) > lo[ax_] + 0.25f) && (fmaxf(r0, r1) < hi[ax_] - 0.25f);
+            // does the exact filtered support {d^T Qs d < r^2 s2(d)^2} stay inside the
+            // rectangle?  It is the ellipse (d - dc)^T Q2 (d - dc) < kap with
+            // Q2 = Qs - r^2 g g^T, g = (A2, B2), dc = r^2 Q2^-1 g, kap = r^2 + r^2 g.dc
+            const float q00 = qa - rc2 * A2 * A2, q01 = qb - rc2 * A2 * B2, q11 = qc - rc2 * B2 * B2;
+            const float dq = q00 * q11 - q01 * q01;
+            bool inside = (q00 > 0.f) && (dq > 0.f);
+            if (inside) {
+                const float i00 = q11 / dq, i01 = -q01 / dq, i11 = q00 / dq;
+                const float dcx = rc2 * (i00 * A2 + i01 * B2), dcy = rc2 * (i01 * A2 + i11 * B2);
+                const float kap = rc2 * (1.f + A2 * dcx + B2 * dcy);
+                const float hx = sqrtf(fmaxf(kap * i00, 0.f)), hy = sqrtf(fmaxf(kap * i11, 0.f));
+                inside = (dcx - hx > lo[0] + 0.25f) && (dcx + hx < hi[0] - 0.25f) && (dcy - hy > lo[1] + 0.25f) &&
+                         (dcy + hy < hi[1] - 0.25f);
             }
             if (!inside) flags |= SS_FLAG_RECT_TEST;
             flags |= SS_FLAG_VALID;

@@ -39,16 +39,18 @@ struct ss_layout {
 };
 
 // Per (view, surfel) record written by the projection step: 7 x float4.
-//  r0: A0', B0', A1', B1'   primed (filter-whitened) ray coefficients
-//  r1: A2, B2, C2, n_f      homogeneous denominator coefficients, MIP n_f
+//  r0: P00, P01, P10, P11   factor of the screen-space quadratic form, P^T P = (M M^T + sigma_f I)^-1
+//  r1: A2, B2, 1, n_f       perspective denominator s2 = 1 + A2 dx + B2 dy, MIP n_f
 //  r2: px_hi, py_hi, px_lo, py_lo   surfel centre in pixels (double-float)
 //  r3: z_start, z_end, rect_x, rect_y (packed u16 lo | hi << 16; empty = 0xffff0000? see below)
 //  r4: r, g, b, flags       forward-shaded colour (Eq. ibl), flags
 //  r5: albedo rgb, roughness
 //  r6: metallic, normal xyz (facing the camera, world space)
-// With dx = x - px, dy = y - py (pixel offsets from the centre):
-//   s0' = A0' dx + B0' dy,  s1' = A1' dx + B1' dy,  s2 = A2 dx + B2 dy + C2,
-//   rho2_mip = (s0'^2 + s1'^2) / s2^2, the hit is in front iff s2 > 0.
+// With d = (dx, dy) = pixel centre - surfel centre p, the ray hit in the
+// surfel plane is (u, v) = J d / s2(d) (J = d(u,v)/d(x,y) at the centre; the
+// homogeneous hit is linear in d), so rho2_mip = u^T Sigma^-1_mip u equals
+//   rho2_mip = d^T (M M^T + sigma_f I)^-1 d / s2^2 = |P d|^2 / s2^2,
+// M = J^-1, and the hit is in front of the camera iff s2 > 0.
 struct __align__(16) ss_rec {
     float4 r0, r1, r2, r3, r4, r5, r6;
 };
@@ -57,10 +59,21 @@ struct __align__(16) ss_rec {
 #define SS_FLAG_RECT_TEST 2u        // the support rectangle can clip: test it per pixel
 #define SS_FLAG_FLIPPED 4u          // shading normal is -n
 
+// Per-view quantities derived on the device from the camera (every call, so
+// that cameras may change between graph replays): the camera centre
+// o = -R^-1 t in double-float and det R.  R is used as given (its float32
+// rounding need not be orthogonal), so R^-1 is not R^T.
+struct ss_view_geo {
+    float o_hi[3], o_lo[3];
+    float detR;
+    float pad_;
+};
+
 // device status bits live in the first word of the workspace
 struct ss_ws_view {
     int* status;
     ss_layout* layout;
+    ss_view_geo* vgeo;      // [n_views]
     ss_rec* rec;
     uint32_t* tile_count;   // [total_tiles]
     uint32_t* tile_start;   // [total_tiles + 1]
@@ -103,6 +116,11 @@ __device__ __forceinline__ dfl df_add_f(dfl a, float b) {
 __device__ __forceinline__ dfl df_mul_f(dfl a, float b) {
     dfl p = two_prod(a.hi, b);
     return two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
+}
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+    dfl p = two_prod(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+    return two_sum(p.hi, e);
 }
 __device__ __forceinline__ dfl df_div(dfl a, dfl b) {
     float q1 = __fdiv_rn(a.hi, b.hi);

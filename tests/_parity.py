@@ -35,6 +35,21 @@ def ambiguous(margin):
     return (margin[:, 0] < M_CUT) | (margin[:, 1] < M_GAP) | (margin[:, 2] < M_BOX)
 
 
+# a pixel whose decision flips between precisions may differ by one
+# near-cutoff fragment (weight ~ n_f e^-4.5) or one layer boundary; such
+# pixels must still be finite, with coverage in [0, 1], within this of the oracle
+AMBIGUOUS_ABS = 0.25
+MAX_AMBIGUOUS_FRACTION = 1e-2
+
+
+def check_ambiguous(gpu, ref, amb):
+    g, r = gpu[amb], ref[amb]
+    assert np.all(np.isfinite(g))
+    assert np.all((g[:, 3] >= 0) & (g[:, 3] <= 1 + 1e-6))
+    if g.size:
+        assert np.abs(g - r).max() <= AMBIGUOUS_ABS * max(1.0, np.abs(r).max())
+
+
 def compare(gpu, ref, amb, what=""):
     """gpu, ref: [P, C] arrays.  Returns the number of failing entries and a
     message; ambiguous pixels are excluded."""

@@ -31,8 +31,9 @@ def _check_view(r, scene, v, pix=None, env_cache=None):
     amb = _parity.ambiguous(ref["margin"])
     refv = np.concatenate([ref["rgba"], ref["aov"]], 1)
     n_bad, msg = _parity.compare(gpu, refv, amb, f"view {v}")
-    assert amb.mean() < 2e-3, f"too many ambiguous pixels: {amb.sum()}"
+    assert amb.mean() < _parity.MAX_AMBIGUOUS_FRACTION, f"too many ambiguous pixels: {amb.sum()}"
     assert n_bad == 0, msg
+    _parity.check_ambiguous(gpu, refv, amb)
     return ref, gpu
 
 
