@@ -1,5 +1,599 @@
-// Backward render (replaced below by the real kernels).
+// Backward render (App. A "Backward Pass Implementation of Multi-Layer
+// Compositing"): the rasteriser replays each pixel's grouping front to back
+// against the per-layer totals (C_k, W_k) kept by the forward pass, turns the
+// upstream gradient into per-fragment gradients, reduces them over each warp
+// and adds one record of 21 floats per (surfel, view); a second kernel then
+// chains those records back through the projection and the shading to the
+// surfel parameters and the prefiltered environment texels.
+//
+// Every discrete decision (support, cutoff, grouping, K_max, normal flip) is
+// held fixed; the replay uses the same ss_pixel_test and weight expression as
+// the forward kernel, so both take identical decisions.
+#include <math.h>
+
 #include "ss3d_internal.cuh"
 
-void ss_launch_raster_bwd(const ss_ws_view&, const ss_layout&, const ss_bwd_args&, cudaStream_t) {}
-void ss_launch_project_bwd(const ss_ws_view&, const ss_layout&, const ss_bwd_args&, cudaStream_t) {}
+// gradient record layout (floats) of one (view, surfel)
+#define G_P 0      // dL/dP00, P01, P10, P11
+#define G_A2 4
+#define G_B2 5
+#define G_PX 6     // dL/dp_x, dL/dp_y (surfel centre in pixels)
+#define G_PY 7
+#define G_NF 8
+#define G_CH 9     // 12 channels: rgb, albedo 3, roughness, metallic, normal 3, depth
+#define G_N 21
+
+#define RB 256
+
+struct ss_bstage {
+    float4 r0[RB];   // P
+    float4 r1[RB];   // A2, B2, 1, n_f
+    float4 pz[RB];   // centre relative to the tile origin, z_start, z_end
+    uint4 meta[RB];  // rect_x, rect_y, flags, record index
+    float4 c0[RB];   // rgb, albedo r
+    float4 c1[RB];   // albedo g, b, roughness, metallic
+    float4 c2[RB];   // normal xyz, depth
+};
+
+__device__ __forceinline__ int find_view_b(const ss_layout* L, int tile) {
+    int lo = 0, hi = L->n_views - 1;
+    while (lo < hi) {
+        int m = (lo + hi + 1) >> 1;
+        if (L->v[m].tile_off <= tile) lo = m;
+        else hi = m - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) raster_bwd_kernel(ss_ws_view ws, ss_bwd_args a) {
+    __shared__ ss_bstage S;
+    const ss_layout* L = ws.layout;
+    const int tile = blockIdx.x;
+    const int view = find_view_b(L, tile);
+    const ss_view_layout& vl = L->v[view];
+    const int lt = tile - vl.tile_off;
+    const int tx = lt % vl.tiles_x, ty = lt / vl.tiles_x;
+    const int x0 = tx * SS_TILE, y0 = ty * SS_TILE;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wx0 = 8 * (warp & 1), wy0 = 4 * (warp >> 1);
+    const int lx = wx0 + (lane & 7), ly = wy0 + (lane >> 3);
+    const int px = x0 + lx, py = y0 + ly;
+    const bool inside = px < vl.width && py < vl.height;
+    const int gx0 = x0 + wx0, gx1 = gx0 + 7, gy0 = y0 + wy0, gy1 = gy0 + 3;
+    const float xl = (float)lx + 0.5f, yl = (float)ly + 0.5f;
+    const float rc2 = a.f.p.r_cut * a.f.p.r_cut;
+    const float kw = a.f.p.gamma * (0.5f / SS_PI_F);
+    const int64_t P = L->total_pixels;
+    const int64_t gpix = vl.pixel_off + (int64_t)(inside ? py : 0) * vl.width + (inside ? px : 0);
+
+    // per-pixel state from the forward pass
+    int K = 0;
+    float Tend = 1.f, gA = 0.f;
+    float g[SS_NCH], outc[SS_NCH];
+    if (inside) {
+        K = __float_as_int(ws.pix_state[gpix]);
+        Tend = ws.pix_state[P + gpix];
+        float4 d = reinterpret_cast<const float4*>(a.d_rgba)[gpix];
+        float4 o = reinterpret_cast<const float4*>(a.out_rgba)[gpix];
+        g[0] = d.x; g[1] = d.y; g[2] = d.z; gA = d.w;
+        outc[0] = o.x; outc[1] = o.y; outc[2] = o.z;   // includes T_end * bg: R_k below needs it
+#pragma unroll
+        for (int c = 0; c < SS_N_AOV; ++c) {
+            g[3 + c] = a.d_aov ? a.d_aov[c * P + gpix] : 0.f;
+            outc[3 + c] = a.out_aov ? a.out_aov[c * P + gpix] : 0.f;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < SS_NCH; ++c) g[c] = outc[c] = 0.f;
+    }
+    bool done = !inside || K == 0;
+
+    // replay state (Algorithm 1) and per-layer gradient coefficients
+    int k = -1;
+    float Wr = 0.f, zmax = 0.f;
+    float Tb = 1.f;
+    float acc[SS_NCH];
+#pragma unroll
+    for (int c = 0; c < SS_NCH; ++c) acc[c] = 0.f;
+    float G[SS_NCH];      // dL/dC_c for Shepard channels; for the normal channels H = dL/dC_n
+    float Sk = 0.f;       // sum_c G_c Chat_c - dL/dW (alpha path)
+
+    auto enter_layer = [&](int kk) {
+        const float* ls = ws.layer_state + (int64_t)kk * 13 * P + gpix;
+        float C[SS_NCH];
+#pragma unroll
+        for (int c = 0; c < SS_NCH; ++c) C[c] = ls[c * P];
+        const float W = ls[12 * P];
+        const float invW = 1.f / W;
+        float hat[SS_NCH];
+#pragma unroll
+        for (int c = 0; c < SS_NCH; ++c) hat[c] = C[c] * invW;
+        const float nl = sqrtf(C[8] * C[8] + C[9] * C[9] + C[10] * C[10]);
+        const float inl = nl > 0.f ? 1.f / nl : 0.f;
+        hat[8] = C[8] * inl; hat[9] = C[9] * inl; hat[10] = C[10] * inl;
+        const float al = -expm1f(-kw * W);
+        const float e = expf(-kw * W);
+        const float tw = Tb * al;
+        float gChat = 0.f, gR = 0.f;
+#pragma unroll
+        for (int c = 0; c < SS_NCH; ++c) {
+            acc[c] = fmaf(tw, hat[c], acc[c]);
+            gChat = fmaf(g[c], hat[c], gChat);
+            gR = fmaf(g[c], outc[c] - acc[c], gR);
+        }
+        // Eq. alpha / Eq. compositing: dL/dW_k through alpha_k and all later T_j
+        const float dW_alpha = kw * (Tb * e * gChat - gR + gA * Tend);
+        float sG = 0.f;
+#pragma unroll
+        for (int c = 0; c < SS_NCH; ++c) {
+            if (c >= 8 && c <= 10) continue;
+            G[c] = g[c] * tw * invW;          // Eq. shepard: C_hat = C / W
+            sG = fmaf(G[c], hat[c], sG);
+        }
+        // renormalised normal n_hat = C_n / |C_n|
+        const float dn0 = g[8] * tw, dn1 = g[9] * tw, dn2 = g[10] * tw;
+        const float nd = dn0 * hat[8] + dn1 * hat[9] + dn2 * hat[10];
+        G[8] = (dn0 - hat[8] * nd) * inl;
+        G[9] = (dn1 - hat[9] * nd) * inl;
+        G[10] = (dn2 - hat[10] * nd) * inl;
+        Sk = sG - dW_alpha;
+        Tb *= e;
+    };
+
+    const int64_t cap = ws.max_instances;
+    int64_t beg = ws.tile_start[tile], end = ws.tile_start[tile + 1];
+    if (end > cap) end = cap;
+    if (beg > end) beg = end;
+    const ss_rec* recs = ws.rec + vl.rec_off;
+    float* grad = ws.grad_rec + vl.rec_off * SS_NGRAD;
+    for (int64_t base = beg; base < end; base += RB) {
+        const int nb = (int)min((int64_t)RB, end - base);
+        __syncthreads();
+        if ((int)threadIdx.x < nb) {
+            uint32_t id = (uint32_t)(ws.keys[base + threadIdx.x] & 0xffffffffull);
+            const ss_rec rc = recs[id];
+            S.r0[threadIdx.x] = rc.r0;
+            S.r1[threadIdx.x] = rc.r1;
+            float prx = __fadd_rn(__fsub_rn(rc.r2.x, (float)x0), rc.r2.z);
+            float pry = __fadd_rn(__fsub_rn(rc.r2.y, (float)y0), rc.r2.w);
+            S.pz[threadIdx.x] = make_float4(prx, pry, rc.r3.x, rc.r3.y);
+            S.meta[threadIdx.x] = make_uint4(__float_as_uint(rc.r3.z), __float_as_uint(rc.r3.w), __float_as_uint(rc.r4.w), id);
+            S.c0[threadIdx.x] = make_float4(rc.r4.x, rc.r4.y, rc.r4.z, rc.r5.x);
+            S.c1[threadIdx.x] = make_float4(rc.r5.y, rc.r5.z, rc.r5.w, rc.r6.x);
+            S.c2[threadIdx.x] = make_float4(rc.r6.y, rc.r6.z, rc.r6.w, 0.5f * (rc.r3.x + rc.r3.y));
+        }
+        __syncthreads();
+        if (__all_sync(0xffffffffu, done)) continue;
+        for (int c0 = 0; c0 < nb; c0 += 32) {
+            const int j = c0 + lane;
+            bool ov = false;
+            if (j < nb) {
+                uint4 m = S.meta[j];
+                int i0 = m.x & 0xffff, i1 = m.x >> 16, j0 = m.y & 0xffff, j1 = m.y >> 16;
+                ov = i0 <= gx1 && i1 >= gx0 && j0 <= gy1 && j1 >= gy0;
+            }
+            uint32_t mask = __ballot_sync(0xffffffffu, ov);
+            while (mask) {
+                const int b = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const int s = c0 + b;
+                const float4 r0 = S.r0[s], r1 = S.r1[s], pz = S.pz[s];
+                const float dx = xl - pz.x, dy = yl - pz.y;
+                ss_hit h = ss_pixel_test(r0, r1, dx, dy, rc2);
+                bool cov = h.cover && !done;
+                const uint4 m = S.meta[s];
+                if (m.z & SS_FLAG_RECT_TEST) {
+                    int i0 = m.x & 0xffff, i1 = m.x >> 16, j0 = m.y & 0xffff, j1 = m.y >> 16;
+                    cov = cov && px >= i0 && px <= i1 && py >= j0 && py <= j1;
+                }
+                float gr[G_N];
+#pragma unroll
+                for (int q = 0; q < G_N; ++q) gr[q] = 0.f;
+                bool contrib = false;
+                if (cov) {
+                    const float rho2 = __fdividef(h.q, h.t);
+                    const float ex = __expf(-0.5f * rho2);
+                    const float w = r1.w * ex;
+                    // replay of Algorithm 1: same condition as the forward kernel
+                    if (k < 0) {
+                        k = 0;
+                        enter_layer(0);
+                    } else if (Wr > 0.f && pz.z > zmax) {
+                        ++k;
+                        Wr = 0.f;
+                        zmax = 0.f;
+                        if (k >= K) done = true;
+                        else enter_layer(k);
+                    }
+                    if (!done) {
+                        zmax = fmaxf(zmax, pz.w);
+                        Wr += w;
+                        const float4 c0v = S.c0[s], c1v = S.c1[s], c2v = S.c2[s];
+                        const float ch[SS_NCH] = {c0v.x, c0v.y, c0v.z, c0v.w, c1v.x, c1v.y,
+                                                  c1v.z, c1v.w, c2v.x, c2v.y, c2v.z, c2v.w};
+                        float dLdw = -Sk;
+#pragma unroll
+                        for (int c = 0; c < SS_NCH; ++c) {
+                            dLdw = fmaf(G[c], ch[c], dLdw);
+                            gr[G_CH + c] = G[c] * w;
+                        }
+                        // w = n_f exp(-rho2 / 2), rho2 = q / s2^2 (Eq. mip_weight)
+                        gr[G_NF] = dLdw * ex;
+                        const float grho = -0.5f * w * dLdw;
+                        const float it = 1.f / h.t;
+                        const float gs0 = 2.f * grho * h.s0 * it, gs1 = 2.f * grho * h.s1 * it;
+                        const float gs2 = -2.f * grho * rho2 / h.s2;
+                        gr[G_P + 0] = gs0 * dx; gr[G_P + 1] = gs0 * dy;
+                        gr[G_P + 2] = gs1 * dx; gr[G_P + 3] = gs1 * dy;
+                        gr[G_A2] = gs2 * dx; gr[G_B2] = gs2 * dy;
+                        gr[G_PX] = -(gs0 * r0.x + gs1 * r0.z + gs2 * r1.x);
+                        gr[G_PY] = -(gs0 * r0.y + gs1 * r0.w + gs2 * r1.y);
+                        contrib = true;
+                    }
+                }
+                // warp reduction, then one add per value
+                if (__any_sync(0xffffffffu, contrib)) {
+#pragma unroll
+                    for (int q = 0; q < G_N; ++q) {
+                        float v = gr[q];
+                        v += __shfl_xor_sync(0xffffffffu, v, 16);
+                        v += __shfl_xor_sync(0xffffffffu, v, 8);
+                        v += __shfl_xor_sync(0xffffffffu, v, 4);
+                        v += __shfl_xor_sync(0xffffffffu, v, 2);
+                        v += __shfl_xor_sync(0xffffffffu, v, 1);
+                        gr[q] = v;
+                    }
+                    float mine = 0.f;
+#pragma unroll
+                    for (int q = 0; q < G_N; ++q)
+                        if (lane == q) mine = gr[q];
+                    if (lane < G_N) atomicAdd(grad + (int64_t)m.w * SS_NGRAD + lane, mine);
+                }
+            }
+        }
+    }
+}
+
+void ss_launch_raster_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st) {
+    if (L.total_tiles <= 0) return;
+    raster_bwd_kernel<<<L.total_tiles, 256, 0, st>>>(ws, a);
+}
+
+// ------------------------------------------------------------------------
+// projection + shading adjoint: one thread per surfel, loop over its views
+
+__device__ __forceinline__ int64_t spec_level_off_b(const ss_env_desc& ed, int i, int& W, int& H) {
+    int64_t off = 0;
+    for (int k = 0; k < i; ++k) off += (int64_t)max(ed.width >> k, 8) * max(ed.height >> k, 4) * 3;
+    W = max(ed.width >> i, 8);
+    H = max(ed.height >> i, 4);
+    return off;
+}
+
+// bilinear value, d/du, d/dv of a 3-channel map; optionally scatter dOut * weights
+struct lk3 {
+    float v[3], du[3], dv[3];
+};
+__device__ __forceinline__ lk3 lookup3(const float* T, float u, float v, int W, int H, bool wrap) {
+    ss_taps t = bilinear_taps(u, v, W, H, wrap);
+    lk3 r;
+    for (int c = 0; c < 3; ++c) {
+        float a = T[t.i00 * 3 + c], b = T[t.i01 * 3 + c], d = T[t.i10 * 3 + c], e = T[t.i11 * 3 + c];
+        r.v[c] = (1.f - t.fy) * ((1.f - t.fx) * a + t.fx * b) + t.fy * ((1.f - t.fx) * d + t.fx * e);
+        r.du[c] = (float)W * ((1.f - t.fy) * (b - a) + t.fy * (e - d));
+        r.dv[c] = (float)H * ((1.f - t.fx) * (d - a) + t.fx * (e - b));
+    }
+    return r;
+}
+__device__ __forceinline__ void scatter3(float* D, float u, float v, int W, int H, bool wrap, const float g[3],
+                                         float scale) {
+    ss_taps t = bilinear_taps(u, v, W, H, wrap);
+    const float w00 = (1.f - t.fx) * (1.f - t.fy) * scale, w01 = t.fx * (1.f - t.fy) * scale,
+                w10 = (1.f - t.fx) * t.fy * scale, w11 = t.fx * t.fy * scale;
+    for (int c = 0; c < 3; ++c) {
+        if (g[c] == 0.f) continue;
+        atomicAdd(D + t.i00 * 3 + c, w00 * g[c]);
+        atomicAdd(D + t.i01 * 3 + c, w01 * g[c]);
+        atomicAdd(D + t.i10 * 3 + c, w10 * g[c]);
+        atomicAdd(D + t.i11 * 3 + c, w11 * g[c]);
+    }
+}
+// d(u, v)/d(direction) for the equirect map of a unit direction d
+__device__ __forceinline__ void uv_grad(const float d[3], float gu, float gv, float out[3]) {
+    const float rxz = fmaxf(d[0] * d[0] + d[2] * d[2], 1e-20f);
+    // u = atan2(d_x, -d_z) / 2pi + 1/2
+    const float k = gu * (0.5f / SS_PI_F) / rxz;
+    out[0] = k * (-d[2]);
+    out[2] = k * d[0];
+    out[1] = 0.f;
+    // v = acos(d_y / |d|) / pi; with |d| = 1: dv/dd = -(e_y - d_y d) / (pi sqrt(1 - d_y^2))
+    const float s = sqrtf(rxz);
+    const float kv = -gv / (SS_PI_F * s);
+    out[0] += kv * (-d[1] * d[0]);
+    out[1] += kv * (1.f - d[1] * d[1]);
+    out[2] += kv * (-d[1] * d[2]);
+}
+
+__global__ void __launch_bounds__(128) project_bwd_kernel(ss_ws_view ws, ss_bwd_args A, int64_t n_total) {
+    const ss_layout* L = ws.layout;
+    const ss_fwd_args& a = A.f;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_total) return;
+    int scene = 0;
+    while (scene + 1 < L->n_scenes && i >= L->scene_begin[scene + 1]) ++scene;
+    const float c[3] = {a.s.pos[i * 3], a.s.pos[i * 3 + 1], a.s.pos[i * 3 + 2]};
+    const float4 q4 = *reinterpret_cast<const float4*>(a.s.quat + i * 4);
+    const float2 ls = *reinterpret_cast<const float2*>(a.s.log_scale + i * 2);
+    const float rho[3] = {a.s.albedo[i * 3], a.s.albedo[i * 3 + 1], a.s.albedo[i * 3 + 2]};
+    const float rough = a.s.roughness[i], metal = a.s.metallic[i];
+    float Rq[9];
+    quat_rot(q4.x, q4.y, q4.z, q4.w, Rq);
+    const float su = expf(ls.x), sv = expf(ls.y);
+    const float tu[3] = {su * Rq[0], su * Rq[3], su * Rq[6]};
+    const float tv[3] = {sv * Rq[1], sv * Rq[4], sv * Rq[7]};
+    const float nrm[3] = {Rq[2], Rq[5], Rq[8]};
+    const float sig = a.p.sigma_f;
+    const int nL = a.ed.n_levels;
+    const int64_t irr_stride = (int64_t)a.ed.irr_width * a.ed.irr_height * 3;
+    int Wt, Ht;
+    const int64_t spec_stride = spec_level_off_b(a.ed, nL, Wt, Ht);
+    const float* irr = a.env.irr + scene * irr_stride;
+    const float* spec = a.env.spec + scene * spec_stride;
+    float* d_irr = A.genv.irr ? A.genv.irr + scene * irr_stride : nullptr;
+    float* d_spec = A.genv.spec ? A.genv.spec + scene * spec_stride : nullptr;
+    const int lutn = a.p.lut_n;
+    const float* LUT = a.env.lut;
+
+    // accumulated parameter gradients
+    float gc[3] = {0, 0, 0}, gRq[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, gsu = 0.f, gsv = 0.f;
+    float grho[3] = {0, 0, 0}, grough = 0.f, gmetal = 0.f;
+
+    for (int v = L->scene_view_begin[scene]; v < L->scene_view_begin[scene + 1]; ++v) {
+        const ss_view_layout& vl = L->v[v];
+        const int64_t r = vl.rec_off + (i - vl.surfel_begin);
+        const uint32_t flags = __float_as_uint(ws.rec[r].r4.w);
+        if (!(flags & SS_FLAG_VALID)) continue;
+        const float* gr = ws.grad_rec + r * SS_NGRAD;
+        float G[G_N];
+        bool any = false;
+        for (int k = 0; k < G_N; ++k) {
+            G[k] = gr[k];
+            any = any || (G[k] != 0.f);
+        }
+        if (!any) continue;
+        const ss_camera& cam = a.cams[v];
+        const float* Rc = cam.R;
+        const float fx = cam.fx, fy = cam.fy;
+        // ---- recompute the forward quantities (FP32 suffices for derivatives)
+        float cp[3], tuc[3], tvc[3];
+        for (int k = 0; k < 3; ++k) {
+            cp[k] = Rc[k * 3] * c[0] + Rc[k * 3 + 1] * c[1] + Rc[k * 3 + 2] * c[2] + cam.t[k];
+            tuc[k] = Rc[k * 3] * tu[0] + Rc[k * 3 + 1] * tu[1] + Rc[k * 3 + 2] * tu[2];
+            tvc[k] = Rc[k * 3] * tv[0] + Rc[k * 3 + 1] * tv[1] + Rc[k * 3 + 2] * tv[2];
+        }
+        const float cz = cp[2];
+        const float mx = cp[0] / cz, my = cp[1] / cz;
+        const float ax = tuc[0] - mx * tuc[2], ay = tuc[1] - my * tuc[2];
+        const float bx = tvc[0] - mx * tvc[2], by = tvc[1] - my * tvc[2];
+        const ss_view_geo& vg = ws.vgeo[v];
+        const float cmo[3] = {(c[0] - vg.o_hi[0]) - vg.o_lo[0], (c[1] - vg.o_hi[1]) - vg.o_lo[1],
+                              (c[2] - vg.o_hi[2]) - vg.o_lo[2]};
+        const float ncx = Rc[0] * nrm[0] + Rc[1] * nrm[1] + Rc[2] * nrm[2];
+        const float ncy = Rc[3] * nrm[0] + Rc[4] * nrm[1] + Rc[5] * nrm[2];
+        const float4 r1 = ws.rec[r].r1;
+        const float A2 = r1.x, B2 = r1.y;
+        const float Nd = ss_plane_distance(q4, c[0], c[1], c[2], vg.o_hi, vg.o_lo);
+        const float detR = vg.detR;
+        const float det0 = detR * su * sv * Nd / cz;
+        const float icz = 1.f / cz, icz2 = icz * icz;
+        const float m11 = fx * fx * (ax * ax + bx * bx) * icz2;
+        const float m12 = fx * fy * (ax * ay + bx * by) * icz2;
+        const float m22 = fy * fy * (ay * ay + by * by) * icz2;
+        const float sdg = fx * fy * det0 * icz2;
+        const float Dn = sdg * sdg + sig * (m11 + m22) + sig * sig;
+        const float nf = fabsf(sdg) * rsqrtf(Dn);
+        const float qa = (m22 + sig) / Dn, qb = -m12 / Dn, qc = (m11 + sig) / Dn;
+        const float rsD = rsqrtf(Dn);
+
+        // ---- raster parameters -> (qa, qb, qc, Dn)
+        float dqa = 0.f, dqb = 0.f, dqc = 0.f, dDn = 0.f;
+        if (qa >= qc) {
+            const float P00 = sqrtf(qa), P01 = qb / P00, P11 = rsD / P00;
+            dqb += G[G_P + 1] / P00;
+            dDn += G[G_P + 3] * (-0.5f * rsD / Dn) / P00;
+            const float dP00 = G[G_P + 0] - G[G_P + 1] * P01 / P00 - G[G_P + 3] * P11 / P00;
+            dqa += dP00 / (2.f * P00);
+        } else {
+            const float l = sqrtf(qc), P00 = qb / l, P10 = rsD / l;
+            dqb += G[G_P + 0] / l;
+            dDn += G[G_P + 2] * (-0.5f * rsD / Dn) / l;
+            const float dl = G[G_P + 1] - G[G_P + 0] * P00 / l - G[G_P + 2] * P10 / l;
+            dqc += dl / (2.f * l);
+        }
+        float dm11 = dqc / Dn, dm12 = -dqb / Dn, dm22 = dqa / Dn;
+        dDn += -(dqa * qa + dqb * qb + dqc * qc) / Dn;
+        // n_f = |sdg| / sqrt(Dn)
+        float dsdg = G[G_NF] * copysignf(1.f, sdg) * rsD;
+        dDn += -0.5f * G[G_NF] * nf / Dn;
+        // Dn = sdg^2 + sig (m11 + m22) + sig^2
+        dsdg += 2.f * sdg * dDn;
+        dm11 += sig * dDn;
+        dm22 += sig * dDn;
+        // ---- (m11, m12, m22, sdg) -> (a, b, det0, cz)
+        float dcz = 0.f;
+        const float ddet0 = dsdg * fx * fy * icz2;
+        dcz += -2.f * dsdg * sdg * icz;
+        float dax = icz2 * (dm11 * fx * fx * 2.f * ax + dm12 * fx * fy * ay);
+        float dbx = icz2 * (dm11 * fx * fx * 2.f * bx + dm12 * fx * fy * by);
+        float day = icz2 * (dm22 * fy * fy * 2.f * ay + dm12 * fx * fy * ax);
+        float dby = icz2 * (dm22 * fy * fy * 2.f * by + dm12 * fx * fy * bx);
+        dcz += -2.f * icz * (dm11 * m11 + dm12 * m12 + dm22 * m22);
+        // ---- A2 = cz n'_x / (fx Nd), B2 = cz n'_y / (fy Nd), det0 = detR su sv Nd / cz
+        float dNd = 0.f, dncx = 0.f, dncy = 0.f;
+        dcz += (G[G_A2] * A2 + G[G_B2] * B2) * icz;
+        dncx += G[G_A2] * cz / (fx * Nd);
+        dncy += G[G_B2] * cz / (fy * Nd);
+        dNd += -(G[G_A2] * A2 + G[G_B2] * B2) / Nd;
+        const float kdet = detR * su * sv * icz;     // det0 / Nd
+        dNd += ddet0 * kdet;
+        gsu += ddet0 * detR * sv * Nd * icz;
+        gsv += ddet0 * detR * su * Nd * icz;
+        dcz += -ddet0 * det0 * icz;
+        float dn[3], dcv[3];
+        for (int k = 0; k < 3; ++k) {
+            dn[k] = dncx * Rc[k] + dncy * Rc[3 + k] + dNd * cmo[k];   // n' = R n, Nd = n.(c - o)
+            dcv[k] = dNd * nrm[k];
+        }
+        // ---- a = t'_u - m t'_uz, b = t'_v - m t'_vz ; p = f m + c
+        float dtuc[3] = {dax, day, -(dax * mx + day * my)};
+        float dtvc[3] = {dbx, dby, -(dbx * mx + dby * my)};
+        float dmx = -(dax * tuc[2] + dbx * tvc[2]) + fx * G[G_PX];
+        float dmy = -(day * tuc[2] + dby * tvc[2]) + fy * G[G_PY];
+        // depth channel = c'_z
+        dcz += G[G_CH + 11];
+        float dcp[3] = {dmx * icz, dmy * icz, dcz - (dmx * mx + dmy * my) * icz};
+        for (int k = 0; k < 3; ++k) {
+            dcv[k] += Rc[k] * dcp[0] + Rc[3 + k] * dcp[1] + Rc[6 + k] * dcp[2];
+            const float dtu = Rc[k] * dtuc[0] + Rc[3 + k] * dtuc[1] + Rc[6 + k] * dtuc[2];
+            const float dtv = Rc[k] * dtvc[0] + Rc[3 + k] * dtvc[1] + Rc[6 + k] * dtvc[2];
+            // t_u = su R[:,0], t_v = sv R[:,1]
+            gsu += dtu * Rq[k * 3 + 0];
+            gsv += dtv * Rq[k * 3 + 1];
+            gRq[k * 3 + 0] += su * dtu;
+            gRq[k * 3 + 1] += sv * dtv;
+        }
+        // ---- shading (Eq. ibl) and the AOV channels
+        const float ox = -(Rc[0] * cam.t[0] + Rc[3] * cam.t[1] + Rc[6] * cam.t[2]);
+        const float oy = -(Rc[1] * cam.t[0] + Rc[4] * cam.t[1] + Rc[7] * cam.t[2]);
+        const float oz = -(Rc[2] * cam.t[0] + Rc[5] * cam.t[1] + Rc[8] * cam.t[2]);
+        float wv[3] = {ox - c[0], oy - c[1], oz - c[2]};
+        const float wl = sqrtf(wv[0] * wv[0] + wv[1] * wv[1] + wv[2] * wv[2]);
+        const float wo[3] = {wv[0] / wl, wv[1] / wl, wv[2] / wl};
+        const float fs = (flags & SS_FLAG_FLIPPED) ? -1.f : 1.f;
+        const float ns[3] = {fs * nrm[0], fs * nrm[1], fs * nrm[2]};
+        const float mup = ns[0] * wo[0] + ns[1] * wo[1] + ns[2] * wo[2];
+        const float mu = fminf(fmaxf(mup, 0.f), 1.f);
+        const float refl[3] = {2.f * mup * ns[0] - wo[0], 2.f * mup * ns[1] - wo[1], 2.f * mup * ns[2] - wo[2]};
+        float dns[3] = {G[G_CH + 8], G[G_CH + 9], G[G_CH + 10]};
+        for (int k = 0; k < 3; ++k) grho[k] += G[G_CH + 3 + k];
+        grough += G[G_CH + 6];
+        gmetal += G[G_CH + 7];
+        const float dcol[3] = {G[G_CH + 0], G[G_CH + 1], G[G_CH + 2]};
+        if (dcol[0] != 0.f || dcol[1] != 0.f || dcol[2] != 0.f) {
+            float un, vn, ur, vr;
+            dir_to_uv(ns[0], ns[1], ns[2], un, vn);
+            dir_to_uv(refl[0], refl[1], refl[2], ur, vr);
+            lk3 Ld = lookup3(irr, un, vn, a.ed.irr_width, a.ed.irr_height, true);
+            const float rcl = fminf(fmaxf(rough, 0.f), 1.f);
+            const float lc = rcl * (float)(nL - 1);
+            const int l0 = min((int)floorf(lc), nL - 1), l1 = min(l0 + 1, nL - 1);
+            const float lf = lc - (float)l0;
+            int W0, H0, W1, H1;
+            const int64_t o0 = spec_level_off_b(a.ed, l0, W0, H0), o1 = spec_level_off_b(a.ed, l1, W1, H1);
+            lk3 S0 = lookup3(spec + o0, ur, vr, W0, H0, true), S1 = lookup3(spec + o1, ur, vr, W1, H1, true);
+            ss_taps lt = bilinear_taps(mu, rcl, lutn, lutn, false);
+            float be[2], dbe_mu[2], dbe_r[2];
+            for (int z = 0; z < 2; ++z) {
+                const float a0 = LUT[lt.i00 * 2 + z], a1 = LUT[lt.i01 * 2 + z], a2 = LUT[lt.i10 * 2 + z],
+                            a3 = LUT[lt.i11 * 2 + z];
+                be[z] = (1.f - lt.fy) * ((1.f - lt.fx) * a0 + lt.fx * a1) + lt.fy * ((1.f - lt.fx) * a2 + lt.fx * a3);
+                dbe_mu[z] = (float)lutn * ((1.f - lt.fy) * (a1 - a0) + lt.fy * (a3 - a2));
+                dbe_r[z] = (float)lutn * ((1.f - lt.fx) * (a2 - a0) + lt.fx * (a3 - a1));
+            }
+            float dLd[3], dLs[3], dbe1 = 0.f, dbe2 = 0.f, dlf = 0.f;
+            for (int k = 0; k < 3; ++k) {
+                const float F0 = 0.04f * (1.f - metal) + rho[k] * metal;
+                const float kd = (1.f - F0) * (1.f - metal);
+                const float Ls = (1.f - lf) * S0.v[k] + lf * S1.v[k];
+                // col = kd rho Ld + Ls (F0 be1 + be2)
+                const float dkd = dcol[k] * rho[k] * Ld.v[k];
+                grho[k] += dcol[k] * kd * Ld.v[k];
+                dLd[k] = dcol[k] * kd * rho[k];
+                dLs[k] = dcol[k] * (F0 * be[0] + be[1]);
+                float dF0 = dcol[k] * Ls * be[0];
+                dbe1 += dcol[k] * Ls * F0;
+                dbe2 += dcol[k] * Ls;
+                dF0 += -dkd * (1.f - metal);
+                gmetal += -dkd * (1.f - F0);
+                grho[k] += dF0 * metal;
+                gmetal += dF0 * (rho[k] - 0.04f);
+                dlf += dLs[k] * (S1.v[k] - S0.v[k]);
+            }
+            // roughness: LUT row and level coordinate (both clamped to [0, 1])
+            if (rough > 0.f && rough < 1.f) grough += dbe1 * dbe_r[0] + dbe2 * dbe_r[1] + dlf * (float)(nL - 1);
+            float dmu = dbe1 * dbe_mu[0] + dbe2 * dbe_mu[1];
+            float dmup = (mup > 0.f && mup < 1.f) ? dmu : 0.f;
+            // environment texels
+            if (d_irr) scatter3(d_irr, un, vn, a.ed.irr_width, a.ed.irr_height, true, dLd, 1.f);
+            if (d_spec) {
+                scatter3(d_spec + o0, ur, vr, W0, H0, true, dLs, 1.f - lf);
+                scatter3(d_spec + o1, ur, vr, W1, H1, true, dLs, lf);
+            }
+            // directions: Ld(uv(ns)), Ls(uv(refl))
+            float gun = 0.f, gvn = 0.f, gur = 0.f, gvr = 0.f;
+            for (int k = 0; k < 3; ++k) {
+                gun += dLd[k] * Ld.du[k];
+                gvn += dLd[k] * Ld.dv[k];
+                gur += dLs[k] * ((1.f - lf) * S0.du[k] + lf * S1.du[k]);
+                gvr += dLs[k] * ((1.f - lf) * S0.dv[k] + lf * S1.dv[k]);
+            }
+            float dnsv[3], drefl[3];
+            uv_grad(ns, gun, gvn, dnsv);
+            float rl = sqrtf(refl[0] * refl[0] + refl[1] * refl[1] + refl[2] * refl[2]);
+            float rn[3] = {refl[0] / rl, refl[1] / rl, refl[2] / rl};
+            float drn[3];
+            uv_grad(rn, gur, gvr, drn);
+            // through the normalisation of refl (|refl| = 1 up to rounding)
+            float rd = drn[0] * rn[0] + drn[1] * rn[1] + drn[2] * rn[2];
+            for (int k = 0; k < 3; ++k) drefl[k] = (drn[k] - rn[k] * rd) / rl;
+            // refl = 2 mup ns - wo, mup = ns.wo
+            float dwo[3];
+            const float rdn = drefl[0] * ns[0] + drefl[1] * ns[1] + drefl[2] * ns[2];
+            dmup += 2.f * rdn;
+            for (int k = 0; k < 3; ++k) {
+                dns[k] += dnsv[k] + 2.f * mup * drefl[k] + dmup * wo[k];
+                dwo[k] = -drefl[k] + dmup * ns[k];
+            }
+            // wo = normalize(o - c)
+            const float wd = dwo[0] * wo[0] + dwo[1] * wo[1] + dwo[2] * wo[2];
+            for (int k = 0; k < 3; ++k) dcv[k] += -(dwo[k] - wo[k] * wd) / wl;
+        }
+        for (int k = 0; k < 3; ++k) dn[k] += fs * dns[k];
+        for (int k = 0; k < 3; ++k) {
+            gRq[k * 3 + 2] += dn[k];
+            gc[k] += dcv[k];
+        }
+    }
+    // ---- R(q / |q|) -> q
+    const float qn = rsqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
+    const float w = q4.x * qn, x = q4.y * qn, y = q4.z * qn, z = q4.w * qn;
+    const float* d = gRq;
+    const float gw = 2.f * (-z * d[1] + y * d[2] + z * d[3] - x * d[5] - y * d[6] + x * d[7]);
+    const float gx = 2.f * (y * d[1] + z * d[2] + y * d[3] - 2.f * x * d[4] - w * d[5] + z * d[6] + w * d[7] - 2.f * x * d[8]);
+    const float gy = 2.f * (-2.f * y * d[0] + x * d[1] + w * d[2] + x * d[3] + z * d[5] - w * d[6] + z * d[7] - 2.f * y * d[8]);
+    const float gz = 2.f * (-2.f * z * d[0] - w * d[1] + x * d[2] + w * d[3] - 2.f * z * d[4] + y * d[5] + x * d[6] + y * d[7]);
+    const float dotq = gw * w + gx * x + gy * y + gz * z;
+    const ss_surfel_grads& g = A.g;
+    if (g.quat) {
+        g.quat[i * 4 + 0] += (gw - w * dotq) * qn;
+        g.quat[i * 4 + 1] += (gx - x * dotq) * qn;
+        g.quat[i * 4 + 2] += (gy - y * dotq) * qn;
+        g.quat[i * 4 + 3] += (gz - z * dotq) * qn;
+    }
+    if (g.log_scale) {
+        g.log_scale[i * 2 + 0] += gsu * su;
+        g.log_scale[i * 2 + 1] += gsv * sv;
+    }
+    if (g.pos)
+        for (int k = 0; k < 3; ++k) g.pos[i * 3 + k] += gc[k];
+    if (g.albedo)
+        for (int k = 0; k < 3; ++k) g.albedo[i * 3 + k] += grho[k];
+    if (g.roughness) g.roughness[i] += grough;
+    if (g.metallic) g.metallic[i] += gmetal;
+}
+
+void ss_launch_project_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st) {
+    int64_t n = L.scene_begin[L.n_scenes];
+    if (n <= 0) return;
+    project_bwd_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(ws, a, n);
+}

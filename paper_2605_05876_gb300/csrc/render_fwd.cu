@@ -104,22 +104,7 @@ __global__ void __launch_bounds__(256) project_kernel(ss_ws_view ws, ss_fwd_args
         // camera from the surfel plane.  It is the one ill-conditioned quantity for
         // nearly edge-on surfels, so it is formed in double-float from the quaternion,
         // n = (2(xz+wy), 2(yz-wx), w^2-x^2-y^2+z^2) / |q|^2.
-        float Nd;
-        {
-            const ss_view_geo& vg = ws.vgeo[v];
-            const float qw = q.x, qx = q.y, qy = q.z, qz = q.w;
-            dfl n0 = df_add(two_prod(qx, qz), two_prod(qw, qy));
-            dfl n1 = df_add(two_prod(qy, qz), two_prod(-qw, qx));
-            dfl n2 = df_add(df_add(two_prod(qw, qw), two_prod(-qx, qx)), df_add(two_prod(-qy, qy), two_prod(qz, qz)));
-            n0 = {2.f * n0.hi, 2.f * n0.lo};
-            n1 = {2.f * n1.hi, 2.f * n1.lo};
-            dfl d0 = df_add_f({-vg.o_hi[0], -vg.o_lo[0]}, c0);
-            dfl d1 = df_add_f({-vg.o_hi[1], -vg.o_lo[1]}, c1);
-            dfl d2 = df_add_f({-vg.o_hi[2], -vg.o_lo[2]}, c2);
-            dfl nd = df_add(df_add(df_mul(n0, d0), df_mul(n1, d1)), df_mul(n2, d2));
-            const float qq = qw * qw + qx * qx + qy * qy + qz * qz;
-            Nd = (nd.hi + nd.lo) / qq;
-        }
+        const float Nd = ss_plane_distance(q, c0, c1, c2, ws.vgeo[v].o_hi, ws.vgeo[v].o_lo);
         const float ncx = cam.R[0] * nrm[0] + cam.R[1] * nrm[1] + cam.R[2] * nrm[2];   // n' = R n
         const float ncy = cam.R[3] * nrm[0] + cam.R[4] * nrm[1] + cam.R[5] * nrm[2];
         // (t'_u x t'_v) . c'/c'_z = det R s_u s_v N_d / c'_z

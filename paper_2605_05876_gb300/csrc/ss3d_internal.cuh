@@ -138,6 +138,26 @@ __device__ __forceinline__ dfl df_dot3_add(float a0, float a1, float a2, float x
     return df_add_f(acc, b);
 }
 
+// N_d = n . (c - o): signed distance of the camera centre o from the plane of
+// a surfel with centre c and normal n = R(q/|q|) e_z.  For nearly edge-on
+// surfels it is a small difference of O(1) terms, so it is formed in
+// double-float from n = (2(xz+wy), 2(yz-wx), w^2-x^2-y^2+z^2) / |q|^2 and o.
+__device__ __forceinline__ float ss_plane_distance(float4 q, float c0, float c1, float c2, const float o_hi[3],
+                                                   const float o_lo[3]) {
+    const float qw = q.x, qx = q.y, qy = q.z, qz = q.w;
+    dfl n0 = df_add(two_prod(qx, qz), two_prod(qw, qy));
+    dfl n1 = df_add(two_prod(qy, qz), two_prod(-qw, qx));
+    dfl n2 = df_add(df_add(two_prod(qw, qw), two_prod(-qx, qx)), df_add(two_prod(-qy, qy), two_prod(qz, qz)));
+    n0 = {2.f * n0.hi, 2.f * n0.lo};
+    n1 = {2.f * n1.hi, 2.f * n1.lo};
+    dfl d0 = df_add_f({-o_hi[0], -o_lo[0]}, c0);
+    dfl d1 = df_add_f({-o_hi[1], -o_lo[1]}, c1);
+    dfl d2 = df_add_f({-o_hi[2], -o_lo[2]}, c2);
+    dfl nd = df_add(df_add(df_mul(n0, d0), df_mul(n1, d1)), df_mul(n2, d2));
+    const float qq = qw * qw + qx * qx + qy * qy + qz * qz;
+    return (nd.hi + nd.lo) / qq;
+}
+
 // ------------------------------------------------------------------------
 // small math
 
