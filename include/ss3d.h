@@ -114,7 +114,31 @@ typedef struct ss_render_params {
     int32_t write_aov;       /* 1: also write the 9 AOV channels */
     int32_t lut_n;           /* BRDF table resolution (n x n) */
     int64_t max_instances;   /* capacity of the (tile, surfel) instance list */
+    int32_t collect_stats;   /* 1: count work (see ss_read_stats); off by default */
+    int32_t pad_;
 } ss_render_params;
+
+/* Work counters of the last forward/backward pair (collect_stats = 1). */
+typedef struct ss_stats {
+    int64_t instances;       /* (tile, surfel) instances */
+    int64_t rect_tests;      /* (pixel, surfel) pairs with the pixel inside the support rectangle */
+    int64_t lane_tests;      /* pixel tests executed by the forward raster */
+    int64_t fragments;       /* covering fragments accumulated by the forward raster */
+    int64_t layers;          /* composited layers summed over pixels */
+    int64_t bwd_fragments;   /* fragments differentiated by the backward raster */
+    int64_t reserved[2];
+} ss_stats;
+
+/* Stage timing: CUDA events recorded on the launching stream around each
+ * stage of every call made between ss_profile_begin and ss_profile_end
+ * (host-side state, one profile at a time; not for use inside stream
+ * capture).  Stages: 0 project, 1 bin+sort, 2 raster_fwd, 3 raster_bwd,
+ * 4 project_bwd, 5 env_prefilter, 6 env_prefilter_backward. */
+#define SS_N_STAGES 7
+typedef struct ss_stage_times {
+    float ms[SS_N_STAGES];       /* summed event durations */
+    int32_t launches[SS_N_STAGES];
+} ss_stage_times;
 
 /* Environment map shape.  Every scene has one map of this shape. */
 typedef struct ss_env_desc {
@@ -227,6 +251,14 @@ ss_status ss_render_backward(const ss_batch_desc* b, const ss_surfels* s, const 
                              const float* out_aov_dev, const float* d_rgba_dev, const float* d_aov_dev,
                              ss_surfel_grads* g, ss_env_map_grads* genv, void* ws, size_t ws_bytes,
                              void* stream);
+
+/* Start / stop collecting stage timings (see ss_stage_times).  end
+ * synchronises the recorded events and fills *out. */
+ss_status ss_profile_begin(void);
+ss_status ss_profile_end(ss_stage_times* out);
+
+/* Synchronise the stream and copy the work counters of ws into *out. */
+ss_status ss_read_stats(void* ws, ss_stats* out, void* stream);
 
 /* Synchronise the stream and return (and clear) the device status word in
  * ws: SS_OK or an OR of SS_ERR_CAPACITY / SS_ERR_TIMEOUT / SS_ERR_NONFINITE. */

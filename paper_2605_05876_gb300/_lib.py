@@ -50,7 +50,21 @@ class ss_batch_desc(ctypes.Structure):
 
 class ss_render_params(ctypes.Structure):
     _fields_ = [("r_cut", c_f), ("sigma_f", c_f), ("gamma", c_f), ("k_max", c_i32), ("z_near", c_f),
-                ("bg", c_f * 3), ("write_aov", c_i32), ("lut_n", c_i32), ("max_instances", c_i64)]
+                ("bg", c_f * 3), ("write_aov", c_i32), ("lut_n", c_i32), ("max_instances", c_i64),
+                ("collect_stats", c_i32), ("pad_", c_i32)]
+
+
+class ss_stats(ctypes.Structure):
+    _fields_ = [("instances", c_i64), ("rect_tests", c_i64), ("lane_tests", c_i64), ("fragments", c_i64),
+                ("layers", c_i64), ("bwd_fragments", c_i64), ("reserved", c_i64 * 2)]
+
+
+SS_N_STAGES = 7
+STAGES = ("project", "bin_sort", "raster_fwd", "raster_bwd", "project_bwd", "env_prefilter", "env_prefilter_bwd")
+
+
+class ss_stage_times(ctypes.Structure):
+    _fields_ = [("ms", c_f * SS_N_STAGES), ("launches", c_i32 * SS_N_STAGES)]
 
 
 class ss_env_desc(ctypes.Structure):
@@ -89,6 +103,9 @@ EXPORTS = {
                                    ctypes.POINTER(ss_surfel_grads), ctypes.POINTER(ss_env_map_grads), c_vp,
                                    ctypes.c_size_t, c_vp]),
     "ss_read_status": (c_i32, [c_vp, c_vp]),
+    "ss_read_stats": (c_i32, [c_vp, ctypes.c_void_p, c_vp]),
+    "ss_profile_begin": (c_i32, []),
+    "ss_profile_end": (c_i32, [ctypes.c_void_p]),
 }
 
 

@@ -56,14 +56,18 @@ class Renderer:
     """
 
     def __init__(self, scene, params: dict | None = None, env_levels: int = 6, irr_size=(32, 16),
-                 with_backward: bool = True, capacity_slack: float = 1.3, device: str = "cuda"):
+                 with_backward: bool = True, capacity_slack: float = 1.3, device: str = "cuda",
+                 share_from: "Renderer | None" = None):
         import torch
         self.torch = torch
         self.dev = torch.device(device)
         self.scene = scene
         s = scene.surfels
         f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(self.dev)
-        self.params_t = {k: f32(getattr(s, k)) for k in SURFEL_FIELDS}
+        if share_from is not None:   # same surfels and env maps, other views
+            self.params_t = share_from.params_t
+        else:
+            self.params_t = {k: f32(getattr(s, k)) for k in SURFEL_FIELDS}
         self.n_surfels = s.n
         self.n_views = len(scene.cameras)
         self.n_scenes = scene.n_scenes
@@ -82,14 +86,18 @@ class Renderer:
         check(lib().ss_env_sizes(ctypes.byref(self.ed), ctypes.byref(ni), ctypes.byref(ns), ctypes.byref(na)),
               "ss_env_sizes")
         S = self.n_scenes
-        self.env = torch.from_numpy(np.stack([np.asarray(e, np.float32) for e in scene.envs])).to(self.dev)
-        self.irr = torch.zeros(S, ni.value, device=self.dev)
-        self.spec = torch.zeros(S, ns.value, device=self.dev)
-        self.aux = torch.zeros(S, na.value, device=self.dev)
         self.prm = default_params(**(params or {}))
-        self.lut = torch.zeros(self.prm.lut_n, self.prm.lut_n, 2, device=self.dev)
-        check(lib().ss_brdf_lut(_ptr(self.lut), self.prm.lut_n, _stream()), "ss_brdf_lut")
-        self.prefilter_env()
+        if share_from is not None:
+            self.env, self.irr, self.spec, self.aux, self.lut = (share_from.env, share_from.irr, share_from.spec,
+                                                                 share_from.aux, share_from.lut)
+        else:
+            self.env = torch.from_numpy(np.stack([np.asarray(e, np.float32) for e in scene.envs])).to(self.dev)
+            self.irr = torch.zeros(S, ni.value, device=self.dev)
+            self.spec = torch.zeros(S, ns.value, device=self.dev)
+            self.aux = torch.zeros(S, na.value, device=self.dev)
+            self.lut = torch.zeros(self.prm.lut_n, self.prm.lut_n, 2, device=self.dev)
+            check(lib().ss_brdf_lut(_ptr(self.lut), self.prm.lut_n, _stream()), "ss_brdf_lut")
+            self.prefilter_env()
         self.maps = C.ss_env_maps(_ptr(self.irr), _ptr(self.spec), _ptr(self.lut))
         # outputs
         self.rgba = torch.zeros(self.n_pixels, 4, device=self.dev)
@@ -139,12 +147,33 @@ class Renderer:
               "ss_render_forward")
         return self.rgba, self.aov
 
-    def zero_grads(self):
+    def zero_grads(self, share_from: "Renderer | None" = None):
         torch = self.torch
+        if share_from is not None:
+            self.grads, self.d_irr, self.d_spec, self.d_env = (share_from.grads, share_from.d_irr,
+                                                               share_from.d_spec, share_from.d_env)
+            return
+        if hasattr(self, "grads"):
+            for v in self.grads.values():
+                v.zero_()
+            self.d_irr.zero_()
+            self.d_spec.zero_()
+            self.d_env.zero_()
+            return
         self.grads = {k: torch.zeros_like(v) for k, v in self.params_t.items()}
         self.d_irr = torch.zeros_like(self.irr)
         self.d_spec = torch.zeros_like(self.spec)
         self.d_env = torch.zeros_like(self.env)
+
+    def env_backward(self):
+        check(lib().ss_env_prefilter_backward(ctypes.byref(self.ed), self.n_scenes, _ptr(self.d_irr),
+                                              _ptr(self.d_spec), _ptr(self.aux), _ptr(self.d_env), _stream()),
+              "ss_env_prefilter_backward")
+
+    def stats(self):
+        st = C.ss_stats()
+        check(lib().ss_read_stats(_ptr(self.ws), ctypes.byref(st), _stream()), "ss_read_stats")
+        return {k: int(getattr(st, k)) for k, _ in C.ss_stats._fields_ if k != "reserved"}
 
     def backward(self, d_rgba, d_aov=None, env_grad: bool = True):
         """Accumulate gradients of sum(d_rgba * rgba) + sum(d_aov * aov) into
@@ -160,10 +189,18 @@ class Renderer:
                                        ctypes.byref(ge), _ptr(self.ws), self.ws_bytes, _stream()),
               "ss_render_backward")
         if env_grad:
-            check(lib().ss_env_prefilter_backward(ctypes.byref(self.ed), self.n_scenes, _ptr(self.d_irr),
-                                                  _ptr(self.d_spec), _ptr(self.aux), _ptr(self.d_env), _stream()),
-                  "ss_env_prefilter_backward")
+            self.env_backward()
         return self.grads
+
+
+def profile_begin():
+    check(lib().ss_profile_begin(), "ss_profile_begin")
+
+
+def profile_end() -> dict:
+    t = C.ss_stage_times()
+    check(lib().ss_profile_end(ctypes.byref(t)), "ss_profile_end")
+    return {name: (float(t.ms[i]), int(t.launches[i])) for i, name in enumerate(C.STAGES)}
 
     def read_status(self) -> int:
         return int(lib().ss_read_status(_ptr(self.ws), _stream()))

@@ -3,7 +3,78 @@
 #include <math.h>
 #include <string.h>
 
+#include <vector>
+
 #include "ss3d_internal.cuh"
+
+// ------------------------------------------------------------------------
+// stage timing (host side): events recorded around each stage launch while a
+// profile is open
+namespace {
+struct prof_rec {
+    int stage;
+    cudaEvent_t a, b;
+};
+struct profiler {
+    bool on = false;
+    std::vector<prof_rec> recs;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t take() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+};
+profiler g_prof;
+
+struct stage_scope {
+    int idx = -1;
+    cudaStream_t st;
+    stage_scope(int stage, cudaStream_t s) : st(s) {
+        if (!g_prof.on) return;
+        prof_rec r{stage, g_prof.take(), g_prof.take()};
+        cudaEventRecord(r.a, st);
+        g_prof.recs.push_back(r);
+        idx = (int)g_prof.recs.size() - 1;
+    }
+    ~stage_scope() {
+        if (idx >= 0) cudaEventRecord(g_prof.recs[idx].b, st);
+    }
+};
+}  // namespace
+
+extern "C" ss_status ss_profile_begin(void) {
+    g_prof.on = true;
+    for (auto& r : g_prof.recs) {
+        g_prof.pool.push_back(r.a);
+        g_prof.pool.push_back(r.b);
+    }
+    g_prof.recs.clear();
+    return SS_OK;
+}
+
+extern "C" ss_status ss_profile_end(ss_stage_times* out) {
+    if (!out) return SS_ERR_INVALID_ARG;
+    memset(out, 0, sizeof(*out));
+    ss_status st = SS_OK;
+    for (auto& r : g_prof.recs) {
+        if (cudaEventSynchronize(r.b) != cudaSuccess) st = SS_ERR_CUDA;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) st = SS_ERR_CUDA;
+        out->ms[r.stage] += ms;
+        out->launches[r.stage] += 1;
+        g_prof.pool.push_back(r.a);
+        g_prof.pool.push_back(r.b);
+    }
+    g_prof.recs.clear();
+    g_prof.on = false;
+    return st;
+}
 
 #define CK(x)                                      \
     do {                                           \
@@ -126,6 +197,7 @@ static ss_ws_view carve(void* ws, const ws_plan& w, const ss_render_params& p, i
     char* b = (char*)ws;
     ss_ws_view v;
     v.status = (int*)(b + w.status);
+    v.stats = (unsigned long long*)(b + w.status + SS_STATS_OFFSET);
     v.layout = (ss_layout*)(b + w.layout);
     v.vgeo = (ss_view_geo*)(b + w.vgeo);
     v.rec = (ss_rec*)(b + w.rec);
@@ -183,6 +255,14 @@ extern "C" ss_status ss_workspace_size(const ss_batch_desc* b, const ss_render_p
 // ------------------------------------------------------------------------
 // BRDF table and environment
 
+extern "C" ss_status ss_read_stats(void* ws, ss_stats* out, void* stream) {
+    if (!ws || !out) return SS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(out, (char*)ws + SS_STATS_OFFSET, sizeof(ss_stats), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return SS_OK;
+}
+
 extern "C" ss_status ss_brdf_lut(float* lut_dev, int32_t n, void* stream) {
     if (!lut_dev || n < 4 || n > 1024) return SS_ERR_INVALID_ARG;
     ss_launch_brdf_lut(lut_dev, n, (cudaStream_t)stream);
@@ -211,7 +291,10 @@ extern "C" ss_status ss_env_prefilter(const ss_env_desc* d, int32_t n_envs, cons
                                       float* spec_dev, float* aux_dev, void* stream) {
     if (!env_desc_ok(d) || n_envs < 1 || !env_dev || !irr_dev || !spec_dev || !aux_dev) return SS_ERR_INVALID_ARG;
     if (d->n_levels < 2 && d->n_levels != 1) return SS_ERR_INVALID_ARG;
-    ss_launch_env_prefilter(d, n_envs, env_dev, irr_dev, spec_dev, aux_dev, (cudaStream_t)stream);
+    {
+        stage_scope sc(5, (cudaStream_t)stream);
+        ss_launch_env_prefilter(d, n_envs, env_dev, irr_dev, spec_dev, aux_dev, (cudaStream_t)stream);
+    }
     CK(cudaGetLastError());
     return SS_OK;
 }
@@ -220,7 +303,10 @@ extern "C" ss_status ss_env_prefilter_backward(const ss_env_desc* d, int32_t n_e
                                                const float* d_spec_dev, const float* aux_dev, float* d_env_dev,
                                                void* stream) {
     if (!env_desc_ok(d) || n_envs < 1 || !aux_dev || !d_env_dev) return SS_ERR_INVALID_ARG;
-    ss_launch_env_prefilter_bwd(d, n_envs, d_irr_dev, d_spec_dev, aux_dev, d_env_dev, (cudaStream_t)stream);
+    {
+        stage_scope sc(6, (cudaStream_t)stream);
+        ss_launch_env_prefilter_bwd(d, n_envs, d_irr_dev, d_spec_dev, aux_dev, d_env_dev, (cudaStream_t)stream);
+    }
     CK(cudaGetLastError());
     return SS_OK;
 }
@@ -258,19 +344,27 @@ static ss_status forward_core(const ss_batch_desc* b, const ss_surfels* s, const
     a.out_rgba = out_rgba;
     a.out_aov = p->write_aov ? out_aov : nullptr;
     a.with_backward = with_bwd;
-    CK(cudaMemsetAsync(W.status, 0, sizeof(int), st));
+    CK(cudaMemsetAsync(W.status, 0, 256, st));   // status word and work counters
     set_layout_kernel<<<1, 256, 0, st>>>(W.layout, L);
     view_geo_kernel<<<(L.n_views + 63) / 64, 64, 0, st>>>(b->cams_dev, W.vgeo, L.n_views);
     CK(cudaMemsetAsync(W.tile_count, 0, sizeof(uint32_t) * (size_t)L.total_tiles, st));
     CK(cudaMemsetAsync(W.tile_cursor, 0, sizeof(uint32_t) * (size_t)L.total_tiles, st));
-    ss_launch_project(W, L, a, st);
+    {
+        stage_scope sc(0, st);
+        ss_launch_project(W, L, a, st);
+    }
+    {
+        stage_scope sc(1, st);
+        ss_launch_bin_sort(W, L, a, st);  // for a count, the scatter is bounded by capacity 1
+    }
     if (stop_after_count) {
-        ss_launch_bin_sort(W, L, a, st);  // scan gives the total; scatter is bounded by capacity
         CK(cudaGetLastError());
         return SS_OK;
     }
-    ss_launch_bin_sort(W, L, a, st);
-    ss_launch_raster_fwd(W, L, a, st);
+    {
+        stage_scope sc(2, st);
+        ss_launch_raster_fwd(W, L, a, st);
+    }
     CK(cudaGetLastError());
     return SS_OK;
 }
@@ -342,8 +436,14 @@ extern "C" ss_status ss_render_backward(const ss_batch_desc* b, const ss_surfels
     ss_env_map_grads ge = {nullptr, nullptr};
     a.genv = genv ? *genv : ge;
     CK(cudaMemsetAsync(W.grad_rec, 0, sizeof(float) * SS_NGRAD * (size_t)L.total_records, st));
-    ss_launch_raster_bwd(W, L, a, st);
-    ss_launch_project_bwd(W, L, a, st);
+    {
+        stage_scope sc(3, st);
+        ss_launch_raster_bwd(W, L, a, st);
+    }
+    {
+        stage_scope sc(4, st);
+        ss_launch_project_bwd(W, L, a, st);
+    }
     CK(cudaGetLastError());
     return SS_OK;
 }

@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(256) raster_bwd_kernel(ss_ws_view ws, ss_bwd_a
         for (int c = 0; c < SS_NCH; ++c) g[c] = outc[c] = 0.f;
     }
     bool done = !inside || K == 0;
+    unsigned n_frag = 0;
 
     // replay state (Algorithm 1) and per-layer gradient coefficients
     int k = -1;
@@ -229,6 +230,7 @@ __global__ void __launch_bounds__(256) raster_bwd_kernel(ss_ws_view ws, ss_bwd_a
                         gr[G_PX] = -(gs0 * r0.x + gs1 * r0.z + gs2 * r1.x);
                         gr[G_PY] = -(gs0 * r0.y + gs1 * r0.w + gs2 * r1.y);
                         contrib = true;
+                        ++n_frag;
                     }
                 }
                 // warp reduction, then one add per value
@@ -251,6 +253,11 @@ __global__ void __launch_bounds__(256) raster_bwd_kernel(ss_ws_view ws, ss_bwd_a
                 }
             }
         }
+    }
+    if (a.f.p.collect_stats) {
+        unsigned long long x = n_frag;
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0 && x) atomicAdd(ws.stats + 5, x);
     }
 }
 

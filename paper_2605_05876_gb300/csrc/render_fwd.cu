@@ -252,7 +252,7 @@ void ss_launch_project(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_ar
 // per-tile sort by (z_start, id) (Sec. 3.2.1: sort key z_start; ties by id)
 
 __global__ void __launch_bounds__(1024) scan_kernel(const uint32_t* cnt, uint32_t* start, int n, int* status,
-                                                    int64_t cap) {
+                                                    int64_t cap, unsigned long long* stats) {
     __shared__ uint32_t wsum[32];
     __shared__ uint32_t carry;
     if (threadIdx.x == 0) carry = 0;
@@ -285,6 +285,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const uint32_t* cnt, uint32_
     }
     if (threadIdx.x == 0) {
         start[n] = carry;
+        stats[0] = carry;
         if ((int64_t)carry > cap) atomicOr(status, SS_ERR_CAPACITY);
     }
 }
@@ -399,7 +400,8 @@ __global__ void __launch_bounds__(SORT_THREADS) tile_sort_kernel(ss_ws_view ws, 
 
 void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st) {
     (void)a;
-    scan_kernel<<<1, 1024, 0, st>>>(ws.tile_count, ws.tile_start, L.total_tiles, ws.status, ws.max_instances);
+    scan_kernel<<<1, 1024, 0, st>>>(ws.tile_count, ws.tile_start, L.total_tiles, ws.status, ws.max_instances,
+                                    ws.stats);
     if (L.total_records > 0)
         scatter_kernel<<<(unsigned)((L.total_records + 255) / 256), 256, 0, st>>>(ws, L.total_records);
     static bool attr = false;
@@ -480,6 +482,8 @@ __global__ void __launch_bounds__(256) raster_fwd_kernel(ss_ws_view ws, ss_fwd_a
     float Wg = 0.f, zmax = 0.f, Tb = 1.f, Acov = 0.f;
     int K = 0;
     bool done = !inside;
+    const bool stats = a.p.collect_stats != 0;
+    unsigned n_lane = 0, n_rect = 0, n_frag = 0;
 
     auto flush = [&]() {
         const float invW = 1.f / Wg;
@@ -544,6 +548,12 @@ __global__ void __launch_bounds__(256) raster_fwd_kernel(ss_ws_view ws, ss_fwd_a
                     int i0 = m.x & 0xffff, i1 = m.x >> 16, j0 = m.y & 0xffff, j1 = m.y >> 16;
                     cov = cov && px >= i0 && px <= i1 && py >= j0 && py <= j1;
                 }
+                if (stats && inside) {
+                    int i0 = m.x & 0xffff, i1 = m.x >> 16, j0 = m.y & 0xffff, j1 = m.y >> 16;
+                    ++n_lane;
+                    n_rect += (px >= i0 && px <= i1 && py >= j0 && py <= j1) ? 1u : 0u;
+                    n_frag += cov ? 1u : 0u;
+                }
                 if (cov) {
                     const float w = r1.w * __expf(-0.5f * __fdividef(h.q, h.t));   // Eq. mip_weight
                     if (Wg > 0.f && pz.z > zmax) flush();                          // gap: new layer
@@ -561,6 +571,14 @@ __global__ void __launch_bounds__(256) raster_fwd_kernel(ss_ws_view ws, ss_fwd_a
         }
     }
     if (!done && Wg > 0.f) flush();
+    if (stats) {
+        unsigned long long v[4] = {n_rect, n_lane, n_frag, (unsigned)K * (inside ? 1u : 0u)};
+        for (int q = 0; q < 4; ++q) {
+            unsigned long long x = v[q];
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0 && x) atomicAdd(ws.stats + 1 + q, x);
+        }
+    }
     if (!inside) return;
     float4 o;
     o.x = fmaf(Tb, a.p.bg[0], out[0]);

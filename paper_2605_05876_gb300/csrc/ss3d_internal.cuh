@@ -69,9 +69,12 @@ struct ss_view_geo {
     float pad_;
 };
 
-// device status bits live in the first word of the workspace
+// device status bits live in the first word of the workspace; the work
+// counters (ss_stats, int64 x 8) at byte 64 of the same 256-byte block
+#define SS_STATS_OFFSET 64
 struct ss_ws_view {
     int* status;
+    unsigned long long* stats;
     ss_layout* layout;
     ss_view_geo* vgeo;      // [n_views]
     ss_rec* rec;

@@ -32,7 +32,8 @@ def test_library_exports_every_declared_symbol():
 
 def test_struct_sizes_match_header():
     assert ctypes.sizeof(_lib.ss_camera) == 80
-    assert ctypes.sizeof(_lib.ss_render_params) == 48
+    assert ctypes.sizeof(_lib.ss_render_params) == 56
+    assert ctypes.sizeof(_lib.ss_stats) == 64
 
 
 def test_host_side_argument_errors():
