@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--config", default="config3")
+    ap.add_argument("--views", type=int, default=0, help="render only the first N views (profiling)")
     ap.add_argument("--no-per-view", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -233,6 +234,8 @@ def run_ours(args):
     from paper_2605_05876_gb300.api import Renderer, profile_begin, profile_end
 
     scene = scenes.by_name(args.config)
+    if args.views:
+        scene.cameras = scene.cameras[:args.views]
     V = len(scene.cameras)
     r = Renderer(scene)
     P = r.n_pixels
@@ -352,7 +355,7 @@ def run_ours(args):
     else:
         flops = counts["rect_tests"] * FLOP_TEST + counts["bwd_fragments"] * FLOP_FRAG_BWD
     achieved = flops / t_launch / 1e12
-    workload = f"{args.config}_16x800"
+    workload = f"{args.config}_{V}x800"
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": recorded_traffic(dom, workload),
                 "peak_note": f"FP32 FMA issue: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz "
@@ -381,7 +384,7 @@ def run_ours(args):
         # our kernels per step: env fwd (1 + 1 copy + 2 per level>=1), layout+view_geo, project,
         # scan, scatter, sort, raster fwd, raster bwd, project bwd, env bwd (1 + 1 add + 1 per level>=1)
         L = r.ed.n_levels
-        per_step = (2 + 2 * (L - 1)) + 2 + 1 + 3 + 1 + 1 + 1 + (2 + (L - 1))
+        per_step = (2 + 2 * (L - 1)) + 2 + 1 + 3 + 1 + 1 + 2 + (2 + (L - 1))
         line["gpu_launches"] = per_step * args.steps
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -460,6 +460,44 @@ def composite(rec: dict, fr: Fragments, W: int, prm: Params):
     return rgba, out[:, 3:]
 
 
+def lookup_margins(S: dict, cam: dict, env_shape, prm: Params) -> np.ndarray:
+    """Per surfel: the smallest distance (in texels) of any bilinear or level
+    coordinate used by the shading (irradiance at n, the two specular levels
+    at r, the BRDF table at (n.v, r), the level coordinate r (L-1)) to a
+    cell boundary.  The interpolation cell is a discrete choice; where this
+    margin is within rounding, implementations in different precisions may
+    pick neighbouring cells and differ in the derivative w.r.t. the lookup
+    direction (the value itself is continuous)."""
+    with torch.no_grad():
+        R = quat_to_rot(S["quat"])
+        n = R[:, :, 2]
+        o = -(cam["R"].T @ cam["t"])
+        w_o = o[None, :] - S["pos"]
+        w_o = w_o / torch.linalg.norm(w_o, dim=-1, keepdim=True)
+        facing = (n * w_o).sum(-1, keepdim=True)
+        n_s = torch.where(facing < 0, -n, n)
+        mu = torch.clamp((n_s * w_o).sum(-1), 0.0, 1.0)
+        refl = 2.0 * (w_o * n_s).sum(-1, keepdim=True) * n_s - w_o
+        r = torch.clamp(S["roughness"], 0.0, 1.0)
+        He, We = env_shape[0], env_shape[1]
+        L = prm.env_levels
+        sizes = level_sizes(We, He, L)
+        frac = lambda X: torch.abs(X - torch.round(X))
+        m = torch.full((n.shape[0],), float("inf"), dtype=F64)
+        u, v = dir_to_uv(n_s)
+        m = torch.minimum(m, torch.minimum(frac(u * prm.irr_w - 0.5), frac(v * prm.irr_h - 0.5)))
+        u, v = dir_to_uv(refl)
+        lc = r * (L - 1)
+        i0 = torch.clamp(torch.floor(lc).long(), 0, L - 1)
+        for lv in (i0, torch.clamp(i0 + 1, max=L - 1)):
+            Ws = torch.tensor([sizes[k][0] for k in range(L)], dtype=F64)[lv]
+            Hs = torch.tensor([sizes[k][1] for k in range(L)], dtype=F64)[lv]
+            m = torch.minimum(m, torch.minimum(frac(u * Ws - 0.5), frac(v * Hs - 0.5)))
+        m = torch.minimum(m, torch.minimum(frac(mu * prm.lut_n - 0.5), frac(r * prm.lut_n - 0.5)))
+        m = torch.minimum(m, frac(lc))
+    return m.numpy()
+
+
 # ---------------------------------------------------------------------------
 # convenience: a whole view
 
@@ -534,7 +572,7 @@ def render_view(surf, cam, env: EnvState, prm: Params = Params(), pix=None, G=No
         mg_parts.append(fr.margin)
     out = dict(rgba=np.concatenate(rgba_parts), aov=np.concatenate(aov_parts),
                n_layers=np.concatenate(nl_parts), margin=np.concatenate(mg_parts), rect=rect,
-               valid=rec["valid"].numpy())
+               valid=rec["valid"].numpy(), lookup_margin=lookup_margins(S, cd, env.shape, prm))
     if need_grad:
         tens = [rec[k] for k in ("T", "Sinv", "n_f", "ch")]
         grads = [leaf[k].grad if leaf[k].grad is not None else torch.zeros_like(leaf[k]) for k in

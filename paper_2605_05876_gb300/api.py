@@ -193,15 +193,6 @@ class Renderer:
         return self.grads
 
 
-def profile_begin():
-    check(lib().ss_profile_begin(), "ss_profile_begin")
-
-
-def profile_end() -> dict:
-    t = C.ss_stage_times()
-    check(lib().ss_profile_end(ctypes.byref(t)), "ss_profile_end")
-    return {name: (float(t.ms[i]), int(t.launches[i])) for i, name in enumerate(C.STAGES)}
-
     def read_status(self) -> int:
         return int(lib().ss_read_status(_ptr(self.ws), _stream()))
 
@@ -227,3 +218,13 @@ def profile_end() -> dict:
     def view_aov(self, v: int):
         w, h = self.sizes[v]
         return self.aov[:, self.view_slice(v)].reshape(C.SS_N_AOV, h, w)
+
+
+def profile_begin():
+    check(lib().ss_profile_begin(), "ss_profile_begin")
+
+
+def profile_end() -> dict:
+    t = C.ss_stage_times()
+    check(lib().ss_profile_end(ctypes.byref(t)), "ss_profile_end")
+    return {name: (float(t.ms[i]), int(t.launches[i])) for i, name in enumerate(C.STAGES)}

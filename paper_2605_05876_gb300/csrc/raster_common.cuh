@@ -1,0 +1,107 @@
+// Per-warp streaming of a tile's sorted instance list, shared by the forward
+// and backward rasterisers.
+//
+// Each warp owns an 8 x 4 pixel block of a 16 x 16 tile and walks the tile's
+// list on its own (no block-wide barrier): 32 keys at a time, it reads the
+// support rectangles, keeps the instances whose rectangle meets its block
+// (ballot + prefix count, so the order by z_start is kept) and copies only
+// those records into its own shared-memory slots with cp.async.  The next
+// chunk's keys and rectangles are loaded before the current chunk is
+// processed.
+#pragma once
+
+#include "ss3d_internal.cuh"
+
+#define WSLOTS 32
+
+struct ss_wstage {
+    float4 r0[WSLOTS];  // P (screen quadratic-form factor)
+    float4 r1[WSLOTS];  // A2, B2, 1, n_f
+    float4 r2[WSLOTS];  // centre relative to the tile origin (x, y), then copy of px_lo, py_lo
+    float4 r3[WSLOTS];  // z_start, z_end, rect_x, rect_y
+    float4 r4[WSLOTS];  // rgb, flags
+    float4 r5[WSLOTS];  // albedo, roughness
+    float4 r6[WSLOTS];  // metallic, normal
+    uint32_t id[WSLOTS];
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n" ::);
+    asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+// One chunk of up to 32 instances: fetched (key, rectangle) of this lane.
+struct ss_chunk {
+    uint32_t id;
+    float4 r3;
+    bool live;
+};
+
+__device__ __forceinline__ ss_chunk fetch_chunk(const unsigned long long* keys, const ss_rec* recs, int64_t j,
+                                                int64_t end) {
+    ss_chunk c;
+    c.live = j < end;
+    c.id = 0;
+    c.r3 = make_float4(0.f, 0.f, __uint_as_float(0xffffu), __uint_as_float(0xffffu));
+    if (c.live) {
+        c.id = (uint32_t)(__ldg(keys + j) & 0xffffffffull);
+        c.r3 = __ldg(&recs[c.id].r3);
+    }
+    return c;
+}
+
+// Stage the instances of chunk c whose rectangle meets the warp's pixel block
+// [gx0, gx1] x [gy0, gy1]; returns how many were staged (slots 0 .. n-1, in
+// list order).  Centres are rewritten relative to the tile origin (tx0, ty0)
+// from their double-float value.
+__device__ __forceinline__ int stage_chunk(ss_wstage& W, const ss_chunk& c, const ss_rec* recs, int lane, int gx0,
+                                           int gx1, int gy0, int gy1, float tx0, float ty0) {
+    bool ov = false;
+    if (c.live) {
+        uint32_t rx = __float_as_uint(c.r3.z), ry = __float_as_uint(c.r3.w);
+        int i0 = rx & 0xffff, i1 = rx >> 16, j0 = ry & 0xffff, j1 = ry >> 16;
+        ov = i0 <= gx1 && i1 >= gx0 && j0 <= gy1 && j1 >= gy0;
+    }
+    const uint32_t mask = __ballot_sync(0xffffffffu, ov);
+    if (ov) {
+        const int pos = __popc(mask & ((1u << lane) - 1u));
+        const ss_rec* rc = recs + c.id;
+        cp_async16(&W.r0[pos], &rc->r0);
+        cp_async16(&W.r1[pos], &rc->r1);
+        cp_async16(&W.r2[pos], &rc->r2);
+        cp_async16(&W.r4[pos], &rc->r4);
+        cp_async16(&W.r5[pos], &rc->r5);
+        cp_async16(&W.r6[pos], &rc->r6);
+        W.r3[pos] = c.r3;
+        W.id[pos] = c.id;
+    }
+    cp_async_wait_all();
+    if (ov) {
+        const int pos = __popc(mask & ((1u << lane) - 1u));
+        float4 p = W.r2[pos];
+        p.x = __fadd_rn(__fsub_rn(p.x, tx0), p.z);
+        p.y = __fadd_rn(__fsub_rn(p.y, ty0), p.w);
+        W.r2[pos] = p;
+    }
+    __syncwarp();
+    return __popc(mask);
+}
+
+__device__ __forceinline__ bool in_rect(uint32_t rx, uint32_t ry, int px, int py) {
+    int i0 = rx & 0xffff, i1 = rx >> 16, j0 = ry & 0xffff, j1 = ry >> 16;
+    return px >= i0 && px <= i1 && py >= j0 && py <= j1;
+}
+
+__device__ __forceinline__ int find_view_tile(const ss_layout* L, int tile) {
+    int lo = 0, hi = L->n_views - 1;
+    while (lo < hi) {
+        int m = (lo + hi + 1) >> 1;
+        if (L->v[m].tile_off <= tile) lo = m;
+        else hi = m - 1;
+    }
+    return lo;
+}

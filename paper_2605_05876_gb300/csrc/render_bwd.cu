@@ -12,6 +12,7 @@
 #include <math.h>
 
 #include "ss3d_internal.cuh"
+#include "raster_common.cuh"
 
 // gradient record layout (floats) of one (view, surfel)
 #define G_P 0      // dL/dP00, P01, P10, P11
@@ -23,38 +24,34 @@
 #define G_CH 9     // 12 channels: rgb, albedo 3, roughness, metallic, normal 3, depth
 #define G_N 21
 
-#define RB 256
-
-struct ss_bstage {
-    float4 r0[RB];   // P
-    float4 r1[RB];   // A2, B2, 1, n_f
-    float4 pz[RB];   // centre relative to the tile origin, z_start, z_end
-    uint4 meta[RB];  // rect_x, rect_y, flags, record index
-    float4 c0[RB];   // rgb, albedo r
-    float4 c1[RB];   // albedo g, b, roughness, metallic
-    float4 c2[RB];   // normal xyz, depth
-};
-
-__device__ __forceinline__ int find_view_b(const ss_layout* L, int tile) {
-    int lo = 0, hi = L->n_views - 1;
-    while (lo < hi) {
-        int m = (lo + hi + 1) >> 1;
-        if (L->v[m].tile_off <= tile) lo = m;
-        else hi = m - 1;
+// Butterfly reduce-scatter over the warp: on entry every lane holds 32
+// values, on exit lane q holds the warp total of value q (31 shuffles instead
+// of 5 per value).
+__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const bool hi = (lane & o) != 0;
+#pragma unroll
+        for (int j = 0; j < o; ++j) {
+            const float send = hi ? v[j] : v[j + o];
+            const float keep = hi ? v[j + o] : v[j];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
     }
-    return lo;
+    return v[0];
 }
 
-__global__ void __launch_bounds__(256) raster_bwd_kernel(ss_ws_view ws, ss_bwd_args a) {
-    __shared__ ss_bstage S;
+__global__ void __launch_bounds__(256, 2) raster_bwd_kernel(ss_ws_view ws, ss_bwd_args a) {
+    __shared__ ss_wstage Wst[8];
     const ss_layout* L = ws.layout;
     const int tile = blockIdx.x;
-    const int view = find_view_b(L, tile);
+    const int view = find_view_tile(L, tile);
     const ss_view_layout& vl = L->v[view];
     const int lt = tile - vl.tile_off;
     const int tx = lt % vl.tiles_x, ty = lt / vl.tiles_x;
     const int x0 = tx * SS_TILE, y0 = ty * SS_TILE;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    ss_wstage& W = Wst[warp];
     const int wx0 = 8 * (warp & 1), wy0 = 4 * (warp >> 1);
     const int lx = wx0 + (lane & 7), ly = wy0 + (lane >> 3);
     const int px = x0 + lx, py = y0 + ly;
@@ -69,22 +66,22 @@ __global__ void __launch_bounds__(256) raster_bwd_kernel(ss_ws_view ws, ss_bwd_a
     // per-pixel state from the forward pass
     int K = 0;
     float Tend = 1.f, gA = 0.f;
-    float g[SS_NCH], outc[SS_NCH];
+    float g[SS_NCH], rem[SS_NCH];   // rem_c = out_c - sum_{j<=k} T_j alpha_j C_hat_j (colour behind layer k)
     if (inside) {
         K = __float_as_int(ws.pix_state[gpix]);
         Tend = ws.pix_state[P + gpix];
         float4 d = reinterpret_cast<const float4*>(a.d_rgba)[gpix];
         float4 o = reinterpret_cast<const float4*>(a.out_rgba)[gpix];
         g[0] = d.x; g[1] = d.y; g[2] = d.z; gA = d.w;
-        outc[0] = o.x; outc[1] = o.y; outc[2] = o.z;   // includes T_end * bg: R_k below needs it
+        rem[0] = o.x; rem[1] = o.y; rem[2] = o.z;   // includes T_end * bg: R_k below needs it
 #pragma unroll
         for (int c = 0; c < SS_N_AOV; ++c) {
             g[3 + c] = a.d_aov ? a.d_aov[c * P + gpix] : 0.f;
-            outc[3 + c] = a.out_aov ? a.out_aov[c * P + gpix] : 0.f;
+            rem[3 + c] = a.out_aov ? a.out_aov[c * P + gpix] : 0.f;
         }
     } else {
 #pragma unroll
-        for (int c = 0; c < SS_NCH; ++c) g[c] = outc[c] = 0.f;
+        for (int c = 0; c < SS_NCH; ++c) g[c] = rem[c] = 0.f;
     }
     bool done = !inside || K == 0;
     unsigned n_frag = 0;
@@ -93,9 +90,6 @@ __global__ void __launch_bounds__(256) raster_bwd_kernel(ss_ws_view ws, ss_bwd_a
     int k = -1;
     float Wr = 0.f, zmax = 0.f;
     float Tb = 1.f;
-    float acc[SS_NCH];
-#pragma unroll
-    for (int c = 0; c < SS_NCH; ++c) acc[c] = 0.f;
     float G[SS_NCH];      // dL/dC_c for Shepard channels; for the normal channels H = dL/dC_n
     float Sk = 0.f;       // sum_c G_c Chat_c - dL/dW (alpha path)
 
@@ -118,9 +112,9 @@ __global__ void __launch_bounds__(256) raster_bwd_kernel(ss_ws_view ws, ss_bwd_a
         float gChat = 0.f, gR = 0.f;
 #pragma unroll
         for (int c = 0; c < SS_NCH; ++c) {
-            acc[c] = fmaf(tw, hat[c], acc[c]);
+            rem[c] = fmaf(-tw, hat[c], rem[c]);
             gChat = fmaf(g[c], hat[c], gChat);
-            gR = fmaf(g[c], outc[c] - acc[c], gR);
+            gR = fmaf(g[c], rem[c], gR);
         }
         // Eq. alpha / Eq. compositing: dL/dW_k through alpha_k and all later T_j
         const float dW_alpha = kw * (Tb * e * gChat - gR + gA * Tend);
@@ -147,112 +141,72 @@ __global__ void __launch_bounds__(256) raster_bwd_kernel(ss_ws_view ws, ss_bwd_a
     if (beg > end) beg = end;
     const ss_rec* recs = ws.rec + vl.rec_off;
     float* grad = ws.grad_rec + vl.rec_off * SS_NGRAD;
-    for (int64_t base = beg; base < end; base += RB) {
-        const int nb = (int)min((int64_t)RB, end - base);
-        __syncthreads();
-        if ((int)threadIdx.x < nb) {
-            uint32_t id = (uint32_t)(ws.keys[base + threadIdx.x] & 0xffffffffull);
-            const ss_rec rc = recs[id];
-            S.r0[threadIdx.x] = rc.r0;
-            S.r1[threadIdx.x] = rc.r1;
-            float prx = __fadd_rn(__fsub_rn(rc.r2.x, (float)x0), rc.r2.z);
-            float pry = __fadd_rn(__fsub_rn(rc.r2.y, (float)y0), rc.r2.w);
-            S.pz[threadIdx.x] = make_float4(prx, pry, rc.r3.x, rc.r3.y);
-            S.meta[threadIdx.x] = make_uint4(__float_as_uint(rc.r3.z), __float_as_uint(rc.r3.w), __float_as_uint(rc.r4.w), id);
-            S.c0[threadIdx.x] = make_float4(rc.r4.x, rc.r4.y, rc.r4.z, rc.r5.x);
-            S.c1[threadIdx.x] = make_float4(rc.r5.y, rc.r5.z, rc.r5.w, rc.r6.x);
-            S.c2[threadIdx.x] = make_float4(rc.r6.y, rc.r6.z, rc.r6.w, 0.5f * (rc.r3.x + rc.r3.y));
-        }
-        __syncthreads();
-        if (__all_sync(0xffffffffu, done)) continue;
-        for (int c0 = 0; c0 < nb; c0 += 32) {
-            const int j = c0 + lane;
-            bool ov = false;
-            if (j < nb) {
-                uint4 m = S.meta[j];
-                int i0 = m.x & 0xffff, i1 = m.x >> 16, j0 = m.y & 0xffff, j1 = m.y >> 16;
-                ov = i0 <= gx1 && i1 >= gx0 && j0 <= gy1 && j1 >= gy0;
-            }
-            uint32_t mask = __ballot_sync(0xffffffffu, ov);
-            while (mask) {
-                const int b = __ffs(mask) - 1;
-                mask &= mask - 1;
-                const int s = c0 + b;
-                const float4 r0 = S.r0[s], r1 = S.r1[s], pz = S.pz[s];
-                const float dx = xl - pz.x, dy = yl - pz.y;
-                ss_hit h = ss_pixel_test(r0, r1, dx, dy, rc2);
-                bool cov = h.cover && !done;
-                const uint4 m = S.meta[s];
-                if (m.z & SS_FLAG_RECT_TEST) {
-                    int i0 = m.x & 0xffff, i1 = m.x >> 16, j0 = m.y & 0xffff, j1 = m.y >> 16;
-                    cov = cov && px >= i0 && px <= i1 && py >= j0 && py <= j1;
+    ss_chunk nxt = fetch_chunk(ws.keys, recs, beg + lane, end);
+    for (int64_t base = beg; base < end; base += 32) {
+        if (__all_sync(0xffffffffu, done)) break;
+        const ss_chunk cur = nxt;
+        const int n = stage_chunk(W, cur, recs, lane, gx0, gx1, gy0, gy1, (float)x0, (float)y0);
+        nxt = fetch_chunk(ws.keys, recs, base + 32 + lane, end);
+        for (int s = 0; s < n; ++s) {
+            const float4 r0 = W.r0[s], r1 = W.r1[s], r2 = W.r2[s], r3 = W.r3[s];
+            const float dx = xl - r2.x, dy = yl - r2.y;
+            ss_hit h = ss_pixel_test(r0, r1, dx, dy, rc2);
+            bool cov = h.cover && !done;
+            const uint32_t fl = __float_as_uint(W.r4[s].w);
+            if (fl & SS_FLAG_RECT_TEST) cov = cov && in_rect(__float_as_uint(r3.z), __float_as_uint(r3.w), px, py);
+            float gr[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) gr[q] = 0.f;
+            bool contrib = false;
+            if (cov) {
+                const float rho2 = __fdividef(h.q, h.t);
+                const float ex = __expf(-0.5f * rho2);
+                const float w = r1.w * ex;
+                // replay of Algorithm 1: the forward kernel's condition, bit for bit
+                if (k < 0) {
+                    k = 0;
+                    enter_layer(0);
+                } else if (Wr > 0.f && r3.x > zmax) {
+                    ++k;
+                    Wr = 0.f;
+                    zmax = 0.f;
+                    if (k >= K) done = true;
+                    else enter_layer(k);
                 }
-                float gr[G_N];
+                if (!done) {
+                    zmax = fmaxf(zmax, r3.y);
+                    Wr += w;
+                    const float4 c0v = W.r4[s], c1v = W.r5[s], c2v = W.r6[s];
+                    const float ch[SS_NCH] = {c0v.x, c0v.y, c0v.z, c1v.x, c1v.y, c1v.z,
+                                              c1v.w, c2v.x, c2v.y, c2v.z, c2v.w, 0.5f * (r3.x + r3.y)};
+                    float dLdw = -Sk;
 #pragma unroll
-                for (int q = 0; q < G_N; ++q) gr[q] = 0.f;
-                bool contrib = false;
-                if (cov) {
-                    const float rho2 = __fdividef(h.q, h.t);
-                    const float ex = __expf(-0.5f * rho2);
-                    const float w = r1.w * ex;
-                    // replay of Algorithm 1: same condition as the forward kernel
-                    if (k < 0) {
-                        k = 0;
-                        enter_layer(0);
-                    } else if (Wr > 0.f && pz.z > zmax) {
-                        ++k;
-                        Wr = 0.f;
-                        zmax = 0.f;
-                        if (k >= K) done = true;
-                        else enter_layer(k);
+                    for (int c = 0; c < SS_NCH; ++c) {
+                        dLdw = fmaf(G[c], ch[c], dLdw);
+                        gr[G_CH + c] = G[c] * w;
                     }
-                    if (!done) {
-                        zmax = fmaxf(zmax, pz.w);
-                        Wr += w;
-                        const float4 c0v = S.c0[s], c1v = S.c1[s], c2v = S.c2[s];
-                        const float ch[SS_NCH] = {c0v.x, c0v.y, c0v.z, c0v.w, c1v.x, c1v.y,
-                                                  c1v.z, c1v.w, c2v.x, c2v.y, c2v.z, c2v.w};
-                        float dLdw = -Sk;
-#pragma unroll
-                        for (int c = 0; c < SS_NCH; ++c) {
-                            dLdw = fmaf(G[c], ch[c], dLdw);
-                            gr[G_CH + c] = G[c] * w;
-                        }
-                        // w = n_f exp(-rho2 / 2), rho2 = q / s2^2 (Eq. mip_weight)
-                        gr[G_NF] = dLdw * ex;
-                        const float grho = -0.5f * w * dLdw;
-                        const float it = 1.f / h.t;
-                        const float gs0 = 2.f * grho * h.s0 * it, gs1 = 2.f * grho * h.s1 * it;
-                        const float gs2 = -2.f * grho * rho2 / h.s2;
-                        gr[G_P + 0] = gs0 * dx; gr[G_P + 1] = gs0 * dy;
-                        gr[G_P + 2] = gs1 * dx; gr[G_P + 3] = gs1 * dy;
-                        gr[G_A2] = gs2 * dx; gr[G_B2] = gs2 * dy;
-                        gr[G_PX] = -(gs0 * r0.x + gs1 * r0.z + gs2 * r1.x);
-                        gr[G_PY] = -(gs0 * r0.y + gs1 * r0.w + gs2 * r1.y);
-                        contrib = true;
-                        ++n_frag;
-                    }
-                }
-                // warp reduction, then one add per value
-                if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-                    for (int q = 0; q < G_N; ++q) {
-                        float v = gr[q];
-                        v += __shfl_xor_sync(0xffffffffu, v, 16);
-                        v += __shfl_xor_sync(0xffffffffu, v, 8);
-                        v += __shfl_xor_sync(0xffffffffu, v, 4);
-                        v += __shfl_xor_sync(0xffffffffu, v, 2);
-                        v += __shfl_xor_sync(0xffffffffu, v, 1);
-                        gr[q] = v;
-                    }
-                    float mine = 0.f;
-#pragma unroll
-                    for (int q = 0; q < G_N; ++q)
-                        if (lane == q) mine = gr[q];
-                    if (lane < G_N) atomicAdd(grad + (int64_t)m.w * SS_NGRAD + lane, mine);
+                    // w = n_f exp(-rho2 / 2), rho2 = q / s2^2 (Eq. mip_weight)
+                    gr[G_NF] = dLdw * ex;
+                    const float grho = -0.5f * w * dLdw;
+                    const float it = 1.f / h.t;
+                    const float gs0 = 2.f * grho * h.s0 * it, gs1 = 2.f * grho * h.s1 * it;
+                    const float gs2 = -2.f * grho * rho2 / h.s2;
+                    gr[G_P + 0] = gs0 * dx; gr[G_P + 1] = gs0 * dy;
+                    gr[G_P + 2] = gs1 * dx; gr[G_P + 3] = gs1 * dy;
+                    gr[G_A2] = gs2 * dx; gr[G_B2] = gs2 * dy;
+                    gr[G_PX] = -(gs0 * r0.x + gs1 * r0.z + gs2 * r1.x);
+                    gr[G_PY] = -(gs0 * r0.y + gs1 * r0.w + gs2 * r1.y);
+                    contrib = true;
+                    ++n_frag;
                 }
             }
+            // warp reduction, then one add per value
+            if (__any_sync(0xffffffffu, contrib)) {
+                const float tot = warp_reduce_scatter32(gr, lane);
+                if (lane < G_N && tot != 0.f) atomicAdd(grad + (int64_t)W.id[s] * SS_NGRAD + lane, tot);
+            }
         }
+        __syncwarp();
     }
     if (a.f.p.collect_stats) {
         unsigned long long x = n_frag;
@@ -321,13 +275,40 @@ __device__ __forceinline__ void uv_grad(const float d[3], float gu, float gv, fl
     out[2] += kv * (-d[1] * d[2]);
 }
 
-__global__ void __launch_bounds__(128) project_bwd_kernel(ss_ws_view ws, ss_bwd_args A, int64_t n_total) {
+// One thread per (view, surfel) record: the record's raster gradient is
+// chained back to the surfel parameters, and the 14 parameter gradients of
+// this view overwrite the first 14 floats of the record (a per-surfel kernel
+// then sums them over the views, in a fixed order).
+#define PG_N 14   // pos 3, quat 4, log_scale 2, albedo 3, roughness, metallic
+
+__global__ void __launch_bounds__(128) project_bwd_kernel(ss_ws_view ws, ss_bwd_args A, int64_t n_records) {
     const ss_layout* L = ws.layout;
     const ss_fwd_args& a = A.f;
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n_total) return;
-    int scene = 0;
-    while (scene + 1 < L->n_scenes && i >= L->scene_begin[scene + 1]) ++scene;
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n_records) return;
+    int v = 0;
+    {
+        int lo = 0, hi = L->n_views - 1;
+        while (lo < hi) {
+            int m = (lo + hi + 1) >> 1;
+            if (L->v[m].rec_off <= r) lo = m;
+            else hi = m - 1;
+        }
+        v = lo;
+    }
+    const ss_view_layout& vl = L->v[v];
+    const int scene = vl.scene;
+    const int64_t i = vl.surfel_begin + (r - vl.rec_off);
+    const uint32_t flags = __float_as_uint(ws.rec[r].r4.w);
+    if (!(flags & SS_FLAG_VALID)) return;
+    float* gr = ws.grad_rec + r * SS_NGRAD;
+    float G[G_N];
+    bool any = false;
+    for (int k = 0; k < G_N; ++k) {
+        G[k] = gr[k];
+        any = any || (G[k] != 0.f);
+    }
+    if (!any) return;
     const float c[3] = {a.s.pos[i * 3], a.s.pos[i * 3 + 1], a.s.pos[i * 3 + 2]};
     const float4 q4 = *reinterpret_cast<const float4*>(a.s.quat + i * 4);
     const float2 ls = *reinterpret_cast<const float2*>(a.s.log_scale + i * 2);
@@ -351,23 +332,10 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ss_ws_view ws, ss_bwd_
     const int lutn = a.p.lut_n;
     const float* LUT = a.env.lut;
 
-    // accumulated parameter gradients
+    // parameter gradients of this view
     float gc[3] = {0, 0, 0}, gRq[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, gsu = 0.f, gsv = 0.f;
     float grho[3] = {0, 0, 0}, grough = 0.f, gmetal = 0.f;
-
-    for (int v = L->scene_view_begin[scene]; v < L->scene_view_begin[scene + 1]; ++v) {
-        const ss_view_layout& vl = L->v[v];
-        const int64_t r = vl.rec_off + (i - vl.surfel_begin);
-        const uint32_t flags = __float_as_uint(ws.rec[r].r4.w);
-        if (!(flags & SS_FLAG_VALID)) continue;
-        const float* gr = ws.grad_rec + r * SS_NGRAD;
-        float G[G_N];
-        bool any = false;
-        for (int k = 0; k < G_N; ++k) {
-            G[k] = gr[k];
-            any = any || (G[k] != 0.f);
-        }
-        if (!any) continue;
+    {
         const ss_camera& cam = a.cams[v];
         const float* Rc = cam.R;
         const float fx = cam.fx, fy = cam.fy;
@@ -580,27 +548,46 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ss_ws_view ws, ss_bwd_
     const float gy = 2.f * (-2.f * y * d[0] + x * d[1] + w * d[2] + x * d[3] + z * d[5] - w * d[6] + z * d[7] - 2.f * y * d[8]);
     const float gz = 2.f * (-2.f * z * d[0] - w * d[1] + x * d[2] + w * d[3] - 2.f * z * d[4] + y * d[5] + x * d[6] + y * d[7]);
     const float dotq = gw * w + gx * x + gy * y + gz * z;
-    const ss_surfel_grads& g = A.g;
-    if (g.quat) {
-        g.quat[i * 4 + 0] += (gw - w * dotq) * qn;
-        g.quat[i * 4 + 1] += (gx - x * dotq) * qn;
-        g.quat[i * 4 + 2] += (gy - y * dotq) * qn;
-        g.quat[i * 4 + 3] += (gz - z * dotq) * qn;
-    }
-    if (g.log_scale) {
-        g.log_scale[i * 2 + 0] += gsu * su;
-        g.log_scale[i * 2 + 1] += gsv * sv;
+    float out[PG_N] = {gc[0], gc[1], gc[2], (gw - w * dotq) * qn, (gx - x * dotq) * qn, (gy - y * dotq) * qn,
+                       (gz - z * dotq) * qn, gsu * su, gsv * sv, grho[0], grho[1], grho[2], grough, gmetal};
+    for (int k = 0; k < PG_N; ++k) gr[k] = out[k];
+}
+
+// Sum the per-view parameter gradients of each surfel (views in order) and
+// add them to the caller's gradients.
+__global__ void __launch_bounds__(256) param_reduce_kernel(ss_ws_view ws, ss_surfel_grads g, int64_t n_total) {
+    const ss_layout* L = ws.layout;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_total) return;
+    int scene = 0;
+    while (scene + 1 < L->n_scenes && i >= L->scene_begin[scene + 1]) ++scene;
+    float acc[PG_N];
+    for (int k = 0; k < PG_N; ++k) acc[k] = 0.f;
+    for (int v = L->scene_view_begin[scene]; v < L->scene_view_begin[scene + 1]; ++v) {
+        const ss_view_layout& vl = L->v[v];
+        const float* gr = ws.grad_rec + (vl.rec_off + (i - vl.surfel_begin)) * SS_NGRAD;
+        const float4 a0 = *reinterpret_cast<const float4*>(gr), a1 = *reinterpret_cast<const float4*>(gr + 4),
+                     a2 = *reinterpret_cast<const float4*>(gr + 8), a3 = *reinterpret_cast<const float4*>(gr + 12);
+        acc[0] += a0.x; acc[1] += a0.y; acc[2] += a0.z; acc[3] += a0.w;
+        acc[4] += a1.x; acc[5] += a1.y; acc[6] += a1.z; acc[7] += a1.w;
+        acc[8] += a2.x; acc[9] += a2.y; acc[10] += a2.z; acc[11] += a2.w;
+        acc[12] += a3.x; acc[13] += a3.y;
     }
     if (g.pos)
-        for (int k = 0; k < 3; ++k) g.pos[i * 3 + k] += gc[k];
+        for (int k = 0; k < 3; ++k) g.pos[i * 3 + k] += acc[k];
+    if (g.quat)
+        for (int k = 0; k < 4; ++k) g.quat[i * 4 + k] += acc[3 + k];
+    if (g.log_scale)
+        for (int k = 0; k < 2; ++k) g.log_scale[i * 2 + k] += acc[7 + k];
     if (g.albedo)
-        for (int k = 0; k < 3; ++k) g.albedo[i * 3 + k] += grho[k];
-    if (g.roughness) g.roughness[i] += grough;
-    if (g.metallic) g.metallic[i] += gmetal;
+        for (int k = 0; k < 3; ++k) g.albedo[i * 3 + k] += acc[9 + k];
+    if (g.roughness) g.roughness[i] += acc[12];
+    if (g.metallic) g.metallic[i] += acc[13];
 }
 
 void ss_launch_project_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st) {
     int64_t n = L.scene_begin[L.n_scenes];
-    if (n <= 0) return;
-    project_bwd_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(ws, a, n);
+    if (n <= 0 || L.total_records <= 0) return;
+    project_bwd_kernel<<<(unsigned)((L.total_records + 127) / 128), 128, 0, st>>>(ws, a, L.total_records);
+    param_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ws, a.g, n);
 }

@@ -3,6 +3,7 @@
 #include <math.h>
 
 #include "ss3d_internal.cuh"
+#include "raster_common.cuh"
 
 // ------------------------------------------------------------------------
 // projection (Sec. 3.1), centre-precomputed MIP filter (Sec. 3.3.2) and
@@ -415,52 +416,23 @@ void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_a
 
 // ------------------------------------------------------------------------
 // per-pixel rasteriser (Algorithm 1, Eq. alpha, Eq. compositing)
+//
+// One CTA per tile, one warp per 8 x 4 pixel block; every warp streams the
+// tile's z_start-sorted list on its own (raster_common.cuh), so a warp with
+// little work never waits for a busy one, and a warp whose 32 pixels have all
+// reached K_max layers stops reading the list.
 
-#define RB 256  // instances staged per batch (one per thread)
-
-struct ss_stage {
-    float4 r0[RB];   // primed J rows
-    float4 r1[RB];   // A2, B2, 1, n_f
-    float4 pz[RB];   // centre relative to the tile origin (x, y), z_start, z_end
-    uint4 meta[RB];  // rect_x, rect_y, flags, -
-    float4 c0[RB];   // rgb, albedo r
-    float4 c1[RB];   // albedo g, b, roughness, metallic
-    float4 c2[RB];   // normal xyz, depth
-};
-
-__device__ __forceinline__ int find_view(const ss_layout* L, int tile) {
-    int lo = 0, hi = L->n_views - 1;
-    while (lo < hi) {
-        int m = (lo + hi + 1) >> 1;
-        if (L->v[m].tile_off <= tile) lo = m;
-        else hi = m - 1;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ void stage_instance(ss_stage& S, int slot, const ss_rec& rc, float tx0, float ty0) {
-    S.r0[slot] = rc.r0;
-    S.r1[slot] = rc.r1;
-    // centre relative to the tile origin, from the double-float centre
-    float prx = __fadd_rn(__fsub_rn(rc.r2.x, tx0), rc.r2.z);
-    float pry = __fadd_rn(__fsub_rn(rc.r2.y, ty0), rc.r2.w);
-    S.pz[slot] = make_float4(prx, pry, rc.r3.x, rc.r3.y);
-    S.meta[slot] = make_uint4(__float_as_uint(rc.r3.z), __float_as_uint(rc.r3.w), __float_as_uint(rc.r4.w), 0u);
-    S.c0[slot] = make_float4(rc.r4.x, rc.r4.y, rc.r4.z, rc.r5.x);
-    S.c1[slot] = make_float4(rc.r5.y, rc.r5.z, rc.r5.w, rc.r6.x);
-    S.c2[slot] = make_float4(rc.r6.y, rc.r6.z, rc.r6.w, 0.5f * (rc.r3.x + rc.r3.y));
-}
-
-__global__ void __launch_bounds__(256) raster_fwd_kernel(ss_ws_view ws, ss_fwd_args a) {
-    __shared__ ss_stage S;
+__global__ void __launch_bounds__(256, 3) raster_fwd_kernel(ss_ws_view ws, ss_fwd_args a) {
+    __shared__ ss_wstage Wst[8];
     const ss_layout* L = ws.layout;
     const int tile = blockIdx.x;
-    const int view = find_view(L, tile);
+    const int view = find_view_tile(L, tile);
     const ss_view_layout& vl = L->v[view];
     const int lt = tile - vl.tile_off;
     const int tx = lt % vl.tiles_x, ty = lt / vl.tiles_x;
     const int x0 = tx * SS_TILE, y0 = ty * SS_TILE;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    ss_wstage& W = Wst[warp];
     const int wx0 = 8 * (warp & 1), wy0 = 4 * (warp >> 1);         // 8 x 4 pixel block per warp
     const int lx = wx0 + (lane & 7), ly = wy0 + (lane >> 3);
     const int px = x0 + lx, py = y0 + ly;
@@ -472,6 +444,8 @@ __global__ void __launch_bounds__(256) raster_fwd_kernel(ss_ws_view ws, ss_fwd_a
     const int kmax = a.p.k_max;
     const int64_t gpix = vl.pixel_off + (int64_t)py * vl.width + px;
     const int64_t P = L->total_pixels;
+    const bool stats = a.p.collect_stats != 0;
+    unsigned n_lane = 0, n_rect = 0, n_frag = 0;
 
     float C[SS_NCH];
 #pragma unroll
@@ -482,8 +456,6 @@ __global__ void __launch_bounds__(256) raster_fwd_kernel(ss_ws_view ws, ss_fwd_a
     float Wg = 0.f, zmax = 0.f, Tb = 1.f, Acov = 0.f;
     int K = 0;
     bool done = !inside;
-    const bool stats = a.p.collect_stats != 0;
-    unsigned n_lane = 0, n_rect = 0, n_frag = 0;
 
     auto flush = [&]() {
         const float invW = 1.f / Wg;
@@ -518,57 +490,40 @@ __global__ void __launch_bounds__(256) raster_fwd_kernel(ss_ws_view ws, ss_fwd_a
     if (end > cap) end = cap;
     if (beg > end) beg = end;
     const ss_rec* recs = ws.rec + vl.rec_off;
-    for (int64_t base = beg; base < end; base += RB) {
-        const int nb = (int)min((int64_t)RB, end - base);
-        __syncthreads();
-        if ((int)threadIdx.x < nb) {
-            uint32_t id = (uint32_t)(ws.keys[base + threadIdx.x] & 0xffffffffull);
-            stage_instance(S, threadIdx.x, recs[id], (float)x0, (float)y0);
-        }
-        __syncthreads();
-        if (__all_sync(0xffffffffu, done)) continue;
-        for (int c0 = 0; c0 < nb; c0 += 32) {
-            const int j = c0 + lane;
-            bool ov = false;
-            if (j < nb) {
-                uint4 m = S.meta[j];
-                int i0 = m.x & 0xffff, i1 = m.x >> 16, j0 = m.y & 0xffff, j1 = m.y >> 16;
-                ov = i0 <= gx1 && i1 >= gx0 && j0 <= gy1 && j1 >= gy0;
+    ss_chunk nxt = fetch_chunk(ws.keys, recs, beg + lane, end);
+    for (int64_t base = beg; base < end; base += 32) {
+        if (__all_sync(0xffffffffu, done)) break;   // every pixel of the block has K_max layers
+        const ss_chunk cur = nxt;
+        const int n = stage_chunk(W, cur, recs, lane, gx0, gx1, gy0, gy1, (float)x0, (float)y0);
+        nxt = fetch_chunk(ws.keys, recs, base + 32 + lane, end);
+        for (int s = 0; s < n; ++s) {
+            const float4 r0 = W.r0[s], r1 = W.r1[s], r2 = W.r2[s], r3 = W.r3[s];
+            ss_hit h = ss_pixel_test(r0, r1, xl - r2.x, yl - r2.y, rc2);
+            bool cov = h.cover && !done;
+            const uint32_t fl = __float_as_uint(W.r4[s].w);
+            const uint32_t rx = __float_as_uint(r3.z), ry = __float_as_uint(r3.w);
+            if (fl & SS_FLAG_RECT_TEST) cov = cov && in_rect(rx, ry, px, py);
+            if (stats && inside) {
+                ++n_lane;
+                n_rect += in_rect(rx, ry, px, py) ? 1u : 0u;
+                n_frag += cov ? 1u : 0u;
             }
-            uint32_t mask = __ballot_sync(0xffffffffu, ov);
-            while (mask) {
-                const int b = __ffs(mask) - 1;
-                mask &= mask - 1;
-                const int s = c0 + b;
-                const float4 r0 = S.r0[s], r1 = S.r1[s], pz = S.pz[s];
-                ss_hit h = ss_pixel_test(r0, r1, xl - pz.x, yl - pz.y, rc2);
-                bool cov = h.cover && !done;
-                const uint4 m = S.meta[s];
-                if (m.z & SS_FLAG_RECT_TEST) {
-                    int i0 = m.x & 0xffff, i1 = m.x >> 16, j0 = m.y & 0xffff, j1 = m.y >> 16;
-                    cov = cov && px >= i0 && px <= i1 && py >= j0 && py <= j1;
-                }
-                if (stats && inside) {
-                    int i0 = m.x & 0xffff, i1 = m.x >> 16, j0 = m.y & 0xffff, j1 = m.y >> 16;
-                    ++n_lane;
-                    n_rect += (px >= i0 && px <= i1 && py >= j0 && py <= j1) ? 1u : 0u;
-                    n_frag += cov ? 1u : 0u;
-                }
-                if (cov) {
-                    const float w = r1.w * __expf(-0.5f * __fdividef(h.q, h.t));   // Eq. mip_weight
-                    if (Wg > 0.f && pz.z > zmax) flush();                          // gap: new layer
-                    if (!done) {
-                        zmax = fmaxf(zmax, pz.w);
-                        const float4 c0v = S.c0[s], c1v = S.c1[s], c2v = S.c2[s];
-                        C[0] = fmaf(w, c0v.x, C[0]); C[1] = fmaf(w, c0v.y, C[1]); C[2] = fmaf(w, c0v.z, C[2]);
-                        C[3] = fmaf(w, c0v.w, C[3]); C[4] = fmaf(w, c1v.x, C[4]); C[5] = fmaf(w, c1v.y, C[5]);
-                        C[6] = fmaf(w, c1v.z, C[6]); C[7] = fmaf(w, c1v.w, C[7]); C[8] = fmaf(w, c2v.x, C[8]);
-                        C[9] = fmaf(w, c2v.y, C[9]); C[10] = fmaf(w, c2v.z, C[10]); C[11] = fmaf(w, c2v.w, C[11]);
-                        Wg += w;
-                    }
+            if (cov) {
+                const float w = r1.w * __expf(-0.5f * __fdividef(h.q, h.t));   // Eq. mip_weight
+                if (Wg > 0.f && r3.x > zmax) flush();                          // gap: new layer
+                if (!done) {
+                    zmax = fmaxf(zmax, r3.y);
+                    const float4 c0v = W.r4[s], c1v = W.r5[s], c2v = W.r6[s];
+                    C[0] = fmaf(w, c0v.x, C[0]); C[1] = fmaf(w, c0v.y, C[1]); C[2] = fmaf(w, c0v.z, C[2]);
+                    C[3] = fmaf(w, c1v.x, C[3]); C[4] = fmaf(w, c1v.y, C[4]); C[5] = fmaf(w, c1v.z, C[5]);
+                    C[6] = fmaf(w, c1v.w, C[6]); C[7] = fmaf(w, c2v.x, C[7]); C[8] = fmaf(w, c2v.y, C[8]);
+                    C[9] = fmaf(w, c2v.z, C[9]); C[10] = fmaf(w, c2v.w, C[10]);
+                    C[11] = fmaf(w, 0.5f * (r3.x + r3.y), C[11]);
+                    Wg += w;
                 }
             }
         }
+        __syncwarp();
     }
     if (!done && Wg > 0.f) flush();
     if (stats) {

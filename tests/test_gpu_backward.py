@@ -17,6 +17,10 @@ FIELDS = ("pos", "quat", "log_scale", "albedo", "roughness", "metallic", "env")
 BLOCK_RTOL = 1e-4
 ELEM_RTOL = 1e-3
 ELEM_ATOL = 1e-5
+# surfels whose shading lookups sit within this many texels of a cell
+# boundary take a different interpolation cell in FP32 and FP64; their
+# per-element check is skipped (the block norms still include them)
+LOOKUP_MARGIN = 1e-4
 
 
 def _run(scene, seed=0, params=None, env_levels=6):
@@ -45,25 +49,34 @@ def _run(scene, seed=0, params=None, env_levels=6):
     gpu["env"] = r.d_env.cpu().numpy().astype(np.float64)
     # oracle: sum over views (each view's surfels are its scene's slice)
     ref = {k: np.zeros_like(v) for k, v in gpu.items()}
+    near = np.zeros(scene.surfels.n, bool)
     for v, rv in enumerate(refs):
         cam = scene.cameras[v]
         s0, s1 = int(scene.scene_offsets[cam.scene]), int(scene.scene_offsets[cam.scene + 1])
         for k in FIELDS[:-1]:
             ref[k][s0:s1] += rv["grad"][k].reshape(ref[k][s0:s1].shape)
+        near[s0:s1] |= rv["lookup_margin"] < LOOKUP_MARGIN
         ref["env"][cam.scene] += rv["grad"]["env"]
+    gpu["_near"] = near
     return gpu, ref
 
 
 def _compare(gpu, ref):
     msgs = []
+    near = gpu["_near"]
+    assert near.mean() < 1e-2, f"{near.sum()} surfels near a lookup cell boundary"
     for k in FIELDS:
-        g, rr = gpu[k].ravel(), ref[k].ravel()
+        g, rr = gpu[k], ref[k]
+        keep = np.ones(g.shape, bool)
+        if k != "env":
+            keep[near] = False
+        g, rr, keep = g.ravel(), rr.ravel(), keep.ravel()
         nrm = np.linalg.norm(rr)
         if nrm == 0:
             assert np.abs(g).max() == 0, k
             continue
         blk = np.linalg.norm(g - rr) / nrm
-        el = (np.abs(g - rr) / (ELEM_RTOL * np.abs(rr) + ELEM_ATOL * np.abs(rr).max())).max()
+        el = (np.abs(g - rr) / (ELEM_RTOL * np.abs(rr) + ELEM_ATOL * np.abs(rr).max()))[keep].max()
         print(f"{k}: block {blk:.2e} elem/bound {el:.2f}")
         if blk > BLOCK_RTOL or el > 1.0:
             msgs.append(f"{k}: block {blk:.2e} elem/bound {el:.2f}")
