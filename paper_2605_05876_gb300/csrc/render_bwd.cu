@@ -41,60 +41,40 @@ __device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane)
     return v[0];
 }
 
-__global__ void __launch_bounds__(256, 2) raster_bwd_kernel(ss_ws_view ws, ss_bwd_args a) {
-    __shared__ ss_wstage Wst[8];
+// Per pixel, per composited layer k (front to back), from the upstream
+// gradient g and the layer totals (C_k, W_k) kept by the forward pass:
+//   C_hat_k = C_k / W_k (normal: C_n / |C_n|), alpha_k = 1 - exp(-gamma W_k / 2 pi),
+//   G_k,c  = dL/dC_k,c = g_c T_k alpha_k / W_k                   (Eq. shepard)
+//   G_k,n  = dL/dC_n   = (d - n_hat (n_hat . d)) / |C_n|, d = g_n T_k alpha_k
+//   dL/dW_k (alpha path) = gamma/2pi (T_{k+1} g.C_hat_k - g.R_k + g_A T_end)
+//                          with R_k the radiance behind layer k (Eq. alpha, Eq. compositing)
+//   S_k = sum_c G_k,c C_hat_k,c - dL/dW_k (alpha path)
+// so that a fragment of weight w and channels ch in layer k has
+// dL/dw = sum_c G_k,c ch_c - S_k and dL/dch_c = G_k,c w.  (G_k, S_k) are
+// written over (C_k, W_k).
+__global__ void __launch_bounds__(256) layer_coeff_kernel(ss_ws_view ws, ss_bwd_args a) {
     const ss_layout* L = ws.layout;
-    const int tile = blockIdx.x;
-    const int view = find_view_tile(L, tile);
-    const ss_view_layout& vl = L->v[view];
-    const int lt = tile - vl.tile_off;
-    const int tx = lt % vl.tiles_x, ty = lt / vl.tiles_x;
-    const int x0 = tx * SS_TILE, y0 = ty * SS_TILE;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    ss_wstage& W = Wst[warp];
-    const int wx0 = 8 * (warp & 1), wy0 = 4 * (warp >> 1);
-    const int lx = wx0 + (lane & 7), ly = wy0 + (lane >> 3);
-    const int px = x0 + lx, py = y0 + ly;
-    const bool inside = px < vl.width && py < vl.height;
-    const int gx0 = x0 + wx0, gx1 = gx0 + 7, gy0 = y0 + wy0, gy1 = gy0 + 3;
-    const float xl = (float)lx + 0.5f, yl = (float)ly + 0.5f;
-    const float rc2 = a.f.p.r_cut * a.f.p.r_cut;
-    const float kw = a.f.p.gamma * (0.5f / SS_PI_F);
     const int64_t P = L->total_pixels;
-    const int64_t gpix = vl.pixel_off + (int64_t)(inside ? py : 0) * vl.width + (inside ? px : 0);
-
-    // per-pixel state from the forward pass
-    int K = 0;
-    float Tend = 1.f, gA = 0.f;
-    float g[SS_NCH], rem[SS_NCH];   // rem_c = out_c - sum_{j<=k} T_j alpha_j C_hat_j (colour behind layer k)
-    if (inside) {
-        K = __float_as_int(ws.pix_state[gpix]);
-        Tend = ws.pix_state[P + gpix];
-        float4 d = reinterpret_cast<const float4*>(a.d_rgba)[gpix];
-        float4 o = reinterpret_cast<const float4*>(a.out_rgba)[gpix];
-        g[0] = d.x; g[1] = d.y; g[2] = d.z; gA = d.w;
-        rem[0] = o.x; rem[1] = o.y; rem[2] = o.z;   // includes T_end * bg: R_k below needs it
+    const int64_t gpix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gpix >= P) return;
+    const int K = __float_as_int(ws.pix_state[gpix]);
+    if (K <= 0) return;
+    const float kw = a.f.p.gamma * (0.5f / SS_PI_F);
+    const float Tend = ws.pix_state[P + gpix];
+    float g[SS_NCH], rem[SS_NCH];   // rem_c = out_c - sum_{j<=k} T_j alpha_j C_hat_j
+    const float4 d = reinterpret_cast<const float4*>(a.d_rgba)[gpix];
+    const float4 o = reinterpret_cast<const float4*>(a.out_rgba)[gpix];
+    g[0] = d.x; g[1] = d.y; g[2] = d.z;
+    const float gA = d.w;
+    rem[0] = o.x; rem[1] = o.y; rem[2] = o.z;   // includes T_end * bg
 #pragma unroll
-        for (int c = 0; c < SS_N_AOV; ++c) {
-            g[3 + c] = a.d_aov ? a.d_aov[c * P + gpix] : 0.f;
-            rem[3 + c] = a.out_aov ? a.out_aov[c * P + gpix] : 0.f;
-        }
-    } else {
-#pragma unroll
-        for (int c = 0; c < SS_NCH; ++c) g[c] = rem[c] = 0.f;
+    for (int c = 0; c < SS_N_AOV; ++c) {
+        g[3 + c] = a.d_aov ? a.d_aov[c * P + gpix] : 0.f;
+        rem[3 + c] = a.out_aov ? a.out_aov[c * P + gpix] : 0.f;
     }
-    bool done = !inside || K == 0;
-    unsigned n_frag = 0;
-
-    // replay state (Algorithm 1) and per-layer gradient coefficients
-    int k = -1;
-    float Wr = 0.f, zmax = 0.f;
     float Tb = 1.f;
-    float G[SS_NCH];      // dL/dC_c for Shepard channels; for the normal channels H = dL/dC_n
-    float Sk = 0.f;       // sum_c G_c Chat_c - dL/dW (alpha path)
-
-    auto enter_layer = [&](int kk) {
-        const float* ls = ws.layer_state + (int64_t)kk * 13 * P + gpix;
+    for (int kk = 0; kk < K; ++kk) {
+        float* ls = ws.layer_state + (int64_t)kk * 13 * P + gpix;
         float C[SS_NCH];
 #pragma unroll
         for (int c = 0; c < SS_NCH; ++c) C[c] = ls[c * P];
@@ -116,23 +96,67 @@ __global__ void __launch_bounds__(256, 2) raster_bwd_kernel(ss_ws_view ws, ss_bw
             gChat = fmaf(g[c], hat[c], gChat);
             gR = fmaf(g[c], rem[c], gR);
         }
-        // Eq. alpha / Eq. compositing: dL/dW_k through alpha_k and all later T_j
         const float dW_alpha = kw * (Tb * e * gChat - gR + gA * Tend);
+        float G[SS_NCH];
         float sG = 0.f;
 #pragma unroll
         for (int c = 0; c < SS_NCH; ++c) {
             if (c >= 8 && c <= 10) continue;
-            G[c] = g[c] * tw * invW;          // Eq. shepard: C_hat = C / W
+            G[c] = g[c] * tw * invW;
             sG = fmaf(G[c], hat[c], sG);
         }
-        // renormalised normal n_hat = C_n / |C_n|
         const float dn0 = g[8] * tw, dn1 = g[9] * tw, dn2 = g[10] * tw;
         const float nd = dn0 * hat[8] + dn1 * hat[9] + dn2 * hat[10];
         G[8] = (dn0 - hat[8] * nd) * inl;
         G[9] = (dn1 - hat[9] * nd) * inl;
         G[10] = (dn2 - hat[10] * nd) * inl;
-        Sk = sG - dW_alpha;
+#pragma unroll
+        for (int c = 0; c < SS_NCH; ++c) ls[c * P] = G[c];
+        ls[12 * P] = sG - dW_alpha;
         Tb *= e;
+    }
+}
+
+__global__ void __launch_bounds__(256, 3) raster_bwd_kernel(ss_ws_view ws, ss_bwd_args a) {
+    __shared__ ss_wstage Wst[8];
+    const ss_layout* L = ws.layout;
+    const int tile = blockIdx.x;
+    const int view = find_view_tile(L, tile);
+    const ss_view_layout& vl = L->v[view];
+    const int lt = tile - vl.tile_off;
+    const int tx = lt % vl.tiles_x, ty = lt / vl.tiles_x;
+    const int x0 = tx * SS_TILE, y0 = ty * SS_TILE;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    ss_wstage& W = Wst[warp];
+    const int wx0 = 8 * (warp & 1), wy0 = 4 * (warp >> 1);
+    const int lx = wx0 + (lane & 7), ly = wy0 + (lane >> 3);
+    const int px = x0 + lx, py = y0 + ly;
+    const bool inside = px < vl.width && py < vl.height;
+    const int gx0 = x0 + wx0, gx1 = gx0 + 7, gy0 = y0 + wy0, gy1 = gy0 + 3;
+    const float xl = (float)lx + 0.5f, yl = (float)ly + 0.5f;
+    const float rc2 = a.f.p.r_cut * a.f.p.r_cut;
+    const float kw = a.f.p.gamma * (0.5f / SS_PI_F);
+    const int64_t P = L->total_pixels;
+    const int64_t gpix = vl.pixel_off + (int64_t)(inside ? py : 0) * vl.width + (inside ? px : 0);
+
+    // per-pixel state: layer count from the forward pass; the per-layer
+    // gradient coefficients (G_k, S_k) were written over the layer totals by
+    // layer_coeff_kernel
+    const int K = inside ? __float_as_int(ws.pix_state[gpix]) : 0;
+    bool done = !inside || K == 0;
+    unsigned n_frag = 0;
+
+    // replay state (Algorithm 1) and the current layer's coefficients
+    int k = -1;
+    float Wr = 0.f, zmax = 0.f;
+    float G[SS_NCH];      // dL/dC_c for Shepard channels; for the normal channels dL/dC_n
+    float Sk = 0.f;       // sum_c G_c Chat_c - dL/dW (alpha path)
+
+    auto enter_layer = [&](int kk) {
+        const float* ls = ws.layer_state + (int64_t)kk * 13 * P + gpix;
+#pragma unroll
+        for (int c = 0; c < SS_NCH; ++c) G[c] = ls[c * P];
+        Sk = ls[12 * P];
     };
 
     const int64_t cap = ws.max_instances;
@@ -217,6 +241,7 @@ __global__ void __launch_bounds__(256, 2) raster_bwd_kernel(ss_ws_view ws, ss_bw
 
 void ss_launch_raster_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st) {
     if (L.total_tiles <= 0) return;
+    layer_coeff_kernel<<<(unsigned)((L.total_pixels + 255) / 256), 256, 0, st>>>(ws, a);
     raster_bwd_kernel<<<L.total_tiles, 256, 0, st>>>(ws, a);
 }
 
@@ -281,11 +306,22 @@ __device__ __forceinline__ void uv_grad(const float d[3], float gu, float gv, fl
 // then sums them over the views, in a fixed order).
 #define PG_N 14   // pos 3, quat 4, log_scale 2, albedo 3, roughness, metallic
 
-__global__ void __launch_bounds__(128) project_bwd_kernel(ss_ws_view ws, ss_bwd_args A, int64_t n_records) {
+// Shared-memory copies of the environment gradients of one scene: the
+// irradiance map and the specular levels from `level` on (the small, most
+// contended ones).  Records of other scenes or larger levels add to global
+// memory directly.
+struct env_priv {
+    float* irr;        // [irr floats] or nullptr
+    float* spec;       // levels level .. L-1, back to back
+    int scene;
+    int level;
+    int64_t spec_off;  // offset of level `level` inside one scene's spec stack
+};
+
+__device__ __forceinline__ void pbwd_record(const ss_ws_view& ws, const ss_bwd_args& A, const int64_t r,
+                                            const env_priv& pv) {
     const ss_layout* L = ws.layout;
     const ss_fwd_args& a = A.f;
-    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (r >= n_records) return;
     int v = 0;
     {
         int lo = 0, hi = L->n_views - 1;
@@ -499,10 +535,16 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ss_ws_view ws, ss_bwd_
             float dmu = dbe1 * dbe_mu[0] + dbe2 * dbe_mu[1];
             float dmup = (mup > 0.f && mup < 1.f) ? dmu : 0.f;
             // environment texels
-            if (d_irr) scatter3(d_irr, un, vn, a.ed.irr_width, a.ed.irr_height, true, dLd, 1.f);
+            if (d_irr) {
+                float* dst = (pv.irr && scene == pv.scene) ? pv.irr : d_irr;
+                scatter3(dst, un, vn, a.ed.irr_width, a.ed.irr_height, true, dLd, 1.f);
+            }
             if (d_spec) {
-                scatter3(d_spec + o0, ur, vr, W0, H0, true, dLs, 1.f - lf);
-                scatter3(d_spec + o1, ur, vr, W1, H1, true, dLs, lf);
+                const bool mine = pv.spec && scene == pv.scene;
+                float* dst0 = (mine && l0 >= pv.level) ? pv.spec + (o0 - pv.spec_off) : d_spec + o0;
+                float* dst1 = (mine && l1 >= pv.level) ? pv.spec + (o1 - pv.spec_off) : d_spec + o1;
+                scatter3(dst0, ur, vr, W0, H0, true, dLs, 1.f - lf);
+                scatter3(dst1, ur, vr, W1, H1, true, dLs, lf);
             }
             // directions: Ld(uv(ns)), Ls(uv(refl))
             float gun = 0.f, gvn = 0.f, gur = 0.f, gvr = 0.f;
@@ -553,6 +595,54 @@ __global__ void __launch_bounds__(128) project_bwd_kernel(ss_ws_view ws, ss_bwd_
     for (int k = 0; k < PG_N; ++k) gr[k] = out[k];
 }
 
+// One CTA per contiguous block of records; env gradients of the block's
+// first scene are accumulated in shared memory and flushed once.
+__global__ void __launch_bounds__(128, 4) project_bwd_kernel(ss_ws_view ws, ss_bwd_args A, int64_t n_records,
+                                                            int64_t per_block, int priv_level, int64_t priv_spec_off,
+                                                            int priv_spec_floats) {
+    extern __shared__ float priv[];
+    const ss_layout* L = ws.layout;
+    const int64_t r0 = blockIdx.x * per_block;
+    if (r0 >= n_records) return;
+    const int64_t r1 = min(n_records, r0 + per_block);
+    int v0 = 0;
+    {
+        int lo = 0, hi = L->n_views - 1;
+        while (lo < hi) {
+            int m = (lo + hi + 1) >> 1;
+            if (L->v[m].rec_off <= r0) lo = m;
+            else hi = m - 1;
+        }
+        v0 = lo;
+    }
+    const int scene = L->v[v0].scene;
+    const int irr_floats = A.f.ed.irr_width * A.f.ed.irr_height * 3;
+    const bool use = A.genv.irr != nullptr && A.genv.spec != nullptr;
+    env_priv pv;
+    pv.irr = use ? priv : nullptr;
+    pv.spec = use ? priv + irr_floats : nullptr;
+    pv.scene = scene;
+    pv.level = priv_level;
+    pv.spec_off = priv_spec_off;
+    const int n_priv = irr_floats + priv_spec_floats;
+    if (use)
+        for (int k = threadIdx.x; k < n_priv; k += blockDim.x) priv[k] = 0.f;
+    __syncthreads();
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) pbwd_record(ws, A, r, pv);
+    __syncthreads();
+    if (use) {
+        const int64_t irr_stride = irr_floats;
+        int Wt, Ht;
+        const int64_t spec_stride = spec_level_off_b(A.f.ed, A.f.ed.n_levels, Wt, Ht);
+        float* gi = A.genv.irr + scene * irr_stride;
+        float* gs = A.genv.spec + scene * spec_stride + priv_spec_off;
+        for (int k = threadIdx.x; k < n_priv; k += blockDim.x) {
+            const float v = priv[k];
+            if (v != 0.f) atomicAdd(k < irr_floats ? gi + k : gs + (k - irr_floats), v);
+        }
+    }
+}
+
 // Sum the per-view parameter gradients of each surfel (views in order) and
 // add them to the caller's gradients.
 __global__ void __launch_bounds__(256) param_reduce_kernel(ss_ws_view ws, ss_surfel_grads g, int64_t n_total) {
@@ -588,6 +678,31 @@ __global__ void __launch_bounds__(256) param_reduce_kernel(ss_ws_view ws, ss_sur
 void ss_launch_project_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st) {
     int64_t n = L.scene_begin[L.n_scenes];
     if (n <= 0 || L.total_records <= 0) return;
-    project_bwd_kernel<<<(unsigned)((L.total_records + 127) / 128), 128, 0, st>>>(ws, a, L.total_records);
+    // privatise the irradiance map and the specular levels whose total fits 48 KB
+    const int irr_floats = a.f.ed.irr_width * a.f.ed.irr_height * 3;
+    int level = a.f.ed.n_levels;
+    int64_t priv_spec = 0;
+    while (level > 1) {
+        int W, H;
+        ss_env_level_size(&a.f.ed, level - 1, &W, &H);
+        if (irr_floats + priv_spec + (int64_t)W * H * 3 > 12288) break;
+        priv_spec += (int64_t)W * H * 3;
+        --level;
+    }
+    int64_t spec_off = 0;
+    for (int i = 0; i < level; ++i) {
+        int W, H;
+        ss_env_level_size(&a.f.ed, i, &W, &H);
+        spec_off += (int64_t)W * H * 3;
+    }
+    const int64_t per_block = 128 * 32;
+    const unsigned blocks = (unsigned)((L.total_records + per_block - 1) / per_block);
+    const size_t smem = sizeof(float) * (size_t)(irr_floats + priv_spec);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(project_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+        attr = true;
+    }
+    project_bwd_kernel<<<blocks, 128, smem, st>>>(ws, a, L.total_records, per_block, level, spec_off, (int)priv_spec);
     param_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ws, a.g, n);
 }

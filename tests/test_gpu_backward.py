@@ -17,6 +17,10 @@ FIELDS = ("pos", "quat", "log_scale", "albedo", "roughness", "metallic", "env")
 BLOCK_RTOL = 1e-4
 ELEM_RTOL = 1e-3
 ELEM_ATOL = 1e-5
+# an environment texel's gradient sums ~1e5 surfel contributions with
+# cancellation; FP32 accumulation in any order leaves ~eps sqrt(n) ~ 2e-5 of
+# the block scale
+ELEM_ATOL_ENV = 3e-5
 # surfels whose shading lookups sit within this many texels of a cell
 # boundary take a different interpolation cell in FP32 and FP64; their
 # per-element check is skipped (the block norms still include them)
@@ -76,7 +80,8 @@ def _compare(gpu, ref):
             assert np.abs(g).max() == 0, k
             continue
         blk = np.linalg.norm(g - rr) / nrm
-        el = (np.abs(g - rr) / (ELEM_RTOL * np.abs(rr) + ELEM_ATOL * np.abs(rr).max()))[keep].max()
+        atol = ELEM_ATOL_ENV if k == "env" else ELEM_ATOL
+        el = (np.abs(g - rr) / (ELEM_RTOL * np.abs(rr) + atol * np.abs(rr).max()))[keep].max()
         print(f"{k}: block {blk:.2e} elem/bound {el:.2f}")
         if blk > BLOCK_RTOL or el > 1.0:
             msgs.append(f"{k}: block {blk:.2e} elem/bound {el:.2f}")
