@@ -5,5 +5,5 @@ from . import scenes  # noqa: F401
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    from .build import build as _b
+    from .compile import build as _b
     return _b(force=force, verbose=verbose)
