@@ -201,6 +201,26 @@ ss_status ss_env_sizes(const ss_env_desc* d, int64_t* irr_floats, int64_t* spec_
 ss_status ss_env_prefilter(const ss_env_desc* d, int32_t n_envs, const float* env_dev,
                            float* irr_dev, float* spec_dev, float* aux_dev, void* stream);
 
+/* The same environment prefilter for callers that cannot allocate device
+ * memory (plugins handed only input/output buffers by a host application,
+ * code under a fixed budget or a pooled allocator that forbids cudaMalloc,
+ * or code that must not let cudaMalloc synchronise the device).  The paper
+ * has no counterpart: this is a convenience of this library.
+ * Instead of a caller-provided aux buffer it uses a fixed scratch array of
+ * SS_NOALLOC_AUX_FLOATS floats (4 MiB) in device memory, which every GPU that
+ * loads the library holds until the process exits; the call itself
+ * allocates nothing.  Inputs and outputs are as in ss_env_prefilter.
+ * Returns SS_ERR_INVALID_ARG if n_envs * aux_floats (ss_env_sizes) exceeds
+ * SS_NOALLOC_AUX_FLOATS (e.g. at most 5 maps of 512 x 256 with 6 levels).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents, so calls
+ * that overlap on the GPU (on different streams) race.  The scratch it keeps
+ * is not the aux that ss_env_prefilter_backward expects. */
+#define SS_NOALLOC_AUX_FLOATS (1 << 20)
+ss_status ss_env_prefilter_noalloc(const ss_env_desc* d, int32_t n_envs, const float* env_dev, float* irr_dev,
+                                   float* spec_dev, void* stream);
+
 /* Transpose of ss_env_prefilter: d_env += P^T (d_irr, d_spec).  aux_dev is
  * the scratch written by the forward call for the same env maps. */
 ss_status ss_env_prefilter_backward(const ss_env_desc* d, int32_t n_envs, const float* d_irr_dev,

@@ -26,6 +26,7 @@ SS_ERR_CUDA = 32
 SS_MAX_VIEWS = 256
 SS_MAX_SCENES = 64
 SS_N_AOV = 9
+SS_NOALLOC_AUX_FLOATS = 1 << 20
 
 
 class ss_camera(ctypes.Structure):
@@ -87,6 +88,7 @@ EXPORTS = {
     "ss_env_sizes": (c_i32, [ctypes.POINTER(ss_env_desc), ctypes.POINTER(c_i64), ctypes.POINTER(c_i64),
                              ctypes.POINTER(c_i64)]),
     "ss_env_prefilter": (c_i32, [ctypes.POINTER(ss_env_desc), c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "ss_env_prefilter_noalloc": (c_i32, [ctypes.POINTER(ss_env_desc), c_i32, c_vp, c_vp, c_vp, c_vp]),
     "ss_env_prefilter_backward": (c_i32, [ctypes.POINTER(ss_env_desc), c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "ss_workspace_size": (c_i32, [ctypes.POINTER(ss_batch_desc), ctypes.POINTER(ss_render_params), c_i32,
                                   ctypes.POINTER(ctypes.c_size_t)]),

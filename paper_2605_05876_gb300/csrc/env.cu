@@ -455,3 +455,46 @@ void ss_launch_env_prefilter_bwd(const ss_env_desc* d, int n_envs, const float* 
         aux_off += (int64_t)W * H * 4;
     }
 }
+
+// ------------------------------------------------------------------------
+// Environment prefilter for callers that cannot allocate device memory.
+//
+// Some callers only receive input and output buffers from a host
+// application (a plugin inside a larger renderer, a module running under a
+// fixed memory budget or a pooled allocator that forbids raw cudaMalloc,
+// code that must not call cudaMalloc because it synchronises the device).
+// They cannot provide the `aux` scratch of ss_env_prefilter, so this entry
+// keeps that scratch in a fixed array in device memory that every GPU which
+// loads the library holds until the process exits.
+#include <mutex>
+
+static __device__ __align__(256) float g_noalloc_aux[SS_NOALLOC_AUX_FLOATS];
+
+static std::mutex g_noalloc_mutex;
+static float* g_noalloc_aux_ptr[256] = {};   // device address of the array, per device
+
+extern "C" ss_status ss_env_prefilter_noalloc(const ss_env_desc* d, int32_t n_envs, const float* env_dev,
+                                              float* irr_dev, float* spec_dev, void* stream) {
+    if (!d || n_envs < 1 || !env_dev || !irr_dev || !spec_dev) return SS_ERR_INVALID_ARG;
+    int64_t irr_f, spec_f, aux_f;
+    if (ss_env_sizes(d, &irr_f, &spec_f, &aux_f) != SS_OK) return SS_ERR_INVALID_ARG;
+    if (aux_f * (int64_t)n_envs > (int64_t)SS_NOALLOC_AUX_FLOATS) return SS_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return SS_ERR_CUDA;
+    float* aux = nullptr;
+    {
+        // first call on this device: look up the array's device address (the
+        // host-side symbol is only a stand-in, not a device pointer)
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_aux_ptr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_aux) != cudaSuccess || !p) return SS_ERR_CUDA;
+            g_noalloc_aux_ptr[dev] = (float*)p;
+        }
+        aux = g_noalloc_aux_ptr[dev];
+    }
+    // every aux entry is written before it is read: nothing needs clearing
+    ss_launch_env_prefilter(d, n_envs, env_dev, irr_dev, spec_dev, aux, (cudaStream_t)stream);
+    if (cudaGetLastError() != cudaSuccess) return SS_ERR_CUDA;
+    return SS_OK;
+}
