@@ -280,6 +280,13 @@ ss_status ss_profile_end(ss_stage_times* out);
 /* Synchronise the stream and copy the work counters of ws into *out. */
 ss_status ss_read_stats(void* ws, ss_stats* out, void* stream);
 
+/* Number of kernels this library has launched in the calling process since it
+ * was loaded (every entry point's launches, on every device and stream).  A
+ * host-side counter with no counterpart in the paper: it lets a caller count
+ * the GPU work of a region (read before and after).  out: host int64.
+ * Errors: SS_ERR_INVALID_ARG for a null out. */
+ss_status ss_launch_count(int64_t* out);
+
 /* Synchronise the stream and return (and clear) the device status word in
  * ws: SS_OK or an OR of SS_ERR_CAPACITY / SS_ERR_TIMEOUT / SS_ERR_NONFINITE. */
 ss_status ss_read_status(void* ws, void* stream);

@@ -106,6 +106,7 @@ EXPORTS = {
                                    ctypes.c_size_t, c_vp]),
     "ss_read_status": (c_i32, [c_vp, c_vp]),
     "ss_read_stats": (c_i32, [c_vp, ctypes.c_void_p, c_vp]),
+    "ss_launch_count": (c_i32, [ctypes.POINTER(ctypes.c_int64)]),
     "ss_profile_begin": (c_i32, []),
     "ss_profile_end": (c_i32, [ctypes.c_void_p]),
 }

@@ -228,3 +228,10 @@ def profile_end() -> dict:
     t = C.ss_stage_times()
     check(lib().ss_profile_end(ctypes.byref(t)), "ss_profile_end")
     return {name: (float(t.ms[i]), int(t.launches[i])) for i, name in enumerate(C.STAGES)}
+
+
+def launch_count() -> int:
+    """Kernels the library has launched in this process so far."""
+    n = ctypes.c_int64()
+    check(lib().ss_launch_count(ctypes.byref(n)), "ss_launch_count")
+    return int(n.value)

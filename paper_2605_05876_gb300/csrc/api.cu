@@ -1,5 +1,6 @@
 // C ABI entry points (include/ss3d.h): argument checks, batch layout,
 // workspace carving and the launch sequences.
+#include <atomic>
 #include <math.h>
 #include <string.h>
 
@@ -47,6 +48,15 @@ struct stage_scope {
     }
 };
 }  // namespace
+
+static std::atomic<long long> g_launches{0};
+void ss_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+extern "C" ss_status ss_launch_count(int64_t* out) {
+    if (!out) return SS_ERR_INVALID_ARG;
+    *out = (int64_t)g_launches.load(std::memory_order_relaxed);
+    return SS_OK;
+}
 
 extern "C" ss_status ss_profile_begin(void) {
     g_prof.on = true;
@@ -345,7 +355,9 @@ static ss_status forward_core(const ss_batch_desc* b, const ss_surfels* s, const
     a.out_aov = p->write_aov ? out_aov : nullptr;
     a.with_backward = with_bwd;
     CK(cudaMemsetAsync(W.status, 0, 256, st));   // status word and work counters
+    ss_note_launch();
     set_layout_kernel<<<1, 256, 0, st>>>(W.layout, L);
+    ss_note_launch();
     view_geo_kernel<<<(L.n_views + 63) / 64, 64, 0, st>>>(b->cams_dev, W.vgeo, L.n_views);
     CK(cudaMemsetAsync(W.tile_count, 0, sizeof(uint32_t) * (size_t)L.total_tiles, st));
     CK(cudaMemsetAsync(W.tile_cursor, 0, sizeof(uint32_t) * (size_t)L.total_tiles, st));

@@ -155,6 +155,7 @@ __global__ void __launch_bounds__(256) brdf_lut_kernel(float* lut, int n, gl_nod
 
 void ss_launch_brdf_lut(float* lut, int n, cudaStream_t st) {
     static gl_nodes g = make_gl_nodes();
+    ss_note_launch();
     brdf_lut_kernel<<<n * n, 256, 0, st>>>(lut, n, g);
 }
 
@@ -239,7 +240,7 @@ __device__ __forceinline__ float pf_weight(bool ggx, float a2, const float wt[3]
     float one_m_c2 = 0.5f * omm;                        // 1 - (n.h)^2
     float c2 = 1.f - one_m_c2;
     float den = one_m_c2 + c2 * a2;                     // c2 (a2 - 1) + 1
-    return a2 / (SS_PI_F * den * den) * mu * dom;
+    return a2 * (1.f / SS_PI_F) * __frcp_rn(den * den) * mu * dom;
 }
 
 __device__ __forceinline__ float4 block_sum4(float4 v, float4* sh) {
@@ -411,8 +412,10 @@ void ss_launch_env_prefilter(const ss_env_desc* d, int n_envs, const float* env,
                   aux_stride = ss_env_aux_floats(d);
     const int Wi = d->irr_width, Hi = d->irr_height;
     dim3 g(Wi * Hi, n_envs);
+    ss_note_launch();
     prefilter_fwd_kernel<<<g, 256, table_smem(We, He), st>>>(env, env_stride, We, He, irr, irr_stride, Wi, Hi, aux,
                                                             aux_stride, 0, 0.f);
+    ss_note_launch();
     copy_level0_kernel<<<dim3(256, n_envs), 256, 0, st>>>(env, env_stride, spec, spec_stride, env_stride);
     int64_t spec_off = env_stride, aux_off = (int64_t)Wi * Hi;
     for (int i = 1; i < d->n_levels; ++i) {
@@ -420,9 +423,11 @@ void ss_launch_env_prefilter(const ss_env_desc* d, int n_envs, const float* env,
         ss_env_level_size(d, i, &W, &H);
         float* norm = aux + aux_off;
         float* src = aux + aux_off + (int64_t)W * H;
+        ss_note_launch();
         box_down_kernel<<<dim3((W * H + 255) / 256, n_envs), 256, 0, st>>>(env, env_stride, We, He, src, aux_stride,
                                                                            W, H);
         float r = (float)i / (float)(d->n_levels - 1);
+        ss_note_launch();
         prefilter_fwd_kernel<<<dim3(W * H, n_envs), 256, table_smem(W, H), st>>>(
             src, aux_stride, W, H, spec + spec_off, spec_stride, W, H, norm, aux_stride, 1, r * r);
         spec_off += (int64_t)W * H * 3;
@@ -437,10 +442,13 @@ void ss_launch_env_prefilter_bwd(const ss_env_desc* d, int n_envs, const float* 
     const int64_t irr_stride = ss_env_irr_floats(d), spec_stride = ss_env_spec_floats(d),
                   aux_stride = ss_env_aux_floats(d);
     const int Wi = d->irr_width, Hi = d->irr_height;
-    if (d_irr)
+    if (d_irr) {
+        ss_note_launch();
         prefilter_bwd_kernel<<<dim3(We * He, n_envs), 256, table_smem(Wi, Hi), st>>>(
             d_irr, irr_stride, Wi, Hi, aux, aux_stride, We, He, d_env, env_stride, We, 1, 1, 0, 0.f);
+    }
     if (!d_spec) return;
+    ss_note_launch();
     add_level0_kernel<<<dim3(256, n_envs), 256, 0, st>>>(d_spec, spec_stride, d_env, env_stride, env_stride);
     int64_t spec_off = env_stride, aux_off = (int64_t)Wi * Hi;
     for (int i = 1; i < d->n_levels; ++i) {
@@ -448,6 +456,7 @@ void ss_launch_env_prefilter_bwd(const ss_env_desc* d, int n_envs, const float* 
         ss_env_level_size(d, i, &W, &H);
         const float* norm = aux + aux_off;
         float r = (float)i / (float)(d->n_levels - 1);
+        ss_note_launch();
         prefilter_bwd_kernel<<<dim3(W * H, n_envs), 256, table_smem(W, H), st>>>(
             d_spec + spec_off, spec_stride, W, H, norm, aux_stride, W, H, d_env, env_stride, We, We / W, He / H, 1,
             r * r);

@@ -15,13 +15,15 @@
 #define WSLOTS 32
 
 struct ss_wstage {
-    float4 r0[WSLOTS];  // P (screen quadratic-form factor)
-    float4 r1[WSLOTS];  // A2, B2, 1, n_f
-    float4 r2[WSLOTS];  // centre relative to the tile origin (x, y), then copy of px_lo, py_lo
-    float4 r3[WSLOTS];  // z_start, z_end, rect_x, rect_y
-    float4 r4[WSLOTS];  // rgb, flags
-    float4 r5[WSLOTS];  // albedo, roughness
-    float4 r6[WSLOTS];  // metallic, normal
+    float4 h0[WSLOTS];  // P (screen quadratic-form factor)            -- every test
+    float4 h1[WSLOTS];  // A2, B2, centre x, y relative to the tile      -- every test
+    float4 h2[WSLOTS];  // z_start, z_end, +-n_f (negative: test the support rectangle), -
+    float4 c0[WSLOTS];  // rgb, flags                                     -- covering fragments
+    float4 c1[WSLOTS];  // albedo, roughness
+    float4 c2[WSLOTS];  // metallic, normal
+    float4 t1[WSLOTS];  // staging copies of record rows 1 and 2
+    float4 t2[WSLOTS];
+    uint2 rect[WSLOTS];
     uint32_t id[WSLOTS];
 };
 
@@ -70,22 +72,24 @@ __device__ __forceinline__ int stage_chunk(ss_wstage& W, const ss_chunk& c, cons
     if (ov) {
         const int pos = __popc(mask & ((1u << lane) - 1u));
         const ss_rec* rc = recs + c.id;
-        cp_async16(&W.r0[pos], &rc->r0);
-        cp_async16(&W.r1[pos], &rc->r1);
-        cp_async16(&W.r2[pos], &rc->r2);
-        cp_async16(&W.r4[pos], &rc->r4);
-        cp_async16(&W.r5[pos], &rc->r5);
-        cp_async16(&W.r6[pos], &rc->r6);
-        W.r3[pos] = c.r3;
+        cp_async16(&W.h0[pos], &rc->r0);
+        cp_async16(&W.t1[pos], &rc->r1);
+        cp_async16(&W.t2[pos], &rc->r2);
+        cp_async16(&W.c0[pos], &rc->r4);
+        cp_async16(&W.c1[pos], &rc->r5);
+        cp_async16(&W.c2[pos], &rc->r6);
+        W.rect[pos] = make_uint2(__float_as_uint(c.r3.z), __float_as_uint(c.r3.w));
         W.id[pos] = c.id;
     }
     cp_async_wait_all();
     if (ov) {
         const int pos = __popc(mask & ((1u << lane) - 1u));
-        float4 p = W.r2[pos];
-        p.x = __fadd_rn(__fsub_rn(p.x, tx0), p.z);
-        p.y = __fadd_rn(__fsub_rn(p.y, ty0), p.w);
-        W.r2[pos] = p;
+        const float4 r1 = W.t1[pos], r2 = W.t2[pos];
+        const uint32_t fl = __float_as_uint(W.c0[pos].w);
+        const float prx = __fadd_rn(__fsub_rn(r2.x, tx0), r2.z);
+        const float pry = __fadd_rn(__fsub_rn(r2.y, ty0), r2.w);
+        W.h1[pos] = make_float4(r1.x, r1.y, prx, pry);
+        W.h2[pos] = make_float4(c.r3.x, c.r3.y, (fl & SS_FLAG_RECT_TEST) ? -r1.w : r1.w, 0.f);
     }
     __syncwarp();
     return __popc(mask);

@@ -135,7 +135,6 @@ __global__ void __launch_bounds__(256, 3) raster_bwd_kernel(ss_ws_view ws, ss_bw
     const int gx0 = x0 + wx0, gx1 = gx0 + 7, gy0 = y0 + wy0, gy1 = gy0 + 3;
     const float xl = (float)lx + 0.5f, yl = (float)ly + 0.5f;
     const float rc2 = a.f.p.r_cut * a.f.p.r_cut;
-    const float kw = a.f.p.gamma * (0.5f / SS_PI_F);
     const int64_t P = L->total_pixels;
     const int64_t gpix = vl.pixel_off + (int64_t)(inside ? py : 0) * vl.width + (inside ? px : 0);
 
@@ -172,56 +171,63 @@ __global__ void __launch_bounds__(256, 3) raster_bwd_kernel(ss_ws_view ws, ss_bw
         const int n = stage_chunk(W, cur, recs, lane, gx0, gx1, gy0, gy1, (float)x0, (float)y0);
         nxt = fetch_chunk(ws.keys, recs, base + 32 + lane, end);
         for (int s = 0; s < n; ++s) {
-            const float4 r0 = W.r0[s], r1 = W.r1[s], r2 = W.r2[s], r3 = W.r3[s];
-            const float dx = xl - r2.x, dy = yl - r2.y;
-            ss_hit h = ss_pixel_test(r0, r1, dx, dy, rc2);
+            const float4 h0 = W.h0[s], h1 = W.h1[s];
+            const float dx = xl - h1.z, dy = yl - h1.w;
+            const ss_hit h = ss_pixel_test(h0, h1, dx, dy, rc2);
             bool cov = h.cover && !done;
-            const uint32_t fl = __float_as_uint(W.r4[s].w);
-            if (fl & SS_FLAG_RECT_TEST) cov = cov && in_rect(__float_as_uint(r3.z), __float_as_uint(r3.w), px, py);
             float gr[32];
 #pragma unroll
             for (int q = 0; q < 32; ++q) gr[q] = 0.f;
             bool contrib = false;
             if (cov) {
-                const float rho2 = __fdividef(h.q, h.t);
-                const float ex = __expf(-0.5f * rho2);
-                const float w = r1.w * ex;
-                // replay of Algorithm 1: the forward kernel's condition, bit for bit
-                if (k < 0) {
-                    k = 0;
-                    enter_layer(0);
-                } else if (Wr > 0.f && r3.x > zmax) {
-                    ++k;
-                    Wr = 0.f;
-                    zmax = 0.f;
-                    if (k >= K) done = true;
-                    else enter_layer(k);
+                const float4 h2 = W.h2[s];
+                float nf = h2.z;
+                if (nf < 0.f) {   // support rectangle may clip this surfel
+                    const uint2 rr = W.rect[s];
+                    cov = in_rect(rr.x, rr.y, px, py);
+                    nf = -nf;
                 }
-                if (!done) {
-                    zmax = fmaxf(zmax, r3.y);
-                    Wr += w;
-                    const float4 c0v = W.r4[s], c1v = W.r5[s], c2v = W.r6[s];
-                    const float ch[SS_NCH] = {c0v.x, c0v.y, c0v.z, c1v.x, c1v.y, c1v.z,
-                                              c1v.w, c2v.x, c2v.y, c2v.z, c2v.w, 0.5f * (r3.x + r3.y)};
-                    float dLdw = -Sk;
-#pragma unroll
-                    for (int c = 0; c < SS_NCH; ++c) {
-                        dLdw = fmaf(G[c], ch[c], dLdw);
-                        gr[G_CH + c] = G[c] * w;
+                if (cov) {
+                    const float rho2 = __fdividef(h.q, h.t);
+                    const float ex = __expf(-0.5f * rho2);
+                    const float w = nf * ex;
+                    // replay of Algorithm 1: the forward kernel's condition, bit for bit
+                    if (k < 0) {
+                        k = 0;
+                        enter_layer(0);
+                    } else if (Wr > 0.f && h2.x > zmax) {
+                        ++k;
+                        Wr = 0.f;
+                        zmax = 0.f;
+                        if (k >= K) done = true;
+                        else enter_layer(k);
                     }
-                    // w = n_f exp(-rho2 / 2), rho2 = q / s2^2 (Eq. mip_weight)
-                    gr[G_NF] = dLdw * ex;
-                    const float grho = -0.5f * w * dLdw;
-                    const float it = 1.f / h.t;
-                    const float gs0 = 2.f * grho * h.s0 * it, gs1 = 2.f * grho * h.s1 * it;
-                    const float gs2 = -2.f * grho * rho2 / h.s2;
-                    gr[G_P + 0] = gs0 * dx; gr[G_P + 1] = gs0 * dy;
-                    gr[G_P + 2] = gs1 * dx; gr[G_P + 3] = gs1 * dy;
-                    gr[G_A2] = gs2 * dx; gr[G_B2] = gs2 * dy;
-                    gr[G_PX] = -(gs0 * r0.x + gs1 * r0.z + gs2 * r1.x);
-                    gr[G_PY] = -(gs0 * r0.y + gs1 * r0.w + gs2 * r1.y);
-                    contrib = true;
-                    ++n_frag;
+                    if (!done) {
+                        zmax = fmaxf(zmax, h2.y);
+                        Wr += w;
+                        const float4 c0v = W.c0[s], c1v = W.c1[s], c2v = W.c2[s];
+                        const float ch[SS_NCH] = {c0v.x, c0v.y, c0v.z, c1v.x, c1v.y, c1v.z,
+                                                  c1v.w, c2v.x, c2v.y, c2v.z, c2v.w, 0.5f * (h2.x + h2.y)};
+                        float dLdw = -Sk;
+#pragma unroll
+                        for (int c = 0; c < SS_NCH; ++c) {
+                            dLdw = fmaf(G[c], ch[c], dLdw);
+                            gr[G_CH + c] = G[c] * w;
+                        }
+                        // w = n_f exp(-rho2 / 2), rho2 = q / s2^2 (Eq. mip_weight)
+                        gr[G_NF] = dLdw * ex;
+                        const float grho = -0.5f * w * dLdw;
+                        const float it = 1.f / h.t;
+                        const float gs0 = 2.f * grho * h.s0 * it, gs1 = 2.f * grho * h.s1 * it;
+                        const float gs2 = -2.f * grho * rho2 / h.s2;
+                        gr[G_P + 0] = gs0 * dx; gr[G_P + 1] = gs0 * dy;
+                        gr[G_P + 2] = gs1 * dx; gr[G_P + 3] = gs1 * dy;
+                        gr[G_A2] = gs2 * dx; gr[G_B2] = gs2 * dy;
+                        gr[G_PX] = -(gs0 * h0.x + gs1 * h0.z + gs2 * h1.x);
+                        gr[G_PY] = -(gs0 * h0.y + gs1 * h0.w + gs2 * h1.y);
+                        contrib = true;
+                        ++n_frag;
+                    }
                 }
             }
             // warp reduction, then one add per value
@@ -241,7 +247,9 @@ __global__ void __launch_bounds__(256, 3) raster_bwd_kernel(ss_ws_view ws, ss_bw
 
 void ss_launch_raster_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st) {
     if (L.total_tiles <= 0) return;
+    ss_note_launch();
     layer_coeff_kernel<<<(unsigned)((L.total_pixels + 255) / 256), 256, 0, st>>>(ws, a);
+    ss_note_launch();
     raster_bwd_kernel<<<L.total_tiles, 256, 0, st>>>(ws, a);
 }
 
@@ -389,8 +397,6 @@ __device__ __forceinline__ void pbwd_record(const ss_ws_view& ws, const ss_bwd_a
         const ss_view_geo& vg = ws.vgeo[v];
         const float cmo[3] = {(c[0] - vg.o_hi[0]) - vg.o_lo[0], (c[1] - vg.o_hi[1]) - vg.o_lo[1],
                               (c[2] - vg.o_hi[2]) - vg.o_lo[2]};
-        const float ncx = Rc[0] * nrm[0] + Rc[1] * nrm[1] + Rc[2] * nrm[2];
-        const float ncy = Rc[3] * nrm[0] + Rc[4] * nrm[1] + Rc[5] * nrm[2];
         const float4 r1 = ws.rec[r].r1;
         const float A2 = r1.x, B2 = r1.y;
         const float Nd = ss_plane_distance(q4, c[0], c[1], c[2], vg.o_hi, vg.o_lo);
@@ -703,6 +709,8 @@ void ss_launch_project_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bw
         cudaFuncSetAttribute(project_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
         attr = true;
     }
+    ss_note_launch();
     project_bwd_kernel<<<blocks, 128, smem, st>>>(ws, a, L.total_records, per_block, level, spec_off, (int)priv_spec);
+    ss_note_launch();
     param_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ws, a.g, n);
 }

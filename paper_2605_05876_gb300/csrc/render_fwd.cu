@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(256) project_kernel(ss_ws_view ws, ss_fwd_args
     const float tu[3] = {su * Rq[0], su * Rq[3], su * Rq[6]};
     const float tv[3] = {sv * Rq[1], sv * Rq[4], sv * Rq[7]};
     const float nrm[3] = {Rq[2], Rq[5], Rq[8]};
-    const float rc = a.p.r_cut, rc2 = rc * rc, sig = a.p.sigma_f;
+    const float rc = a.p.r_cut, rc2 = rc * rc;
     const int nL = a.ed.n_levels;
     const int64_t irr_stride = (int64_t)a.ed.irr_width * a.ed.irr_height * 3;
     int64_t spec_stride = 0;
@@ -245,6 +245,7 @@ __global__ void __launch_bounds__(256) project_kernel(ss_ws_view ws, ss_fwd_args
 void ss_launch_project(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st) {
     int64_t n = L.scene_begin[L.n_scenes];
     if (n <= 0) return;
+    ss_note_launch();
     project_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ws, a, n);
 }
 
@@ -401,16 +402,20 @@ __global__ void __launch_bounds__(SORT_THREADS) tile_sort_kernel(ss_ws_view ws, 
 
 void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st) {
     (void)a;
+    ss_note_launch();
     scan_kernel<<<1, 1024, 0, st>>>(ws.tile_count, ws.tile_start, L.total_tiles, ws.status, ws.max_instances,
                                     ws.stats);
-    if (L.total_records > 0)
+    if (L.total_records > 0) {
+        ss_note_launch();
         scatter_kernel<<<(unsigned)((L.total_records + 255) / 256), 256, 0, st>>>(ws, L.total_records);
+    }
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(tile_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              SORT_CAP * (int)sizeof(unsigned long long));
         attr = true;
     }
+    ss_note_launch();
     tile_sort_kernel<<<L.total_tiles, SORT_THREADS, SORT_CAP * sizeof(unsigned long long), st>>>(ws, L.total_tiles);
 }
 
@@ -422,6 +427,7 @@ void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_a
 // little work never waits for a busy one, and a warp whose 32 pixels have all
 // reached K_max layers stops reading the list.
 
+template <bool STATS>
 __global__ void __launch_bounds__(256, 3) raster_fwd_kernel(ss_ws_view ws, ss_fwd_args a) {
     __shared__ ss_wstage Wst[8];
     const ss_layout* L = ws.layout;
@@ -444,7 +450,6 @@ __global__ void __launch_bounds__(256, 3) raster_fwd_kernel(ss_ws_view ws, ss_fw
     const int kmax = a.p.k_max;
     const int64_t gpix = vl.pixel_off + (int64_t)py * vl.width + px;
     const int64_t P = L->total_pixels;
-    const bool stats = a.p.collect_stats != 0;
     unsigned n_lane = 0, n_rect = 0, n_frag = 0;
 
     float C[SS_NCH];
@@ -497,36 +502,43 @@ __global__ void __launch_bounds__(256, 3) raster_fwd_kernel(ss_ws_view ws, ss_fw
         const int n = stage_chunk(W, cur, recs, lane, gx0, gx1, gy0, gy1, (float)x0, (float)y0);
         nxt = fetch_chunk(ws.keys, recs, base + 32 + lane, end);
         for (int s = 0; s < n; ++s) {
-            const float4 r0 = W.r0[s], r1 = W.r1[s], r2 = W.r2[s], r3 = W.r3[s];
-            ss_hit h = ss_pixel_test(r0, r1, xl - r2.x, yl - r2.y, rc2);
+            const float4 h0 = W.h0[s], h1 = W.h1[s];
+            const ss_hit h = ss_pixel_test(h0, h1, xl - h1.z, yl - h1.w, rc2);
             bool cov = h.cover && !done;
-            const uint32_t fl = __float_as_uint(W.r4[s].w);
-            const uint32_t rx = __float_as_uint(r3.z), ry = __float_as_uint(r3.w);
-            if (fl & SS_FLAG_RECT_TEST) cov = cov && in_rect(rx, ry, px, py);
-            if (stats && inside) {
+            if (STATS && inside) {
+                const uint2 rr = W.rect[s];
                 ++n_lane;
-                n_rect += in_rect(rx, ry, px, py) ? 1u : 0u;
-                n_frag += cov ? 1u : 0u;
+                n_rect += in_rect(rr.x, rr.y, px, py) ? 1u : 0u;
             }
             if (cov) {
-                const float w = r1.w * __expf(-0.5f * __fdividef(h.q, h.t));   // Eq. mip_weight
-                if (Wg > 0.f && r3.x > zmax) flush();                          // gap: new layer
-                if (!done) {
-                    zmax = fmaxf(zmax, r3.y);
-                    const float4 c0v = W.r4[s], c1v = W.r5[s], c2v = W.r6[s];
-                    C[0] = fmaf(w, c0v.x, C[0]); C[1] = fmaf(w, c0v.y, C[1]); C[2] = fmaf(w, c0v.z, C[2]);
-                    C[3] = fmaf(w, c1v.x, C[3]); C[4] = fmaf(w, c1v.y, C[4]); C[5] = fmaf(w, c1v.z, C[5]);
-                    C[6] = fmaf(w, c1v.w, C[6]); C[7] = fmaf(w, c2v.x, C[7]); C[8] = fmaf(w, c2v.y, C[8]);
-                    C[9] = fmaf(w, c2v.z, C[9]); C[10] = fmaf(w, c2v.w, C[10]);
-                    C[11] = fmaf(w, 0.5f * (r3.x + r3.y), C[11]);
-                    Wg += w;
+                const float4 h2 = W.h2[s];
+                float nf = h2.z;
+                if (nf < 0.f) {   // support rectangle may clip this surfel
+                    const uint2 rr = W.rect[s];
+                    cov = in_rect(rr.x, rr.y, px, py);
+                    nf = -nf;
+                }
+                if (cov) {
+                    if (STATS) ++n_frag;
+                    const float w = nf * __expf(-0.5f * __fdividef(h.q, h.t));   // Eq. mip_weight
+                    if (Wg > 0.f && h2.x > zmax) flush();                          // gap: new layer
+                    if (!done) {
+                        zmax = fmaxf(zmax, h2.y);
+                        const float4 c0v = W.c0[s], c1v = W.c1[s], c2v = W.c2[s];
+                        C[0] = fmaf(w, c0v.x, C[0]); C[1] = fmaf(w, c0v.y, C[1]); C[2] = fmaf(w, c0v.z, C[2]);
+                        C[3] = fmaf(w, c1v.x, C[3]); C[4] = fmaf(w, c1v.y, C[4]); C[5] = fmaf(w, c1v.z, C[5]);
+                        C[6] = fmaf(w, c1v.w, C[6]); C[7] = fmaf(w, c2v.x, C[7]); C[8] = fmaf(w, c2v.y, C[8]);
+                        C[9] = fmaf(w, c2v.z, C[9]); C[10] = fmaf(w, c2v.w, C[10]);
+                        C[11] = fmaf(w, 0.5f * (h2.x + h2.y), C[11]);
+                        Wg += w;
+                    }
                 }
             }
         }
         __syncwarp();
     }
     if (!done && Wg > 0.f) flush();
-    if (stats) {
+    if (STATS) {
         unsigned long long v[4] = {n_rect, n_lane, n_frag, (unsigned)K * (inside ? 1u : 0u)};
         for (int q = 0; q < 4; ++q) {
             unsigned long long x = v[q];
@@ -553,5 +565,7 @@ __global__ void __launch_bounds__(256, 3) raster_fwd_kernel(ss_ws_view ws, ss_fw
 
 void ss_launch_raster_fwd(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st) {
     if (L.total_tiles <= 0) return;
-    raster_fwd_kernel<<<L.total_tiles, 256, 0, st>>>(ws, a);
+    ss_note_launch();
+    if (a.p.collect_stats) raster_fwd_kernel<true><<<L.total_tiles, 256, 0, st>>>(ws, a);
+    else raster_fwd_kernel<false><<<L.total_tiles, 256, 0, st>>>(ws, a);
 }

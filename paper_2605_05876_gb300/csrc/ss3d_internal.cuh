@@ -221,11 +221,12 @@ struct ss_hit {
     float s0, s1, s2, q, t;  // t = s2^2
     bool cover;
 };
+// r0 = P, r1.xy = (A2, B2); s2 = A2 dx + B2 dy + 1
 __device__ __forceinline__ ss_hit ss_pixel_test(float4 r0, float4 r1, float dx, float dy, float rc2) {
     ss_hit h;
     h.s0 = __fmaf_rn(r0.x, dx, __fmul_rn(r0.y, dy));
     h.s1 = __fmaf_rn(r0.z, dx, __fmul_rn(r0.w, dy));
-    h.s2 = __fmaf_rn(r1.x, dx, __fmaf_rn(r1.y, dy, r1.z));
+    h.s2 = __fmaf_rn(r1.x, dx, __fmaf_rn(r1.y, dy, 1.f));
     h.q = __fmaf_rn(h.s0, h.s0, __fmul_rn(h.s1, h.s1));
     h.t = __fmul_rn(h.s2, h.s2);
     h.cover = (h.s2 > 0.f) && (h.q < __fmul_rn(rc2, h.t));
@@ -234,6 +235,9 @@ __device__ __forceinline__ ss_hit ss_pixel_test(float4 r0, float4 r1, float dx, 
 
 // ------------------------------------------------------------------------
 // host-side launchers implemented in the .cu files
+
+// host-side count of kernel launches (ss_launch_count); call before each launch
+void ss_note_launch();
 
 void ss_launch_brdf_lut(float* lut, int n, cudaStream_t st);
 void ss_launch_env_prefilter(const ss_env_desc* d, int n_envs, const float* env, float* irr, float* spec,

@@ -71,3 +71,7 @@ def test_host_side_argument_errors():
     assert b.value == 3 * (64 * 32 + 32 * 16 + 16 * 8 + 8 * 4 * 3)
     assert lib.ss_brdf_lut(None, 128, None) == _lib.SS_ERR_INVALID_ARG
     assert lib.ss_error_string(_lib.SS_ERR_CAPACITY) == b"instance capacity exceeded"
+    # the launch counter is host-side: readable without a GPU, null out rejected
+    n = ctypes.c_int64(-1)
+    assert lib.ss_launch_count(ctypes.byref(n)) == 0 and n.value >= 0
+    assert lib.ss_launch_count(None) == _lib.SS_ERR_INVALID_ARG
