@@ -144,7 +144,8 @@ typedef struct ss_stage_times {
 typedef struct ss_env_desc {
     int32_t width, height;   /* base map, width = 2 height, both powers of two */
     int32_t n_levels;        /* specular levels (roughness i/(n_levels-1)) */
-    int32_t irr_width, irr_height; /* diffuse irradiance map size */
+    int32_t irr_width, irr_height; /* diffuse irradiance map size; irr_width a power of
+                                      two <= width, irr_height in [1, 512] */
 } ss_env_desc;
 
 /* Prefiltered environment of every scene plus the BRDF table (device). */

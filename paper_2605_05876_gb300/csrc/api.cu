@@ -285,7 +285,7 @@ static bool env_desc_ok(const ss_env_desc* d) {
     auto pow2 = [](int x) { return x > 0 && (x & (x - 1)) == 0; };
     return pow2(d->width) && pow2(d->height) && d->width >= 8 && d->height >= 4 && d->width <= 16384 &&
            d->height <= 8192 && d->n_levels >= 1 && d->n_levels <= 16 && d->irr_width >= 1 && d->irr_height >= 1 &&
-           d->irr_width <= 1024 && d->irr_height <= 512;
+           d->irr_width <= d->width && pow2(d->irr_width) && d->irr_height <= 512;
 }
 
 extern "C" ss_status ss_env_sizes(const ss_env_desc* d, int64_t* irr_floats, int64_t* spec_floats,

@@ -1,16 +1,21 @@
 // Split-sum BRDF table and environment prefilter (Sec. 3.4.2, Eq. ibl).
 //
-// The prefilter is a dense linear operator per output texel: every output
-// texel is a normalised weighted sum over all texels of its source map.  It
-// is bound by FP32 issue (a few GFLOP per call), not by memory, so one CTA
-// owns one output texel and its threads stride over the source texels with
-// the per-row / per-column trigonometry staged in shared memory.
+// The prefilter is a dense linear operator: every output texel is a
+// normalised weighted sum over all texels of its source map.  Its weight
+// depends only on the angle between the two texel directions, so on the
+// equirectangular grid each pair of rows contributes a circular convolution
+// along phi; the kernels evaluate one weight per (row pair, phi offset) and
+// spend the rest of their time in shared-memory multiply-adds (FP32 issue
+// bound, a few GFLOP per call).
 #include <math.h>
 #include <stdio.h>
 
+#include <cooperative_groups.h>
 #include <vector>
 
 #include "ss3d_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 // ------------------------------------------------------------------------
 // BRDF table
@@ -190,178 +195,208 @@ int64_t ss_env_aux_floats(const ss_env_desc* d) {
     return t;
 }
 
-// Source-map trigonometry staged in shared memory: per column (sin phi,
-// cos phi), per row (sin th, cos th, dOmega).
-struct src_tables {
-    float* sphi;
-    float* cphi;
-    float* sth;
-    float* cth;
-    float* dom;
+// Row-pair circular convolutions.  Output texel (a, b) of a Wo x Ho map and
+// source texel (j, b') of a Ws x Hs map (Ws = r Wo, both equirectangular,
+// texel centres at phi = 2 pi ((i + 1/2)/W - 1/2), th = pi (i + 1/2)/H) see
+// each other at
+//   1 - mu = 2 sin^2((th_b - th_b')/2) + 2 sin th_b sin th_b' sin^2(dphi/2),
+//   dphi/2 = pi (2 delta - r + 1) / (2 Ws),  delta = (j - r a) mod Ws,
+// so one row pair (b, b') adds a circular convolution along phi whose weights
+// depend on delta alone.  Every term of 1 - mu is non-negative, so it keeps
+// full relative precision next to the lobe peak, where the GGX weight of a
+// low roughness is steepest.
+
+struct conv_row {
+    float A, B, dom;   // 2 sin^2((th_b - th_b')/2), 2 sin th_b sin th_b', dOmega of row b'
 };
 
-__device__ void load_tables(src_tables t, int W, int H) {
-    for (int a = threadIdx.x; a < W; a += blockDim.x) {
-        float s, c;
-        sincospif(2.f * ((a + 0.5f) / W - 0.5f), &s, &c);
-        t.sphi[a] = s;
-        t.cphi[a] = c;
-    }
-    for (int b = threadIdx.x; b < H; b += blockDim.x) {
-        float s, c;
-        sincospif((b + 0.5f) / H, &s, &c);
-        t.sth[b] = s;
-        t.cth[b] = c;
-        // (2 pi / W)(cos th- - cos th+) = (2 pi / W) 2 sin(th_b) sin(pi / 2H)
-        t.dom[b] = (2.f * SS_PI_F / W) * 2.f * s * sinpif(0.5f / H);
-    }
+__device__ __forceinline__ conv_row conv_rowpair(int b, int Ho, int bs, int Hs, int Ws) {
+    conv_row c;
+    // (th_b - th_b') / 2 = pi ((2b + 1) Hs - (2b' + 1) Ho) / (4 Ho Hs); the
+    // denominator is exact in float (Hs is a power of two, Ho <= 8192)
+    const long long num = (long long)(2 * b + 1) * Hs - (long long)(2 * bs + 1) * Ho;
+    const float sa = sinpif((float)num / (float)(4LL * Ho * Hs));
+    c.A = 2.f * sa * sa;
+    const float so = sinpif((b + 0.5f) / Ho), ss = sinpif((bs + 0.5f) / Hs);
+    c.B = 2.f * so * ss;
+    // (2 pi / Ws)(cos th- - cos th+) = (2 pi / Ws) 2 sin th_b' sin(pi / 2 Hs)
+    c.dom = (2.f * SS_PI_F / Ws) * 2.f * ss * sinpif(0.5f / Hs);
+    return c;
 }
 
-__device__ __forceinline__ void texel_dir(int a, int b, int W, int H, float d[3]) {
-    float sp, cp, stt, ctt;
-    sincospif(2.f * ((a + 0.5f) / W - 0.5f), &sp, &cp);
-    sincospif((b + 0.5f) / H, &stt, &ctt);
-    d[0] = stt * sp;
-    d[1] = ctt;
-    d[2] = -stt * cp;
+__device__ __forceinline__ float conv_T(int delta, int r, int Ws) {
+    const float s = sinpif((float)(2 * delta - r + 1) / (float)(2 * Ws));   // sin(dphi / 2)
+    return s * s;
 }
 
-// Weight of source direction wj for output direction wt: diffuse kind uses
-// max(0, mu) dOmega; GGX kind uses D(h) max(0, mu) dOmega with
-// (n.h)^2 = (1 + mu)/2.  1 - mu is formed as |wt - wj|^2 / 2 (exact for unit
-// vectors, no cancellation near the lobe peak).
-__device__ __forceinline__ float pf_weight(bool ggx, float a2, const float wt[3], float x, float y, float z,
-                                           float dom) {
-    float e0 = wt[0] - x, e1 = wt[1] - y, e2 = wt[2] - z;
-    float omm = 0.5f * (e0 * e0 + e1 * e1 + e2 * e2);  // 1 - mu
-    float mu = 1.f - omm;
+// Weight of one (output, source) pair: diffuse kind max(0, mu) dOmega; GGX
+// kind D(h) max(0, mu) dOmega with (n.h)^2 = (1 + mu)/2 (n = v = r).
+__device__ __forceinline__ float conv_weight(int ggx, float a2, const conv_row& c, float T) {
+    const float omm = fmaf(c.B, T, c.A);   // 1 - mu
+    const float mu = 1.f - omm;
     if (!(mu > 0.f)) return 0.f;
-    if (!ggx) return mu * dom;
-    float one_m_c2 = 0.5f * omm;                        // 1 - (n.h)^2
-    float c2 = 1.f - one_m_c2;
-    float den = one_m_c2 + c2 * a2;                     // c2 (a2 - 1) + 1
-    return a2 * (1.f / SS_PI_F) * __frcp_rn(den * den) * mu * dom;
+    if (!ggx) return mu * c.dom;
+    const float h = 0.5f * omm;             // 1 - (n.h)^2
+    const float den = fmaf(1.f - h, a2, h); // (n.h)^2 (a2 - 1) + 1
+    return a2 * (1.f / SS_PI_F) * __frcp_rn(den * den) * mu * c.dom;
 }
 
-__device__ __forceinline__ float4 block_sum4(float4 v, float4* sh) {
-    // warp shuffle then shared
-    for (int o = 16; o > 0; o >>= 1) {
-        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
-        v.z += __shfl_xor_sync(0xffffffffu, v.z, o);
-        v.w += __shfl_xor_sync(0xffffffffu, v.w, o);
-    }
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    float4 r = make_float4(0, 0, 0, 0);
-    if (threadIdx.x < 32) {
-        int nw = blockDim.x >> 5;
-        r = l < nw ? sh[l] : make_float4(0, 0, 0, 0);
-        for (int o = 16; o > 0; o >>= 1) {
-            r.x += __shfl_xor_sync(0xffffffffu, r.x, o);
-            r.y += __shfl_xor_sync(0xffffffffu, r.y, o);
-            r.z += __shfl_xor_sync(0xffffffffu, r.z, o);
-            r.w += __shfl_xor_sync(0xffffffffu, r.w, o);
-        }
-    }
-    return r;  // valid in thread 0
-}
+// Staged rows are read at stride r or R by consecutive lanes; one pad float
+// per 32 keeps those reads free of bank conflicts.
+__device__ __forceinline__ int conv_pad(int k) { return k + (k >> 5); }
+static inline int conv_pad_h(int k) { return k + (k >> 5); }
 
-// One CTA per output texel (blockIdx.x), blockIdx.y = env index.
-// out[t] = sum_j w_tj src[j] / sum_j w_tj ; inv_norm[t] = 1 / sum_j w_tj.
-__global__ void __launch_bounds__(256) prefilter_fwd_kernel(const float* src, int64_t src_stride, int Ws, int Hs,
-                                                            float* out, int64_t out_stride, int Wo, int Ho,
-                                                            float* inv_norm, int64_t norm_stride, int ggx,
-                                                            float alpha) {
-    extern __shared__ float smem[];
-    src_tables tb{smem, smem + Ws, smem + 2 * Ws, smem + 2 * Ws + Hs, smem + 2 * Ws + 2 * Hs};
-    __shared__ float4 red[8];
+// Forward: out[b][a] = sum_{b', j} w src[b'][j] / sum_{b', j} w.
+//
+// A cluster of KS CTAs owns one (output row b, tile of TA*R outputs, env);
+// CTA q of the cluster takes the source rows [q Hs/KS, (q+1) Hs/KS), its
+// thread (al, p) the rows p (mod P) of those and the R consecutive outputs
+// a0 + R al + t.  The weights of TD offsets delta and the source columns
+// they reach are staged in shared memory per row; with R = 4 (r = 1) a
+// thread reuses each staged source value for 4 outputs.  The cluster's
+// partial sums meet in the leader's reduction through distributed shared
+// memory, in a fixed order (deterministic), summed in FP64.
+template <int R>
+__global__ void __launch_bounds__(256) envconv_fwd_kernel(const float* __restrict__ src, int64_t src_stride, int Ws,
+                                                          int Hs, float* out, int64_t out_stride, int Wo, int Ho,
+                                                          float* inv_norm, int64_t norm_stride, int ggx, float alpha,
+                                                          int TA, int P, int TD, int SCP) {
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(16) float csm[];
+    const int KS = (int)cluster.num_blocks();
+    const int q = (int)cluster.block_rank();
+    const int r = Ws / Wo;
+    const int OT = TA * R;
+    const int n_ab = Wo / OT;
+    const int tile = blockIdx.x / KS;
+    const int b = tile / n_ab, a0 = (tile % n_ab) * OT;
     const int e = blockIdx.y;
+    const int al = threadIdx.x % TA, p = threadIdx.x / TA;
+    float* wts = csm;               // [P][TD]
+    float* srcs = csm + P * TD;     // [P][3][SCP]
     const float* S = src + e * src_stride;
-    load_tables(tb, Ws, Hs);
-    __syncthreads();
-    const int t = blockIdx.x;
-    float wt[3];
-    texel_dir(t % Wo, t / Wo, Wo, Ho, wt);
     const float a2 = alpha * alpha;
-    float4 acc = make_float4(0, 0, 0, 0);
-    const int n_src = Ws * Hs;
-    for (int j = threadIdx.x; j < n_src; j += blockDim.x) {
-        int a = j % Ws, b = j / Ws;
-        float st = tb.sth[b];
-        float w = pf_weight(ggx != 0, a2, wt, st * tb.sphi[a], tb.cth[b], -st * tb.cphi[a], tb.dom[b]);
-        if (w != 0.f) {
-            const float* s = S + (int64_t)j * 3;
-            acc.x = fmaf(w, s[0], acc.x);
-            acc.y = fmaf(w, s[1], acc.y);
-            acc.z = fmaf(w, s[2], acc.z);
-            acc.w += w;
-        }
-    }
-    float4 r = block_sum4(acc, red);
-    if (threadIdx.x == 0) {
-        float inv = 1.f / r.w;
-        float* o = out + e * out_stride + (int64_t)t * 3;
-        o[0] = r.x * inv;
-        o[1] = r.y * inv;
-        o[2] = r.z * inv;
-        inv_norm[e * norm_stride + t] = inv;
-    }
-}
-
-// d_src[j] (+)= sum_t w_tj inv_norm[t] d_out[t]; one CTA per source texel.
-// If box > 0, the result is spread over the box x box block of the base map
-// (adjoint of the box average), else added to d_src[j] directly.
-__global__ void __launch_bounds__(256) prefilter_bwd_kernel(const float* d_out, int64_t dout_stride, int Wo,
-                                                            int Ho, const float* inv_norm, int64_t norm_stride,
-                                                            int Ws, int Hs, float* d_base, int64_t base_stride,
-                                                            int Wb, int bw, int bh, int ggx, float alpha) {
-    extern __shared__ float smem[];
-    src_tables tb{smem, smem + Wo, smem + 2 * Wo, smem + 2 * Wo + Ho, smem + 2 * Wo + 2 * Ho};
-    __shared__ float4 red[8];
-    const int e = blockIdx.y;
-    // tables of the OUTPUT grid (we loop over outputs)
-    load_tables(tb, Wo, Ho);
-    __syncthreads();
-    const int j = blockIdx.x;
-    float wj[3];
-    texel_dir(j % Ws, j / Ws, Ws, Hs, wj);
-    // dOmega of the source texel
-    float sj, cj;
-    sincospif((j / Ws + 0.5f) / Hs, &sj, &cj);
-    const float domj = (2.f * SS_PI_F / Ws) * 2.f * sj * sinpif(0.5f / Hs);
-    const float a2 = alpha * alpha;
-    const float* dO = d_out + e * dout_stride;
-    const float* inv = inv_norm + e * norm_stride;
-    float4 acc = make_float4(0, 0, 0, 0);
-    const int n_out = Wo * Ho;
-    for (int t = threadIdx.x; t < n_out; t += blockDim.x) {
-        int a = t % Wo, b = t / Wo;
-        float st = tb.sth[b];
-        float wt[3] = {st * tb.sphi[a], tb.cth[b], -st * tb.cphi[a]};
-        float w = pf_weight(ggx != 0, a2, wt, wj[0], wj[1], wj[2], domj);
-        if (w != 0.f) {
-            w *= inv[t];
-            const float* g = dO + (int64_t)t * 3;
-            acc.x = fmaf(w, g[0], acc.x);
-            acc.y = fmaf(w, g[1], acc.y);
-            acc.z = fmaf(w, g[2], acc.z);
-        }
-    }
-    float4 r = block_sum4(acc, red);
-    if (threadIdx.x == 0) {
-        float* D = d_base + e * base_stride;
-        int ja = j % Ws, jb = j / Ws;
-        float sc = 1.f / (bw * bh);
-        for (int y = 0; y < bh; ++y)
-            for (int x = 0; x < bw; ++x) {
-                float* o = D + ((int64_t)(jb * bh + y) * Wb + (ja * bw + x)) * 3;
-                o[0] += r.x * sc;
-                o[1] += r.y * sc;
-                o[2] += r.z * sc;
+    const int SC = r * (OT - 1) + TD;
+    const int RPC = (Hs + KS - 1) / KS, row0 = q * RPC;
+    float acc[R][3];
+#pragma unroll
+    for (int t = 0; t < R; ++t) acc[t][0] = acc[t][1] = acc[t][2] = 0.f;
+    float nsum = 0.f;
+    for (int i0 = 0; i0 < RPC; i0 += P) {
+        const bool row_ok = i0 + p < RPC && row0 + i0 + p < Hs;
+        const int bs = row0 + (row_ok ? i0 + p : 0);
+        const conv_row c = conv_rowpair(b, Ho, bs, Hs, Ws);
+        const float* Srow = S + (int64_t)bs * Ws * 3;
+        for (int d0 = 0; d0 < Ws; d0 += TD) {
+            for (int i = al; i < TD; i += TA) {
+                const float w = row_ok ? conv_weight(ggx, a2, c, conv_T(d0 + i, r, Ws)) : 0.f;
+                wts[p * TD + i] = w;
+                nsum += w;
             }
+            if (row_ok) {
+                const int jb = r * a0 + d0;
+                for (int k = al; k < SC; k += TA) {
+                    const float* g = Srow + (int64_t)((jb + k) & (Ws - 1)) * 3;
+                    const int pk = conv_pad(k);
+                    srcs[(p * 3 + 0) * SCP + pk] = __ldg(g);
+                    srcs[(p * 3 + 1) * SCP + pk] = __ldg(g + 1);
+                    srcs[(p * 3 + 2) * SCP + pk] = __ldg(g + 2);
+                }
+            }
+            __syncthreads();
+            if (row_ok) {
+                const float4* wp = reinterpret_cast<const float4*>(wts + p * TD);
+                const float* s0 = srcs + p * 3 * SCP;
+                const float* s1 = s0 + SCP;
+                const float* s2 = s1 + SCP;
+                const int kb = r * R * al;
+                float x[R][3][2];
+#pragma unroll
+                for (int t = 0; t < R; ++t)
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) x[t][ch][0] = x[t][ch][1] = 0.f;
+                for (int i = 0; i < TD; i += 4) {
+                    const float4 w4 = wp[i >> 2];
+                    const float w[4] = {w4.x, w4.y, w4.z, w4.w};
+                    if constexpr (R == 1) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int pk = conv_pad(kb + i + u);
+                            x[0][0][u & 1] = fmaf(w[u], s0[pk], x[0][0][u & 1]);
+                            x[0][1][u & 1] = fmaf(w[u], s1[pk], x[0][1][u & 1]);
+                            x[0][2][u & 1] = fmaf(w[u], s2[pk], x[0][2][u & 1]);
+                        }
+                    } else {
+                        // r = 1: output t at offset i + u reads source k = kb + t + i + u
+                        float v0[R + 3], v1[R + 3], v2[R + 3];
+#pragma unroll
+                        for (int m = 0; m < R + 3; ++m) {
+                            const int pk = conv_pad(kb + i + m);
+                            v0[m] = s0[pk];
+                            v1[m] = s1[pk];
+                            v2[m] = s2[pk];
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+#pragma unroll
+                            for (int t = 0; t < R; ++t) {
+                                x[t][0][u & 1] = fmaf(w[u], v0[u + t], x[t][0][u & 1]);
+                                x[t][1][u & 1] = fmaf(w[u], v1[u + t], x[t][1][u & 1]);
+                                x[t][2][u & 1] = fmaf(w[u], v2[u + t], x[t][2][u & 1]);
+                            }
+                    }
+                }
+#pragma unroll
+                for (int t = 0; t < R; ++t)
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) acc[t][ch] += x[t][ch][0] + x[t][ch][1];
+            }
+            __syncthreads();
+        }
     }
+    // CTA partials: per output over the parts, normaliser over all threads
+    const int nt = blockDim.x;
+    float* red = csm;                                          // [nt][3R], then [nt] weights
+    double* cpart = reinterpret_cast<double*>(csm + ((nt * (3 * R + 1) + 1) & ~1));   // [OT][3], then norm
+#pragma unroll
+    for (int t = 0; t < R; ++t)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) red[threadIdx.x * 3 * R + t * 3 + ch] = acc[t][ch];
+    red[nt * 3 * R + threadIdx.x] = nsum;
+    __syncthreads();
+    if (p == 0) {
+        for (int v = 0; v < 3 * R; ++v) {
+            double s = 0.0;
+            for (int pp = 0; pp < P; ++pp) s += red[(pp * TA + al) * 3 * R + v];
+            cpart[R * al * 3 + v] = s;   // output R al + v / 3, channel v % 3
+        }
+    }
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < nt; ++i) s += red[nt * 3 * R + i];
+        cpart[OT * 3] = s;
+    }
+    cluster.sync();
+    if (q == 0) {
+        for (int o = threadIdx.x; o < OT; o += nt) {
+            double t0 = 0.0, t1 = 0.0, t2 = 0.0, nrm = 0.0;
+            for (int qq = 0; qq < KS; ++qq) {
+                const double* pc = cluster.map_shared_rank(cpart, qq);
+                t0 += pc[o * 3];
+                t1 += pc[o * 3 + 1];
+                t2 += pc[o * 3 + 2];
+                nrm += pc[OT * 3];
+            }
+            const double inv = 1.0 / nrm;
+            const int a = a0 + o;
+            float* po = out + e * out_stride + ((int64_t)b * Wo + a) * 3;
+            po[0] = (float)(t0 * inv);
+            po[1] = (float)(t1 * inv);
+            po[2] = (float)(t2 * inv);
+            inv_norm[e * norm_stride + (int64_t)b * Wo + a] = (float)inv;
+        }
+    }
+    cluster.sync();   // peers keep their shared memory until the leader has read it
 }
 
 // box average of the base map into a level-sized source
@@ -402,7 +437,243 @@ __global__ void add_level0_kernel(const float* d_spec, int64_t spec_stride, floa
         d_env[e * env_stride + i] += d_spec[e * spec_stride + i];
 }
 
-static size_t table_smem(int W, int H) { return sizeof(float) * (2 * W + 3 * H); }
+// Adjoint: d_src[b'][j] = sum_{b, a} w(b, b', (j - r a) mod Ws) inv_norm[b][a]
+// d_out[b][a], spread over the bw x bh block of the base map that source
+// texel was box-averaged from.
+//
+// A cluster of KS CTAs owns one (source row b', tile of TJ*R columns, env);
+// CTA q takes the output rows [q Ho/KS, (q+1) Ho/KS), its thread (jl, p) the
+// rows p (mod P) of those and the R consecutive columns j0 + R jl + t.  TAC
+// outputs a at a time, the weights of the offset window they reach and the
+// scaled upstream values inv_norm d_out are staged in shared memory; with
+// R = 4 (r = 1) a thread reuses each staged weight for 4 columns.  The
+// leader CTA sums the cluster's partials (FP64, fixed order) and writes the
+// base-map block.
+template <int R>
+__global__ void __launch_bounds__(256) envconv_bwd_kernel(const float* __restrict__ d_out, int64_t dout_stride,
+                                                          int Wo, int Ho, const float* __restrict__ inv_norm,
+                                                          int64_t norm_stride, int Ws, int Hs, float* d_base,
+                                                          int64_t base_stride, int Wb, int bw, int bh, int ggx,
+                                                          float alpha, int TJ, int P, int TAC, int WWP) {
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(16) float csm[];
+    const int KS = (int)cluster.num_blocks();
+    const int q = (int)cluster.block_rank();
+    const int r = Ws / Wo;
+    const int JT = TJ * R;
+    const int n_jb = Ws / JT;
+    const int tile = blockIdx.x / KS;
+    const int bs = tile / n_jb, j0 = (tile % n_jb) * JT;
+    const int e = blockIdx.y;
+    const int jl = threadIdx.x % TJ, p = threadIdx.x / TJ;
+    const int WW = JT + r * (TAC - 1);
+    float4* gs = reinterpret_cast<float4*>(csm);   // [P][TAC]
+    float* wwin = csm + 4 * P * TAC;                // [P][WWP]
+    const float* dO = d_out + e * dout_stride;
+    const float* inv = inv_norm + e * norm_stride;
+    const float a2 = alpha * alpha;
+    const int RPC = (Ho + KS - 1) / KS, row0 = q * RPC;
+    float acc[R][3];
+#pragma unroll
+    for (int t = 0; t < R; ++t) acc[t][0] = acc[t][1] = acc[t][2] = 0.f;
+    for (int i0 = 0; i0 < RPC; i0 += P) {
+        const bool row_ok = i0 + p < RPC && row0 + i0 + p < Ho;
+        const int b = row0 + (row_ok ? i0 + p : 0);
+        const conv_row c = conv_rowpair(b, Ho, bs, Hs, Ws);
+        for (int c0 = 0; c0 < Wo; c0 += TAC) {
+            // window entry k holds delta = (dstart + k) mod Ws
+            const int dstart = j0 - r * (c0 + TAC - 1);
+            for (int k = jl; k < WW; k += TJ) {
+                const float w = row_ok ? conv_weight(ggx, a2, c, conv_T((dstart + k) & (Ws - 1), r, Ws)) : 0.f;
+                wwin[p * WWP + (R > 1 ? conv_pad(k) : k)] = w;
+            }
+            for (int u = jl; u < TAC; u += TJ) {
+                float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (row_ok) {
+                    const int64_t t = (int64_t)b * Wo + c0 + u;
+                    const float s = __ldg(inv + t);
+                    g = make_float4(__ldg(dO + t * 3) * s, __ldg(dO + t * 3 + 1) * s, __ldg(dO + t * 3 + 2) * s, 0.f);
+                }
+                gs[p * TAC + u] = g;
+            }
+            __syncthreads();
+            if (row_ok) {
+                const float* wp = wwin + p * WWP;
+                const float4* gp = gs + p * TAC;
+                // column t of this thread and output c0 + u meet at k = kb + t - u
+                const int kb = R * jl + r * (TAC - 1);
+                float x[R][3][2];
+#pragma unroll
+                for (int t = 0; t < R; ++t)
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) x[t][ch][0] = x[t][ch][1] = 0.f;
+                if constexpr (R == 1) {
+                    for (int u = 0; u < TAC; ++u) {   // TAC <= 64 terms per chain
+                        const float w = wp[kb - r * u];
+                        const float4 g = gp[u];
+                        x[0][0][0] = fmaf(w, g.x, x[0][0][0]);
+                        x[0][1][0] = fmaf(w, g.y, x[0][1][0]);
+                        x[0][2][0] = fmaf(w, g.z, x[0][2][0]);
+                    }
+                } else {
+                    for (int u = 0; u < TAC; u += 4) {
+                        // k = kb + t - (u + v) = (kb - u - 3) + m with m = t - v + 3
+                        float wv[R + 3];
+#pragma unroll
+                        for (int m = 0; m < R + 3; ++m) wv[m] = wp[conv_pad(kb - u - 3 + m)];
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            const float4 g = gp[u + v];
+#pragma unroll
+                            for (int t = 0; t < R; ++t) {
+                                const float w = wv[t - v + 3];
+                                x[t][0][v & 1] = fmaf(w, g.x, x[t][0][v & 1]);
+                                x[t][1][v & 1] = fmaf(w, g.y, x[t][1][v & 1]);
+                                x[t][2][v & 1] = fmaf(w, g.z, x[t][2][v & 1]);
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int t = 0; t < R; ++t)
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) acc[t][ch] += x[t][ch][0] + x[t][ch][1];
+            }
+            __syncthreads();
+        }
+    }
+    const int nt = blockDim.x;
+    float* red = csm;                                                              // [nt][3R]
+    double* cpart = reinterpret_cast<double*>(csm + ((nt * 3 * R + 1) & ~1));     // [JT][3]
+#pragma unroll
+    for (int t = 0; t < R; ++t)
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) red[threadIdx.x * 3 * R + t * 3 + ch] = acc[t][ch];
+    __syncthreads();
+    if (p == 0) {
+        for (int v = 0; v < 3 * R; ++v) {
+            double s = 0.0;
+            for (int pp = 0; pp < P; ++pp) s += red[(pp * TJ + jl) * 3 * R + v];
+            cpart[R * jl * 3 + v] = s;
+        }
+    }
+    cluster.sync();
+    if (q == 0) {
+        const double sc = 1.0 / (bw * bh);
+        float* D = d_base + e * base_stride;
+        for (int o = threadIdx.x; o < JT; o += nt) {
+            double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+            for (int qq = 0; qq < KS; ++qq) {
+                const double* pc = cluster.map_shared_rank(cpart, qq);
+                t0 += pc[o * 3];
+                t1 += pc[o * 3 + 1];
+                t2 += pc[o * 3 + 2];
+            }
+            const float v0 = (float)(t0 * sc), v1 = (float)(t1 * sc), v2 = (float)(t2 * sc);
+            const int j = j0 + o;
+            for (int y = 0; y < bh; ++y)
+                for (int x = 0; x < bw; ++x) {
+                    float* po = D + ((int64_t)(bs * bh + y) * Wb + (j * bw + x)) * 3;
+                    po[0] += v0;
+                    po[1] += v1;
+                    po[2] += v2;
+                }
+        }
+    }
+    cluster.sync();
+}
+
+// launch shapes: power-of-two block sizes, clusters of <= 8 CTAs, <= 48 KB of
+// shared memory per CTA
+static const int CONV_SMEM = 48 * 1024;
+static const int CONV_KS = 8;
+
+static int pow2_floor(int x) {
+    int p = 1;
+    while (p * 2 <= x) p *= 2;
+    return p;
+}
+
+template <typename... KArgs, typename... Args>
+static void launch_cluster(void (*kern)(KArgs...), dim3 grid, int block, int smem, int ks, cudaStream_t st,
+                           Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(block, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = ks;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    ss_note_launch();
+    cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+static void launch_conv_fwd(const float* src, int64_t src_stride, int Ws, int Hs, float* out, int64_t out_stride,
+                            int Wo, int Ho, float* inv_norm, int64_t norm_stride, int ggx, float alpha, int n_envs,
+                            cudaStream_t st) {
+    const int r = Ws / Wo;
+    const int R = (r == 1 && Wo >= 64) ? 4 : 1;
+    const int TA = (Wo / R < 256 / R) ? Wo / R : 256 / R;
+    const int OT = TA * R;
+    const int TD = Ws < 256 ? Ws : 256;
+    const int SC = r * (OT - 1) + TD;
+    const int SCP = conv_pad_h(SC - 1) + 1;
+    const int per_part = (TD + 3 * SCP) * (int)sizeof(float);
+    int P = 256 / TA;
+    if (P > Hs) P = Hs;
+    if (P * per_part > CONV_SMEM) P = CONV_SMEM / per_part;
+    P = pow2_floor(P < 1 ? 1 : P);
+    int KS = Hs / P;
+    if (KS > CONV_KS) KS = CONV_KS;
+    KS = pow2_floor(KS < 1 ? 1 : KS);
+    const int nt = TA * P;
+    int smem = P * per_part;
+    const int red = (((nt * (3 * R + 1) + 1) & ~1) + 2 * (OT * 3 + 1)) * (int)sizeof(float);
+    if (smem < red) smem = red;
+    const dim3 grid(Ho * (Wo / OT) * KS, n_envs);
+    if (R == 4)
+        launch_cluster(envconv_fwd_kernel<4>, grid, nt, smem, KS, st, src, src_stride, Ws, Hs, out, out_stride, Wo, Ho,
+                       inv_norm, norm_stride, ggx, alpha, TA, P, TD, SCP);
+    else
+        launch_cluster(envconv_fwd_kernel<1>, grid, nt, smem, KS, st, src, src_stride, Ws, Hs, out, out_stride, Wo, Ho,
+                       inv_norm, norm_stride, ggx, alpha, TA, P, TD, SCP);
+}
+
+static void launch_conv_bwd(const float* d_out, int64_t dout_stride, int Wo, int Ho, const float* inv_norm,
+                            int64_t norm_stride, int Ws, int Hs, float* d_base, int64_t base_stride, int Wb, int bw,
+                            int bh, int ggx, float alpha, int n_envs, cudaStream_t st) {
+    const int r = Ws / Wo;
+    const int R = (r == 1 && Ws >= 64) ? 4 : 1;
+    const int TJ = (Ws / R < 256 / R) ? Ws / R : 256 / R;
+    const int JT = TJ * R;
+    const int TAC = Wo < 64 ? Wo : 64;
+    const int WW = JT + r * (TAC - 1);
+    const int WWP = R > 1 ? conv_pad_h(WW - 1) + 1 : WW;
+    const int per_part = (4 * TAC + WWP) * (int)sizeof(float);
+    int P = 256 / TJ;
+    if (P > Ho) P = Ho;
+    if (P * per_part > CONV_SMEM) P = CONV_SMEM / per_part;
+    P = pow2_floor(P < 1 ? 1 : P);
+    int KS = Ho / P;
+    if (KS > CONV_KS) KS = CONV_KS;
+    KS = pow2_floor(KS < 1 ? 1 : KS);
+    const int nt = TJ * P;
+    int smem = P * per_part;
+    const int red = (((nt * 3 * R + 1) & ~1) + 2 * JT * 3) * (int)sizeof(float);
+    if (smem < red) smem = red;
+    const dim3 grid(Hs * (Ws / JT) * KS, n_envs);
+    if (R == 4)
+        launch_cluster(envconv_bwd_kernel<4>, grid, nt, smem, KS, st, d_out, dout_stride, Wo, Ho, inv_norm,
+                       norm_stride, Ws, Hs, d_base, base_stride, Wb, bw, bh, ggx, alpha, TJ, P, TAC, WWP);
+    else
+        launch_cluster(envconv_bwd_kernel<1>, grid, nt, smem, KS, st, d_out, dout_stride, Wo, Ho, inv_norm,
+                       norm_stride, Ws, Hs, d_base, base_stride, Wb, bw, bh, ggx, alpha, TJ, P, TAC, WWP);
+}
 
 void ss_launch_env_prefilter(const ss_env_desc* d, int n_envs, const float* env, float* irr, float* spec,
                              float* aux, cudaStream_t st) {
@@ -411,10 +682,7 @@ void ss_launch_env_prefilter(const ss_env_desc* d, int n_envs, const float* env,
     const int64_t irr_stride = ss_env_irr_floats(d), spec_stride = ss_env_spec_floats(d),
                   aux_stride = ss_env_aux_floats(d);
     const int Wi = d->irr_width, Hi = d->irr_height;
-    dim3 g(Wi * Hi, n_envs);
-    ss_note_launch();
-    prefilter_fwd_kernel<<<g, 256, table_smem(We, He), st>>>(env, env_stride, We, He, irr, irr_stride, Wi, Hi, aux,
-                                                            aux_stride, 0, 0.f);
+    launch_conv_fwd(env, env_stride, We, He, irr, irr_stride, Wi, Hi, aux, aux_stride, 0, 0.f, n_envs, st);
     ss_note_launch();
     copy_level0_kernel<<<dim3(256, n_envs), 256, 0, st>>>(env, env_stride, spec, spec_stride, env_stride);
     int64_t spec_off = env_stride, aux_off = (int64_t)Wi * Hi;
@@ -427,9 +695,8 @@ void ss_launch_env_prefilter(const ss_env_desc* d, int n_envs, const float* env,
         box_down_kernel<<<dim3((W * H + 255) / 256, n_envs), 256, 0, st>>>(env, env_stride, We, He, src, aux_stride,
                                                                            W, H);
         float r = (float)i / (float)(d->n_levels - 1);
-        ss_note_launch();
-        prefilter_fwd_kernel<<<dim3(W * H, n_envs), 256, table_smem(W, H), st>>>(
-            src, aux_stride, W, H, spec + spec_off, spec_stride, W, H, norm, aux_stride, 1, r * r);
+        launch_conv_fwd(src, aux_stride, W, H, spec + spec_off, spec_stride, W, H, norm, aux_stride, 1, r * r, n_envs,
+                        st);
         spec_off += (int64_t)W * H * 3;
         aux_off += (int64_t)W * H * 4;
     }
@@ -442,11 +709,9 @@ void ss_launch_env_prefilter_bwd(const ss_env_desc* d, int n_envs, const float* 
     const int64_t irr_stride = ss_env_irr_floats(d), spec_stride = ss_env_spec_floats(d),
                   aux_stride = ss_env_aux_floats(d);
     const int Wi = d->irr_width, Hi = d->irr_height;
-    if (d_irr) {
-        ss_note_launch();
-        prefilter_bwd_kernel<<<dim3(We * He, n_envs), 256, table_smem(Wi, Hi), st>>>(
-            d_irr, irr_stride, Wi, Hi, aux, aux_stride, We, He, d_env, env_stride, We, 1, 1, 0, 0.f);
-    }
+    if (d_irr)
+        launch_conv_bwd(d_irr, irr_stride, Wi, Hi, aux, aux_stride, We, He, d_env, env_stride, We, 1, 1, 0, 0.f, n_envs,
+                        st);
     if (!d_spec) return;
     ss_note_launch();
     add_level0_kernel<<<dim3(256, n_envs), 256, 0, st>>>(d_spec, spec_stride, d_env, env_stride, env_stride);
@@ -456,10 +721,8 @@ void ss_launch_env_prefilter_bwd(const ss_env_desc* d, int n_envs, const float* 
         ss_env_level_size(d, i, &W, &H);
         const float* norm = aux + aux_off;
         float r = (float)i / (float)(d->n_levels - 1);
-        ss_note_launch();
-        prefilter_bwd_kernel<<<dim3(W * H, n_envs), 256, table_smem(W, H), st>>>(
-            d_spec + spec_off, spec_stride, W, H, norm, aux_stride, W, H, d_env, env_stride, We, We / W, He / H, 1,
-            r * r);
+        launch_conv_bwd(d_spec + spec_off, spec_stride, W, H, norm, aux_stride, W, H, d_env, env_stride, We, We / W,
+                        He / H, 1, r * r, n_envs, st);
         spec_off += (int64_t)W * H * 3;
         aux_off += (int64_t)W * H * 4;
     }

@@ -24,22 +24,13 @@
 #define G_CH 9     // 12 channels: rgb, albedo 3, roughness, metallic, normal 3, depth
 #define G_N 21
 
-// Butterfly reduce-scatter over the warp: on entry every lane holds 32
-// values, on exit lane q holds the warp total of value q (31 shuffles instead
-// of 5 per value).
-__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const bool hi = (lane & o) != 0;
-#pragma unroll
-        for (int j = 0; j < o; ++j) {
-            const float send = hi ? v[j] : v[j + o];
-            const float keep = hi ? v[j + o] : v[j];
-            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-        }
-    }
-    return v[0];
-}
+// Per-warp gradient rows: the lanes with a fragment of the current surfel
+// write their 22 values to consecutive rows (rank among those lanes, so the
+// sum runs in lane order); lane q < 22 then sums column q.  The row stride of
+// 28 floats puts the 16-byte stores of 8 consecutive ranks in distinct bank
+// groups, and a column read touches 22 consecutive floats of one row.
+#define GROW 28
+#define GROWS 32
 
 // Per pixel, per composited layer k (front to back), from the upstream
 // gradient g and the layer totals (C_k, W_k) kept by the forward pass:
@@ -118,7 +109,9 @@ __global__ void __launch_bounds__(256) layer_coeff_kernel(ss_ws_view ws, ss_bwd_
 }
 
 __global__ void __launch_bounds__(256, 3) raster_bwd_kernel(ss_ws_view ws, ss_bwd_args a) {
-    __shared__ ss_wstage Wst[8];
+    extern __shared__ __align__(16) unsigned char bwd_smem[];
+    ss_wstage* Wst = reinterpret_cast<ss_wstage*>(bwd_smem);
+    float* Racc = reinterpret_cast<float*>(bwd_smem + 8 * sizeof(ss_wstage));
     const ss_layout* L = ws.layout;
     const int tile = blockIdx.x;
     const int view = find_view_tile(L, tile);
@@ -128,6 +121,7 @@ __global__ void __launch_bounds__(256, 3) raster_bwd_kernel(ss_ws_view ws, ss_bw
     const int x0 = tx * SS_TILE, y0 = ty * SS_TILE;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     ss_wstage& W = Wst[warp];
+    float* R = Racc + warp * (GROWS * GROW);
     const int wx0 = 8 * (warp & 1), wy0 = 4 * (warp >> 1);
     const int lx = wx0 + (lane & 7), ly = wy0 + (lane >> 3);
     const int px = x0 + lx, py = y0 + ly;
@@ -135,6 +129,7 @@ __global__ void __launch_bounds__(256, 3) raster_bwd_kernel(ss_ws_view ws, ss_bw
     const int gx0 = x0 + wx0, gx1 = gx0 + 7, gy0 = y0 + wy0, gy1 = gy0 + 3;
     const float xl = (float)lx + 0.5f, yl = (float)ly + 0.5f;
     const float rc2 = a.f.p.r_cut * a.f.p.r_cut;
+    const unsigned lanes_below = (1u << lane) - 1u;
     const int64_t P = L->total_pixels;
     const int64_t gpix = vl.pixel_off + (int64_t)(inside ? py : 0) * vl.width + (inside ? px : 0);
 
@@ -175,9 +170,7 @@ __global__ void __launch_bounds__(256, 3) raster_bwd_kernel(ss_ws_view ws, ss_bw
             const float dx = xl - h1.z, dy = yl - h1.w;
             const ss_hit h = ss_pixel_test(h0, h1, dx, dy, rc2);
             bool cov = h.cover && !done;
-            float gr[32];
-#pragma unroll
-            for (int q = 0; q < 32; ++q) gr[q] = 0.f;
+            float gr[24];
             bool contrib = false;
             if (cov) {
                 const float4 h2 = W.h2[s];
@@ -217,23 +210,37 @@ __global__ void __launch_bounds__(256, 3) raster_bwd_kernel(ss_ws_view ws, ss_bw
                         // w = n_f exp(-rho2 / 2), rho2 = q / s2^2 (Eq. mip_weight)
                         gr[G_NF] = dLdw * ex;
                         const float grho = -0.5f * w * dLdw;
-                        const float it = 1.f / h.t;
-                        const float gs0 = 2.f * grho * h.s0 * it, gs1 = 2.f * grho * h.s1 * it;
-                        const float gs2 = -2.f * grho * rho2 / h.s2;
+                        const float it2 = __fdividef(2.f * grho, h.t);
+                        const float gs0 = it2 * h.s0, gs1 = it2 * h.s1;
+                        const float gs2 = -2.f * grho * __fdividef(rho2, h.s2);
                         gr[G_P + 0] = gs0 * dx; gr[G_P + 1] = gs0 * dy;
                         gr[G_P + 2] = gs1 * dx; gr[G_P + 3] = gs1 * dy;
                         gr[G_A2] = gs2 * dx; gr[G_B2] = gs2 * dy;
                         gr[G_PX] = -(gs0 * h0.x + gs1 * h0.z + gs2 * h1.x);
                         gr[G_PY] = -(gs0 * h0.y + gs1 * h0.w + gs2 * h1.y);
+                        gr[G_N] = 0.f;
+                        gr[G_N + 1] = 0.f;
                         contrib = true;
                         ++n_frag;
                     }
                 }
             }
-            // warp reduction, then one add per value
-            if (__any_sync(0xffffffffu, contrib)) {
-                const float tot = warp_reduce_scatter32(gr, lane);
-                if (lane < G_N && tot != 0.f) atomicAdd(grad + (int64_t)W.id[s] * SS_NGRAD + lane, tot);
+            // sum over the warp's fragments of this surfel, then one add per value
+            const unsigned m = __ballot_sync(0xffffffffu, contrib);
+            if (m) {
+                if (contrib) {
+                    float4* row = reinterpret_cast<float4*>(R + __popc(m & lanes_below) * GROW);
+#pragma unroll
+                    for (int v = 0; v < 6; ++v) row[v] = make_float4(gr[4 * v], gr[4 * v + 1], gr[4 * v + 2], gr[4 * v + 3]);
+                }
+                __syncwarp();
+                if (lane < G_N) {
+                    const int nrow = __popc(m);
+                    float tot = R[lane];
+                    for (int j = 1; j < nrow; ++j) tot += R[j * GROW + lane];
+                    if (tot != 0.f) atomicAdd(grad + (int64_t)W.id[s] * SS_NGRAD + lane, tot);
+                }
+                __syncwarp();
             }
         }
         __syncwarp();
@@ -249,8 +256,14 @@ void ss_launch_raster_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd
     if (L.total_tiles <= 0) return;
     ss_note_launch();
     layer_coeff_kernel<<<(unsigned)((L.total_pixels + 255) / 256), 256, 0, st>>>(ws, a);
+    const int smem = 8 * (int)sizeof(ss_wstage) + 8 * GROWS * GROW * (int)sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(raster_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr = true;
+    }
     ss_note_launch();
-    raster_bwd_kernel<<<L.total_tiles, 256, 0, st>>>(ws, a);
+    raster_bwd_kernel<<<L.total_tiles, 256, smem, st>>>(ws, a);
 }
 
 // ------------------------------------------------------------------------
