@@ -172,7 +172,7 @@ static ss_status build_layout(const ss_batch_desc* b, const ss_render_params* p,
 }
 
 struct ws_plan {
-    size_t status, layout, vgeo, rec, tc, ts, tcur, keys, keys_alt, layer, pix, grad, total;
+    size_t status, layout, vgeo, rec, tc, ts, tcur, keys, keys_alt, layer, pix, grad, masks, total;
 };
 
 static ws_plan plan_ws(const ss_layout& L, const ss_render_params& p, int with_bwd) {
@@ -196,8 +196,9 @@ static ws_plan plan_ws(const ss_layout& L, const ss_render_params& p, int with_b
         w.layer = take(sizeof(float) * (size_t)p.k_max * 13 * (size_t)L.total_pixels);
         w.pix = take(sizeof(float) * 2 * (size_t)L.total_pixels);
         w.grad = take(sizeof(float) * SS_NGRAD * (size_t)L.total_records);
+        w.masks = take(sizeof(uint32_t) * 8 * (size_t)p.max_instances);
     } else {
-        w.layer = w.pix = w.grad = 0;
+        w.layer = w.pix = w.grad = w.masks = 0;
     }
     w.total = o;
     return w;
@@ -219,6 +220,7 @@ static ss_ws_view carve(void* ws, const ws_plan& w, const ss_render_params& p, i
     v.layer_state = with_bwd ? (float*)(b + w.layer) : nullptr;
     v.pix_state = with_bwd ? (float*)(b + w.pix) : nullptr;
     v.grad_rec = with_bwd ? (float*)(b + w.grad) : nullptr;
+    v.cover_masks = with_bwd ? (uint32_t*)(b + w.masks) : nullptr;
     v.max_instances = p.max_instances;
     return v;
 }

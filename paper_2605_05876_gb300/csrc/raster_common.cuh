@@ -21,9 +21,6 @@ struct ss_wstage {
     float4 c0[WSLOTS];  // rgb, flags                                     -- covering fragments
     float4 c1[WSLOTS];  // albedo, roughness
     float4 c2[WSLOTS];  // metallic, normal
-    float4 t1[WSLOTS];  // staging copies of record rows 1 and 2
-    float4 t2[WSLOTS];
-    uint2 rect[WSLOTS];
     uint32_t id[WSLOTS];
 };
 
@@ -59,9 +56,11 @@ __device__ __forceinline__ ss_chunk fetch_chunk(const unsigned long long* keys, 
 // Stage the instances of chunk c whose rectangle meets the warp's pixel block
 // [gx0, gx1] x [gy0, gy1]; returns how many were staged (slots 0 .. n-1, in
 // list order).  Centres are rewritten relative to the tile origin (tx0, ty0)
-// from their double-float value.
-__device__ __forceinline__ int stage_chunk(ss_wstage& W, const ss_chunk& c, const ss_rec* recs, int lane, int gx0,
-                                           int gx1, int gy0, int gy1, float tx0, float ty0) {
+// from their double-float value.  With RECT the support rectangles are
+// staged too (rect[], for the surfels whose n_f carries the rectangle flag).
+template <bool RECT>
+__device__ __forceinline__ int stage_chunk(ss_wstage& W, uint2* rect, const ss_chunk& c, const ss_rec* recs,
+                                           int lane, int gx0, int gx1, int gy0, int gy1, float tx0, float ty0) {
     bool ov = false;
     if (c.live) {
         uint32_t rx = __float_as_uint(c.r3.z), ry = __float_as_uint(c.r3.w);
@@ -73,24 +72,19 @@ __device__ __forceinline__ int stage_chunk(ss_wstage& W, const ss_chunk& c, cons
         const int pos = __popc(mask & ((1u << lane) - 1u));
         const ss_rec* rc = recs + c.id;
         cp_async16(&W.h0[pos], &rc->r0);
-        cp_async16(&W.t1[pos], &rc->r1);
-        cp_async16(&W.t2[pos], &rc->r2);
         cp_async16(&W.c0[pos], &rc->r4);
         cp_async16(&W.c1[pos], &rc->r5);
         cp_async16(&W.c2[pos], &rc->r6);
-        W.rect[pos] = make_uint2(__float_as_uint(c.r3.z), __float_as_uint(c.r3.w));
-        W.id[pos] = c.id;
-    }
-    cp_async_wait_all();
-    if (ov) {
-        const int pos = __popc(mask & ((1u << lane) - 1u));
-        const float4 r1 = W.t1[pos], r2 = W.t2[pos];
-        const uint32_t fl = __float_as_uint(W.c0[pos].w);
+        const float4 r1 = __ldg(&rc->r1), r2 = __ldg(&rc->r2);
+        const uint32_t fl = __float_as_uint(__ldg(&rc->r4.w));
         const float prx = __fadd_rn(__fsub_rn(r2.x, tx0), r2.z);
         const float pry = __fadd_rn(__fsub_rn(r2.y, ty0), r2.w);
         W.h1[pos] = make_float4(r1.x, r1.y, prx, pry);
         W.h2[pos] = make_float4(c.r3.x, c.r3.y, (fl & SS_FLAG_RECT_TEST) ? -r1.w : r1.w, 0.f);
+        if (RECT) rect[pos] = make_uint2(__float_as_uint(c.r3.z), __float_as_uint(c.r3.w));
+        W.id[pos] = c.id;
     }
+    cp_async_wait_all();
     __syncwarp();
     return __popc(mask);
 }

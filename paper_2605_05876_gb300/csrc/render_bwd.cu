@@ -1,8 +1,8 @@
 // Backward render (App. A "Backward Pass Implementation of Multi-Layer
 // Compositing"): the rasteriser replays each pixel's grouping front to back
 // against the per-layer totals (C_k, W_k) kept by the forward pass, turns the
-// upstream gradient into per-fragment gradients, reduces them over each warp
-// and adds one record of 21 floats per (surfel, view); a second kernel then
+// upstream gradient into per-fragment gradients, sums them per surfel and
+// adds one record of 21 floats per (surfel, view); a second kernel then
 // chains those records back through the projection and the shading to the
 // surfel parameters and the prefiltered environment texels.
 //
@@ -24,13 +24,23 @@
 #define G_CH 9     // 12 channels: rgb, albedo 3, roughness, metallic, normal 3, depth
 #define G_N 21
 
-// Per-warp gradient rows: the lanes with a fragment of the current surfel
-// write their 22 values to consecutive rows (rank among those lanes, so the
-// sum runs in lane order); lane q < 22 then sums column q.  The row stride of
-// 28 floats puts the 16-byte stores of 8 consecutive ranks in distinct bank
-// groups, and a column read touches 22 consecutive floats of one row.
-#define GROW 28
-#define GROWS 32
+// Backward rasteriser, per warp (8 x 4 pixels): the forward pass left one
+// coverage word per (warp, staged surfel); the replay of each pixel's
+// grouping only reads those words, and every fragment it accepts is
+// recorded (slot, pixel lane).  The recorded fragments are then
+// differentiated 32 at a time, one per lane: lane f writes its 22 values to
+// column f of a 22 x 32 table, and lane q sums row q over each run of
+// columns of the same surfel (records are in surfel order) before one
+// atomic add per value.
+#define GCOL 33     // table row stride (32 fragments + 1: conflict-free column writes)
+#define GT 13       // floats per pixel lane in the layer-coefficient table: G_k (12), S_k
+#define BW_CAP 128  // recorded fragments per warp before they are differentiated
+
+struct ss_bwarp {
+    float tab[G_N * GCOL];
+    float gtab[32 * GT];
+    uint32_t rec[BW_CAP];
+};
 
 // Per pixel, per composited layer k (front to back), from the upstream
 // gradient g and the layer totals (C_k, W_k) kept by the forward pass:
@@ -111,7 +121,7 @@ __global__ void __launch_bounds__(256) layer_coeff_kernel(ss_ws_view ws, ss_bwd_
 __global__ void __launch_bounds__(256, 3) raster_bwd_kernel(ss_ws_view ws, ss_bwd_args a) {
     extern __shared__ __align__(16) unsigned char bwd_smem[];
     ss_wstage* Wst = reinterpret_cast<ss_wstage*>(bwd_smem);
-    float* Racc = reinterpret_cast<float*>(bwd_smem + 8 * sizeof(ss_wstage));
+    ss_bwarp* Bws = reinterpret_cast<ss_bwarp*>(bwd_smem + 8 * sizeof(ss_wstage));
     const ss_layout* L = ws.layout;
     const int tile = blockIdx.x;
     const int view = find_view_tile(L, tile);
@@ -121,17 +131,16 @@ __global__ void __launch_bounds__(256, 3) raster_bwd_kernel(ss_ws_view ws, ss_bw
     const int x0 = tx * SS_TILE, y0 = ty * SS_TILE;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     ss_wstage& W = Wst[warp];
-    float* R = Racc + warp * (GROWS * GROW);
+    ss_bwarp& B = Bws[warp];
     const int wx0 = 8 * (warp & 1), wy0 = 4 * (warp >> 1);
     const int lx = wx0 + (lane & 7), ly = wy0 + (lane >> 3);
     const int px = x0 + lx, py = y0 + ly;
     const bool inside = px < vl.width && py < vl.height;
     const int gx0 = x0 + wx0, gx1 = gx0 + 7, gy0 = y0 + wy0, gy1 = gy0 + 3;
-    const float xl = (float)lx + 0.5f, yl = (float)ly + 0.5f;
     const float rc2 = a.f.p.r_cut * a.f.p.r_cut;
-    const unsigned lanes_below = (1u << lane) - 1u;
     const int64_t P = L->total_pixels;
     const int64_t gpix = vl.pixel_off + (int64_t)(inside ? py : 0) * vl.width + (inside ? px : 0);
+    const unsigned lanes_below = (1u << lane) - 1u;
 
     // per-pixel state: layer count from the forward pass; the per-layer
     // gradient coefficients (G_k, S_k) were written over the layer totals by
@@ -140,17 +149,19 @@ __global__ void __launch_bounds__(256, 3) raster_bwd_kernel(ss_ws_view ws, ss_bw
     bool done = !inside || K == 0;
     unsigned n_frag = 0;
 
-    // replay state (Algorithm 1) and the current layer's coefficients
+    // replay state (Algorithm 1): layer index, whether the open layer holds a
+    // fragment of positive weight (w = n_f exp(-rho^2/2) > 0 exactly when
+    // n_f > 0: exp(-rho^2/2) >= e^-4.5 on the support and n_f, when not 0,
+    // is far above the FP32 underflow range), its largest z_end
     int k = -1;
-    float Wr = 0.f, zmax = 0.f;
-    float G[SS_NCH];      // dL/dC_c for Shepard channels; for the normal channels dL/dC_n
-    float Sk = 0.f;       // sum_c G_c Chat_c - dL/dW (alpha path)
+    bool have_w = false, pend = false;
+    float zmax = 0.f;
+    int npend = 0;   // warp-uniform: fragments recorded, not yet differentiated
 
-    auto enter_layer = [&](int kk) {
+    auto enter_layer = [&](int kk) {   // this lane's layer coefficients -> B.gtab
         const float* ls = ws.layer_state + (int64_t)kk * 13 * P + gpix;
 #pragma unroll
-        for (int c = 0; c < SS_NCH; ++c) G[c] = ls[c * P];
-        Sk = ls[12 * P];
+        for (int c = 0; c < 13; ++c) B.gtab[lane * GT + c] = ls[c * P];
     };
 
     const int64_t cap = ws.max_instances;
@@ -159,90 +170,118 @@ __global__ void __launch_bounds__(256, 3) raster_bwd_kernel(ss_ws_view ws, ss_bw
     if (beg > end) beg = end;
     const ss_rec* recs = ws.rec + vl.rec_off;
     float* grad = ws.grad_rec + vl.rec_off * SS_NGRAD;
+    const uint32_t* masks = ws.cover_masks + 8 * beg + (int64_t)warp * (end - beg);
+
+    // Differentiate every recorded fragment, 32 at a time (one per lane), then
+    // sum the gradient rows of each run of equal surfels and add the sums.
+    auto run_batches = [&]() {
+        __syncwarp();   // records and layer tables written by other lanes
+        for (int b0 = 0; b0 < npend; b0 += 32) {
+            const int nb = min(32, npend - b0);
+            const bool valid = lane < nb;
+            const uint32_t rc = valid ? B.rec[b0 + lane] : 0u;
+            const int s = rc & 31, pl = (rc >> 5) & 31;
+            if (valid) {
+                const float4 h0 = W.h0[s], h1 = W.h1[s], h2 = W.h2[s];
+                const float dx = (float)(wx0 + (pl & 7)) + 0.5f - h1.z;
+                const float dy = (float)(wy0 + (pl >> 3)) + 0.5f - h1.w;
+                const ss_hit h = ss_pixel_test(h0, h1, dx, dy, rc2);
+                const float nf = fabsf(h2.z);
+                const float rho2 = __fdividef(h.q, h.t);
+                const float ex = __expf(-0.5f * rho2);
+                const float w = nf * ex;   // the forward kernel's weight, same operations
+                const float* gt = B.gtab + pl * GT;
+                const float4 c0v = W.c0[s], c1v = W.c1[s], c2v = W.c2[s];
+                const float ch[SS_NCH] = {c0v.x, c0v.y, c0v.z, c1v.x, c1v.y, c1v.z,
+                                          c1v.w, c2v.x, c2v.y, c2v.z, c2v.w, 0.5f * (h2.x + h2.y)};
+                float gr[G_N];
+                float dLdw = -gt[12];
+#pragma unroll
+                for (int c = 0; c < SS_NCH; ++c) {
+                    const float G = gt[c];
+                    dLdw = fmaf(G, ch[c], dLdw);
+                    gr[G_CH + c] = G * w;
+                }
+                // w = n_f exp(-rho2 / 2), rho2 = q / s2^2 (Eq. mip_weight)
+                gr[G_NF] = dLdw * ex;
+                const float grho = -0.5f * w * dLdw;
+                const float it2 = __fdividef(2.f * grho, h.t);
+                const float gs0 = it2 * h.s0, gs1 = it2 * h.s1;
+                const float gs2 = -2.f * grho * __fdividef(rho2, h.s2);
+                gr[G_P + 0] = gs0 * dx; gr[G_P + 1] = gs0 * dy;
+                gr[G_P + 2] = gs1 * dx; gr[G_P + 3] = gs1 * dy;
+                gr[G_A2] = gs2 * dx; gr[G_B2] = gs2 * dy;
+                gr[G_PX] = -(gs0 * h0.x + gs1 * h0.z + gs2 * h1.x);
+                gr[G_PY] = -(gs0 * h0.y + gs1 * h0.w + gs2 * h1.y);
+#pragma unroll
+                for (int q = 0; q < G_N; ++q) B.tab[q * GCOL + lane] = gr[q];
+            }
+            const int sprev = __shfl_up_sync(0xffffffffu, s, 1);
+            uint32_t runs = __ballot_sync(0xffffffffu, valid && (lane == 0 || sprev != s));
+            __syncwarp();
+            while (runs) {   // warp-uniform loop over the runs of equal slots
+                const int r0 = __ffs(runs) - 1;
+                runs &= runs - 1;
+                const int r1 = runs ? __ffs(runs) - 1 : nb;
+                const int sl = __shfl_sync(0xffffffffu, s, r0);
+                if (lane < G_N) {
+                    const float* t = B.tab + lane * GCOL;
+                    float tot = t[r0];
+                    for (int j = r0 + 1; j < r1; ++j) tot += t[j];
+                    if (tot != 0.f) atomicAdd(grad + (int64_t)W.id[sl] * SS_NGRAD + lane, tot);
+                }
+            }
+            __syncwarp();
+        }
+        npend = 0;
+        pend = false;
+    };
+
     ss_chunk nxt = fetch_chunk(ws.keys, recs, beg + lane, end);
     for (int64_t base = beg; base < end; base += 32) {
         if (__all_sync(0xffffffffu, done)) break;
         const ss_chunk cur = nxt;
-        const int n = stage_chunk(W, cur, recs, lane, gx0, gx1, gy0, gy1, (float)x0, (float)y0);
+        const int n = stage_chunk<false>(W, nullptr, cur, recs, lane, gx0, gx1, gy0, gy1, (float)x0, (float)y0);
         nxt = fetch_chunk(ws.keys, recs, base + 32 + lane, end);
-        for (int s = 0; s < n; ++s) {
-            const float4 h0 = W.h0[s], h1 = W.h1[s];
-            const float dx = xl - h1.z, dy = yl - h1.w;
-            const ss_hit h = ss_pixel_test(h0, h1, dx, dy, rc2);
-            bool cov = h.cover && !done;
-            float gr[24];
-            bool contrib = false;
-            if (cov) {
-                const float4 h2 = W.h2[s];
-                float nf = h2.z;
-                if (nf < 0.f) {   // support rectangle may clip this surfel
-                    const uint2 rr = W.rect[s];
-                    cov = in_rect(rr.x, rr.y, px, py);
-                    nf = -nf;
-                }
-                if (cov) {
-                    const float rho2 = __fdividef(h.q, h.t);
-                    const float ex = __expf(-0.5f * rho2);
-                    const float w = nf * ex;
-                    // replay of Algorithm 1: the forward kernel's condition, bit for bit
-                    if (k < 0) {
-                        k = 0;
-                        enter_layer(0);
-                    } else if (Wr > 0.f && h2.x > zmax) {
-                        ++k;
-                        Wr = 0.f;
-                        zmax = 0.f;
-                        if (k >= K) done = true;
-                        else enter_layer(k);
-                    }
-                    if (!done) {
-                        zmax = fmaxf(zmax, h2.y);
-                        Wr += w;
-                        const float4 c0v = W.c0[s], c1v = W.c1[s], c2v = W.c2[s];
-                        const float ch[SS_NCH] = {c0v.x, c0v.y, c0v.z, c1v.x, c1v.y, c1v.z,
-                                                  c1v.w, c2v.x, c2v.y, c2v.z, c2v.w, 0.5f * (h2.x + h2.y)};
-                        float dLdw = -Sk;
-#pragma unroll
-                        for (int c = 0; c < SS_NCH; ++c) {
-                            dLdw = fmaf(G[c], ch[c], dLdw);
-                            gr[G_CH + c] = G[c] * w;
-                        }
-                        // w = n_f exp(-rho2 / 2), rho2 = q / s2^2 (Eq. mip_weight)
-                        gr[G_NF] = dLdw * ex;
-                        const float grho = -0.5f * w * dLdw;
-                        const float it2 = __fdividef(2.f * grho, h.t);
-                        const float gs0 = it2 * h.s0, gs1 = it2 * h.s1;
-                        const float gs2 = -2.f * grho * __fdividef(rho2, h.s2);
-                        gr[G_P + 0] = gs0 * dx; gr[G_P + 1] = gs0 * dy;
-                        gr[G_P + 2] = gs1 * dx; gr[G_P + 3] = gs1 * dy;
-                        gr[G_A2] = gs2 * dx; gr[G_B2] = gs2 * dy;
-                        gr[G_PX] = -(gs0 * h0.x + gs1 * h0.z + gs2 * h1.x);
-                        gr[G_PY] = -(gs0 * h0.y + gs1 * h0.w + gs2 * h1.y);
-                        gr[G_N] = 0.f;
-                        gr[G_N + 1] = 0.f;
-                        contrib = true;
-                        ++n_frag;
-                    }
-                }
+        const uint32_t cm = lane < n ? masks[lane] : 0u;   // forward coverage of slot `lane`
+        masks += n;
+        uint32_t nz = __ballot_sync(0xffffffffu, cm != 0u);
+        while (nz) {
+            const int s = __ffs(nz) - 1;
+            nz &= nz - 1;
+            const uint32_t m = __shfl_sync(0xffffffffu, cm, s);
+            const bool my = ((m >> lane) & 1u) && !done;
+            const float4 h2 = W.h2[s];
+            // replay of Algorithm 1: the forward kernel's grouping decisions
+            const bool first = my && k < 0;
+            const bool adv = my && k >= 0 && have_w && h2.x > zmax;
+            if (__any_sync(0xffffffffu, adv && pend)) run_batches();   // pending fragments use the open layer
+            if (first) {
+                k = 0;
+                enter_layer(0);
+            } else if (adv) {
+                ++k;
+                have_w = false;
+                zmax = 0.f;
+                if (k >= K) done = true;
+                else enter_layer(k);
             }
-            // sum over the warp's fragments of this surfel, then one add per value
-            const unsigned m = __ballot_sync(0xffffffffu, contrib);
-            if (m) {
-                if (contrib) {
-                    float4* row = reinterpret_cast<float4*>(R + __popc(m & lanes_below) * GROW);
-#pragma unroll
-                    for (int v = 0; v < 6; ++v) row[v] = make_float4(gr[4 * v], gr[4 * v + 1], gr[4 * v + 2], gr[4 * v + 3]);
-                }
-                __syncwarp();
-                if (lane < G_N) {
-                    const int nrow = __popc(m);
-                    float tot = R[lane];
-                    for (int j = 1; j < nrow; ++j) tot += R[j * GROW + lane];
-                    if (tot != 0.f) atomicAdd(grad + (int64_t)W.id[s] * SS_NGRAD + lane, tot);
-                }
-                __syncwarp();
+            const bool app = my && !done;
+            if (app) {
+                zmax = fmaxf(zmax, h2.y);
+                have_w = have_w || h2.z != 0.f;
             }
+            const uint32_t am = __ballot_sync(0xffffffffu, app);
+            if (npend + __popc(am) > BW_CAP) run_batches();
+            if (app) {
+                B.rec[npend + __popc(am & lanes_below)] = (uint32_t)s | ((uint32_t)lane << 5);
+                pend = true;
+                ++n_frag;
+            }
+            npend += __popc(am);
+            __syncwarp();
         }
+        if (npend) run_batches();   // the next chunk rewrites the staged slots
         __syncwarp();
     }
     if (a.f.p.collect_stats) {
@@ -256,7 +295,7 @@ void ss_launch_raster_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd
     if (L.total_tiles <= 0) return;
     ss_note_launch();
     layer_coeff_kernel<<<(unsigned)((L.total_pixels + 255) / 256), 256, 0, st>>>(ws, a);
-    const int smem = 8 * (int)sizeof(ss_wstage) + 8 * GROWS * GROW * (int)sizeof(float);
+    const int smem = 8 * (int)(sizeof(ss_wstage) + sizeof(ss_bwarp));
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(raster_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

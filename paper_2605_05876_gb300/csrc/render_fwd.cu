@@ -430,6 +430,7 @@ void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_a
 template <bool STATS>
 __global__ void __launch_bounds__(256, 3) raster_fwd_kernel(ss_ws_view ws, ss_fwd_args a) {
     __shared__ ss_wstage Wst[8];
+    __shared__ uint2 Wrect[8][WSLOTS];
     const ss_layout* L = ws.layout;
     const int tile = blockIdx.x;
     const int view = find_view_tile(L, tile);
@@ -495,46 +496,50 @@ __global__ void __launch_bounds__(256, 3) raster_fwd_kernel(ss_ws_view ws, ss_fw
     if (end > cap) end = cap;
     if (beg > end) beg = end;
     const ss_rec* recs = ws.rec + vl.rec_off;
+    // coverage masks for the backward pass: one word per (warp, staged surfel)
+    // in staging order, in the warp's own region of 8 x the tile's list
+    uint32_t* masks = ws.cover_masks ? ws.cover_masks + 8 * beg + (int64_t)warp * (end - beg) : nullptr;
     ss_chunk nxt = fetch_chunk(ws.keys, recs, beg + lane, end);
     for (int64_t base = beg; base < end; base += 32) {
         if (__all_sync(0xffffffffu, done)) break;   // every pixel of the block has K_max layers
         const ss_chunk cur = nxt;
-        const int n = stage_chunk(W, cur, recs, lane, gx0, gx1, gy0, gy1, (float)x0, (float)y0);
+        const int n = stage_chunk<true>(W, Wrect[warp], cur, recs, lane, gx0, gx1, gy0, gy1, (float)x0, (float)y0);
         nxt = fetch_chunk(ws.keys, recs, base + 32 + lane, end);
+        uint32_t my_mask = 0;
         for (int s = 0; s < n; ++s) {
-            const float4 h0 = W.h0[s], h1 = W.h1[s];
+            const float4 h0 = W.h0[s], h1 = W.h1[s], h2 = W.h2[s];
             const ss_hit h = ss_pixel_test(h0, h1, xl - h1.z, yl - h1.w, rc2);
-            bool cov = h.cover && !done;
+            bool cg = h.cover && inside;   // geometric coverage (support and cutoff)
             if (STATS && inside) {
-                const uint2 rr = W.rect[s];
+                const uint2 rr = Wrect[warp][s];
                 ++n_lane;
                 n_rect += in_rect(rr.x, rr.y, px, py) ? 1u : 0u;
             }
-            if (cov) {
-                const float4 h2 = W.h2[s];
-                float nf = h2.z;
-                if (nf < 0.f) {   // support rectangle may clip this surfel
-                    const uint2 rr = W.rect[s];
-                    cov = in_rect(rr.x, rr.y, px, py);
-                    nf = -nf;
-                }
-                if (cov) {
-                    if (STATS) ++n_frag;
-                    const float w = nf * __expf(-0.5f * __fdividef(h.q, h.t));   // Eq. mip_weight
-                    if (Wg > 0.f && h2.x > zmax) flush();                          // gap: new layer
-                    if (!done) {
-                        zmax = fmaxf(zmax, h2.y);
-                        const float4 c0v = W.c0[s], c1v = W.c1[s], c2v = W.c2[s];
-                        C[0] = fmaf(w, c0v.x, C[0]); C[1] = fmaf(w, c0v.y, C[1]); C[2] = fmaf(w, c0v.z, C[2]);
-                        C[3] = fmaf(w, c1v.x, C[3]); C[4] = fmaf(w, c1v.y, C[4]); C[5] = fmaf(w, c1v.z, C[5]);
-                        C[6] = fmaf(w, c1v.w, C[6]); C[7] = fmaf(w, c2v.x, C[7]); C[8] = fmaf(w, c2v.y, C[8]);
-                        C[9] = fmaf(w, c2v.z, C[9]); C[10] = fmaf(w, c2v.w, C[10]);
-                        C[11] = fmaf(w, 0.5f * (h2.x + h2.y), C[11]);
-                        Wg += w;
-                    }
+            if (cg && h2.z < 0.f) {   // support rectangle may clip this surfel
+                const uint2 rr = Wrect[warp][s];
+                cg = in_rect(rr.x, rr.y, px, py);
+            }
+            const uint32_t cm = __ballot_sync(0xffffffffu, cg);
+            my_mask = lane == s ? cm : my_mask;
+            if (cg && !done) {
+                if (STATS) ++n_frag;
+                const float nf = fabsf(h2.z);
+                const float w = nf * __expf(-0.5f * __fdividef(h.q, h.t));   // Eq. mip_weight
+                if (Wg > 0.f && h2.x > zmax) flush();                          // gap: new layer
+                if (!done) {
+                    zmax = fmaxf(zmax, h2.y);
+                    const float4 c0v = W.c0[s], c1v = W.c1[s], c2v = W.c2[s];
+                    C[0] = fmaf(w, c0v.x, C[0]); C[1] = fmaf(w, c0v.y, C[1]); C[2] = fmaf(w, c0v.z, C[2]);
+                    C[3] = fmaf(w, c1v.x, C[3]); C[4] = fmaf(w, c1v.y, C[4]); C[5] = fmaf(w, c1v.z, C[5]);
+                    C[6] = fmaf(w, c1v.w, C[6]); C[7] = fmaf(w, c2v.x, C[7]); C[8] = fmaf(w, c2v.y, C[8]);
+                    C[9] = fmaf(w, c2v.z, C[9]); C[10] = fmaf(w, c2v.w, C[10]);
+                    C[11] = fmaf(w, 0.5f * (h2.x + h2.y), C[11]);
+                    Wg += w;
                 }
             }
         }
+        if (masks && lane < n) masks[lane] = my_mask;
+        if (masks) masks += n;
         __syncwarp();
     }
     if (!done && Wg > 0.f) flush();

@@ -86,6 +86,7 @@ struct ss_ws_view {
     float* layer_state;     // [k_max][13][total_pixels]  (raw C (12), W)
     float* pix_state;       // [2][total_pixels]  (K as float bits, T_end)
     float* grad_rec;        // [total_records][SS_NGRAD]
+    uint32_t* cover_masks;  // [8 * max_instances]: per (warp, staged surfel) pixel coverage, forward -> backward
     int64_t max_instances;
 };
 
