@@ -2,12 +2,13 @@
 // and backward rasterisers.
 //
 // Each warp owns an 8 x 4 pixel block of a 16 x 16 tile and walks the tile's
-// list on its own (no block-wide barrier): 32 keys at a time, it reads the
+// list on its own (no block-wide barrier), 32 keys at a time: it reads the
 // support rectangles, keeps the instances whose rectangle meets its block
-// (ballot + prefix count, so the order by z_start is kept) and copies only
-// those records into its own shared-memory slots with cp.async.  The next
-// chunk's keys and rectangles are loaded before the current chunk is
-// processed.
+// (ballot + prefix count, so the order by z_start is kept) and copies those
+// records into one of its two shared-memory staging buffers with cp.async.
+// The pipeline is two chunks deep: while the warp works on chunk c, the
+// records of chunk c+1 are in flight into the other buffer and the keys and
+// rectangles of chunk c+2 are being loaded.
 #pragma once
 
 #include "ss3d_internal.cuh"
@@ -15,12 +16,14 @@
 #define WSLOTS 32
 
 struct ss_wstage {
-    float4 h0[WSLOTS];  // P (screen quadratic-form factor)            -- every test
-    float4 h1[WSLOTS];  // A2, B2, centre x, y relative to the tile      -- every test
-    float4 h2[WSLOTS];  // z_start, z_end, +-n_f (negative: test the support rectangle), -
-    float4 c0[WSLOTS];  // rgb, flags                                     -- covering fragments
+    float4 h0[WSLOTS];  // P (screen quadratic-form factor)                  -- every test
+    float4 h1[WSLOTS];  // record row 1 on arrival; then A2, B2, centre x, y relative to the tile
+    float4 h2[WSLOTS];  // record row 2 on arrival; then z_start, z_end, +-n_f (negative: test the
+                        // support rectangle), -
+    float4 c0[WSLOTS];  // rgb, flags                                         -- covering fragments
     float4 c1[WSLOTS];  // albedo, roughness
     float4 c2[WSLOTS];  // metallic, normal
+    float2 zz[WSLOTS];  // z_start, z_end until the fix-up
     uint32_t id[WSLOTS];
 };
 
@@ -28,10 +31,8 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
 }
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\n" ::);
-    asm volatile("cp.async.wait_group 0;\n" ::);
-}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
 // One chunk of up to 32 instances: fetched (key, rectangle) of this lane.
 struct ss_chunk {
@@ -53,14 +54,13 @@ __device__ __forceinline__ ss_chunk fetch_chunk(const unsigned long long* keys, 
     return c;
 }
 
-// Stage the instances of chunk c whose rectangle meets the warp's pixel block
-// [gx0, gx1] x [gy0, gy1]; returns how many were staged (slots 0 .. n-1, in
-// list order).  Centres are rewritten relative to the tile origin (tx0, ty0)
-// from their double-float value.  With RECT the support rectangles are
-// staged too (rect[], for the surfels whose n_f carries the rectangle flag).
+// Issue the copies of the instances of chunk c whose rectangle meets the
+// warp's pixel block [gx0, gx1] x [gy0, gy1] into slots 0 .. n-1 of W (list
+// order kept); returns n.  With RECT the support rectangles are staged too
+// (rect[], for the surfels whose n_f carries the rectangle flag).
 template <bool RECT>
-__device__ __forceinline__ int stage_chunk(ss_wstage& W, uint2* rect, const ss_chunk& c, const ss_rec* recs,
-                                           int lane, int gx0, int gx1, int gy0, int gy1, float tx0, float ty0) {
+__device__ __forceinline__ int stage_issue(ss_wstage& W, uint2* rect, const ss_chunk& c, const ss_rec* recs,
+                                           int lane, int gx0, int gx1, int gy0, int gy1) {
     bool ov = false;
     if (c.live) {
         uint32_t rx = __float_as_uint(c.r3.z), ry = __float_as_uint(c.r3.w);
@@ -72,21 +72,49 @@ __device__ __forceinline__ int stage_chunk(ss_wstage& W, uint2* rect, const ss_c
         const int pos = __popc(mask & ((1u << lane) - 1u));
         const ss_rec* rc = recs + c.id;
         cp_async16(&W.h0[pos], &rc->r0);
+        cp_async16(&W.h1[pos], &rc->r1);
+        cp_async16(&W.h2[pos], &rc->r2);
         cp_async16(&W.c0[pos], &rc->r4);
         cp_async16(&W.c1[pos], &rc->r5);
         cp_async16(&W.c2[pos], &rc->r6);
-        const float4 r1 = __ldg(&rc->r1), r2 = __ldg(&rc->r2);
-        const uint32_t fl = __float_as_uint(__ldg(&rc->r4.w));
-        const float prx = __fadd_rn(__fsub_rn(r2.x, tx0), r2.z);
-        const float pry = __fadd_rn(__fsub_rn(r2.y, ty0), r2.w);
-        W.h1[pos] = make_float4(r1.x, r1.y, prx, pry);
-        W.h2[pos] = make_float4(c.r3.x, c.r3.y, (fl & SS_FLAG_RECT_TEST) ? -r1.w : r1.w, 0.f);
+        W.zz[pos] = make_float2(c.r3.x, c.r3.y);
         if (RECT) rect[pos] = make_uint2(__float_as_uint(c.r3.z), __float_as_uint(c.r3.w));
         W.id[pos] = c.id;
     }
-    cp_async_wait_all();
-    __syncwarp();
+    cp_async_commit();
     return __popc(mask);
+}
+
+// Ask L2 for the records of the instances of chunk c that stage_issue will
+// copy (same overlap test), so that their copies wait less.
+__device__ __forceinline__ void stage_prefetch(const ss_chunk& c, const ss_rec* recs, int gx0, int gx1, int gy0,
+                                               int gy1) {
+    if (!c.live) return;
+    uint32_t rx = __float_as_uint(c.r3.z), ry = __float_as_uint(c.r3.w);
+    int i0 = rx & 0xffff, i1 = rx >> 16, j0 = ry & 0xffff, j1 = ry >> 16;
+    if (i0 <= gx1 && i1 >= gx0 && j0 <= gy1 && j1 >= gy0) {
+        const char* p = reinterpret_cast<const char*>(recs + c.id);
+        asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p));
+        asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p + sizeof(ss_rec) - 1));
+    }
+}
+
+// Wait for the copies of the n staged slots of W and rewrite them in place:
+// the centre relative to the tile origin (tx0, ty0) from its double-float
+// value, and (z_start, z_end, +-n_f).
+__device__ __forceinline__ void stage_finish(ss_wstage& W, int n, int lane, float tx0, float ty0) {
+    cp_async_wait0();
+    __syncwarp();
+    if (lane < n) {
+        const float4 r1 = W.h1[lane], r2 = W.h2[lane];
+        const uint32_t fl = __float_as_uint(W.c0[lane].w);
+        const float2 z = W.zz[lane];
+        const float prx = __fadd_rn(__fsub_rn(r2.x, tx0), r2.z);
+        const float pry = __fadd_rn(__fsub_rn(r2.y, ty0), r2.w);
+        W.h1[lane] = make_float4(r1.x, r1.y, prx, pry);
+        W.h2[lane] = make_float4(z.x, z.y, (fl & SS_FLAG_RECT_TEST) ? -r1.w : r1.w, 0.f);
+    }
+    __syncwarp();
 }
 
 __device__ __forceinline__ bool in_rect(uint32_t rx, uint32_t ry, int px, int py) {

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256, 3) raster_bwd_kernel(ss_ws_view ws, ss_bw
     const int tx = lt % vl.tiles_x, ty = lt / vl.tiles_x;
     const int x0 = tx * SS_TILE, y0 = ty * SS_TILE;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    ss_wstage& W = Wst[warp];
+    ss_wstage* Wc = Wst + warp;       // staging buffer
     ss_bwarp& B = Bws[warp];
     const int wx0 = 8 * (warp & 1), wy0 = 4 * (warp >> 1);
     const int lx = wx0 + (lane & 7), ly = wy0 + (lane >> 3);
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(256, 3) raster_bwd_kernel(ss_ws_view ws, ss_bw
             const uint32_t rc = valid ? B.rec[b0 + lane] : 0u;
             const int s = rc & 31, pl = (rc >> 5) & 31;
             if (valid) {
-                const float4 h0 = W.h0[s], h1 = W.h1[s], h2 = W.h2[s];
+                const float4 h0 = Wc->h0[s], h1 = Wc->h1[s], h2 = Wc->h2[s];
                 const float dx = (float)(wx0 + (pl & 7)) + 0.5f - h1.z;
                 const float dy = (float)(wy0 + (pl >> 3)) + 0.5f - h1.w;
                 const ss_hit h = ss_pixel_test(h0, h1, dx, dy, rc2);
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(256, 3) raster_bwd_kernel(ss_ws_view ws, ss_bw
                 const float ex = __expf(-0.5f * rho2);
                 const float w = nf * ex;   // the forward kernel's weight, same operations
                 const float* gt = B.gtab + pl * GT;
-                const float4 c0v = W.c0[s], c1v = W.c1[s], c2v = W.c2[s];
+                const float4 c0v = Wc->c0[s], c1v = Wc->c1[s], c2v = Wc->c2[s];
                 const float ch[SS_NCH] = {c0v.x, c0v.y, c0v.z, c1v.x, c1v.y, c1v.z,
                                           c1v.w, c2v.x, c2v.y, c2v.z, c2v.w, 0.5f * (h2.x + h2.y)};
                 float gr[G_N];
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(256, 3) raster_bwd_kernel(ss_ws_view ws, ss_bw
                     const float* t = B.tab + lane * GCOL;
                     float tot = t[r0];
                     for (int j = r0 + 1; j < r1; ++j) tot += t[j];
-                    if (tot != 0.f) atomicAdd(grad + (int64_t)W.id[sl] * SS_NGRAD + lane, tot);
+                    if (tot != 0.f) atomicAdd(grad + (int64_t)Wc->id[sl] * SS_NGRAD + lane, tot);
                 }
             }
             __syncwarp();
@@ -237,21 +237,24 @@ __global__ void __launch_bounds__(256, 3) raster_bwd_kernel(ss_ws_view ws, ss_bw
         pend = false;
     };
 
+    // one staging buffer (shared memory for three CTAs per SM); the records
+    // of the next chunk are prefetched into L2 instead
     ss_chunk nxt = fetch_chunk(ws.keys, recs, beg + lane, end);
     for (int64_t base = beg; base < end; base += 32) {
         if (__all_sync(0xffffffffu, done)) break;
-        const ss_chunk cur = nxt;
-        const int n = stage_chunk<false>(W, nullptr, cur, recs, lane, gx0, gx1, gy0, gy1, (float)x0, (float)y0);
-        nxt = fetch_chunk(ws.keys, recs, base + 32 + lane, end);
+        const int n = stage_issue<false>(*Wc, nullptr, nxt, recs, lane, gx0, gx1, gy0, gy1);
         const uint32_t cm = lane < n ? masks[lane] : 0u;   // forward coverage of slot `lane`
         masks += n;
+        nxt = fetch_chunk(ws.keys, recs, base + 32 + lane, end);
+        stage_prefetch(nxt, recs, gx0, gx1, gy0, gy1);
+        stage_finish(*Wc, n, lane, (float)x0, (float)y0);
         uint32_t nz = __ballot_sync(0xffffffffu, cm != 0u);
         while (nz) {
             const int s = __ffs(nz) - 1;
             nz &= nz - 1;
             const uint32_t m = __shfl_sync(0xffffffffu, cm, s);
             const bool my = ((m >> lane) & 1u) && !done;
-            const float4 h2 = W.h2[s];
+            const float4 h2 = Wc->h2[s];
             // replay of Algorithm 1: the forward kernel's grouping decisions
             const bool first = my && k < 0;
             const bool adv = my && k >= 0 && have_w && h2.x > zmax;

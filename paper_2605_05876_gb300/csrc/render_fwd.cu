@@ -429,8 +429,9 @@ void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_a
 
 template <bool STATS>
 __global__ void __launch_bounds__(256, 3) raster_fwd_kernel(ss_ws_view ws, ss_fwd_args a) {
-    __shared__ ss_wstage Wst[8];
-    __shared__ uint2 Wrect[8][WSLOTS];
+    extern __shared__ __align__(16) unsigned char fwd_smem[];
+    ss_wstage* Wst = reinterpret_cast<ss_wstage*>(fwd_smem);                          // [8 warps][2]
+    uint2* Wrect = reinterpret_cast<uint2*>(fwd_smem + 16 * sizeof(ss_wstage));        // [8][2][WSLOTS]
     const ss_layout* L = ws.layout;
     const int tile = blockIdx.x;
     const int view = find_view_tile(L, tile);
@@ -439,7 +440,6 @@ __global__ void __launch_bounds__(256, 3) raster_fwd_kernel(ss_ws_view ws, ss_fw
     const int tx = lt % vl.tiles_x, ty = lt / vl.tiles_x;
     const int x0 = tx * SS_TILE, y0 = ty * SS_TILE;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    ss_wstage& W = Wst[warp];
     const int wx0 = 8 * (warp & 1), wy0 = 4 * (warp >> 1);         // 8 x 4 pixel block per warp
     const int lx = wx0 + (lane & 7), ly = wy0 + (lane >> 3);
     const int px = x0 + lx, py = y0 + ly;
@@ -499,24 +499,33 @@ __global__ void __launch_bounds__(256, 3) raster_fwd_kernel(ss_ws_view ws, ss_fw
     // coverage masks for the backward pass: one word per (warp, staged surfel)
     // in staging order, in the warp's own region of 8 x the tile's list
     uint32_t* masks = ws.cover_masks ? ws.cover_masks + 8 * beg + (int64_t)warp * (end - beg) : nullptr;
-    ss_chunk nxt = fetch_chunk(ws.keys, recs, beg + lane, end);
+    ss_wstage* Wb = Wst + 2 * warp;
+    uint2* Rb = Wrect + 2 * warp * WSLOTS;
+    int buf = 0, n_next = 0;
+    if (beg < end)
+        n_next = stage_issue<true>(Wb[0], Rb, fetch_chunk(ws.keys, recs, beg + lane, end), recs, lane, gx0, gx1,
+                                   gy0, gy1);
+    ss_chunk nxt = fetch_chunk(ws.keys, recs, beg + 32 + lane, end);
     for (int64_t base = beg; base < end; base += 32) {
         if (__all_sync(0xffffffffu, done)) break;   // every pixel of the block has K_max layers
-        const ss_chunk cur = nxt;
-        const int n = stage_chunk<true>(W, Wrect[warp], cur, recs, lane, gx0, gx1, gy0, gy1, (float)x0, (float)y0);
-        nxt = fetch_chunk(ws.keys, recs, base + 32 + lane, end);
+        ss_wstage& W = Wb[buf];
+        const uint2* R = Rb + buf * WSLOTS;
+        const int n = n_next;
+        stage_finish(W, n, lane, (float)x0, (float)y0);
+        n_next = stage_issue<true>(Wb[buf ^ 1], Rb + (buf ^ 1) * WSLOTS, nxt, recs, lane, gx0, gx1, gy0, gy1);
+        nxt = fetch_chunk(ws.keys, recs, base + 64 + lane, end);
         uint32_t my_mask = 0;
         for (int s = 0; s < n; ++s) {
             const float4 h0 = W.h0[s], h1 = W.h1[s], h2 = W.h2[s];
             const ss_hit h = ss_pixel_test(h0, h1, xl - h1.z, yl - h1.w, rc2);
             bool cg = h.cover && inside;   // geometric coverage (support and cutoff)
             if (STATS && inside) {
-                const uint2 rr = Wrect[warp][s];
+                const uint2 rr = R[s];
                 ++n_lane;
                 n_rect += in_rect(rr.x, rr.y, px, py) ? 1u : 0u;
             }
             if (cg && h2.z < 0.f) {   // support rectangle may clip this surfel
-                const uint2 rr = Wrect[warp][s];
+                const uint2 rr = R[s];
                 cg = in_rect(rr.x, rr.y, px, py);
             }
             const uint32_t cm = __ballot_sync(0xffffffffu, cg);
@@ -540,8 +549,10 @@ __global__ void __launch_bounds__(256, 3) raster_fwd_kernel(ss_ws_view ws, ss_fw
         }
         if (masks && lane < n) masks[lane] = my_mask;
         if (masks) masks += n;
+        buf ^= 1;
         __syncwarp();
     }
+    cp_async_wait0();   // copies of a chunk an early exit left unread
     if (!done && Wg > 0.f) flush();
     if (STATS) {
         unsigned long long v[4] = {n_rect, n_lane, n_frag, (unsigned)K * (inside ? 1u : 0u)};
@@ -571,6 +582,13 @@ __global__ void __launch_bounds__(256, 3) raster_fwd_kernel(ss_ws_view ws, ss_fw
 void ss_launch_raster_fwd(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st) {
     if (L.total_tiles <= 0) return;
     ss_note_launch();
-    if (a.p.collect_stats) raster_fwd_kernel<true><<<L.total_tiles, 256, 0, st>>>(ws, a);
-    else raster_fwd_kernel<false><<<L.total_tiles, 256, 0, st>>>(ws, a);
+    const int smem = 16 * (int)sizeof(ss_wstage) + 16 * WSLOTS * (int)sizeof(uint2);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(raster_fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(raster_fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr = true;
+    }
+    if (a.p.collect_stats) raster_fwd_kernel<true><<<L.total_tiles, 256, smem, st>>>(ws, a);
+    else raster_fwd_kernel<false><<<L.total_tiles, 256, smem, st>>>(ws, a);
 }
