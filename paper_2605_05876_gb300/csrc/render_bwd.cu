@@ -29,10 +29,10 @@
 // grouping only reads those words, and every fragment it accepts is
 // recorded (slot, pixel lane).  The recorded fragments are then
 // differentiated 32 at a time, one per lane: lane f writes its 22 values to
-// column f of a 22 x 32 table, and lane q sums row q over each run of
-// columns of the same surfel (records are in surfel order) before one
-// atomic add per value.
-#define GCOL 33     // table row stride (32 fragments + 1: conflict-free column writes)
+// column f of a 22 x 32 table; lane q loads row q into registers and sums it
+// over each run of columns of the same surfel (records are in surfel order),
+// with one atomic add per value and run.
+#define GCOL 36     // table row stride: 16-byte aligned rows, conflict-free column writes
 #define GT 13       // floats per pixel lane in the layer-coefficient table: G_k (12), S_k
 #define BW_CAP 128  // recorded fragments per warp before they are differentiated
 
@@ -118,20 +118,21 @@ __global__ void __launch_bounds__(256) layer_coeff_kernel(ss_ws_view ws, ss_bwd_
     }
 }
 
-__global__ void __launch_bounds__(256, 3) raster_bwd_kernel(ss_ws_view ws, ss_bwd_args a) {
+__global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kernel(ss_ws_view ws, ss_bwd_args a) {
     extern __shared__ __align__(16) unsigned char bwd_smem[];
     ss_wstage* Wst = reinterpret_cast<ss_wstage*>(bwd_smem);
-    ss_bwarp* Bws = reinterpret_cast<ss_bwarp*>(bwd_smem + 8 * sizeof(ss_wstage));
+    ss_bwarp* Bws = reinterpret_cast<ss_bwarp*>(bwd_smem + RWPB_BWD * sizeof(ss_wstage));
     const ss_layout* L = ws.layout;
-    const int tile = blockIdx.x;
+    const int lw = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * RWPB_BWD + lw;        // 8 warps per tile
+    const int tile = gw >> 3, warp = gw & 7;
     const int view = find_view_tile(L, tile);
     const ss_view_layout& vl = L->v[view];
     const int lt = tile - vl.tile_off;
     const int tx = lt % vl.tiles_x, ty = lt / vl.tiles_x;
     const int x0 = tx * SS_TILE, y0 = ty * SS_TILE;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    ss_wstage* Wc = Wst + warp;       // staging buffer
-    ss_bwarp& B = Bws[warp];
+    ss_wstage* Wc = Wst + lw;         // staging buffer
+    ss_bwarp& B = Bws[lw];
     const int wx0 = 8 * (warp & 1), wy0 = 4 * (warp >> 1);
     const int lx = wx0 + (lane & 7), ly = wy0 + (lane >> 3);
     const int px = x0 + lx, py = y0 + ly;
@@ -216,19 +217,27 @@ __global__ void __launch_bounds__(256, 3) raster_bwd_kernel(ss_ws_view ws, ss_bw
 #pragma unroll
                 for (int q = 0; q < G_N; ++q) B.tab[q * GCOL + lane] = gr[q];
             }
-            const int sprev = __shfl_up_sync(0xffffffffu, s, 1);
-            uint32_t runs = __ballot_sync(0xffffffffu, valid && (lane == 0 || sprev != s));
+            const int snext = __shfl_down_sync(0xffffffffu, s, 1);
+            // run ends: the last valid column and every column followed by another surfel
+            const uint32_t ends = __ballot_sync(0xffffffffu, valid && (lane == nb - 1 || snext != s));
             __syncwarp();
-            while (runs) {   // warp-uniform loop over the runs of equal slots
-                const int r0 = __ffs(runs) - 1;
-                runs &= runs - 1;
-                const int r1 = runs ? __ffs(runs) - 1 : nb;
-                const int sl = __shfl_sync(0xffffffffu, s, r0);
-                if (lane < G_N) {
-                    const float* t = B.tab + lane * GCOL;
-                    float tot = t[r0];
-                    for (int j = r0 + 1; j < r1; ++j) tot += t[j];
-                    if (tot != 0.f) atomicAdd(grad + (int64_t)Wc->id[sl] * SS_NGRAD + lane, tot);
+            float v[32];
+            {
+                const float4* t4 = reinterpret_cast<const float4*>(B.tab + (lane < G_N ? lane : 0) * GCOL);
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    const float4 x = t4[m];
+                    v[4 * m] = x.x; v[4 * m + 1] = x.y; v[4 * m + 2] = x.z; v[4 * m + 3] = x.w;
+                }
+            }
+            float tot = 0.f;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                tot += v[j];
+                if ((ends >> j) & 1u) {   // warp-uniform
+                    const int sl = __shfl_sync(0xffffffffu, s, j);
+                    if (lane < G_N && tot != 0.f) atomicAdd(grad + (int64_t)Wc->id[sl] * SS_NGRAD + lane, tot);
+                    tot = 0.f;
                 }
             }
             __syncwarp();
@@ -298,14 +307,14 @@ void ss_launch_raster_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd
     if (L.total_tiles <= 0) return;
     ss_note_launch();
     layer_coeff_kernel<<<(unsigned)((L.total_pixels + 255) / 256), 256, 0, st>>>(ws, a);
-    const int smem = 8 * (int)(sizeof(ss_wstage) + sizeof(ss_bwarp));
+    const int smem = RWPB_BWD * (int)(sizeof(ss_wstage) + sizeof(ss_bwarp));
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(raster_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = true;
     }
     ss_note_launch();
-    raster_bwd_kernel<<<L.total_tiles, 256, smem, st>>>(ws, a);
+    raster_bwd_kernel<<<(unsigned)(L.total_tiles * 8 / RWPB_BWD), 32 * RWPB_BWD, smem, st>>>(ws, a);
 }
 
 // ------------------------------------------------------------------------

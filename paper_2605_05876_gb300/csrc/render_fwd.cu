@@ -428,18 +428,19 @@ void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_a
 // reached K_max layers stops reading the list.
 
 template <bool STATS>
-__global__ void __launch_bounds__(256, 3) raster_fwd_kernel(ss_ws_view ws, ss_fwd_args a) {
+__global__ void __launch_bounds__(32 * RWPB_FWD, 24 / RWPB_FWD) raster_fwd_kernel(ss_ws_view ws, ss_fwd_args a) {
     extern __shared__ __align__(16) unsigned char fwd_smem[];
-    ss_wstage* Wst = reinterpret_cast<ss_wstage*>(fwd_smem);                          // [8 warps][2]
-    uint2* Wrect = reinterpret_cast<uint2*>(fwd_smem + 16 * sizeof(ss_wstage));        // [8][2][WSLOTS]
+    ss_wstage* Wst = reinterpret_cast<ss_wstage*>(fwd_smem);                          // [RWPB_FWD warps][2]
+    uint2* Wrect = reinterpret_cast<uint2*>(fwd_smem + 2 * RWPB_FWD * sizeof(ss_wstage));  // [RWPB_FWD][2][WSLOTS]
     const ss_layout* L = ws.layout;
-    const int tile = blockIdx.x;
+    const int lw = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * RWPB_FWD + lw;        // 8 warps per tile
+    const int tile = gw >> 3, warp = gw & 7;
     const int view = find_view_tile(L, tile);
     const ss_view_layout& vl = L->v[view];
     const int lt = tile - vl.tile_off;
     const int tx = lt % vl.tiles_x, ty = lt / vl.tiles_x;
     const int x0 = tx * SS_TILE, y0 = ty * SS_TILE;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wx0 = 8 * (warp & 1), wy0 = 4 * (warp >> 1);         // 8 x 4 pixel block per warp
     const int lx = wx0 + (lane & 7), ly = wy0 + (lane >> 3);
     const int px = x0 + lx, py = y0 + ly;
@@ -499,8 +500,8 @@ __global__ void __launch_bounds__(256, 3) raster_fwd_kernel(ss_ws_view ws, ss_fw
     // coverage masks for the backward pass: one word per (warp, staged surfel)
     // in staging order, in the warp's own region of 8 x the tile's list
     uint32_t* masks = ws.cover_masks ? ws.cover_masks + 8 * beg + (int64_t)warp * (end - beg) : nullptr;
-    ss_wstage* Wb = Wst + 2 * warp;
-    uint2* Rb = Wrect + 2 * warp * WSLOTS;
+    ss_wstage* Wb = Wst + 2 * lw;
+    uint2* Rb = Wrect + 2 * lw * WSLOTS;
     int buf = 0, n_next = 0;
     if (beg < end)
         n_next = stage_issue<true>(Wb[0], Rb, fetch_chunk(ws.keys, recs, beg + lane, end), recs, lane, gx0, gx1,
@@ -582,13 +583,14 @@ __global__ void __launch_bounds__(256, 3) raster_fwd_kernel(ss_ws_view ws, ss_fw
 void ss_launch_raster_fwd(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st) {
     if (L.total_tiles <= 0) return;
     ss_note_launch();
-    const int smem = 16 * (int)sizeof(ss_wstage) + 16 * WSLOTS * (int)sizeof(uint2);
+    const int smem = 2 * RWPB_FWD * ((int)sizeof(ss_wstage) + WSLOTS * (int)sizeof(uint2));
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(raster_fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         cudaFuncSetAttribute(raster_fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = true;
     }
-    if (a.p.collect_stats) raster_fwd_kernel<true><<<L.total_tiles, 256, smem, st>>>(ws, a);
-    else raster_fwd_kernel<false><<<L.total_tiles, 256, smem, st>>>(ws, a);
+    const unsigned grid = (unsigned)(L.total_tiles * 8 / RWPB_FWD);
+    if (a.p.collect_stats) raster_fwd_kernel<true><<<grid, 32 * RWPB_FWD, smem, st>>>(ws, a);
+    else raster_fwd_kernel<false><<<grid, 32 * RWPB_FWD, smem, st>>>(ws, a);
 }
