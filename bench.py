@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "fwd+bwd views/s at 1M surfels 16x800² (batched vs per-view); % HBM roofline"
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-# algorithmic FP32 work per unit:
+# algorithmic FP32 work per unit (counted from the kernels' arithmetic):
 FLOP_TEST = 17        # one (pixel, surfel) test inside the support rectangle
 FLOP_FRAG_FWD = 30    # one covering fragment: weight + 12-channel accumulation
 FLOP_FRAG_BWD = 66    # one covering fragment in the backward pass
@@ -291,6 +291,27 @@ def run_ours(args):
     ms_per_step = ms / args.steps
     value = world * V * args.steps / (ms / 1000.0)
 
+    # --- the same step replayed from a CUDA graph (no host work per step)
+    graph = None
+    try:
+        cg = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            step()
+        torch.cuda.current_stream().wait_stream(side)
+        with torch.cuda.graph(cg):
+            step()
+        for _ in range(max(args.warmup, 1)):
+            cg.replay()
+        ms_g = timed(cg.replay, args.steps)
+        graph = {"value": world * V * args.steps / (ms_g / 1000.0), "unit": "views/s",
+                 "ms_per_step": ms_g / args.steps}
+        del cg
+    except RuntimeError as e:   # capture refused: report it, keep the eager number
+        graph = {"error": str(e)[:300]}
+    torch.cuda.synchronize()
+
     # --- work counters (one extra, untimed, step)
     r.prm.collect_stats = 1
     step()
@@ -346,7 +367,7 @@ def run_ours(args):
         e2e = {"value": world * V * args.steps / (ms_e2e / 1000.0), "unit": "views/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
-    # --- roofline of the dominant kernel (FP32-issue bound)
+    # --- roofline of the dominant kernel (FP32-issue bound: no memory or tensor-core limit applies)
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12     # TFLOP/s
@@ -380,10 +401,134 @@ def run_ours(args):
                                        f"{V} views 800x800, env 512x256, batched in one launch per stage",
                            "inputs_vs_l2": "inputs and intermediates > 129 MB L2 (no flush)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
-                "per_view": per_view, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+                "per_view": per_view, "graph": graph, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
+                "clocks": clocks,
                 "gpu_launches": None, "stages": stage_share, "work": counts, "hbm_peak_gbs": hbm,
                 "device_status": status}
         line["gpu_launches"] = n_launched   # counted by the library over the timed steps
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# the inverse-rendering step loop (3M surfels, 8 of 64 targets of 1024^2 per
+# iteration, L1 loss, fused Adam on all surfel parameters and the env map)
+
+LOOP_METRIC = "inverse-rendering iterations/s at 3M surfels, 8 of 64 views of 1024² per iteration (fwd+L1+bwd+Adam)"
+LOOP_LR = {"pos": 1.6e-4, "quat": 1e-3, "log_scale": 5e-3, "albedo": 2.5e-3, "roughness": 2.5e-3,
+           "metallic": 2.5e-3, "env": 1e-2}
+
+
+def run_loop(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_2605_05876_gb300 import build, scenes
+    if rank == 0 or world == 1:
+        build()
+    if world > 1:
+        dist.barrier()
+    from paper_2605_05876_gb300 import _lib as C
+    from paper_2605_05876_gb300.api import Adam, Renderer, SURFEL_ACTIVATIONS, launch_count, loss_l1, make_cameras
+
+    B = 8
+    gt = scenes.config5_gt()
+    T = len(gt.cameras)
+    # targets: the ground truth rendered by the same renderer, 8 views at a time
+    rg = Renderer(scenes.Scene(gt.surfels, gt.scene_offsets, gt.envs, gt.cameras[:B], "gt"), with_backward=False)
+    HW = rg.n_pixels // B
+    targets = torch.empty(T, HW, 4, device=dev)
+    for b0 in range(0, T, B):
+        rg.set_cameras(gt.cameras[b0:b0 + B])
+        rg.forward()
+        targets[b0:b0 + B] = rg.rgba.view(B, HW, 4)
+    torch.cuda.synchronize()
+    del rg
+    torch.cuda.empty_cache()
+
+    surf, env0 = scenes.config5_init()
+    r = Renderer(scenes.Scene(surf, np.array([0, surf.n], np.int64), [env0], gt.cameras[:B], "loop"),
+                 capacity_slack=2.0)
+    r.zero_grads()
+    # raw parameters: sigmoid groups keep logits, the others are the renderer's own arrays
+    groups = {}
+    for k, act in SURFEL_ACTIVATIONS.items():
+        a = r.params_t[k]
+        if act == C.SS_ACT_SIGMOID:
+            x = a.clamp(1e-4, 1 - 1e-4)
+            raw = torch.log(x / (1 - x)).contiguous()
+            groups[k] = (raw, r.grads[k], a, LOOP_LR[k], act)
+        else:
+            groups[k] = (a, r.grads[k], None, LOOP_LR[k], act)
+    groups["env"] = (r.env, r.d_env, None, LOOP_LR["env"], C.SS_ACT_CLAMP0)
+    opt = Adam(groups)
+    cam_host = make_cameras(gt.cameras)
+    cam_dev = torch.frombuffer(bytearray(bytes(cam_host)), dtype=torch.uint8).to(dev).view(T, -1)
+    perm = np.random.default_rng(5).permutation(np.tile(np.arange(T), 64)).reshape(-1, B)
+    idx_dev = torch.from_numpy(perm).to(dev)
+    tbatch = torch.empty(B, HW, 4, device=dev)
+    d_rgba = torch.empty(B * HW, 4, device=dev)
+    loss = torch.zeros(1, device=dev)
+    it_no = [0]
+
+    def iteration():
+        i = it_no[0] % perm.shape[0]
+        it_no[0] += 1
+        r.cams_dev.view(B, -1).copy_(cam_dev[idx_dev[i]])
+        for j, v in enumerate(perm[i]):
+            r._cams_host[j] = cam_host[int(v)]
+        torch.index_select(targets, 0, idx_dev[i], out=tbatch)
+        r.prefilter_env()
+        r.forward()
+        loss_l1(r.rgba, tbatch.view(-1, 4), d_rgba, loss, scale=1.0 / d_rgba.numel())
+        r.zero_grads()
+        r.backward(d_rgba, None)
+        opt.step()
+
+    for _ in range(args.warmup):
+        iteration()
+    torch.cuda.synchronize()
+    loss_first = float(loss.item())
+    if world > 1:
+        dist.barrier()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        n0 = launch_count()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            iteration()
+        e1.record(st)
+        torch.cuda.synchronize()
+        n_launched = launch_count() - n0
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    status = r.read_status()
+    if rank == 0:
+        its = world * args.steps / (ms / 1000.0)
+        line = {"metric": LOOP_METRIC, "value": its, "unit": "it/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "inverse-rendering loop: ground truth 1.5M surfels (displaced sphere, "
+                                       "value-noise materials), 64 targets 1024x1024 rendered by the same "
+                                       "renderer; 3M surfels initialised on a sphere of radius 1.2, env 512x256 "
+                                       "constant 0.5; 8 views per iteration",
+                           "inputs_vs_l2": "inputs and intermediates > 129 MB L2 (no flush)",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "views_per_s": B * its, "loss_after_warmup": loss_first, "loss_last": float(loss.item()),
+                "clocks": clk.summary(), "gpu_launches": n_launched, "device_status": status}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -394,6 +539,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "config5":
+        run_loop(args)
     else:
         run_ours(args)
 

@@ -292,6 +292,68 @@ ss_status ss_launch_count(int64_t* out);
  * ws: SS_OK or an OR of SS_ERR_CAPACITY / SS_ERR_TIMEOUT / SS_ERR_NONFINITE. */
 ss_status ss_read_status(void* ws, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Optimisation (section "Training and Optimization": all surfel parameters
+ * and the HDR environment are optimised jointly with Adam, Kingma & Ba 2014,
+ * Algorithm 1).
+ *
+ * The renderer reads activated values; the optimiser owns the raw ones.  A
+ * parameter group is one array of raw values with its Adam moments, the
+ * gradient of the loss with respect to the ACTIVATED values (what
+ * ss_render_backward / ss_env_prefilter_backward produce) and the activation
+ * that maps raw to activated:
+ *   SS_ACT_IDENTITY  a = theta          (positions, quaternions -- normalised
+ *                                        inside the renderer -- and log-scales)
+ *   SS_ACT_SIGMOID   a = 1/(1+e^-theta) (albedo, roughness, metallic)
+ *   SS_ACT_CLAMP0    a = theta, and theta is projected onto theta >= 0 after
+ *                    the step            (environment texels)
+ * One step, per element, with g = dL/da * da/dtheta at the current theta:
+ *   m = b1 m + (1 - b1) g;  v = b2 v + (1 - b2) g^2
+ *   theta -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps)
+ * then act = a(theta) when act is not NULL.  The paper gives no Adam
+ * constants; ss_default_adam gives Kingma & Ba's (0.9, 0.999, 1e-8). */
+#define SS_ACT_IDENTITY 0
+#define SS_ACT_SIGMOID 1
+#define SS_ACT_CLAMP0 2
+#define SS_MAX_ADAM_GROUPS 16
+
+typedef struct ss_adam_group {
+    float* param_dev;       /* [n] raw values, updated in place */
+    const float* grad_dev;  /* [n] dL/d(activated value) */
+    float* m_dev;           /* [n] first moment, updated in place */
+    float* v_dev;           /* [n] second moment, updated in place */
+    float* act_dev;         /* [n] activated values written after the step, or NULL */
+    int64_t n;
+    float lr;
+    int32_t activation;     /* SS_ACT_* */
+} ss_adam_group;
+
+typedef struct ss_adam_params {
+    float beta1, beta2, eps;
+    int32_t step;           /* t >= 1: index of this step (bias correction) */
+} ss_adam_params;
+
+void ss_default_adam(ss_adam_params* p);
+
+/* One fused Adam step over n_groups (1 .. SS_MAX_ADAM_GROUPS) groups in a
+ * single launch; arrays of different groups must not overlap.  Errors:
+ * SS_ERR_INVALID_ARG for a NULL param/grad/m/v of a group with n > 0, a
+ * negative n, an unknown activation, step < 1 or a bad group count. */
+ss_status ss_adam_step(const ss_adam_group* groups_host, int32_t n_groups, const ss_adam_params* p,
+                       void* stream);
+
+/* L1 photometric loss between rendered and target images (the l1 term of
+ * Eq. photo_loss, on linear values; the SSIM term and the log/sRGB transfer
+ * are not part of this entry point): over n floats of out and
+ * target (device), loss = scale * sum |out - target| is written to
+ * *loss_dev (one float, overwritten) and d_out = scale * sign(out - target)
+ * (0 where equal) to d_out_dev (overwritten).  The sum is deterministic
+ * (fixed order).  Its partial sums live in a fixed per-device array, so calls
+ * on one device must not overlap in time (one stream, or serialised).
+ * Errors: SS_ERR_INVALID_ARG for NULL pointers or n < 0. */
+ss_status ss_loss_l1(const float* out_dev, const float* target_dev, int64_t n, float scale, float* d_out_dev,
+                     float* loss_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

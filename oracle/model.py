@@ -20,8 +20,8 @@ The oracle is the method written out plainly, in double precision:
   of any loss is PyTorch autograd with every discrete decision held fixed
   (which is the definition of the gradient used here).
 
-Readings where the paper is silent are listed in the design doc; each is restated
-at the function that applies it.
+Every reading where the paper is silent is restated at the function that
+applies it.
 """
 from __future__ import annotations
 

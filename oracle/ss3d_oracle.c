@@ -24,8 +24,8 @@
  * are computed from these decisions in oracle/model.py with PyTorch FP64.
  *
  * Readings where the paper is silent (equirect convention, level sizes,
- * normalised prefilter sums, GGX/Smith forms) are listed in the design doc and
- * restated next to each function.
+ * normalised prefilter sums, GGX/Smith forms) are restated next to each
+ * function.
  */
 #include <math.h>
 #include <stdint.h>

@@ -81,6 +81,21 @@ class ss_env_map_grads(ctypes.Structure):
     _fields_ = [("irr", c_vp), ("spec", c_vp)]
 
 
+SS_ACT_IDENTITY = 0
+SS_ACT_SIGMOID = 1
+SS_ACT_CLAMP0 = 2
+SS_MAX_ADAM_GROUPS = 16
+
+
+class ss_adam_group(ctypes.Structure):
+    _fields_ = [("param", c_vp), ("grad", c_vp), ("m", c_vp), ("v", c_vp), ("act", c_vp), ("n", c_i64),
+                ("lr", c_f), ("activation", c_i32)]
+
+
+class ss_adam_params(ctypes.Structure):
+    _fields_ = [("beta1", c_f), ("beta2", c_f), ("eps", c_f), ("step", c_i32)]
+
+
 EXPORTS = {
     "ss_default_params": (None, [ctypes.POINTER(ss_render_params)]),
     "ss_error_string": (ctypes.c_char_p, [c_i32]),
@@ -109,6 +124,9 @@ EXPORTS = {
     "ss_launch_count": (c_i32, [ctypes.POINTER(ctypes.c_int64)]),
     "ss_profile_begin": (c_i32, []),
     "ss_profile_end": (c_i32, [ctypes.c_void_p]),
+    "ss_default_adam": (None, [ctypes.POINTER(ss_adam_params)]),
+    "ss_adam_step": (c_i32, [ctypes.POINTER(ss_adam_group), c_i32, ctypes.POINTER(ss_adam_params), c_vp]),
+    "ss_loss_l1": (c_i32, [c_vp, c_vp, c_i64, c_f, c_vp, c_vp, c_vp]),
 }
 
 

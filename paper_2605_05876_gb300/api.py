@@ -235,3 +235,51 @@ def launch_count() -> int:
     n = ctypes.c_int64()
     check(lib().ss_launch_count(ctypes.byref(n)), "ss_launch_count")
     return int(n.value)
+
+
+# ------------------------------------------------------------------------
+# optimisation
+
+SURFEL_ACTIVATIONS = {"pos": C.SS_ACT_IDENTITY, "quat": C.SS_ACT_IDENTITY, "log_scale": C.SS_ACT_IDENTITY,
+                      "albedo": C.SS_ACT_SIGMOID, "roughness": C.SS_ACT_SIGMOID, "metallic": C.SS_ACT_SIGMOID}
+
+
+class Adam:
+    """Fused Adam (ss_adam_step) over named parameter groups.
+
+    Each group is (raw, grad, act, lr, activation): raw values owned by the
+    optimiser, the gradient w.r.t. the activated values the renderer reads
+    (act; may be raw itself for identity activations) and its learning rate.
+    """
+
+    def __init__(self, groups: dict, beta1=0.9, beta2=0.999, eps=1e-8):
+        import torch
+        if not 1 <= len(groups) <= C.SS_MAX_ADAM_GROUPS:
+            raise ValueError("1 .. 16 groups")
+        self.groups = groups
+        self.moments = {k: (torch.zeros_like(g[0]), torch.zeros_like(g[0])) for k, g in groups.items()}
+        self.p = C.ss_adam_params()
+        lib().ss_default_adam(ctypes.byref(self.p))
+        self.p.beta1, self.p.beta2, self.p.eps = beta1, beta2, eps
+        self.t = 0
+        arr = (C.ss_adam_group * len(groups))()
+        for i, (k, (raw, grad, act, lr, activation)) in enumerate(groups.items()):
+            m, v = self.moments[k]
+            for t in (raw, grad, m, v) + ((act,) if act is not None else ()):
+                if not t.is_contiguous() or t.dtype != torch.float32:
+                    raise ValueError(f"group {k}: float32 contiguous tensors")
+            arr[i] = C.ss_adam_group(_ptr(raw), _ptr(grad), _ptr(m), _ptr(v),
+                                     _ptr(act) if act is not None and act.data_ptr() != raw.data_ptr() else None,
+                                     raw.numel(), float(lr), int(activation))
+        self._arr = arr
+
+    def step(self):
+        self.t += 1
+        self.p.step = self.t
+        check(lib().ss_adam_step(self._arr, len(self.groups), ctypes.byref(self.p), _stream()), "ss_adam_step")
+
+
+def loss_l1(out, target, d_out, loss, scale: float = 1.0):
+    """loss[0] = scale * sum|out - target|, d_out = scale * sign(out - target) (device tensors)."""
+    check(lib().ss_loss_l1(_ptr(out), _ptr(target), out.numel(), float(scale), _ptr(d_out), _ptr(loss), _stream()),
+          "ss_loss_l1")

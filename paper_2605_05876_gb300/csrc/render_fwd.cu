@@ -292,25 +292,49 @@ __global__ void __launch_bounds__(1024) scan_kernel(const uint32_t* cnt, uint32_
     }
 }
 
+// One thread per record: its keys go to the bins of the tiles its support
+// rectangle covers, at positions taken from the tiles' cursors.  The cursor
+// atomics of up to 4 tiles are issued back to back so that their round trips
+// overlap.
 __global__ void __launch_bounds__(256) scatter_kernel(ss_ws_view ws, int64_t total_records) {
     const ss_layout* L = ws.layout;
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= total_records) return;
-    int v = 0;
-    while (v + 1 < L->n_views && r >= L->v[v + 1].rec_off) ++v;
-    const ss_view_layout& vl = L->v[v];
-    float4 r3 = ws.rec[r].r3;
-    uint32_t flags = __float_as_uint(ws.rec[r].r4.w);
+    const uint32_t flags = __float_as_uint(ws.rec[r].r4.w);
     if (!(flags & SS_FLAG_VALID)) return;
-    uint32_t rx = __float_as_uint(r3.z), ry = __float_as_uint(r3.w);
-    int i0 = rx & 0xffff, i1 = rx >> 16, j0 = ry & 0xffff, j1 = ry >> 16;
-    unsigned long long key = ((unsigned long long)__float_as_uint(r3.x) << 32) | (uint32_t)(r - vl.rec_off);
-    for (int ty = j0 / SS_TILE; ty <= j1 / SS_TILE; ++ty)
-        for (int tx = i0 / SS_TILE; tx <= i1 / SS_TILE; ++tx) {
-            int t = vl.tile_off + ty * vl.tiles_x + tx;
-            uint32_t pos = ws.tile_start[t] + atomicAdd(&ws.tile_cursor[t], 1u);
-            if ((int64_t)pos < ws.max_instances) ws.keys[pos] = key;
+    const float4 r3 = ws.rec[r].r3;
+    int v = 0;
+    {
+        int lo = 0, hi = L->n_views - 1;
+        while (lo < hi) {
+            int m = (lo + hi + 1) >> 1;
+            if (L->v[m].rec_off <= r) lo = m;
+            else hi = m - 1;
         }
+        v = lo;
+    }
+    const ss_view_layout& vl = L->v[v];
+    const uint32_t rx = __float_as_uint(r3.z), ry = __float_as_uint(r3.w);
+    const int tx0 = (int)(rx & 0xffff) / SS_TILE, tx1 = (int)(rx >> 16) / SS_TILE;
+    const int ty0 = (int)(ry & 0xffff) / SS_TILE, ty1 = (int)(ry >> 16) / SS_TILE;
+    const int ntx = tx1 - tx0 + 1, nt = ntx * (ty1 - ty0 + 1);
+    const unsigned long long key = ((unsigned long long)__float_as_uint(r3.x) << 32) | (uint32_t)(r - vl.rec_off);
+    for (int b = 0; b < nt; b += 4) {
+        int t[4];
+        uint32_t pos[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = b + u;
+            t[u] = q < nt ? vl.tile_off + (ty0 + q / ntx) * vl.tiles_x + tx0 + q % ntx : -1;
+            if (t[u] >= 0) pos[u] = atomicAdd(&ws.tile_cursor[t[u]], 1u);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (t[u] >= 0) {
+                const uint32_t p = ws.tile_start[t[u]] + pos[u];
+                if ((int64_t)p < ws.max_instances) ws.keys[p] = key;
+            }
+    }
 }
 
 #define SORT_THREADS 512

@@ -3,7 +3,7 @@ import numpy as np
 
 from oracle import model as M
 
-# the benchmark spec tolerance: 1e-4 relative per pixel, 1e-5 absolute where |value| < 1e-2
+# image tolerance: 1e-4 relative per pixel, 1e-5 absolute where |value| < 1e-2
 RTOL, ATOL, SMALL = 1e-4, 1e-5, 1e-2
 # decisions closer than this to flipping are set aside (rounding of FP32 vs FP64)
 M_CUT, M_GAP, M_BOX = 1e-5, 1e-5, 2e-3
