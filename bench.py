@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--config", default="config3")
+    ap.add_argument("--config", default="displaced_sphere_1m")
     ap.add_argument("--views", type=int, default=0, help="render only the first N views (profiling)")
     ap.add_argument("--no-per-view", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -440,7 +440,7 @@ def run_loop(args):
     from paper_2605_05876_gb300.api import Adam, Renderer, SURFEL_ACTIVATIONS, launch_count, loss_l1, make_cameras
 
     B = 8
-    gt = scenes.config5_gt()
+    gt = scenes.loop_ground_truth()
     T = len(gt.cameras)
     # targets: the ground truth rendered by the same renderer, 8 views at a time
     rg = Renderer(scenes.Scene(gt.surfels, gt.scene_offsets, gt.envs, gt.cameras[:B], "gt"), with_backward=False)
@@ -454,7 +454,7 @@ def run_loop(args):
     del rg
     torch.cuda.empty_cache()
 
-    surf, env0 = scenes.config5_init()
+    surf, env0 = scenes.loop_init()
     r = Renderer(scenes.Scene(surf, np.array([0, surf.n], np.int64), [env0], gt.cameras[:B], "loop"),
                  capacity_slack=2.0)
     r.zero_grads()
@@ -539,7 +539,7 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.config == "config5":
+    elif args.config == "inverse_loop":
         run_loop(args)
     else:
         run_ours(args)

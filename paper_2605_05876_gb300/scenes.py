@@ -85,9 +85,9 @@ class Scene:
 # geometric helpers (input construction only)
 
 
-def rng_streams(config_id: int, n: int):
+def rng_streams(seed_id: int, n: int):
     """Independent sub-streams of PCG64 seeded by SeedSequence(1000 + id)."""
-    ss = np.random.SeedSequence(1000 + int(config_id))
+    ss = np.random.SeedSequence(1000 + int(seed_id))
     return [np.random.Generator(np.random.PCG64(s)) for s in ss.spawn(n)]
 
 
@@ -308,7 +308,7 @@ def fib_cameras(n, radius, fov=60.0, width=800, height=800, scene=0, center=(0, 
             for i in range(n)]
 
 
-def config1(n=4096, res=128, seed_id=1) -> Scene:
+def sphere_4k(n=4096, res=128, seed_id=1) -> Scene:
     """4096 Fibonacci surfels on the unit sphere, isotropic tangent std 0.03,
     one 128^2 view at distance 3, 64x32 log-normal env."""
     r_geo, r_att, r_env, _ = rng_streams(seed_id, 4)
@@ -319,7 +319,7 @@ def config1(n=4096, res=128, seed_id=1) -> Scene:
     s = _pack(pos, quat, ls, alb, rough, metal)
     env = lognormal_env(r_env, 64, 32)
     cam = look_at((0.0, 0.0, 3.0), width=res, height=res)
-    return Scene(s, np.array([0, n], np.int64), [env], [cam], "config1")
+    return Scene(s, np.array([0, n], np.int64), [env], [cam], "sphere_4k")
 
 
 def torus_sphere_surfels(rng_geo, rng_att, n, scale_lo=0.005, scale_hi=0.02):
@@ -340,7 +340,7 @@ def torus_sphere_surfels(rng_geo, rng_att, n, scale_lo=0.005, scale_hi=0.02):
     return pos, quat, ls, alb, rough, metal
 
 
-def config2(n=100_000, res=512, seed_id=2) -> Scene:
+def torus_sphere_100k(n=100_000, res=512, seed_id=2) -> Scene:
     """Torus (R=1, r=0.35) U sphere (r=0.6 at (0.8,0.4,0)), anisotropic
     scales U[0.005,0.02], one 512^2 view at distance 3, elevation 30 deg,
     azimuth 45 deg, 256x128 log-normal env."""
@@ -350,7 +350,7 @@ def config2(n=100_000, res=512, seed_id=2) -> Scene:
     el, az = math.radians(30.0), math.radians(45.0)
     eye = 3.0 * np.array([math.cos(el) * math.sin(az), math.sin(el), math.cos(el) * math.cos(az)])
     cam = look_at(eye, width=res, height=res)
-    return Scene(s, np.array([0, n], np.int64), [env], [cam], "config2")
+    return Scene(s, np.array([0, n], np.int64), [env], [cam], "torus_sphere_100k")
 
 
 def displaced_sphere_surfels(rng_geo, rng_att, n, attrs="uniform"):
@@ -368,7 +368,7 @@ def displaced_sphere_surfels(rng_geo, rng_att, n, attrs="uniform"):
     return pos, quat, ls, alb, rough, metal
 
 
-def config3(n=1_000_000, views=16, res=800, env_w=512, seed_id=3) -> Scene:
+def displaced_sphere_1m(n=1_000_000, views=16, res=800, env_w=512, seed_id=3) -> Scene:
     """1M surfels on the displaced sphere r = 1 + 0.05 sin(8th) sin(8ph),
     isotropic scale sqrt(area/N), 16 Fibonacci views at radius 3, 800^2,
     512x256 log-normal env."""
@@ -376,13 +376,13 @@ def config3(n=1_000_000, views=16, res=800, env_w=512, seed_id=3) -> Scene:
     s = _pack(*displaced_sphere_surfels(r_geo, r_att, n))
     env = lognormal_env(r_env, env_w, env_w // 2)
     cams = fib_cameras(views, 3.0, width=res, height=res)
-    return Scene(s, np.array([0, n], np.int64), [env], cams, "config3")
+    return Scene(s, np.array([0, n], np.int64), [env], cams, "displaced_sphere_1m")
 
 
-def config4(n_scenes=8, views_per_scene=4, seed_id=4, n_lo=50_000, n_hi=2_000_000,
+def uneven_scenes(n_scenes=8, views_per_scene=4, seed_id=4, n_lo=50_000, n_hi=2_000_000,
             resolutions=(256, 512, 800, 1024)) -> Scene:
     """Uneven batch: 8 scenes with log-uniform surfel counts, alternating the
-    sphere (config 1) and torus U sphere (config 2) generators with seeded
+    sphere (sphere_4k) and torus U sphere (torus_sphere_100k) generators with seeded
     scale and offset, 4 views each at random resolutions, one 256x128 env per
     scene."""
     r_meta, r_geo, r_att, r_env = rng_streams(seed_id, 4)
@@ -408,20 +408,20 @@ def config4(n_scenes=8, views_per_scene=4, seed_id=4, n_lo=50_000, n_hi=2_000_00
             res = int(resolutions[r_meta.integers(0, len(resolutions))])
             eye = off + 3.0 * scale * dirs[i]
             cams.append(look_at(eye, off, width=res, height=res, scene=k))
-    return Scene(Surfels.concat(parts), np.array(offs, np.int64), envs, cams, "config4")
+    return Scene(Surfels.concat(parts), np.array(offs, np.int64), envs, cams, "uneven_scenes")
 
 
-def config5_gt(n=1_500_000, targets=64, res=1024, seed_id=5) -> Scene:
+def loop_ground_truth(n=1_500_000, targets=64, res=1024, seed_id=5) -> Scene:
     """Ground truth of the inverse-rendering loop: displaced sphere with
     value-noise albedo/roughness, 64 targets of 1024^2, 512x256 env."""
     r_geo, r_att, r_env, _ = rng_streams(seed_id, 4)
     s = _pack(*displaced_sphere_surfels(r_geo, r_att, n, attrs="noise"))
     env = lognormal_env(r_env, 512, 256)
     cams = fib_cameras(targets, 3.0, width=res, height=res)
-    return Scene(s, np.array([0, n], np.int64), [env], cams, "config5_gt")
+    return Scene(s, np.array([0, n], np.int64), [env], cams, "loop_ground_truth")
 
 
-def config5_init(n=3_000_000, seed_id=55, env_w=512) -> tuple:
+def loop_init(n=3_000_000, seed_id=55, env_w=512) -> tuple:
     """Initial state of the loop: 3M isotropic surfels on a sphere of radius
     1.2, random attributes, constant 0.5 env."""
     r_geo, r_att, _, _ = rng_streams(seed_id, 4)
@@ -438,5 +438,5 @@ def config5_init(n=3_000_000, seed_id=55, env_w=512) -> tuple:
 
 
 def by_name(name: str, **kw) -> Scene:
-    return {"config1": config1, "config2": config2, "config3": config3,
-            "config4": config4, "config5_gt": config5_gt}[name](**kw)
+    return {"sphere_4k": sphere_4k, "torus_sphere_100k": torus_sphere_100k, "displaced_sphere_1m": displaced_sphere_1m,
+            "uneven_scenes": uneven_scenes, "loop_ground_truth": loop_ground_truth}[name](**kw)

@@ -98,14 +98,14 @@ def test_backward_tiny(seed, sigma_f):
     _compare(gpu, ref)
 
 
-def test_backward_config1():
-    gpu, ref = _run(S.config1(), 5)
+def test_backward_sphere_4k():
+    gpu, ref = _run(S.sphere_4k(), 5)
     _compare(gpu, ref)
 
 
 def test_backward_multi_view_multi_scene():
-    a = S.config1(n=2048, res=64)
-    b = S.config2(n=20000, res=96)
+    a = S.sphere_4k(n=2048, res=64)
+    b = S.torus_sphere_100k(n=20000, res=96)
     cams = [a.cameras[0], S.look_at((0.5, 0.3, 2.8), width=37, height=53, scene=0),
             S.look_at(b.cameras[0].R.T @ -b.cameras[0].t, width=96, height=80, scene=1)]
     rng = np.random.default_rng(6)
@@ -116,6 +116,6 @@ def test_backward_multi_view_multi_scene():
 
 
 @pytest.mark.slow
-def test_backward_config2():
-    gpu, ref = _run(S.config2(), 9)
+def test_backward_torus_sphere_100k():
+    gpu, ref = _run(S.torus_sphere_100k(), 9)
     _compare(gpu, ref)

@@ -98,8 +98,8 @@ def test_env_prefilter_backward_matches_oracle():
     assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
 
 
-def test_forward_config1():
-    sc = S.config1()
+def test_forward_sphere_4k():
+    sc = S.sphere_4k()
     r = _renderer(sc)
     r.forward()
     assert r.read_status() == 0
@@ -143,8 +143,8 @@ def test_forward_empty_and_culled():
     assert np.all(gpu[:, 4:] == 0)
 
 
-def test_forward_config2():
-    sc = S.config2()
+def test_forward_torus_sphere_100k():
+    sc = S.torus_sphere_100k()
     r = _renderer(sc)
     r.forward()
     assert r.read_status() == 0
@@ -154,8 +154,8 @@ def test_forward_config2():
 def test_forward_multi_scene_uneven():
     """Two scenes, three views of different sizes (ragged tiles), one env each."""
     rng = np.random.default_rng(5)
-    a = S.config1(n=2048, res=64)
-    b = S.config2(n=20000, res=96)
+    a = S.sphere_4k(n=2048, res=64)
+    b = S.torus_sphere_100k(n=20000, res=96)
     cams = [a.cameras[0], S.look_at((0.5, 0.3, 2.8), width=37, height=53, scene=0),
             S.look_at(b.cameras[0].R.T @ -b.cameras[0].t, width=96, height=80, scene=1)]
     env_b = np.exp(rng.normal(size=(32, 64, 3))).astype(np.float32)
@@ -170,10 +170,10 @@ def test_forward_multi_scene_uneven():
 
 
 @pytest.mark.slow
-def test_forward_config3_sampled():
+def test_forward_displaced_sphere_1m_sampled():
     """Full-size headline workload (1M surfels, 16 views of 800^2), sampled
     pixels of two views checked one by one against the oracle."""
-    sc = S.config3()
+    sc = S.displaced_sphere_1m()
     r = _renderer(sc)
     r.forward()
     assert r.read_status() == 0
