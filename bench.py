@@ -375,8 +375,8 @@ def run_ours(args):
     t_launch = stages[dom][0] / max(stages[dom][1], 1) / 1000.0
     if dom == "raster_fwd":
         flops = counts["rect_tests"] * FLOP_TEST + counts["fragments"] * FLOP_FRAG_FWD
-    else:
-        flops = counts["rect_tests"] * FLOP_TEST + counts["bwd_fragments"] * FLOP_FRAG_BWD
+    else:   # the backward replays the grouping from the forward's coverage words: no pixel tests
+        flops = counts["bwd_fragments"] * FLOP_FRAG_BWD
     achieved = flops / t_launch / 1e12
     workload = f"{args.config}_{V}x800"
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",

@@ -229,10 +229,12 @@ ss_status ss_env_prefilter_backward(const ss_env_desc* d, int32_t n_envs, const 
                                     void* stream);
 
 /* Workspace bytes for a render of this batch.  with_backward != 0 adds the
- * per-pixel layer state that ss_render_backward reads.  Requires
- * p->max_instances > 0. */
-ss_status ss_workspace_size(const ss_batch_desc* b, const ss_render_params* p, int32_t with_backward,
-                            size_t* bytes);
+ * per-pixel layer state that ss_render_backward reads and, for the env
+ * description ed (required then: the one later passed to the render calls),
+ * the accumulators of the env-map gradients.  Requires p->max_instances > 0.
+ * Errors: SS_ERR_INVALID_ARG for bad sizes or an invalid ed. */
+ss_status ss_workspace_size(const ss_batch_desc* b, const ss_render_params* p, const ss_env_desc* ed,
+                            int32_t with_backward, size_t* bytes);
 
 /* Exact number of (tile, surfel) instances of a batch: runs the projection
  * step into `ws` and reads the count back (synchronises the stream).  Use it

@@ -105,7 +105,8 @@ EXPORTS = {
     "ss_env_prefilter": (c_i32, [ctypes.POINTER(ss_env_desc), c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "ss_env_prefilter_noalloc": (c_i32, [ctypes.POINTER(ss_env_desc), c_i32, c_vp, c_vp, c_vp, c_vp]),
     "ss_env_prefilter_backward": (c_i32, [ctypes.POINTER(ss_env_desc), c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
-    "ss_workspace_size": (c_i32, [ctypes.POINTER(ss_batch_desc), ctypes.POINTER(ss_render_params), c_i32,
+    "ss_workspace_size": (c_i32, [ctypes.POINTER(ss_batch_desc), ctypes.POINTER(ss_render_params),
+                                  ctypes.POINTER(ss_env_desc), c_i32,
                                   ctypes.POINTER(ctypes.c_size_t)]),
     "ss_count_instances": (c_i32, [ctypes.POINTER(ss_batch_desc), ctypes.POINTER(ss_surfels),
                                    ctypes.POINTER(ss_render_params), ctypes.POINTER(ss_env_desc),

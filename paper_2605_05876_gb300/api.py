@@ -123,7 +123,8 @@ class Renderer:
             ctypes.memmove(ctypes.byref(probe), ctypes.byref(self.prm), ctypes.sizeof(probe))
             probe.max_instances = 1
             nb = ctypes.c_size_t()
-            check(lib().ss_workspace_size(ctypes.byref(self.desc), ctypes.byref(probe), 0, ctypes.byref(nb)),
+            check(lib().ss_workspace_size(ctypes.byref(self.desc), ctypes.byref(probe), ctypes.byref(self.ed), 0,
+                                          ctypes.byref(nb)),
                   "ss_workspace_size")
             ws = torch.empty(nb.value + 256, dtype=torch.uint8, device=self.dev)
             cnt = ctypes.c_int64()
@@ -135,8 +136,8 @@ class Renderer:
             del ws
         self.prm.max_instances = max_instances
         nb = ctypes.c_size_t()
-        check(lib().ss_workspace_size(ctypes.byref(self.desc), ctypes.byref(self.prm), int(self.with_backward),
-                                      ctypes.byref(nb)), "ss_workspace_size")
+        check(lib().ss_workspace_size(ctypes.byref(self.desc), ctypes.byref(self.prm), ctypes.byref(self.ed),
+                                      int(self.with_backward), ctypes.byref(nb)), "ss_workspace_size")
         self.ws_bytes = nb.value
         self.ws = torch.empty(nb.value, dtype=torch.uint8, device=self.dev)
 

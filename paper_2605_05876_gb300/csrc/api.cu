@@ -172,11 +172,13 @@ static ss_status build_layout(const ss_batch_desc* b, const ss_render_params* p,
 }
 
 struct ws_plan {
-    size_t status, layout, vgeo, rec, tc, ts, tcur, keys, keys_alt, layer, pix, grad, masks, total;
+    size_t status, layout, vgeo, rec, tc, ts, tcur, keys, keys_alt, layer, pix, grad, masks, env_acc, total;
+    int64_t env_texels;   // irradiance + specular texels of one scene (0: no env-gradient scratch)
 };
 
-static ws_plan plan_ws(const ss_layout& L, const ss_render_params& p, int with_bwd) {
+static ws_plan plan_ws(const ss_layout& L, const ss_render_params& p, int with_bwd, const ss_env_desc* ed) {
     ws_plan w;
+    w.env_texels = (with_bwd && ed) ? (ss_env_irr_floats(ed) + ss_env_spec_floats(ed)) / 3 : 0;
     size_t o = 0;
     auto take = [&](size_t bytes) {
         size_t at = o;
@@ -197,8 +199,9 @@ static ws_plan plan_ws(const ss_layout& L, const ss_render_params& p, int with_b
         w.pix = take(sizeof(float) * 2 * (size_t)L.total_pixels);
         w.grad = take(sizeof(float) * SS_NGRAD * (size_t)L.total_records);
         w.masks = take(sizeof(uint32_t) * 8 * (size_t)p.max_instances);
+        w.env_acc = take(sizeof(float4) * (size_t)w.env_texels * (size_t)L.n_scenes);
     } else {
-        w.layer = w.pix = w.grad = w.masks = 0;
+        w.layer = w.pix = w.grad = w.masks = w.env_acc = 0;
     }
     w.total = o;
     return w;
@@ -221,6 +224,8 @@ static ss_ws_view carve(void* ws, const ws_plan& w, const ss_render_params& p, i
     v.pix_state = with_bwd ? (float*)(b + w.pix) : nullptr;
     v.grad_rec = with_bwd ? (float*)(b + w.grad) : nullptr;
     v.cover_masks = with_bwd ? (uint32_t*)(b + w.masks) : nullptr;
+    v.env_acc = (with_bwd && w.env_texels) ? (float4*)(b + w.env_acc) : nullptr;
+    v.env_texels = w.env_texels;
     v.max_instances = p.max_instances;
     return v;
 }
@@ -254,13 +259,16 @@ __global__ void set_layout_kernel(ss_layout* dst, ss_layout src) {
     for (int i = threadIdx.x; i < (int)(sizeof(ss_layout) / sizeof(int)); i += blockDim.x) d[i] = s[i];
 }
 
-extern "C" ss_status ss_workspace_size(const ss_batch_desc* b, const ss_render_params* p, int32_t with_backward,
-                                       size_t* bytes) {
+static bool env_desc_ok(const ss_env_desc* d);
+
+extern "C" ss_status ss_workspace_size(const ss_batch_desc* b, const ss_render_params* p, const ss_env_desc* ed,
+                                       int32_t with_backward, size_t* bytes) {
     if (!bytes || !p || p->max_instances <= 0 || p->max_instances > 0xffffffffll) return SS_ERR_INVALID_ARG;
     static ss_layout L;
     ss_status st = build_layout(b, p, &L);
     if (st) return st;
-    *bytes = plan_ws(L, *p, with_backward).total;
+    if (ed && !env_desc_ok(ed)) return SS_ERR_INVALID_ARG;
+    *bytes = plan_ws(L, *p, with_backward, ed).total;
     return SS_OK;
 }
 
@@ -344,7 +352,7 @@ static ss_status forward_core(const ss_batch_desc* b, const ss_surfels* s, const
     if (e) return e;
     e = build_layout(b, p, &L);
     if (e) return e;
-    ws_plan plan = plan_ws(L, *p, with_bwd);
+    ws_plan plan = plan_ws(L, *p, with_bwd, ed);
     if (ws_bytes < plan.total) return SS_ERR_WORKSPACE;
     W = carve(ws, plan, *p, with_bwd);
     ss_fwd_args a;
@@ -393,7 +401,7 @@ extern "C" ss_status ss_render_forward(const ss_batch_desc* b, const ss_surfels*
     int with_bwd = 0;
     if (b && p && p->max_instances > 0) {
         static ss_layout Lt;
-        if (build_layout(b, p, &Lt) == SS_OK && ws_bytes >= plan_ws(Lt, *p, 1).total) with_bwd = 1;
+        if (build_layout(b, p, &Lt) == SS_OK && ws_bytes >= plan_ws(Lt, *p, 1, ed).total) with_bwd = 1;
     }
     return forward_core(b, s, p, ed, env, out_rgba_dev, out_aov_dev, ws, ws_bytes, with_bwd, 0,
                         (cudaStream_t)stream, L, W);
@@ -429,7 +437,7 @@ extern "C" ss_status ss_render_backward(const ss_batch_desc* b, const ss_surfels
     static ss_layout L;
     e = build_layout(b, p, &L);
     if (e) return e;
-    ws_plan plan = plan_ws(L, *p, 1);
+    ws_plan plan = plan_ws(L, *p, 1, ed);
     if (ws_bytes < plan.total) return SS_ERR_WORKSPACE;
     ss_ws_view W = carve(ws, plan, *p, 1);
     cudaStream_t st = (cudaStream_t)stream;
@@ -450,6 +458,8 @@ extern "C" ss_status ss_render_backward(const ss_batch_desc* b, const ss_surfels
     ss_env_map_grads ge = {nullptr, nullptr};
     a.genv = genv ? *genv : ge;
     CK(cudaMemsetAsync(W.grad_rec, 0, sizeof(float) * SS_NGRAD * (size_t)L.total_records, st));
+    if (a.genv.irr || a.genv.spec)
+        CK(cudaMemsetAsync(W.env_acc, 0, sizeof(float4) * (size_t)W.env_texels * (size_t)L.n_scenes, st));
     {
         stage_scope sc(3, st);
         ss_launch_raster_bwd(W, L, a, st);

@@ -356,6 +356,17 @@ __device__ __forceinline__ void scatter3(float* D, float u, float v, int W, int 
         atomicAdd(D + t.i11 * 3 + c, w11 * g[c]);
     }
 }
+// the same bilinear adjoint into RGBA accumulators (one 16-byte atomic per tap)
+__device__ __forceinline__ void scatter4(float4* D, float u, float v, int W, int H, const float g[3], float scale) {
+    if (scale == 0.f || (g[0] == 0.f && g[1] == 0.f && g[2] == 0.f)) return;
+    ss_taps t = bilinear_taps(u, v, W, H, true);
+    const float w00 = (1.f - t.fx) * (1.f - t.fy) * scale, w01 = t.fx * (1.f - t.fy) * scale,
+                w10 = (1.f - t.fx) * t.fy * scale, w11 = t.fx * t.fy * scale;
+    atomicAdd(D + t.i00, make_float4(w00 * g[0], w00 * g[1], w00 * g[2], 0.f));
+    atomicAdd(D + t.i01, make_float4(w01 * g[0], w01 * g[1], w01 * g[2], 0.f));
+    atomicAdd(D + t.i10, make_float4(w10 * g[0], w10 * g[1], w10 * g[2], 0.f));
+    atomicAdd(D + t.i11, make_float4(w11 * g[0], w11 * g[1], w11 * g[2], 0.f));
+}
 // d(u, v)/d(direction) for the equirect map of a unit direction d
 __device__ __forceinline__ void uv_grad(const float d[3], float gu, float gv, float out[3]) {
     const float rxz = fmaxf(d[0] * d[0] + d[2] * d[2], 1e-20f);
@@ -435,8 +446,7 @@ __device__ __forceinline__ void pbwd_record(const ss_ws_view& ws, const ss_bwd_a
     const int64_t spec_stride = spec_level_off_b(a.ed, nL, Wt, Ht);
     const float* irr = a.env.irr + scene * irr_stride;
     const float* spec = a.env.spec + scene * spec_stride;
-    float* d_irr = A.genv.irr ? A.genv.irr + scene * irr_stride : nullptr;
-    float* d_spec = A.genv.spec ? A.genv.spec + scene * spec_stride : nullptr;
+    const bool d_irr = A.genv.irr != nullptr, d_spec = A.genv.spec != nullptr;
     const int lutn = a.p.lut_n;
     const float* LUT = a.env.lut;
 
@@ -605,16 +615,25 @@ __device__ __forceinline__ void pbwd_record(const ss_ws_view& ws, const ss_bwd_a
             float dmu = dbe1 * dbe_mu[0] + dbe2 * dbe_mu[1];
             float dmup = (mup > 0.f && mup < 1.f) ? dmu : 0.f;
             // environment texels
+            // environment texels: the block's own scene into shared memory, the
+            // rest into the workspace's RGBA accumulators (irradiance texels
+            // first, then the specular stack)
+            const bool mine = scene == pv.scene;
+            float4* acc = ws.env_acc + scene * ws.env_texels;
+            const int64_t irr_tex = (int64_t)a.ed.irr_width * a.ed.irr_height;
             if (d_irr) {
-                float* dst = (pv.irr && scene == pv.scene) ? pv.irr : d_irr;
-                scatter3(dst, un, vn, a.ed.irr_width, a.ed.irr_height, true, dLd, 1.f);
+                if (pv.irr && mine) scatter3(pv.irr, un, vn, a.ed.irr_width, a.ed.irr_height, true, dLd, 1.f);
+                else scatter4(acc, un, vn, a.ed.irr_width, a.ed.irr_height, dLd, 1.f);
             }
             if (d_spec) {
-                const bool mine = pv.spec && scene == pv.scene;
-                float* dst0 = (mine && l0 >= pv.level) ? pv.spec + (o0 - pv.spec_off) : d_spec + o0;
-                float* dst1 = (mine && l1 >= pv.level) ? pv.spec + (o1 - pv.spec_off) : d_spec + o1;
-                scatter3(dst0, ur, vr, W0, H0, true, dLs, 1.f - lf);
-                scatter3(dst1, ur, vr, W1, H1, true, dLs, lf);
+                if (pv.spec && mine && l0 >= pv.level)
+                    scatter3(pv.spec + (o0 - pv.spec_off), ur, vr, W0, H0, true, dLs, 1.f - lf);
+                else
+                    scatter4(acc + irr_tex + o0 / 3, ur, vr, W0, H0, dLs, 1.f - lf);
+                if (pv.spec && mine && l1 >= pv.level)
+                    scatter3(pv.spec + (o1 - pv.spec_off), ur, vr, W1, H1, true, dLs, lf);
+                else
+                    scatter4(acc + irr_tex + o1 / 3, ur, vr, W1, H1, dLs, lf);
             }
             // directions: Ld(uv(ns)), Ls(uv(refl))
             float gun = 0.f, gvn = 0.f, gur = 0.f, gvr = 0.f;
@@ -700,17 +719,31 @@ __global__ void __launch_bounds__(128, 4) project_bwd_kernel(ss_ws_view ws, ss_b
     __syncthreads();
     for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) pbwd_record(ws, A, r, pv);
     __syncthreads();
-    if (use) {
-        const int64_t irr_stride = irr_floats;
-        int Wt, Ht;
-        const int64_t spec_stride = spec_level_off_b(A.f.ed, A.f.ed.n_levels, Wt, Ht);
-        float* gi = A.genv.irr + scene * irr_stride;
-        float* gs = A.genv.spec + scene * spec_stride + priv_spec_off;
-        for (int k = threadIdx.x; k < n_priv; k += blockDim.x) {
-            const float v = priv[k];
-            if (v != 0.f) atomicAdd(k < irr_floats ? gi + k : gs + (k - irr_floats), v);
+    if (use) {   // texel by texel into the RGBA accumulators
+        float4* acc = ws.env_acc + scene * ws.env_texels;
+        const int irr_tex = irr_floats / 3;
+        for (int k = threadIdx.x; k < n_priv / 3; k += blockDim.x) {
+            const float4 v = make_float4(priv[3 * k], priv[3 * k + 1], priv[3 * k + 2], 0.f);
+            if (v.x != 0.f || v.y != 0.f || v.z != 0.f)
+                atomicAdd(k < irr_tex ? acc + k : acc + irr_tex + priv_spec_off / 3 + (k - irr_tex), v);
         }
     }
+}
+
+// Add the RGBA accumulators into the caller's env-map gradients (RGB).
+__global__ void env_acc_flush_kernel(const float4* acc, int64_t texels, int64_t irr_tex, int64_t total,
+                                     float* d_irr, float* d_spec) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int64_t sc = i / texels, k = i % texels;
+    const float4 v = acc[i];
+    if (v.x == 0.f && v.y == 0.f && v.z == 0.f) return;
+    float* d = k < irr_tex ? (d_irr ? d_irr + (sc * irr_tex + k) * 3 : nullptr)
+                           : (d_spec ? d_spec + (sc * (texels - irr_tex) + (k - irr_tex)) * 3 : nullptr);
+    if (!d) return;
+    d[0] += v.x;
+    d[1] += v.y;
+    d[2] += v.z;
 }
 
 // Sum the per-view parameter gradients of each surfel (views in order) and
@@ -777,4 +810,10 @@ void ss_launch_project_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bw
     project_bwd_kernel<<<blocks, 128, smem, st>>>(ws, a, L.total_records, per_block, level, spec_off, (int)priv_spec);
     ss_note_launch();
     param_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ws, a.g, n);
+    if ((a.genv.irr || a.genv.spec) && ws.env_acc) {
+        const int64_t total = ws.env_texels * L.n_scenes;
+        ss_note_launch();
+        env_acc_flush_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
+            ws.env_acc, ws.env_texels, (int64_t)a.f.ed.irr_width * a.f.ed.irr_height, total, a.genv.irr, a.genv.spec);
+    }
 }

@@ -87,6 +87,8 @@ struct ss_ws_view {
     float* pix_state;       // [2][total_pixels]  (K as float bits, T_end)
     float* grad_rec;        // [total_records][SS_NGRAD]
     uint32_t* cover_masks;  // [8 * max_instances]: per (warp, staged surfel) pixel coverage, forward -> backward
+    float4* env_acc;        // [scenes][env_texels] RGBA accumulators of the env-map gradients (backward)
+    int64_t env_texels;     // irradiance + specular texels per scene
     int64_t max_instances;
 };
 

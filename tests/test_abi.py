@@ -49,17 +49,17 @@ def test_host_side_argument_errors():
     cams[0].fx = cams[0].fy = 10.0
     off = (ctypes.c_int64 * 2)(0, 10)
     d = _lib.ss_batch_desc(1, 1, off, cams, None)
-    assert lib.ss_workspace_size(ctypes.byref(d), ctypes.byref(p), 0, ctypes.byref(nb)) == _lib.SS_ERR_INVALID_ARG
+    assert lib.ss_workspace_size(ctypes.byref(d), ctypes.byref(p), None, 0, ctypes.byref(nb)) == _lib.SS_ERR_INVALID_ARG
     p.max_instances = 1000
-    assert lib.ss_workspace_size(ctypes.byref(d), ctypes.byref(p), 1, ctypes.byref(nb)) == 0 and nb.value > 0
+    assert lib.ss_workspace_size(ctypes.byref(d), ctypes.byref(p), None, 1, ctypes.byref(nb)) == 0 and nb.value > 0
     # views out of scene order, bad scene index, zero views
     d0 = _lib.ss_batch_desc(1, 0, off, cams, None)
-    assert lib.ss_workspace_size(ctypes.byref(d0), ctypes.byref(p), 0, ctypes.byref(nb)) == _lib.SS_ERR_INVALID_ARG
+    assert lib.ss_workspace_size(ctypes.byref(d0), ctypes.byref(p), None, 0, ctypes.byref(nb)) == _lib.SS_ERR_INVALID_ARG
     cams[0].scene = 3
-    assert lib.ss_workspace_size(ctypes.byref(d), ctypes.byref(p), 0, ctypes.byref(nb)) == _lib.SS_ERR_INVALID_ARG
+    assert lib.ss_workspace_size(ctypes.byref(d), ctypes.byref(p), None, 0, ctypes.byref(nb)) == _lib.SS_ERR_INVALID_ARG
     cams[0].scene = 0
     p.k_max = 17
-    assert lib.ss_workspace_size(ctypes.byref(d), ctypes.byref(p), 0, ctypes.byref(nb)) == _lib.SS_ERR_INVALID_ARG
+    assert lib.ss_workspace_size(ctypes.byref(d), ctypes.byref(p), None, 0, ctypes.byref(nb)) == _lib.SS_ERR_INVALID_ARG
     # env descriptor checks
     ed = _lib.ss_env_desc(100, 50, 6, 32, 16)
     a = ctypes.c_int64()
