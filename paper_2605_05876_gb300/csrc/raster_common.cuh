@@ -28,7 +28,7 @@ struct ss_wstage {
     float4 c0[WSLOTS];  // rgb, flags                                         -- covering fragments
     float4 c1[WSLOTS];  // albedo, roughness
     float4 c2[WSLOTS];  // metallic, normal
-    float2 zz[WSLOTS];  // z_start, z_end until the fix-up
+    float4 zr[WSLOTS];  // record row 3 (z_start, z_end, rectangle) until the fix-up
     uint32_t id[WSLOTS];
 };
 
@@ -39,22 +39,24 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
-// One chunk of up to 32 instances: fetched (key, rectangle) of this lane.
+// One chunk of up to 32 instances: this lane's record index and support
+// rectangle, read from the tile list and its parallel rectangle list (both
+// coalesced; the sort kernel gathered the rectangles once per instance).
 struct ss_chunk {
     uint32_t id;
-    float4 r3;
+    uint2 rect;
     bool live;
 };
 
-__device__ __forceinline__ ss_chunk fetch_chunk(const unsigned long long* keys, const ss_rec* recs, int64_t j,
+__device__ __forceinline__ ss_chunk fetch_chunk(const unsigned long long* keys, const uint2* rects, int64_t j,
                                                 int64_t end) {
     ss_chunk c;
     c.live = j < end;
     c.id = 0;
-    c.r3 = make_float4(0.f, 0.f, __uint_as_float(0xffffu), __uint_as_float(0xffffu));
+    c.rect = make_uint2(0xffffu, 0xffffu);   // empty
     if (c.live) {
         c.id = (uint32_t)(__ldg(keys + j) & 0xffffffffull);
-        c.r3 = __ldg(&recs[c.id].r3);
+        c.rect = __ldg(rects + j);
     }
     return c;
 }
@@ -68,7 +70,7 @@ __device__ __forceinline__ int stage_issue(ss_wstage& W, uint2* rect, const ss_c
                                            int lane, int gx0, int gx1, int gy0, int gy1) {
     bool ov = false;
     if (c.live) {
-        uint32_t rx = __float_as_uint(c.r3.z), ry = __float_as_uint(c.r3.w);
+        const uint32_t rx = c.rect.x, ry = c.rect.y;
         int i0 = rx & 0xffff, i1 = rx >> 16, j0 = ry & 0xffff, j1 = ry >> 16;
         ov = i0 <= gx1 && i1 >= gx0 && j0 <= gy1 && j1 >= gy0;
     }
@@ -82,8 +84,8 @@ __device__ __forceinline__ int stage_issue(ss_wstage& W, uint2* rect, const ss_c
         cp_async16(&W.c0[pos], &rc->r4);
         cp_async16(&W.c1[pos], &rc->r5);
         cp_async16(&W.c2[pos], &rc->r6);
-        W.zz[pos] = make_float2(c.r3.x, c.r3.y);
-        if (RECT) rect[pos] = make_uint2(__float_as_uint(c.r3.z), __float_as_uint(c.r3.w));
+        cp_async16(&W.zr[pos], &rc->r3);
+        if (RECT) rect[pos] = c.rect;
         W.id[pos] = c.id;
     }
     cp_async_commit();
@@ -95,7 +97,7 @@ __device__ __forceinline__ int stage_issue(ss_wstage& W, uint2* rect, const ss_c
 __device__ __forceinline__ void stage_prefetch(const ss_chunk& c, const ss_rec* recs, int gx0, int gx1, int gy0,
                                                int gy1) {
     if (!c.live) return;
-    uint32_t rx = __float_as_uint(c.r3.z), ry = __float_as_uint(c.r3.w);
+    const uint32_t rx = c.rect.x, ry = c.rect.y;
     int i0 = rx & 0xffff, i1 = rx >> 16, j0 = ry & 0xffff, j1 = ry >> 16;
     if (i0 <= gx1 && i1 >= gx0 && j0 <= gy1 && j1 >= gy0) {
         const char* p = reinterpret_cast<const char*>(recs + c.id);
@@ -113,7 +115,7 @@ __device__ __forceinline__ void stage_finish(ss_wstage& W, int n, int lane, floa
     if (lane < n) {
         const float4 r1 = W.h1[lane], r2 = W.h2[lane];
         const uint32_t fl = __float_as_uint(W.c0[lane].w);
-        const float2 z = W.zz[lane];
+        const float4 z = W.zr[lane];
         const float prx = __fadd_rn(__fsub_rn(r2.x, tx0), r2.z);
         const float pry = __fadd_rn(__fsub_rn(r2.y, ty0), r2.w);
         W.h1[lane] = make_float4(r1.x, r1.y, prx, pry);

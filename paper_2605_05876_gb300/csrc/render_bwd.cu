@@ -169,8 +169,8 @@ __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kerne
     int64_t beg = ws.tile_start[tile], end = ws.tile_start[tile + 1];
     if (end > cap) end = cap;
     if (beg > end) beg = end;
-    const ss_rec* recs = ws.rec + vl.rec_off;
-    float* grad = ws.grad_rec + vl.rec_off * SS_NGRAD;
+    const ss_rec* recs = ws.rec;   // keys hold batch-wide record indices
+    float* grad = ws.grad_rec;
     const uint32_t* masks = ws.cover_masks + 8 * beg + (int64_t)warp * (end - beg);
 
     // Differentiate every recorded fragment, 32 at a time (one per lane), then
@@ -248,13 +248,13 @@ __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kerne
 
     // one staging buffer (shared memory for three CTAs per SM); the records
     // of the next chunk are prefetched into L2 instead
-    ss_chunk nxt = fetch_chunk(ws.keys, recs, beg + lane, end);
+    ss_chunk nxt = fetch_chunk(ws.keys, ws.rects, beg + lane, end);
     for (int64_t base = beg; base < end; base += 32) {
         if (__all_sync(0xffffffffu, done)) break;
         const int n = stage_issue<false>(*Wc, nullptr, nxt, recs, lane, gx0, gx1, gy0, gy1);
         const uint32_t cm = lane < n ? masks[lane] : 0u;   // forward coverage of slot `lane`
         masks += n;
-        nxt = fetch_chunk(ws.keys, recs, base + 32 + lane, end);
+        nxt = fetch_chunk(ws.keys, ws.rects, base + 32 + lane, end);
         stage_prefetch(nxt, recs, gx0, gx1, gy0, gy1);
         stage_finish(*Wc, n, lane, (float)x0, (float)y0);
         uint32_t nz = __ballot_sync(0xffffffffu, cm != 0u);

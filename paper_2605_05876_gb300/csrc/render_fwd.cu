@@ -318,7 +318,9 @@ __global__ void __launch_bounds__(256) scatter_kernel(ss_ws_view ws, int64_t tot
     const int tx0 = (int)(rx & 0xffff) / SS_TILE, tx1 = (int)(rx >> 16) / SS_TILE;
     const int ty0 = (int)(ry & 0xffff) / SS_TILE, ty1 = (int)(ry >> 16) / SS_TILE;
     const int ntx = tx1 - tx0 + 1, nt = ntx * (ty1 - ty0 + 1);
-    const unsigned long long key = ((unsigned long long)__float_as_uint(r3.x) << 32) | (uint32_t)(r - vl.rec_off);
+    // low half: the batch-wide record index (ties of z_start in one tile, which
+    // belongs to one view, are broken by surfel index all the same)
+    const unsigned long long key = ((unsigned long long)__float_as_uint(r3.x) << 32) | (uint32_t)r;
     for (int b = 0; b < nt; b += 4) {
         int t[4];
         uint32_t pos[4];
@@ -337,21 +339,30 @@ __global__ void __launch_bounds__(256) scatter_kernel(ss_ws_view ws, int64_t tot
     }
 }
 
+// support rectangle of the record a key refers to
+__device__ __forceinline__ uint2 rect_of(const ss_ws_view& ws, unsigned long long key) {
+    const float4 r3 = __ldg(&ws.rec[(uint32_t)(key & 0xffffffffull)].r3);
+    return make_uint2(__float_as_uint(r3.z), __float_as_uint(r3.w));
+}
+
 #define SORT_THREADS 512
 #define SORT_CAP 8192  // keys sorted in shared memory at once (64 KB)
 
+// Bitonic sort of npow2 keys in shared memory: every thread takes whole
+// compare-exchange pairs (i, i + j), i with bit j clear, so no iteration is
+// spent on the upper element of a pair.
 __device__ void bitonic_smem(unsigned long long* s, int npow2) {
+    const int half = npow2 >> 1;
     for (int k = 2; k <= npow2; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < npow2; i += blockDim.x) {
-                int ixj = i ^ j;
-                if (ixj > i) {
-                    unsigned long long a = s[i], b = s[ixj];
-                    bool up = (i & k) == 0;
-                    if ((a > b) == up) {
-                        s[i] = b;
-                        s[ixj] = a;
-                    }
+            for (int c = threadIdx.x; c < half; c += blockDim.x) {
+                const int i = ((c & ~(j - 1)) << 1) | (c & (j - 1));   // insert a 0 at bit log2(j)
+                const int ixj = i | j;
+                const unsigned long long a = s[i], b = s[ixj];
+                const bool up = (i & k) == 0;
+                if ((a > b) == up) {
+                    s[i] = b;
+                    s[ixj] = a;
                 }
             }
             __syncthreads();
@@ -388,8 +399,12 @@ __global__ void __launch_bounds__(SORT_THREADS) tile_sort_kernel(ss_ws_view ws, 
     if (e > cap) e = cap;
     if (b >= e) return;
     const int n = (int)(e - b);
-    if (n == 1) return;
     unsigned long long* K = ws.keys + b;
+    uint2* RC = ws.rects + b;
+    if (n == 1) {
+        if (threadIdx.x == 0) RC[0] = rect_of(ws, K[0]);
+        return;
+    }
     unsigned long long* Alt = ws.keys_alt + b;
     // chunks of SORT_CAP sorted in shared memory
     for (int c0 = 0; c0 < n; c0 += SORT_CAP) {
@@ -399,7 +414,10 @@ __global__ void __launch_bounds__(SORT_THREADS) tile_sort_kernel(ss_ws_view ws, 
         for (int i = threadIdx.x; i < p2; i += blockDim.x) sk[i] = i < m ? K[c0 + i] : ~0ull;
         __syncthreads();
         bitonic_smem(sk, p2);
-        for (int i = threadIdx.x; i < m; i += blockDim.x) K[c0 + i] = sk[i];
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            K[c0 + i] = sk[i];
+            if (n <= SORT_CAP) RC[i] = rect_of(ws, sk[i]);
+        }
         __syncthreads();
     }
     if (n <= SORT_CAP) return;
@@ -419,8 +437,10 @@ __global__ void __launch_bounds__(SORT_THREADS) tile_sort_kernel(ss_ws_view ws, 
         src = dst;
         dst = tmp;
     }
-    if (src != K) {
-        for (int i = threadIdx.x; i < n; i += blockDim.x) K[i] = src[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const unsigned long long k = src[i];
+        if (src != K) K[i] = k;
+        RC[i] = rect_of(ws, k);
     }
 }
 
@@ -520,7 +540,7 @@ __global__ void __launch_bounds__(32 * RWPB_FWD, 24 / RWPB_FWD) raster_fwd_kerne
     int64_t beg = ws.tile_start[tile], end = ws.tile_start[tile + 1];
     if (end > cap) end = cap;
     if (beg > end) beg = end;
-    const ss_rec* recs = ws.rec + vl.rec_off;
+    const ss_rec* recs = ws.rec;   // keys hold batch-wide record indices
     // coverage masks for the backward pass: one word per (warp, staged surfel)
     // in staging order, in the warp's own region of 8 x the tile's list
     uint32_t* masks = ws.cover_masks ? ws.cover_masks + 8 * beg + (int64_t)warp * (end - beg) : nullptr;
@@ -528,9 +548,9 @@ __global__ void __launch_bounds__(32 * RWPB_FWD, 24 / RWPB_FWD) raster_fwd_kerne
     uint2* Rb = Wrect + 2 * lw * WSLOTS;
     int buf = 0, n_next = 0;
     if (beg < end)
-        n_next = stage_issue<true>(Wb[0], Rb, fetch_chunk(ws.keys, recs, beg + lane, end), recs, lane, gx0, gx1,
+        n_next = stage_issue<true>(Wb[0], Rb, fetch_chunk(ws.keys, ws.rects, beg + lane, end), recs, lane, gx0, gx1,
                                    gy0, gy1);
-    ss_chunk nxt = fetch_chunk(ws.keys, recs, beg + 32 + lane, end);
+    ss_chunk nxt = fetch_chunk(ws.keys, ws.rects, beg + 32 + lane, end);
     for (int64_t base = beg; base < end; base += 32) {
         if (__all_sync(0xffffffffu, done)) break;   // every pixel of the block has K_max layers
         ss_wstage& W = Wb[buf];
@@ -538,7 +558,7 @@ __global__ void __launch_bounds__(32 * RWPB_FWD, 24 / RWPB_FWD) raster_fwd_kerne
         const int n = n_next;
         stage_finish(W, n, lane, (float)x0, (float)y0);
         n_next = stage_issue<true>(Wb[buf ^ 1], Rb + (buf ^ 1) * WSLOTS, nxt, recs, lane, gx0, gx1, gy0, gy1);
-        nxt = fetch_chunk(ws.keys, recs, base + 64 + lane, end);
+        nxt = fetch_chunk(ws.keys, ws.rects, base + 64 + lane, end);
         uint32_t my_mask = 0;
         for (int s = 0; s < n; ++s) {
             const float4 h0 = W.h0[s], h1 = W.h1[s], h2 = W.h2[s];
