@@ -157,6 +157,16 @@ def recorded_traffic(kernel: str, workload: str):
     return None
 
 
+def describe(scene, name: str) -> str:
+    """The workload in words: surfels, scenes, views and their sizes, env size."""
+    sizes = sorted({(c.width, c.height) for c in scene.cameras})
+    He, We, _ = scene.envs[0].shape
+    what = {"displaced_sphere_1m": "surfels on a displaced sphere (amp 0.05, freq 8)",
+            "uneven_scenes": "surfels in spheres and torus-sphere pairs of log-uniform size"}.get(name, "surfels")
+    return (f"{name}: {scene.surfels.n:,} {what}, {scene.n_scenes} scene(s), {len(scene.cameras)} views of "
+            + "/".join(f"{w}x{h}" for w, h in sizes) + f", env {We}x{He}")
+
+
 def cpu_baseline(scene, rows: int, grad: bool = True):
     """The FP64 oracle as it stands, on a bounded sample of the workload: the
     pixel rows of view 0 through the image centre, forward and backward,
@@ -203,7 +213,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "views/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.config}: 1M surfels displaced sphere, 16 views 800x800, env 512x256",
+            "config": {"workload": describe(scene, args.config),
                        "inputs_vs_l2": "host memory"},
             "cpu_baseline": {"value": v, "unit": "views/s", "cores": last["cores"], "kind": "oracle",
                              "sample": last["sample"]},
@@ -397,8 +407,7 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": "views/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": f"{args.config}: 1M surfels displaced sphere (amp 0.05, freq 8), "
-                                       f"{V} views 800x800, env 512x256, batched in one launch per stage",
+                "config": {"workload": describe(scene, args.config) + ", batched in one launch per stage",
                            "inputs_vs_l2": "inputs and intermediates > 129 MB L2 (no flush)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "per_view": per_view, "graph": graph, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,

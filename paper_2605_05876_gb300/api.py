@@ -284,3 +284,54 @@ def loss_l1(out, target, d_out, loss, scale: float = 1.0):
     """loss[0] = scale * sum|out - target|, d_out = scale * sign(out - target) (device tensors)."""
     check(lib().ss_loss_l1(_ptr(out), _ptr(target), out.numel(), float(scale), _ptr(d_out), _ptr(loss), _stream()),
           "ss_loss_l1")
+
+
+# ------------------------------------------------------------------------
+# autograd
+
+class RenderFunction:
+    """``torch.autograd.Function`` over a Renderer: forward renders RGBA and
+    AOVs from the renderer's surfel parameters and environment map; backward
+    calls ss_render_backward and ss_env_prefilter_backward and returns the
+    gradients of the surfel parameters and of the base env map.
+
+        rgba, aov = render(renderer, pos, quat, log_scale, albedo, roughness, metallic, env)
+
+    The tensors passed in must be the renderer's own parameter tensors (the
+    library reads them by pointer); their .grad receives the gradients."""
+
+    @staticmethod
+    def build():
+        import torch
+
+        class _F(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, r, *tensors):
+                for k, t in zip(SURFEL_FIELDS + ("env",), tensors):
+                    own = r.env if k == "env" else r.params_t[k]
+                    if t.data_ptr() != own.data_ptr():
+                        raise ValueError(f"{k}: pass the renderer's own tensor")
+                r.prefilter_env()
+                rgba, aov = r.forward()
+                ctx.r = r
+                return rgba.clone(), aov.clone()
+
+            @staticmethod
+            def backward(ctx, d_rgba, d_aov):
+                r = ctx.r
+                r.zero_grads()
+                r.backward(d_rgba.contiguous(), d_aov.contiguous() if d_aov is not None else None)
+                return (None,) + tuple(r.grads[k].clone() for k in SURFEL_FIELDS) + (r.d_env.clone(),)
+
+        return _F
+
+
+_RENDER_FN = None
+
+
+def render(r: "Renderer", *tensors):
+    """Differentiable render (see RenderFunction)."""
+    global _RENDER_FN
+    if _RENDER_FN is None:
+        _RENDER_FN = RenderFunction.build()
+    return _RENDER_FN.apply(r, *tensors)
