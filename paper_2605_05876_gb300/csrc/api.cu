@@ -172,7 +172,8 @@ static ss_status build_layout(const ss_batch_desc* b, const ss_render_params* p,
 }
 
 struct ws_plan {
-    size_t status, layout, vgeo, rec, tc, ts, tcur, keys, keys_alt, rects, layer, pix, grad, masks, env_acc, total;
+    size_t status, layout, vgeo, rec, tc, ts, tcur, keys, keys_alt, rects, layer, pix, grad, masks, mcount, env_acc,
+        total;
     int64_t env_texels;   // irradiance + specular texels of one scene (0: no env-gradient scratch)
 };
 
@@ -199,10 +200,11 @@ static ws_plan plan_ws(const ss_layout& L, const ss_render_params& p, int with_b
         w.layer = take(sizeof(float) * (size_t)p.k_max * 13 * (size_t)L.total_pixels);
         w.pix = take(sizeof(float) * 2 * (size_t)L.total_pixels);
         w.grad = take(sizeof(float) * SS_NGRAD * (size_t)L.total_records);
-        w.masks = take(sizeof(uint32_t) * 8 * (size_t)p.max_instances);
+        w.masks = take(sizeof(uint2) * 8 * (size_t)p.max_instances);
+        w.mcount = take(sizeof(uint32_t) * 8 * (size_t)L.total_tiles);
         w.env_acc = take(sizeof(float4) * (size_t)w.env_texels * (size_t)L.n_scenes);
     } else {
-        w.layer = w.pix = w.grad = w.masks = w.env_acc = 0;
+        w.layer = w.pix = w.grad = w.masks = w.mcount = w.env_acc = 0;
     }
     w.total = o;
     return w;
@@ -225,7 +227,8 @@ static ss_ws_view carve(void* ws, const ws_plan& w, const ss_render_params& p, i
     v.layer_state = with_bwd ? (float*)(b + w.layer) : nullptr;
     v.pix_state = with_bwd ? (float*)(b + w.pix) : nullptr;
     v.grad_rec = with_bwd ? (float*)(b + w.grad) : nullptr;
-    v.cover_masks = with_bwd ? (uint32_t*)(b + w.masks) : nullptr;
+    v.cover_list = with_bwd ? (uint2*)(b + w.masks) : nullptr;
+    v.cover_count = with_bwd ? (uint32_t*)(b + w.mcount) : nullptr;
     v.env_acc = (with_bwd && w.env_texels) ? (float4*)(b + w.env_acc) : nullptr;
     v.env_texels = w.env_texels;
     v.max_instances = p.max_instances;

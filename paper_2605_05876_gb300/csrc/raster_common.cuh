@@ -92,6 +92,23 @@ __device__ __forceinline__ int stage_issue(ss_wstage& W, uint2* rect, const ss_c
     return __popc(mask);
 }
 
+// Issue the copies of record `id` into slot `lane` of W (lanes with
+// active), for lists that are already filtered.
+__device__ __forceinline__ void stage_ids(ss_wstage& W, const ss_rec* recs, uint32_t id, int lane, bool active) {
+    if (active) {
+        const ss_rec* rc = recs + id;
+        cp_async16(&W.h0[lane], &rc->r0);
+        cp_async16(&W.h1[lane], &rc->r1);
+        cp_async16(&W.h2[lane], &rc->r2);
+        cp_async16(&W.c0[lane], &rc->r4);
+        cp_async16(&W.c1[lane], &rc->r5);
+        cp_async16(&W.c2[lane], &rc->r6);
+        cp_async16(&W.zr[lane], &rc->r3);
+        W.id[lane] = id;
+    }
+    cp_async_commit();
+}
+
 // Ask L2 for the records of the instances of chunk c that stage_issue will
 // copy (same overlap test), so that their copies wait less.
 __device__ __forceinline__ void stage_prefetch(const ss_chunk& c, const ss_rec* recs, int gx0, int gx1, int gy0,

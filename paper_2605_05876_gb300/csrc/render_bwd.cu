@@ -137,7 +137,6 @@ __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kerne
     const int lx = wx0 + (lane & 7), ly = wy0 + (lane >> 3);
     const int px = x0 + lx, py = y0 + ly;
     const bool inside = px < vl.width && py < vl.height;
-    const int gx0 = x0 + wx0, gx1 = gx0 + 7, gy0 = y0 + wy0, gy1 = gy0 + 3;
     const float rc2 = a.f.p.r_cut * a.f.p.r_cut;
     const int64_t P = L->total_pixels;
     const int64_t gpix = vl.pixel_off + (int64_t)(inside ? py : 0) * vl.width + (inside ? px : 0);
@@ -171,7 +170,9 @@ __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kerne
     if (beg > end) beg = end;
     const ss_rec* recs = ws.rec;   // keys hold batch-wide record indices
     float* grad = ws.grad_rec;
-    const uint32_t* masks = ws.cover_masks + 8 * beg + (int64_t)warp * (end - beg);
+    // the forward pass's list of covering staged surfels of this warp
+    const uint2* clist = ws.cover_list + 8 * beg + (int64_t)warp * (end - beg);
+    const int64_t n_list = ws.cover_count[(int64_t)tile * 8 + warp];
 
     // Differentiate every recorded fragment, 32 at a time (one per lane), then
     // sum the gradient rows of each run of equal surfels and add the sums.
@@ -246,17 +247,21 @@ __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kerne
         pend = false;
     };
 
-    // one staging buffer (shared memory for three CTAs per SM); the records
-    // of the next chunk are prefetched into L2 instead
-    ss_chunk nxt = fetch_chunk(ws.keys, ws.rects, beg + lane, end);
-    for (int64_t base = beg; base < end; base += 32) {
+    // one staging buffer; the records of the next chunk are prefetched into L2
+    uint2 nxt = lane < n_list ? __ldg(clist + lane) : make_uint2(0u, 0u);
+    for (int64_t base = 0; base < n_list; base += 32) {
         if (__all_sync(0xffffffffu, done)) break;
-        const int n = stage_issue<false>(*Wc, nullptr, nxt, recs, lane, gx0, gx1, gy0, gy1);
-        const uint32_t cm = lane < n ? masks[lane] : 0u;   // forward coverage of slot `lane`
-        masks += n;
-        nxt = fetch_chunk(ws.keys, ws.rects, base + 32 + lane, end);
-        stage_prefetch(nxt, recs, gx0, gx1, gy0, gy1);
+        const int n = (int)min((int64_t)32, n_list - base);
+        const uint2 cur = nxt;
+        stage_ids(*Wc, recs, cur.x, lane, lane < n);
+        nxt = base + 32 + lane < n_list ? __ldg(clist + base + 32 + lane) : make_uint2(0u, 0u);
+        if (base + 32 + lane < n_list) {
+            const char* pr = reinterpret_cast<const char*>(recs + nxt.x);
+            asm volatile("prefetch.global.L2 [%0];\n" ::"l"(pr));
+            asm volatile("prefetch.global.L2 [%0];\n" ::"l"(pr + sizeof(ss_rec) - 1));
+        }
         stage_finish(*Wc, n, lane, (float)x0, (float)y0);
+        const uint32_t cm = lane < n ? cur.y : 0u;   // forward coverage of slot `lane`
         uint32_t nz = __ballot_sync(0xffffffffu, cm != 0u);
         while (nz) {
             const int s = __ffs(nz) - 1;

@@ -541,9 +541,11 @@ __global__ void __launch_bounds__(32 * RWPB_FWD, 24 / RWPB_FWD) raster_fwd_kerne
     if (end > cap) end = cap;
     if (beg > end) beg = end;
     const ss_rec* recs = ws.rec;   // keys hold batch-wide record indices
-    // coverage masks for the backward pass: one word per (warp, staged surfel)
-    // in staging order, in the warp's own region of 8 x the tile's list
-    uint32_t* masks = ws.cover_masks ? ws.cover_masks + 8 * beg + (int64_t)warp * (end - beg) : nullptr;
+    // the backward pass's fragment list: (record, coverage word) of every
+    // staged surfel that covers a pixel of this block, in list order, in the
+    // warp's own region of 8 x the tile's list
+    uint2* clist = ws.cover_list ? ws.cover_list + 8 * beg + (int64_t)warp * (end - beg) : nullptr;
+    uint32_t n_list = 0;
     ss_wstage* Wb = Wst + 2 * lw;
     uint2* Rb = Wrect + 2 * lw * WSLOTS;
     int buf = 0, n_next = 0;
@@ -592,12 +594,17 @@ __global__ void __launch_bounds__(32 * RWPB_FWD, 24 / RWPB_FWD) raster_fwd_kerne
                 }
             }
         }
-        if (masks && lane < n) masks[lane] = my_mask;
-        if (masks) masks += n;
+        if (clist) {
+            const bool keep = lane < n && my_mask != 0u;
+            const uint32_t km = __ballot_sync(0xffffffffu, keep);
+            if (keep) clist[n_list + __popc(km & ((1u << lane) - 1u))] = make_uint2(W.id[lane], my_mask);
+            n_list += __popc(km);
+        }
         buf ^= 1;
         __syncwarp();
     }
     cp_async_wait0();   // copies of a chunk an early exit left unread
+    if (clist && lane == 0) ws.cover_count[(int64_t)tile * 8 + warp] = n_list;
     if (!done && Wg > 0.f) flush();
     if (STATS) {
         unsigned long long v[4] = {n_rect, n_lane, n_frag, (unsigned)K * (inside ? 1u : 0u)};

@@ -87,7 +87,9 @@ struct ss_ws_view {
     float* layer_state;     // [k_max][13][total_pixels]  (raw C (12), W)
     float* pix_state;       // [2][total_pixels]  (K as float bits, T_end)
     float* grad_rec;        // [total_records][SS_NGRAD]
-    uint32_t* cover_masks;  // [8 * max_instances]: per (warp, staged surfel) pixel coverage, forward -> backward
+    uint2* cover_list;      // [8 * max_instances]: per warp, (record, 32-pixel coverage word) of every staged
+                            // surfel that covers a pixel of the warp's block, in list order (forward -> backward)
+    uint32_t* cover_count;  // [8 * tiles]: entries of each warp's list
     float4* env_acc;        // [scenes][env_texels] RGBA accumulators of the env-map gradients (backward)
     int64_t env_texels;     // irradiance + specular texels per scene
     int64_t max_instances;
