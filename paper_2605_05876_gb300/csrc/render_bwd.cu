@@ -388,11 +388,9 @@ __device__ __forceinline__ void uv_grad(const float d[3], float gu, float gv, fl
     out[2] += kv * (-d[1] * d[2]);
 }
 
-// One thread per (view, surfel) record: the record's raster gradient is
-// chained back to the surfel parameters, and the 14 parameter gradients of
-// this view overwrite the first 14 floats of the record (a per-surfel kernel
-// then sums them over the views, in a fixed order).
-#define PG_N 14   // pos 3, quat 4, log_scale 2, albedo 3, roughness, metallic
+// One thread per surfel: the raster gradient record of each of its views is
+// chained back to the surfel parameters; the views are summed in order
+// (deterministic) and added to the caller's gradients.
 
 // Shared-memory copies of the environment gradients of one scene: the
 // irradiance map and the specular levels from `level` on (the small, most
@@ -406,33 +404,10 @@ struct env_priv {
     int64_t spec_off;  // offset of level `level` inside one scene's spec stack
 };
 
-__device__ __forceinline__ void pbwd_record(const ss_ws_view& ws, const ss_bwd_args& A, const int64_t r,
-                                            const env_priv& pv) {
+__device__ __forceinline__ void pbwd_surfel(const ss_ws_view& ws, const ss_bwd_args& A, const int64_t i,
+                                            const int scene, const env_priv& pv) {
     const ss_layout* L = ws.layout;
     const ss_fwd_args& a = A.f;
-    int v = 0;
-    {
-        int lo = 0, hi = L->n_views - 1;
-        while (lo < hi) {
-            int m = (lo + hi + 1) >> 1;
-            if (L->v[m].rec_off <= r) lo = m;
-            else hi = m - 1;
-        }
-        v = lo;
-    }
-    const ss_view_layout& vl = L->v[v];
-    const int scene = vl.scene;
-    const int64_t i = vl.surfel_begin + (r - vl.rec_off);
-    const uint32_t flags = __float_as_uint(ws.rec[r].r4.w);
-    if (!(flags & SS_FLAG_VALID)) return;
-    float* gr = ws.grad_rec + r * SS_NGRAD;
-    float G[G_N];
-    bool any = false;
-    for (int k = 0; k < G_N; ++k) {
-        G[k] = gr[k];
-        any = any || (G[k] != 0.f);
-    }
-    if (!any) return;
     const float c[3] = {a.s.pos[i * 3], a.s.pos[i * 3 + 1], a.s.pos[i * 3 + 2]};
     const float4 q4 = *reinterpret_cast<const float4*>(a.s.quat + i * 4);
     const float2 ls = *reinterpret_cast<const float2*>(a.s.log_scale + i * 2);
@@ -455,10 +430,25 @@ __device__ __forceinline__ void pbwd_record(const ss_ws_view& ws, const ss_bwd_a
     const int lutn = a.p.lut_n;
     const float* LUT = a.env.lut;
 
-    // parameter gradients of this view
+    // parameter gradients, summed over the scene's views in order
     float gc[3] = {0, 0, 0}, gRq[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, gsu = 0.f, gsv = 0.f;
     float grho[3] = {0, 0, 0}, grough = 0.f, gmetal = 0.f;
-    {
+    bool any_view = false;
+    for (int v = L->scene_view_begin[scene]; v < L->scene_view_begin[scene + 1]; ++v) {
+        const ss_view_layout& vl = L->v[v];
+        const int64_t r = vl.rec_off + (i - vl.surfel_begin);
+        const uint32_t flags = __float_as_uint(ws.rec[r].r4.w);
+        if (!(flags & SS_FLAG_VALID)) continue;
+        const float* gr = ws.grad_rec + r * SS_NGRAD;
+        float G[G_N];
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < G_N; ++k) {
+            G[k] = gr[k];
+            any = any || (G[k] != 0.f);
+        }
+        if (!any) continue;
+        any_view = true;
         const ss_camera& cam = a.cams[v];
         const float* Rc = cam.R;
         const float fx = cam.fx, fy = cam.fy;
@@ -675,7 +665,8 @@ __device__ __forceinline__ void pbwd_record(const ss_ws_view& ws, const ss_bwd_a
             gc[k] += dcv[k];
         }
     }
-    // ---- R(q / |q|) -> q
+    if (!any_view) return;
+    // ---- R(q / |q|) -> q (linear in the summed dL/dR)
     const float qn = rsqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
     const float w = q4.x * qn, x = q4.y * qn, y = q4.z * qn, z = q4.w * qn;
     const float* d = gRq;
@@ -684,32 +675,45 @@ __device__ __forceinline__ void pbwd_record(const ss_ws_view& ws, const ss_bwd_a
     const float gy = 2.f * (-2.f * y * d[0] + x * d[1] + w * d[2] + x * d[3] + z * d[5] - w * d[6] + z * d[7] - 2.f * y * d[8]);
     const float gz = 2.f * (-2.f * z * d[0] - w * d[1] + x * d[2] + w * d[3] - 2.f * z * d[4] + y * d[5] + x * d[6] + y * d[7]);
     const float dotq = gw * w + gx * x + gy * y + gz * z;
-    float out[PG_N] = {gc[0], gc[1], gc[2], (gw - w * dotq) * qn, (gx - x * dotq) * qn, (gy - y * dotq) * qn,
-                       (gz - z * dotq) * qn, gsu * su, gsv * sv, grho[0], grho[1], grho[2], grough, gmetal};
-    for (int k = 0; k < PG_N; ++k) gr[k] = out[k];
+    const ss_surfel_grads& g = A.g;
+    if (g.pos)
+        for (int k = 0; k < 3; ++k) g.pos[i * 3 + k] += gc[k];
+    if (g.quat) {
+        g.quat[i * 4 + 0] += (gw - w * dotq) * qn;
+        g.quat[i * 4 + 1] += (gx - x * dotq) * qn;
+        g.quat[i * 4 + 2] += (gy - y * dotq) * qn;
+        g.quat[i * 4 + 3] += (gz - z * dotq) * qn;
+    }
+    if (g.log_scale) {
+        g.log_scale[i * 2 + 0] += gsu * su;
+        g.log_scale[i * 2 + 1] += gsv * sv;
+    }
+    if (g.albedo)
+        for (int k = 0; k < 3; ++k) g.albedo[i * 3 + k] += grho[k];
+    if (g.roughness) g.roughness[i] += grough;
+    if (g.metallic) g.metallic[i] += gmetal;
 }
 
-// One CTA per contiguous block of records; env gradients of the block's
+// One CTA per contiguous block of surfels; env gradients of the block's
 // first scene are accumulated in shared memory and flushed once.
-__global__ void __launch_bounds__(128, 4) project_bwd_kernel(ss_ws_view ws, ss_bwd_args A, int64_t n_records,
+__global__ void __launch_bounds__(128, 4) project_bwd_kernel(ss_ws_view ws, ss_bwd_args A, int64_t n_surfels,
                                                             int64_t per_block, int priv_level, int64_t priv_spec_off,
                                                             int priv_spec_floats) {
     extern __shared__ float priv[];
     const ss_layout* L = ws.layout;
-    const int64_t r0 = blockIdx.x * per_block;
-    if (r0 >= n_records) return;
-    const int64_t r1 = min(n_records, r0 + per_block);
-    int v0 = 0;
-    {
-        int lo = 0, hi = L->n_views - 1;
+    const int64_t i0 = blockIdx.x * per_block;
+    if (i0 >= n_surfels) return;
+    const int64_t i1 = min(n_surfels, i0 + per_block);
+    auto scene_of = [&](int64_t i) {
+        int lo = 0, hi = L->n_scenes - 1;
         while (lo < hi) {
             int m = (lo + hi + 1) >> 1;
-            if (L->v[m].rec_off <= r0) lo = m;
+            if (L->scene_begin[m] <= i) lo = m;
             else hi = m - 1;
         }
-        v0 = lo;
-    }
-    const int scene = L->v[v0].scene;
+        return lo;
+    };
+    const int scene = scene_of(i0);
     const int irr_floats = A.f.ed.irr_width * A.f.ed.irr_height * 3;
     const bool use = A.genv.irr != nullptr && A.genv.spec != nullptr;
     env_priv pv;
@@ -722,7 +726,8 @@ __global__ void __launch_bounds__(128, 4) project_bwd_kernel(ss_ws_view ws, ss_b
     if (use)
         for (int k = threadIdx.x; k < n_priv; k += blockDim.x) priv[k] = 0.f;
     __syncthreads();
-    for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) pbwd_record(ws, A, r, pv);
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x)
+        pbwd_surfel(ws, A, i, i < L->scene_begin[scene + 1] ? scene : scene_of(i), pv);
     __syncthreads();
     if (use) {   // texel by texel into the RGBA accumulators
         float4* acc = ws.env_acc + scene * ws.env_texels;
@@ -751,38 +756,6 @@ __global__ void env_acc_flush_kernel(const float4* acc, int64_t texels, int64_t 
     d[2] += v.z;
 }
 
-// Sum the per-view parameter gradients of each surfel (views in order) and
-// add them to the caller's gradients.
-__global__ void __launch_bounds__(256) param_reduce_kernel(ss_ws_view ws, ss_surfel_grads g, int64_t n_total) {
-    const ss_layout* L = ws.layout;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n_total) return;
-    int scene = 0;
-    while (scene + 1 < L->n_scenes && i >= L->scene_begin[scene + 1]) ++scene;
-    float acc[PG_N];
-    for (int k = 0; k < PG_N; ++k) acc[k] = 0.f;
-    for (int v = L->scene_view_begin[scene]; v < L->scene_view_begin[scene + 1]; ++v) {
-        const ss_view_layout& vl = L->v[v];
-        const float* gr = ws.grad_rec + (vl.rec_off + (i - vl.surfel_begin)) * SS_NGRAD;
-        const float4 a0 = *reinterpret_cast<const float4*>(gr), a1 = *reinterpret_cast<const float4*>(gr + 4),
-                     a2 = *reinterpret_cast<const float4*>(gr + 8), a3 = *reinterpret_cast<const float4*>(gr + 12);
-        acc[0] += a0.x; acc[1] += a0.y; acc[2] += a0.z; acc[3] += a0.w;
-        acc[4] += a1.x; acc[5] += a1.y; acc[6] += a1.z; acc[7] += a1.w;
-        acc[8] += a2.x; acc[9] += a2.y; acc[10] += a2.z; acc[11] += a2.w;
-        acc[12] += a3.x; acc[13] += a3.y;
-    }
-    if (g.pos)
-        for (int k = 0; k < 3; ++k) g.pos[i * 3 + k] += acc[k];
-    if (g.quat)
-        for (int k = 0; k < 4; ++k) g.quat[i * 4 + k] += acc[3 + k];
-    if (g.log_scale)
-        for (int k = 0; k < 2; ++k) g.log_scale[i * 2 + k] += acc[7 + k];
-    if (g.albedo)
-        for (int k = 0; k < 3; ++k) g.albedo[i * 3 + k] += acc[9 + k];
-    if (g.roughness) g.roughness[i] += acc[12];
-    if (g.metallic) g.metallic[i] += acc[13];
-}
-
 void ss_launch_project_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st) {
     int64_t n = L.scene_begin[L.n_scenes];
     if (n <= 0 || L.total_records <= 0) return;
@@ -803,8 +776,8 @@ void ss_launch_project_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bw
         ss_env_level_size(&a.f.ed, i, &W, &H);
         spec_off += (int64_t)W * H * 3;
     }
-    const int64_t per_block = 128 * 32;
-    const unsigned blocks = (unsigned)((L.total_records + per_block - 1) / per_block);
+    const int64_t per_block = 128;   // surfels per CTA (each with all its views)
+    const unsigned blocks = (unsigned)((n + per_block - 1) / per_block);
     const size_t smem = sizeof(float) * (size_t)(irr_floats + priv_spec);
     static bool attr = false;
     if (!attr) {
@@ -812,9 +785,7 @@ void ss_launch_project_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bw
         attr = true;
     }
     ss_note_launch();
-    project_bwd_kernel<<<blocks, 128, smem, st>>>(ws, a, L.total_records, per_block, level, spec_off, (int)priv_spec);
-    ss_note_launch();
-    param_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ws, a.g, n);
+    project_bwd_kernel<<<blocks, 128, smem, st>>>(ws, a, n, per_block, level, spec_off, (int)priv_spec);
     if ((a.genv.irr || a.genv.spec) && ws.env_acc) {
         const int64_t total = ws.env_texels * L.n_scenes;
         ss_note_launch();
