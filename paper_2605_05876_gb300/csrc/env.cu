@@ -399,7 +399,9 @@ __global__ void __launch_bounds__(256) envconv_fwd_kernel(const float* __restric
     cluster.sync();   // peers keep their shared memory until the leader has read it
 }
 
-// box average of the base map into a level-sized source
+// box average of a map (the base map, or the previous level's source) into a
+// level-sized source; averages of block averages are the block average of
+// the base map, since every level's blocks tile the previous level's
 __global__ void box_down_kernel(const float* env, int64_t env_stride, int We, int He, float* out,
                                 int64_t out_stride, int W, int H) {
     int e = blockIdx.y;
@@ -569,15 +571,19 @@ __global__ void __launch_bounds__(256) envconv_bwd_kernel(const float* __restric
                 t1 += pc[o * 3 + 1];
                 t2 += pc[o * 3 + 2];
             }
-            const float v0 = (float)(t0 * sc), v1 = (float)(t1 * sc), v2 = (float)(t2 * sc);
-            const int j = j0 + o;
-            for (int y = 0; y < bh; ++y)
-                for (int x = 0; x < bw; ++x) {
-                    float* po = D + ((int64_t)(bs * bh + y) * Wb + (j * bw + x)) * 3;
-                    po[0] += v0;
-                    po[1] += v1;
-                    po[2] += v2;
-                }
+            cpart[o * 3] = t0 * sc;   // own partials are no longer read by anyone
+            cpart[o * 3 + 1] = t1 * sc;
+            cpart[o * 3 + 2] = t2 * sc;
+        }
+        __syncthreads();
+        // spread over the bw x bh base texels of each column, all threads
+        const int per = bw * bh;
+        for (int idx = threadIdx.x; idx < JT * per; idx += nt) {
+            const int o = idx / per, y = (idx % per) / bw, x = idx % bw;
+            float* po = D + ((int64_t)(bs * bh + y) * Wb + ((j0 + o) * bw + x)) * 3;
+            po[0] += (float)cpart[o * 3];
+            po[1] += (float)cpart[o * 3 + 1];
+            po[2] += (float)cpart[o * 3 + 2];
         }
     }
     cluster.sync();
@@ -686,14 +692,21 @@ void ss_launch_env_prefilter(const ss_env_desc* d, int n_envs, const float* env,
     ss_note_launch();
     copy_level0_kernel<<<dim3(256, n_envs), 256, 0, st>>>(env, env_stride, spec, spec_stride, env_stride);
     int64_t spec_off = env_stride, aux_off = (int64_t)Wi * Hi;
+    const float* prev = env;
+    int64_t prev_stride = env_stride;
+    int Wp = We, Hp = He;
     for (int i = 1; i < d->n_levels; ++i) {
         int W, H;
         ss_env_level_size(d, i, &W, &H);
         float* norm = aux + aux_off;
         float* src = aux + aux_off + (int64_t)W * H;
         ss_note_launch();
-        box_down_kernel<<<dim3((W * H + 255) / 256, n_envs), 256, 0, st>>>(env, env_stride, We, He, src, aux_stride,
+        box_down_kernel<<<dim3((W * H + 255) / 256, n_envs), 256, 0, st>>>(prev, prev_stride, Wp, Hp, src, aux_stride,
                                                                            W, H);
+        prev = src;
+        prev_stride = aux_stride;
+        Wp = W;
+        Hp = H;
         float r = (float)i / (float)(d->n_levels - 1);
         launch_conv_fwd(src, aux_stride, W, H, spec + spec_off, spec_stride, W, H, norm, aux_stride, 1, r * r, n_envs,
                         st);
