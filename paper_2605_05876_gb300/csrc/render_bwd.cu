@@ -118,7 +118,13 @@ __global__ void __launch_bounds__(256) layer_coeff_kernel(ss_ws_view ws, ss_bwd_
     }
 }
 
+// AOV = false when no AOV gradient is given: the AOV channels' coefficients
+// are zero, so only P, A2, B2, the centre, n_f and RGB (the first 12 values
+// of the record) are differentiated and summed.
+template <bool AOV>
 __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kernel(ss_ws_view ws, ss_bwd_args a) {
+    constexpr int NV = AOV ? G_N : G_CH + 3;   // values per fragment
+    constexpr int NC = AOV ? SS_NCH : 3;       // channels with a coefficient
     extern __shared__ __align__(16) unsigned char bwd_smem[];
     ss_wstage* Wst = reinterpret_cast<ss_wstage*>(bwd_smem);
     ss_bwarp* Bws = reinterpret_cast<ss_bwarp*>(bwd_smem + RWPB_BWD * sizeof(ss_wstage));
@@ -199,7 +205,7 @@ __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kerne
                 float gr[G_N];
                 float dLdw = -gt[12];
 #pragma unroll
-                for (int c = 0; c < SS_NCH; ++c) {
+                for (int c = 0; c < NC; ++c) {
                     const float G = gt[c];
                     dLdw = fmaf(G, ch[c], dLdw);
                     gr[G_CH + c] = G * w;
@@ -216,7 +222,7 @@ __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kerne
                 gr[G_PX] = -(gs0 * h0.x + gs1 * h0.z + gs2 * h1.x);
                 gr[G_PY] = -(gs0 * h0.y + gs1 * h0.w + gs2 * h1.y);
 #pragma unroll
-                for (int q = 0; q < G_N; ++q) B.tab[q * GCOL + lane] = gr[q];
+                for (int q = 0; q < NV; ++q) B.tab[q * GCOL + lane] = gr[q];
             }
             const int snext = __shfl_down_sync(0xffffffffu, s, 1);
             // run ends: the last valid column and every column followed by another surfel
@@ -224,7 +230,7 @@ __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kerne
             __syncwarp();
             float v[32];
             {
-                const float4* t4 = reinterpret_cast<const float4*>(B.tab + (lane < G_N ? lane : 0) * GCOL);
+                const float4* t4 = reinterpret_cast<const float4*>(B.tab + (lane < NV ? lane : 0) * GCOL);
 #pragma unroll
                 for (int m = 0; m < 8; ++m) {
                     const float4 x = t4[m];
@@ -237,7 +243,7 @@ __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kerne
                 tot += v[j];
                 if ((ends >> j) & 1u) {   // warp-uniform
                     const int sl = __shfl_sync(0xffffffffu, s, j);
-                    if (lane < G_N && tot != 0.f) atomicAdd(grad + (int64_t)Wc->id[sl] * SS_NGRAD + lane, tot);
+                    if (lane < NV && tot != 0.f) atomicAdd(grad + (int64_t)Wc->id[sl] * SS_NGRAD + lane, tot);
                     tot = 0.f;
                 }
             }
@@ -315,11 +321,14 @@ void ss_launch_raster_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd
     const int smem = RWPB_BWD * (int)(sizeof(ss_wstage) + sizeof(ss_bwarp));
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(raster_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(raster_bwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(raster_bwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         attr = true;
     }
     ss_note_launch();
-    raster_bwd_kernel<<<(unsigned)(L.total_tiles * 8 / RWPB_BWD), 32 * RWPB_BWD, smem, st>>>(ws, a);
+    const unsigned grid = (unsigned)(L.total_tiles * 8 / RWPB_BWD);
+    if (a.d_aov) raster_bwd_kernel<true><<<grid, 32 * RWPB_BWD, smem, st>>>(ws, a);
+    else raster_bwd_kernel<false><<<grid, 32 * RWPB_BWD, smem, st>>>(ws, a);
 }
 
 // ------------------------------------------------------------------------

@@ -27,7 +27,7 @@ ELEM_ATOL_ENV = 3e-5
 LOOKUP_MARGIN = 1e-4
 
 
-def _run(scene, seed=0, params=None, env_levels=6):
+def _run(scene, seed=0, params=None, env_levels=6, aov_grad=True):
     import torch
     from paper_2605_05876_gb300.api import Renderer
     r = Renderer(scene, params=params, env_levels=env_levels)
@@ -36,6 +36,8 @@ def _run(scene, seed=0, params=None, env_levels=6):
     rng = np.random.default_rng(seed)
     P = r.n_pixels
     G = rng.normal(size=(P, 13))
+    if not aov_grad:
+        G[:, 4:] = 0.0            # RGBA-only upstream gradient (d_aov = NULL on the GPU side)
     refs, cache = [], {}
     for v in range(r.n_views):
         sl = r.view_slice(v)
@@ -46,7 +48,7 @@ def _run(scene, seed=0, params=None, env_levels=6):
     d_rgba = torch.from_numpy(G[:, :4].astype(np.float32)).cuda().contiguous()
     d_aov = torch.from_numpy(np.ascontiguousarray(G[:, 4:].T).astype(np.float32)).cuda()
     r.zero_grads()
-    r.backward(d_rgba, d_aov)
+    r.backward(d_rgba, d_aov if aov_grad else None)
     torch.cuda.synchronize()
     assert r.read_status() == 0
     gpu = {k: r.grads[k].cpu().numpy().astype(np.float64) for k in FIELDS[:-1]}
@@ -118,4 +120,16 @@ def test_backward_multi_view_multi_scene():
 @pytest.mark.slow
 def test_backward_torus_sphere_100k():
     gpu, ref = _run(S.torus_sphere_100k(), 9)
+    _compare(gpu, ref)
+
+
+@pytest.mark.parametrize("seed", [11, 13])
+def test_backward_rgba_only(seed):
+    """Without an AOV gradient the kernel differentiates only the RGB
+    channels; the result must equal the full gradient with zero AOV terms."""
+    rng = np.random.default_rng(300 + seed)
+    surf = _tiny.random_scene(rng, n=200, spread=0.5, scale=(0.02, 0.09))
+    sc = S.Scene(surf, np.array([0, surf.n]), [_tiny.lognormal_env(rng, 64, 32)],
+                 [_tiny.front_camera(res=40, width=45)], "tiny")
+    gpu, ref = _run(sc, seed, aov_grad=False)
     _compare(gpu, ref)
