@@ -133,3 +133,42 @@ def test_backward_rgba_only(seed):
                  [_tiny.front_camera(res=40, width=45)], "tiny")
     gpu, ref = _run(sc, seed, aov_grad=False)
     _compare(gpu, ref)
+
+
+@pytest.mark.slow
+def test_backward_displaced_sphere_1m_sampled():
+    """Full-size headline workload (1M surfels, 16 views of 800^2, the launch
+    configuration bench.py times): an upstream gradient on sampled pixels of
+    view 0 only, so the oracle needs just those pixels; every surfel's and
+    every env texel's gradient is compared."""
+    import torch
+    from paper_2605_05876_gb300.api import Renderer
+    sc = S.displaced_sphere_1m()
+    r = Renderer(sc)
+    r.forward()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(21)
+    cov = np.where(r.view_rgba(0).reshape(-1, 4)[:, 3].cpu().numpy() > 0)[0]
+    pix = np.sort(np.concatenate([rng.choice(cov, 400, replace=False), rng.choice(640000, 50, replace=False)]))
+    pix = np.unique(pix).astype(np.int32)
+    cache = {}
+    ref0 = _parity.oracle_view(sc, 0, r.prm, pix=pix, env_cache=cache)
+    keep = ~_parity.ambiguous(ref0["margin"])
+    pix = pix[keep]
+    Gs = rng.normal(size=(pix.size, 13))
+    ref = _parity.oracle_view(sc, 0, r.prm, pix=pix, G=Gs, env_cache=cache)
+    G = np.zeros((r.n_pixels, 13))
+    G[pix] = Gs                     # view 0 is the first slice of the batch
+    d_rgba = torch.from_numpy(G[:, :4].astype(np.float32)).cuda().contiguous()
+    d_aov = torch.from_numpy(np.ascontiguousarray(G[:, 4:].T).astype(np.float32)).cuda()
+    r.zero_grads()
+    r.backward(d_rgba, d_aov)
+    torch.cuda.synchronize()
+    assert r.read_status() == 0
+    gpu = {k: r.grads[k].cpu().numpy().astype(np.float64) for k in FIELDS[:-1]}
+    gpu["env"] = r.d_env.cpu().numpy().astype(np.float64)
+    refd = {k: ref["grad"][k].reshape(gpu[k].shape) for k in FIELDS[:-1]}
+    refd["env"] = ref["grad"]["env"].reshape(gpu["env"].shape)
+    gpu["_near"] = ref["lookup_margin"] < LOOKUP_MARGIN
+    assert (np.abs(refd["pos"]).sum(1) > 0).sum() > 1000     # many surfels receive gradient
+    _compare(gpu, refd)
