@@ -115,7 +115,10 @@ typedef struct ss_render_params {
     int32_t lut_n;           /* BRDF table resolution (n x n) */
     int64_t max_instances;   /* capacity of the (tile, surfel) instance list */
     int32_t collect_stats;   /* 1: count work (see ss_read_stats); off by default */
-    int32_t pad_;
+    /* launch shapes (0 = default); they change speed, never results */
+    int32_t fwd_warps;       /* warps per CTA of the forward rasteriser: 1 (default), 2 or 4 */
+    int32_t bwd_warps;       /* warps per CTA of the backward rasteriser: 2, 4 (default) or 8 */
+    int32_t pbwd_block;      /* surfels per CTA of the projection adjoint: 32..1024, default 128 */
 } ss_render_params;
 
 /* Work counters of the last forward/backward pair (collect_stats = 1). */

@@ -194,6 +194,45 @@ class Renderer:
         return self.grads
 
 
+    TUNE_SPACE = {"fwd_warps": (1, 2, 4), "bwd_warps": (2, 4, 8), "pbwd_block": (64, 128, 256)}
+
+    def autotune(self, d_rgba, d_aov=None, reps: int = 3, space: dict | None = None) -> dict:
+        """Choose the launch shapes of ss_render_params (fwd_warps, bwd_warps,
+        pbwd_block) that render and differentiate this batch fastest, one
+        knob at a time in the order given, each candidate timed with CUDA
+        events over `reps` forward+backward passes after one untimed pass.
+        The shapes change speed only, never results.  Returns
+        {knob: (chosen value, {value: ms per pass})}."""
+        torch = self.torch
+        space = space or self.TUNE_SPACE
+
+        def one():
+            self.forward()
+            self.zero_grads()
+            self.backward(d_rgba, d_aov, env_grad=False)
+
+        def timed() -> float:
+            one()
+            st = torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(reps):
+                one()
+            e1.record(st)
+            e1.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        chosen = {}
+        for knob, values in space.items():
+            times = {}
+            for v in values:
+                setattr(self.prm, knob, int(v))
+                times[int(v)] = timed()
+            best = min(times, key=times.get)
+            setattr(self.prm, knob, best)
+            chosen[knob] = (best, times)
+        return chosen
+
     def read_status(self) -> int:
         return int(lib().ss_read_status(_ptr(self.ws), _stream()))
 

@@ -346,6 +346,9 @@ static ss_status check_render_args(const ss_batch_desc* b, const ss_surfels* s, 
     if (!env->irr || !env->spec || !env->lut || !env_desc_ok(ed)) return SS_ERR_INVALID_ARG;
     if (((uintptr_t)s->quat & 15) || ((uintptr_t)s->log_scale & 7) || ((uintptr_t)ws & 255)) return SS_ERR_INVALID_ARG;
     if (p->max_instances <= 0 || p->max_instances > 0xffffffffll) return SS_ERR_INVALID_ARG;
+    if (!(p->fwd_warps == 0 || p->fwd_warps == 1 || p->fwd_warps == 2 || p->fwd_warps == 4)) return SS_ERR_INVALID_ARG;
+    if (!(p->bwd_warps == 0 || p->bwd_warps == 2 || p->bwd_warps == 4 || p->bwd_warps == 8)) return SS_ERR_INVALID_ARG;
+    if (!(p->pbwd_block == 0 || (p->pbwd_block >= 32 && p->pbwd_block <= 1024))) return SS_ERR_INVALID_ARG;
     return SS_OK;
 }
 

@@ -14,11 +14,12 @@
 #include "ss3d_internal.cuh"
 
 #define WSLOTS 32
-// Warps per CTA of the rasterisers.  Every warp is independent (no block
-// barrier), so small CTAs let an SM refill a finished warp's slot at once
-// instead of waiting for the slowest warp of its tile.
-#define RWPB_FWD 1
-#define RWPB_BWD 4
+// Warps per CTA of the rasterisers (a template parameter, chosen at launch
+// from ss_render_params).  Every warp is independent (no block barrier), so
+// small CTAs let an SM refill a finished warp's slot at once instead of
+// waiting for the slowest warp of its tile.
+#define RWPB_FWD_DEFAULT 1
+#define RWPB_BWD_DEFAULT 4
 
 struct ss_wstage {
     float4 h0[WSLOTS];  // P (screen quadratic-form factor)                  -- every test

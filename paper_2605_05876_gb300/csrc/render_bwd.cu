@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(256) layer_coeff_kernel(ss_ws_view ws, ss_bwd_
 // AOV = false when no AOV gradient is given: the AOV channels' coefficients
 // are zero, so only P, A2, B2, the centre, n_f and RGB (the first 12 values
 // of the record) are differentiated and summed.
-template <bool AOV>
+template <bool AOV, int RWPB_BWD>
 __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kernel(ss_ws_view ws, ss_bwd_args a) {
     constexpr int NV = AOV ? G_N : G_CH + 3;   // values per fragment
     constexpr int NC = AOV ? SS_NCH : 3;       // channels with a coefficient
@@ -314,21 +314,32 @@ __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kerne
     }
 }
 
+template <bool AOV, int W>
+static void launch_raster_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st) {
+    const int smem = W * (int)(sizeof(ss_wstage) + sizeof(ss_bwarp));
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(raster_bwd_kernel<AOV, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr = true;
+    }
+    raster_bwd_kernel<AOV, W><<<(unsigned)(L.total_tiles * 8 / W), 32 * W, smem, st>>>(ws, a);
+}
+
 void ss_launch_raster_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st) {
     if (L.total_tiles <= 0) return;
     ss_note_launch();
     layer_coeff_kernel<<<(unsigned)((L.total_pixels + 255) / 256), 256, 0, st>>>(ws, a);
-    const int smem = RWPB_BWD * (int)(sizeof(ss_wstage) + sizeof(ss_bwarp));
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(raster_bwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(raster_bwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr = true;
-    }
+    const int w = a.f.p.bwd_warps ? a.f.p.bwd_warps : RWPB_BWD_DEFAULT;
     ss_note_launch();
-    const unsigned grid = (unsigned)(L.total_tiles * 8 / RWPB_BWD);
-    if (a.d_aov) raster_bwd_kernel<true><<<grid, 32 * RWPB_BWD, smem, st>>>(ws, a);
-    else raster_bwd_kernel<false><<<grid, 32 * RWPB_BWD, smem, st>>>(ws, a);
+    if (a.d_aov) {
+        if (w == 2) launch_raster_bwd<true, 2>(ws, L, a, st);
+        else if (w == 4) launch_raster_bwd<true, 4>(ws, L, a, st);
+        else launch_raster_bwd<true, 8>(ws, L, a, st);
+    } else {
+        if (w == 2) launch_raster_bwd<false, 2>(ws, L, a, st);
+        else if (w == 4) launch_raster_bwd<false, 4>(ws, L, a, st);
+        else launch_raster_bwd<false, 8>(ws, L, a, st);
+    }
 }
 
 // ------------------------------------------------------------------------
@@ -785,7 +796,7 @@ void ss_launch_project_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bw
         ss_env_level_size(&a.f.ed, i, &W, &H);
         spec_off += (int64_t)W * H * 3;
     }
-    const int64_t per_block = 128;   // surfels per CTA (each with all its views)
+    const int64_t per_block = a.f.p.pbwd_block ? a.f.p.pbwd_block : 128;   // surfels per CTA (all their views)
     const unsigned blocks = (unsigned)((n + per_block - 1) / per_block);
     const size_t smem = sizeof(float) * (size_t)(irr_floats + priv_spec);
     static bool attr = false;

@@ -471,7 +471,7 @@ void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_a
 // little work never waits for a busy one, and a warp whose 32 pixels have all
 // reached K_max layers stops reading the list.
 
-template <bool STATS>
+template <bool STATS, int RWPB_FWD>
 __global__ void __launch_bounds__(32 * RWPB_FWD, 24 / RWPB_FWD) raster_fwd_kernel(ss_ws_view ws, ss_fwd_args a) {
     extern __shared__ __align__(16) unsigned char fwd_smem[];
     ss_wstage* Wst = reinterpret_cast<ss_wstage*>(fwd_smem);                          // [RWPB_FWD warps][2]
@@ -631,17 +631,28 @@ __global__ void __launch_bounds__(32 * RWPB_FWD, 24 / RWPB_FWD) raster_fwd_kerne
     }
 }
 
+template <bool STATS, int W>
+static void launch_raster_fwd(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st) {
+    const int smem = 2 * W * ((int)sizeof(ss_wstage) + WSLOTS * (int)sizeof(uint2));
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(raster_fwd_kernel<STATS, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr = true;
+    }
+    raster_fwd_kernel<STATS, W><<<(unsigned)(L.total_tiles * 8 / W), 32 * W, smem, st>>>(ws, a);
+}
+
 void ss_launch_raster_fwd(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st) {
     if (L.total_tiles <= 0) return;
     ss_note_launch();
-    const int smem = 2 * RWPB_FWD * ((int)sizeof(ss_wstage) + WSLOTS * (int)sizeof(uint2));
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(raster_fwd_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(raster_fwd_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr = true;
+    const int w = a.p.fwd_warps ? a.p.fwd_warps : RWPB_FWD_DEFAULT;
+    if (a.p.collect_stats) {
+        if (w == 1) launch_raster_fwd<true, 1>(ws, L, a, st);
+        else if (w == 2) launch_raster_fwd<true, 2>(ws, L, a, st);
+        else launch_raster_fwd<true, 4>(ws, L, a, st);
+    } else {
+        if (w == 1) launch_raster_fwd<false, 1>(ws, L, a, st);
+        else if (w == 2) launch_raster_fwd<false, 2>(ws, L, a, st);
+        else launch_raster_fwd<false, 4>(ws, L, a, st);
     }
-    const unsigned grid = (unsigned)(L.total_tiles * 8 / RWPB_FWD);
-    if (a.p.collect_stats) raster_fwd_kernel<true><<<grid, 32 * RWPB_FWD, smem, st>>>(ws, a);
-    else raster_fwd_kernel<false><<<grid, 32 * RWPB_FWD, smem, st>>>(ws, a);
 }

@@ -32,7 +32,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_struct_sizes_match_header():
     assert ctypes.sizeof(_lib.ss_camera) == 80
-    assert ctypes.sizeof(_lib.ss_render_params) == 56
+    assert ctypes.sizeof(_lib.ss_render_params) == 64
     assert ctypes.sizeof(_lib.ss_stats) == 64
 
 
@@ -75,3 +75,29 @@ def test_host_side_argument_errors():
     n = ctypes.c_int64(-1)
     assert lib.ss_launch_count(ctypes.byref(n)) == 0 and n.value >= 0
     assert lib.ss_launch_count(None) == _lib.SS_ERR_INVALID_ARG
+
+
+def test_launch_shape_knobs_are_validated_on_the_host():
+    """Unsupported launch shapes are rejected before anything is enqueued
+    (the pointers below are never dereferenced)."""
+    lib = _lib.lib()
+    p = _lib.ss_render_params()
+    lib.ss_default_params(ctypes.byref(p))
+    assert (p.fwd_warps, p.bwd_warps, p.pbwd_block) == (0, 0, 0)
+    p.max_instances = 1000
+    cams = (_lib.ss_camera * 1)()
+    cams[0].width = cams[0].height = 16
+    cams[0].fx = cams[0].fy = 10.0
+    off = (ctypes.c_int64 * 2)(0, 10)
+    fake = ctypes.c_void_p(1 << 20)
+    d = _lib.ss_batch_desc(1, 1, off, cams, fake)
+    s = _lib.ss_surfels(fake, fake, fake, fake, fake, fake)
+    ed = _lib.ss_env_desc(64, 32, 6, 32, 16)
+    em = _lib.ss_env_maps(fake, fake, fake)
+    for knob, bad in (("fwd_warps", 3), ("bwd_warps", 1), ("pbwd_block", 16), ("pbwd_block", 4096)):
+        q = _lib.ss_render_params()
+        ctypes.memmove(ctypes.byref(q), ctypes.byref(p), ctypes.sizeof(q))
+        setattr(q, knob, bad)
+        st = lib.ss_render_forward(ctypes.byref(d), ctypes.byref(s), ctypes.byref(q), ctypes.byref(ed),
+                                   ctypes.byref(em), fake, fake, fake, 1 << 40, None)
+        assert st == _lib.SS_ERR_INVALID_ARG, knob
