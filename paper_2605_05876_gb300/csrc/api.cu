@@ -269,7 +269,7 @@ static bool env_desc_ok(const ss_env_desc* d);
 extern "C" ss_status ss_workspace_size(const ss_batch_desc* b, const ss_render_params* p, const ss_env_desc* ed,
                                        int32_t with_backward, size_t* bytes) {
     if (!bytes || !p || p->max_instances <= 0 || p->max_instances > 0xffffffffll) return SS_ERR_INVALID_ARG;
-    static ss_layout L;
+    ss_layout L;   // on the stack: entry points may be called from several threads
     ss_status st = build_layout(b, p, &L);
     if (st) return st;
     if (ed && !env_desc_ok(ed)) return SS_ERR_INVALID_ARG;
@@ -408,7 +408,7 @@ extern "C" ss_status ss_render_forward(const ss_batch_desc* b, const ss_surfels*
     // the workspace decides whether backward state is kept: use the larger plan if it fits
     int with_bwd = 0;
     if (b && p && p->max_instances > 0) {
-        static ss_layout Lt;
+        ss_layout Lt;
         if (build_layout(b, p, &Lt) == SS_OK && ws_bytes >= plan_ws(Lt, *p, 1, ed).total) with_bwd = 1;
     }
     return forward_core(b, s, p, ed, env, out_rgba_dev, out_aov_dev, ws, ws_bytes, with_bwd, 0,
@@ -442,7 +442,7 @@ extern "C" ss_status ss_render_backward(const ss_batch_desc* b, const ss_surfels
     if (e) return e;
     if (!out_rgba_dev || !d_rgba_dev || !g) return SS_ERR_INVALID_ARG;
     if (p->write_aov && d_aov_dev && !out_aov_dev) return SS_ERR_INVALID_ARG;
-    static ss_layout L;
+    ss_layout L;   // on the stack: entry points may be called from several threads
     e = build_layout(b, p, &L);
     if (e) return e;
     ws_plan plan = plan_ws(L, *p, 1, ed);

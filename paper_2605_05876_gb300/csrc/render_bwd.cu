@@ -317,11 +317,8 @@ __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kerne
 template <bool AOV, int W>
 static void launch_raster_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st) {
     const int smem = W * (int)(sizeof(ss_wstage) + sizeof(ss_bwarp));
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(raster_bwd_kernel<AOV, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr = true;
-    }
+    static std::atomic<unsigned long long> optin{0};
+    ss_smem_optin(raster_bwd_kernel<AOV, W>, smem, optin);
     raster_bwd_kernel<AOV, W><<<(unsigned)(L.total_tiles * 8 / W), 32 * W, smem, st>>>(ws, a);
 }
 
@@ -799,11 +796,8 @@ void ss_launch_project_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bw
     const int64_t per_block = a.f.p.pbwd_block ? a.f.p.pbwd_block : 128;   // surfels per CTA (all their views)
     const unsigned blocks = (unsigned)((n + per_block - 1) / per_block);
     const size_t smem = sizeof(float) * (size_t)(irr_floats + priv_spec);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(project_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-        attr = true;
-    }
+    static std::atomic<unsigned long long> optin{0};
+    ss_smem_optin(project_bwd_kernel, 64 * 1024, optin);
     ss_note_launch();
     project_bwd_kernel<<<blocks, 128, smem, st>>>(ws, a, n, per_block, level, spec_off, (int)priv_spec);
     if ((a.genv.irr || a.genv.spec) && ws.env_acc) {

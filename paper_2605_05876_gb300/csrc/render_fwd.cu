@@ -453,12 +453,8 @@ void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_a
         ss_note_launch();
         scatter_kernel<<<(unsigned)((L.total_records + 255) / 256), 256, 0, st>>>(ws, L.total_records);
     }
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(tile_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             SORT_CAP * (int)sizeof(unsigned long long));
-        attr = true;
-    }
+    static std::atomic<unsigned long long> optin{0};
+    ss_smem_optin(tile_sort_kernel, SORT_CAP * (int)sizeof(unsigned long long), optin);
     ss_note_launch();
     tile_sort_kernel<<<L.total_tiles, SORT_THREADS, SORT_CAP * sizeof(unsigned long long), st>>>(ws, L.total_tiles);
 }
@@ -634,11 +630,8 @@ __global__ void __launch_bounds__(32 * RWPB_FWD, 24 / RWPB_FWD) raster_fwd_kerne
 template <bool STATS, int W>
 static void launch_raster_fwd(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st) {
     const int smem = 2 * W * ((int)sizeof(ss_wstage) + WSLOTS * (int)sizeof(uint2));
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(raster_fwd_kernel<STATS, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr = true;
-    }
+    static std::atomic<unsigned long long> optin{0};
+    ss_smem_optin(raster_fwd_kernel<STATS, W>, smem, optin);
     raster_fwd_kernel<STATS, W><<<(unsigned)(L.total_tiles * 8 / W), 32 * W, smem, st>>>(ws, a);
 }
 

@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <stdint.h>
 
 #include "ss3d.h"
@@ -244,6 +246,18 @@ __device__ __forceinline__ ss_hit ss_pixel_test(float4 r0, float4 r1, float dx, 
 
 // host-side count of kernel launches (ss_launch_count); call before each launch
 void ss_note_launch();
+
+// Opt kernel `k` in to `bytes` of dynamic shared memory on the current device
+// (a per-device attribute): once per device, tracked in `done` (bit = device).
+template <typename K>
+inline void ss_smem_optin(K k, int bytes, std::atomic<unsigned long long>& done) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+    if (bit && (done.load(std::memory_order_relaxed) & bit)) return;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (bit) done.fetch_or(bit, std::memory_order_relaxed);
+}
 
 void ss_launch_brdf_lut(float* lut, int n, cudaStream_t st);
 void ss_launch_env_prefilter(const ss_env_desc* d, int n_envs, const float* env, float* irr, float* spec,
