@@ -120,6 +120,23 @@ class ClockSampler:
 # helpers
 
 
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's time of the timed region (each rank renders its
+    own full batch: replicas, weak scaling)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job throughput: the units of all ranks over the slowest rank's time."""
+    return world * units_per_rank * steps / (max_ms / 1000.0)
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -277,12 +294,7 @@ def run_ours(args):
         e1.record(st)
         torch.cuda.synchronize()
         barrier()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        return max_over_ranks(e0.elapsed_time(e1), world, dev)
 
     # launch shapes for this workload (untimed; speed only, results unchanged)
     tuned = None
@@ -305,7 +317,7 @@ def run_ours(args):
         stages = profile_end()
     clocks = clk.summary()
     ms_per_step = ms / args.steps
-    value = world * V * args.steps / (ms / 1000.0)
+    value = job_rate(V, args.steps, world, ms)
 
     # --- the same step replayed from a CUDA graph (no host work per step)
     graph = None
@@ -321,7 +333,7 @@ def run_ours(args):
         for _ in range(max(args.warmup, 1)):
             cg.replay()
         ms_g = timed(cg.replay, args.steps)
-        graph = {"value": world * V * args.steps / (ms_g / 1000.0), "unit": "views/s",
+        graph = {"value": job_rate(V, args.steps, world, ms_g), "unit": "views/s",
                  "ms_per_step": ms_g / args.steps}
         del cg
     except RuntimeError as e:   # capture refused: report it, keep the eager number
@@ -357,7 +369,7 @@ def run_ours(args):
         for _ in range(args.warmup):
             step_pv()
         ms_pv = timed(step_pv, args.steps)
-        per_view = {"value": world * V * args.steps / (ms_pv / 1000.0), "unit": "views/s",
+        per_view = {"value": job_rate(V, args.steps, world, ms_pv), "unit": "views/s",
                     "ms_per_step": ms_pv / args.steps}
         del singles
 
@@ -382,7 +394,7 @@ def run_ours(args):
         for _ in range(args.warmup):
             step_e2e()
         ms_e2e = timed(step_e2e, args.steps)
-        e2e = {"value": world * V * args.steps / (ms_e2e / 1000.0), "unit": "views/s",
+        e2e = {"value": job_rate(V, args.steps, world, ms_e2e), "unit": "views/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     # --- roofline of the dominant kernel (FP32-issue bound: no memory or tensor-core limit applies)
@@ -528,14 +540,10 @@ def run_loop(args):
         e1.record(st)
         torch.cuda.synchronize()
         n_launched = launch_count() - n0
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     status = r.read_status()
     if rank == 0:
-        its = world * args.steps / (ms / 1000.0)
+        its = job_rate(1, args.steps, world, ms)
         line = {"metric": LOOP_METRIC, "value": its, "unit": "it/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",

@@ -129,7 +129,8 @@ typedef struct ss_stats {
     int64_t fragments;       /* covering fragments accumulated by the forward raster */
     int64_t layers;          /* composited layers summed over pixels */
     int64_t bwd_fragments;   /* fragments differentiated by the backward raster */
-    int64_t reserved[2];
+    int64_t staged;          /* (warp block, surfel) pairs the forward raster staged */
+    int64_t staged_covering; /* ... of which cover at least one pixel of the block */
 } ss_stats;
 
 /* Stage timing: CUDA events recorded on the launching stream around each

@@ -492,7 +492,7 @@ __global__ void __launch_bounds__(32 * RWPB_FWD, 24 / RWPB_FWD) raster_fwd_kerne
     const int kmax = a.p.k_max;
     const int64_t gpix = vl.pixel_off + (int64_t)py * vl.width + px;
     const int64_t P = L->total_pixels;
-    unsigned n_lane = 0, n_rect = 0, n_frag = 0;
+    unsigned n_lane = 0, n_rect = 0, n_frag = 0, n_staged = 0, n_cov = 0;
 
     float C[SS_NCH];
 #pragma unroll
@@ -590,6 +590,10 @@ __global__ void __launch_bounds__(32 * RWPB_FWD, 24 / RWPB_FWD) raster_fwd_kerne
                 }
             }
         }
+        if (STATS) {   // warp-uniform counts, kept by lane 0
+            n_staged += n;
+            n_cov += __popc(__ballot_sync(0xffffffffu, lane < n && my_mask != 0u));
+        }
         if (clist) {
             const bool keep = lane < n && my_mask != 0u;
             const uint32_t km = __ballot_sync(0xffffffffu, keep);
@@ -609,6 +613,8 @@ __global__ void __launch_bounds__(32 * RWPB_FWD, 24 / RWPB_FWD) raster_fwd_kerne
             for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
             if (lane == 0 && x) atomicAdd(ws.stats + 1 + q, x);
         }
+        if (lane == 0 && n_staged) atomicAdd(ws.stats + 6, (unsigned long long)n_staged);
+        if (lane == 0 && n_cov) atomicAdd(ws.stats + 7, (unsigned long long)n_cov);
     }
     if (!inside) return;
     float4 o;
