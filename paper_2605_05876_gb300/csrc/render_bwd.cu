@@ -350,12 +350,21 @@ __device__ __forceinline__ int64_t spec_level_off_b(const ss_env_desc& ed, int i
     return off;
 }
 
-// bilinear value, d/du, d/dv of a 3-channel map; optionally scatter dOut * weights
+// bilinear value of a 3-channel map
+__device__ __forceinline__ float3 bilerp3b(const float* T, ss_taps t) {
+    float w00 = (1.f - t.fx) * (1.f - t.fy), w01 = t.fx * (1.f - t.fy), w10 = (1.f - t.fx) * t.fy, w11 = t.fx * t.fy;
+    float3 r;
+    r.x = w00 * T[t.i00 * 3] + w01 * T[t.i01 * 3] + w10 * T[t.i10 * 3] + w11 * T[t.i11 * 3];
+    r.y = w00 * T[t.i00 * 3 + 1] + w01 * T[t.i01 * 3 + 1] + w10 * T[t.i10 * 3 + 1] + w11 * T[t.i11 * 3 + 1];
+    r.z = w00 * T[t.i00 * 3 + 2] + w01 * T[t.i01 * 3 + 2] + w10 * T[t.i10 * 3 + 2] + w11 * T[t.i11 * 3 + 2];
+    return r;
+}
+
+// bilinear value, d/du, d/dv of a 3-channel map at precomputed taps
 struct lk3 {
     float v[3], du[3], dv[3];
 };
-__device__ __forceinline__ lk3 lookup3(const float* T, float u, float v, int W, int H, bool wrap) {
-    ss_taps t = bilinear_taps(u, v, W, H, wrap);
+__device__ __forceinline__ lk3 lookup3(const float* T, const ss_taps& t, int W, int H) {
     lk3 r;
     for (int c = 0; c < 3; ++c) {
         float a = T[t.i00 * 3 + c], b = T[t.i01 * 3 + c], d = T[t.i10 * 3 + c], e = T[t.i11 * 3 + c];
@@ -365,9 +374,8 @@ __device__ __forceinline__ lk3 lookup3(const float* T, float u, float v, int W, 
     }
     return r;
 }
-__device__ __forceinline__ void scatter3(float* D, float u, float v, int W, int H, bool wrap, const float g[3],
-                                         float scale) {
-    ss_taps t = bilinear_taps(u, v, W, H, wrap);
+// bilinear adjoint: g * scale * tap weights added to a 3-channel map in shared memory
+__device__ __forceinline__ void scatter3(float* D, const ss_taps& t, const float g[3], float scale) {
     const float w00 = (1.f - t.fx) * (1.f - t.fy) * scale, w01 = t.fx * (1.f - t.fy) * scale,
                 w10 = (1.f - t.fx) * t.fy * scale, w11 = t.fx * t.fy * scale;
     for (int c = 0; c < 3; ++c) {
@@ -379,9 +387,8 @@ __device__ __forceinline__ void scatter3(float* D, float u, float v, int W, int 
     }
 }
 // the same bilinear adjoint into RGBA accumulators (one 16-byte atomic per tap)
-__device__ __forceinline__ void scatter4(float4* D, float u, float v, int W, int H, const float g[3], float scale) {
+__device__ __forceinline__ void scatter4(float4* D, const ss_taps& t, const float g[3], float scale) {
     if (scale == 0.f || (g[0] == 0.f && g[1] == 0.f && g[2] == 0.f)) return;
-    ss_taps t = bilinear_taps(u, v, W, H, true);
     const float w00 = (1.f - t.fx) * (1.f - t.fy) * scale, w01 = t.fx * (1.f - t.fy) * scale,
                 w10 = (1.f - t.fx) * t.fy * scale, w11 = t.fx * t.fy * scale;
     atomicAdd(D + t.i00, make_float4(w00 * g[0], w00 * g[1], w00 * g[2], 0.f));
@@ -393,13 +400,13 @@ __device__ __forceinline__ void scatter4(float4* D, float u, float v, int W, int
 __device__ __forceinline__ void uv_grad(const float d[3], float gu, float gv, float out[3]) {
     const float rxz = fmaxf(d[0] * d[0] + d[2] * d[2], 1e-20f);
     // u = atan2(d_x, -d_z) / 2pi + 1/2
-    const float k = gu * (0.5f / SS_PI_F) / rxz;
+    const float irs = rsqrtf(rxz);
+    const float k = gu * (0.5f / SS_PI_F) * irs * irs;
     out[0] = k * (-d[2]);
     out[2] = k * d[0];
     out[1] = 0.f;
     // v = acos(d_y / |d|) / pi; with |d| = 1: dv/dd = -(e_y - d_y d) / (pi sqrt(1 - d_y^2))
-    const float s = sqrtf(rxz);
-    const float kv = -gv / (SS_PI_F * s);
+    const float kv = -gv * (1.f / SS_PI_F) * irs;
     out[0] += kv * (-d[1] * d[0]);
     out[1] += kv * (1.f - d[1] * d[1]);
     out[2] += kv * (-d[1] * d[2]);
@@ -407,19 +414,42 @@ __device__ __forceinline__ void uv_grad(const float d[3], float gu, float gv, fl
 
 // One thread per surfel: the raster gradient record of each of its views is
 // chained back to the surfel parameters; the views are summed in order
-// (deterministic) and added to the caller's gradients.
+// (deterministic) and added to the caller's gradients.  The irradiance lookup
+// depends on the surfel's normal and on the side it shows, not on the view,
+// so its adjoint is taken once per side, from the sum over the views that
+// see that side.
 
-// Shared-memory copies of the environment gradients of one scene: the
-// irradiance map and the specular levels from `level` on (the small, most
-// contended ones).  Records of other scenes or larger levels add to global
-// memory directly.
+// Shared-memory copies of the specular gradient levels from `level` on (the
+// small, most contended ones) of one scene.  Records of other scenes, the
+// larger levels and the irradiance map add to the RGBA accumulators.
 struct env_priv {
-    float* irr;        // [irr floats] or nullptr
-    float* spec;       // levels level .. L-1, back to back
+    float* spec;       // levels level .. L-1, back to back, or nullptr
     int scene;
     int level;
     int64_t spec_off;  // offset of level `level` inside one scene's spec stack
 };
+
+// Irradiance adjoint of one side of a surfel (fs = +1 front, -1 back) given
+// g = sum over that side's views of dL/dLd: the texel gradients (bilinear
+// adjoint) and the normal column of dL/dR through uv(fs n).
+__device__ __forceinline__ void irr_side_adjoint(const float* irr, int W, int H, const float nrm[3], float fs,
+                                                 const float g[3], float4* acc, float gRn[3]) {
+    if (g[0] == 0.f && g[1] == 0.f && g[2] == 0.f) return;
+    const float ns[3] = {fs * nrm[0], fs * nrm[1], fs * nrm[2]};
+    float un, vn;
+    dir_to_uv(ns[0], ns[1], ns[2], un, vn);
+    const ss_taps t = bilinear_taps(un, vn, W, H, true);
+    const lk3 Ld = lookup3(irr, t, W, H);
+    if (acc) scatter4(acc, t, g, 1.f);
+    float gun = 0.f, gvn = 0.f;
+    for (int k = 0; k < 3; ++k) {
+        gun += g[k] * Ld.du[k];
+        gvn += g[k] * Ld.dv[k];
+    }
+    float dnsv[3];
+    uv_grad(ns, gun, gvn, dnsv);
+    for (int k = 0; k < 3; ++k) gRn[k] += fs * dnsv[k];
+}
 
 __device__ __forceinline__ void pbwd_surfel(const ss_ws_view& ws, const ss_bwd_args& A, const int64_t i,
                                             const int scene, const env_priv& pv) {
@@ -438,7 +468,8 @@ __device__ __forceinline__ void pbwd_surfel(const ss_ws_view& ws, const ss_bwd_a
     const float nrm[3] = {Rq[2], Rq[5], Rq[8]};
     const float sig = a.p.sigma_f;
     const int nL = a.ed.n_levels;
-    const int64_t irr_stride = (int64_t)a.ed.irr_width * a.ed.irr_height * 3;
+    const int IW = a.ed.irr_width, IH = a.ed.irr_height;
+    const int64_t irr_stride = (int64_t)IW * IH * 3;
     int Wt, Ht;
     const int64_t spec_stride = spec_level_off_b(a.ed, nL, Wt, Ht);
     const float* irr = a.env.irr + scene * irr_stride;
@@ -446,24 +477,47 @@ __device__ __forceinline__ void pbwd_surfel(const ss_ws_view& ws, const ss_bwd_a
     const bool d_irr = A.genv.irr != nullptr, d_spec = A.genv.spec != nullptr;
     const int lutn = a.p.lut_n;
     const float* LUT = a.env.lut;
+    // roughness-only shading quantities: the two specular levels and their blend
+    const float rcl = fminf(fmaxf(rough, 0.f), 1.f);
+    const float lc = rcl * (float)(nL - 1);
+    const int l0 = min((int)floorf(lc), nL - 1), l1 = min(l0 + 1, nL - 1);
+    const float lf = lc - (float)l0;
+    int W0, H0, W1, H1;
+    const int64_t o0 = spec_level_off_b(a.ed, l0, W0, H0), o1 = spec_level_off_b(a.ed, l1, W1, H1);
+    // irradiance at the front and the back side of the normal (the same in every view)
+    float LdF[3], LdB[3];
+    {
+        float u, v;
+        dir_to_uv(nrm[0], nrm[1], nrm[2], u, v);
+        const float3 f = bilerp3b(irr, bilinear_taps(u, v, IW, IH, true));
+        dir_to_uv(-nrm[0], -nrm[1], -nrm[2], u, v);
+        const float3 b = bilerp3b(irr, bilinear_taps(u, v, IW, IH, true));
+        LdF[0] = f.x; LdF[1] = f.y; LdF[2] = f.z;
+        LdB[0] = b.x; LdB[1] = b.y; LdB[2] = b.z;
+    }
 
     // parameter gradients, summed over the scene's views in order
     float gc[3] = {0, 0, 0}, gRq[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, gsu = 0.f, gsv = 0.f;
     float grho[3] = {0, 0, 0}, grough = 0.f, gmetal = 0.f;
+    float gLdF[3] = {0, 0, 0}, gLdB[3] = {0, 0, 0};   // dL/dLd summed per side
     bool any_view = false;
     for (int v = L->scene_view_begin[scene]; v < L->scene_view_begin[scene + 1]; ++v) {
         const ss_view_layout& vl = L->v[v];
         const int64_t r = vl.rec_off + (i - vl.surfel_begin);
+        // every load of the view first (one round trip), then the decisions
         const uint32_t flags = __float_as_uint(ws.rec[r].r4.w);
+        const float4 r0 = ws.rec[r].r0, r1 = ws.rec[r].r1;
+        const float4* gr4 = reinterpret_cast<const float4*>(ws.grad_rec + r * SS_NGRAD);
+        float G[24];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float4 t = gr4[k];
+            G[4 * k] = t.x; G[4 * k + 1] = t.y; G[4 * k + 2] = t.z; G[4 * k + 3] = t.w;
+        }
         if (!(flags & SS_FLAG_VALID)) continue;
-        const float* gr = ws.grad_rec + r * SS_NGRAD;
-        float G[G_N];
         bool any = false;
 #pragma unroll
-        for (int k = 0; k < G_N; ++k) {
-            G[k] = gr[k];
-            any = any || (G[k] != 0.f);
-        }
+        for (int k = 0; k < G_N; ++k) any = any || (G[k] != 0.f);
         if (!any) continue;
         any_view = true;
         const ss_camera& cam = a.cams[v];
@@ -477,47 +531,49 @@ __device__ __forceinline__ void pbwd_surfel(const ss_ws_view& ws, const ss_bwd_a
             tvc[k] = Rc[k * 3] * tv[0] + Rc[k * 3 + 1] * tv[1] + Rc[k * 3 + 2] * tv[2];
         }
         const float cz = cp[2];
-        const float mx = cp[0] / cz, my = cp[1] / cz;
+        const float icz = 1.f / cz, icz2 = icz * icz;
+        const float mx = cp[0] * icz, my = cp[1] * icz;
         const float ax = tuc[0] - mx * tuc[2], ay = tuc[1] - my * tuc[2];
         const float bx = tvc[0] - mx * tvc[2], by = tvc[1] - my * tvc[2];
         const ss_view_geo& vg = ws.vgeo[v];
         const float cmo[3] = {(c[0] - vg.o_hi[0]) - vg.o_lo[0], (c[1] - vg.o_hi[1]) - vg.o_lo[1],
                               (c[2] - vg.o_hi[2]) - vg.o_lo[2]};
-        const float4 r1 = ws.rec[r].r1;
         const float A2 = r1.x, B2 = r1.y;
         const float Nd = ss_plane_distance(q4, c[0], c[1], c[2], vg.o_hi, vg.o_lo);
+        const float iNd = 1.f / Nd;
         const float detR = vg.detR;
-        const float det0 = detR * su * sv * Nd / cz;
-        const float icz = 1.f / cz, icz2 = icz * icz;
+        const float det0 = detR * su * sv * Nd * icz;
         const float m11 = fx * fx * (ax * ax + bx * bx) * icz2;
         const float m12 = fx * fy * (ax * ay + bx * by) * icz2;
         const float m22 = fy * fy * (ay * ay + by * by) * icz2;
         const float sdg = fx * fy * det0 * icz2;
         const float Dn = sdg * sdg + sig * (m11 + m22) + sig * sig;
-        const float nf = fabsf(sdg) * rsqrtf(Dn);
-        const float qa = (m22 + sig) / Dn, qb = -m12 / Dn, qc = (m11 + sig) / Dn;
+        const float iDn = 1.f / Dn;
         const float rsD = rsqrtf(Dn);
+        const float nf = fabsf(sdg) * rsD;
+        const float qa = (m22 + sig) * iDn, qb = -m12 * iDn, qc = (m11 + sig) * iDn;
 
-        // ---- raster parameters -> (qa, qb, qc, Dn)
+        // ---- raster parameters -> (qa, qb, qc, Dn); the factorisation the
+        // forward chose is the one whose P10 it stored as zero
         float dqa = 0.f, dqb = 0.f, dqc = 0.f, dDn = 0.f;
-        if (qa >= qc) {
-            const float P00 = sqrtf(qa), P01 = qb / P00, P11 = rsD / P00;
-            dqb += G[G_P + 1] / P00;
-            dDn += G[G_P + 3] * (-0.5f * rsD / Dn) / P00;
-            const float dP00 = G[G_P + 0] - G[G_P + 1] * P01 / P00 - G[G_P + 3] * P11 / P00;
-            dqa += dP00 / (2.f * P00);
+        if (r0.z == 0.f) {
+            const float P00 = sqrtf(qa), iP = 1.f / P00, P01 = qb * iP, P11 = rsD * iP;
+            dqb += G[G_P + 1] * iP;
+            dDn += G[G_P + 3] * (-0.5f * rsD * iDn) * iP;
+            const float dP00 = G[G_P + 0] - (G[G_P + 1] * P01 + G[G_P + 3] * P11) * iP;
+            dqa += 0.5f * dP00 * iP;
         } else {
-            const float l = sqrtf(qc), P00 = qb / l, P10 = rsD / l;
-            dqb += G[G_P + 0] / l;
-            dDn += G[G_P + 2] * (-0.5f * rsD / Dn) / l;
-            const float dl = G[G_P + 1] - G[G_P + 0] * P00 / l - G[G_P + 2] * P10 / l;
-            dqc += dl / (2.f * l);
+            const float l = sqrtf(qc), il = 1.f / l, P00 = qb * il, P10 = rsD * il;
+            dqb += G[G_P + 0] * il;
+            dDn += G[G_P + 2] * (-0.5f * rsD * iDn) * il;
+            const float dl = G[G_P + 1] - (G[G_P + 0] * P00 + G[G_P + 2] * P10) * il;
+            dqc += 0.5f * dl * il;
         }
-        float dm11 = dqc / Dn, dm12 = -dqb / Dn, dm22 = dqa / Dn;
-        dDn += -(dqa * qa + dqb * qb + dqc * qc) / Dn;
+        float dm11 = dqc * iDn, dm12 = -dqb * iDn, dm22 = dqa * iDn;
+        dDn += -(dqa * qa + dqb * qb + dqc * qc) * iDn;
         // n_f = |sdg| / sqrt(Dn)
         float dsdg = G[G_NF] * copysignf(1.f, sdg) * rsD;
-        dDn += -0.5f * G[G_NF] * nf / Dn;
+        dDn += -0.5f * G[G_NF] * nf * iDn;
         // Dn = sdg^2 + sig (m11 + m22) + sig^2
         dsdg += 2.f * sdg * dDn;
         dm11 += sig * dDn;
@@ -532,11 +588,11 @@ __device__ __forceinline__ void pbwd_surfel(const ss_ws_view& ws, const ss_bwd_a
         float dby = icz2 * (dm22 * fy * fy * 2.f * by + dm12 * fx * fy * bx);
         dcz += -2.f * icz * (dm11 * m11 + dm12 * m12 + dm22 * m22);
         // ---- A2 = cz n'_x / (fx Nd), B2 = cz n'_y / (fy Nd), det0 = detR su sv Nd / cz
-        float dNd = 0.f, dncx = 0.f, dncy = 0.f;
+        float dNd = 0.f;
         dcz += (G[G_A2] * A2 + G[G_B2] * B2) * icz;
-        dncx += G[G_A2] * cz / (fx * Nd);
-        dncy += G[G_B2] * cz / (fy * Nd);
-        dNd += -(G[G_A2] * A2 + G[G_B2] * B2) / Nd;
+        const float dncx = G[G_A2] * cz * iNd / fx;
+        const float dncy = G[G_B2] * cz * iNd / fy;
+        dNd += -(G[G_A2] * A2 + G[G_B2] * B2) * iNd;
         const float kdet = detR * su * sv * icz;     // det0 / Nd
         dNd += ddet0 * kdet;
         gsu += ddet0 * detR * sv * Nd * icz;
@@ -565,14 +621,16 @@ __device__ __forceinline__ void pbwd_surfel(const ss_ws_view& ws, const ss_bwd_a
             gRq[k * 3 + 0] += su * dtu;
             gRq[k * 3 + 1] += sv * dtv;
         }
-        // ---- shading (Eq. ibl) and the AOV channels
+        // ---- shading (Eq. ibl) and the AOV channels; the view direction as
+        // the forward forms it
         const float ox = -(Rc[0] * cam.t[0] + Rc[3] * cam.t[1] + Rc[6] * cam.t[2]);
         const float oy = -(Rc[1] * cam.t[0] + Rc[4] * cam.t[1] + Rc[7] * cam.t[2]);
         const float oz = -(Rc[2] * cam.t[0] + Rc[5] * cam.t[1] + Rc[8] * cam.t[2]);
-        float wv[3] = {ox - c[0], oy - c[1], oz - c[2]};
-        const float wl = sqrtf(wv[0] * wv[0] + wv[1] * wv[1] + wv[2] * wv[2]);
-        const float wo[3] = {wv[0] / wl, wv[1] / wl, wv[2] / wl};
-        const float fs = (flags & SS_FLAG_FLIPPED) ? -1.f : 1.f;
+        const float wv[3] = {ox - c[0], oy - c[1], oz - c[2]};
+        const float iwl = rsqrtf(wv[0] * wv[0] + wv[1] * wv[1] + wv[2] * wv[2]);
+        const float wo[3] = {wv[0] * iwl, wv[1] * iwl, wv[2] * iwl};
+        const bool back = (flags & SS_FLAG_FLIPPED) != 0;
+        const float fs = back ? -1.f : 1.f;
         const float ns[3] = {fs * nrm[0], fs * nrm[1], fs * nrm[2]};
         const float mup = ns[0] * wo[0] + ns[1] * wo[1] + ns[2] * wo[2];
         const float mu = fminf(fmaxf(mup, 0.f), 1.f);
@@ -583,17 +641,11 @@ __device__ __forceinline__ void pbwd_surfel(const ss_ws_view& ws, const ss_bwd_a
         gmetal += G[G_CH + 7];
         const float dcol[3] = {G[G_CH + 0], G[G_CH + 1], G[G_CH + 2]};
         if (dcol[0] != 0.f || dcol[1] != 0.f || dcol[2] != 0.f) {
-            float un, vn, ur, vr;
-            dir_to_uv(ns[0], ns[1], ns[2], un, vn);
+            float ur, vr;
             dir_to_uv(refl[0], refl[1], refl[2], ur, vr);
-            lk3 Ld = lookup3(irr, un, vn, a.ed.irr_width, a.ed.irr_height, true);
-            const float rcl = fminf(fmaxf(rough, 0.f), 1.f);
-            const float lc = rcl * (float)(nL - 1);
-            const int l0 = min((int)floorf(lc), nL - 1), l1 = min(l0 + 1, nL - 1);
-            const float lf = lc - (float)l0;
-            int W0, H0, W1, H1;
-            const int64_t o0 = spec_level_off_b(a.ed, l0, W0, H0), o1 = spec_level_off_b(a.ed, l1, W1, H1);
-            lk3 S0 = lookup3(spec + o0, ur, vr, W0, H0, true), S1 = lookup3(spec + o1, ur, vr, W1, H1, true);
+            const float Ld[3] = {back ? LdB[0] : LdF[0], back ? LdB[1] : LdF[1], back ? LdB[2] : LdF[2]};
+            const ss_taps t0 = bilinear_taps(ur, vr, W0, H0, true), t1 = bilinear_taps(ur, vr, W1, H1, true);
+            const lk3 S0 = lookup3(spec + o0, t0, W0, H0), S1 = lookup3(spec + o1, t1, W1, H1);
             ss_taps lt = bilinear_taps(mu, rcl, lutn, lutn, false);
             float be[2], dbe_mu[2], dbe_r[2];
             for (int z = 0; z < 2; ++z) {
@@ -603,15 +655,17 @@ __device__ __forceinline__ void pbwd_surfel(const ss_ws_view& ws, const ss_bwd_a
                 dbe_mu[z] = (float)lutn * ((1.f - lt.fy) * (a1 - a0) + lt.fy * (a3 - a2));
                 dbe_r[z] = (float)lutn * ((1.f - lt.fx) * (a2 - a0) + lt.fx * (a3 - a1));
             }
-            float dLd[3], dLs[3], dbe1 = 0.f, dbe2 = 0.f, dlf = 0.f;
+            float dLs[3], dbe1 = 0.f, dbe2 = 0.f, dlf = 0.f;
             for (int k = 0; k < 3; ++k) {
                 const float F0 = 0.04f * (1.f - metal) + rho[k] * metal;
                 const float kd = (1.f - F0) * (1.f - metal);
                 const float Ls = (1.f - lf) * S0.v[k] + lf * S1.v[k];
                 // col = kd rho Ld + Ls (F0 be1 + be2)
-                const float dkd = dcol[k] * rho[k] * Ld.v[k];
-                grho[k] += dcol[k] * kd * Ld.v[k];
-                dLd[k] = dcol[k] * kd * rho[k];
+                const float dkd = dcol[k] * rho[k] * Ld[k];
+                grho[k] += dcol[k] * kd * Ld[k];
+                const float dLd = dcol[k] * kd * rho[k];
+                if (back) gLdB[k] += dLd;
+                else gLdF[k] += dLd;
                 dLs[k] = dcol[k] * (F0 * be[0] + be[1]);
                 float dF0 = dcol[k] * Ls * be[0];
                 dbe1 += dcol[k] * Ls * F0;
@@ -626,55 +680,46 @@ __device__ __forceinline__ void pbwd_surfel(const ss_ws_view& ws, const ss_bwd_a
             if (rough > 0.f && rough < 1.f) grough += dbe1 * dbe_r[0] + dbe2 * dbe_r[1] + dlf * (float)(nL - 1);
             float dmu = dbe1 * dbe_mu[0] + dbe2 * dbe_mu[1];
             float dmup = (mup > 0.f && mup < 1.f) ? dmu : 0.f;
-            // environment texels
-            // environment texels: the block's own scene into shared memory, the
-            // rest into the workspace's RGBA accumulators (irradiance texels
-            // first, then the specular stack)
-            const bool mine = scene == pv.scene;
-            float4* acc = ws.env_acc + scene * ws.env_texels;
-            const int64_t irr_tex = (int64_t)a.ed.irr_width * a.ed.irr_height;
-            if (d_irr) {
-                if (pv.irr && mine) scatter3(pv.irr, un, vn, a.ed.irr_width, a.ed.irr_height, true, dLd, 1.f);
-                else scatter4(acc, un, vn, a.ed.irr_width, a.ed.irr_height, dLd, 1.f);
-            }
+            // specular texels: the block's own scene's small levels into shared
+            // memory, the rest into the workspace's RGBA accumulators
+            // (irradiance texels first, then the specular stack)
             if (d_spec) {
+                const bool mine = scene == pv.scene;
+                float4* acc = ws.env_acc + scene * ws.env_texels + (int64_t)IW * IH;
                 if (pv.spec && mine && l0 >= pv.level)
-                    scatter3(pv.spec + (o0 - pv.spec_off), ur, vr, W0, H0, true, dLs, 1.f - lf);
+                    scatter3(pv.spec + (o0 - pv.spec_off), t0, dLs, 1.f - lf);
                 else
-                    scatter4(acc + irr_tex + o0 / 3, ur, vr, W0, H0, dLs, 1.f - lf);
+                    scatter4(acc + o0 / 3, t0, dLs, 1.f - lf);
                 if (pv.spec && mine && l1 >= pv.level)
-                    scatter3(pv.spec + (o1 - pv.spec_off), ur, vr, W1, H1, true, dLs, lf);
+                    scatter3(pv.spec + (o1 - pv.spec_off), t1, dLs, lf);
                 else
-                    scatter4(acc + irr_tex + o1 / 3, ur, vr, W1, H1, dLs, lf);
+                    scatter4(acc + o1 / 3, t1, dLs, lf);
             }
-            // directions: Ld(uv(ns)), Ls(uv(refl))
-            float gun = 0.f, gvn = 0.f, gur = 0.f, gvr = 0.f;
+            // reflected direction: Ls(uv(refl))
+            float gur = 0.f, gvr = 0.f;
             for (int k = 0; k < 3; ++k) {
-                gun += dLd[k] * Ld.du[k];
-                gvn += dLd[k] * Ld.dv[k];
                 gur += dLs[k] * ((1.f - lf) * S0.du[k] + lf * S1.du[k]);
                 gvr += dLs[k] * ((1.f - lf) * S0.dv[k] + lf * S1.dv[k]);
             }
-            float dnsv[3], drefl[3];
-            uv_grad(ns, gun, gvn, dnsv);
-            float rl = sqrtf(refl[0] * refl[0] + refl[1] * refl[1] + refl[2] * refl[2]);
-            float rn[3] = {refl[0] / rl, refl[1] / rl, refl[2] / rl};
+            float drefl[3];
+            const float irl = rsqrtf(refl[0] * refl[0] + refl[1] * refl[1] + refl[2] * refl[2]);
+            const float rn[3] = {refl[0] * irl, refl[1] * irl, refl[2] * irl};
             float drn[3];
             uv_grad(rn, gur, gvr, drn);
             // through the normalisation of refl (|refl| = 1 up to rounding)
-            float rd = drn[0] * rn[0] + drn[1] * rn[1] + drn[2] * rn[2];
-            for (int k = 0; k < 3; ++k) drefl[k] = (drn[k] - rn[k] * rd) / rl;
+            const float rd = drn[0] * rn[0] + drn[1] * rn[1] + drn[2] * rn[2];
+            for (int k = 0; k < 3; ++k) drefl[k] = (drn[k] - rn[k] * rd) * irl;
             // refl = 2 mup ns - wo, mup = ns.wo
             float dwo[3];
             const float rdn = drefl[0] * ns[0] + drefl[1] * ns[1] + drefl[2] * ns[2];
             dmup += 2.f * rdn;
             for (int k = 0; k < 3; ++k) {
-                dns[k] += dnsv[k] + 2.f * mup * drefl[k] + dmup * wo[k];
+                dns[k] += 2.f * mup * drefl[k] + dmup * wo[k];
                 dwo[k] = -drefl[k] + dmup * ns[k];
             }
             // wo = normalize(o - c)
             const float wd = dwo[0] * wo[0] + dwo[1] * wo[1] + dwo[2] * wo[2];
-            for (int k = 0; k < 3; ++k) dcv[k] += -(dwo[k] - wo[k] * wd) / wl;
+            for (int k = 0; k < 3; ++k) dcv[k] += -(dwo[k] - wo[k] * wd) * iwl;
         }
         for (int k = 0; k < 3; ++k) dn[k] += fs * dns[k];
         for (int k = 0; k < 3; ++k) {
@@ -683,6 +728,14 @@ __device__ __forceinline__ void pbwd_surfel(const ss_ws_view& ws, const ss_bwd_a
         }
     }
     if (!any_view) return;
+    // ---- irradiance: once per side, from the view sums
+    {
+        float gRn[3] = {0.f, 0.f, 0.f};
+        float4* acc = d_irr ? ws.env_acc + scene * ws.env_texels : nullptr;
+        irr_side_adjoint(irr, IW, IH, nrm, 1.f, gLdF, acc, gRn);
+        irr_side_adjoint(irr, IW, IH, nrm, -1.f, gLdB, acc, gRn);
+        for (int k = 0; k < 3; ++k) gRq[k * 3 + 2] += gRn[k];
+    }
     // ---- R(q / |q|) -> q (linear in the summed dL/dR)
     const float qn = rsqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
     const float w = q4.x * qn, x = q4.y * qn, y = q4.z * qn, z = q4.w * qn;
@@ -731,15 +784,13 @@ __global__ void __launch_bounds__(128, 4) project_bwd_kernel(ss_ws_view ws, ss_b
         return lo;
     };
     const int scene = scene_of(i0);
-    const int irr_floats = A.f.ed.irr_width * A.f.ed.irr_height * 3;
-    const bool use = A.genv.irr != nullptr && A.genv.spec != nullptr;
+    const bool use = A.genv.spec != nullptr && priv_spec_floats > 0;
     env_priv pv;
-    pv.irr = use ? priv : nullptr;
-    pv.spec = use ? priv + irr_floats : nullptr;
+    pv.spec = use ? priv : nullptr;
     pv.scene = scene;
     pv.level = priv_level;
     pv.spec_off = priv_spec_off;
-    const int n_priv = irr_floats + priv_spec_floats;
+    const int n_priv = priv_spec_floats;
     if (use)
         for (int k = threadIdx.x; k < n_priv; k += blockDim.x) priv[k] = 0.f;
     __syncthreads();
@@ -747,12 +798,11 @@ __global__ void __launch_bounds__(128, 4) project_bwd_kernel(ss_ws_view ws, ss_b
         pbwd_surfel(ws, A, i, i < L->scene_begin[scene + 1] ? scene : scene_of(i), pv);
     __syncthreads();
     if (use) {   // texel by texel into the RGBA accumulators
-        float4* acc = ws.env_acc + scene * ws.env_texels;
-        const int irr_tex = irr_floats / 3;
+        float4* acc = ws.env_acc + scene * ws.env_texels + (int64_t)A.f.ed.irr_width * A.f.ed.irr_height +
+                      priv_spec_off / 3;
         for (int k = threadIdx.x; k < n_priv / 3; k += blockDim.x) {
             const float4 v = make_float4(priv[3 * k], priv[3 * k + 1], priv[3 * k + 2], 0.f);
-            if (v.x != 0.f || v.y != 0.f || v.z != 0.f)
-                atomicAdd(k < irr_tex ? acc + k : acc + irr_tex + priv_spec_off / 3 + (k - irr_tex), v);
+            if (v.x != 0.f || v.y != 0.f || v.z != 0.f) atomicAdd(acc + k, v);
         }
     }
 }
@@ -776,14 +826,13 @@ __global__ void env_acc_flush_kernel(const float4* acc, int64_t texels, int64_t 
 void ss_launch_project_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st) {
     int64_t n = L.scene_begin[L.n_scenes];
     if (n <= 0 || L.total_records <= 0) return;
-    // privatise the irradiance map and the specular levels whose total fits 48 KB
-    const int irr_floats = a.f.ed.irr_width * a.f.ed.irr_height * 3;
+    // privatise the smallest specular levels whose total fits 48 KB
     int level = a.f.ed.n_levels;
     int64_t priv_spec = 0;
     while (level > 1) {
         int W, H;
         ss_env_level_size(&a.f.ed, level - 1, &W, &H);
-        if (irr_floats + priv_spec + (int64_t)W * H * 3 > 12288) break;
+        if (priv_spec + (int64_t)W * H * 3 > 12288) break;
         priv_spec += (int64_t)W * H * 3;
         --level;
     }
@@ -795,7 +844,7 @@ void ss_launch_project_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bw
     }
     const int64_t per_block = a.f.p.pbwd_block ? a.f.p.pbwd_block : 128;   // surfels per CTA (all their views)
     const unsigned blocks = (unsigned)((n + per_block - 1) / per_block);
-    const size_t smem = sizeof(float) * (size_t)(irr_floats + priv_spec);
+    const size_t smem = sizeof(float) * (size_t)priv_spec;
     static std::atomic<unsigned long long> optin{0};
     ss_smem_optin(project_bwd_kernel, 64 * 1024, optin);
     ss_note_launch();

@@ -38,7 +38,7 @@ __device__ __forceinline__ int64_t spec_level_off(const ss_env_desc& ed, int i, 
     return off;
 }
 
-__global__ void __launch_bounds__(256) project_kernel(ss_ws_view ws, ss_fwd_args a, int64_t n_total) {
+__global__ void __launch_bounds__(256, 4) project_kernel(ss_ws_view ws, ss_fwd_args a, int64_t n_total) {
     const ss_layout* L = ws.layout;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n_total) return;

@@ -153,20 +153,32 @@ __device__ __forceinline__ dfl df_dot3_add(float a0, float a1, float a2, float x
 // a surfel with centre c and normal n = R(q/|q|) e_z.  For nearly edge-on
 // surfels it is a small difference of O(1) terms, so it is formed in
 // double-float from n = (2(xz+wy), 2(yz-wx), w^2-x^2-y^2+z^2) / |q|^2 and o.
-__device__ __forceinline__ float ss_plane_distance(float4 q, float c0, float c1, float c2, const float o_hi[3],
-                                                   const float o_lo[3]) {
+struct ss_plane_n {
+    dfl n0, n1, n2;   // 2(xz+wy), 2(yz-wx), w^2-x^2-y^2+z^2 in double-float
+    float qq;         // |q|^2
+};
+__device__ __forceinline__ ss_plane_n ss_plane_normal(float4 q) {
     const float qw = q.x, qx = q.y, qy = q.z, qz = q.w;
+    ss_plane_n p;
     dfl n0 = df_add(two_prod(qx, qz), two_prod(qw, qy));
     dfl n1 = df_add(two_prod(qy, qz), two_prod(-qw, qx));
-    dfl n2 = df_add(df_add(two_prod(qw, qw), two_prod(-qx, qx)), df_add(two_prod(-qy, qy), two_prod(qz, qz)));
-    n0 = {2.f * n0.hi, 2.f * n0.lo};
-    n1 = {2.f * n1.hi, 2.f * n1.lo};
+    p.n2 = df_add(df_add(two_prod(qw, qw), two_prod(-qx, qx)), df_add(two_prod(-qy, qy), two_prod(qz, qz)));
+    p.n0 = {2.f * n0.hi, 2.f * n0.lo};
+    p.n1 = {2.f * n1.hi, 2.f * n1.lo};
+    p.qq = qw * qw + qx * qx + qy * qy + qz * qz;
+    return p;
+}
+__device__ __forceinline__ float ss_plane_distance_n(const ss_plane_n& p, float c0, float c1, float c2,
+                                                     const float o_hi[3], const float o_lo[3]) {
     dfl d0 = df_add_f({-o_hi[0], -o_lo[0]}, c0);
     dfl d1 = df_add_f({-o_hi[1], -o_lo[1]}, c1);
     dfl d2 = df_add_f({-o_hi[2], -o_lo[2]}, c2);
-    dfl nd = df_add(df_add(df_mul(n0, d0), df_mul(n1, d1)), df_mul(n2, d2));
-    const float qq = qw * qw + qx * qx + qy * qy + qz * qz;
-    return (nd.hi + nd.lo) / qq;
+    dfl nd = df_add(df_add(df_mul(p.n0, d0), df_mul(p.n1, d1)), df_mul(p.n2, d2));
+    return (nd.hi + nd.lo) / p.qq;
+}
+__device__ __forceinline__ float ss_plane_distance(float4 q, float c0, float c1, float c2, const float o_hi[3],
+                                                   const float o_lo[3]) {
+    return ss_plane_distance_n(ss_plane_normal(q), c0, c1, c2, o_hi, o_lo);
 }
 
 // ------------------------------------------------------------------------
@@ -207,9 +219,10 @@ __device__ __forceinline__ ss_taps bilinear_taps(float u, float v, int W, int H,
     t.fx = X - x0f;
     t.fy = Y - y0f;
     int xa, xb;
-    if (wrap) {
-        xa = ((x0 % W) + W) % W;
-        xb = (xa + 1) % W;
+    if (wrap) {   // x0 mod W: one compare for (u in [0, 1] gives x0 in [-1, W - 1]), the division otherwise
+        xa = x0 < 0 ? x0 + W : (x0 >= W ? x0 - W : x0);
+        if ((unsigned)xa >= (unsigned)W) xa = ((x0 % W) + W) % W;
+        xb = xa + 1 == W ? 0 : xa + 1;
     } else {
         xa = min(max(x0, 0), W - 1);
         xb = min(max(x0 + 1, 0), W - 1);
