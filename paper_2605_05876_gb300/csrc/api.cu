@@ -190,9 +190,9 @@ static ws_plan plan_ws(const ss_layout& L, const ss_render_params& p, int with_b
     w.layout = take(sizeof(ss_layout));
     w.vgeo = take(sizeof(ss_view_geo) * SS_MAX_VIEWS);
     w.rec = take(sizeof(ss_rec) * (size_t)L.total_records);
-    w.tc = take(sizeof(uint32_t) * (size_t)L.total_tiles);
+    w.tc = take(sizeof(uint32_t) * SS_CNT_STRIDE * (size_t)L.total_tiles);
     w.ts = take(sizeof(uint32_t) * ((size_t)L.total_tiles + 1));
-    w.tcur = take(sizeof(uint32_t) * (size_t)L.total_tiles);
+    w.tcur = take(sizeof(uint32_t) * SS_CNT_STRIDE * (size_t)L.total_tiles);
     w.keys = take(sizeof(unsigned long long) * (size_t)p.max_instances);
     w.keys_alt = take(sizeof(unsigned long long) * (size_t)p.max_instances);
     w.rects = take(sizeof(uint2) * (size_t)p.max_instances);
@@ -377,8 +377,8 @@ static ss_status forward_core(const ss_batch_desc* b, const ss_surfels* s, const
     set_layout_kernel<<<1, 256, 0, st>>>(W.layout, L);
     ss_note_launch();
     view_geo_kernel<<<(L.n_views + 63) / 64, 64, 0, st>>>(b->cams_dev, W.vgeo, L.n_views);
-    CK(cudaMemsetAsync(W.tile_count, 0, sizeof(uint32_t) * (size_t)L.total_tiles, st));
-    CK(cudaMemsetAsync(W.tile_cursor, 0, sizeof(uint32_t) * (size_t)L.total_tiles, st));
+    CK(cudaMemsetAsync(W.tile_count, 0, sizeof(uint32_t) * SS_CNT_STRIDE * (size_t)L.total_tiles, st));
+    CK(cudaMemsetAsync(W.tile_cursor, 0, sizeof(uint32_t) * SS_CNT_STRIDE * (size_t)L.total_tiles, st));
     {
         stage_scope sc(0, st);
         ss_launch_project(W, L, a, st);

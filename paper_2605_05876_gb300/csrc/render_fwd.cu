@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(256, 4) project_kernel(ss_ws_view ws, ss_fwd_a
         if (valid) {
             int tx0 = i0 / SS_TILE, tx1 = i1 / SS_TILE, ty0 = j0 / SS_TILE, ty1 = j1 / SS_TILE;
             for (int ty = ty0; ty <= ty1; ++ty)
-                for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&ws.tile_count[vl.tile_off + ty * vl.tiles_x + tx], 1u);
+                for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&ws.tile_count[(size_t)(vl.tile_off + ty * vl.tiles_x + tx) * SS_CNT_STRIDE], 1u);
         }
     }
 }
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const uint32_t* cnt, uint32_
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int base = 0; base < n; base += blockDim.x) {
         int i = base + threadIdx.x;
-        uint32_t v = i < n ? cnt[i] : 0u;
+        uint32_t v = i < n ? cnt[(size_t)i * SS_CNT_STRIDE] : 0u;
         uint32_t x = v;
         for (int o = 1; o < 32; o <<= 1) {
             uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -328,7 +328,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(ss_ws_view ws, int64_t tot
         for (int u = 0; u < 4; ++u) {
             const int q = b + u;
             t[u] = q < nt ? vl.tile_off + (ty0 + q / ntx) * vl.tiles_x + tx0 + q % ntx : -1;
-            if (t[u] >= 0) pos[u] = atomicAdd(&ws.tile_cursor[t[u]], 1u);
+            if (t[u] >= 0) pos[u] = atomicAdd(&ws.tile_cursor[(size_t)t[u] * SS_CNT_STRIDE], 1u);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
@@ -345,27 +345,67 @@ __device__ __forceinline__ uint2 rect_of(const ss_ws_view& ws, unsigned long lon
     return make_uint2(__float_as_uint(r3.z), __float_as_uint(r3.w));
 }
 
-#define SORT_THREADS 512
-#define SORT_CAP 8192  // keys sorted in shared memory at once (64 KB)
+#define SORT_THREADS 256
+#define SORT_KPL 32                              // keys per thread, held in registers
+#define SORT_CAP (SORT_THREADS * SORT_KPL)       // keys sorted by one CTA at once (8192)
 
-// Bitonic sort of npow2 keys in shared memory: every thread takes whole
-// compare-exchange pairs (i, i + j), i with bit j clear, so no iteration is
-// spent on the upper element of a pair.
-__device__ void bitonic_smem(unsigned long long* s, int npow2) {
-    const int half = npow2 >> 1;
-    for (int k = 2; k <= npow2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int c = threadIdx.x; c < half; c += blockDim.x) {
-                const int i = ((c & ~(j - 1)) << 1) | (c & (j - 1));   // insert a 0 at bit log2(j)
-                const int ixj = i | j;
-                const unsigned long long a = s[i], b = s[ixj];
-                const bool up = (i & k) == 0;
-                if ((a > b) == up) {
-                    s[i] = b;
-                    s[ixj] = a;
+// Bitonic sort of N (a power of two, N <= SORT_CAP) keys held in registers:
+// thread t holds positions t*KPL .. t*KPL + KPL - 1.  Compare-exchange
+// distances j < KPL stay inside a thread, KPL <= j < 32 KPL go across the
+// lanes of a warp by shuffles, and only j >= 32 KPL across warps through
+// shared memory (laid out [k][thread], so that every access is conflict-free).
+__device__ __forceinline__ void cmpx(unsigned long long& a, unsigned long long& b, bool up) {
+    const bool sw = (a > b) == up;
+    const unsigned long long lo = sw ? b : a, hi = sw ? a : b;
+    a = lo;
+    b = hi;
+}
+
+template <int KPL>
+__device__ void bitonic_regs(unsigned long long (&x)[KPL], int N, unsigned long long* xs) {
+    const int t = threadIdx.x, lane = t & 31;
+    // whole warps take part (the shuffles need every lane); lanes past N hold padding
+    const bool active = (t & ~31) * KPL < N;
+    for (int size = 2; size <= N; size <<= 1) {
+        // across warps
+        for (int j = size >> 1; j >= 32 * KPL; j >>= 1) {
+            if (active) {
+#pragma unroll
+                for (int k = 0; k < KPL; ++k) xs[k * SORT_THREADS + t] = x[k];
+            }
+            __syncthreads();
+            if (active) {
+                const int pt = t ^ (j / KPL);
+                const bool up = ((t * KPL) & size) == 0, lower = (t & (j / KPL)) == 0;
+#pragma unroll
+                for (int k = 0; k < KPL; ++k) {
+                    const unsigned long long y = xs[k * SORT_THREADS + pt];
+                    const bool keep_min = lower == up;
+                    x[k] = keep_min ? (y < x[k] ? y : x[k]) : (y > x[k] ? y : x[k]);
                 }
             }
             __syncthreads();
+        }
+        if (!active) continue;
+        // across the lanes of a warp
+        for (int j = min(size >> 1, 16 * KPL); j >= KPL; j >>= 1) {
+            const int m = j / KPL;
+            const bool up = ((t * KPL) & size) == 0, lower = (lane & m) == 0;
+            const bool keep_min = lower == up;
+#pragma unroll
+            for (int k = 0; k < KPL; ++k) {
+                const unsigned long long y = __shfl_xor_sync(0xffffffffu, x[k], m);
+                x[k] = keep_min ? (y < x[k] ? y : x[k]) : (y > x[k] ? y : x[k]);
+            }
+        }
+        // inside the thread
+#pragma unroll
+        for (int j = KPL / 2; j >= 1; j >>= 1) {
+            if (j < size) {
+#pragma unroll
+                for (int k = 0; k < KPL; ++k)
+                    if ((k & j) == 0) cmpx(x[k], x[k | j], ((t * KPL + k) & size) == 0);
+            }
         }
     }
 }
@@ -391,8 +431,8 @@ __device__ void merge_runs(const unsigned long long* A, int na, const unsigned l
     }
 }
 
-__global__ void __launch_bounds__(SORT_THREADS) tile_sort_kernel(ss_ws_view ws, int total_tiles) {
-    extern __shared__ unsigned long long sk[];
+__global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view ws, int total_tiles) {
+    extern __shared__ unsigned long long xs[];
     const int t = blockIdx.x;
     const int64_t cap = ws.max_instances;
     int64_t b = ws.tile_start[t], e = ws.tile_start[t + 1];
@@ -406,17 +446,32 @@ __global__ void __launch_bounds__(SORT_THREADS) tile_sort_kernel(ss_ws_view ws, 
         return;
     }
     unsigned long long* Alt = ws.keys_alt + b;
-    // chunks of SORT_CAP sorted in shared memory
+    const int base = threadIdx.x * SORT_KPL;
+    // chunks of SORT_CAP sorted in registers
     for (int c0 = 0; c0 < n; c0 += SORT_CAP) {
-        int m = min(SORT_CAP, n - c0);
-        int p2 = 1;
-        while (p2 < m) p2 <<= 1;
-        for (int i = threadIdx.x; i < p2; i += blockDim.x) sk[i] = i < m ? K[c0 + i] : ~0ull;
-        __syncthreads();
-        bitonic_smem(sk, p2);
-        for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            K[c0 + i] = sk[i];
-            if (n <= SORT_CAP) RC[i] = rect_of(ws, sk[i]);
+        const int m = min(SORT_CAP, n - c0);
+        int N = 2;
+        while (N < m) N <<= 1;
+        unsigned long long x[SORT_KPL];
+#pragma unroll
+        for (int k = 0; k < SORT_KPL; ++k) x[k] = base + k < m ? K[c0 + base + k] : ~0ull;
+        bitonic_regs<SORT_KPL>(x, N, xs);
+        __syncthreads();   // every thread's reads of this chunk are done before the stores
+#pragma unroll
+        for (int k = 0; k < SORT_KPL; ++k)
+            if (base + k < m) K[c0 + base + k] = x[k];
+        if (n <= SORT_CAP) {
+            // rectangles of the sorted keys, 8 gathers in flight
+#pragma unroll
+            for (int k0 = 0; k0 < SORT_KPL; k0 += 8) {
+                uint2 rr[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (base + k0 + k < m) rr[k] = rect_of(ws, x[k0 + k]);
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (base + k0 + k < m) RC[base + k0 + k] = rr[k];
+            }
         }
         __syncthreads();
     }

@@ -11,6 +11,9 @@
 #define SS_TILE 16                 // 16 x 16 pixel tiles (App. A)
 #define SS_TILE_PIX (SS_TILE * SS_TILE)
 #define SS_NCH 12                  // averaged channels: rgb, albedo 3, rough, metal, normal 3, depth
+// Tile counters and cursors take the atomics of every tile instance; one per
+// SS_CNT_STRIDE words spreads them over the L2 slices instead of a few.
+#define SS_CNT_STRIDE 32
 #define SS_NGRAD 24                // floats per (view, surfel) gradient record (22 used)
 #define SS_PI_F 3.14159265358979323846f
 
@@ -80,9 +83,9 @@ struct ss_ws_view {
     ss_layout* layout;
     ss_view_geo* vgeo;      // [n_views]
     ss_rec* rec;
-    uint32_t* tile_count;   // [total_tiles]
+    uint32_t* tile_count;   // [total_tiles][SS_CNT_STRIDE] (first word used)
     uint32_t* tile_start;   // [total_tiles + 1]
-    uint32_t* tile_cursor;  // [total_tiles]
+    uint32_t* tile_cursor;  // [total_tiles][SS_CNT_STRIDE] (first word used)
     unsigned long long* keys;      // [max_instances]
     unsigned long long* keys_alt;  // [max_instances]
     uint2* rects;           // [max_instances] support rectangle of each sorted instance
