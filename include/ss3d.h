@@ -131,6 +131,7 @@ typedef struct ss_stats {
     int64_t bwd_fragments;   /* fragments differentiated by the backward raster */
     int64_t staged;          /* (warp block, surfel) pairs the forward raster staged */
     int64_t staged_covering; /* ... of which cover at least one pixel of the block */
+    int64_t bwd_batches;     /* groups of up to 32 fragments the backward raster differentiated together */
 } ss_stats;
 
 /* Stage timing: CUDA events recorded on the launching stream around each

@@ -57,7 +57,8 @@ class ss_render_params(ctypes.Structure):
 
 class ss_stats(ctypes.Structure):
     _fields_ = [("instances", c_i64), ("rect_tests", c_i64), ("lane_tests", c_i64), ("fragments", c_i64),
-                ("layers", c_i64), ("bwd_fragments", c_i64), ("staged", c_i64), ("staged_covering", c_i64)]
+                ("layers", c_i64), ("bwd_fragments", c_i64), ("staged", c_i64), ("staged_covering", c_i64),
+                ("bwd_batches", c_i64)]
 
 
 SS_N_STAGES = 7

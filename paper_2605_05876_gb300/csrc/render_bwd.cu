@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kerne
     // layer_coeff_kernel
     const int K = inside ? __float_as_int(ws.pix_state[gpix]) : 0;
     bool done = !inside || K == 0;
-    unsigned n_frag = 0;
+    unsigned n_frag = 0, n_batch = 0;
 
     // replay state (Algorithm 1): layer index, whether the open layer holds a
     // fragment of positive weight (w = n_f exp(-rho^2/2) > 0 exactly when
@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kerne
     auto run_batches = [&]() {
         __syncwarp();   // records and layer tables written by other lanes
         for (int b0 = 0; b0 < npend; b0 += 32) {
+            ++n_batch;
             const int nb = min(32, npend - b0);
             const bool valid = lane < nb;
             const uint32_t rc = valid ? B.rec[b0 + lane] : 0u;
@@ -311,6 +312,7 @@ __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kerne
         unsigned long long x = n_frag;
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         if (lane == 0 && x) atomicAdd(ws.stats + 5, x);
+        if (lane == 0 && n_batch) atomicAdd(ws.stats + 8, (unsigned long long)n_batch);
     }
 }
 
