@@ -215,6 +215,7 @@ static ss_ws_view carve(void* ws, const ws_plan& w, const ss_render_params& p, i
     ss_ws_view v;
     v.status = (int*)(b + w.status);
     v.stats = (unsigned long long*)(b + w.status + SS_STATS_OFFSET);
+    v.work = (unsigned int*)(b + w.status + SS_WORK_OFFSET);
     v.layout = (ss_layout*)(b + w.layout);
     v.vgeo = (ss_view_geo*)(b + w.vgeo);
     v.rec = (ss_rec*)(b + w.rec);
@@ -468,6 +469,7 @@ extern "C" ss_status ss_render_backward(const ss_batch_desc* b, const ss_surfels
     CK(cudaMemsetAsync(W.grad_rec, 0, sizeof(float) * SS_NGRAD * (size_t)L.total_records, st));
     if (a.genv.irr || a.genv.spec)
         CK(cudaMemsetAsync(W.env_acc, 0, sizeof(float4) * (size_t)W.env_texels * (size_t)L.n_scenes, st));
+    CK(cudaMemsetAsync(W.work + 1, 0, sizeof(unsigned int), st));   // backward work-queue head
     {
         stage_scope sc(3, st);
         ss_launch_raster_bwd(W, L, a, st);

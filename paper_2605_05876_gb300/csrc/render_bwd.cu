@@ -121,17 +121,18 @@ __global__ void __launch_bounds__(256) layer_coeff_kernel(ss_ws_view ws, ss_bwd_
 // AOV = false when no AOV gradient is given: the AOV channels' coefficients
 // are zero, so only P, A2, B2, the centre, n_f and RGB (the first 12 values
 // of the record) are differentiated and summed.
+// The kernel is persistent, like the forward one: warps take (tile, block)
+// items from a queue.
 template <bool AOV, int RWPB_BWD>
-__global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kernel(ss_ws_view ws, ss_bwd_args a) {
+__device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_bwd_args& a, const int gw,
+                                                 unsigned char* bwd_smem) {
     constexpr int NV = AOV ? G_N : G_CH + 3;   // values per fragment
     constexpr int NC = AOV ? SS_NCH : 3;       // channels with a coefficient
-    extern __shared__ __align__(16) unsigned char bwd_smem[];
     ss_wstage* Wst = reinterpret_cast<ss_wstage*>(bwd_smem);
     ss_bwarp* Bws = reinterpret_cast<ss_bwarp*>(bwd_smem + RWPB_BWD * sizeof(ss_wstage));
     const ss_layout* L = ws.layout;
     const int lw = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * RWPB_BWD + lw;        // 8 warps per tile
-    const int tile = gw >> 3, warp = gw & 7;
+    const int tile = gw >> 3, warp = gw & 7;          // 8 blocks per tile
     const int view = find_view_tile(L, tile);
     const ss_view_layout& vl = L->v[view];
     const int lt = tile - vl.tile_off;
@@ -316,12 +317,30 @@ __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kerne
     }
 }
 
+template <bool AOV, int RWPB_BWD>
+__global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kernel(ss_ws_view ws, ss_bwd_args a,
+                                                                                  int n_items) {
+    extern __shared__ __align__(16) unsigned char bwd_smem[];
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = (int)atomicAdd(ws.work + 1, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= n_items) break;
+        raster_bwd_block<AOV, RWPB_BWD>(ws, a, item, bwd_smem);
+        __syncwarp();
+    }
+}
+
 template <bool AOV, int W>
 static void launch_raster_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st) {
     const int smem = W * (int)(sizeof(ss_wstage) + sizeof(ss_bwarp));
-    static std::atomic<unsigned long long> optin{0};
+    static std::atomic<unsigned long long> optin{0}, resident{0};
     ss_smem_optin(raster_bwd_kernel<AOV, W>, smem, optin);
-    raster_bwd_kernel<AOV, W><<<(unsigned)(L.total_tiles * 8 / W), 32 * W, smem, st>>>(ws, a);
+    const int n_items = (int)(L.total_tiles * 8);
+    const int ctas = ss_resident_ctas(raster_bwd_kernel<AOV, W>, 32 * W, smem, resident);
+    const int grid = max(1, min(ctas > 0 ? ctas : 1, (n_items + W - 1) / W));
+    raster_bwd_kernel<AOV, W><<<grid, 32 * W, smem, st>>>(ws, a, n_items);
 }
 
 void ss_launch_raster_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st) {

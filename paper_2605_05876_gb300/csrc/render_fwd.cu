@@ -517,20 +517,21 @@ void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_a
 // ------------------------------------------------------------------------
 // per-pixel rasteriser (Algorithm 1, Eq. alpha, Eq. compositing)
 //
-// One CTA per tile, one warp per 8 x 4 pixel block; every warp streams the
-// tile's z_start-sorted list on its own (raster_common.cuh), so a warp with
-// little work never waits for a busy one, and a warp whose 32 pixels have all
-// reached K_max layers stops reading the list.
+// One warp per 8 x 4 pixel block of a tile; every warp streams the tile's
+// z_start-sorted list on its own (raster_common.cuh), so a warp with little
+// work never waits for a busy one, and a warp whose 32 pixels have all
+// reached K_max layers stops reading the list.  The kernel is persistent:
+// as many warps as fit on the device take (tile, block) items from a queue
+// in item order, so no warp slot idles while items are left.
 
 template <bool STATS, int RWPB_FWD>
-__global__ void __launch_bounds__(32 * RWPB_FWD, 24 / RWPB_FWD) raster_fwd_kernel(ss_ws_view ws, ss_fwd_args a) {
-    extern __shared__ __align__(16) unsigned char fwd_smem[];
+__device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_fwd_args& a, const int gw,
+                                                 unsigned char* fwd_smem) {
     ss_wstage* Wst = reinterpret_cast<ss_wstage*>(fwd_smem);                          // [RWPB_FWD warps][2]
     uint2* Wrect = reinterpret_cast<uint2*>(fwd_smem + 2 * RWPB_FWD * sizeof(ss_wstage));  // [RWPB_FWD][2][WSLOTS]
     const ss_layout* L = ws.layout;
     const int lw = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * RWPB_FWD + lw;        // 8 warps per tile
-    const int tile = gw >> 3, warp = gw & 7;
+    const int tile = gw >> 3, warp = gw & 7;          // 8 blocks per tile
     const int view = find_view_tile(L, tile);
     const ss_view_layout& vl = L->v[view];
     const int lt = tile - vl.tile_off;
@@ -688,12 +689,30 @@ __global__ void __launch_bounds__(32 * RWPB_FWD, 24 / RWPB_FWD) raster_fwd_kerne
     }
 }
 
+template <bool STATS, int RWPB_FWD>
+__global__ void __launch_bounds__(32 * RWPB_FWD, 24 / RWPB_FWD) raster_fwd_kernel(ss_ws_view ws, ss_fwd_args a,
+                                                                                  int n_items) {
+    extern __shared__ __align__(16) unsigned char fwd_smem[];
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = (int)atomicAdd(ws.work + 0, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= n_items) break;
+        raster_fwd_block<STATS, RWPB_FWD>(ws, a, item, fwd_smem);
+        __syncwarp();
+    }
+}
+
 template <bool STATS, int W>
 static void launch_raster_fwd(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st) {
     const int smem = 2 * W * ((int)sizeof(ss_wstage) + WSLOTS * (int)sizeof(uint2));
-    static std::atomic<unsigned long long> optin{0};
+    static std::atomic<unsigned long long> optin{0}, resident{0};
     ss_smem_optin(raster_fwd_kernel<STATS, W>, smem, optin);
-    raster_fwd_kernel<STATS, W><<<(unsigned)(L.total_tiles * 8 / W), 32 * W, smem, st>>>(ws, a);
+    const int n_items = (int)(L.total_tiles * 8);
+    const int ctas = ss_resident_ctas(raster_fwd_kernel<STATS, W>, 32 * W, smem, resident);
+    const int grid = max(1, min(ctas > 0 ? ctas : 1, (n_items + W - 1) / W));
+    raster_fwd_kernel<STATS, W><<<grid, 32 * W, smem, st>>>(ws, a, n_items);
 }
 
 void ss_launch_raster_fwd(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st) {

@@ -77,9 +77,13 @@ struct ss_view_geo {
 // device status bits live in the first word of the workspace; the work
 // counters (ss_stats, int64 x 8) at byte 64 of the same 256-byte block
 #define SS_STATS_OFFSET 64
+// work-queue heads of the persistent rasterisers (uint32: forward, backward)
+// at byte 192 of the same block
+#define SS_WORK_OFFSET 192
 struct ss_ws_view {
     int* status;
     unsigned long long* stats;
+    unsigned int* work;     // [2] next (tile, warp block) item of the forward / backward raster
     ss_layout* layout;
     ss_view_geo* vgeo;      // [n_views]
     ss_rec* rec;
@@ -273,6 +277,26 @@ inline void ss_smem_optin(K k, int bytes, std::atomic<unsigned long long>& done)
     if (bit && (done.load(std::memory_order_relaxed) & bit)) return;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (bit) done.fetch_or(bit, std::memory_order_relaxed);
+}
+
+// CTAs of kernel `k` (block threads, dynamic shared memory bytes) that are
+// resident at once on the current device: the grid of a persistent kernel.
+// Cached per device in `cache` (device d at bits 16 d .. 16 d + 15; devices
+// past 3 query every time).
+template <typename K>
+inline int ss_resident_ctas(K k, int threads, int smem, std::atomic<unsigned long long>& cache) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (dev < 4) {
+        const unsigned c = (unsigned)(cache.load(std::memory_order_relaxed) >> (16 * dev)) & 0xffffu;
+        if (c) return (int)c;
+    }
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    const int n = per_sm * sms;
+    if (dev < 4 && n > 0 && n < 65536) cache.fetch_or((unsigned long long)n << (16 * dev), std::memory_order_relaxed);
+    return n;
 }
 
 void ss_launch_brdf_lut(float* lut, int n, cudaStream_t st);
