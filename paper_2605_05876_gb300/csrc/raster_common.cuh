@@ -142,6 +142,37 @@ __device__ __forceinline__ void stage_finish(ss_wstage& W, int n, int lane, floa
     __syncwarp();
 }
 
+// Can a staged surfel cover a pixel whose centre offset d from the surfel
+// centre lies in the box [dx0, dx1] x [dy0, dy1]?  Coverage (ss_pixel_test)
+// needs f(d) = |P d|^2 - r^2 s2(d)^2 < 0 with s2 = 1 + A2 dx + B2 dy; f is the
+// quadratic d^T Q2 d - 2 r^2 g.d - r^2 with Q2 = P^T P - r^2 g g^T, g = (A2, B2).
+// When Q2 is positive definite the minimum of f over the box is at the free
+// minimiser (if inside; f < 0 there) or on an edge (a clamped 1-D minimum per
+// edge).  Returns false only when that minimum exceeds a margin far above the
+// rounding of the per-pixel test (f is checked in FP32 against r^2 s2^2,
+// whose size over the box is at most r^2 (1 + |A2| max|dx| + |B2| max|dy|)^2),
+// so a surfel it rejects covers no pixel of the box.
+__device__ __forceinline__ bool ss_box_may_cover(float4 P, float A2, float B2, float rc2, float dx0, float dx1,
+                                                 float dy0, float dy1) {
+    const float a = P.x * P.x + P.z * P.z - rc2 * A2 * A2;
+    const float b = P.x * P.y + P.z * P.w - rc2 * A2 * B2;
+    const float c = P.y * P.y + P.w * P.w - rc2 * B2 * B2;
+    const float det = a * c - b * b;
+    if (!(a > 0.f) || !(c > 0.f) || !(det > 0.f)) return true;
+    const float ga = rc2 * A2, gb = rc2 * B2;
+    const float idet = 1.f / det;
+    const float xs = (c * ga - b * gb) * idet, ys = (a * gb - b * ga) * idet;
+    if (xs >= dx0 && xs <= dx1 && ys >= dy0 && ys <= dy1) return true;
+    auto f = [&](float x, float y) { return x * (a * x + 2.f * b * y - 2.f * ga) + y * (c * y - 2.f * gb) - rc2; };
+    const float ia = 1.f / a, ic = 1.f / c;
+    float m = f(dx0, fminf(fmaxf((gb - b * dx0) * ic, dy0), dy1));
+    m = fminf(m, f(dx1, fminf(fmaxf((gb - b * dx1) * ic, dy0), dy1)));
+    m = fminf(m, f(fminf(fmaxf((ga - b * dy0) * ia, dx0), dx1), dy0));
+    m = fminf(m, f(fminf(fmaxf((ga - b * dy1) * ia, dx0), dx1), dy1));
+    const float sc = 1.f + fabsf(A2) * fmaxf(fabsf(dx0), fabsf(dx1)) + fabsf(B2) * fmaxf(fabsf(dy0), fabsf(dy1));
+    return !(m > 1e-5f * rc2 * sc * sc);   // NaN keeps the surfel
+}
+
 __device__ __forceinline__ bool in_rect(uint32_t rx, uint32_t ry, int px, int py) {
     int i0 = rx & 0xffff, i1 = rx >> 16, j0 = ry & 0xffff, j1 = ry >> 16;
     return px >= i0 && px <= i1 && py >= j0 && py <= j1;

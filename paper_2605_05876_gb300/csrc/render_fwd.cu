@@ -614,7 +614,15 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
         n_next = stage_issue<true>(Wb[buf ^ 1], Rb + (buf ^ 1) * WSLOTS, nxt, recs, lane, gx0, gx1, gy0, gy1);
         nxt = fetch_chunk(ws.keys, ws.rects, base + 64 + lane, end);
         uint32_t my_mask = 0;
-        for (int s = 0; s < n; ++s) {
+        // staged surfels whose exact support can reach a pixel centre of the block
+        bool may = false;
+        if (lane < n) {
+            const float4 g1 = W.h1[lane];
+            const float bx = (float)wx0 - g1.z, by = (float)wy0 - g1.w;
+            may = ss_box_may_cover(W.h0[lane], g1.x, g1.y, rc2, bx + 0.5f, bx + 7.5f, by + 0.5f, by + 3.5f);
+        }
+        for (uint32_t live = __ballot_sync(0xffffffffu, may); live; live &= live - 1) {
+            const int s = __ffs(live) - 1;
             const float4 h0 = W.h0[s], h1 = W.h1[s], h2 = W.h2[s];
             const ss_hit h = ss_pixel_test(h0, h1, xl - h1.z, yl - h1.w, rc2);
             bool cg = h.cover && inside;   // geometric coverage (support and cutoff)
