@@ -205,13 +205,15 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
                 const float ch[SS_NCH] = {c0v.x, c0v.y, c0v.z, c1v.x, c1v.y, c1v.z,
                                           c1v.w, c2v.x, c2v.y, c2v.z, c2v.w, 0.5f * (h2.x + h2.y)};
                 float gr[G_N];
-                float dLdw = -gt[12];
+                // dL/dw = sum_c G_c ch_c - S_k, in three interleaved chains
+                float dl[3] = {-gt[12], 0.f, 0.f};
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
                     const float G = gt[c];
-                    dLdw = fmaf(G, ch[c], dLdw);
+                    dl[c % 3] = fmaf(G, ch[c], dl[c % 3]);
                     gr[G_CH + c] = G * w;
                 }
+                const float dLdw = dl[0] + (dl[1] + dl[2]);
                 // w = n_f exp(-rho2 / 2), rho2 = q / s2^2 (Eq. mip_weight)
                 gr[G_NF] = dLdw * ex;
                 const float grho = -0.5f * w * dLdw;
@@ -239,14 +241,22 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
                     v[4 * m] = x.x; v[4 * m + 1] = x.y; v[4 * m + 2] = x.z; v[4 * m + 3] = x.w;
                 }
             }
+            // run sums, four columns at a time where no run ends inside them
             float tot = 0.f;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                tot += v[j];
-                if ((ends >> j) & 1u) {   // warp-uniform
-                    const int sl = __shfl_sync(0xffffffffu, s, j);
-                    if (lane < NV && tot != 0.f) atomicAdd(grad + (int64_t)Wc->id[sl] * SS_NGRAD + lane, tot);
-                    tot = 0.f;
+            for (int m = 0; m < 8; ++m) {
+                if (((ends >> (4 * m)) & 15u) == 0u) {   // warp-uniform
+                    tot += (v[4 * m] + v[4 * m + 1]) + (v[4 * m + 2] + v[4 * m + 3]);
+                    continue;
+                }
+#pragma unroll
+                for (int j = 4 * m; j < 4 * m + 4; ++j) {
+                    tot += v[j];
+                    if ((ends >> j) & 1u) {   // warp-uniform
+                        const int sl = __shfl_sync(0xffffffffu, s, j);
+                        if (lane < NV && tot != 0.f) atomicAdd(grad + (int64_t)Wc->id[sl] * SS_NGRAD + lane, tot);
+                        tot = 0.f;
+                    }
                 }
             }
             __syncwarp();
