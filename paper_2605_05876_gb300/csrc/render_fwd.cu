@@ -431,6 +431,37 @@ __device__ void merge_runs(const unsigned long long* A, int na, const unsigned l
     }
 }
 
+// Sort one chunk of m keys (N = the power of two >= m, N <= SORT_THREADS * KPL)
+// in registers, KPL per thread, and store it; with `gather`, also write the
+// rectangles of the sorted keys.
+template <int KPL>
+__device__ __noinline__ void sort_chunk(const ss_ws_view& ws, unsigned long long* K, uint2* RC, int m, int N,
+                                           bool gather, unsigned long long* xs) {
+    const int base = threadIdx.x * KPL;
+    unsigned long long x[KPL];
+#pragma unroll
+    for (int k = 0; k < KPL; ++k) x[k] = base + k < m ? K[base + k] : ~0ull;
+    bitonic_regs<KPL>(x, N, xs);
+    __syncthreads();   // every thread's reads of this chunk are done before the stores
+#pragma unroll
+    for (int k = 0; k < KPL; ++k)
+        if (base + k < m) K[base + k] = x[k];
+    if (gather) {
+        constexpr int G = KPL < 8 ? KPL : 8;   // gathers in flight
+#pragma unroll
+        for (int k0 = 0; k0 < KPL; k0 += G) {
+            uint2 rr[G];
+#pragma unroll
+            for (int k = 0; k < G; ++k)
+                if (base + k0 + k < m) rr[k] = rect_of(ws, x[k0 + k]);
+#pragma unroll
+            for (int k = 0; k < G; ++k)
+                if (base + k0 + k < m) RC[base + k0 + k] = rr[k];
+        }
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view ws, int total_tiles) {
     extern __shared__ unsigned long long xs[];
     const int t = blockIdx.x;
@@ -446,34 +477,17 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view w
         return;
     }
     unsigned long long* Alt = ws.keys_alt + b;
-    const int base = threadIdx.x * SORT_KPL;
-    // chunks of SORT_CAP sorted in registers
+    // chunks of SORT_CAP sorted in registers, with as many keys per thread as
+    // spread the chunk over all threads (fewer sequential steps per thread)
     for (int c0 = 0; c0 < n; c0 += SORT_CAP) {
         const int m = min(SORT_CAP, n - c0);
         int N = 2;
         while (N < m) N <<= 1;
-        unsigned long long x[SORT_KPL];
-#pragma unroll
-        for (int k = 0; k < SORT_KPL; ++k) x[k] = base + k < m ? K[c0 + base + k] : ~0ull;
-        bitonic_regs<SORT_KPL>(x, N, xs);
-        __syncthreads();   // every thread's reads of this chunk are done before the stores
-#pragma unroll
-        for (int k = 0; k < SORT_KPL; ++k)
-            if (base + k < m) K[c0 + base + k] = x[k];
-        if (n <= SORT_CAP) {
-            // rectangles of the sorted keys, 8 gathers in flight
-#pragma unroll
-            for (int k0 = 0; k0 < SORT_KPL; k0 += 8) {
-                uint2 rr[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    if (base + k0 + k < m) rr[k] = rect_of(ws, x[k0 + k]);
-#pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    if (base + k0 + k < m) RC[base + k0 + k] = rr[k];
-            }
-        }
-        __syncthreads();
+        const bool gather = n <= SORT_CAP;
+        if (N <= SORT_THREADS * 4) sort_chunk<4>(ws, K + c0, RC + c0, m, N, gather, xs);
+        else if (N <= SORT_THREADS * 8) sort_chunk<8>(ws, K + c0, RC + c0, m, N, gather, xs);
+        else if (N <= SORT_THREADS * 16) sort_chunk<16>(ws, K + c0, RC + c0, m, N, gather, xs);
+        else sort_chunk<SORT_KPL>(ws, K + c0, RC + c0, m, N, gather, xs);
     }
     if (n <= SORT_CAP) return;
     // pairwise merges in global memory, ping-pong between K and Alt
