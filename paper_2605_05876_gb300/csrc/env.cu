@@ -13,6 +13,8 @@
 #include <cooperative_groups.h>
 #include <vector>
 
+#include <mutex>
+
 #include "ss3d_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -681,6 +683,34 @@ static void launch_conv_bwd(const float* d_out, int64_t dout_stride, int Wo, int
                        norm_stride, Ws, Hs, d_base, base_stride, Wb, bw, bh, ggx, alpha, TJ, P, TAC, WWP);
 }
 
+// Side streams of one device on which the prefilter's convolutions run side
+// by side (each is too small to fill the GPU alone), forked from and joined
+// back to the caller's stream with events, so stream capture records them as
+// parallel branches.  Created on first use; fork and join are serialised by a
+// mutex so that concurrent callers never mix their events.
+#define SS_SIDE_STREAMS 8
+struct ss_side {
+    cudaStream_t s[SS_SIDE_STREAMS];
+    cudaEvent_t fork, join[SS_SIDE_STREAMS];
+    bool ok;
+};
+static std::mutex g_side_mutex;
+static ss_side g_side[64];
+static bool g_side_init[64];
+
+static ss_side* side_streams_locked(int dev) {
+    if (dev < 0 || dev >= 64) return nullptr;
+    if (!g_side_init[dev]) {
+        g_side_init[dev] = true;
+        ss_side& x = g_side[dev];
+        x.ok = cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming) == cudaSuccess;
+        for (int i = 0; i < SS_SIDE_STREAMS && x.ok; ++i)
+            x.ok = cudaStreamCreateWithFlags(&x.s[i], cudaStreamNonBlocking) == cudaSuccess &&
+                   cudaEventCreateWithFlags(&x.join[i], cudaEventDisableTiming) == cudaSuccess;
+    }
+    return g_side[dev].ok ? &g_side[dev] : nullptr;
+}
+
 void ss_launch_env_prefilter(const ss_env_desc* d, int n_envs, const float* env, float* irr, float* spec,
                              float* aux, cudaStream_t st) {
     const int We = d->width, He = d->height;
@@ -688,31 +718,56 @@ void ss_launch_env_prefilter(const ss_env_desc* d, int n_envs, const float* env,
     const int64_t irr_stride = ss_env_irr_floats(d), spec_stride = ss_env_spec_floats(d),
                   aux_stride = ss_env_aux_floats(d);
     const int Wi = d->irr_width, Hi = d->irr_height;
-    launch_conv_fwd(env, env_stride, We, He, irr, irr_stride, Wi, Hi, aux, aux_stride, 0, 0.f, n_envs, st);
     ss_note_launch();
     copy_level0_kernel<<<dim3(256, n_envs), 256, 0, st>>>(env, env_stride, spec, spec_stride, env_stride);
+    // sources of the specular levels: the cascade of box filters
+    {
+        int64_t aux_off = (int64_t)Wi * Hi;
+        const float* prev = env;
+        int64_t prev_stride = env_stride;
+        int Wp = We, Hp = He;
+        for (int i = 1; i < d->n_levels; ++i) {
+            int W, H;
+            ss_env_level_size(d, i, &W, &H);
+            float* src = aux + aux_off + (int64_t)W * H;
+            ss_note_launch();
+            box_down_kernel<<<dim3((W * H + 255) / 256, n_envs), 256, 0, st>>>(prev, prev_stride, Wp, Hp, src,
+                                                                               aux_stride, W, H);
+            prev = src;
+            prev_stride = aux_stride;
+            Wp = W;
+            Hp = H;
+            aux_off += (int64_t)W * H * 4;
+        }
+    }
+    // the convolutions (irradiance, specular levels 1 .. L-1) write disjoint
+    // outputs: level i on side stream i - 1, the irradiance map on `st`
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(g_side_mutex);
+    ss_side* sd = side_streams_locked(dev);
+    const bool fork = sd && d->n_levels - 1 <= SS_SIDE_STREAMS && cudaEventRecord(sd->fork, st) == cudaSuccess;
     int64_t spec_off = env_stride, aux_off = (int64_t)Wi * Hi;
-    const float* prev = env;
-    int64_t prev_stride = env_stride;
-    int Wp = We, Hp = He;
     for (int i = 1; i < d->n_levels; ++i) {
         int W, H;
         ss_env_level_size(d, i, &W, &H);
         float* norm = aux + aux_off;
         float* src = aux + aux_off + (int64_t)W * H;
-        ss_note_launch();
-        box_down_kernel<<<dim3((W * H + 255) / 256, n_envs), 256, 0, st>>>(prev, prev_stride, Wp, Hp, src, aux_stride,
-                                                                           W, H);
-        prev = src;
-        prev_stride = aux_stride;
-        Wp = W;
-        Hp = H;
         float r = (float)i / (float)(d->n_levels - 1);
+        cudaStream_t si = st;
+        if (fork) {
+            si = sd->s[i - 1];
+            cudaStreamWaitEvent(si, sd->fork, 0);
+        }
         launch_conv_fwd(src, aux_stride, W, H, spec + spec_off, spec_stride, W, H, norm, aux_stride, 1, r * r, n_envs,
-                        st);
+                        si);
+        if (fork) cudaEventRecord(sd->join[i - 1], si);
         spec_off += (int64_t)W * H * 3;
         aux_off += (int64_t)W * H * 4;
     }
+    launch_conv_fwd(env, env_stride, We, He, irr, irr_stride, Wi, Hi, aux, aux_stride, 0, 0.f, n_envs, st);
+    if (fork)
+        for (int i = 1; i < d->n_levels; ++i) cudaStreamWaitEvent(st, sd->join[i - 1], 0);
 }
 
 void ss_launch_env_prefilter_bwd(const ss_env_desc* d, int n_envs, const float* d_irr, const float* d_spec,
@@ -751,7 +806,6 @@ void ss_launch_env_prefilter_bwd(const ss_env_desc* d, int n_envs, const float* 
 // They cannot provide the `aux` scratch of ss_env_prefilter, so this entry
 // keeps that scratch in a fixed array in device memory that every GPU which
 // loads the library holds until the process exits.
-#include <mutex>
 
 static __device__ __align__(256) float g_noalloc_aux[SS_NOALLOC_AUX_FLOATS];
 
