@@ -583,9 +583,10 @@ __global__ void __launch_bounds__(256) envconv_bwd_kernel(const float* __restric
         for (int idx = threadIdx.x; idx < JT * per; idx += nt) {
             const int o = idx / per, y = (idx % per) / bw, x = idx % bw;
             float* po = D + ((int64_t)(bs * bh + y) * Wb + ((j0 + o) * bw + x)) * 3;
-            po[0] += (float)cpart[o * 3];
-            po[1] += (float)cpart[o * 3 + 1];
-            po[2] += (float)cpart[o * 3 + 2];
+            // atomic: the level convolutions run side by side into one map
+            atomicAdd(po, (float)cpart[o * 3]);
+            atomicAdd(po + 1, (float)cpart[o * 3 + 1]);
+            atomicAdd(po + 2, (float)cpart[o * 3 + 2]);
         }
     }
     cluster.sync();
@@ -777,23 +778,41 @@ void ss_launch_env_prefilter_bwd(const ss_env_desc* d, int n_envs, const float* 
     const int64_t irr_stride = ss_env_irr_floats(d), spec_stride = ss_env_spec_floats(d),
                   aux_stride = ss_env_aux_floats(d);
     const int Wi = d->irr_width, Hi = d->irr_height;
+    if (d_spec) {
+        ss_note_launch();
+        add_level0_kernel<<<dim3(256, n_envs), 256, 0, st>>>(d_spec, spec_stride, d_env, env_stride, env_stride);
+    }
+    // the transposed convolutions add into d_env with atomics: specular levels
+    // on the side streams, the irradiance map on `st`
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(g_side_mutex);
+    ss_side* sd = d_spec ? side_streams_locked(dev) : nullptr;
+    const bool fork = sd && d->n_levels - 1 <= SS_SIDE_STREAMS && cudaEventRecord(sd->fork, st) == cudaSuccess;
+    if (d_spec) {
+        int64_t spec_off = env_stride, aux_off = (int64_t)Wi * Hi;
+        for (int i = 1; i < d->n_levels; ++i) {
+            int W, H;
+            ss_env_level_size(d, i, &W, &H);
+            const float* norm = aux + aux_off;
+            float r = (float)i / (float)(d->n_levels - 1);
+            cudaStream_t si = st;
+            if (fork) {
+                si = sd->s[i - 1];
+                cudaStreamWaitEvent(si, sd->fork, 0);
+            }
+            launch_conv_bwd(d_spec + spec_off, spec_stride, W, H, norm, aux_stride, W, H, d_env, env_stride, We,
+                            We / W, He / H, 1, r * r, n_envs, si);
+            if (fork) cudaEventRecord(sd->join[i - 1], si);
+            spec_off += (int64_t)W * H * 3;
+            aux_off += (int64_t)W * H * 4;
+        }
+    }
     if (d_irr)
         launch_conv_bwd(d_irr, irr_stride, Wi, Hi, aux, aux_stride, We, He, d_env, env_stride, We, 1, 1, 0, 0.f, n_envs,
                         st);
-    if (!d_spec) return;
-    ss_note_launch();
-    add_level0_kernel<<<dim3(256, n_envs), 256, 0, st>>>(d_spec, spec_stride, d_env, env_stride, env_stride);
-    int64_t spec_off = env_stride, aux_off = (int64_t)Wi * Hi;
-    for (int i = 1; i < d->n_levels; ++i) {
-        int W, H;
-        ss_env_level_size(d, i, &W, &H);
-        const float* norm = aux + aux_off;
-        float r = (float)i / (float)(d->n_levels - 1);
-        launch_conv_bwd(d_spec + spec_off, spec_stride, W, H, norm, aux_stride, W, H, d_env, env_stride, We, We / W,
-                        He / H, 1, r * r, n_envs, st);
-        spec_off += (int64_t)W * H * 3;
-        aux_off += (int64_t)W * H * 4;
-    }
+    if (fork)
+        for (int i = 1; i < d->n_levels; ++i) cudaStreamWaitEvent(st, sd->join[i - 1], 0);
 }
 
 // ------------------------------------------------------------------------
