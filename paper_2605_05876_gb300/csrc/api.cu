@@ -202,7 +202,7 @@ static ws_plan plan_ws(const ss_layout& L, const ss_render_params& p, int with_b
         w.grad = take(sizeof(float) * SS_NGRAD * (size_t)L.total_records);
         w.masks = take(sizeof(uint2) * 8 * (size_t)p.max_instances);
         w.mcount = take(sizeof(uint32_t) * 8 * (size_t)L.total_tiles);
-        w.env_acc = take(sizeof(float4) * (size_t)w.env_texels * (size_t)L.n_scenes);
+        w.env_acc = take(sizeof(float4) * SS_ACC_STRIDE * (size_t)w.env_texels * (size_t)L.n_scenes);
     } else {
         w.layer = w.pix = w.grad = w.masks = w.mcount = w.env_acc = 0;
     }
@@ -468,7 +468,8 @@ extern "C" ss_status ss_render_backward(const ss_batch_desc* b, const ss_surfels
     a.genv = genv ? *genv : ge;
     CK(cudaMemsetAsync(W.grad_rec, 0, sizeof(float) * SS_NGRAD * (size_t)L.total_records, st));
     if (a.genv.irr || a.genv.spec)
-        CK(cudaMemsetAsync(W.env_acc, 0, sizeof(float4) * (size_t)W.env_texels * (size_t)L.n_scenes, st));
+        CK(cudaMemsetAsync(W.env_acc, 0, sizeof(float4) * SS_ACC_STRIDE * (size_t)W.env_texels * (size_t)L.n_scenes,
+                           st));
     CK(cudaMemsetAsync(W.work + 1, 0, sizeof(unsigned int), st));   // backward work-queue head
     {
         stage_scope sc(3, st);

@@ -405,27 +405,16 @@ __device__ __forceinline__ lk3 lookup3(const float* T, const ss_taps& t, int W, 
     }
     return r;
 }
-// bilinear adjoint: g * scale * tap weights added to a 3-channel map in shared memory
-__device__ __forceinline__ void scatter3(float* D, const ss_taps& t, const float g[3], float scale) {
-    const float w00 = (1.f - t.fx) * (1.f - t.fy) * scale, w01 = t.fx * (1.f - t.fy) * scale,
-                w10 = (1.f - t.fx) * t.fy * scale, w11 = t.fx * t.fy * scale;
-    for (int c = 0; c < 3; ++c) {
-        if (g[c] == 0.f) continue;
-        atomicAdd(D + t.i00 * 3 + c, w00 * g[c]);
-        atomicAdd(D + t.i01 * 3 + c, w01 * g[c]);
-        atomicAdd(D + t.i10 * 3 + c, w10 * g[c]);
-        atomicAdd(D + t.i11 * 3 + c, w11 * g[c]);
-    }
-}
-// the same bilinear adjoint into RGBA accumulators (one 16-byte atomic per tap)
+// bilinear adjoint: g * scale * tap weights added to RGBA accumulators (one
+// 16-byte atomic per tap; accumulators SS_ACC_STRIDE float4 apart)
 __device__ __forceinline__ void scatter4(float4* D, const ss_taps& t, const float g[3], float scale) {
     if (scale == 0.f || (g[0] == 0.f && g[1] == 0.f && g[2] == 0.f)) return;
     const float w00 = (1.f - t.fx) * (1.f - t.fy) * scale, w01 = t.fx * (1.f - t.fy) * scale,
                 w10 = (1.f - t.fx) * t.fy * scale, w11 = t.fx * t.fy * scale;
-    atomicAdd(D + t.i00, make_float4(w00 * g[0], w00 * g[1], w00 * g[2], 0.f));
-    atomicAdd(D + t.i01, make_float4(w01 * g[0], w01 * g[1], w01 * g[2], 0.f));
-    atomicAdd(D + t.i10, make_float4(w10 * g[0], w10 * g[1], w10 * g[2], 0.f));
-    atomicAdd(D + t.i11, make_float4(w11 * g[0], w11 * g[1], w11 * g[2], 0.f));
+    atomicAdd(D + (int64_t)t.i00 * SS_ACC_STRIDE, make_float4(w00 * g[0], w00 * g[1], w00 * g[2], 0.f));
+    atomicAdd(D + (int64_t)t.i01 * SS_ACC_STRIDE, make_float4(w01 * g[0], w01 * g[1], w01 * g[2], 0.f));
+    atomicAdd(D + (int64_t)t.i10 * SS_ACC_STRIDE, make_float4(w10 * g[0], w10 * g[1], w10 * g[2], 0.f));
+    atomicAdd(D + (int64_t)t.i11 * SS_ACC_STRIDE, make_float4(w11 * g[0], w11 * g[1], w11 * g[2], 0.f));
 }
 // d(u, v)/d(direction) for the equirect map of a unit direction d
 __device__ __forceinline__ void uv_grad(const float d[3], float gu, float gv, float out[3]) {
@@ -450,15 +439,6 @@ __device__ __forceinline__ void uv_grad(const float d[3], float gu, float gv, fl
 // so its adjoint is taken once per side, from the sum over the views that
 // see that side.
 
-// Shared-memory copies of the specular gradient levels from `level` on (the
-// small, most contended ones) of one scene.  Records of other scenes, the
-// larger levels and the irradiance map add to the RGBA accumulators.
-struct env_priv {
-    float* spec;       // levels level .. L-1, back to back, or nullptr
-    int scene;
-    int level;
-    int64_t spec_off;  // offset of level `level` inside one scene's spec stack
-};
 
 // Irradiance adjoint of one side of a surfel (fs = +1 front, -1 back) given
 // g = sum over that side's views of dL/dLd: the texel gradients (bilinear
@@ -483,7 +463,7 @@ __device__ __forceinline__ void irr_side_adjoint(const float* irr, int W, int H,
 }
 
 __device__ __forceinline__ void pbwd_surfel(const ss_ws_view& ws, const ss_bwd_args& A, const int64_t i,
-                                            const int scene, const env_priv& pv) {
+                                            const int scene) {
     const ss_layout* L = ws.layout;
     const ss_fwd_args& a = A.f;
     const float c[3] = {a.s.pos[i * 3], a.s.pos[i * 3 + 1], a.s.pos[i * 3 + 2]};
@@ -711,20 +691,12 @@ __device__ __forceinline__ void pbwd_surfel(const ss_ws_view& ws, const ss_bwd_a
             if (rough > 0.f && rough < 1.f) grough += dbe1 * dbe_r[0] + dbe2 * dbe_r[1] + dlf * (float)(nL - 1);
             float dmu = dbe1 * dbe_mu[0] + dbe2 * dbe_mu[1];
             float dmup = (mup > 0.f && mup < 1.f) ? dmu : 0.f;
-            // specular texels: the block's own scene's small levels into shared
-            // memory, the rest into the workspace's RGBA accumulators
-            // (irradiance texels first, then the specular stack)
+            // specular texels into the workspace's RGBA accumulators (irradiance
+            // texels first, then the specular stack)
             if (d_spec) {
-                const bool mine = scene == pv.scene;
-                float4* acc = ws.env_acc + scene * ws.env_texels + (int64_t)IW * IH;
-                if (pv.spec && mine && l0 >= pv.level)
-                    scatter3(pv.spec + (o0 - pv.spec_off), t0, dLs, 1.f - lf);
-                else
-                    scatter4(acc + o0 / 3, t0, dLs, 1.f - lf);
-                if (pv.spec && mine && l1 >= pv.level)
-                    scatter3(pv.spec + (o1 - pv.spec_off), t1, dLs, lf);
-                else
-                    scatter4(acc + o1 / 3, t1, dLs, lf);
+                float4* acc = ws.env_acc + (scene * ws.env_texels + (int64_t)IW * IH) * SS_ACC_STRIDE;
+                scatter4(acc + o0 / 3 * SS_ACC_STRIDE, t0, dLs, 1.f - lf);
+                scatter4(acc + o1 / 3 * SS_ACC_STRIDE, t1, dLs, lf);
             }
             // reflected direction: Ls(uv(refl))
             float gur = 0.f, gvr = 0.f;
@@ -762,7 +734,7 @@ __device__ __forceinline__ void pbwd_surfel(const ss_ws_view& ws, const ss_bwd_a
     // ---- irradiance: once per side, from the view sums
     {
         float gRn[3] = {0.f, 0.f, 0.f};
-        float4* acc = d_irr ? ws.env_acc + scene * ws.env_texels : nullptr;
+        float4* acc = d_irr ? ws.env_acc + scene * ws.env_texels * SS_ACC_STRIDE : nullptr;
         irr_side_adjoint(irr, IW, IH, nrm, 1.f, gLdF, acc, gRn);
         irr_side_adjoint(irr, IW, IH, nrm, -1.f, gLdB, acc, gRn);
         for (int k = 0; k < 3; ++k) gRq[k * 3 + 2] += gRn[k];
@@ -795,12 +767,9 @@ __device__ __forceinline__ void pbwd_surfel(const ss_ws_view& ws, const ss_bwd_a
     if (g.metallic) g.metallic[i] += gmetal;
 }
 
-// One CTA per contiguous block of surfels; env gradients of the block's
-// first scene are accumulated in shared memory and flushed once.
+// One CTA per contiguous block of surfels (each thread one surfel at a time).
 __global__ void __launch_bounds__(128, 4) project_bwd_kernel(ss_ws_view ws, ss_bwd_args A, int64_t n_surfels,
-                                                            int64_t per_block, int priv_level, int64_t priv_spec_off,
-                                                            int priv_spec_floats) {
-    extern __shared__ float priv[];
+                                                            int64_t per_block) {
     const ss_layout* L = ws.layout;
     const int64_t i0 = blockIdx.x * per_block;
     if (i0 >= n_surfels) return;
@@ -815,27 +784,8 @@ __global__ void __launch_bounds__(128, 4) project_bwd_kernel(ss_ws_view ws, ss_b
         return lo;
     };
     const int scene = scene_of(i0);
-    const bool use = A.genv.spec != nullptr && priv_spec_floats > 0;
-    env_priv pv;
-    pv.spec = use ? priv : nullptr;
-    pv.scene = scene;
-    pv.level = priv_level;
-    pv.spec_off = priv_spec_off;
-    const int n_priv = priv_spec_floats;
-    if (use)
-        for (int k = threadIdx.x; k < n_priv; k += blockDim.x) priv[k] = 0.f;
-    __syncthreads();
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x)
-        pbwd_surfel(ws, A, i, i < L->scene_begin[scene + 1] ? scene : scene_of(i), pv);
-    __syncthreads();
-    if (use) {   // texel by texel into the RGBA accumulators
-        float4* acc = ws.env_acc + scene * ws.env_texels + (int64_t)A.f.ed.irr_width * A.f.ed.irr_height +
-                      priv_spec_off / 3;
-        for (int k = threadIdx.x; k < n_priv / 3; k += blockDim.x) {
-            const float4 v = make_float4(priv[3 * k], priv[3 * k + 1], priv[3 * k + 2], 0.f);
-            if (v.x != 0.f || v.y != 0.f || v.z != 0.f) atomicAdd(acc + k, v);
-        }
-    }
+        pbwd_surfel(ws, A, i, i < L->scene_begin[scene + 1] ? scene : scene_of(i));
 }
 
 // Add the RGBA accumulators into the caller's env-map gradients (RGB).
@@ -844,7 +794,7 @@ __global__ void env_acc_flush_kernel(const float4* acc, int64_t texels, int64_t 
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= total) return;
     const int64_t sc = i / texels, k = i % texels;
-    const float4 v = acc[i];
+    const float4 v = acc[i * SS_ACC_STRIDE];
     if (v.x == 0.f && v.y == 0.f && v.z == 0.f) return;
     float* d = k < irr_tex ? (d_irr ? d_irr + (sc * irr_tex + k) * 3 : nullptr)
                            : (d_spec ? d_spec + (sc * (texels - irr_tex) + (k - irr_tex)) * 3 : nullptr);
@@ -857,29 +807,10 @@ __global__ void env_acc_flush_kernel(const float4* acc, int64_t texels, int64_t 
 void ss_launch_project_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st) {
     int64_t n = L.scene_begin[L.n_scenes];
     if (n <= 0 || L.total_records <= 0) return;
-    // privatise the smallest specular levels whose total fits 48 KB
-    int level = a.f.ed.n_levels;
-    int64_t priv_spec = 0;
-    while (level > 1) {
-        int W, H;
-        ss_env_level_size(&a.f.ed, level - 1, &W, &H);
-        if (priv_spec + (int64_t)W * H * 3 > 12288) break;
-        priv_spec += (int64_t)W * H * 3;
-        --level;
-    }
-    int64_t spec_off = 0;
-    for (int i = 0; i < level; ++i) {
-        int W, H;
-        ss_env_level_size(&a.f.ed, i, &W, &H);
-        spec_off += (int64_t)W * H * 3;
-    }
     const int64_t per_block = a.f.p.pbwd_block ? a.f.p.pbwd_block : 128;   // surfels per CTA (all their views)
     const unsigned blocks = (unsigned)((n + per_block - 1) / per_block);
-    const size_t smem = sizeof(float) * (size_t)priv_spec;
-    static std::atomic<unsigned long long> optin{0};
-    ss_smem_optin(project_bwd_kernel, 64 * 1024, optin);
     ss_note_launch();
-    project_bwd_kernel<<<blocks, 128, smem, st>>>(ws, a, n, per_block, level, spec_off, (int)priv_spec);
+    project_bwd_kernel<<<blocks, 128, 0, st>>>(ws, a, n, per_block);
     if ((a.genv.irr || a.genv.spec) && ws.env_acc) {
         const int64_t total = ws.env_texels * L.n_scenes;
         ss_note_launch();

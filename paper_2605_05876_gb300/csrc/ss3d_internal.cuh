@@ -14,6 +14,8 @@
 // Tile counters and cursors take the atomics of every tile instance; one per
 // SS_CNT_STRIDE words spreads them over the L2 slices instead of a few.
 #define SS_CNT_STRIDE 32
+// Likewise the env-map gradient accumulators: one float4 per texel, 128 bytes apart.
+#define SS_ACC_STRIDE 8
 #define SS_NGRAD 24                // floats per (view, surfel) gradient record (22 used)
 #define SS_PI_F 3.14159265358979323846f
 
@@ -99,7 +101,7 @@ struct ss_ws_view {
     uint2* cover_list;      // [8 * max_instances]: per warp, (record, 32-pixel coverage word) of every staged
                             // surfel that covers a pixel of the warp's block, in list order (forward -> backward)
     uint32_t* cover_count;  // [8 * tiles]: entries of each warp's list
-    float4* env_acc;        // [scenes][env_texels] RGBA accumulators of the env-map gradients (backward)
+    float4* env_acc;        // [scenes][env_texels][SS_ACC_STRIDE] RGBA accumulators of the env-map gradients (backward)
     int64_t env_texels;     // irradiance + specular texels per scene
     int64_t max_instances;
 };
