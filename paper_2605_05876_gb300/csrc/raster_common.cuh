@@ -1,14 +1,15 @@
 // Per-warp streaming of a tile's sorted instance list, shared by the forward
 // and backward rasterisers.
 //
-// Each warp owns an 8 x 4 pixel block of a 16 x 16 tile and walks the tile's
-// list on its own (no block-wide barrier), 32 keys at a time: it reads the
-// support rectangles, keeps the instances whose rectangle meets its block
-// (ballot + prefix count, so the order by z_start is kept) and copies those
-// records into one of its two shared-memory staging buffers with cp.async.
-// The pipeline is two chunks deep: while the warp works on chunk c, the
-// records of chunk c+1 are in flight into the other buffer and the keys and
-// rectangles of chunk c+2 are being loaded.
+// Each warp owns an 8 x 4 pixel block of a 16 x 16 tile and works on its own
+// (no block-wide barrier).  The forward first walks the tile's list 32 keys at
+// a time, reading the support rectangles, and keeps the instances whose
+// rectangle meets its block (ballot + prefix count, so the order by z_start is
+// kept) in a candidate list; the backward reads the forward's list of
+// covering instances.  Either list is then consumed 32 records at a time:
+// the records are copied into shared-memory staging slots with cp.async, two
+// chunks deep in the forward (while the warp works on chunk c, the records of
+// chunk c+1 are in flight into the other buffer).
 #pragma once
 
 #include "ss3d_internal.cuh"
@@ -29,7 +30,7 @@ struct ss_wstage {
     float4 c0[WSLOTS];  // rgb, flags                                         -- covering fragments
     float4 c1[WSLOTS];  // albedo, roughness
     float4 c2[WSLOTS];  // metallic, normal
-    float4 zr[WSLOTS];  // record row 3 (z_start, z_end, rectangle) until the fix-up
+    float4 zr[WSLOTS];  // record row 3 (z_start, z_end, rectangle); the rectangle is read by the forward
     uint32_t id[WSLOTS];
 };
 
@@ -62,37 +63,6 @@ __device__ __forceinline__ ss_chunk fetch_chunk(const unsigned long long* keys, 
     return c;
 }
 
-// Issue the copies of the instances of chunk c whose rectangle meets the
-// warp's pixel block [gx0, gx1] x [gy0, gy1] into slots 0 .. n-1 of W (list
-// order kept); returns n.  With RECT the support rectangles are staged too
-// (rect[], for the surfels whose n_f carries the rectangle flag).
-template <bool RECT>
-__device__ __forceinline__ int stage_issue(ss_wstage& W, uint2* rect, const ss_chunk& c, const ss_rec* recs,
-                                           int lane, int gx0, int gx1, int gy0, int gy1) {
-    bool ov = false;
-    if (c.live) {
-        const uint32_t rx = c.rect.x, ry = c.rect.y;
-        int i0 = rx & 0xffff, i1 = rx >> 16, j0 = ry & 0xffff, j1 = ry >> 16;
-        ov = i0 <= gx1 && i1 >= gx0 && j0 <= gy1 && j1 >= gy0;
-    }
-    const uint32_t mask = __ballot_sync(0xffffffffu, ov);
-    if (ov) {
-        const int pos = __popc(mask & ((1u << lane) - 1u));
-        const ss_rec* rc = recs + c.id;
-        cp_async16(&W.h0[pos], &rc->r0);
-        cp_async16(&W.h1[pos], &rc->r1);
-        cp_async16(&W.h2[pos], &rc->r2);
-        cp_async16(&W.c0[pos], &rc->r4);
-        cp_async16(&W.c1[pos], &rc->r5);
-        cp_async16(&W.c2[pos], &rc->r6);
-        cp_async16(&W.zr[pos], &rc->r3);
-        if (RECT) rect[pos] = c.rect;
-        W.id[pos] = c.id;
-    }
-    cp_async_commit();
-    return __popc(mask);
-}
-
 // Issue the copies of record `id` into slot `lane` of W (lanes with
 // active), for lists that are already filtered.
 __device__ __forceinline__ void stage_ids(ss_wstage& W, const ss_rec* recs, uint32_t id, int lane, bool active) {
@@ -108,20 +78,6 @@ __device__ __forceinline__ void stage_ids(ss_wstage& W, const ss_rec* recs, uint
         W.id[lane] = id;
     }
     cp_async_commit();
-}
-
-// Ask L2 for the records of the instances of chunk c that stage_issue will
-// copy (same overlap test), so that their copies wait less.
-__device__ __forceinline__ void stage_prefetch(const ss_chunk& c, const ss_rec* recs, int gx0, int gx1, int gy0,
-                                               int gy1) {
-    if (!c.live) return;
-    const uint32_t rx = c.rect.x, ry = c.rect.y;
-    int i0 = rx & 0xffff, i1 = rx >> 16, j0 = ry & 0xffff, j1 = ry >> 16;
-    if (i0 <= gx1 && i1 >= gx0 && j0 <= gy1 && j1 >= gy0) {
-        const char* p = reinterpret_cast<const char*>(recs + c.id);
-        asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p));
-        asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p + sizeof(ss_rec) - 1));
-    }
 }
 
 // Wait for the copies of the n staged slots of W and rewrite them in place:

@@ -541,8 +541,7 @@ void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_a
 template <bool STATS, int RWPB_FWD>
 __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_fwd_args& a, const int gw,
                                                  unsigned char* fwd_smem) {
-    ss_wstage* Wst = reinterpret_cast<ss_wstage*>(fwd_smem);                          // [RWPB_FWD warps][2]
-    uint2* Wrect = reinterpret_cast<uint2*>(fwd_smem + 2 * RWPB_FWD * sizeof(ss_wstage));  // [RWPB_FWD][2][WSLOTS]
+    ss_wstage* Wst = reinterpret_cast<ss_wstage*>(fwd_smem);   // [RWPB_FWD warps][2]
     const ss_layout* L = ws.layout;
     const int lw = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile = gw >> 3, warp = gw & 7;          // 8 blocks per tile
@@ -613,20 +612,41 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
     uint2* clist = ws.cover_list ? ws.cover_list + 8 * beg + (int64_t)warp * (end - beg) : nullptr;
     uint32_t n_list = 0;
     ss_wstage* Wb = Wst + 2 * lw;
-    uint2* Rb = Wrect + 2 * lw * WSLOTS;
-    int buf = 0, n_next = 0;
-    if (beg < end)
-        n_next = stage_issue<true>(Wb[0], Rb, fetch_chunk(ws.keys, ws.rects, beg + lane, end), recs, lane, gx0, gx1,
-                                   gy0, gy1);
-    ss_chunk nxt = fetch_chunk(ws.keys, ws.rects, beg + 32 + lane, end);
-    for (int64_t base = beg; base < end; base += 32) {
+    // pass 1: the records whose support rectangle meets the block, in list
+    // order, into the warp's candidate list (four chunks of keys in flight)
+    uint32_t* cand = ws.cand_list + 8 * beg + (int64_t)warp * (end - beg);
+    int n_cand = 0;
+    for (int64_t j0 = beg; j0 < end; j0 += 128) {
+        ss_chunk c[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) c[u] = fetch_chunk(ws.keys, ws.rects, j0 + 32 * u + lane, end);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            bool ov = false;
+            if (c[u].live) {
+                const uint32_t rx = c[u].rect.x, ry = c[u].rect.y;
+                ov = (int)(rx & 0xffff) <= gx1 && (int)(rx >> 16) >= gx0 && (int)(ry & 0xffff) <= gy1 &&
+                     (int)(ry >> 16) >= gy0;
+            }
+            const uint32_t m = __ballot_sync(0xffffffffu, ov);
+            if (ov) cand[n_cand + __popc(m & ((1u << lane) - 1u))] = c[u].id;
+            n_cand += __popc(m);
+        }
+    }
+    __syncwarp();
+    // pass 2: the candidates 32 at a time, two-deep staging pipeline
+    int buf = 0;
+    uint32_t idn = lane < n_cand ? cand[lane] : 0u;
+    if (n_cand > 0) stage_ids(Wb[0], recs, idn, lane, lane < n_cand);
+    idn = 32 + lane < n_cand ? cand[32 + lane] : 0u;
+    for (int b0 = 0; b0 < n_cand; b0 += 32) {
         if (__all_sync(0xffffffffu, done)) break;   // every pixel of the block has K_max layers
         ss_wstage& W = Wb[buf];
-        const uint2* R = Rb + buf * WSLOTS;
-        const int n = n_next;
+        const int n = min(32, n_cand - b0);
         stage_finish(W, n, lane, (float)x0, (float)y0);
-        n_next = stage_issue<true>(Wb[buf ^ 1], Rb + (buf ^ 1) * WSLOTS, nxt, recs, lane, gx0, gx1, gy0, gy1);
-        nxt = fetch_chunk(ws.keys, ws.rects, base + 64 + lane, end);
+        const int n2 = min(32, n_cand - b0 - 32);
+        if (n2 > 0) stage_ids(Wb[buf ^ 1], recs, idn, lane, lane < n2);
+        idn = b0 + 64 + lane < n_cand ? cand[b0 + 64 + lane] : 0u;
         uint32_t my_mask = 0;
         // staged surfels whose exact support can reach a pixel centre of the block
         bool may = false;
@@ -641,12 +661,12 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
             const ss_hit h = ss_pixel_test(h0, h1, xl - h1.z, yl - h1.w, rc2);
             bool cg = h.cover && inside;   // geometric coverage (support and cutoff)
             if (STATS && inside) {
-                const uint2 rr = R[s];
+                const uint2 rr = make_uint2(__float_as_uint(W.zr[s].z), __float_as_uint(W.zr[s].w));
                 ++n_lane;
                 n_rect += in_rect(rr.x, rr.y, px, py) ? 1u : 0u;
             }
             if (cg && h2.z < 0.f) {   // support rectangle may clip this surfel
-                const uint2 rr = R[s];
+                const uint2 rr = make_uint2(__float_as_uint(W.zr[s].z), __float_as_uint(W.zr[s].w));
                 cg = in_rect(rr.x, rr.y, px, py);
             }
             const uint32_t cm = __ballot_sync(0xffffffffu, cg);
@@ -728,7 +748,7 @@ __global__ void __launch_bounds__(32 * RWPB_FWD, 24 / RWPB_FWD) raster_fwd_kerne
 
 template <bool STATS, int W>
 static void launch_raster_fwd(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st) {
-    const int smem = 2 * W * ((int)sizeof(ss_wstage) + WSLOTS * (int)sizeof(uint2));
+    const int smem = 2 * W * (int)sizeof(ss_wstage);
     static std::atomic<unsigned long long> optin{0}, resident{0};
     ss_smem_optin(raster_fwd_kernel<STATS, W>, smem, optin);
     const int n_items = (int)(L.total_tiles * 8);

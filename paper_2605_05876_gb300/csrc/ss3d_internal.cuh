@@ -95,6 +95,7 @@ struct ss_ws_view {
     unsigned long long* keys;      // [max_instances]
     unsigned long long* keys_alt;  // [max_instances]
     uint2* rects;           // [max_instances] support rectangle of each sorted instance
+    uint32_t* cand_list;    // [8 x max_instances] per (tile, block): records whose rectangle meets the block
     float* layer_state;     // [k_max][13][total_pixels]  (raw C (12), W)
     float* pix_state;       // [2][total_pixels]  (K as float bits, T_end)
     float* grad_rec;        // [total_records][SS_NGRAD]
