@@ -647,6 +647,11 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
         const int n2 = min(32, n_cand - b0 - 32);
         if (n2 > 0) stage_ids(Wb[buf ^ 1], recs, idn, lane, lane < n2);
         idn = b0 + 64 + lane < n_cand ? cand[b0 + 64 + lane] : 0u;
+        if (b0 + 64 + lane < n_cand) {   // ask L2 for the records two chunks ahead
+            const char* pr = reinterpret_cast<const char*>(recs + idn);
+            asm volatile("prefetch.global.L2 [%0];\n" ::"l"(pr));
+            asm volatile("prefetch.global.L2 [%0];\n" ::"l"(pr + sizeof(ss_rec) - 1));
+        }
         uint32_t my_mask = 0;
         // staged surfels whose exact support can reach a pixel centre of the block
         bool may = false;
