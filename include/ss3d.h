@@ -203,7 +203,11 @@ ss_status ss_env_sizes(const ss_env_desc* d, int64_t* irr_floats, int64_t* spec_
  *               L_i(w_t) = sum_j S_j D(h_j) max(0, w_t.w_j) dW_j / sum_j D(h_j) max(0, w_t.w_j) dW_j
  *               with GGX D at alpha = r_i^2 and (n.h_j)^2 = (1 + w_t.w_j)/2.
  * env_dev: [n_envs][H][W][3].  Writes irr, spec and aux (normalisers and
- * box-averaged sources, read by ss_env_prefilter_backward). */
+ * box-averaged sources, read by ss_env_prefilter_backward).
+ * The per-level convolutions run side by side on side streams that the
+ * library creates on the first call on a device and keeps; they are forked
+ * from `stream` and joined back to it with events before the call returns,
+ * so the work is ordered on `stream` as usual (and is capturable). */
 ss_status ss_env_prefilter(const ss_env_desc* d, int32_t n_envs, const float* env_dev,
                            float* irr_dev, float* spec_dev, float* aux_dev, void* stream);
 
@@ -228,7 +232,9 @@ ss_status ss_env_prefilter_noalloc(const ss_env_desc* d, int32_t n_envs, const f
                                    float* spec_dev, void* stream);
 
 /* Transpose of ss_env_prefilter: d_env += P^T (d_irr, d_spec).  aux_dev is
- * the scratch written by the forward call for the same env maps. */
+ * the scratch written by the forward call for the same env maps.  The level
+ * terms are added on the side streams with atomics, so the last bits of d_env
+ * can differ from call to call. */
 ss_status ss_env_prefilter_backward(const ss_env_desc* d, int32_t n_envs, const float* d_irr_dev,
                                     const float* d_spec_dev, const float* aux_dev, float* d_env_dev,
                                     void* stream);
