@@ -699,9 +699,13 @@ static std::mutex g_side_mutex;
 static ss_side g_side[64];
 static bool g_side_init[64];
 
-static ss_side* side_streams_locked(int dev) {
+static ss_side* side_streams_locked(int dev, cudaStream_t st) {
     if (dev < 0 || dev >= 64) return nullptr;
     if (!g_side_init[dev]) {
+        // creating streams inside a stream capture could end the caller's
+        // capture: a call captured before any eager one runs on `st` alone
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
         g_side_init[dev] = true;
         ss_side& x = g_side[dev];
         x.ok = cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming) == cudaSuccess;
@@ -746,7 +750,7 @@ void ss_launch_env_prefilter(const ss_env_desc* d, int n_envs, const float* env,
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(g_side_mutex);
-    ss_side* sd = side_streams_locked(dev);
+    ss_side* sd = side_streams_locked(dev, st);
     const bool fork = sd && d->n_levels - 1 <= SS_SIDE_STREAMS && cudaEventRecord(sd->fork, st) == cudaSuccess;
     int64_t spec_off = env_stride, aux_off = (int64_t)Wi * Hi;
     for (int i = 1; i < d->n_levels; ++i) {
@@ -787,7 +791,7 @@ void ss_launch_env_prefilter_bwd(const ss_env_desc* d, int n_envs, const float* 
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(g_side_mutex);
-    ss_side* sd = d_spec ? side_streams_locked(dev) : nullptr;
+    ss_side* sd = d_spec ? side_streams_locked(dev, st) : nullptr;
     const bool fork = sd && d->n_levels - 1 <= SS_SIDE_STREAMS && cudaEventRecord(sd->fork, st) == cudaSuccess;
     if (d_spec) {
         int64_t spec_off = env_stride, aux_off = (int64_t)Wi * Hi;
