@@ -172,8 +172,8 @@ static ss_status build_layout(const ss_batch_desc* b, const ss_render_params* p,
 }
 
 struct ws_plan {
-    size_t status, layout, vgeo, rec, tc, ts, tcur, keys, keys_alt, rects, cand, layer, pix, grad, masks, mcount,
-        env_acc, total;
+    size_t status, layout, vgeo, rec, rank, tc, ts, tcur, keys, keys_alt, rects, cand, layer, pix, grad, masks,
+        mcount, env_acc, total;
     int64_t env_texels;   // irradiance + specular texels of one scene (0: no env-gradient scratch)
 };
 
@@ -190,6 +190,7 @@ static ws_plan plan_ws(const ss_layout& L, const ss_render_params& p, int with_b
     w.layout = take(sizeof(ss_layout));
     w.vgeo = take(sizeof(ss_view_geo) * SS_MAX_VIEWS);
     w.rec = take(sizeof(ss_rec) * (size_t)L.total_records);
+    w.rank = take(sizeof(uint4) * (size_t)L.total_records);
     w.tc = take(sizeof(uint32_t) * SS_CNT_STRIDE * (size_t)L.total_tiles);
     w.ts = take(sizeof(uint32_t) * ((size_t)L.total_tiles + 1));
     w.tcur = take(sizeof(uint32_t) * SS_CNT_STRIDE * (size_t)L.total_tiles);
@@ -220,6 +221,7 @@ static ss_ws_view carve(void* ws, const ws_plan& w, const ss_render_params& p, i
     v.layout = (ss_layout*)(b + w.layout);
     v.vgeo = (ss_view_geo*)(b + w.vgeo);
     v.rec = (ss_rec*)(b + w.rec);
+    v.inst_rank = (uint4*)(b + w.rank);
     v.tile_count = (uint32_t*)(b + w.tc);
     v.tile_start = (uint32_t*)(b + w.ts);
     v.tile_cursor = (uint32_t*)(b + w.tcur);

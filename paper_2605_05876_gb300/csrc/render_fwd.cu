@@ -235,9 +235,23 @@ __global__ void __launch_bounds__(256, 4) project_kernel(ss_ws_view ws, ss_fwd_a
         rec.r6 = make_float4(metal, ns[0], ns[1], ns[2]);
         ws.rec[vl.rec_off + local] = rec;
         if (valid) {
-            int tx0 = i0 / SS_TILE, tx1 = i1 / SS_TILE, ty0 = j0 / SS_TILE, ty1 = j1 / SS_TILE;
-            for (int ty = ty0; ty <= ty1; ++ty)
-                for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&ws.tile_count[(size_t)(vl.tile_off + ty * vl.tiles_x + tx) * SS_CNT_STRIDE], 1u);
+            // bin counts: the record's rank in the bins of its first four tiles
+            // (kept for the scatter, which then needs no atomics for them),
+            // plain counts for the rest
+            const int tx0 = i0 / SS_TILE, tx1 = i1 / SS_TILE, ty0 = j0 / SS_TILE, ty1 = j1 / SS_TILE;
+            const int ntx = tx1 - tx0 + 1, nt = ntx * (ty1 - ty0 + 1);
+            uint32_t rk[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (q < nt) {
+                    const int t = vl.tile_off + (ty0 + q / ntx) * vl.tiles_x + tx0 + q % ntx;
+                    rk[q] = atomicAdd(&ws.tile_count[(size_t)t * SS_CNT_STRIDE], 1u);
+                }
+            for (int q = 4; q < nt; ++q) {
+                const int t = vl.tile_off + (ty0 + q / ntx) * vl.tiles_x + tx0 + q % ntx;
+                atomicAdd(&ws.tile_cursor[(size_t)t * SS_CNT_STRIDE], 1u);
+            }
+            ws.inst_rank[vl.rec_off + local] = make_uint4(rk[0], rk[1], rk[2], rk[3]);
         }
     }
 }
@@ -253,7 +267,8 @@ void ss_launch_project(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_ar
 // binning: exclusive scan of tile counts, scatter of (z_start, id) keys,
 // per-tile sort by (z_start, id) (Sec. 3.2.1: sort key z_start; ties by id)
 
-__global__ void __launch_bounds__(1024) scan_kernel(const uint32_t* cnt, uint32_t* start, int n, int* status,
+__global__ void __launch_bounds__(1024) scan_kernel(const uint32_t* cnt, const uint32_t* extra, uint32_t* start, int n,
+                                                    int* status,
                                                     int64_t cap, unsigned long long* stats) {
     __shared__ uint32_t wsum[32];
     __shared__ uint32_t carry;
@@ -262,7 +277,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const uint32_t* cnt, uint32_
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int base = 0; base < n; base += blockDim.x) {
         int i = base + threadIdx.x;
-        uint32_t v = i < n ? cnt[(size_t)i * SS_CNT_STRIDE] : 0u;
+        uint32_t v = i < n ? cnt[(size_t)i * SS_CNT_STRIDE] + extra[(size_t)i * SS_CNT_STRIDE] : 0u;
         uint32_t x = v;
         for (int o = 1; o < 32; o <<= 1) {
             uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -293,16 +308,17 @@ __global__ void __launch_bounds__(1024) scan_kernel(const uint32_t* cnt, uint32_
 }
 
 // One thread per record: its keys go to the bins of the tiles its support
-// rectangle covers, at positions taken from the tiles' cursors.  The cursor
-// atomics of up to 4 tiles are issued back to back so that their round trips
-// overlap.
+// rectangle covers, at the ranks the projection took in the bins of its
+// first four tiles; instances past those take positions behind the first-
+// four instances of their bin by counting the bin's cursor down.
 __global__ void __launch_bounds__(256) scatter_kernel(ss_ws_view ws, int64_t total_records) {
     const ss_layout* L = ws.layout;
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= total_records) return;
     const uint32_t flags = __float_as_uint(ws.rec[r].r4.w);
-    if (!(flags & SS_FLAG_VALID)) return;
     const float4 r3 = ws.rec[r].r3;
+    const uint4 rk = ws.inst_rank[r];
+    if (!(flags & SS_FLAG_VALID)) return;
     int v = 0;
     {
         int lo = 0, hi = L->n_views - 1;
@@ -321,21 +337,19 @@ __global__ void __launch_bounds__(256) scatter_kernel(ss_ws_view ws, int64_t tot
     // low half: the batch-wide record index (ties of z_start in one tile, which
     // belongs to one view, are broken by surfel index all the same)
     const unsigned long long key = ((unsigned long long)__float_as_uint(r3.x) << 32) | (uint32_t)r;
-    for (int b = 0; b < nt; b += 4) {
-        int t[4];
-        uint32_t pos[4];
+    const uint32_t rks[4] = {rk.x, rk.y, rk.z, rk.w};
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int q = b + u;
-            t[u] = q < nt ? vl.tile_off + (ty0 + q / ntx) * vl.tiles_x + tx0 + q % ntx : -1;
-            if (t[u] >= 0) pos[u] = atomicAdd(&ws.tile_cursor[(size_t)t[u] * SS_CNT_STRIDE], 1u);
+    for (int q = 0; q < 4; ++q)
+        if (q < nt) {
+            const int t = vl.tile_off + (ty0 + q / ntx) * vl.tiles_x + tx0 + q % ntx;
+            const uint32_t p = ws.tile_start[t] + rks[q];
+            if ((int64_t)p < ws.max_instances) ws.keys[p] = key;
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (t[u] >= 0) {
-                const uint32_t p = ws.tile_start[t[u]] + pos[u];
-                if ((int64_t)p < ws.max_instances) ws.keys[p] = key;
-            }
+    for (int q = 4; q < nt; ++q) {
+        const int t = vl.tile_off + (ty0 + q / ntx) * vl.tiles_x + tx0 + q % ntx;
+        const uint32_t k = atomicSub(&ws.tile_cursor[(size_t)t * SS_CNT_STRIDE], 1u) - 1u;
+        const uint32_t p = ws.tile_start[t] + ws.tile_count[(size_t)t * SS_CNT_STRIDE] + k;
+        if ((int64_t)p < ws.max_instances) ws.keys[p] = key;
     }
 }
 
@@ -516,7 +530,8 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view w
 void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st) {
     (void)a;
     ss_note_launch();
-    scan_kernel<<<1, 1024, 0, st>>>(ws.tile_count, ws.tile_start, L.total_tiles, ws.status, ws.max_instances,
+    scan_kernel<<<1, 1024, 0, st>>>(ws.tile_count, ws.tile_cursor, ws.tile_start, L.total_tiles, ws.status,
+                                    ws.max_instances,
                                     ws.stats);
     if (L.total_records > 0) {
         ss_note_launch();

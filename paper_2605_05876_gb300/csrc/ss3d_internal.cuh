@@ -89,9 +89,11 @@ struct ss_ws_view {
     ss_layout* layout;
     ss_view_geo* vgeo;      // [n_views]
     ss_rec* rec;
-    uint32_t* tile_count;   // [total_tiles][SS_CNT_STRIDE] (first word used)
+    uint32_t* tile_count;   // [total_tiles][SS_CNT_STRIDE] (first word used): instances of records' first four tiles
     uint32_t* tile_start;   // [total_tiles + 1]
-    uint32_t* tile_cursor;  // [total_tiles][SS_CNT_STRIDE] (first word used)
+    uint32_t* tile_cursor;  // [total_tiles][SS_CNT_STRIDE] (first word used): instances past a record's
+                            // first four tiles, counted by the projection, taken down by the scatter
+    uint4* inst_rank;       // [total_records] rank of the record in the bins of its first four tiles
     unsigned long long* keys;      // [max_instances]
     unsigned long long* keys_alt;  // [max_instances]
     uint2* rects;           // [max_instances] support rectangle of each sorted instance
