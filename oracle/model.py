@@ -53,7 +53,7 @@ class Params:
     """Renderer constants.  r_cut = 3 (App. A "Cutoff radius"),
     gamma = 2 pi (Sec. 3.5.1), K_max = 16 (App. A "Maximum layer count").
     sigma_f (the screen prefilter variance of Eq. mip_cov) is not given by
-    the paper; 0.5 px^2 is this build's default.  z_near and the background
+    the paper; 0.5 px^2 is the default here.  z_near and the background
     are not given either."""
     r_cut: float = 3.0
     sigma_f: float = 0.5
