@@ -38,7 +38,12 @@ FP32_LANES_PER_SM = 128
 # algorithmic FP32 work per unit (counted from the kernels' arithmetic):
 FLOP_TEST = 17        # one (pixel, surfel) test inside the support rectangle
 FLOP_FRAG_FWD = 30    # one covering fragment: weight + 12-channel accumulation
-FLOP_FRAG_BWD = 66    # one covering fragment in the backward pass
+# one covering fragment in the backward pass (with AOV gradients): pixel offset
+# 4, screen test 14, rho^2, exp and weight 4, depth channel 2, dL/dw over 12
+# channels 26, 12 channel gradients 12, dL/dn_f 1, dL/drho^2 and its chain to
+# s0, s1, s2 9, to P, A2, B2 6, to the centre 10; then the 21 values added
+# into their surfel's sums 21
+FLOP_FRAG_BWD = 109
 
 
 def parse():
