@@ -626,7 +626,7 @@ static void launch_conv_fwd(const float* src, int64_t src_stride, int Ws, int Hs
                             int Wo, int Ho, float* inv_norm, int64_t norm_stride, int ggx, float alpha, int n_envs,
                             cudaStream_t st) {
     const int r = Ws / Wo;
-    const int R = (r == 1 && Wo >= 64) ? 4 : 1;
+    const int R = (r == 1 && Wo >= 128) ? 8 : (r == 1 && Wo >= 64) ? 4 : 1;
     const int TA = (Wo / R < 256 / R) ? Wo / R : 256 / R;
     const int OT = TA * R;
     const int TD = Ws < 256 ? Ws : 256;
@@ -645,7 +645,10 @@ static void launch_conv_fwd(const float* src, int64_t src_stride, int Ws, int Hs
     const int red = (((nt * (3 * R + 1) + 1) & ~1) + 2 * (OT * 3 + 1)) * (int)sizeof(float);
     if (smem < red) smem = red;
     const dim3 grid(Ho * (Wo / OT) * KS, n_envs);
-    if (R == 4)
+    if (R == 8)
+        launch_cluster(envconv_fwd_kernel<8>, grid, nt, smem, KS, st, src, src_stride, Ws, Hs, out, out_stride, Wo, Ho,
+                       inv_norm, norm_stride, ggx, alpha, TA, P, TD, SCP);
+    else if (R == 4)
         launch_cluster(envconv_fwd_kernel<4>, grid, nt, smem, KS, st, src, src_stride, Ws, Hs, out, out_stride, Wo, Ho,
                        inv_norm, norm_stride, ggx, alpha, TA, P, TD, SCP);
     else
