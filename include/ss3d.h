@@ -23,7 +23,7 @@
  *  - Surfel i: centre pos[i], unit quaternion quat[i] = (w, x, y, z) (it is
  *    normalised inside), log-scales (s_u, s_v); the tangent vectors are
  *    t_u = exp(s_u) R(q) e_x, t_v = exp(s_v) R(q) e_y and the normal is
- *    R(q) e_z (Sec. 3.1, Sec. 3.6).  Albedo, roughness and metallic are
+ *    R(q) e_z (Sec. 3.1, Sec. 3.7).  Albedo, roughness and metallic are
  *    activated values in [0, 1].
  *  - Camera: OpenCV pinhole, x_cam = R x_world + t, pixel (i, j) has its
  *    centre at (i + 0.5, j + 0.5), x_pix = fx X/Z + cx.

@@ -252,6 +252,28 @@ def quat_to_rot(q: torch.Tensor):
         torch.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)], -2)
 
 
+def mip_filter(T: torch.Tensor, depth_ok: torch.Tensor, prm: Params):
+    """Centre-precomputed MIP filter (Sec. 3.3.2) of T-matrix rows
+    T [N, 3, 3] = (T1, T2, T4): J = d(u,v)/d(x,y) at the centre is the inverse
+    of M = d(x,y)/d(u,v) there, with x = T1.u/T4.u; Sigma = I + sigma_f J J^T
+    (Eq. mip_cov), n_f = sqrt(|I| / |Sigma|) (Eq. mip_eval).  Returns
+    (Sigma^-1, n_f, M, valid) with valid = depth_ok and det M != 0."""
+    T1, T2, T4 = T[:, 0], T[:, 1], T[:, 2]
+    px = T1[:, 2] / T4[:, 2]
+    py = T2[:, 2] / T4[:, 2]
+    M = torch.stack([
+        torch.stack([T1[:, 0] - px * T4[:, 0], T1[:, 1] - px * T4[:, 1]], -1),
+        torch.stack([T2[:, 0] - py * T4[:, 0], T2[:, 1] - py * T4[:, 1]], -1)], -2) / T4[:, 2, None, None]
+    detM = M[:, 0, 0] * M[:, 1, 1] - M[:, 0, 1] * M[:, 1, 0]
+    valid = depth_ok & (detM != 0)
+    Msafe = torch.where(valid[:, None, None], M, torch.eye(2, dtype=F64).expand_as(M))
+    J = torch.linalg.inv(Msafe)
+    Sigma = torch.eye(2, dtype=F64) + prm.sigma_f * (J @ J.transpose(1, 2))   # Eq. mip_cov
+    Sinv = torch.linalg.inv(Sigma)
+    n_f = torch.rsqrt(torch.linalg.det(Sigma))                                # sqrt(|I| / |Sigma|)
+    return Sinv, n_f, M, valid
+
+
 def records(S: dict, cam: dict, irr, levels, lut, prm: Params):
     """Everything the rasteriser needs for one view, as FP64 tensors that
     stay differentiable w.r.t. the surfel parameters in S and the env
@@ -262,7 +284,7 @@ def records(S: dict, cam: dict, irr, levels, lut, prm: Params):
     """
     R = quat_to_rot(S["quat"])
     scale = torch.exp(S["log_scale"])
-    t_u = scale[:, 0:1] * R[:, :, 0]          # Sec. 3.6: quaternion + log scales
+    t_u = scale[:, 0:1] * R[:, :, 0]          # Sec. 3.7: quaternion + log scales
     t_v = scale[:, 1:2] * R[:, :, 1]
     n = R[:, :, 2]                            # = t_u x t_v / |.| (Sec. 3.1)
     Rc, tc = cam["R"], cam["t"]
@@ -283,20 +305,8 @@ def records(S: dict, cam: dict, irr, levels, lut, prm: Params):
     z = c_cam[:, 2]
     eps = prm.r_cut * torch.sqrt(tu_c[:, 2] ** 2 + tv_c[:, 2] ** 2)
     zs, ze = z - eps, z + eps
-    # centre-precomputed MIP filter (Sec. 3.3.2): J = d(u,v)/d(x,y) at the
-    # centre is the inverse of M = d(x,y)/d(u,v) there, with x = T1.u/T4.u.
-    px = T1[:, 2] / T4[:, 2]
-    py = T2[:, 2] / T4[:, 2]
-    M = torch.stack([
-        torch.stack([T1[:, 0] - px * T4[:, 0], T1[:, 1] - px * T4[:, 1]], -1),
-        torch.stack([T2[:, 0] - py * T4[:, 0], T2[:, 1] - py * T4[:, 1]], -1)], -2) / T4[:, 2, None, None]
-    detM = M[:, 0, 0] * M[:, 1, 1] - M[:, 0, 1] * M[:, 1, 0]
-    valid = (zs > prm.z_near) & (detM != 0)
-    Msafe = torch.where(valid[:, None, None], M, torch.eye(2, dtype=F64).expand_as(M))
-    J = torch.linalg.inv(Msafe)
-    Sigma = torch.eye(2, dtype=F64) + prm.sigma_f * (J @ J.transpose(1, 2))   # Eq. mip_cov
-    Sinv = torch.linalg.inv(Sigma)
-    n_f = torch.rsqrt(torch.linalg.det(Sigma))                                # sqrt(|I| / |Sigma|)
+    T = torch.stack([T1, T2, T4], 1)                                     # [N, 3, 3]
+    Sinv, n_f, M, valid = mip_filter(T, zs > prm.z_near, prm)
 
     # forward shading (Sec. 3.4, Eq. ibl), one colour per surfel and view
     o = -(Rc.T @ tc)                                   # camera centre
@@ -316,7 +326,6 @@ def records(S: dict, cam: dict, irr, levels, lut, prm: Params):
     colour = k_d * rho * L_d + L_s * (F0 * beta[:, 0:1] + beta[:, 1:2])
 
     ch = torch.cat([colour, rho, r[:, None], m, n_s, z[:, None]], -1)   # [N, 12]
-    T = torch.stack([T1, T2, T4], 1)                                     # [N, 3, 3]
     return dict(T=T, Sinv=Sinv, n_f=n_f, zs=zs, ze=ze, valid=valid, ch=ch, M=M)
 
 
@@ -407,10 +416,12 @@ def fragments(rec: dict, rect: np.ndarray, W: int, H: int, prm: Params, pix=None
     return Fragments(fp, fs, fl, q, nl, mg, cnt)
 
 
-def composite(rec: dict, fr: Fragments, W: int, prm: Params):
+def composite(rec: dict, fr: Fragments, W: int, prm: Params, per_frag: dict | None = None):
     """Layer sums, Shepard normalisation, coverage opacity and compositing
     for the queried pixels.  Returns (rgba [P,4], aov [P,9]) as FP64
-    tensors, differentiable w.r.t. the record tensors."""
+    tensors, differentiable w.r.t. the record tensors.  per_frag, if given,
+    holds the fragments' own copies of T, Sinv, n_f and ch (rec[k][fr.sid]),
+    so that autograd yields one gradient per fragment."""
     P = fr.q_pix.shape[0]
     Kq = max(1, int(fr.n_layers.max()) if P else 1)
     # row of each fragment within the query
@@ -426,7 +437,8 @@ def composite(rec: dict, fr: Fragments, W: int, prm: Params):
     layer = torch.from_numpy(fr.layer.astype(np.int64))
     x = torch.from_numpy((fr.pix % W).astype(np.float64)) + 0.5
     y = torch.from_numpy((fr.pix // W).astype(np.float64)) + 0.5
-    T = rec["T"][sid]
+    fv = (lambda k: per_frag[k]) if per_frag is not None else (lambda k: rec[k][sid])
+    T = fv("T")
     T1, T2, T4 = T[:, 0], T[:, 1], T[:, 2]
     # ray planes pulled back through T (Sec. 3.1) and their common zero
     k = x[:, None] * T4 - T1
@@ -434,12 +446,12 @@ def composite(rec: dict, fr: Fragments, W: int, prm: Params):
     s = torch.linalg.cross(k, l, dim=-1)
     u = s[:, 0] / s[:, 2]
     v = s[:, 1] / s[:, 2]
-    Si = rec["Sinv"][sid]
+    Si = fv("Sinv")
     rho2 = Si[:, 0, 0] * u * u + 2.0 * Si[:, 0, 1] * u * v + Si[:, 1, 1] * v * v   # Eq. mip_weight
-    w = rec["n_f"][sid] * torch.exp(-0.5 * rho2)
+    w = fv("n_f") * torch.exp(-0.5 * rho2)
     key = row_t * Kq + layer
     Wk = torch.zeros(P * Kq, dtype=F64).index_add(0, key, w).reshape(P, Kq)
-    Ck = torch.zeros(P * Kq, N_CH, dtype=F64).index_add(0, key, w[:, None] * rec["ch"][sid]).reshape(P, Kq, N_CH)
+    Ck = torch.zeros(P * Kq, N_CH, dtype=F64).index_add(0, key, w[:, None] * fv("ch")).reshape(P, Kq, N_CH)
     present = torch.arange(Kq)[None, :] < torch.from_numpy(fr.n_layers.astype(np.int64))[:, None]
     Wsafe = torch.where(present, Wk, torch.ones_like(Wk))
     Chat = Ck / Wsafe[..., None]                                   # Eq. shepard
@@ -584,3 +596,59 @@ def render_view(surf, cam, env: EnvState, prm: Params = Params(), pix=None, G=No
         He, We, _ = env.shape
         out["grad"]["env"] = env_adjoint(d_irr, d_lv, We, He)
     return out
+
+
+def screen_grad_stat(surf, cam, env: EnvState, prm: Params = Params(), G=None, pix=None):
+    """Per-fragment screen-space positional gradients of Eq. ss_grad and
+    their per-surfel sum of norms, for one view.
+
+    The screen centre is (T_{1,z} / T_{4,z}, T_{2,z} / T_{4,z}) (the z
+    entries are the columns that multiply the centre c'); a fragment's
+    contribution is g_x = dL_p/dT_{1,z} T_{4,z}, g_y = dL_p/dT_{2,z} T_{4,z},
+    where L_p = sum(G[p] * [rgba, aov](p)) is the loss of the fragment's pixel
+    and dL_p/dT covers both the ray-plane intersection and the centre-
+    precomputed MIP filter (Sigma^-1 and n_f are functions of T), with every
+    discrete decision and the shaded channels held fixed (the shading is
+    not part of the T-matrix backward).  The statistic accumulates the
+    per-fragment norms |(g_x, g_y)|, so that opposite contributions do not
+    cancel (Sec. 3.6.1, densification criterion).
+
+    G: upstream gradient [P, 13] for the queried pixels (all pixels, or
+    `pix`).  Returns dict(sid, pix, gx, gy) per fragment and per surfel
+    sum_norm [N] and n_frag [N] (fragments that reached it)."""
+    S = to_torch_surfels(surf)
+    cd = cam_dict(cam)
+    irr = torch.from_numpy(env.irr.copy())
+    levels = [torch.from_numpy(l.copy()) for l in env.levels]
+    lut = torch.from_numpy(env.lut.copy())
+    W, H = cd["width"], cd["height"]
+    with torch.no_grad():
+        rec = records(S, cd, irr, levels, lut, prm)
+    rect = support_rect(rec, prm)
+    q = np.arange(W * H, dtype=np.int32) if pix is None else np.asarray(pix, np.int32)
+    fr = fragments(rec, rect, W, H, prm, pix=q)
+    sid = torch.from_numpy(fr.sid.astype(np.int64))
+    pf = {k: rec[k][sid].detach().clone().requires_grad_(k != "ch") for k in ("T", "Sinv", "n_f", "ch")}
+    rgba, aov = composite(rec, fr, W, prm, per_frag=pf)
+    Gt = torch.from_numpy(np.asarray(G, np.float64))
+    (torch.cat([rgba, aov], 1) * Gt).sum().backward()
+    # directional derivatives of the MIP filter along T_{1,z} and T_{2,z}
+    T = rec["T"].detach()
+    depth_ok = rec["zs"] > prm.z_near
+
+    def mip(Tv):
+        Sinv, n_f, _, _ = mip_filter(Tv, depth_ok, prm)
+        return Sinv, n_f
+
+    g = {}
+    for row, name in ((0, "gx"), (1, "gy")):
+        tang = torch.zeros_like(T)
+        tang[:, row, 2] = 1.0
+        _, (dS, dn) = torch.func.jvp(mip, (T,), (tang,))
+        dLdT = (pf["T"].grad[:, row, 2] + (pf["Sinv"].grad * dS[sid]).sum((1, 2)) + pf["n_f"].grad * dn[sid])
+        g[name] = (dLdT * T[sid, 2, 2]).numpy()
+    norm = np.sqrt(g["gx"] ** 2 + g["gy"] ** 2)
+    N = T.shape[0]
+    return dict(sid=fr.sid.copy(), pix=fr.pix.copy(), gx=g["gx"], gy=g["gy"],
+                sum_norm=np.bincount(fr.sid, weights=norm, minlength=N),
+                n_frag=np.bincount(fr.sid, minlength=N))
