@@ -132,6 +132,24 @@ def test_forward_layer_cap(k_max):
     assert ref["n_layers"].max() == min(k_max, 4)
 
 
+def test_forward_crowded_tile_sorted_in_several_chunks():
+    """12800 surfels in one 16 x 16 tile (16 planes of 800, K_max layers at
+    the covered pixels): the tile's list is longer than one sorting chunk,
+    so it is sorted in chunks and merged; ties of z_start within a plane are
+    broken by record index."""
+    rng = np.random.default_rng(17)
+    pos = np.concatenate([np.concatenate([rng.uniform(-1.2, -0.8, size=(800, 2)), np.full((800, 1), 0.05 * k)], 1)
+                          for k in range(16)])
+    surf = _tiny.surfels(pos, scale=0.03, albedo=rng.uniform(0, 1, (pos.shape[0], 3)))
+    sc = S.Scene(surf, np.array([0, surf.n]), [_tiny.lognormal_env(rng, 32, 16)], [_tiny.front_camera(res=32)],
+                 "crowd")
+    r = _renderer(sc)
+    r.forward()
+    assert r.stats()["instances"] >= 12800     # all in the one tile the positions project into
+    ref, gpu = _check_view(r, sc, 0)
+    assert ref["n_layers"].max() == 16
+
+
 def test_forward_empty_and_culled():
     """All surfels behind the camera: image is the background, alpha 0."""
     surf = _tiny.surfels([[0, 0, 5.0], [0.1, 0, 4.0]], scale=0.1)
