@@ -224,6 +224,9 @@ ss_status ss_env_prefilter(const ss_env_desc* d, int32_t n_envs, const float* en
  * SS_NOALLOC_AUX_FLOATS (e.g. at most 5 maps of 512 x 256 with 6 levels).
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * That address is kept for the rest of the process and is only valid while
+ * the device's context lives: after cudaDeviceReset on that device, do not
+ * call this entry point again in the same process.
  * All calls share the array and it keeps the last call's contents, so calls
  * that overlap on the GPU (on different streams) race.  The scratch it keeps
  * is not the aux that ss_env_prefilter_backward expects. */
@@ -243,7 +246,9 @@ ss_status ss_env_prefilter_backward(const ss_env_desc* d, int32_t n_envs, const 
  * per-pixel layer state that ss_render_backward reads and, for the env
  * description ed (required then: the one later passed to the render calls),
  * the accumulators of the env-map gradients.  Requires p->max_instances > 0.
- * Errors: SS_ERR_INVALID_ARG for bad sizes or an invalid ed. */
+ * Host only (reads no device memory).  Errors: SS_ERR_INVALID_ARG for bad
+ * sizes, an invalid ed or a launch shape (fwd_warps, bwd_warps, pbwd_block)
+ * without a compiled kernel; the render calls reject the same values. */
 ss_status ss_workspace_size(const ss_batch_desc* b, const ss_render_params* p, const ss_env_desc* ed,
                             int32_t with_backward, size_t* bytes);
 

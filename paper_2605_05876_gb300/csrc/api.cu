@@ -33,21 +33,19 @@ struct profiler {
 };
 profiler g_prof;
 
-struct stage_scope {
-    int idx = -1;
-    cudaStream_t st;
-    stage_scope(int stage, cudaStream_t s) : st(s) {
-        if (!g_prof.on) return;
-        prof_rec r{stage, g_prof.take(), g_prof.take()};
-        cudaEventRecord(r.a, st);
-        g_prof.recs.push_back(r);
-        idx = (int)g_prof.recs.size() - 1;
-    }
-    ~stage_scope() {
-        if (idx >= 0) cudaEventRecord(g_prof.recs[idx].b, st);
-    }
-};
 }  // namespace
+
+int ss_stage_open(int stage, cudaStream_t st) {
+    if (!g_prof.on) return -1;
+    prof_rec r{stage, g_prof.take(), g_prof.take()};
+    cudaEventRecord(r.a, st);
+    g_prof.recs.push_back(r);
+    return (int)g_prof.recs.size() - 1;
+}
+
+void ss_stage_close(int handle, cudaStream_t st) {
+    if (handle >= 0 && handle < (int)g_prof.recs.size()) cudaEventRecord(g_prof.recs[handle].b, st);
+}
 
 static std::atomic<long long> g_launches{0};
 void ss_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -92,6 +90,14 @@ extern "C" ss_status ss_profile_end(ss_stage_times* out) {
     } while (0)
 
 static inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// launch shapes: only the values with a compiled kernel instance
+static ss_status check_knobs(const ss_render_params* p) {
+    if (!(p->fwd_warps == 0 || p->fwd_warps == 1 || p->fwd_warps == 2 || p->fwd_warps == 4)) return SS_ERR_INVALID_ARG;
+    if (!(p->bwd_warps == 0 || p->bwd_warps == 2 || p->bwd_warps == 4 || p->bwd_warps == 8)) return SS_ERR_INVALID_ARG;
+    if (!(p->pbwd_block == 0 || (p->pbwd_block >= 32 && p->pbwd_block <= 1024))) return SS_ERR_INVALID_ARG;
+    return SS_OK;
+}
 
 extern "C" void ss_default_params(ss_render_params* p) {
     if (!p) return;
@@ -274,6 +280,7 @@ static bool env_desc_ok(const ss_env_desc* d);
 extern "C" ss_status ss_workspace_size(const ss_batch_desc* b, const ss_render_params* p, const ss_env_desc* ed,
                                        int32_t with_backward, size_t* bytes) {
     if (!bytes || !p || p->max_instances <= 0 || p->max_instances > 0xffffffffll) return SS_ERR_INVALID_ARG;
+    if (check_knobs(p)) return SS_ERR_INVALID_ARG;
     ss_layout L;   // on the stack: entry points may be called from several threads
     ss_status st = build_layout(b, p, &L);
     if (st) return st;
@@ -322,7 +329,7 @@ extern "C" ss_status ss_env_prefilter(const ss_env_desc* d, int32_t n_envs, cons
     if (!env_desc_ok(d) || n_envs < 1 || !env_dev || !irr_dev || !spec_dev || !aux_dev) return SS_ERR_INVALID_ARG;
     if (d->n_levels < 2 && d->n_levels != 1) return SS_ERR_INVALID_ARG;
     {
-        stage_scope sc(5, (cudaStream_t)stream);
+        ss_stage_scope sc(5, (cudaStream_t)stream);
         ss_launch_env_prefilter(d, n_envs, env_dev, irr_dev, spec_dev, aux_dev, (cudaStream_t)stream);
     }
     CK(cudaGetLastError());
@@ -334,7 +341,7 @@ extern "C" ss_status ss_env_prefilter_backward(const ss_env_desc* d, int32_t n_e
                                                void* stream) {
     if (!env_desc_ok(d) || n_envs < 1 || !aux_dev || !d_env_dev) return SS_ERR_INVALID_ARG;
     {
-        stage_scope sc(6, (cudaStream_t)stream);
+        ss_stage_scope sc(6, (cudaStream_t)stream);
         ss_launch_env_prefilter_bwd(d, n_envs, d_irr_dev, d_spec_dev, aux_dev, d_env_dev, (cudaStream_t)stream);
     }
     CK(cudaGetLastError());
@@ -351,10 +358,7 @@ static ss_status check_render_args(const ss_batch_desc* b, const ss_surfels* s, 
     if (!env->irr || !env->spec || !env->lut || !env_desc_ok(ed)) return SS_ERR_INVALID_ARG;
     if (((uintptr_t)s->quat & 15) || ((uintptr_t)s->log_scale & 7) || ((uintptr_t)ws & 255)) return SS_ERR_INVALID_ARG;
     if (p->max_instances <= 0 || p->max_instances > 0xffffffffll) return SS_ERR_INVALID_ARG;
-    if (!(p->fwd_warps == 0 || p->fwd_warps == 1 || p->fwd_warps == 2 || p->fwd_warps == 4)) return SS_ERR_INVALID_ARG;
-    if (!(p->bwd_warps == 0 || p->bwd_warps == 2 || p->bwd_warps == 4 || p->bwd_warps == 8)) return SS_ERR_INVALID_ARG;
-    if (!(p->pbwd_block == 0 || (p->pbwd_block >= 32 && p->pbwd_block <= 1024))) return SS_ERR_INVALID_ARG;
-    return SS_OK;
+    return check_knobs(p);
 }
 
 static ss_status forward_core(const ss_batch_desc* b, const ss_surfels* s, const ss_render_params* p,
@@ -385,11 +389,11 @@ static ss_status forward_core(const ss_batch_desc* b, const ss_surfels* s, const
     CK(cudaMemsetAsync(W.tile_count, 0, sizeof(uint32_t) * SS_CNT_STRIDE * (size_t)L.total_tiles, st));
     CK(cudaMemsetAsync(W.tile_cursor, 0, sizeof(uint32_t) * SS_CNT_STRIDE * (size_t)L.total_tiles, st));
     {
-        stage_scope sc(0, st);
+        ss_stage_scope sc(0, st);
         ss_launch_project(W, L, a, st);
     }
     {
-        stage_scope sc(1, st);
+        ss_stage_scope sc(1, st);
         ss_launch_bin_sort(W, L, a, st);  // for a count, the scatter is bounded by capacity 1
     }
     if (stop_after_count) {
@@ -397,7 +401,7 @@ static ss_status forward_core(const ss_batch_desc* b, const ss_surfels* s, const
         return SS_OK;
     }
     {
-        stage_scope sc(2, st);
+        ss_stage_scope sc(2, st);
         ss_launch_raster_fwd(W, L, a, st);
     }
     CK(cudaGetLastError());
@@ -431,8 +435,9 @@ extern "C" ss_status ss_count_instances(const ss_batch_desc* b, const ss_surfels
     cudaStream_t st = (cudaStream_t)stream;
     ss_status e = forward_core(b, s, &q, ed, env, nullptr, nullptr, ws, ws_bytes, 0, 1, st, L, W);
     if (e) return e;
-    uint32_t total = 0;
-    CK(cudaMemcpyAsync(&total, W.tile_start + L.total_tiles, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    // the scan's 64-bit total (the 32-bit tile starts are clamped to the capacity)
+    unsigned long long total = 0;
+    CK(cudaMemcpyAsync(&total, W.stats, sizeof(total), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     *count = (int64_t)total;
     return SS_OK;
@@ -476,11 +481,11 @@ extern "C" ss_status ss_render_backward(const ss_batch_desc* b, const ss_surfels
                            st));
     CK(cudaMemsetAsync(W.work + 1, 0, sizeof(unsigned int), st));   // backward work-queue head
     {
-        stage_scope sc(3, st);
+        ss_stage_scope sc(3, st);
         ss_launch_raster_bwd(W, L, a, st);
     }
     {
-        stage_scope sc(4, st);
+        ss_stage_scope sc(4, st);
         ss_launch_project_bwd(W, L, a, st);
     }
     CK(cudaGetLastError());

@@ -849,7 +849,9 @@ extern "C" ss_status ss_env_prefilter_noalloc(const ss_env_desc* d, int32_t n_en
     float* aux = nullptr;
     {
         // first call on this device: look up the array's device address (the
-        // host-side symbol is only a stand-in, not a device pointer)
+        // host-side symbol is only a stand-in, not a device pointer).  It is
+        // kept for the life of the process: it stays valid as long as the
+        // device's context does (a cudaDeviceReset ends it).
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);
         if (!g_noalloc_aux_ptr[dev]) {
             void* p = nullptr;
@@ -859,7 +861,10 @@ extern "C" ss_status ss_env_prefilter_noalloc(const ss_env_desc* d, int32_t n_en
         aux = g_noalloc_aux_ptr[dev];
     }
     // every aux entry is written before it is read: nothing needs clearing
-    ss_launch_env_prefilter(d, n_envs, env_dev, irr_dev, spec_dev, aux, (cudaStream_t)stream);
+    {
+        ss_stage_scope sc(5, (cudaStream_t)stream);   // timed as the prefilter stage
+        ss_launch_env_prefilter(d, n_envs, env_dev, irr_dev, spec_dev, aux, (cudaStream_t)stream);
+    }
     if (cudaGetLastError() != cudaSuccess) return SS_ERR_CUDA;
     return SS_OK;
 }

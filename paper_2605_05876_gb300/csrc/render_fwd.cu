@@ -270,15 +270,20 @@ void ss_launch_project(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_ar
 __global__ void __launch_bounds__(1024) scan_kernel(const uint32_t* cnt, const uint32_t* extra, uint32_t* start, int n,
                                                     int* status,
                                                     int64_t cap, unsigned long long* stats) {
+    // The running total is kept in 64 bits: a batch with 2^32 or more
+    // instances must be reported, not wrapped.  Tile starts past the 32-bit
+    // range (or past the capacity) are stored clamped to the capacity, so
+    // those tiles read as empty and the scatter places none of their keys.
     __shared__ uint32_t wsum[32];
-    __shared__ uint32_t carry;
+    __shared__ unsigned long long carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned long long lim = (unsigned long long)cap;   // cap <= 0xffffffff (host-checked)
     for (int base = 0; base < n; base += blockDim.x) {
         int i = base + threadIdx.x;
         uint32_t v = i < n ? cnt[(size_t)i * SS_CNT_STRIDE] + extra[(size_t)i * SS_CNT_STRIDE] : 0u;
-        uint32_t x = v;
+        uint32_t x = v;   // a prefix of at most 1024 tile counts; counts per tile stay far below 2^22
         for (int o = 1; o < 32; o <<= 1) {
             uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
@@ -294,16 +299,16 @@ __global__ void __launch_bounds__(1024) scan_kernel(const uint32_t* cnt, const u
             wsum[lane] = s;
         }
         __syncthreads();
-        uint32_t excl = carry + (w > 0 ? wsum[w - 1] : 0u) + x - v;
-        if (i < n) start[i] = excl;
+        const unsigned long long excl = carry + (w > 0 ? wsum[w - 1] : 0u) + x - v;
+        if (i < n) start[i] = (uint32_t)(excl < lim ? excl : lim);
         __syncthreads();
         if (threadIdx.x == blockDim.x - 1) carry = excl + v;
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        start[n] = carry;
+        start[n] = (uint32_t)(carry < lim ? carry : lim);
         stats[0] = carry;
-        if ((int64_t)carry > cap) atomicOr(status, SS_ERR_CAPACITY);
+        if (carry > lim) atomicOr(status, SS_ERR_CAPACITY);
     }
 }
 
@@ -342,13 +347,13 @@ __global__ void __launch_bounds__(256) scatter_kernel(ss_ws_view ws, int64_t tot
     for (int q = 0; q < 4; ++q)
         if (q < nt) {
             const int t = vl.tile_off + (ty0 + q / ntx) * vl.tiles_x + tx0 + q % ntx;
-            const uint32_t p = ws.tile_start[t] + rks[q];
+            const uint64_t p = (uint64_t)ws.tile_start[t] + rks[q];
             if ((int64_t)p < ws.max_instances) ws.keys[p] = key;
         }
     for (int q = 4; q < nt; ++q) {
         const int t = vl.tile_off + (ty0 + q / ntx) * vl.tiles_x + tx0 + q % ntx;
         const uint32_t k = atomicSub(&ws.tile_cursor[(size_t)t * SS_CNT_STRIDE], 1u) - 1u;
-        const uint32_t p = ws.tile_start[t] + ws.tile_count[(size_t)t * SS_CNT_STRIDE] + k;
+        const uint64_t p = (uint64_t)ws.tile_start[t] + ws.tile_count[(size_t)t * SS_CNT_STRIDE] + k;
         if ((int64_t)p < ws.max_instances) ws.keys[p] = key;
     }
 }

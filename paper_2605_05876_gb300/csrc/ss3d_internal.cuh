@@ -272,6 +272,18 @@ __device__ __forceinline__ ss_hit ss_pixel_test(float4 r0, float4 r1, float dx, 
 // host-side count of kernel launches (ss_launch_count); call before each launch
 void ss_note_launch();
 
+// Stage timing of ss_profile_begin / ss_profile_end: events recorded on the
+// launching stream around one stage's launches (nothing while no profile is
+// open).  ss_stage_open returns a handle for ss_stage_close (-1: not profiling).
+int ss_stage_open(int stage, cudaStream_t st);
+void ss_stage_close(int handle, cudaStream_t st);
+struct ss_stage_scope {
+    int h;
+    cudaStream_t st;
+    ss_stage_scope(int stage, cudaStream_t s) : h(ss_stage_open(stage, s)), st(s) {}
+    ~ss_stage_scope() { ss_stage_close(h, st); }
+};
+
 // Opt kernel `k` in to `bytes` of dynamic shared memory on the current device
 // (a per-device attribute): once per device, tracked in `done` (bit = device).
 template <typename K>

@@ -78,8 +78,8 @@ def test_host_side_argument_errors():
 
 
 def test_launch_shape_knobs_are_validated_on_the_host():
-    """Unsupported launch shapes are rejected before anything is enqueued
-    (the pointers below are never dereferenced)."""
+    """Unsupported launch shapes are rejected by the host-only workspace query
+    (no device pointer is involved; the render calls share the same check)."""
     lib = _lib.lib()
     p = _lib.ss_render_params()
     lib.ss_default_params(ctypes.byref(p))
@@ -89,15 +89,43 @@ def test_launch_shape_knobs_are_validated_on_the_host():
     cams[0].width = cams[0].height = 16
     cams[0].fx = cams[0].fy = 10.0
     off = (ctypes.c_int64 * 2)(0, 10)
-    fake = ctypes.c_void_p(1 << 20)
-    d = _lib.ss_batch_desc(1, 1, off, cams, fake)
-    s = _lib.ss_surfels(fake, fake, fake, fake, fake, fake)
+    d = _lib.ss_batch_desc(1, 1, off, cams, None)
     ed = _lib.ss_env_desc(64, 32, 6, 32, 16)
-    em = _lib.ss_env_maps(fake, fake, fake)
-    for knob, bad in (("fwd_warps", 3), ("bwd_warps", 1), ("pbwd_block", 16), ("pbwd_block", 4096)):
+    nb = ctypes.c_size_t()
+    assert lib.ss_workspace_size(ctypes.byref(d), ctypes.byref(p), ctypes.byref(ed), 1, ctypes.byref(nb)) == 0
+    for knob, bad, good in (("fwd_warps", 3, 4), ("bwd_warps", 1, 8), ("pbwd_block", 16, 32),
+                            ("pbwd_block", 4096, 1024)):
         q = _lib.ss_render_params()
         ctypes.memmove(ctypes.byref(q), ctypes.byref(p), ctypes.sizeof(q))
         setattr(q, knob, bad)
-        st = lib.ss_render_forward(ctypes.byref(d), ctypes.byref(s), ctypes.byref(q), ctypes.byref(ed),
-                                   ctypes.byref(em), fake, fake, fake, 1 << 40, None)
+        st = lib.ss_workspace_size(ctypes.byref(d), ctypes.byref(q), ctypes.byref(ed), 1, ctypes.byref(nb))
         assert st == _lib.SS_ERR_INVALID_ARG, knob
+        setattr(q, knob, good)
+        st = lib.ss_workspace_size(ctypes.byref(d), ctypes.byref(q), ctypes.byref(ed), 1, ctypes.byref(nb))
+        assert st == 0, knob
+
+
+def test_render_calls_reject_null_device_pointers():
+    """The render entry points reject NULL device pointers on the host before
+    anything is enqueued (no device address is ever made up here)."""
+    lib = _lib.lib()
+    p = _lib.ss_render_params()
+    lib.ss_default_params(ctypes.byref(p))
+    p.max_instances = 1000
+    cams = (_lib.ss_camera * 1)()
+    cams[0].width = cams[0].height = 16
+    cams[0].fx = cams[0].fy = 10.0
+    off = (ctypes.c_int64 * 2)(0, 10)
+    d = _lib.ss_batch_desc(1, 1, off, cams, None)
+    s = _lib.ss_surfels(None, None, None, None, None, None)
+    ed = _lib.ss_env_desc(64, 32, 6, 32, 16)
+    em = _lib.ss_env_maps(None, None, None)
+    st = lib.ss_render_forward(ctypes.byref(d), ctypes.byref(s), ctypes.byref(p), ctypes.byref(ed), ctypes.byref(em),
+                               None, None, None, 0, None)
+    assert st == _lib.SS_ERR_INVALID_ARG
+    g = _lib.ss_surfel_grads(None, None, None, None, None, None)
+    st = lib.ss_render_backward(ctypes.byref(d), ctypes.byref(s), ctypes.byref(p), ctypes.byref(ed),
+                                ctypes.byref(em), None, None, None, None, ctypes.byref(g), None, None, 0, None)
+    assert st == _lib.SS_ERR_INVALID_ARG
+    assert lib.ss_env_prefilter(ctypes.byref(ed), 1, None, None, None, None, None) == _lib.SS_ERR_INVALID_ARG
+    assert lib.ss_env_prefilter_noalloc(ctypes.byref(ed), 1, None, None, None, None) == _lib.SS_ERR_INVALID_ARG
