@@ -99,6 +99,9 @@ def lib():
                                  ctypes.c_double, ctypes.c_int, ctypes.c_int, i32p, i32p, dp, i64p,
                                  i64p, i32p, i32p, i32p]
     L.oref_fragments.restype = ctypes.c_longlong
+    L.oref_pixel_candidates.argtypes = [ctypes.c_int, dp, dp, dp, u8p, dp, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_double, ctypes.c_int, i32p, dp, dp, dp, dp]
+    L.oref_pixel_candidates.restype = ctypes.c_int
     return L
 
 
@@ -416,6 +419,104 @@ def fragments(rec: dict, rect: np.ndarray, W: int, H: int, prm: Params, pix=None
     return Fragments(fp, fs, fl, q, nl, mg, cnt)
 
 
+def decision_variants(rec: dict, rect: np.ndarray, W: int, prm: Params, pid: int, tol_cut: float,
+                      tol_gap: float, tol_box: float, max_variants: int = 512):
+    """Every outcome of the discrete decisions of pixel `pid` that sit within
+    rounding of flipping, as alternative fragment sets.
+
+    A surfel's coverage (Algorithm 1: inside the support rectangle and
+    rho2_mip < r_cut^2) is flippable when |rho2_mip - r_cut^2| / r_cut^2 <
+    tol_cut, or when the pixel centre is within tol_box px of the
+    rectangle's edge (inside or out).  For each choice of the flippable
+    coverages, the covering surfels are visited in (z_start, index) order
+    and grouped as Algorithm 1 groups them; a gap test z_start > z_max_end
+    with |z_start - z_max_end| / |z_max_end| < tol_gap (and not an exact tie)
+    is taken both ways; layers past the K_max-th are discarded.  Returns a
+    list of (sid [F], layer [F], n_layers) -- the variant without any flip
+    first -- and whether the enumeration was complete (at most max_variants)."""
+    T = np.ascontiguousarray(rec["T"].detach().numpy().reshape(-1, 9))
+    Sinv = rec["Sinv"].detach().numpy()
+    Sv = np.ascontiguousarray(np.stack([Sinv[:, 0, 0], Sinv[:, 0, 1], Sinv[:, 1, 1]], 1))
+    zse = np.ascontiguousarray(np.stack([rec["zs"].detach().numpy(), rec["ze"].detach().numpy()], 1))
+    valid = np.ascontiguousarray(rec["valid"].numpy().astype(np.uint8))
+    rect = np.ascontiguousarray(rect, np.float64)
+    near = max(tol_box, 1e-9)
+    cap = 256
+    while True:
+        idx = np.zeros(cap, np.int32)
+        r2, zs, ze, dist = (np.zeros(cap) for _ in range(4))
+        n = lib().oref_pixel_candidates(T.shape[0], _p(T, ctypes.c_double), _p(Sv, ctypes.c_double),
+                                        _p(zse, ctypes.c_double), _p(valid, ctypes.c_uint8),
+                                        _p(rect, ctypes.c_double), W, int(pid), near, cap,
+                                        _p(idx, ctypes.c_int32), _p(r2, ctypes.c_double), _p(zs, ctypes.c_double),
+                                        _p(ze, ctypes.c_double), _p(dist, ctypes.c_double))
+        if n <= cap:
+            break
+        cap = n
+    idx, r2, zs, ze, dist = idx[:n], r2[:n], zs[:n], ze[:n], dist[:n]
+    rc2 = prm.r_cut ** 2
+    # coverage = (inside the rectangle) and (rho2 < r^2); either part may be
+    # within rounding of flipping; a surfel is flippable when its two parts
+    # can give both outcomes
+    in_r, cut_ok = dist >= 0.0, r2 < rc2
+    f_r, f_c = np.abs(dist) < tol_box, np.abs(r2 - rc2) / rc2 < tol_cut
+    base = in_r & cut_ok
+    can_cover = (in_r | f_r) & (cut_ok | f_c)
+    can_miss = ~in_r | f_r | ~cut_ok | f_c
+    fl = np.where(can_cover & can_miss)[0]
+    out, complete = [], True
+    n_sets = 1 << len(fl)
+    if n_sets > max_variants:
+        n_sets, complete = max_variants, False
+    for m in range(n_sets):
+        cov = base.copy()
+        for b, j in enumerate(fl):
+            if (m >> b) & 1:
+                cov[j] = not cov[j]
+        order = sorted(np.where(cov)[0], key=lambda j: (zs[j], idx[j]))
+        # Algorithm 1 with near-tie gap tests taken both ways (depth-first)
+        stack = [(0, -1, 0.0, [])]
+        while stack:
+            f, layer, zmax, acc = stack.pop()
+            if f == len(order) or layer >= prm.k_max:
+                kept = [(a, l) for a, l in acc if l < prm.k_max]
+                nl = min(layer + 1, prm.k_max)
+                out.append((np.array([idx[a] for a, _ in kept], np.int32),
+                            np.array([l for _, l in kept], np.int32), nl))
+                if len(out) >= max_variants:
+                    return out, False
+                continue
+            j = order[f]
+            choices = []
+            if layer < 0:
+                choices = [True]
+            else:
+                gap = zs[j] > zmax
+                choices = [gap]
+                m_g = abs(zs[j] - zmax) / abs(zmax) if zmax != 0 else np.inf
+                if 0.0 < m_g < tol_gap:
+                    choices.append(not gap)
+            for new_layer in reversed(choices):
+                l2, z2 = (layer + 1, 0.0) if new_layer else (layer, zmax)
+                if l2 >= prm.k_max:
+                    stack.append((len(order), l2, z2, acc))
+                    continue
+                stack.append((f + 1, l2, max(z2, ze[j]), acc + [(j, l2)]))
+    return out, complete
+
+
+def composite_variant(rec: dict, W: int, prm: Params, pid: int, sid: np.ndarray, layer: np.ndarray,
+                      n_layers: int):
+    """Composite one pixel from a given fragment set (see decision_variants):
+    returns its 13 values (rgba, then the 9 AOV channels) in FP64."""
+    fr = Fragments(np.full(sid.shape[0], pid, np.int32), sid.astype(np.int32), layer.astype(np.int32),
+                   np.array([pid], np.int32), np.array([n_layers], np.int32), np.zeros((1, 3)),
+                   np.array([sid.shape[0]], np.int64))
+    with torch.no_grad():
+        rgba, aov = composite(rec, fr, W, prm)
+    return torch.cat([rgba, aov], 1)[0].numpy()
+
+
 def composite(rec: dict, fr: Fragments, W: int, prm: Params, per_frag: dict | None = None):
     """Layer sums, Shepard normalisation, coverage opacity and compositing
     for the queried pixels.  Returns (rgba [P,4], aov [P,9]) as FP64
@@ -584,7 +685,9 @@ def render_view(surf, cam, env: EnvState, prm: Params = Params(), pix=None, G=No
         mg_parts.append(fr.margin)
     out = dict(rgba=np.concatenate(rgba_parts), aov=np.concatenate(aov_parts),
                n_layers=np.concatenate(nl_parts), margin=np.concatenate(mg_parts), rect=rect,
-               valid=rec["valid"].numpy(), lookup_margin=lookup_margins(S, cd, env.shape, prm))
+               valid=rec["valid"].numpy(), lookup_margin=lookup_margins(S, cd, env.shape, prm),
+               records={k: leaf[k].detach() for k in ("T", "Sinv", "n_f", "ch", "zs", "ze", "valid")},
+               width=W)
     if need_grad:
         tens = [rec[k] for k in ("T", "Sinv", "n_f", "ch")]
         grads = [leaf[k].grad if leaf[k].grad is not None else torch.zeros_like(leaf[k]) for k in

@@ -360,6 +360,11 @@ typedef struct {
     int idx;
 } frag_t;
 
+/* Pixels outside a support rectangle by less than this (px) still count
+ * toward the rectangle margin (a covering surfel there is a decision within
+ * rounding of flipping). */
+#define RECT_NEAR 0.01
+
 static int frag_cmp(const void* a, const void* b) {
     const frag_t* x = (const frag_t*)a;
     const frag_t* y = (const frag_t*)b;
@@ -398,10 +403,13 @@ long long oref_fragments(int N, const double* T /* [N][9] */, const double* Sinv
                          int64_t* frag_count /* [P] */, const int64_t* frag_offset /* [P] */,
                          int32_t* frag_pix, int32_t* frag_sid, int32_t* frag_layer) {
     int P = pix ? npix : W * H;
-    /* integer pixel ranges whose centres lie in each rectangle */
+    /* integer pixel ranges whose centres lie in each rectangle widened by
+     * RECT_NEAR px (the pixels outside the rectangle proper only enter the
+     * rectangle margin) */
     int32_t* bbox = (int32_t*)malloc(sizeof(int32_t) * 4 * (size_t)(N > 0 ? N : 1));
     for (int i = 0; i < N; ++i) {
-        double lo[2] = {rect[i * 4 + 0], rect[i * 4 + 2]}, hi[2] = {rect[i * 4 + 1], rect[i * 4 + 3]};
+        double lo[2] = {rect[i * 4 + 0] - RECT_NEAR, rect[i * 4 + 2] - RECT_NEAR},
+               hi[2] = {rect[i * 4 + 1] + RECT_NEAR, rect[i * 4 + 3] + RECT_NEAR};
         int lim[2] = {W, H};
         for (int a = 0; a < 2; ++a) {
             double i0 = ceil(lo[a] - 0.5), i1 = floor(hi[a] - 0.5);
@@ -444,14 +452,17 @@ long long oref_fragments(int N, const double* T /* [N][9] */, const double* Sinv
                 if (px < bbox[i * 4 + 0] || px > bbox[i * 4 + 1]) continue;
                 double rho2;
                 if (!hit_rho2(T + (size_t)i * 9, Sinv + (size_t)i * 3, x, y, &rho2)) continue;
+                const double* R = rect + (size_t)i * 4;
+                /* signed distance of the pixel centre from the rectangle's edge (< 0 outside) */
+                double d = fmin(fmin(x - R[0], R[1] - x), fmin(y - R[2], R[3] - y));
+                if (!(d >= 0.0)) {   /* outside: a candidate only within rounding of the edge */
+                    if (rho2 < rcut2 && -d < m_box) m_box = -d;
+                    continue;
+                }
                 double m = fabs(rho2 - rcut2) / rcut2;
                 if (m < m_cut) m_cut = m;
                 if (!(rho2 < rcut2)) continue;
-                {
-                    const double* R = rect + (size_t)i * 4;
-                    double d = fmin(fmin(x - R[0], R[1] - x), fmin(y - R[2], R[3] - y));
-                    if (d < m_box) m_box = d;
-                }
+                if (d < m_box) m_box = d;
                 if (nf == capf) {
                     capf *= 2;
                     fr = (frag_t*)realloc(fr, sizeof(frag_t) * capf);
@@ -501,4 +512,38 @@ long long oref_fragments(int N, const double* T /* [N][9] */, const double* Sinv
     free(row_list);
     free(bbox);
     return total;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Every surfel that may take part in the decisions of pixel `pid`: those
+ * whose support rectangle, widened by `near` px, contains the pixel centre
+ * and whose plane is hit in front of the camera.  For each: its index, rho2_mip
+ * at the pixel centre, its depth interval and the signed distance (px) of the
+ * pixel centre from the rectangle's edge (negative outside).  Fills at most
+ * `cap` entries; returns how many there are (call again with a larger cap if
+ * the return value exceeds it).  Tests use it to enumerate the outcomes of
+ * decisions that sit within rounding of flipping. */
+int oref_pixel_candidates(int N, const double* T, const double* Sinv, const double* zse, const uint8_t* valid,
+                          const double* rect, int W, int pid, double near, int cap, int32_t* idx,
+                          double* rho2_out, double* zs_out, double* ze_out, double* dist_out) {
+    int px = pid % W, py = pid / W;
+    double x = px + 0.5, y = py + 0.5;
+    int n = 0;
+    for (int i = 0; i < N; ++i) {
+        if (!valid[i]) continue;
+        const double* R = rect + (size_t)i * 4;
+        double d = fmin(fmin(x - R[0], R[1] - x), fmin(y - R[2], R[3] - y));
+        if (!(d > -near)) continue;
+        double rho2;
+        if (!hit_rho2(T + (size_t)i * 9, Sinv + (size_t)i * 3, x, y, &rho2)) continue;
+        if (n < cap) {
+            idx[n] = i;
+            rho2_out[n] = rho2;
+            zs_out[n] = zse[i * 2 + 0];
+            ze_out[n] = zse[i * 2 + 1];
+            dist_out[n] = d;
+        }
+        n++;
+    }
+    return n;
 }

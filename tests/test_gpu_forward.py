@@ -33,7 +33,10 @@ def _check_view(r, scene, v, pix=None, env_cache=None):
     n_bad, msg = _parity.compare(gpu, refv, amb, f"view {v}")
     assert amb.mean() < _parity.MAX_AMBIGUOUS_FRACTION, f"too many ambiguous pixels: {amb.sum()}"
     assert n_bad == 0, msg
-    _parity.check_ambiguous(gpu, refv, amb)
+    n_amb, n_flip = _parity.check_variants(gpu, ref, amb, pix=pix, prm=r.prm)
+    print(f"view {v}: {n_amb} of {amb.size} pixels with a decision within rounding (fraction {amb.mean():.2e}), "
+          f"each matched an outcome at the strict tolerance; the GPU took the other outcome at {n_flip}")
+    _parity.check_flip_fraction(n_flip, amb.size, f"view {v}")
     return ref, gpu
 
 
@@ -188,17 +191,20 @@ def test_forward_multi_scene_uneven():
 
 
 @pytest.mark.slow
-def test_forward_displaced_sphere_1m_sampled():
-    """Full-size headline workload (1M surfels, 16 views of 800^2), sampled
-    pixels of two views checked one by one against the oracle."""
+def test_forward_displaced_sphere_1m():
+    """Full-size headline workload (1M surfels, 16 views of 800^2, rendered in
+    one batch as bench.py times it): every pixel of view 0 and sampled
+    pixels of view 9 against the oracle, element by element; pixels with a
+    decision within rounding match one of its outcomes, and the GPU takes
+    the other outcome at no more than 1e-4 of the pixels."""
     sc = S.displaced_sphere_1m()
     r = _renderer(sc)
     r.forward()
     assert r.read_status() == 0
     rng = np.random.default_rng(0)
     cache = {}
-    for v in (0, 9):
-        gpu = _gpu_view(r, v)
-        cov = np.where(gpu[:, 3] > 0)[0]
-        pix = np.sort(np.concatenate([rng.choice(cov, 600, replace=False), rng.choice(640000, 200, replace=False)]))
-        _check_view(r, sc, v, pix=pix, env_cache=cache)
+    _check_view(r, sc, 0, env_cache=cache)
+    gpu = _gpu_view(r, 9)
+    cov = np.where(gpu[:, 3] > 0)[0]
+    pix = np.sort(np.concatenate([rng.choice(cov, 600, replace=False), rng.choice(640000, 200, replace=False)]))
+    _check_view(r, sc, 9, pix=np.unique(pix), env_cache=cache)
