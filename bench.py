@@ -33,7 +33,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "fwd+bwd views/s at 1M surfels 16x800² (batched vs per-view); % HBM roofline"
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 # algorithmic FP32 work per unit (counted from the kernels' arithmetic):
 FLOP_TEST = 17        # one (pixel, surfel) test inside the support rectangle
@@ -44,6 +43,37 @@ FLOP_FRAG_FWD = 30    # one covering fragment: weight + 12-channel accumulation
 # s0, s1, s2 9, to P, A2, B2 6, to the centre 10; then the 21 values added
 # into their surfel's sums 21
 FLOP_FRAG_BWD = 109
+
+
+# Bytes the method must move (the algorithmic floor, not what the kernels
+# move), per unit of work: N surfels, V views, M (tile, surfel) instances of
+# the batch, P pixels.
+B_PARAMS = 64          # per surfel, once per batch: c 3, q 4, log s 2, albedo 3, r, m, 2 pad (FP32)
+B_RECORD = 80          # per (surfel, view): T rows 9, Sigma^-1 3, n_f, z interval 2, RGB 3, rectangle 2
+B_SORT = 24            # per instance: key written by the binning, read and written by the sort
+B_RASTER = 76          # per instance, forward and again backward: id + the record fields the test reads
+B_PIXEL_FWD = 24       # per pixel: RGBA out + per-pixel state
+B_PIXEL_BWD = 24       # per pixel: dL/dRGBA + state in
+B_SCATTER = 64         # per instance: the per-surfel gradient sums added once per (tile, surfel)
+B_GRAD_REC = 64 + 80   # per (surfel, view): gradient record + record re-read by the projection adjoint
+B_PARAM_GRAD = 128     # per surfel, once per batch: parameter gradients read and written
+
+
+def algorithmic_bytes(N: int, V: int, M: int, P: int, env_floats: int, per_view: bool = False) -> dict:
+    """Algorithmic HBM bytes of one step (all views, forward and backward),
+    stage by stage.  In the per-view form the parameters are read, and their
+    gradients read and written, once per view instead of once per batch."""
+    reps = V if per_view else 1
+    b = {"params": B_PARAMS * N * reps,
+         "records": B_RECORD * N * V,
+         "bin_sort": B_SORT * M,
+         "raster_fwd": B_RASTER * M + B_PIXEL_FWD * P,
+         "raster_bwd": B_RASTER * M + B_PIXEL_BWD * P,
+         "gradient_scatter": B_SCATTER * M,
+         "project_bwd": B_GRAD_REC * N * V + B_PARAM_GRAD * N * reps,
+         "env": 4 * 4 * env_floats}       # prefilter and adjoint: maps read and written once each
+    b["total"] = sum(b.values())
+    return b
 
 
 def parse():
@@ -58,7 +88,6 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
-    ap.add_argument("--cpu-rows", type=int, default=16, help="rows of view 0 in the oracle sample")
     return ap.parse_args()
 
 
@@ -155,22 +184,25 @@ def measured_peaks():
 
 
 # the sources the rasteriser kernels are built from (their recorded DRAM
-# traffic stays valid while these are unchanged)
+# traffic stays valid while these are unchanged); the whole step's traffic
+# depends on every source
 RASTER_SOURCES = ("raster_common.cuh", "render_bwd.cu", "render_fwd.cu", "ss3d_internal.cuh")
+STEP_SOURCES = ("api.cu", "env.cu", "optim.cu", "raster_common.cuh", "render_bwd.cu", "render_fwd.cu",
+                "ss3d_internal.cuh")
 
 
-def source_hash() -> str:
+def source_hash(sources=RASTER_SOURCES) -> str:
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2605_05876_gb300", "csrc")
-    for f in RASTER_SOURCES:
+    for f in sources:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
 
 
-def recorded_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+def recorded_traffic(kernel: str, workload: str, sources=RASTER_SOURCES):
+    """DRAM bytes per launch (or per step, kernel "step") from the committed
+    ncu summary, if it was taken on the current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         with open(path) as fh:
@@ -178,7 +210,7 @@ def recorded_traffic(kernel: str, workload: str):
                 if line.startswith("#") or not line.strip():
                     continue
                 f = line.split()
-                if len(f) >= 4 and f[0] == kernel and f[1] == workload and f[3] == source_hash():
+                if len(f) >= 4 and f[0] == kernel and f[1] == workload and f[3] == source_hash(sources):
                     return float(f[2])
     except OSError:
         pass
@@ -195,29 +227,130 @@ def describe(scene, name: str) -> str:
             + "/".join(f"{w}x{h}" for w, h in sizes) + f", env {We}x{He}")
 
 
-def cpu_baseline(scene, rows: int, grad: bool = True):
-    """The FP64 oracle as it stands, on a bounded sample of the workload: the
-    pixel rows of view 0 through the image centre, forward and backward,
-    including the environment prefilter and the per-surfel records."""
-    import numpy as np
-    import torch
+ORACLE_CHUNK = 1 << 16   # pixels per decision call of the oracle (render_pixels' chunk)
+
+
+class OracleTimer:
+    """The FP64 oracle as it stands, timed on the host cores phase by phase
+    on a bounded sample of a workload, and its cost per step extrapolated:
+    per step the environment prefilter and, for the gradient, its transpose
+    once; per view the records of all surfels and their adjoint; per pixel
+    the decisions, values and back-propagation of a pixel sample.  The
+    per-pixel cost is fitted from two sample sizes (a per-call part plus a
+    part per pixel), so only that part is scaled to the view's pixels."""
+
+    def __init__(self, scene, grad: bool = True):
+        import torch
+        from oracle import model as M
+        self.M, self.torch = M, torch
+        self.threads = os.cpu_count() or 1
+        torch.set_num_threads(self.threads)
+        self.scene, self.grad = scene, grad
+        self.prm = M.Params()
+        self.cam = scene.cameras[0]
+        self.W, self.H = self.cam.width, self.cam.height
+        self.V = len(scene.cameras)
+        self.P = sum(c.width * c.height for c in scene.cameras) / self.V     # mean pixels per view
+        t0 = time.perf_counter()
+        self.env = M.prepare_env(scene.envs[0], self.prm)
+        self.t_env = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        self.vs = M.prepare_view(scene.surfels, self.cam, self.env, self.prm, need_grad=grad)
+        self.t_view = time.perf_counter() - t0
+        self.samples = []     # (pixels, seconds)
+        self.next_row = 0
+
+    def pixel_step(self, rows=(2, 8)) -> float:
+        """One timed step: two row samples of view 0, forward (+ backward).
+        Returns the step's seconds."""
+        t_all = 0.0
+        rng = np.random.default_rng(len(self.samples))
+        for nr in rows:
+            r0 = (self.H // 2 - 8 + self.next_row) % max(1, self.H - nr)
+            self.next_row += nr
+            pix = np.arange(r0 * self.W, (r0 + nr) * self.W, dtype=np.int32)
+            G = rng.normal(size=(pix.size, 13)) if self.grad else None
+            t0 = time.perf_counter()
+            self.M.render_pixels(self.vs, pix, G)
+            dt = time.perf_counter() - t0
+            self.samples.append((pix.size, dt))
+            t_all += dt
+        return t_all
+
+    def finish(self):
+        """Per-view adjoint of the records and the per-step env adjoint (timed once)."""
+        self.t_chain = self.t_adj = 0.0
+        if self.grad:
+            t0 = time.perf_counter()
+            _, d_irr, d_lv = self.M.chain_records(self.vs)
+            self.t_chain = time.perf_counter() - t0
+            He, We, _ = self.env.shape
+            t0 = time.perf_counter()
+            self.M.env_adjoint(d_irr, d_lv, We, He)
+            self.t_adj = time.perf_counter() - t0
+
+    def estimate(self) -> dict:
+        n = np.array([p for p, _ in self.samples], np.float64)
+        t = np.array([d for _, d in self.samples], np.float64)
+        A = np.stack([np.ones_like(n), n], 1)
+        (a, b), *_ = np.linalg.lstsq(A, t, rcond=None)
+        a, b = max(a, 0.0), max(b, 0.0)
+        t_pixels = math.ceil(self.P / ORACLE_CHUNK) * a + self.P * b
+        per_view = self.t_view + self.t_chain + t_pixels
+        per_step = self.t_env + self.t_adj + self.V * per_view
+        return {"views_per_s": self.V / per_step, "s_per_step": per_step, "s_per_view": per_view,
+                "env_prefilter_s": self.t_env, "env_adjoint_s": self.t_adj, "records_s": self.t_view,
+                "records_adjoint_s": self.t_chain, "pixel_s": b, "pixel_call_s": a,
+                "pixels_per_view": self.P, "sampled_pixels": int(n.sum())}
+
+    def describe(self, est) -> str:
+        return (f"oracle phases timed on view 0 of the same workload: env prefilter {est['env_prefilter_s']:.1f} s "
+                f"and its adjoint {est['env_adjoint_s']:.1f} s once per step; records of all "
+                f"{self.scene.surfels.n:,} surfels {est['records_s']:.1f} s and their adjoint "
+                f"{est['records_adjoint_s']:.1f} s per view; {est['sampled_pixels']} sampled pixels (row samples of "
+                f"2 and 8 rows) fitted to {est['pixel_call_s']:.2f} s per call + {1e6 * est['pixel_s']:.1f} us per "
+                f"pixel, scaled to {est['pixels_per_view']:.0f} px per view; "
+                f"{'forward+backward' if self.grad else 'forward'}; {est['s_per_step']:.0f} s per step of {self.V} views")
+
+
+def oracle_full_views():
+    """The oracle on whole views of the two small workloads (the 4096-surfel
+    sphere at 128^2 and the 100k-surfel torus + sphere at 512^2): seconds per
+    view, forward and forward+backward, env prefilter included."""
     from oracle import model as M
-    threads = os.cpu_count() or 1
-    torch.set_num_threads(threads)
-    prm = M.Params()
-    cam = scene.cameras[0]
-    W, H = cam.width, cam.height
-    r0 = H // 2 - rows // 2
-    pix = np.arange(r0 * W, (r0 + rows) * W, dtype=np.int32)
-    G = np.random.default_rng(0).normal(size=(pix.size, 13)) if grad else None
-    t0 = time.perf_counter()
-    env = M.prepare_env(scene.envs[0], prm)
-    M.render_view(scene.surfels, cam, env, prm, pix=pix, G=G)
-    dt = time.perf_counter() - t0
-    frac = pix.size / float(W * H)
-    return {"value": frac / dt, "unit": "views/s", "cores": threads, "kind": "oracle",
-            "sample": f"view 0 of the same workload, rows {r0}-{r0 + rows - 1} ({pix.size} px = {frac:.4f} view), "
-                      f"forward+backward incl. env prefilter and 1M per-surfel records, {dt:.1f} s"}
+    from paper_2605_05876_gb300 import scenes
+    out = {}
+    for name, modes in (("sphere_4k", ("fwd", "fwd_bwd")), ("torus_sphere_100k", ("fwd_bwd",))):
+        sc = getattr(scenes, name)()
+        prm = M.Params()
+        cam = sc.cameras[0]
+        t0 = time.perf_counter()
+        env = M.prepare_env(sc.envs[0], prm)
+        t_env = time.perf_counter() - t0
+        row = {"env_prefilter_s": t_env}
+        for mode in modes:
+            G = np.random.default_rng(0).normal(size=(cam.width * cam.height, 13)) if mode == "fwd_bwd" else None
+            t0 = time.perf_counter()
+            M.render_view(sc.surfels, cam, env, prm, G=G)
+            row[f"{mode}_s"] = time.perf_counter() - t0
+            row[f"{mode}_views_per_s"] = 1.0 / (row[f"{mode}_s"] + t_env)
+        out[name] = row
+    return out
+
+
+def cpu_baseline(scene, full_views: bool = True):
+    """The oracle's views/s on this workload from one phase-split sample
+    (about 45 s of host work), plus whole views of the small workloads."""
+    import numpy as np   # noqa: F401
+    ot = OracleTimer(scene)
+    ot.pixel_step()
+    ot.finish()
+    est = ot.estimate()
+    res = {"value": est["views_per_s"], "unit": "views/s", "cores": ot.threads, "kind": "oracle",
+           "sample": ot.describe(est), "phases": est}
+    if full_views:
+        res["full_views"] = oracle_full_views()
+    return res
 
 
 # ---------------------------------------------------------------------------
@@ -225,26 +358,34 @@ def cpu_baseline(scene, rows: int, grad: bool = True):
 
 
 def run_reference(args):
+    """Each timed step is one bounded sample of the workload through the
+    oracle (two row samples of view 0, forward and backward); the per-view
+    and per-step fixed phases are timed once around the steps, and the
+    line's value is the oracle's views/s extrapolated from all of them
+    (OracleTimer).  ms_per_step is the measured time of the timed steps."""
     rank, world, _ = dist_env()
     if world > 1 and rank != 0:
         return
     from paper_2605_05876_gb300 import scenes
     scene = scenes.by_name(args.config)
-    times, last = [], None
-    for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(scene, args.cpu_rows)
-        if i >= args.warmup:
-            times.append(cb)
-        last = cb
-    v = sum(c["value"] for c in times) / len(times)
-    ms = 1000.0 * 16 / v if v > 0 else None
+    ot = OracleTimer(scene)
+    for _ in range(args.warmup):
+        ot.pixel_step()
+    ot.samples.clear()
+    t_steps = [ot.pixel_step() for _ in range(args.steps)]
+    ot.finish()
+    est = ot.estimate()
+    v = est["views_per_s"]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "views/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sum(t_steps) / len(t_steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": describe(scene, args.config),
-                       "inputs_vs_l2": "host memory"},
-            "cpu_baseline": {"value": v, "unit": "views/s", "cores": last["cores"], "kind": "oracle",
-                             "sample": last["sample"]},
+                       "inputs_vs_l2": "host memory",
+                       "step": "one timed step = the oracle on two row samples of view 0 (2 and 8 rows of "
+                               f"{ot.W} px), forward and backward; value = the oracle's views/s extrapolated "
+                               "from those and the once-timed fixed phases"},
+            "cpu_baseline": {"value": v, "unit": "views/s", "cores": ot.threads, "kind": "oracle",
+                             "sample": ot.describe(est), "phases": est},
             "e2e": {"value": v, "unit": "views/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -410,7 +551,8 @@ def run_ours(args):
     # --- roofline of the dominant kernel (FP32-issue bound: no memory or tensor-core limit applies)
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12     # TFLOP/s
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12     # TFLOP/s
     dom = max(("raster_fwd", "raster_bwd"), key=lambda s: stages[s][0])
     t_launch = stages[dom][0] / max(stages[dom][1], 1) / 1000.0
     if dom == "raster_fwd":
@@ -421,17 +563,34 @@ def run_ours(args):
     workload = f"{args.config}_{V}x800"
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": recorded_traffic(dom, workload),
-                "peak_note": f"FP32 FMA issue: {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz "
-                             "(max SM clock of measured)",
+                "peak_note": f"FP32 FMA issue: {sm_count} SMs (device) x {FP32_LANES_PER_SM} lanes x 2 x "
+                             f"{sm_max:.0f} MHz (max SM clock of measured)",
                 "algorithmic_flops_per_launch": flops, "launch_ms": t_launch * 1000.0}
     hbm = float(peaks.get("hbm_gbs", 6694.5))
+    # --- the metric's HBM roofline: algorithmic bytes of the step over its time
+    env_floats = int(r.env.numel() + r.irr.numel() + r.spec.numel())
+    alg = algorithmic_bytes(r.n_surfels, V, counts["instances"], P, env_floats)
+    step_workload = f"{args.config}_{V}x800"
+    dram_step = recorded_traffic("step", step_workload, STEP_SOURCES)
+    hbm_line = {"peak_gbs": hbm, "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_step": alg["total"], "algorithmic_by_stage": alg,
+                "achieved_algorithmic_gbs": alg["total"] / (ms_per_step / 1000.0) / 1e9,
+                "frac": alg["total"] / (ms_per_step / 1000.0) / 1e9 / hbm,
+                "dram_bytes_per_step": dram_step,
+                "dram_frac": (dram_step / (ms_per_step / 1000.0) / 1e9 / hbm) if dram_step else None}
+    if per_view is not None:
+        alg_pv = algorithmic_bytes(r.n_surfels, V, counts["instances"], P, env_floats, per_view=True)
+        t_pv = per_view["ms_per_step"] / 1000.0
+        hbm_line["per_view_form"] = {"algorithmic_bytes_per_step": alg_pv["total"],
+                                     "achieved_algorithmic_gbs": alg_pv["total"] / t_pv / 1e9,
+                                     "frac": alg_pv["total"] / t_pv / 1e9 / hbm}
     total_stage_ms = sum(v[0] for v in stages.values())
     stage_share = {k: {"ms_per_step": v[0] / args.steps, "share": v[0] / total_stage_ms if total_stage_ms else 0}
                    for k, v in stages.items()}
 
     cpu = None
-    if not args.no_cpu and rank == 0:
-        cpu = cpu_baseline(scene, args.cpu_rows)
+    if not args.no_cpu and rank == 0 and world == 1:
+        cpu = cpu_baseline(scene)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "views/s", "n_gpus": world, "steps": args.steps,
@@ -441,7 +600,8 @@ def run_ours(args):
                            "inputs_vs_l2": "inputs and intermediates > 129 MB L2 (no flush)",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "launch_shapes": tuned or "defaults"},
-                "per_view": per_view, "graph": graph, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
+                "per_view": per_view, "graph": graph, "e2e": e2e, "roofline": roofline, "hbm": hbm_line,
+                "cpu_baseline": cpu,
                 "clocks": clocks,
                 "gpu_launches": None, "stages": stage_share, "work": counts, "hbm_peak_gbs": hbm,
                 "device_status": status}

@@ -648,6 +648,85 @@ def prepare_env(env: np.ndarray, prm: Params, lut_nq: int = 128) -> EnvState:
     return EnvState(irr, levels, brdf_lut(prm.lut_n, lut_nq), env32.shape)
 
 
+@dataclasses.dataclass
+class ViewState:
+    """One view between the phases of render_view: the per-surfel records
+    (differentiable), their support rectangles and the leaves the per-pixel
+    part differentiates into."""
+    S: dict
+    cd: dict
+    irr: torch.Tensor
+    levels: list
+    rec: dict
+    rect: np.ndarray
+    leaf: dict
+    need_grad: bool
+    env: EnvState
+    prm: Params
+
+
+def prepare_view(surf, cam, env: EnvState, prm: Params = Params(), need_grad: bool = False) -> ViewState:
+    """Per-view part of render_view that does not depend on the pixels:
+    the records of every surfel and their support rectangles."""
+    S = to_torch_surfels(surf, requires_grad=need_grad)
+    cd = cam_dict(cam)
+    irr = torch.from_numpy(env.irr.copy()).requires_grad_(need_grad)
+    levels = [torch.from_numpy(l.copy()).requires_grad_(need_grad) for l in env.levels]
+    lut = torch.from_numpy(env.lut.copy())
+    with torch.set_grad_enabled(need_grad):
+        rec = records(S, cd, irr, levels, lut, prm)
+    rect = support_rect(rec, prm)
+    # leaves for the per-pixel part, so pixel chunks can be back-propagated one at a time
+    leaf = {k: rec[k].detach().clone().requires_grad_(need_grad) for k in ("T", "Sinv", "n_f", "ch")}
+    leaf.update(zs=rec["zs"].detach(), ze=rec["ze"].detach(), valid=rec["valid"])
+    return ViewState(S, cd, irr, levels, rec, rect, leaf, need_grad, env, prm)
+
+
+def render_pixels(vs: ViewState, q_all: np.ndarray, G=None, chunk: int = 1 << 16) -> dict:
+    """Per-pixel part of render_view for the pixel ids q_all: decisions,
+    values and (G given) the back-propagation of sum(G * [rgba, aov]) into
+    the view's leaves."""
+    W, H = vs.cd["width"], vs.cd["height"]
+    rgba_parts, aov_parts, nl_parts, mg_parts = [], [], [], []
+    for c0 in range(0, q_all.shape[0], chunk):
+        q = q_all[c0:c0 + chunk]
+        fr = fragments(vs.leaf, vs.rect, W, H, vs.prm, pix=q)
+        with torch.set_grad_enabled(vs.need_grad):
+            rgba, aov = composite(vs.leaf, fr, W, vs.prm)
+            if vs.need_grad and G is not None:
+                Gc = torch.from_numpy(np.asarray(G[c0:c0 + chunk], np.float64))
+                (torch.cat([rgba, aov], 1) * Gc).sum().backward()
+        rgba_parts.append(rgba.detach().numpy())
+        aov_parts.append(aov.detach().numpy())
+        nl_parts.append(fr.n_layers)
+        mg_parts.append(fr.margin)
+    return dict(rgba=np.concatenate(rgba_parts), aov=np.concatenate(aov_parts),
+                n_layers=np.concatenate(nl_parts), margin=np.concatenate(mg_parts))
+
+
+def chain_records(vs: ViewState):
+    """The gradients accumulated in the view's leaves chained back through
+    the records: returns (surfel parameter gradients, d_irr, d_levels)."""
+    tens = [vs.rec[k] for k in ("T", "Sinv", "n_f", "ch")]
+    grads = [vs.leaf[k].grad if vs.leaf[k].grad is not None else torch.zeros_like(vs.leaf[k]) for k in
+             ("T", "Sinv", "n_f", "ch")]
+    torch.autograd.backward(tens, grads)
+    out = {k: (v.grad.numpy() if v.grad is not None else np.zeros(v.shape)) for k, v in vs.S.items()}
+    d_irr = vs.irr.grad.numpy() if vs.irr.grad is not None else np.zeros(vs.irr.shape)
+    d_lv = [lv.grad.numpy() if lv.grad is not None else np.zeros(lv.shape) for lv in vs.levels]
+    return out, d_irr, d_lv
+
+
+def finish_view(vs: ViewState) -> dict:
+    """Per-view part of render_view after the pixels: chain_records, then the
+    prefiltered-map gradients through the prefilter's transpose to the base
+    env."""
+    out, d_irr, d_lv = chain_records(vs)
+    He, We, _ = vs.env.shape
+    out["env"] = env_adjoint(d_irr, d_lv, We, He)
+    return out
+
+
 def render_view(surf, cam, env: EnvState, prm: Params = Params(), pix=None, G=None,
                 chunk: int = 1 << 16):
     """Render one view (all pixels, or the pixel ids in `pix`).
@@ -657,47 +736,15 @@ def render_view(surf, cam, env: EnvState, prm: Params = Params(), pix=None, G=No
     sum(G * [rgba, aov]) w.r.t. the surfel parameters and the base env.
     """
     need_grad = G is not None
-    S = to_torch_surfels(surf, requires_grad=need_grad)
-    cd = cam_dict(cam)
-    irr = torch.from_numpy(env.irr.copy()).requires_grad_(need_grad)
-    levels = [torch.from_numpy(l.copy()).requires_grad_(need_grad) for l in env.levels]
-    lut = torch.from_numpy(env.lut.copy())
-    W, H = cd["width"], cd["height"]
-    with torch.set_grad_enabled(need_grad):
-        rec = records(S, cd, irr, levels, lut, prm)
-    rect = support_rect(rec, prm)
+    vs = prepare_view(surf, cam, env, prm, need_grad)
+    W, H = vs.cd["width"], vs.cd["height"]
     q_all = np.arange(W * H, dtype=np.int32) if pix is None else np.asarray(pix, np.int32)
-    # leaves for the per-pixel part, so pixel chunks can be back-propagated one at a time
-    leaf = {k: rec[k].detach().clone().requires_grad_(need_grad) for k in ("T", "Sinv", "n_f", "ch")}
-    leaf.update(zs=rec["zs"].detach(), ze=rec["ze"].detach(), valid=rec["valid"])
-    rgba_parts, aov_parts, nl_parts, mg_parts = [], [], [], []
-    for c0 in range(0, q_all.shape[0], chunk):
-        q = q_all[c0:c0 + chunk]
-        fr = fragments(leaf, rect, W, H, prm, pix=q)
-        with torch.set_grad_enabled(need_grad):
-            rgba, aov = composite(leaf, fr, W, prm)
-            if need_grad:
-                Gc = torch.from_numpy(np.asarray(G[c0:c0 + chunk], np.float64))
-                (torch.cat([rgba, aov], 1) * Gc).sum().backward()
-        rgba_parts.append(rgba.detach().numpy())
-        aov_parts.append(aov.detach().numpy())
-        nl_parts.append(fr.n_layers)
-        mg_parts.append(fr.margin)
-    out = dict(rgba=np.concatenate(rgba_parts), aov=np.concatenate(aov_parts),
-               n_layers=np.concatenate(nl_parts), margin=np.concatenate(mg_parts), rect=rect,
-               valid=rec["valid"].numpy(), lookup_margin=lookup_margins(S, cd, env.shape, prm),
-               records={k: leaf[k].detach() for k in ("T", "Sinv", "n_f", "ch", "zs", "ze", "valid")},
+    out = render_pixels(vs, q_all, G, chunk)
+    out.update(rect=vs.rect, valid=vs.rec["valid"].numpy(), lookup_margin=lookup_margins(vs.S, vs.cd, env.shape, prm),
+               records={k: vs.leaf[k].detach() for k in ("T", "Sinv", "n_f", "ch", "zs", "ze", "valid")},
                width=W)
     if need_grad:
-        tens = [rec[k] for k in ("T", "Sinv", "n_f", "ch")]
-        grads = [leaf[k].grad if leaf[k].grad is not None else torch.zeros_like(leaf[k]) for k in
-                 ("T", "Sinv", "n_f", "ch")]
-        torch.autograd.backward(tens, grads)
-        out["grad"] = {k: (v.grad.numpy() if v.grad is not None else np.zeros(v.shape)) for k, v in S.items()}
-        d_irr = irr.grad.numpy() if irr.grad is not None else np.zeros(irr.shape)
-        d_lv = [lv.grad.numpy() if lv.grad is not None else np.zeros(lv.shape) for lv in levels]
-        He, We, _ = env.shape
-        out["grad"]["env"] = env_adjoint(d_irr, d_lv, We, He)
+        out["grad"] = finish_view(vs)
     return out
 
 

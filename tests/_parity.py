@@ -45,9 +45,28 @@ MAX_AMBIGUOUS_FRACTION = 1e-2
 MAX_FLIP_FRACTION = 1e-4
 
 
+# columns of the composited normal in a [.., 13] row (rgba, then the AOVs:
+# albedo 3, roughness, metallic, normal 3, depth)
+NORMAL_COLS = slice(9, 12)
+
+
+def scale_of(r):
+    """The magnitude each value's tolerance is relative to: the value itself,
+    except the normal AOV, which is a direction (renormalised per layer,
+    Sec. 4.2.3): its components are sums of unit-length terms that cancel, so
+    its FP32 rounding scales with the composited normal's length, and all
+    three components are measured against that length."""
+    sc = np.abs(r).astype(np.float64, copy=True)
+    if r.shape[-1] == 13:
+        sc[..., NORMAL_COLS] = np.linalg.norm(r[..., NORMAL_COLS], axis=-1, keepdims=True)
+    return sc
+
+
 def within(g, r):
-    """Element-wise image tolerance: 1e-4 relative, 1e-5 absolute below 1e-2."""
-    return np.abs(g - r) <= np.where(np.abs(r) < SMALL, ATOL, RTOL * np.abs(r))
+    """Image tolerance: 1e-4 relative, 1e-5 absolute where the magnitude
+    (scale_of) is below 1e-2."""
+    sc = scale_of(r)
+    return np.abs(g - r) <= np.where(sc < SMALL, ATOL, RTOL * sc)
 
 
 def check_variants(gpu, ref, amb, pix=None, prm=None):
