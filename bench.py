@@ -29,6 +29,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -341,7 +343,6 @@ def oracle_full_views():
 def cpu_baseline(scene, full_views: bool = True):
     """The oracle's views/s on this workload from one phase-split sample
     (about 45 s of host work), plus whole views of the small workloads."""
-    import numpy as np   # noqa: F401
     ot = OracleTimer(scene)
     ot.pixel_step()
     ot.finish()
