@@ -90,6 +90,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--no-screen-grad", action="store_true", help="skip timing the densification statistic")
     return ap.parse_args()
 
 
@@ -525,6 +526,27 @@ def run_ours(args):
                     "ms_per_step": ms_pv / args.steps}
         del singles
 
+    # --- the same step with the densification statistic (Eq. ss_grad) accumulated
+    screen_grad = None
+    if not args.no_screen_grad:
+        rs = Renderer(scene, share_from=r, screen_grad=True)
+        for k in ("fwd_warps", "bwd_warps", "pbwd_block"):
+            setattr(rs.prm, k, getattr(r.prm, k))
+        rs.zero_grads()
+
+        def step_ssg():
+            rs.prefilter_env()
+            rs.forward()
+            rs.zero_grads()
+            rs.backward(d_rgba, d_aov)
+        for _ in range(args.warmup):
+            step_ssg()
+        ms_s = timed(step_ssg, args.steps)
+        screen_grad = {"value": job_rate(V, args.steps, world, ms_s), "unit": "views/s",
+                       "ms_per_step": ms_s / args.steps, "cost_vs_step": ms_s / ms - 1.0}
+        del rs
+        torch.cuda.empty_cache()
+
     # --- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -601,7 +623,8 @@ def run_ours(args):
                            "inputs_vs_l2": "inputs and intermediates > 129 MB L2 (no flush)",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "launch_shapes": tuned or "defaults"},
-                "per_view": per_view, "graph": graph, "e2e": e2e, "roofline": roofline, "hbm": hbm_line,
+                "per_view": per_view, "graph": graph, "screen_grad": screen_grad, "e2e": e2e,
+                "roofline": roofline, "hbm": hbm_line,
                 "cpu_baseline": cpu,
                 "clocks": clocks,
                 "gpu_launches": None, "stages": stage_share, "work": counts, "hbm_peak_gbs": hbm,

@@ -80,7 +80,22 @@ typedef struct ss_surfels {
 } ss_surfels;
 
 /* Gradients w.r.t. ss_surfels (device, same layout, accumulated +=).
- * Any member may be NULL to skip it. */
+ * Any member may be NULL to skip it.
+ *
+ * The last two members are the densification statistic of Sec. 3.6.1
+ * (Eq. ss_grad), filled only when ss_render_params.screen_grad = 1 (else
+ * they must be NULL).  Every covering fragment of surfel i in view j adds
+ * |(g_x, g_y)| with g_x = dL/dT_{1,z} T_{4,z}, g_y = dL/dT_{2,z} T_{4,z}: the
+ * derivative of the fragment's own term of the loss with respect to the
+ * z entries of the T-matrix rows (the column that multiplies the centre c',
+ * so that (T_{1,z}, T_{2,z}) / T_{4,z} is the screen centre), through the
+ * ray-plane intersection and the centre-precomputed MIP filter, with every
+ * discrete decision and the shaded channels held fixed; norms, not signed
+ * values, are summed, so contributions do not cancel.
+ *   screen_grad_norm[i]  += sum over views and fragments of |(g_x, g_y)|
+ *   screen_grad_views[i] += number of views in which surfel i has at least one
+ *                           covering fragment (exact small integers in FP32)
+ * The criterion of Eq. 3dgs_grad is their ratio, taken by the caller. */
 typedef struct ss_surfel_grads {
     float* pos;
     float* quat;
@@ -88,6 +103,8 @@ typedef struct ss_surfel_grads {
     float* albedo;
     float* roughness;
     float* metallic;
+    float* screen_grad_norm;   /* [N] or NULL */
+    float* screen_grad_views;  /* [N] or NULL */
 } ss_surfel_grads;
 
 /* A batch: several scenes, each with its surfels and views.
@@ -119,6 +136,10 @@ typedef struct ss_render_params {
     int32_t fwd_warps;       /* warps per CTA of the forward rasteriser: 1 (default), 2 or 4 */
     int32_t bwd_warps;       /* warps per CTA of the backward rasteriser: 2, 4 (default) or 8 */
     int32_t pbwd_block;      /* surfels per CTA of the projection adjoint: 32..1024, default 128 */
+    int32_t screen_grad;     /* 1: the backward also accumulates the densification statistic
+                                (ss_surfel_grads.screen_grad_*); the workspace then holds 64 more
+                                bytes per (surfel, view) record */
+    int32_t pad_;
 } ss_render_params;
 
 /* Work counters of the last forward/backward pair (collect_stats = 1). */

@@ -41,7 +41,7 @@ class ss_surfels(ctypes.Structure):
 
 class ss_surfel_grads(ctypes.Structure):
     _fields_ = [("pos", c_vp), ("quat", c_vp), ("log_scale", c_vp), ("albedo", c_vp), ("roughness", c_vp),
-                ("metallic", c_vp)]
+                ("metallic", c_vp), ("screen_grad_norm", c_vp), ("screen_grad_views", c_vp)]
 
 
 class ss_batch_desc(ctypes.Structure):
@@ -52,7 +52,8 @@ class ss_batch_desc(ctypes.Structure):
 class ss_render_params(ctypes.Structure):
     _fields_ = [("r_cut", c_f), ("sigma_f", c_f), ("gamma", c_f), ("k_max", c_i32), ("z_near", c_f),
                 ("bg", c_f * 3), ("write_aov", c_i32), ("lut_n", c_i32), ("max_instances", c_i64),
-                ("collect_stats", c_i32), ("fwd_warps", c_i32), ("bwd_warps", c_i32), ("pbwd_block", c_i32)]
+                ("collect_stats", c_i32), ("fwd_warps", c_i32), ("bwd_warps", c_i32), ("pbwd_block", c_i32),
+                ("screen_grad", c_i32), ("pad_", c_i32)]
 
 
 class ss_stats(ctypes.Structure):

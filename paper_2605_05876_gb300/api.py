@@ -57,7 +57,7 @@ class Renderer:
 
     def __init__(self, scene, params: dict | None = None, env_levels: int = 6, irr_size=(32, 16),
                  with_backward: bool = True, capacity_slack: float = 1.3, device: str = "cuda",
-                 share_from: "Renderer | None" = None):
+                 share_from: "Renderer | None" = None, screen_grad: bool = False):
         import torch
         self.torch = torch
         self.dev = torch.device(device)
@@ -87,6 +87,7 @@ class Renderer:
               "ss_env_sizes")
         S = self.n_scenes
         self.prm = default_params(**(params or {}))
+        self.prm.screen_grad = int(screen_grad)
         if share_from is not None:
             self.env, self.irr, self.spec, self.aux, self.lut = (share_from.env, share_from.irr, share_from.spec,
                                                                  share_from.aux, share_from.lut)
@@ -160,11 +161,19 @@ class Renderer:
             self.d_irr.zero_()
             self.d_spec.zero_()
             self.d_env.zero_()
+            if self.prm.screen_grad:
+                self.screen_grad_norm.zero_()
+                self.screen_grad_views.zero_()
             return
         self.grads = {k: torch.zeros_like(v) for k, v in self.params_t.items()}
         self.d_irr = torch.zeros_like(self.irr)
         self.d_spec = torch.zeros_like(self.spec)
         self.d_env = torch.zeros_like(self.env)
+        if self.prm.screen_grad:
+            # densification statistic (Sec. 3.6.1, Eq. ss_grad): per surfel the summed
+            # |(g_x, g_y)| of its fragments and the number of views it appeared in
+            self.screen_grad_norm = torch.zeros(self.n_surfels, device=self.dev)
+            self.screen_grad_views = torch.zeros(self.n_surfels, device=self.dev)
 
     def env_backward(self):
         check(lib().ss_env_prefilter_backward(ctypes.byref(self.ed), self.n_scenes, _ptr(self.d_irr),
@@ -181,7 +190,8 @@ class Renderer:
         self.grads (surfel params) and self.d_env (base env texels)."""
         if not hasattr(self, "grads"):
             self.zero_grads()
-        g = C.ss_surfel_grads(*(ctypes.c_void_p(self.grads[k].data_ptr()) for k in SURFEL_FIELDS))
+        ssg = (_ptr(self.screen_grad_norm), _ptr(self.screen_grad_views)) if self.prm.screen_grad else (None, None)
+        g = C.ss_surfel_grads(*(ctypes.c_void_p(self.grads[k].data_ptr()) for k in SURFEL_FIELDS), *ssg)
         ge = C.ss_env_map_grads(_ptr(self.d_irr), _ptr(self.d_spec))
         check(lib().ss_render_backward(ctypes.byref(self.desc), ctypes.byref(self.surfels_struct()),
                                        ctypes.byref(self.prm), ctypes.byref(self.ed), ctypes.byref(self.maps),

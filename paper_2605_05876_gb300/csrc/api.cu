@@ -96,6 +96,7 @@ static ss_status check_knobs(const ss_render_params* p) {
     if (!(p->fwd_warps == 0 || p->fwd_warps == 1 || p->fwd_warps == 2 || p->fwd_warps == 4)) return SS_ERR_INVALID_ARG;
     if (!(p->bwd_warps == 0 || p->bwd_warps == 2 || p->bwd_warps == 4 || p->bwd_warps == 8)) return SS_ERR_INVALID_ARG;
     if (!(p->pbwd_block == 0 || (p->pbwd_block >= 32 && p->pbwd_block <= 1024))) return SS_ERR_INVALID_ARG;
+    if (p->screen_grad != 0 && p->screen_grad != 1) return SS_ERR_INVALID_ARG;
     return SS_OK;
 }
 
@@ -179,7 +180,7 @@ static ss_status build_layout(const ss_batch_desc* b, const ss_render_params* p,
 
 struct ws_plan {
     size_t status, layout, vgeo, rec, rank, tc, ts, tcur, keys, keys_alt, rects, cand, layer, pix, grad, masks,
-        mcount, env_acc, total;
+        mcount, env_acc, jac, total;
     int64_t env_texels;   // irradiance + specular texels of one scene (0: no env-gradient scratch)
 };
 
@@ -211,8 +212,9 @@ static ws_plan plan_ws(const ss_layout& L, const ss_render_params& p, int with_b
         w.masks = take(sizeof(uint2) * 8 * (size_t)p.max_instances);
         w.mcount = take(sizeof(uint32_t) * 8 * (size_t)L.total_tiles);
         w.env_acc = take(sizeof(float4) * SS_ACC_STRIDE * (size_t)w.env_texels * (size_t)L.n_scenes);
+        w.jac = p.screen_grad ? take(sizeof(float4) * 4 * (size_t)L.total_records) : 0;
     } else {
-        w.layer = w.pix = w.grad = w.masks = w.mcount = w.env_acc = 0;
+        w.layer = w.pix = w.grad = w.masks = w.mcount = w.env_acc = w.jac = 0;
     }
     w.total = o;
     return w;
@@ -241,6 +243,7 @@ static ss_ws_view carve(void* ws, const ws_plan& w, const ss_render_params& p, i
     v.cover_list = with_bwd ? (uint2*)(b + w.masks) : nullptr;
     v.cover_count = with_bwd ? (uint32_t*)(b + w.mcount) : nullptr;
     v.env_acc = (with_bwd && w.env_texels) ? (float4*)(b + w.env_acc) : nullptr;
+    v.ssg_jac = (with_bwd && p.screen_grad) ? (float4*)(b + w.jac) : nullptr;
     v.env_texels = w.env_texels;
     v.max_instances = p.max_instances;
     return v;
@@ -451,6 +454,8 @@ extern "C" ss_status ss_render_backward(const ss_batch_desc* b, const ss_surfels
     ss_status e = check_render_args(b, s, p, ed, env, ws);
     if (e) return e;
     if (!out_rgba_dev || !d_rgba_dev || !g) return SS_ERR_INVALID_ARG;
+    // the densification statistic needs its per-record scratch in the workspace
+    if ((g->screen_grad_norm || g->screen_grad_views) && !p->screen_grad) return SS_ERR_INVALID_ARG;
     if (p->write_aov && d_aov_dev && !out_aov_dev) return SS_ERR_INVALID_ARG;
     ss_layout L;   // on the stack: entry points may be called from several threads
     e = build_layout(b, p, &L);

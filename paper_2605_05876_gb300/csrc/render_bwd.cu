@@ -23,6 +23,8 @@
 #define G_NF 8
 #define G_CH 9     // 12 channels: rgb, albedo 3, roughness, metallic, normal 3, depth
 #define G_N 21
+#define G_SSN 21   // densification statistic: sum of the fragments' |(g_x, g_y)| (Eq. ss_grad)
+#define G_SSC 22   // ... and their number
 
 // Backward rasteriser, per warp (8 x 4 pixels): the forward pass left one
 // coverage word per (warp, staged surfel); the replay of each pixel's
@@ -36,8 +38,9 @@
 #define GT 13       // floats per pixel lane in the layer-coefficient table: G_k (12), S_k
 #define BW_CAP 128  // recorded fragments per warp before they are differentiated
 
-struct ss_bwarp {
-    float tab[G_N * GCOL];
+template <int ROWS>   // ROWS table rows: G_N, or G_N + 2 with the densification statistic
+struct ss_bwarp_t {
+    float tab[ROWS * GCOL];
     float gtab[32 * GT];
     uint32_t rec[BW_CAP];
 };
@@ -118,18 +121,139 @@ __global__ void __launch_bounds__(256) layer_coeff_kernel(ss_ws_view ws, ss_bwd_
     }
 }
 
+// ------------------------------------------------------------------------
+// Densification statistic (Sec. 3.6.1, Eq. ss_grad): per (surfel, view)
+// record, the derivatives of the record values the per-pixel weight depends
+// on -- P (factor of the screen quadratic form), A2, B2 (perspective term),
+// n_f -- along the camera-space centre c'_x and c'_y with the tangents held
+// fixed.  T_{1,z} = f_x c'_x + c_x c'_z is the only T entry that c'_x moves
+// (T_{2,z}: c'_y), so d/dT_{1,z} = (1/f_x) d/dc'_x; with T_{4,z} = c'_z and
+// dp_x/dc'_x = f_x / c'_z, a fragment's
+//   g_x = dL/dT_{1,z} T_{4,z} = dL/dp_x + sum_k dL/dval_k (c'_z / f_x) dval_k/dc'_x,
+// likewise g_y.  The derivatives are taken in forward mode (value and two
+// partials carried through the projection's arithmetic), with the
+// factorisation branch the forward pass chose for P.
+
+struct d3 {   // value and its partials along c'_x, c'_y
+    float v, x, y;
+};
+__device__ __forceinline__ d3 dc(float v) { return {v, 0.f, 0.f}; }
+__device__ __forceinline__ d3 operator+(d3 a, d3 b) { return {a.v + b.v, a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ d3 operator-(d3 a, d3 b) { return {a.v - b.v, a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ d3 operator-(d3 a) { return {-a.v, -a.x, -a.y}; }
+__device__ __forceinline__ d3 operator*(d3 a, d3 b) {
+    return {a.v * b.v, a.x * b.v + a.v * b.x, a.y * b.v + a.v * b.y};
+}
+__device__ __forceinline__ d3 operator*(float k, d3 a) { return {k * a.v, k * a.x, k * a.y}; }
+__device__ __forceinline__ d3 operator/(d3 a, d3 b) {
+    const float q = a.v / b.v, ib = 1.f / b.v;
+    return {q, (a.x - q * b.x) * ib, (a.y - q * b.y) * ib};
+}
+__device__ __forceinline__ d3 dsqrt(d3 a) {
+    const float r = sqrtf(a.v), h = 0.5f / r;
+    return {r, a.x * h, a.y * h};
+}
+__device__ __forceinline__ d3 dabs(d3 a) { return a.v < 0.f ? -a : a; }
+
+__global__ void __launch_bounds__(256) ssg_jac_kernel(ss_ws_view ws, ss_fwd_args a, int64_t n_total) {
+    const ss_layout* L = ws.layout;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_total) return;
+    int scene = 0;
+    while (scene + 1 < L->n_scenes && i >= L->scene_begin[scene + 1]) ++scene;
+    const float c0 = a.s.pos[i * 3], c1 = a.s.pos[i * 3 + 1], c2 = a.s.pos[i * 3 + 2];
+    const float4 q = *reinterpret_cast<const float4*>(a.s.quat + i * 4);
+    const float2 ls = *reinterpret_cast<const float2*>(a.s.log_scale + i * 2);
+    float Rq[9];
+    quat_rot(q.x, q.y, q.z, q.w, Rq);
+    const float su = expf(ls.x), sv = expf(ls.y);
+    const float tu[3] = {su * Rq[0], su * Rq[3], su * Rq[6]};
+    const float tv[3] = {sv * Rq[1], sv * Rq[4], sv * Rq[7]};
+    const float nrm[3] = {Rq[2], Rq[5], Rq[8]};
+    const float sig = a.p.sigma_f;
+    for (int v = L->scene_view_begin[scene]; v < L->scene_view_begin[scene + 1]; ++v) {
+        const ss_view_layout& vl = L->v[v];
+        const int64_t r = vl.rec_off + (i - vl.surfel_begin);
+        float4 out[4] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
+                         make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+        const uint32_t flags = __float_as_uint(ws.rec[r].r4.w);
+        if (flags & SS_FLAG_VALID) {
+            const ss_camera& cam = a.cams[v];
+            const float* Rc = cam.R;
+            float cp[3], tuc[3], tvc[3];
+            for (int k = 0; k < 3; ++k) {
+                cp[k] = Rc[k * 3] * c0 + Rc[k * 3 + 1] * c1 + Rc[k * 3 + 2] * c2 + cam.t[k];
+                tuc[k] = Rc[k * 3] * tu[0] + Rc[k * 3 + 1] * tu[1] + Rc[k * 3 + 2] * tu[2];
+                tvc[k] = Rc[k * 3] * tv[0] + Rc[k * 3 + 1] * tv[1] + Rc[k * 3 + 2] * tv[2];
+            }
+            const ss_view_geo& vg = ws.vgeo[v];
+            const float Ndv = ss_plane_distance(q, c0, c1, c2, vg.o_hi, vg.o_lo);
+            const float ncx = Rc[0] * nrm[0] + Rc[1] * nrm[1] + Rc[2] * nrm[2];   // n' = R n
+            const float ncy = Rc[3] * nrm[0] + Rc[4] * nrm[1] + Rc[5] * nrm[2];
+            const float fx = a.cams[v].fx, fy = a.cams[v].fy;
+            const d3 cx{cp[0], 1.f, 0.f}, cy{cp[1], 0.f, 1.f}, cz = dc(cp[2]);
+            const d3 Nd{Ndv, ncx, ncy};                      // N_d = n'.c'
+            const d3 mx = cx / cz, my = cy / cz;
+            const d3 ax = dc(tuc[0]) - mx * dc(tuc[2]), ay = dc(tuc[1]) - my * dc(tuc[2]);
+            const d3 bx = dc(tvc[0]) - mx * dc(tvc[2]), by = dc(tvc[1]) - my * dc(tvc[2]);
+            const d3 icz2 = dc(1.f / (cp[2] * cp[2]));
+            const d3 m11 = (fx * fx) * ((ax * ax + bx * bx) * icz2);
+            const d3 m12 = (fx * fy) * ((ax * ay + bx * by) * icz2);
+            const d3 m22 = (fy * fy) * ((ay * ay + by * by) * icz2);
+            const d3 det0 = (vg.detR * su * sv) * (Nd / cz);
+            const d3 sdg = (fx * fy) * (det0 * icz2);
+            const d3 Dn = sdg * sdg + sig * (m11 + m22) + dc(sig * sig);
+            const d3 nf = dabs(sdg) / dsqrt(Dn);
+            const d3 A2 = (1.f / fx) * (cz * dc(ncx) / Nd), B2 = (1.f / fy) * (cz * dc(ncy) / Nd);
+            const d3 qa = (m22 + dc(sig)) / Dn, qb = -m12 / Dn, qc = (m11 + dc(sig)) / Dn;
+            const d3 rsD = dc(1.f) / dsqrt(Dn);
+            d3 P00, P01, P10, P11;
+            if (ws.rec[r].r0.z == 0.f) {   // the branch the forward took (its P10 is zero)
+                P00 = dsqrt(qa);
+                P01 = qb / P00;
+                P10 = dc(0.f);
+                P11 = rsD / P00;
+            } else {
+                const d3 l11 = dsqrt(qc);
+                P00 = qb / l11;
+                P01 = l11;
+                P10 = rsD / l11;
+                P11 = dc(0.f);
+            }
+            const float kx = cp[2] / fx, ky = cp[2] / fy;
+            out[0] = make_float4(kx * P00.x, kx * P01.x, kx * P10.x, kx * P11.x);
+            out[1] = make_float4(kx * A2.x, kx * B2.x, kx * nf.x, 0.f);
+            out[2] = make_float4(ky * P00.y, ky * P01.y, ky * P10.y, ky * P11.y);
+            out[3] = make_float4(ky * A2.y, ky * B2.y, ky * nf.y, 0.f);
+        }
+        float4* J = ws.ssg_jac + r * 4;
+        J[0] = out[0];
+        J[1] = out[1];
+        J[2] = out[2];
+        J[3] = out[3];
+    }
+}
+
+// per warp: the staged records' densification derivatives (screen_grad only)
+struct ss_wjac {
+    float4 j[WSLOTS][4];
+};
+
 // AOV = false when no AOV gradient is given: the AOV channels' coefficients
 // are zero, so only P, A2, B2, the centre, n_f and RGB (the first 12 values
 // of the record) are differentiated and summed.
 // The kernel is persistent, like the forward one: warps take (tile, block)
 // items from a queue.
-template <bool AOV, int RWPB_BWD>
+template <bool AOV, bool SSG, int RWPB_BWD>
 __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_bwd_args& a, const int gw,
                                                  unsigned char* bwd_smem) {
-    constexpr int NV = AOV ? G_N : G_CH + 3;   // values per fragment
+    constexpr int NV = AOV ? G_N : G_CH + 3;   // gradient values per fragment
+    constexpr int NVT = NV + (SSG ? 2 : 0);    // + |(g_x, g_y)| and a count of 1 (Eq. ss_grad)
     constexpr int NC = AOV ? SS_NCH : 3;       // channels with a coefficient
+    using bwarp = ss_bwarp_t<SSG ? G_N + 2 : G_N>;
     ss_wstage* Wst = reinterpret_cast<ss_wstage*>(bwd_smem);
-    ss_bwarp* Bws = reinterpret_cast<ss_bwarp*>(bwd_smem + RWPB_BWD * sizeof(ss_wstage));
+    bwarp* Bws = reinterpret_cast<bwarp*>(bwd_smem + RWPB_BWD * sizeof(ss_wstage));
+    ss_wjac* Wjs = reinterpret_cast<ss_wjac*>(bwd_smem + RWPB_BWD * (sizeof(ss_wstage) + sizeof(bwarp)));
     const ss_layout* L = ws.layout;
     const int lw = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile = gw >> 3, warp = gw & 7;          // 8 blocks per tile
@@ -139,7 +263,7 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
     const int tx = lt % vl.tiles_x, ty = lt / vl.tiles_x;
     const int x0 = tx * SS_TILE, y0 = ty * SS_TILE;
     ss_wstage* Wc = Wst + lw;         // staging buffer
-    ss_bwarp& B = Bws[lw];
+    bwarp& B = Bws[lw];
     const int wx0 = 8 * (warp & 1), wy0 = 4 * (warp >> 1);
     const int lx = wx0 + (lane & 7), ly = wy0 + (lane >> 3);
     const int px = x0 + lx, py = y0 + ly;
@@ -227,6 +351,16 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
                 gr[G_PY] = -(gs0 * h0.y + gs1 * h0.w + gs2 * h1.y);
 #pragma unroll
                 for (int q = 0; q < NV; ++q) B.tab[q * GCOL + lane] = gr[q];
+                if (SSG) {   // Eq. ss_grad: g = dL/dp + sum_k dL/dval_k jac[k]
+                    const float4* J = Wjs[lw].j[s];
+                    const float4 j0 = J[0], j1 = J[1], j2 = J[2], j3 = J[3];
+                    const float gxs = gr[G_PX] + gr[G_P + 0] * j0.x + gr[G_P + 1] * j0.y + gr[G_P + 2] * j0.z +
+                                      gr[G_P + 3] * j0.w + gr[G_A2] * j1.x + gr[G_B2] * j1.y + gr[G_NF] * j1.z;
+                    const float gys = gr[G_PY] + gr[G_P + 0] * j2.x + gr[G_P + 1] * j2.y + gr[G_P + 2] * j2.z +
+                                      gr[G_P + 3] * j2.w + gr[G_A2] * j3.x + gr[G_B2] * j3.y + gr[G_NF] * j3.z;
+                    B.tab[NV * GCOL + lane] = sqrtf(gxs * gxs + gys * gys);
+                    B.tab[(NV + 1) * GCOL + lane] = 1.f;
+                }
             }
             const int snext = __shfl_down_sync(0xffffffffu, s, 1);
             // run ends: the last valid column and every column followed by another surfel
@@ -234,7 +368,7 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
             __syncwarp();
             float v[32];
             {
-                const float4* t4 = reinterpret_cast<const float4*>(B.tab + (lane < NV ? lane : 0) * GCOL);
+                const float4* t4 = reinterpret_cast<const float4*>(B.tab + (lane < NVT ? lane : 0) * GCOL);
 #pragma unroll
                 for (int m = 0; m < 8; ++m) {
                     const float4 x = t4[m];
@@ -254,7 +388,9 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
                     tot += v[j];
                     if ((ends >> j) & 1u) {   // warp-uniform
                         const int sl = __shfl_sync(0xffffffffu, s, j);
-                        if (lane < NV && tot != 0.f) atomicAdd(grad + (int64_t)Wc->id[sl] * SS_NGRAD + lane, tot);
+                        if (lane < NVT && tot != 0.f)   // table row -> record column (the statistic at 21, 22)
+                            atomicAdd(grad + (int64_t)Wc->id[sl] * SS_NGRAD + (lane < NV ? lane : G_SSN + lane - NV),
+                                      tot);
                         tot = 0.f;
                     }
                 }
@@ -271,6 +407,11 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
         if (__all_sync(0xffffffffu, done)) break;
         const int n = (int)min((int64_t)32, n_list - base);
         const uint2 cur = nxt;
+        if (SSG && lane < n) {   // the record's densification derivatives, with the record
+            const float4* J = ws.ssg_jac + (int64_t)cur.x * 4;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) cp_async16(&Wjs[lw].j[lane][k], J + k);
+        }
         stage_ids(*Wc, recs, cur.x, lane, lane < n);
         nxt = base + 32 + lane < n_list ? __ldg(clist + base + 32 + lane) : make_uint2(0u, 0u);
         if (base + 32 + lane < n_list) {
@@ -327,7 +468,7 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
     }
 }
 
-template <bool AOV, int RWPB_BWD>
+template <bool AOV, bool SSG, int RWPB_BWD>
 __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kernel(ss_ws_view ws, ss_bwd_args a,
                                                                                   int n_items) {
     extern __shared__ __align__(16) unsigned char bwd_smem[];
@@ -337,36 +478,51 @@ __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kerne
         if (lane == 0) item = (int)atomicAdd(ws.work + 1, 1u);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
-        raster_bwd_block<AOV, RWPB_BWD>(ws, a, item, bwd_smem);
+        raster_bwd_block<AOV, SSG, RWPB_BWD>(ws, a, item, bwd_smem);
         __syncwarp();
     }
 }
 
-template <bool AOV, int W>
+template <bool AOV, bool SSG, int W>
 static void launch_raster_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st) {
-    const int smem = W * (int)(sizeof(ss_wstage) + sizeof(ss_bwarp));
+    const int smem =
+        W * (int)(sizeof(ss_wstage) + sizeof(ss_bwarp_t<SSG ? G_N + 2 : G_N>) + (SSG ? sizeof(ss_wjac) : 0));
     static std::atomic<unsigned long long> optin{0}, resident{0};
-    ss_smem_optin(raster_bwd_kernel<AOV, W>, smem, optin);
+    ss_smem_optin(raster_bwd_kernel<AOV, SSG, W>, smem, optin);
     const int n_items = (int)(L.total_tiles * 8);
-    const int ctas = ss_resident_ctas(raster_bwd_kernel<AOV, W>, 32 * W, smem, resident);
+    const int ctas = ss_resident_ctas(raster_bwd_kernel<AOV, SSG, W>, 32 * W, smem, resident);
     const int grid = max(1, min(ctas > 0 ? ctas : 1, (n_items + W - 1) / W));
-    raster_bwd_kernel<AOV, W><<<grid, 32 * W, smem, st>>>(ws, a, n_items);
+    raster_bwd_kernel<AOV, SSG, W><<<grid, 32 * W, smem, st>>>(ws, a, n_items);
+}
+
+template <bool AOV, bool SSG>
+static void launch_raster_bwd_w(int w, const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a,
+                                cudaStream_t st) {
+    if (w == 2) launch_raster_bwd<AOV, SSG, 2>(ws, L, a, st);
+    else if (w == 4) launch_raster_bwd<AOV, SSG, 4>(ws, L, a, st);
+    else launch_raster_bwd<AOV, SSG, 8>(ws, L, a, st);
 }
 
 void ss_launch_raster_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st) {
     if (L.total_tiles <= 0) return;
+    const bool ssg = ws.ssg_jac && (a.g.screen_grad_norm || a.g.screen_grad_views);
+    if (ssg) {
+        const int64_t n = L.scene_begin[L.n_scenes];
+        if (n > 0) {
+            ss_note_launch();
+            ssg_jac_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ws, a.f, n);
+        }
+    }
     ss_note_launch();
     layer_coeff_kernel<<<(unsigned)((L.total_pixels + 255) / 256), 256, 0, st>>>(ws, a);
     const int w = a.f.p.bwd_warps ? a.f.p.bwd_warps : RWPB_BWD_DEFAULT;
     ss_note_launch();
     if (a.d_aov) {
-        if (w == 2) launch_raster_bwd<true, 2>(ws, L, a, st);
-        else if (w == 4) launch_raster_bwd<true, 4>(ws, L, a, st);
-        else launch_raster_bwd<true, 8>(ws, L, a, st);
+        if (ssg) launch_raster_bwd_w<true, true>(w, ws, L, a, st);
+        else launch_raster_bwd_w<true, false>(w, ws, L, a, st);
     } else {
-        if (w == 2) launch_raster_bwd<false, 2>(ws, L, a, st);
-        else if (w == 4) launch_raster_bwd<false, 4>(ws, L, a, st);
-        else launch_raster_bwd<false, 8>(ws, L, a, st);
+        if (ssg) launch_raster_bwd_w<false, true>(w, ws, L, a, st);
+        else launch_raster_bwd_w<false, false>(w, ws, L, a, st);
     }
 }
 
@@ -511,6 +667,8 @@ __device__ __forceinline__ void pbwd_surfel(const ss_ws_view& ws, const ss_bwd_a
     float gc[3] = {0, 0, 0}, gRq[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, gsu = 0.f, gsv = 0.f;
     float grho[3] = {0, 0, 0}, grough = 0.f, gmetal = 0.f;
     float gLdF[3] = {0, 0, 0}, gLdB[3] = {0, 0, 0};   // dL/dLd summed per side
+    float ssg_norm = 0.f, ssg_views = 0.f;            // densification statistic (Eq. ss_grad)
+    const bool ssg = A.g.screen_grad_norm || A.g.screen_grad_views;
     bool any_view = false;
     for (int v = L->scene_view_begin[scene]; v < L->scene_view_begin[scene + 1]; ++v) {
         const ss_view_layout& vl = L->v[v];
@@ -526,6 +684,10 @@ __device__ __forceinline__ void pbwd_surfel(const ss_ws_view& ws, const ss_bwd_a
             G[4 * k] = t.x; G[4 * k + 1] = t.y; G[4 * k + 2] = t.z; G[4 * k + 3] = t.w;
         }
         if (!(flags & SS_FLAG_VALID)) continue;
+        if (ssg) {
+            ssg_norm += G[G_SSN];
+            ssg_views += G[G_SSC] > 0.f ? 1.f : 0.f;   // the surfel has a fragment in this view
+        }
         bool any = false;
 #pragma unroll
         for (int k = 0; k < G_N; ++k) any = any || (G[k] != 0.f);
@@ -729,6 +891,10 @@ __device__ __forceinline__ void pbwd_surfel(const ss_ws_view& ws, const ss_bwd_a
             gRq[k * 3 + 2] += dn[k];
             gc[k] += dcv[k];
         }
+    }
+    if (ssg) {
+        if (A.g.screen_grad_norm && ssg_norm != 0.f) A.g.screen_grad_norm[i] += ssg_norm;
+        if (A.g.screen_grad_views && ssg_views != 0.f) A.g.screen_grad_views[i] += ssg_views;
     }
     if (!any_view) return;
     // ---- irradiance: once per side, from the view sums

@@ -16,7 +16,8 @@
 #define SS_CNT_STRIDE 32
 // Likewise the env-map gradient accumulators: one float4 per texel, 128 bytes apart.
 #define SS_ACC_STRIDE 8
-#define SS_NGRAD 24                // floats per (view, surfel) gradient record (22 used)
+#define SS_NGRAD 24                // floats per (view, surfel) gradient record (21 used, 23 with
+                                   // the densification statistic)
 #define SS_PI_F 3.14159265358979323846f
 
 // ------------------------------------------------------------------------
@@ -105,6 +106,9 @@ struct ss_ws_view {
                             // surfel that covers a pixel of the warp's block, in list order (forward -> backward)
     uint32_t* cover_count;  // [8 * tiles]: entries of each warp's list
     float4* env_acc;        // [scenes][env_texels][SS_ACC_STRIDE] RGBA accumulators of the env-map gradients (backward)
+    float4* ssg_jac;        // [total_records][4] (screen_grad only): per record, the derivatives of
+                            // (P00, P01, P10, P11) and (A2, B2, n_f) along the screen centre, scaled so
+                            // that g_x = dL/dp_x + sum_k dL/dval_k jac_x[k] (Eq. ss_grad); x then y
     int64_t env_texels;     // irradiance + specular texels per scene
     int64_t max_instances;
 };
