@@ -139,7 +139,12 @@ typedef struct ss_render_params {
     int32_t screen_grad;     /* 1: the backward also accumulates the densification statistic
                                 (ss_surfel_grads.screen_grad_*); the workspace then holds 64 more
                                 bytes per (surfel, view) record */
-    int32_t pad_;
+    int32_t mip_mode;        /* MIP filter (Sec. 3.3): 0 = centre-precomputed Sigma_mip and n_f
+                                (Sec. 3.3.2, the method; default), 1 = none (Sigma_mip = I, n_f = 1:
+                                sigma_f is taken as 0), 2 = per-pixel Jacobian of the ray-splat
+                                intersection (AA-2DGS, Sec. 3.3.1; the Sec. 4.4.2 ablation): Sigma_mip
+                                = I + sigma_f J J^T and n_f evaluated at every hit.  Mode 2 is
+                                forward-only: ss_render_backward returns SS_ERR_INVALID_ARG */
 } ss_render_params;
 
 /* Work counters of the last forward/backward pair (collect_stats = 1). */
@@ -311,6 +316,14 @@ ss_status ss_render_backward(const ss_batch_desc* b, const ss_surfels* s, const 
                              const float* out_aov_dev, const float* d_rgba_dev, const float* d_aov_dev,
                              ss_surfel_grads* g, ss_env_map_grads* genv, void* ws, size_t ws_bytes,
                              void* stream);
+
+/* Box filter of an RGBA image by an integer factor (the 4x supersampled
+ * reference of Sec. 4.4.2: render at factor x the resolution without the MIP
+ * filter, then average factor x factor blocks).  in_dev [H][W][4] row-major,
+ * out_dev [H/factor][W/factor][4]; W and H multiples of factor, factor in
+ * [1, 16].  Errors: SS_ERR_INVALID_ARG for NULL pointers or bad sizes. */
+ss_status ss_box_downsample(const float* in_dev, int32_t width, int32_t height, int32_t factor, float* out_dev,
+                            void* stream);
 
 /* Start / stop collecting stage timings (see ss_stage_times).  end
  * synchronises the recorded events and fills *out. */

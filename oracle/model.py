@@ -65,6 +65,19 @@ class Params:
     irr_w: int = 32
     irr_h: int = 16
     lut_n: int = 128
+    # MIP filter (Sec. 3.3): "centre" -- the method, Sigma_mip and n_f at the
+    # surfel centre (Sec. 3.3.2); "none" -- no band limiting (Sigma_mip = I,
+    # n_f = 1, i.e. sigma_f = 0); "pixel" -- the per-pixel Jacobian of
+    # AA-2DGS (Sec. 3.3.1), Sigma_mip and n_f at every hit (the Sec. 4.4.2
+    # ablation)
+    mip_mode: str = "centre"
+
+    def sigma_eff(self) -> float:
+        return 0.0 if self.mip_mode == "none" else self.sigma_f
+
+    def pp_sigma(self) -> float:
+        """Argument of the C half: the per-pixel filter's sigma_f, or -1."""
+        return self.sigma_f if self.mip_mode == "pixel" else -1.0
 
 
 # ---------------------------------------------------------------------------
@@ -96,11 +109,11 @@ def lib():
     L.oref_env_adjoint.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int, dp]
     L.oref_fragments.argtypes = [ctypes.c_int, dp, dp, dp, u8p, dp, ctypes.c_int, ctypes.c_int,
-                                 ctypes.c_double, ctypes.c_int, ctypes.c_int, i32p, i32p, dp, i64p,
-                                 i64p, i32p, i32p, i32p]
+                                 ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int, i32p, i32p, dp,
+                                 i64p, i64p, i32p, i32p, i32p]
     L.oref_fragments.restype = ctypes.c_longlong
     L.oref_pixel_candidates.argtypes = [ctypes.c_int, dp, dp, dp, u8p, dp, ctypes.c_int, ctypes.c_int,
-                                        ctypes.c_double, ctypes.c_int, i32p, dp, dp, dp, dp]
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_int, i32p, dp, dp, dp, dp]
     L.oref_pixel_candidates.restype = ctypes.c_int
     return L
 
@@ -271,7 +284,7 @@ def mip_filter(T: torch.Tensor, depth_ok: torch.Tensor, prm: Params):
     valid = depth_ok & (detM != 0)
     Msafe = torch.where(valid[:, None, None], M, torch.eye(2, dtype=F64).expand_as(M))
     J = torch.linalg.inv(Msafe)
-    Sigma = torch.eye(2, dtype=F64) + prm.sigma_f * (J @ J.transpose(1, 2))   # Eq. mip_cov
+    Sigma = torch.eye(2, dtype=F64) + prm.sigma_eff() * (J @ J.transpose(1, 2))   # Eq. mip_cov
     Sinv = torch.linalg.inv(Sigma)
     n_f = torch.rsqrt(torch.linalg.det(Sigma))                                # sqrt(|I| / |Sigma|)
     return Sinv, n_f, M, valid
@@ -361,7 +374,7 @@ def support_rect(rec: dict, prm: Params) -> np.ndarray:
             ca, cb = C[:, a, a], C[:, a, 2]
             disc = np.sqrt(np.maximum(cb * cb - ca * c22, 0.0))
             r0, r1 = (cb + disc) / c22, (cb - disc) / c22
-            ext = prm.r_cut * np.sqrt(MMt[:, a, a] + prm.sigma_f)
+            ext = prm.r_cut * np.sqrt(MMt[:, a, a] + prm.sigma_eff())
             lo = np.minimum(np.minimum(r0, r1), p[:, a] - ext) - 1.0
             hi = np.maximum(np.maximum(r0, r1), p[:, a] + ext) + 1.0
             bad = ~(c22 < 0)
@@ -407,7 +420,7 @@ def fragments(rec: dict, rect: np.ndarray, W: int, H: int, prm: Params, pix=None
     L = lib()
     args = (N, _p(T, ctypes.c_double), _p(Sv, ctypes.c_double), _p(zse, ctypes.c_double),
             _p(valid, ctypes.c_uint8), _p(rect, ctypes.c_double), W, H, prm.r_cut ** 2, prm.k_max,
-            P, pix_ptr, _p(nl, ctypes.c_int32), _p(mg, ctypes.c_double), _p(cnt, ctypes.c_int64))
+            prm.pp_sigma(), P, pix_ptr, _p(nl, ctypes.c_int32), _p(mg, ctypes.c_double), _p(cnt, ctypes.c_int64))
     total = L.oref_fragments(*args, None, None, None, None)
     off = np.zeros(P, np.int64)
     off[1:] = np.cumsum(cnt)[:-1]
@@ -447,7 +460,7 @@ def decision_variants(rec: dict, rect: np.ndarray, W: int, prm: Params, pid: int
         r2, zs, ze, dist = (np.zeros(cap) for _ in range(4))
         n = lib().oref_pixel_candidates(T.shape[0], _p(T, ctypes.c_double), _p(Sv, ctypes.c_double),
                                         _p(zse, ctypes.c_double), _p(valid, ctypes.c_uint8),
-                                        _p(rect, ctypes.c_double), W, int(pid), near, cap,
+                                        _p(rect, ctypes.c_double), W, int(pid), near, prm.pp_sigma(), cap,
                                         _p(idx, ctypes.c_int32), _p(r2, ctypes.c_double), _p(zs, ctypes.c_double),
                                         _p(ze, ctypes.c_double), _p(dist, ctypes.c_double))
         if n <= cap:
@@ -547,9 +560,23 @@ def composite(rec: dict, fr: Fragments, W: int, prm: Params, per_frag: dict | No
     s = torch.linalg.cross(k, l, dim=-1)
     u = s[:, 0] / s[:, 2]
     v = s[:, 1] / s[:, 2]
-    Si = fv("Sinv")
+    if prm.mip_mode == "pixel":
+        # the MIP filter at the hit (Sec. 3.3.1): J = d(u,v)/d(x,y) of this
+        # intersection by the quotient rule (ds/dx = T4 x l, ds/dy = k x T4),
+        # Sigma = I + sigma_f J J^T (Eq. mip_cov), n_f = |Sigma|^-1/2 (Eq. mip_eval)
+        sx = torch.linalg.cross(T4, l, dim=-1)
+        sy = torch.linalg.cross(k, T4, dim=-1)
+        J = torch.stack([torch.stack([(sx[:, 0] - u * sx[:, 2]) / s[:, 2], (sy[:, 0] - u * sy[:, 2]) / s[:, 2]], -1),
+                         torch.stack([(sx[:, 1] - v * sx[:, 2]) / s[:, 2], (sy[:, 1] - v * sy[:, 2]) / s[:, 2]], -1)],
+                        -2)
+        Sigma = torch.eye(2, dtype=F64) + prm.sigma_f * (J @ J.transpose(1, 2))
+        Si = torch.linalg.inv(Sigma)
+        n_f = torch.rsqrt(torch.linalg.det(Sigma))
+    else:
+        Si = fv("Sinv")
+        n_f = fv("n_f")
     rho2 = Si[:, 0, 0] * u * u + 2.0 * Si[:, 0, 1] * u * v + Si[:, 1, 1] * v * v   # Eq. mip_weight
-    w = fv("n_f") * torch.exp(-0.5 * rho2)
+    w = n_f * torch.exp(-0.5 * rho2)
     key = row_t * Kq + layer
     Wk = torch.zeros(P * Kq, dtype=F64).index_add(0, key, w).reshape(P, Kq)
     Ck = torch.zeros(P * Kq, N_CH, dtype=F64).index_add(0, key, w[:, None] * fv("ch")).reshape(P, Kq, N_CH)

@@ -337,7 +337,8 @@ void oref_env_adjoint(const double* d_irr, const double* d_spec, int We, int He,
  * in front of the camera (depth T4.(u, v, 1) > 0).
  *
  * A surfel covers the pixel iff the pixel centre lies in its support
- * rectangle and rho2_mip < r_cut^2 (Algorithm 1).  Covering surfels are
+ * rectangle and rho2_mip < r_cut^2 (Algorithm 1; pp_sigma >= 0 selects the
+ * per-pixel MIP filter, see hit_rho2).  Covering surfels are
  * visited in ascending (z_start, index) order and grouped by Algorithm 1: a
  * new layer starts when the open layer has weight and z_start > z_max_end;
  * layers after the K_max-th are discarded.
@@ -374,8 +375,16 @@ static int frag_cmp(const void* a, const void* b) {
 }
 
 /* rho2_mip of surfel i at pixel centre (x, y); returns 0 if there is no hit
- * in front of the camera. */
-static int hit_rho2(const double* T, const double* Sinv, double x, double y, double* rho2) {
+ * in front of the camera.  With pp_sigma < 0 the MIP filter is the one
+ * precomputed at the surfel centre (Sinv, Sec. 3.3.2, Eq. mip_weight).  With
+ * pp_sigma >= 0 it is evaluated at the hit itself (the per-pixel Jacobian of
+ * AA-2DGS that Sec. 3.3.1 describes and Sec. 4.4.2 ablates):
+ * J = d(u,v)/d(x,y) of the intersection mapping at this pixel, by the
+ * quotient rule on s = k x l (dk/dx = T4, dl/dy = T4), then
+ * Sigma = I + sigma_f J J^T (Eq. mip_cov) and rho2 = u^T Sigma^-1 u; the
+ * per-pixel n_f is then returned in *nf (else *nf is untouched). */
+static int hit_rho2(const double* T, const double* Sinv, double x, double y, double pp_sigma, double* rho2,
+                    double* nf) {
     const double* T1 = T;
     const double* T2 = T + 3;
     const double* T4 = T + 6;
@@ -391,14 +400,32 @@ static int hit_rho2(const double* T, const double* Sinv, double x, double y, dou
     double u = s[0] / s[2], v = s[1] / s[2];
     double depth = T4[0] * u + T4[1] * v + T4[2];
     if (!(depth > 0.0)) return 0;
-    *rho2 = Sinv[0] * u * u + 2.0 * Sinv[1] * u * v + Sinv[2] * v * v;
+    if (pp_sigma < 0.0) {
+        *rho2 = Sinv[0] * u * u + 2.0 * Sinv[1] * u * v + Sinv[2] * v * v;
+        return 1;
+    }
+    double sx[3], sy[3];   /* ds/dx = T4 x l, ds/dy = k x T4 */
+    sx[0] = T4[1] * l[2] - T4[2] * l[1];
+    sx[1] = T4[2] * l[0] - T4[0] * l[2];
+    sx[2] = T4[0] * l[1] - T4[1] * l[0];
+    sy[0] = k[1] * T4[2] - k[2] * T4[1];
+    sy[1] = k[2] * T4[0] - k[0] * T4[2];
+    sy[2] = k[0] * T4[1] - k[1] * T4[0];
+    double Juu = (sx[0] - u * sx[2]) / s[2], Juv = (sy[0] - u * sy[2]) / s[2];
+    double Jvu = (sx[1] - v * sx[2]) / s[2], Jvv = (sy[1] - v * sy[2]) / s[2];
+    double a = 1.0 + pp_sigma * (Juu * Juu + Juv * Juv);
+    double b = pp_sigma * (Juu * Jvu + Juv * Jvv);
+    double c = 1.0 + pp_sigma * (Jvu * Jvu + Jvv * Jvv);
+    double det = a * c - b * b;
+    *rho2 = (c * u * u - 2.0 * b * u * v + a * v * v) / det;
+    if (nf) *nf = 1.0 / sqrt(det);
     return 1;
 }
 
 long long oref_fragments(int N, const double* T /* [N][9] */, const double* Sinv /* [N][3] */,
                          const double* zse /* [N][2] */, const uint8_t* valid,
                          const double* rect /* [N][4] x_lo, x_hi, y_lo, y_hi */, int W, int H,
-                         double rcut2, int kmax, int npix, const int32_t* pix /* [npix] or NULL */,
+                         double rcut2, int kmax, double pp_sigma, int npix, const int32_t* pix /* [npix] or NULL */,
                          int32_t* n_layers /* [P] */, double* margin /* [P][3] */,
                          int64_t* frag_count /* [P] */, const int64_t* frag_offset /* [P] */,
                          int32_t* frag_pix, int32_t* frag_sid, int32_t* frag_layer) {
@@ -451,7 +478,7 @@ long long oref_fragments(int N, const double* T /* [N][9] */, const double* Sinv
                 int i = row_list[c];
                 if (px < bbox[i * 4 + 0] || px > bbox[i * 4 + 1]) continue;
                 double rho2;
-                if (!hit_rho2(T + (size_t)i * 9, Sinv + (size_t)i * 3, x, y, &rho2)) continue;
+                if (!hit_rho2(T + (size_t)i * 9, Sinv + (size_t)i * 3, x, y, pp_sigma, &rho2, NULL)) continue;
                 const double* R = rect + (size_t)i * 4;
                 /* signed distance of the pixel centre from the rectangle's edge (< 0 outside) */
                 double d = fmin(fmin(x - R[0], R[1] - x), fmin(y - R[2], R[3] - y));
@@ -524,7 +551,7 @@ long long oref_fragments(int N, const double* T /* [N][9] */, const double* Sinv
  * the return value exceeds it).  Tests use it to enumerate the outcomes of
  * decisions that sit within rounding of flipping. */
 int oref_pixel_candidates(int N, const double* T, const double* Sinv, const double* zse, const uint8_t* valid,
-                          const double* rect, int W, int pid, double near, int cap, int32_t* idx,
+                          const double* rect, int W, int pid, double near, double pp_sigma, int cap, int32_t* idx,
                           double* rho2_out, double* zs_out, double* ze_out, double* dist_out) {
     int px = pid % W, py = pid / W;
     double x = px + 0.5, y = py + 0.5;
@@ -535,7 +562,7 @@ int oref_pixel_candidates(int N, const double* T, const double* Sinv, const doub
         double d = fmin(fmin(x - R[0], R[1] - x), fmin(y - R[2], R[3] - y));
         if (!(d > -near)) continue;
         double rho2;
-        if (!hit_rho2(T + (size_t)i * 9, Sinv + (size_t)i * 3, x, y, &rho2)) continue;
+        if (!hit_rho2(T + (size_t)i * 9, Sinv + (size_t)i * 3, x, y, pp_sigma, &rho2, NULL)) continue;
         if (n < cap) {
             idx[n] = i;
             rho2_out[n] = rho2;

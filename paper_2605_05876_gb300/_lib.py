@@ -27,6 +27,7 @@ SS_MAX_VIEWS = 256
 SS_MAX_SCENES = 64
 SS_N_AOV = 9
 SS_NOALLOC_AUX_FLOATS = 1 << 20
+SS_MIP_CENTRE, SS_MIP_NONE, SS_MIP_PIXEL = 0, 1, 2
 
 
 class ss_camera(ctypes.Structure):
@@ -53,7 +54,7 @@ class ss_render_params(ctypes.Structure):
     _fields_ = [("r_cut", c_f), ("sigma_f", c_f), ("gamma", c_f), ("k_max", c_i32), ("z_near", c_f),
                 ("bg", c_f * 3), ("write_aov", c_i32), ("lut_n", c_i32), ("max_instances", c_i64),
                 ("collect_stats", c_i32), ("fwd_warps", c_i32), ("bwd_warps", c_i32), ("pbwd_block", c_i32),
-                ("screen_grad", c_i32), ("pad_", c_i32)]
+                ("screen_grad", c_i32), ("mip_mode", c_i32)]
 
 
 class ss_stats(ctypes.Structure):
@@ -123,6 +124,7 @@ EXPORTS = {
                                    ctypes.POINTER(ss_surfel_grads), ctypes.POINTER(ss_env_map_grads), c_vp,
                                    ctypes.c_size_t, c_vp]),
     "ss_read_status": (c_i32, [c_vp, c_vp]),
+    "ss_box_downsample": (c_i32, [c_vp, c_i32, c_i32, c_i32, c_vp, c_vp]),
     "ss_read_stats": (c_i32, [c_vp, ctypes.c_void_p, c_vp]),
     "ss_launch_count": (c_i32, [ctypes.POINTER(ctypes.c_int64)]),
     "ss_profile_begin": (c_i32, []),

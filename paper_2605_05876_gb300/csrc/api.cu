@@ -97,6 +97,7 @@ static ss_status check_knobs(const ss_render_params* p) {
     if (!(p->bwd_warps == 0 || p->bwd_warps == 2 || p->bwd_warps == 4 || p->bwd_warps == 8)) return SS_ERR_INVALID_ARG;
     if (!(p->pbwd_block == 0 || (p->pbwd_block >= 32 && p->pbwd_block <= 1024))) return SS_ERR_INVALID_ARG;
     if (p->screen_grad != 0 && p->screen_grad != 1) return SS_ERR_INVALID_ARG;
+    if (p->mip_mode < 0 || p->mip_mode > 2) return SS_ERR_INVALID_ARG;
     return SS_OK;
 }
 
@@ -378,6 +379,7 @@ static ss_status forward_core(const ss_batch_desc* b, const ss_surfels* s, const
     ss_fwd_args a;
     a.s = *s;
     a.p = *p;
+    if (p->mip_mode == 1) a.p.sigma_f = 0.f;   // no MIP filter: Sigma_mip = I, n_f = 1
     a.ed = *ed;
     a.env = *env;
     a.cams = b->cams_dev;
@@ -456,6 +458,7 @@ extern "C" ss_status ss_render_backward(const ss_batch_desc* b, const ss_surfels
     if (!out_rgba_dev || !d_rgba_dev || !g) return SS_ERR_INVALID_ARG;
     // the densification statistic needs its per-record scratch in the workspace
     if ((g->screen_grad_norm || g->screen_grad_views) && !p->screen_grad) return SS_ERR_INVALID_ARG;
+    if (p->mip_mode == 2) return SS_ERR_INVALID_ARG;   // the per-pixel MIP filter is forward-only
     if (p->write_aov && d_aov_dev && !out_aov_dev) return SS_ERR_INVALID_ARG;
     ss_layout L;   // on the stack: entry points may be called from several threads
     e = build_layout(b, p, &L);
@@ -467,6 +470,7 @@ extern "C" ss_status ss_render_backward(const ss_batch_desc* b, const ss_surfels
     ss_bwd_args a;
     a.f.s = *s;
     a.f.p = *p;
+    if (p->mip_mode == 1) a.f.p.sigma_f = 0.f;
     a.f.ed = *ed;
     a.f.env = *env;
     a.f.cams = b->cams_dev;
@@ -493,6 +497,16 @@ extern "C" ss_status ss_render_backward(const ss_batch_desc* b, const ss_surfels
         ss_stage_scope sc(4, st);
         ss_launch_project_bwd(W, L, a, st);
     }
+    CK(cudaGetLastError());
+    return SS_OK;
+}
+
+extern "C" ss_status ss_box_downsample(const float* in_dev, int32_t width, int32_t height, int32_t factor,
+                                       float* out_dev, void* stream) {
+    if (!in_dev || !out_dev || factor < 1 || factor > 16 || width < 1 || height < 1 || width % factor ||
+        height % factor)
+        return SS_ERR_INVALID_ARG;
+    ss_launch_box_downsample(in_dev, width, height, factor, out_dev, (cudaStream_t)stream);
     CK(cudaGetLastError());
     return SS_OK;
 }

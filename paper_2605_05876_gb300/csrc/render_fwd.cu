@@ -225,8 +225,20 @@ __global__ void __launch_bounds__(256, 4) project_kernel(ss_ws_view ws, ss_fwd_a
             }
             col = make_float3(cc[0], cc[1], cc[2]);
         }
-        rec.r0 = make_float4(P00, P01, P10, P11);
-        rec.r1 = make_float4(A2, B2, 1.f, nf);
+        if (a.p.mip_mode == 2) {
+            // per-pixel MIP filter: the raster needs J0 = M^-1 = d(u,v)/d(x,y) at the
+            // centre, adj(M) / det M with det M = sdg (formed from N_d in double-float,
+            // so it stays accurate for nearly edge-on surfels); n_f is per pixel
+            // there (1 marks a valid record), and the exact support is not the
+            // centre quadratic's, so the support rectangle is always tested
+            const float k = 1.f / (cz * sdg);
+            rec.r0 = make_float4(fy * by * k, -fx * bx * k, -fy * ay * k, fx * ax * k);
+            rec.r1 = make_float4(A2, B2, 1.f, 1.f);
+            if (valid) flags |= SS_FLAG_RECT_TEST;
+        } else {
+            rec.r0 = make_float4(P00, P01, P10, P11);
+            rec.r1 = make_float4(A2, B2, 1.f, nf);
+        }
         rec.r2 = make_float4(px.hi, py.hi, px.lo, py.lo);
         rec.r3 = make_float4(zs, ze, __uint_as_float(valid ? pack16(i0, i1) : 0xffffu),
                              __uint_as_float(valid ? pack16(j0, j1) : 0xffffu));
@@ -558,7 +570,7 @@ void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_a
 // as many warps as fit on the device take (tile, block) items from a queue
 // in item order, so no warp slot idles while items are left.
 
-template <bool STATS, int RWPB_FWD>
+template <bool STATS, bool PP, int RWPB_FWD>
 __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_fwd_args& a, const int gw,
                                                  unsigned char* fwd_smem) {
     ss_wstage* Wst = reinterpret_cast<ss_wstage*>(fwd_smem);   // [RWPB_FWD warps][2]
@@ -678,13 +690,25 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
         if (lane < n) {
             const float4 g1 = W.h1[lane];
             const float bx = (float)wx0 - g1.z, by = (float)wy0 - g1.w;
-            may = ss_box_may_cover(W.h0[lane], g1.x, g1.y, rc2, bx + 0.5f, bx + 7.5f, by + 0.5f, by + 3.5f);
+            // (the per-pixel filter's support is not the centre quadratic's: no block test)
+            may = PP || ss_box_may_cover(W.h0[lane], g1.x, g1.y, rc2, bx + 0.5f, bx + 7.5f, by + 0.5f, by + 3.5f);
         }
         for (uint32_t live = __ballot_sync(0xffffffffu, may); live; live &= live - 1) {
             const int s = __ffs(live) - 1;
             const float4 h0 = W.h0[s], h1 = W.h1[s], h2 = W.h2[s];
-            const ss_hit h = ss_pixel_test(h0, h1, xl - h1.z, yl - h1.w, rc2);
-            bool cg = h.cover && inside;   // geometric coverage (support and cutoff)
+            float rho2, nf;
+            bool cg;
+            if constexpr (PP) {
+                const ss_hit_pp h = ss_pixel_test_pp(h0, h1, xl - h1.z, yl - h1.w, rc2, a.p.sigma_f);
+                rho2 = h.rho2;
+                nf = h.nf;
+                cg = h.cover && inside;
+            } else {
+                const ss_hit h = ss_pixel_test(h0, h1, xl - h1.z, yl - h1.w, rc2);
+                rho2 = __fdividef(h.q, h.t);
+                nf = fabsf(h2.z);
+                cg = h.cover && inside;   // geometric coverage (support and cutoff)
+            }
             if (STATS && inside) {
                 const uint2 rr = make_uint2(__float_as_uint(W.zr[s].z), __float_as_uint(W.zr[s].w));
                 ++n_lane;
@@ -698,8 +722,7 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
             my_mask = lane == s ? cm : my_mask;
             if (cg && !done) {
                 if (STATS) ++n_frag;
-                const float nf = fabsf(h2.z);
-                const float w = nf * __expf(-0.5f * __fdividef(h.q, h.t));   // Eq. mip_weight
+                const float w = nf * __expf(-0.5f * rho2);   // Eq. mip_weight (Eq. mip_eval per pixel)
                 if (Wg > 0.f && h2.x > zmax) flush();                          // gap: new layer
                 if (!done) {
                     zmax = fmaxf(zmax, h2.y);
@@ -756,7 +779,7 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
     }
 }
 
-template <bool STATS, int RWPB_FWD>
+template <bool STATS, bool PP, int RWPB_FWD>
 __global__ void __launch_bounds__(32 * RWPB_FWD, 24 / RWPB_FWD) raster_fwd_kernel(ss_ws_view ws, ss_fwd_args a,
                                                                                   int n_items) {
     extern __shared__ __align__(16) unsigned char fwd_smem[];
@@ -766,33 +789,66 @@ __global__ void __launch_bounds__(32 * RWPB_FWD, 24 / RWPB_FWD) raster_fwd_kerne
         if (lane == 0) item = (int)atomicAdd(ws.work + 0, 1u);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
-        raster_fwd_block<STATS, RWPB_FWD>(ws, a, item, fwd_smem);
+        raster_fwd_block<STATS, PP, RWPB_FWD>(ws, a, item, fwd_smem);
         __syncwarp();
     }
 }
 
-template <bool STATS, int W>
+template <bool STATS, bool PP, int W>
 static void launch_raster_fwd(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st) {
     const int smem = 2 * W * (int)sizeof(ss_wstage);
     static std::atomic<unsigned long long> optin{0}, resident{0};
-    ss_smem_optin(raster_fwd_kernel<STATS, W>, smem, optin);
+    ss_smem_optin(raster_fwd_kernel<STATS, PP, W>, smem, optin);
     const int n_items = (int)(L.total_tiles * 8);
-    const int ctas = ss_resident_ctas(raster_fwd_kernel<STATS, W>, 32 * W, smem, resident);
+    const int ctas = ss_resident_ctas(raster_fwd_kernel<STATS, PP, W>, 32 * W, smem, resident);
     const int grid = max(1, min(ctas > 0 ? ctas : 1, (n_items + W - 1) / W));
-    raster_fwd_kernel<STATS, W><<<grid, 32 * W, smem, st>>>(ws, a, n_items);
+    raster_fwd_kernel<STATS, PP, W><<<grid, 32 * W, smem, st>>>(ws, a, n_items);
+}
+
+template <bool STATS, bool PP>
+static void launch_raster_fwd_w(int w, const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a,
+                                cudaStream_t st) {
+    if (w == 1) launch_raster_fwd<STATS, PP, 1>(ws, L, a, st);
+    else if (w == 2) launch_raster_fwd<STATS, PP, 2>(ws, L, a, st);
+    else launch_raster_fwd<STATS, PP, 4>(ws, L, a, st);
 }
 
 void ss_launch_raster_fwd(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st) {
     if (L.total_tiles <= 0) return;
     ss_note_launch();
     const int w = a.p.fwd_warps ? a.p.fwd_warps : RWPB_FWD_DEFAULT;
+    const bool pp = a.p.mip_mode == 2;
     if (a.p.collect_stats) {
-        if (w == 1) launch_raster_fwd<true, 1>(ws, L, a, st);
-        else if (w == 2) launch_raster_fwd<true, 2>(ws, L, a, st);
-        else launch_raster_fwd<true, 4>(ws, L, a, st);
+        if (pp) launch_raster_fwd_w<true, true>(w, ws, L, a, st);
+        else launch_raster_fwd_w<true, false>(w, ws, L, a, st);
     } else {
-        if (w == 1) launch_raster_fwd<false, 1>(ws, L, a, st);
-        else if (w == 2) launch_raster_fwd<false, 2>(ws, L, a, st);
-        else launch_raster_fwd<false, 4>(ws, L, a, st);
+        if (pp) launch_raster_fwd_w<false, true>(w, ws, L, a, st);
+        else launch_raster_fwd_w<false, false>(w, ws, L, a, st);
     }
+}
+
+// ------------------------------------------------------------------------
+// box filter of an RGBA image by an integer factor (supersampled reference)
+
+__global__ void box_downsample_kernel(const float4* __restrict__ in, int W, int H, int f, float4* __restrict__ out) {
+    const int Wo = W / f, Ho = H / f;
+    const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (o >= (int64_t)Wo * Ho) return;
+    const int xo = (int)(o % Wo), yo = (int)(o / Wo);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int j = 0; j < f; ++j)
+        for (int i = 0; i < f; ++i) {
+            const float4 v = in[(int64_t)(yo * f + j) * W + xo * f + i];
+            acc.x += v.x; acc.y += v.y; acc.z += v.z; acc.w += v.w;
+        }
+    const float k = 1.f / (float)(f * f);
+    out[o] = make_float4(acc.x * k, acc.y * k, acc.z * k, acc.w * k);
+}
+
+void ss_launch_box_downsample(const float* in, int W, int H, int f, float* out, cudaStream_t st) {
+    const int64_t n = (int64_t)(W / f) * (H / f);
+    if (n <= 0) return;
+    ss_note_launch();
+    box_downsample_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<const float4*>(in), W, H, f,
+                                                                       reinterpret_cast<float4*>(out));
 }

@@ -270,6 +270,33 @@ __device__ __forceinline__ ss_hit ss_pixel_test(float4 r0, float4 r1, float dx, 
     return h;
 }
 
+// The per-pixel MIP filter (mip_mode 2, AA-2DGS, Sec. 3.3.1): r0 = J0 =
+// d(u,v)/d(x,y) at the centre; the hit is (u, v) = J0 d / s2, whose Jacobian
+// at d is J = (J0 - (u, v) g^T) / s2 with g = (A2, B2); then
+// Sigma = I + sigma_f J J^T (Eq. mip_cov), rho2 = (u, v) Sigma^-1 (u, v)^T
+// and n_f = |Sigma|^-1/2 (Eq. mip_eval) at this pixel.
+struct ss_hit_pp {
+    float rho2, nf;
+    bool cover;
+};
+__device__ __forceinline__ ss_hit_pp ss_pixel_test_pp(float4 J0, float4 r1, float dx, float dy, float rc2,
+                                                      float sig) {
+    ss_hit_pp h;
+    const float s2 = __fmaf_rn(r1.x, dx, __fmaf_rn(r1.y, dy, 1.f));
+    const float is2 = 1.f / s2;
+    const float u = __fmaf_rn(J0.x, dx, J0.y * dy) * is2, v = __fmaf_rn(J0.z, dx, J0.w * dy) * is2;
+    const float j00 = __fmaf_rn(-u, r1.x, J0.x) * is2, j01 = __fmaf_rn(-u, r1.y, J0.y) * is2;
+    const float j10 = __fmaf_rn(-v, r1.x, J0.z) * is2, j11 = __fmaf_rn(-v, r1.y, J0.w) * is2;
+    const float a = __fmaf_rn(sig, __fmaf_rn(j00, j00, j01 * j01), 1.f);
+    const float b = sig * __fmaf_rn(j00, j10, j01 * j11);
+    const float c = __fmaf_rn(sig, __fmaf_rn(j10, j10, j11 * j11), 1.f);
+    const float D = __fmaf_rn(a, c, -b * b);
+    h.rho2 = __fmaf_rn(c * u, u, __fmaf_rn(-2.f * b * u, v, a * v * v)) / D;
+    h.nf = rsqrtf(D);
+    h.cover = (s2 > 0.f) && (h.rho2 < rc2);
+    return h;
+}
+
 // ------------------------------------------------------------------------
 // host-side launchers implemented in the .cu files
 
@@ -343,6 +370,7 @@ struct ss_fwd_args {
 void ss_launch_project(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st);
 void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st);
 void ss_launch_raster_fwd(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st);
+void ss_launch_box_downsample(const float* in, int W, int H, int f, float* out, cudaStream_t st);
 
 struct ss_bwd_args {
     ss_fwd_args f;

@@ -377,8 +377,10 @@ def _quat_rot(q):
 def brute_force(surf, cam, prm, ch):
     """Independent tiny renderer: per pixel and surfel, intersect the pixel
     ray with the surfel plane by a 3x3 solve, build J by differentiating
-    that intersection numerically at the surfel centre, then group by
-    connected components of depth intervals and composite."""
+    that intersection numerically at the surfel centre (or, for the
+    per-pixel MIP filter, at the pixel), then group by connected components
+    of depth intervals and composite."""
+    sig = 0.0 if prm.mip_mode == "none" else prm.sigma_f
     R = np.asarray(cam.R, np.float32).astype(np.float64)
     t = np.asarray(cam.t, np.float32).astype(np.float64)
     fx, fy, cx, cy = (float(np.float32(v)) for v in (cam.fx, cam.fy, cam.cx, cam.cy))
@@ -400,7 +402,7 @@ def brute_force(surf, cam, prm, ch):
         e = 1e-4
         J = np.array([[(hit(px + e, py)[k] - hit(px - e, py)[k]) / (2 * e) for k in (0, 1)],
                       [(hit(px, py + e)[k] - hit(px, py - e)[k]) / (2 * e) for k in (0, 1)]]).T
-        Sig = np.eye(2) + prm.sigma_f * J @ J.T
+        Sig = np.eye(2) + sig * J @ J.T
         eps = prm.r_cut * math.hypot(tu[2], tv[2])
         # support rectangle: sampled disc boundary U affine EWA ellipse, +1 px
         th = np.linspace(0, 2 * math.pi, 20001)
@@ -408,7 +410,7 @@ def brute_force(surf, cam, prm, ch):
         bx, by = fx * P[:, 0] / P[:, 2] + cx, fy * P[:, 1] / P[:, 2] + cy
         Mj = np.linalg.inv(J)
         MMt = Mj @ Mj.T
-        ex = prm.r_cut * np.sqrt(np.diag(MMt) + prm.sigma_f)
+        ex = prm.r_cut * np.sqrt(np.diag(MMt) + sig)
         rect = (min(bx.min(), px - ex[0]) - 1, max(bx.max(), px + ex[0]) + 1,
                 min(by.min(), py - ex[1]) - 1, max(by.max(), py + ex[1]) + 1)
         geo.append(dict(hit=hit, Sinv=np.linalg.inv(Sig), nf=1 / math.sqrt(np.linalg.det(Sig)),
@@ -430,11 +432,18 @@ def brute_force(surf, cam, prm, ch):
                 if lam <= 0:
                     continue
                 uv = np.array([u, v])
-                rho2 = uv @ g["Sinv"] @ uv
+                Sinv, nf = g["Sinv"], g["nf"]
+                if prm.mip_mode == "pixel":   # J at this pixel, numerically
+                    e = 1e-4
+                    Jp = np.array([[(g["hit"](X + e, Y)[k] - g["hit"](X - e, Y)[k]) / (2 * e) for k in (0, 1)],
+                                   [(g["hit"](X, Y + e)[k] - g["hit"](X, Y - e)[k]) / (2 * e) for k in (0, 1)]]).T
+                    Sg = np.eye(2) + sig * Jp @ Jp.T
+                    Sinv, nf = np.linalg.inv(Sg), 1 / math.sqrt(np.linalg.det(Sg))
+                rho2 = uv @ Sinv @ uv
                 if abs(rho2 - prm.r_cut ** 2) < 1e-6 or min(X - r[0], r[1] - X, Y - r[2], r[3] - Y) < 1e-3:
                     unsure[y * W + x] = True
                 if rho2 < prm.r_cut ** 2:
-                    frs.append((g["zs"], g["ze"], i, g["nf"] * math.exp(-0.5 * rho2)))
+                    frs.append((g["zs"], g["ze"], i, nf * math.exp(-0.5 * rho2)))
             frs.sort(key=lambda f: (f[0], f[2]))
             # connected components of the union of intervals, front to back
             layers = []
@@ -460,10 +469,14 @@ def brute_force(surf, cam, prm, ch):
     return rgba, aov, unsure
 
 
-@pytest.mark.parametrize("seed", [21, 22])
-def test_oracle_matches_brute_force(seed):
+@pytest.mark.parametrize("seed,mip", [(21, "centre"), (22, "centre"), (23, "pixel"), (24, "pixel"), (25, "none")])
+def test_oracle_matches_brute_force(seed, mip):
+    """The oracle against the independent brute-force renderer, for the
+    centre-precomputed MIP filter (the method), the per-pixel Jacobian of
+    the Sec. 4.4.2 ablation (J by finite differences of the 3x3 solve at
+    every pixel) and no filter."""
     rng = np.random.default_rng(seed)
-    prm = M.Params(sigma_f=0.5 if seed == 21 else 1.5)
+    prm = M.Params(sigma_f=0.5 if seed in (21, 23) else 1.5, mip_mode=mip)
     surf = _tiny.random_scene(rng, n=40, spread=0.35, scale=(0.08, 0.2))
     cam = _tiny.front_camera(res=28)
     env = env_state(_tiny.lognormal_env(rng), prm)
@@ -473,7 +486,7 @@ def test_oracle_matches_brute_force(seed):
                     [torch.from_numpy(l) for l in env.levels], torch.from_numpy(env.lut), prm)
     rgba, aov, unsure = brute_force(surf, cam, prm, rec["ch"].detach().numpy())
     ok = ~unsure
-    assert ok.sum() > 0.95 * ok.size and (rgba[:, 3] > 0).sum() > 150
+    assert ok.sum() > 0.95 * ok.size and (rgba[:, 3] > 0).sum() > 100
     np.testing.assert_allclose(out["rgba"][ok], rgba[ok], rtol=1e-6, atol=1e-9)
     np.testing.assert_allclose(out["aov"][ok], aov[ok], rtol=1e-6, atol=1e-9)
 
@@ -533,3 +546,41 @@ def test_gradients_match_finite_differences():
         fd = (loss(surf, env_state(ep, prm)) - loss(surf, env_state(em, prm))) / 2e-5
         an = grads["env"].reshape(-1)[idx]
         assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (idx, fd, an)
+
+
+def test_pixel_mip_equals_centre_mip_for_fronto_parallel_surfels():
+    """A fronto-parallel surfel maps affinely to the screen (its intersection
+    Jacobian is the same at every pixel), so the per-pixel MIP filter equals
+    the centre-precomputed one everywhere (Sec. 3.3.2); tilted surfels make
+    them differ."""
+    rng = np.random.default_rng(41)
+    pos = np.concatenate([rng.uniform(-0.4, 0.4, (30, 2)), rng.uniform(-0.2, 0.2, (30, 1))], 1)
+    surf = _tiny.surfels(pos, scale=rng.uniform(0.02, 0.08, 30), albedo=rng.uniform(0, 1, (30, 3)))
+    cam = _tiny.front_camera(res=24)
+    env = env_state(_tiny.lognormal_env(rng), M.Params())
+    outs = {m: _render(surf, cam, env, M.Params(sigma_f=1.5, mip_mode=m)) for m in ("centre", "pixel")}
+    np.testing.assert_allclose(outs["pixel"]["rgba"], outs["centre"]["rgba"], rtol=1e-10, atol=1e-12)
+    assert (outs["centre"]["rgba"][:, 3] > 0).sum() > 100
+    tilted = _tilt(surf, 1.2)
+    o2 = {m: _render(tilted, cam, env, M.Params(sigma_f=1.5, mip_mode=m)) for m in ("centre", "pixel")}
+    assert np.abs(o2["pixel"]["rgba"] - o2["centre"]["rgba"]).max() > 1e-4
+
+
+def test_no_mip_is_the_unfiltered_unit_kernel():
+    """Without the MIP filter a lone fronto-parallel surfel's weight is
+    exp(-rho^2 / 2) with rho the distance in its tangent frame (n_f = 1), so
+    its coverage at a pixel is 1 - exp(-w) with w known in closed form."""
+    s_ = 0.05
+    surf = _tiny.surfels([[0.0, 0.0, 0.0]], scale=s_)
+    cam = _tiny.front_camera(res=20)
+    env = env_state(_tiny.const_env(1.0), M.Params())
+    out = _render(surf, cam, env, M.Params(mip_mode="none"))
+    f = float(np.float32(cam.fx))
+    cx = float(np.float32(cam.cx))
+    s32 = math.exp(float(np.float32(math.log(s_))))      # the scale as stored (float32 log-scale)
+    x = (np.arange(20) + 0.5 - cx) / f * 3.0 / s32        # tangent-frame coordinates at depth 3
+    U, V = np.meshgrid(x, x, indexing="xy")
+    w = np.exp(-0.5 * (U ** 2 + V ** 2)).ravel()
+    cov = out["rgba"][:, 3]
+    inside = (U ** 2 + V ** 2).ravel() < 9.0 * (1 - 1e-6)
+    np.testing.assert_allclose(cov[inside], 1 - np.exp(-w[inside]), rtol=1e-9, atol=1e-12)
