@@ -437,6 +437,37 @@ def loop_init(n=3_000_000, seed_id=55, env_w=512) -> tuple:
     return _pack(pos, quat, ls, alb, rough, metal), env
 
 
+def checkerboard_plane(n_side=2000, spacing=0.01, cell=0.1, width=800, height=600, supersample=1,
+                       seed_id=6) -> Scene:
+    """A point-sampled checkerboard ground plane receding to the horizon (the
+    MIP-filter ablation's workload, Sec. 4.4.2): n_side^2 surfels on a
+    jittered square grid of the given spacing in the plane y = 0 (x centred,
+    z from 0 to n_side * spacing), normal +y, isotropic scale = spacing,
+    albedo 0.9 / 0.1 in cells of `cell`, roughness 0.5, dielectric; a
+    camera 1 above the plane looking along it (60 degree vertical FOV) sees
+    surfels a few pixels apart in front and ever more minified towards the
+    horizon; constant env 1.  supersample multiplies the resolution and the
+    focal length (the supersampled reference renders the same view at 2x)."""
+    r_geo, r_att, _, _ = rng_streams(seed_id, 4)
+    n = n_side * n_side
+    k = np.arange(n_side, dtype=np.float64)
+    X, Z = np.meshgrid((k - (n_side - 1) / 2.0) * spacing, (k + 0.5) * spacing, indexing="xy")
+    jit = r_geo.uniform(-0.25, 0.25, size=(2, n)) * spacing
+    x, z = X.ravel() + jit[0], Z.ravel() + jit[1]
+    pos = np.stack([x, np.zeros(n), z], 1)
+    nrm = np.tile([0.0, 1.0, 0.0], (n, 1))
+    quat = tangent_quats(nrm, r_att)
+    ls = np.full((n, 2), math.log(spacing))
+    black = ((np.floor(x / cell) + np.floor(z / cell)) % 2) == 0
+    alb = np.where(black[:, None], 0.1, 0.9) * np.ones((1, 3))
+    s = _pack(pos, quat, ls, alb, np.full(n, 0.5), np.zeros(n))
+    env = np.ones((32, 64, 3), np.float32)
+    cam = look_at((0.0, 1.0, -0.5), (0.0, 0.2, 10.0), fov_deg=60.0, width=width * supersample,
+                  height=height * supersample)
+    return Scene(s, np.array([0, n], np.int64), [env], [cam], "checkerboard_plane")
+
+
 def by_name(name: str, **kw) -> Scene:
     return {"sphere_4k": sphere_4k, "torus_sphere_100k": torus_sphere_100k, "displaced_sphere_1m": displaced_sphere_1m,
-            "uneven_scenes": uneven_scenes, "loop_ground_truth": loop_ground_truth}[name](**kw)
+            "uneven_scenes": uneven_scenes, "loop_ground_truth": loop_ground_truth,
+            "checkerboard_plane": checkerboard_plane}[name](**kw)

@@ -9,10 +9,13 @@ RTOL, ATOL, SMALL = 1e-4, 1e-5, 1e-2
 M_CUT, M_GAP, M_BOX = 1e-5, 1e-5, 2e-3
 
 
+MIP_MODES = {0: "centre", 1: "none", 2: "pixel"}
+
+
 def oracle_params(prm) -> M.Params:
     return M.Params(r_cut=float(prm.r_cut), sigma_f=float(prm.sigma_f), gamma=float(prm.gamma),
                     k_max=int(prm.k_max), z_near=float(prm.z_near), bg=tuple(float(b) for b in prm.bg),
-                    lut_n=int(prm.lut_n))
+                    lut_n=int(prm.lut_n), mip_mode=MIP_MODES[int(prm.mip_mode)])
 
 
 def oracle_view(scene, v, prm, env_levels=6, pix=None, G=None, env_cache=None):
