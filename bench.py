@@ -770,7 +770,7 @@ def run_mip(args):
     from paper_2605_05876_gb300 import build, scenes
     build()
     from paper_2605_05876_gb300 import _lib as C
-    from paper_2605_05876_gb300.api import Renderer, _ptr, _stream, launch_count
+    from paper_2605_05876_gb300.api import Renderer, _ptr, _stream, launch_count, profile_begin, profile_end
     from paper_2605_05876_gb300._lib import check, lib
     sc = scenes.checkerboard_plane()
     sc2 = scenes.checkerboard_plane(supersample=2)
@@ -798,7 +798,7 @@ def run_mip(args):
         e1.record(st)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / k
-    res = {}
+    res, stages = {}, {}
     with ClockSampler(torch.cuda.current_device()) as clk:
         n0 = launch_count()
         for name, fn in frames.items():
@@ -806,6 +806,12 @@ def run_mip(args):
                 fn()
             res[name] = timed(fn, args.steps)
         n_launched = launch_count() - n0
+    for name, fn in frames.items():     # stage split (separate, untimed pass)
+        profile_begin()
+        for _ in range(args.steps):
+            fn()
+        st = profile_end()
+        stages[name] = {k: round(v[0] / args.steps, 4) for k, v in st.items() if v[1]}
     for r in list(rs.values()) + [r2]:
         if r.read_status() != 0:
             raise RuntimeError("device status after the frames")
@@ -820,7 +826,7 @@ def run_mip(args):
                                        f"plane receding to the horizon, {W}x{H}, constant env; one frame = "
                                        "projection + shading, binning and sort, forward raster",
                            "inputs_vs_l2": "inputs and intermediates > 129 MB L2 (no flush)"},
-                "variants_ms_per_frame": res,
+                "variants_ms_per_frame": res, "variant_stage_ms": stages,
                 "relative_to_no_mip": {k: v / res["none"] for k, v in res.items()},
                 "paper_ms_per_frame_context": PAPER_MIP_MS,
                 "paper_relative_to_no_mip": {k: v / PAPER_MIP_MS["none"] for k, v in PAPER_MIP_MS.items()},

@@ -180,7 +180,7 @@ static ss_status build_layout(const ss_batch_desc* b, const ss_render_params* p,
 }
 
 struct ws_plan {
-    size_t status, layout, vgeo, rec, rank, tc, ts, tcur, keys, keys_alt, rects, cand, layer, pix, grad, masks,
+    size_t status, layout, vgeo, rec, rank, tc, ts, tcur, keys, keys_alt, bmask, cand, layer, pix, grad, masks,
         mcount, env_acc, jac, total;
     int64_t env_texels;   // irradiance + specular texels of one scene (0: no env-gradient scratch)
 };
@@ -204,7 +204,7 @@ static ws_plan plan_ws(const ss_layout& L, const ss_render_params& p, int with_b
     w.tcur = take(sizeof(uint32_t) * SS_CNT_STRIDE * (size_t)L.total_tiles);
     w.keys = take(sizeof(unsigned long long) * (size_t)p.max_instances);
     w.keys_alt = take(sizeof(unsigned long long) * (size_t)p.max_instances);
-    w.rects = take(sizeof(uint2) * (size_t)p.max_instances);
+    w.bmask = take(sizeof(uint8_t) * (size_t)p.max_instances);
     w.cand = take(sizeof(uint32_t) * 8 * (size_t)p.max_instances);
     if (with_bwd) {
         w.layer = take(sizeof(float) * (size_t)p.k_max * 13 * (size_t)L.total_pixels);
@@ -236,7 +236,7 @@ static ss_ws_view carve(void* ws, const ws_plan& w, const ss_render_params& p, i
     v.tile_cursor = (uint32_t*)(b + w.tcur);
     v.keys = (unsigned long long*)(b + w.keys);
     v.keys_alt = (unsigned long long*)(b + w.keys_alt);
-    v.rects = (uint2*)(b + w.rects);
+    v.bmask = (uint8_t*)(b + w.bmask);
     v.cand_list = (uint32_t*)(b + w.cand);
     v.layer_state = with_bwd ? (float*)(b + w.layer) : nullptr;
     v.pix_state = with_bwd ? (float*)(b + w.pix) : nullptr;

@@ -3,10 +3,12 @@
 //
 // Each warp owns an 8 x 4 pixel block of a 16 x 16 tile and works on its own
 // (no block-wide barrier).  The forward first walks the tile's list 32 keys at
-// a time, reading the support rectangles, and keeps the instances whose
-// rectangle meets its block (ballot + prefix count, so the order by z_start is
-// kept) in a candidate list; the backward reads the forward's list of
-// covering instances.  Either list is then consumed 32 records at a time:
+// a time, reading each instance's block mask (computed once per instance by
+// the sort kernel: support rectangle overlaps the block and the exact support
+// can reach one of its pixel centres), and keeps the instances with its
+// block's bit (ballot + prefix count, so the order by z_start is kept) in a
+// candidate list; the backward reads the forward's list of covering
+// instances.  Either list is then consumed 32 records at a time:
 // the records are copied into shared-memory staging slots with cp.async, two
 // chunks deep in the forward (while the warp works on chunk c, the records of
 // chunk c+1 are in flight into the other buffer).
@@ -41,24 +43,25 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
-// One chunk of up to 32 instances: this lane's record index and support
-// rectangle, read from the tile list and its parallel rectangle list (both
-// coalesced; the sort kernel gathered the rectangles once per instance).
+// One chunk of up to 32 instances: this lane's record index and the
+// instance's block mask (bit b: it may cover a pixel of block b of the tile),
+// read from the tile list and its parallel mask list (both coalesced; the
+// sort kernel computed the masks once per instance).
 struct ss_chunk {
     uint32_t id;
-    uint2 rect;
+    uint32_t bm;
     bool live;
 };
 
-__device__ __forceinline__ ss_chunk fetch_chunk(const unsigned long long* keys, const uint2* rects, int64_t j,
+__device__ __forceinline__ ss_chunk fetch_chunk(const unsigned long long* keys, const uint8_t* bmask, int64_t j,
                                                 int64_t end) {
     ss_chunk c;
     c.live = j < end;
     c.id = 0;
-    c.rect = make_uint2(0xffffu, 0xffffu);   // empty
+    c.bm = 0;
     if (c.live) {
         c.id = (uint32_t)(__ldg(keys + j) & 0xffffffffull);
-        c.rect = __ldg(rects + j);
+        c.bm = __ldg(bmask + j);
     }
     return c;
 }

@@ -228,12 +228,12 @@ __global__ void __launch_bounds__(256, 4) project_kernel(ss_ws_view ws, ss_fwd_a
         if (a.p.mip_mode == 2) {
             // per-pixel MIP filter: the raster needs J0 = M^-1 = d(u,v)/d(x,y) at the
             // centre, adj(M) / det M with det M = sdg (formed from N_d in double-float,
-            // so it stays accurate for nearly edge-on surfels); n_f is per pixel
-            // there (1 marks a valid record), and the exact support is not the
-            // centre quadratic's, so the support rectangle is always tested
+            // so it stays accurate for nearly edge-on surfels), and |det J0| =
+            // 1 / |sdg| in place of n_f (which is per pixel there); the exact support
+            // is not the centre quadratic's, so the support rectangle is always tested
             const float k = 1.f / (cz * sdg);
             rec.r0 = make_float4(fy * by * k, -fx * bx * k, -fy * ay * k, fx * ax * k);
-            rec.r1 = make_float4(A2, B2, 1.f, 1.f);
+            rec.r1 = make_float4(A2, B2, 1.f, 1.f / fabsf(sdg));
             if (valid) flags |= SS_FLAG_RECT_TEST;
         } else {
             rec.r0 = make_float4(P00, P01, P10, P11);
@@ -370,10 +370,41 @@ __global__ void __launch_bounds__(256) scatter_kernel(ss_ws_view ws, int64_t tot
     }
 }
 
-// support rectangle of the record a key refers to
-__device__ __forceinline__ uint2 rect_of(const ss_ws_view& ws, unsigned long long key) {
-    const float4 r3 = __ldg(&ws.rec[(uint32_t)(key & 0xffffffffull)].r3);
-    return make_uint2(__float_as_uint(r3.z), __float_as_uint(r3.w));
+// Block mask of the record a key refers to, in tile (tx, ty): bit b (8 x 4
+// block b = (b & 1, b >> 1) of the 16 x 16 tile) is set when the record's
+// support rectangle overlaps the block and -- except for the per-pixel MIP
+// filter, whose support is not the centre quadratic's -- the exact support
+// can reach one of the block's pixel centres (ss_box_may_cover, with the
+// centre relative to the tile formed exactly as the rasteriser's staging
+// forms it).  The rasterisers stage a record for a block only when its bit is
+// set, so the per-pixel tests they run are unchanged.
+struct ss_tile_box {
+    int x0, y0;        // tile origin (pixels)
+    float rc2;
+    bool exact;        // apply the exact-support test
+};
+__device__ __forceinline__ uint32_t block_mask_of(const ss_ws_view& ws, unsigned long long key, const ss_tile_box& tb) {
+    const ss_rec* rc = ws.rec + (uint32_t)(key & 0xffffffffull);
+    const float4 r3 = __ldg(&rc->r3);
+    const uint32_t rx = __float_as_uint(r3.z), ry = __float_as_uint(r3.w);
+    const int i0 = (int)(rx & 0xffff), i1 = (int)(rx >> 16), j0 = (int)(ry & 0xffff), j1 = (int)(ry >> 16);
+    uint32_t m = 0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const int gx0 = tb.x0 + 8 * (b & 1), gy0 = tb.y0 + 4 * (b >> 1);
+        if (i0 <= gx0 + 7 && i1 >= gx0 && j0 <= gy0 + 3 && j1 >= gy0) m |= 1u << b;
+    }
+    if (m == 0u || !tb.exact) return m;
+    const float4 P = __ldg(&rc->r0), r1 = __ldg(&rc->r1), r2 = __ldg(&rc->r2);
+    const float prx = __fadd_rn(__fsub_rn(r2.x, (float)tb.x0), r2.z);
+    const float pry = __fadd_rn(__fsub_rn(r2.y, (float)tb.y0), r2.w);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        if (!((m >> b) & 1u)) continue;
+        const float bx = (float)(8 * (b & 1)) - prx, by = (float)(4 * (b >> 1)) - pry;
+        if (!ss_box_may_cover(P, r1.x, r1.y, tb.rc2, bx + 0.5f, bx + 7.5f, by + 0.5f, by + 3.5f)) m &= ~(1u << b);
+    }
+    return m;
 }
 
 #define SORT_THREADS 256
@@ -464,10 +495,10 @@ __device__ void merge_runs(const unsigned long long* A, int na, const unsigned l
 
 // Sort one chunk of m keys (N = the power of two >= m, N <= SORT_THREADS * KPL)
 // in registers, KPL per thread, and store it; with `gather`, also write the
-// rectangles of the sorted keys.
+// block masks of the sorted keys.
 template <int KPL>
-__device__ __noinline__ void sort_chunk(const ss_ws_view& ws, unsigned long long* K, uint2* RC, int m, int N,
-                                           bool gather, unsigned long long* xs) {
+__device__ __noinline__ void sort_chunk(const ss_ws_view& ws, unsigned long long* K, uint8_t* BM, int m, int N,
+                                           bool gather, const ss_tile_box& tb, unsigned long long* xs) {
     const int base = threadIdx.x * KPL;
     unsigned long long x[KPL];
 #pragma unroll
@@ -478,22 +509,15 @@ __device__ __noinline__ void sort_chunk(const ss_ws_view& ws, unsigned long long
     for (int k = 0; k < KPL; ++k)
         if (base + k < m) K[base + k] = x[k];
     if (gather) {
-        constexpr int G = KPL < 8 ? KPL : 8;   // gathers in flight
-#pragma unroll
-        for (int k0 = 0; k0 < KPL; k0 += G) {
-            uint2 rr[G];
-#pragma unroll
-            for (int k = 0; k < G; ++k)
-                if (base + k0 + k < m) rr[k] = rect_of(ws, x[k0 + k]);
-#pragma unroll
-            for (int k = 0; k < G; ++k)
-                if (base + k0 + k < m) RC[base + k0 + k] = rr[k];
-        }
+#pragma unroll 4
+        for (int k = 0; k < KPL; ++k)
+            if (base + k < m) BM[base + k] = (uint8_t)block_mask_of(ws, x[k], tb);
     }
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view ws, int total_tiles) {
+__global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view ws, int total_tiles, float rc2,
+                                                                    int exact) {
     extern __shared__ unsigned long long xs[];
     const int t = blockIdx.x;
     const int64_t cap = ws.max_instances;
@@ -502,9 +526,19 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view w
     if (b >= e) return;
     const int n = (int)(e - b);
     unsigned long long* K = ws.keys + b;
-    uint2* RC = ws.rects + b;
+    uint8_t* BM = ws.bmask + b;
+    ss_tile_box tb;
+    {
+        const ss_layout* L = ws.layout;
+        const ss_view_layout& vl = L->v[find_view_tile(L, t)];
+        const int lt = t - vl.tile_off;
+        tb.x0 = (lt % vl.tiles_x) * SS_TILE;
+        tb.y0 = (lt / vl.tiles_x) * SS_TILE;
+        tb.rc2 = rc2;
+        tb.exact = exact != 0;
+    }
     if (n == 1) {
-        if (threadIdx.x == 0) RC[0] = rect_of(ws, K[0]);
+        if (threadIdx.x == 0) BM[0] = (uint8_t)block_mask_of(ws, K[0], tb);
         return;
     }
     unsigned long long* Alt = ws.keys_alt + b;
@@ -515,10 +549,10 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view w
         int N = 2;
         while (N < m) N <<= 1;
         const bool gather = n <= SORT_CAP;
-        if (N <= SORT_THREADS * 4) sort_chunk<4>(ws, K + c0, RC + c0, m, N, gather, xs);
-        else if (N <= SORT_THREADS * 8) sort_chunk<8>(ws, K + c0, RC + c0, m, N, gather, xs);
-        else if (N <= SORT_THREADS * 16) sort_chunk<16>(ws, K + c0, RC + c0, m, N, gather, xs);
-        else sort_chunk<SORT_KPL>(ws, K + c0, RC + c0, m, N, gather, xs);
+        if (N <= SORT_THREADS * 4) sort_chunk<4>(ws, K + c0, BM + c0, m, N, gather, tb, xs);
+        else if (N <= SORT_THREADS * 8) sort_chunk<8>(ws, K + c0, BM + c0, m, N, gather, tb, xs);
+        else if (N <= SORT_THREADS * 16) sort_chunk<16>(ws, K + c0, BM + c0, m, N, gather, tb, xs);
+        else sort_chunk<SORT_KPL>(ws, K + c0, BM + c0, m, N, gather, tb, xs);
     }
     if (n <= SORT_CAP) return;
     // pairwise merges in global memory, ping-pong between K and Alt
@@ -540,12 +574,11 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view w
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const unsigned long long k = src[i];
         if (src != K) K[i] = k;
-        RC[i] = rect_of(ws, k);
+        BM[i] = (uint8_t)block_mask_of(ws, k, tb);
     }
 }
 
 void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st) {
-    (void)a;
     ss_note_launch();
     scan_kernel<<<1, 1024, 0, st>>>(ws.tile_count, ws.tile_cursor, ws.tile_start, L.total_tiles, ws.status,
                                     ws.max_instances,
@@ -557,7 +590,8 @@ void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_a
     static std::atomic<unsigned long long> optin{0};
     ss_smem_optin(tile_sort_kernel, SORT_CAP * (int)sizeof(unsigned long long), optin);
     ss_note_launch();
-    tile_sort_kernel<<<L.total_tiles, SORT_THREADS, SORT_CAP * sizeof(unsigned long long), st>>>(ws, L.total_tiles);
+    tile_sort_kernel<<<L.total_tiles, SORT_THREADS, SORT_CAP * sizeof(unsigned long long), st>>>(
+        ws, L.total_tiles, a.p.r_cut * a.p.r_cut, a.p.mip_mode == 2 ? 0 : 1);
 }
 
 // ------------------------------------------------------------------------
@@ -586,7 +620,6 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
     const int lx = wx0 + (lane & 7), ly = wy0 + (lane >> 3);
     const int px = x0 + lx, py = y0 + ly;
     const bool inside = px < vl.width && py < vl.height;
-    const int gx0 = x0 + wx0, gx1 = gx0 + 7, gy0 = y0 + wy0, gy1 = gy0 + 3;
     const float xl = (float)lx + 0.5f, yl = (float)ly + 0.5f;
     const float rc2 = a.p.r_cut * a.p.r_cut;
     const float kw = a.p.gamma * (0.5f / SS_PI_F);
@@ -651,15 +684,10 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
     for (int64_t j0 = beg; j0 < end; j0 += 128) {
         ss_chunk c[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) c[u] = fetch_chunk(ws.keys, ws.rects, j0 + 32 * u + lane, end);
+        for (int u = 0; u < 4; ++u) c[u] = fetch_chunk(ws.keys, ws.bmask, j0 + 32 * u + lane, end);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            bool ov = false;
-            if (c[u].live) {
-                const uint32_t rx = c[u].rect.x, ry = c[u].rect.y;
-                ov = (int)(rx & 0xffff) <= gx1 && (int)(rx >> 16) >= gx0 && (int)(ry & 0xffff) <= gy1 &&
-                     (int)(ry >> 16) >= gy0;
-            }
+            const bool ov = c[u].live && ((c[u].bm >> warp) & 1u);
             const uint32_t m = __ballot_sync(0xffffffffu, ov);
             if (ov) cand[n_cand + __popc(m & ((1u << lane) - 1u))] = c[u].id;
             n_cand += __popc(m);
@@ -685,21 +713,14 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
             asm volatile("prefetch.global.L2 [%0];\n" ::"l"(pr + sizeof(ss_rec) - 1));
         }
         uint32_t my_mask = 0;
-        // staged surfels whose exact support can reach a pixel centre of the block
-        bool may = false;
-        if (lane < n) {
-            const float4 g1 = W.h1[lane];
-            const float bx = (float)wx0 - g1.z, by = (float)wy0 - g1.w;
-            // (the per-pixel filter's support is not the centre quadratic's: no block test)
-            may = PP || ss_box_may_cover(W.h0[lane], g1.x, g1.y, rc2, bx + 0.5f, bx + 7.5f, by + 0.5f, by + 3.5f);
-        }
-        for (uint32_t live = __ballot_sync(0xffffffffu, may); live; live &= live - 1) {
+        // (every candidate may reach a pixel centre of the block: its block bit is set)
+        for (uint32_t live = n >= 32 ? 0xffffffffu : ((1u << n) - 1u); live; live &= live - 1) {
             const int s = __ffs(live) - 1;
             const float4 h0 = W.h0[s], h1 = W.h1[s], h2 = W.h2[s];
             float rho2, nf;
             bool cg;
             if constexpr (PP) {
-                const ss_hit_pp h = ss_pixel_test_pp(h0, h1, xl - h1.z, yl - h1.w, rc2, a.p.sigma_f);
+                const ss_hit_pp h = ss_pixel_test_pp(h0, h1, fabsf(h2.z), xl - h1.z, yl - h1.w, rc2, a.p.sigma_f);
                 rho2 = h.rho2;
                 nf = h.nf;
                 cg = h.cover && inside;

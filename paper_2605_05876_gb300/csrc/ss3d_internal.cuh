@@ -97,7 +97,9 @@ struct ss_ws_view {
     uint4* inst_rank;       // [total_records] rank of the record in the bins of its first four tiles
     unsigned long long* keys;      // [max_instances]
     unsigned long long* keys_alt;  // [max_instances]
-    uint2* rects;           // [max_instances] support rectangle of each sorted instance
+    uint8_t* bmask;         // [max_instances] per sorted instance: bit b set iff the instance may cover a pixel
+                            // centre of 8 x 4 block b of its tile (support rectangle overlaps the block and
+                            // the exact support's minimum over the block's pixel centres is below the cutoff)
     uint32_t* cand_list;    // [8 x max_instances] per (tile, block): records whose rectangle meets the block
     float* layer_state;     // [k_max][13][total_pixels]  (raw C (12), W)
     float* pix_state;       // [2][total_pixels]  (K as float bits, T_end)
@@ -271,27 +273,35 @@ __device__ __forceinline__ ss_hit ss_pixel_test(float4 r0, float4 r1, float dx, 
 }
 
 // The per-pixel MIP filter (mip_mode 2, AA-2DGS, Sec. 3.3.1): r0 = J0 =
-// d(u,v)/d(x,y) at the centre; the hit is (u, v) = J0 d / s2, whose Jacobian
-// at d is J = (J0 - (u, v) g^T) / s2 with g = (A2, B2); then
-// Sigma = I + sigma_f J J^T (Eq. mip_cov), rho2 = (u, v) Sigma^-1 (u, v)^T
-// and n_f = |Sigma|^-1/2 (Eq. mip_eval) at this pixel.
+// d(u,v)/d(x,y) at the centre, |det J0| (= 1 / |det M|) in the staged n_f
+// slot; the hit is (u, v) = J0 d / s2, whose Jacobian at d is
+// J = (J0 - (u, v) g^T) / s2 with g = (A2, B2); then Sigma = I + sigma_f J J^T
+// (Eq. mip_cov) and n_f = |Sigma|^-1/2 (Eq. mip_eval) at this pixel.  Nearly
+// edge-on surfels have a huge J, so the forms used are free of cancellation:
+//   |Sigma| = 1 + sigma_f |J|_F^2 + sigma_f^2 det(J)^2,  det J = det J0 / s2^3
+//     (det(J0 - x g^T) = det J0 (1 - g^T J0^-1 x) and J0^-1 (u, v) = d / s2),
+//   (u, v) adj(Sigma) (u, v)^T = |(u, v)|^2 + sigma_f |J^T (-v, u)|^2
+//     (adj(Sigma) = (1 + sigma_f tr S) I - sigma_f S with S = J J^T, and
+//      tr(S) |x|^2 - |J^T x|^2 = |J^T x_perp|^2 in two dimensions),
+// so rho2 = the second over the first, both sums of non-negative terms.
 struct ss_hit_pp {
     float rho2, nf;
     bool cover;
 };
-__device__ __forceinline__ ss_hit_pp ss_pixel_test_pp(float4 J0, float4 r1, float dx, float dy, float rc2,
-                                                      float sig) {
+__device__ __forceinline__ ss_hit_pp ss_pixel_test_pp(float4 J0, float4 r1, float detJ0, float dx, float dy,
+                                                      float rc2, float sig) {
     ss_hit_pp h;
     const float s2 = __fmaf_rn(r1.x, dx, __fmaf_rn(r1.y, dy, 1.f));
     const float is2 = 1.f / s2;
     const float u = __fmaf_rn(J0.x, dx, J0.y * dy) * is2, v = __fmaf_rn(J0.z, dx, J0.w * dy) * is2;
     const float j00 = __fmaf_rn(-u, r1.x, J0.x) * is2, j01 = __fmaf_rn(-u, r1.y, J0.y) * is2;
     const float j10 = __fmaf_rn(-v, r1.x, J0.z) * is2, j11 = __fmaf_rn(-v, r1.y, J0.w) * is2;
-    const float a = __fmaf_rn(sig, __fmaf_rn(j00, j00, j01 * j01), 1.f);
-    const float b = sig * __fmaf_rn(j00, j10, j01 * j11);
-    const float c = __fmaf_rn(sig, __fmaf_rn(j10, j10, j11 * j11), 1.f);
-    const float D = __fmaf_rn(a, c, -b * b);
-    h.rho2 = __fmaf_rn(c * u, u, __fmaf_rn(-2.f * b * u, v, a * v * v)) / D;
+    const float dJ = detJ0 * is2 * is2 * is2;
+    const float fro = __fmaf_rn(j00, j00, __fmaf_rn(j01, j01, __fmaf_rn(j10, j10, j11 * j11)));
+    const float D = __fmaf_rn(sig * sig, dJ * dJ, __fmaf_rn(sig, fro, 1.f));
+    const float p0 = __fmaf_rn(u, j10, -v * j00), p1 = __fmaf_rn(u, j11, -v * j01);   // J^T (-v, u)
+    const float num = __fmaf_rn(u, u, __fmaf_rn(v, v, sig * __fmaf_rn(p0, p0, p1 * p1)));
+    h.rho2 = num / D;
     h.nf = rsqrtf(D);
     h.cover = (s2 > 0.f) && (h.rho2 < rc2);
     return h;
