@@ -71,6 +71,10 @@ class Params:
     # AA-2DGS (Sec. 3.3.1), Sigma_mip and n_f at every hit (the Sec. 4.4.2
     # ablation)
     mip_mode: str = "centre"
+    # the depth-consolidation term of Eq. cons_loss (Sec. 3.7.1) as a tenth
+    # AOV column: per pixel, over its composited layers,
+    # sum_{i<j} w_i w_j |z_i - z_j| + sum_i w_i^2 sigma_i^2
+    cons: bool = False
 
     def sigma_eff(self) -> float:
         return 0.0 if self.mip_mode == "none" else self.sigma_f
@@ -597,7 +601,21 @@ def composite(rec: dict, fr: Fragments, W: int, prm: Params, per_frag: dict | No
     bg = torch.tensor(prm.bg, dtype=F64)
     rgb = out[:, :3] + T_end[:, None] * bg
     rgba = torch.cat([rgb, (1.0 - T_end)[:, None]], 1)                # soft silhouette (Sec. 3.5.2)
-    return rgba, out[:, 3:]
+    if not prm.cons:
+        return rgba, out[:, 3:]
+    # Eq. cons_loss: w_i = T_i alpha_i, z_i the layer's mean depth (Shepard mean
+    # of the fragments' depths, the depth channel), sigma_i^2 its variance
+    # (Shepard-weighted mean of (z - z_i)^2 over the layer's fragments)
+    z_f = fv("ch")[:, 11]
+    zbar = torch.where(present, Ck[..., 11] / Wsafe, torch.zeros_like(Wsafe))          # [P, Kq]
+    dev2 = w * (z_f - zbar[row_t, layer]) ** 2
+    var = torch.zeros(P * Kq, dtype=F64).index_add(0, key, dev2).reshape(P, Kq) / Wsafe
+    wl = torch.where(present, wgt, torch.zeros_like(wgt))
+    pair = wl[:, :, None] * wl[:, None, :] * torch.abs(zbar[:, :, None] - zbar[:, None, :])
+    upper = torch.triu(torch.ones(Kq, Kq, dtype=torch.bool), diagonal=1)
+    inter = (pair * upper).sum((1, 2))
+    intra = (wl ** 2 * torch.where(present, var, torch.zeros_like(var))).sum(1)
+    return rgba, torch.cat([out[:, 3:], (inter + intra)[:, None]], 1)
 
 
 def lookup_margins(S: dict, cam: dict, env_shape, prm: Params) -> np.ndarray:

@@ -374,7 +374,7 @@ def _quat_rot(q):
                      [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
 
 
-def brute_force(surf, cam, prm, ch):
+def brute_force(surf, cam, prm, ch, cons=False):
     """Independent tiny renderer: per pixel and surfel, intersect the pixel
     ray with the surfel plane by a 3x3 solve, build J by differentiating
     that intersection numerically at the surfel centre (or, for the
@@ -418,6 +418,7 @@ def brute_force(surf, cam, prm, ch):
     rgba = np.zeros((W * H, 4))
     aov = np.zeros((W * H, 9))
     unsure = np.zeros(W * H, bool)
+    cons_out = np.zeros(W * H)
     for y in range(H):
         for x in range(W):
             X, Y = x + 0.5, y + 0.5
@@ -455,6 +456,7 @@ def brute_force(surf, cam, prm, ch):
                     layers.append(dict(zmax=f[1], f=[f]))
             Tb = 1.0
             out = np.zeros(12)
+            lw, lz, lv = [], [], []
             for L in layers[:prm.k_max]:
                 Wk = sum(f[3] for f in L["f"])
                 C = sum(f[3] * ch[f[2]] for f in L["f"])
@@ -462,10 +464,21 @@ def brute_force(surf, cam, prm, ch):
                 Ch[8:11] = C[8:11] / np.linalg.norm(C[8:11])
                 al = 1 - math.exp(-prm.gamma * Wk / (2 * math.pi))
                 out += Tb * al * Ch
+                # centre depth of each fragment: the middle of its depth interval
+                zc = [0.5 * (f[0] + f[1]) for f in L["f"]]
+                zm = sum(f[3] * z for f, z in zip(L["f"], zc)) / Wk
+                lw.append(Tb * al)
+                lz.append(zm)
+                lv.append(sum(f[3] * (z - zm) ** 2 for f, z in zip(L["f"], zc)) / Wk)
                 Tb *= 1 - al
+            cons_out[y * W + x] = (sum(lw[i] * lw[j] * abs(lz[i] - lz[j]) for i in range(len(lw))
+                                       for j in range(i + 1, len(lw)))
+                                   + sum(a * a * v for a, v in zip(lw, lv)))
             rgba[y * W + x, :3] = out[:3] + Tb * np.asarray(prm.bg)
             rgba[y * W + x, 3] = 1 - Tb
             aov[y * W + x] = out[3:]
+    if cons:
+        return rgba, aov, unsure, cons_out
     return rgba, aov, unsure
 
 
