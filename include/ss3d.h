@@ -145,6 +145,15 @@ typedef struct ss_render_params {
                                 intersection (AA-2DGS, Sec. 3.3.1; the Sec. 4.4.2 ablation): Sigma_mip
                                 = I + sigma_f J J^T and n_f evaluated at every hit.  Mode 2 is
                                 forward-only: ss_render_backward returns SS_ERR_INVALID_ARG */
+    int32_t cons;            /* 1: depth-consolidation term of Eq. cons_loss (Sec. 3.7.1): the
+                                forward writes per pixel, over its composited layers,
+                                sum_{i<j} w_i w_j |z_i - z_j| + sum_i w_i^2 sigma_i^2 (w_i = T_i alpha_i,
+                                z_i / sigma_i^2 the mean / variance of the layer's fragment depths,
+                                the depth channel) as a tenth AOV plane, so out_aov is [10][P]
+                                (write_aov must be 1); the backward then requires d_aov [10][P]
+                                whose tenth plane is the upstream gradient of that term.  Not with
+                                mip_mode 2.  The workspace keeps 3 more floats per pixel layer */
+    int32_t pad_;
 } ss_render_params;
 
 /* Work counters of the last forward/backward pair (collect_stats = 1). */

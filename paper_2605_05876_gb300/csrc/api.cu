@@ -98,6 +98,8 @@ static ss_status check_knobs(const ss_render_params* p) {
     if (!(p->pbwd_block == 0 || (p->pbwd_block >= 32 && p->pbwd_block <= 1024))) return SS_ERR_INVALID_ARG;
     if (p->screen_grad != 0 && p->screen_grad != 1) return SS_ERR_INVALID_ARG;
     if (p->mip_mode < 0 || p->mip_mode > 2) return SS_ERR_INVALID_ARG;
+    if (p->cons != 0 && p->cons != 1) return SS_ERR_INVALID_ARG;
+    if (p->cons && (p->mip_mode == 2 || !p->write_aov)) return SS_ERR_INVALID_ARG;
     return SS_OK;
 }
 
@@ -180,7 +182,7 @@ static ss_status build_layout(const ss_batch_desc* b, const ss_render_params* p,
 }
 
 struct ws_plan {
-    size_t status, layout, vgeo, rec, rank, tc, ts, tcur, keys, keys_alt, bmask, cand, layer, pix, grad, masks,
+    size_t status, layout, vgeo, rec, rank, rbm, tc, ts, tcur, keys, keys_alt, bmask, cand, layer, pix, grad, masks,
         mcount, env_acc, jac, total;
     int64_t env_texels;   // irradiance + specular texels of one scene (0: no env-gradient scratch)
 };
@@ -199,6 +201,7 @@ static ws_plan plan_ws(const ss_layout& L, const ss_render_params& p, int with_b
     w.vgeo = take(sizeof(ss_view_geo) * SS_MAX_VIEWS);
     w.rec = take(sizeof(ss_rec) * (size_t)L.total_records);
     w.rank = take(sizeof(uint4) * (size_t)L.total_records);
+    w.rbm = take(sizeof(uint2) * (size_t)L.total_records);
     w.tc = take(sizeof(uint32_t) * SS_CNT_STRIDE * (size_t)L.total_tiles);
     w.ts = take(sizeof(uint32_t) * ((size_t)L.total_tiles + 1));
     w.tcur = take(sizeof(uint32_t) * SS_CNT_STRIDE * (size_t)L.total_tiles);
@@ -207,7 +210,7 @@ static ws_plan plan_ws(const ss_layout& L, const ss_render_params& p, int with_b
     w.bmask = take(sizeof(uint8_t) * (size_t)p.max_instances);
     w.cand = take(sizeof(uint32_t) * 8 * (size_t)p.max_instances);
     if (with_bwd) {
-        w.layer = take(sizeof(float) * (size_t)p.k_max * 13 * (size_t)L.total_pixels);
+        w.layer = take(sizeof(float) * (size_t)p.k_max * (p.cons ? 16 : 13) * (size_t)L.total_pixels);
         w.pix = take(sizeof(float) * 2 * (size_t)L.total_pixels);
         w.grad = take(sizeof(float) * SS_NGRAD * (size_t)L.total_records);
         w.masks = take(sizeof(uint2) * 8 * (size_t)p.max_instances);
@@ -231,6 +234,7 @@ static ss_ws_view carve(void* ws, const ws_plan& w, const ss_render_params& p, i
     v.vgeo = (ss_view_geo*)(b + w.vgeo);
     v.rec = (ss_rec*)(b + w.rec);
     v.inst_rank = (uint4*)(b + w.rank);
+    v.rec_bmask = (uint2*)(b + w.rbm);
     v.tile_count = (uint32_t*)(b + w.tc);
     v.tile_start = (uint32_t*)(b + w.ts);
     v.tile_cursor = (uint32_t*)(b + w.tcur);
@@ -239,6 +243,7 @@ static ss_ws_view carve(void* ws, const ws_plan& w, const ss_render_params& p, i
     v.bmask = (uint8_t*)(b + w.bmask);
     v.cand_list = (uint32_t*)(b + w.cand);
     v.layer_state = with_bwd ? (float*)(b + w.layer) : nullptr;
+    v.ls_rows = p.cons ? 16 : 13;
     v.pix_state = with_bwd ? (float*)(b + w.pix) : nullptr;
     v.grad_rec = with_bwd ? (float*)(b + w.grad) : nullptr;
     v.cover_list = with_bwd ? (uint2*)(b + w.masks) : nullptr;
@@ -459,6 +464,7 @@ extern "C" ss_status ss_render_backward(const ss_batch_desc* b, const ss_surfels
     // the densification statistic needs its per-record scratch in the workspace
     if ((g->screen_grad_norm || g->screen_grad_views) && !p->screen_grad) return SS_ERR_INVALID_ARG;
     if (p->mip_mode == 2) return SS_ERR_INVALID_ARG;   // the per-pixel MIP filter is forward-only
+    if (p->cons && !d_aov_dev) return SS_ERR_INVALID_ARG;   // its upstream gradient is d_aov's tenth plane
     if (p->write_aov && d_aov_dev && !out_aov_dev) return SS_ERR_INVALID_ARG;
     ss_layout L;   // on the stack: entry points may be called from several threads
     e = build_layout(b, p, &L);

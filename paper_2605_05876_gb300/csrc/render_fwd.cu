@@ -324,11 +324,58 @@ __global__ void __launch_bounds__(1024) scan_kernel(const uint32_t* cnt, const u
     }
 }
 
+// Block masks.  For an instance of a record in a tile, bit b (8 x 4 block
+// b = (b & 1, b >> 1) of the 16 x 16 tile) is set when the record's support
+// rectangle overlaps the block and -- except for the per-pixel MIP filter,
+// whose support is not the centre quadratic's -- the exact support can reach
+// one of the block's pixel centres (ss_box_may_cover, with the centre relative
+// to the tile formed exactly as the rasteriser's staging forms it).  The
+// rasterisers stage a record for a block only when its bit is set, so the
+// per-pixel tests they run are unchanged.  The scatter kernel, which streams
+// the records, computes the masks of each record's first four tiles; the sort
+// kernel reads them back for the sorted instances (instances past a record's
+// fourth tile keep the rectangle test alone).
+__device__ __forceinline__ uint32_t rect_block_bits(uint32_t rx, uint32_t ry, int x0, int y0) {
+    const int i0 = (int)(rx & 0xffff), i1 = (int)(rx >> 16), j0 = (int)(ry & 0xffff), j1 = (int)(ry >> 16);
+    uint32_t m = 0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const int gx0 = x0 + 8 * (b & 1), gy0 = y0 + 4 * (b >> 1);
+        if (i0 <= gx0 + 7 && i1 >= gx0 && j0 <= gy0 + 3 && j1 >= gy0) m |= 1u << b;
+    }
+    return m;
+}
+
+__device__ __forceinline__ uint32_t exact_block_bits(uint32_t m, float4 P, float4 r1, float4 r2, int x0, int y0,
+                                                     float rc2) {
+    const float prx = __fadd_rn(__fsub_rn(r2.x, (float)x0), r2.z);
+    const float pry = __fadd_rn(__fsub_rn(r2.y, (float)y0), r2.w);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        if (!((m >> b) & 1u)) continue;
+        const float bx = (float)(8 * (b & 1)) - prx, by = (float)(4 * (b >> 1)) - pry;
+        if (!ss_box_may_cover(P, r1.x, r1.y, rc2, bx + 0.5f, bx + 7.5f, by + 0.5f, by + 3.5f)) m &= ~(1u << b);
+    }
+    return m;
+}
+
+// the block mask of a sorted instance (key) in tile (x0, y0): from the
+// scatter's per-record masks, or the rectangle test past the fourth tile
+__device__ __forceinline__ uint32_t block_mask_of(const ss_ws_view& ws, unsigned long long key, int x0, int y0) {
+    const uint32_t r = (uint32_t)(key & 0xffffffffull);
+    const uint2 bm = __ldg(ws.rec_bmask + r);
+    const int tx0 = (int)(bm.y & 0xfff), ty0 = (int)((bm.y >> 12) & 0xfff), ntx = (int)(bm.y >> 24);
+    const int q = (y0 / SS_TILE - ty0) * ntx + (x0 / SS_TILE - tx0);
+    if (q < 4) return (bm.x >> (8 * q)) & 0xffu;
+    const float4 r3 = __ldg(&ws.rec[r].r3);
+    return rect_block_bits(__float_as_uint(r3.z), __float_as_uint(r3.w), x0, y0);
+}
+
 // One thread per record: its keys go to the bins of the tiles its support
 // rectangle covers, at the ranks the projection took in the bins of its
 // first four tiles; instances past those take positions behind the first-
 // four instances of their bin by counting the bin's cursor down.
-__global__ void __launch_bounds__(256) scatter_kernel(ss_ws_view ws, int64_t total_records) {
+__global__ void __launch_bounds__(256) scatter_kernel(ss_ws_view ws, int64_t total_records, float rc2, int exact) {
     const ss_layout* L = ws.layout;
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= total_records) return;
@@ -336,6 +383,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(ss_ws_view ws, int64_t tot
     const float4 r3 = ws.rec[r].r3;
     const uint4 rk = ws.inst_rank[r];
     if (!(flags & SS_FLAG_VALID)) return;
+    const float4 P = ws.rec[r].r0, r1 = ws.rec[r].r1, r2 = ws.rec[r].r2;
     int v = 0;
     {
         int lo = 0, hi = L->n_views - 1;
@@ -355,56 +403,25 @@ __global__ void __launch_bounds__(256) scatter_kernel(ss_ws_view ws, int64_t tot
     // belongs to one view, are broken by surfel index all the same)
     const unsigned long long key = ((unsigned long long)__float_as_uint(r3.x) << 32) | (uint32_t)r;
     const uint32_t rks[4] = {rk.x, rk.y, rk.z, rk.w};
+    uint32_t masks = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q)
         if (q < nt) {
-            const int t = vl.tile_off + (ty0 + q / ntx) * vl.tiles_x + tx0 + q % ntx;
+            const int tx = tx0 + q % ntx, ty = ty0 + q / ntx;
+            const int t = vl.tile_off + ty * vl.tiles_x + tx;
             const uint64_t p = (uint64_t)ws.tile_start[t] + rks[q];
             if ((int64_t)p < ws.max_instances) ws.keys[p] = key;
+            uint32_t m = rect_block_bits(rx, ry, tx * SS_TILE, ty * SS_TILE);
+            if (exact && m) m = exact_block_bits(m, P, r1, r2, tx * SS_TILE, ty * SS_TILE, rc2);
+            masks |= m << (8 * q);
         }
+    ws.rec_bmask[r] = make_uint2(masks, (uint32_t)tx0 | ((uint32_t)ty0 << 12) | ((uint32_t)min(ntx, 255) << 24));
     for (int q = 4; q < nt; ++q) {
         const int t = vl.tile_off + (ty0 + q / ntx) * vl.tiles_x + tx0 + q % ntx;
         const uint32_t k = atomicSub(&ws.tile_cursor[(size_t)t * SS_CNT_STRIDE], 1u) - 1u;
         const uint64_t p = (uint64_t)ws.tile_start[t] + ws.tile_count[(size_t)t * SS_CNT_STRIDE] + k;
         if ((int64_t)p < ws.max_instances) ws.keys[p] = key;
     }
-}
-
-// Block mask of the record a key refers to, in tile (tx, ty): bit b (8 x 4
-// block b = (b & 1, b >> 1) of the 16 x 16 tile) is set when the record's
-// support rectangle overlaps the block and -- except for the per-pixel MIP
-// filter, whose support is not the centre quadratic's -- the exact support
-// can reach one of the block's pixel centres (ss_box_may_cover, with the
-// centre relative to the tile formed exactly as the rasteriser's staging
-// forms it).  The rasterisers stage a record for a block only when its bit is
-// set, so the per-pixel tests they run are unchanged.
-struct ss_tile_box {
-    int x0, y0;        // tile origin (pixels)
-    float rc2;
-    bool exact;        // apply the exact-support test
-};
-__device__ __forceinline__ uint32_t block_mask_of(const ss_ws_view& ws, unsigned long long key, const ss_tile_box& tb) {
-    const ss_rec* rc = ws.rec + (uint32_t)(key & 0xffffffffull);
-    const float4 r3 = __ldg(&rc->r3);
-    const uint32_t rx = __float_as_uint(r3.z), ry = __float_as_uint(r3.w);
-    const int i0 = (int)(rx & 0xffff), i1 = (int)(rx >> 16), j0 = (int)(ry & 0xffff), j1 = (int)(ry >> 16);
-    uint32_t m = 0;
-#pragma unroll
-    for (int b = 0; b < 8; ++b) {
-        const int gx0 = tb.x0 + 8 * (b & 1), gy0 = tb.y0 + 4 * (b >> 1);
-        if (i0 <= gx0 + 7 && i1 >= gx0 && j0 <= gy0 + 3 && j1 >= gy0) m |= 1u << b;
-    }
-    if (m == 0u || !tb.exact) return m;
-    const float4 P = __ldg(&rc->r0), r1 = __ldg(&rc->r1), r2 = __ldg(&rc->r2);
-    const float prx = __fadd_rn(__fsub_rn(r2.x, (float)tb.x0), r2.z);
-    const float pry = __fadd_rn(__fsub_rn(r2.y, (float)tb.y0), r2.w);
-#pragma unroll
-    for (int b = 0; b < 8; ++b) {
-        if (!((m >> b) & 1u)) continue;
-        const float bx = (float)(8 * (b & 1)) - prx, by = (float)(4 * (b >> 1)) - pry;
-        if (!ss_box_may_cover(P, r1.x, r1.y, tb.rc2, bx + 0.5f, bx + 7.5f, by + 0.5f, by + 3.5f)) m &= ~(1u << b);
-    }
-    return m;
 }
 
 #define SORT_THREADS 256
@@ -498,7 +515,7 @@ __device__ void merge_runs(const unsigned long long* A, int na, const unsigned l
 // block masks of the sorted keys.
 template <int KPL>
 __device__ __noinline__ void sort_chunk(const ss_ws_view& ws, unsigned long long* K, uint8_t* BM, int m, int N,
-                                           bool gather, const ss_tile_box& tb, unsigned long long* xs) {
+                                           bool gather, int x0, int y0, unsigned long long* xs) {
     const int base = threadIdx.x * KPL;
     unsigned long long x[KPL];
 #pragma unroll
@@ -509,15 +526,22 @@ __device__ __noinline__ void sort_chunk(const ss_ws_view& ws, unsigned long long
     for (int k = 0; k < KPL; ++k)
         if (base + k < m) K[base + k] = x[k];
     if (gather) {
-#pragma unroll 4
-        for (int k = 0; k < KPL; ++k)
-            if (base + k < m) BM[base + k] = (uint8_t)block_mask_of(ws, x[k], tb);
+        constexpr int G = KPL < 8 ? KPL : 8;   // gathers in flight
+#pragma unroll
+        for (int k0 = 0; k0 < KPL; k0 += G) {
+            uint32_t mm[G];
+#pragma unroll
+            for (int k = 0; k < G; ++k)
+                if (base + k0 + k < m) mm[k] = block_mask_of(ws, x[k0 + k], x0, y0);
+#pragma unroll
+            for (int k = 0; k < G; ++k)
+                if (base + k0 + k < m) BM[base + k0 + k] = (uint8_t)mm[k];
+        }
     }
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view ws, int total_tiles, float rc2,
-                                                                    int exact) {
+__global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view ws, int total_tiles) {
     extern __shared__ unsigned long long xs[];
     const int t = blockIdx.x;
     const int64_t cap = ws.max_instances;
@@ -527,18 +551,16 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view w
     const int n = (int)(e - b);
     unsigned long long* K = ws.keys + b;
     uint8_t* BM = ws.bmask + b;
-    ss_tile_box tb;
+    int x0, y0;   // tile origin (pixels)
     {
         const ss_layout* L = ws.layout;
         const ss_view_layout& vl = L->v[find_view_tile(L, t)];
         const int lt = t - vl.tile_off;
-        tb.x0 = (lt % vl.tiles_x) * SS_TILE;
-        tb.y0 = (lt / vl.tiles_x) * SS_TILE;
-        tb.rc2 = rc2;
-        tb.exact = exact != 0;
+        x0 = (lt % vl.tiles_x) * SS_TILE;
+        y0 = (lt / vl.tiles_x) * SS_TILE;
     }
     if (n == 1) {
-        if (threadIdx.x == 0) BM[0] = (uint8_t)block_mask_of(ws, K[0], tb);
+        if (threadIdx.x == 0) BM[0] = (uint8_t)block_mask_of(ws, K[0], x0, y0);
         return;
     }
     unsigned long long* Alt = ws.keys_alt + b;
@@ -549,10 +571,10 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view w
         int N = 2;
         while (N < m) N <<= 1;
         const bool gather = n <= SORT_CAP;
-        if (N <= SORT_THREADS * 4) sort_chunk<4>(ws, K + c0, BM + c0, m, N, gather, tb, xs);
-        else if (N <= SORT_THREADS * 8) sort_chunk<8>(ws, K + c0, BM + c0, m, N, gather, tb, xs);
-        else if (N <= SORT_THREADS * 16) sort_chunk<16>(ws, K + c0, BM + c0, m, N, gather, tb, xs);
-        else sort_chunk<SORT_KPL>(ws, K + c0, BM + c0, m, N, gather, tb, xs);
+        if (N <= SORT_THREADS * 4) sort_chunk<4>(ws, K + c0, BM + c0, m, N, gather, x0, y0, xs);
+        else if (N <= SORT_THREADS * 8) sort_chunk<8>(ws, K + c0, BM + c0, m, N, gather, x0, y0, xs);
+        else if (N <= SORT_THREADS * 16) sort_chunk<16>(ws, K + c0, BM + c0, m, N, gather, x0, y0, xs);
+        else sort_chunk<SORT_KPL>(ws, K + c0, BM + c0, m, N, gather, x0, y0, xs);
     }
     if (n <= SORT_CAP) return;
     // pairwise merges in global memory, ping-pong between K and Alt
@@ -574,7 +596,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view w
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const unsigned long long k = src[i];
         if (src != K) K[i] = k;
-        BM[i] = (uint8_t)block_mask_of(ws, k, tb);
+        BM[i] = (uint8_t)block_mask_of(ws, k, x0, y0);
     }
 }
 
@@ -585,13 +607,13 @@ void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_a
                                     ws.stats);
     if (L.total_records > 0) {
         ss_note_launch();
-        scatter_kernel<<<(unsigned)((L.total_records + 255) / 256), 256, 0, st>>>(ws, L.total_records);
+        scatter_kernel<<<(unsigned)((L.total_records + 255) / 256), 256, 0, st>>>(
+            ws, L.total_records, a.p.r_cut * a.p.r_cut, a.p.mip_mode == 2 ? 0 : 1);
     }
     static std::atomic<unsigned long long> optin{0};
     ss_smem_optin(tile_sort_kernel, SORT_CAP * (int)sizeof(unsigned long long), optin);
     ss_note_launch();
-    tile_sort_kernel<<<L.total_tiles, SORT_THREADS, SORT_CAP * sizeof(unsigned long long), st>>>(
-        ws, L.total_tiles, a.p.r_cut * a.p.r_cut, a.p.mip_mode == 2 ? 0 : 1);
+    tile_sort_kernel<<<L.total_tiles, SORT_THREADS, SORT_CAP * sizeof(unsigned long long), st>>>(ws, L.total_tiles);
 }
 
 // ------------------------------------------------------------------------

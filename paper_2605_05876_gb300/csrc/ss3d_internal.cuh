@@ -95,13 +95,17 @@ struct ss_ws_view {
     uint32_t* tile_cursor;  // [total_tiles][SS_CNT_STRIDE] (first word used): instances past a record's
                             // first four tiles, counted by the projection, taken down by the scatter
     uint4* inst_rank;       // [total_records] rank of the record in the bins of its first four tiles
+    uint2* rec_bmask;       // [total_records] block masks of the record's first four tiles (8 bits each)
+                            // and its first tile (x | y << 12 | tiles across << 24), by the scatter
     unsigned long long* keys;      // [max_instances]
     unsigned long long* keys_alt;  // [max_instances]
     uint8_t* bmask;         // [max_instances] per sorted instance: bit b set iff the instance may cover a pixel
                             // centre of 8 x 4 block b of its tile (support rectangle overlaps the block and
                             // the exact support's minimum over the block's pixel centres is below the cutoff)
     uint32_t* cand_list;    // [8 x max_instances] per (tile, block): records whose rectangle meets the block
-    float* layer_state;     // [k_max][13][total_pixels]  (raw C (12), W)
+    float* layer_state;     // [k_max][ls_rows][total_pixels]: raw C (12), W; with the depth-consolidation
+                            // term also (sum w (z - z_r), sum w (z - z_r)^2, z_r), z_r the layer's first depth
+    int32_t ls_rows;        // 13, or 16 with the depth-consolidation term
     float* pix_state;       // [2][total_pixels]  (K as float bits, T_end)
     float* grad_rec;        // [total_records][SS_NGRAD]
     uint2* cover_list;      // [8 * max_instances]: per warp, (record, 32-pixel coverage word) of every staged

@@ -32,7 +32,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_struct_sizes_match_header():
     assert ctypes.sizeof(_lib.ss_camera) == 80
-    assert ctypes.sizeof(_lib.ss_render_params) == 72
+    assert ctypes.sizeof(_lib.ss_render_params) == 80
     assert ctypes.sizeof(_lib.ss_surfel_grads) == 64
     assert ctypes.sizeof(_lib.ss_stats) == 72
 
