@@ -102,7 +102,9 @@ class Renderer:
         self.maps = C.ss_env_maps(_ptr(self.irr), _ptr(self.spec), _ptr(self.lut))
         # outputs
         self.rgba = torch.zeros(self.n_pixels, 4, device=self.dev)
-        self.aov = torch.zeros(C.SS_N_AOV, self.n_pixels, device=self.dev)
+        # AOV planes: albedo 3, roughness, metallic, normal 3, depth; with the
+        # depth-consolidation term (params cons=1) a tenth plane holds it
+        self.aov = torch.zeros(C.SS_N_AOV + int(self.prm.cons), self.n_pixels, device=self.dev)
         self.with_backward = with_backward
         self.capacity_slack = capacity_slack
         self.ws = None
@@ -267,7 +269,7 @@ class Renderer:
 
     def view_aov(self, v: int):
         w, h = self.sizes[v]
-        return self.aov[:, self.view_slice(v)].reshape(C.SS_N_AOV, h, w)
+        return self.aov[:, self.view_slice(v)].reshape(self.aov.shape[0], h, w)
 
 
 def profile_begin():

@@ -38,10 +38,12 @@
 #define GT 13       // floats per pixel lane in the layer-coefficient table: G_k (12), S_k
 #define BW_CAP 128  // recorded fragments per warp before they are differentiated
 
-template <int ROWS>   // ROWS table rows: G_N, or G_N + 2 with the densification statistic
+// ROWS table rows: G_N, or G_N + 2 with the densification statistic; GTR
+// layer coefficients per pixel lane: GT, or GT + 3 with the consolidation term
+template <int ROWS, int GTR>
 struct ss_bwarp_t {
     float tab[ROWS * GCOL];
-    float gtab[32 * GT];
+    float gtab[32 * GTR];
     uint32_t rec[BW_CAP];
 };
 
@@ -56,6 +58,25 @@ struct ss_bwarp_t {
 // so that a fragment of weight w and channels ch in layer k has
 // dL/dw = sum_c G_k,c ch_c - S_k and dL/dch_c = G_k,c w.  (G_k, S_k) are
 // written over (C_k, W_k).
+//
+// With the depth-consolidation term (CONS, Eq. cons_loss) and its upstream
+// gradient gC, per layer k with w_k = T_k alpha_k, z_k = C_k,11 / W_k,
+// sigma_k^2 = Dz2 / W - (Dz / W)^2 (sums shifted by the layer's first depth
+// z_r; see the forward kernel), S^b / M^b (S^a / M^a) the sums of w_i and
+// w_i z_i over the layers in front of (behind) k:
+//   e_k     = dL/dw_k  = z_k (S^b - S^a) - M^b + M^a + 2 w_k sigma_k^2
+//   dL/dz_k = w_k (S^b - S^a),  dL/dsigma_k^2 = w_k^2,
+// and through w_k = T_k alpha_k (dw_k/dW_k = kappa T_{k+1}, dw_j/dW_k =
+// -kappa w_j for j > k, kappa = gamma / 2 pi), z_k and sigma_k^2:
+//   dL/dC_k,11 += gC dL/dz_k / W_k
+//   dL/dDz_k    = gC w_k^2 (-2 Dz / W^2),  dL/dDz2_k = gC w_k^2 / W
+//   dL/dW_k    += gC (-dL/dz_k z_k / W + w_k^2 (2 Dz^2 / W^3 - Dz2 / W^2)
+//                     + kappa (T_{k+1} e_k - sum_{j>k} e_j w_j)).
+// dL/dDz and dL/dDz2 are written over the sums (z_r stays), so that a
+// fragment of depth z adds dL/dw += dL/dDz (z - z_r) + dL/dDz2 (z - z_r)^2
+// and dL/dz = w (dL/dC_11 + dL/dDz + 2 dL/dDz2 (z - z_r)).  Totals over the
+// layers (sum w, sum w z, sum e w) come from two passes before the main one.
+template <bool CONS>
 __global__ void __launch_bounds__(256) layer_coeff_kernel(ss_ws_view ws, ss_bwd_args a) {
     const ss_layout* L = ws.layout;
     const int64_t P = L->total_pixels;
@@ -63,6 +84,7 @@ __global__ void __launch_bounds__(256) layer_coeff_kernel(ss_ws_view ws, ss_bwd_
     if (gpix >= P) return;
     const int K = __float_as_int(ws.pix_state[gpix]);
     if (K <= 0) return;
+    const int lsr = ws.ls_rows;
     const float kw = a.f.p.gamma * (0.5f / SS_PI_F);
     const float Tend = ws.pix_state[P + gpix];
     float g[SS_NCH], rem[SS_NCH];   // rem_c = out_c - sum_{j<=k} T_j alpha_j C_hat_j
@@ -76,9 +98,45 @@ __global__ void __launch_bounds__(256) layer_coeff_kernel(ss_ws_view ws, ss_bwd_
         g[3 + c] = a.d_aov ? a.d_aov[c * P + gpix] : 0.f;
         rem[3 + c] = a.out_aov ? a.out_aov[c * P + gpix] : 0.f;
     }
+    // consolidation: upstream gradient and the totals of two pre-passes
+    const float gC = CONS ? a.d_aov[SS_N_AOV * P + gpix] : 0.f;
+    float Wt = 0.f, WZt = 0.f, Et = 0.f;
+    auto cons_layer = [&](int kk, float Tk, float& wk, float& zk, float& var, float& alk, float& ek_e) {
+        const float* ls = ws.layer_state + (int64_t)kk * lsr * P + gpix;
+        const float W = ls[12 * P], iW = 1.f / W;
+        zk = ls[11 * P] * iW;
+        const float mdz = ls[13 * P] * iW;
+        var = fmaf(ls[14 * P], iW, -mdz * mdz);
+        ek_e = expf(-kw * W);
+        alk = -expm1f(-kw * W);
+        wk = Tk * alk;
+    };
+    if (CONS && gC != 0.f) {
+        float Tk = 1.f;
+        for (int kk = 0; kk < K; ++kk) {
+            float wk, zk, var, al, e;
+            cons_layer(kk, Tk, wk, zk, var, al, e);
+            Wt += wk;
+            WZt = fmaf(wk, zk, WZt);
+            Tk *= e;
+        }
+        Tk = 1.f;
+        float Sb = 0.f, Mb = 0.f;
+        for (int kk = 0; kk < K; ++kk) {
+            float wk, zk, var, al, e;
+            cons_layer(kk, Tk, wk, zk, var, al, e);
+            const float Sa = Wt - Sb - wk, Ma = WZt - Mb - wk * zk;
+            const float ek = fmaf(zk, Sb - Sa, Ma - Mb) + 2.f * wk * var;
+            Et = fmaf(ek, wk, Et);
+            Sb += wk;
+            Mb = fmaf(wk, zk, Mb);
+            Tk *= e;
+        }
+    }
     float Tb = 1.f;
+    float Sb = 0.f, Mb = 0.f, Pew = 0.f;   // consolidation: running sums over the layers in front
     for (int kk = 0; kk < K; ++kk) {
-        float* ls = ws.layer_state + (int64_t)kk * 13 * P + gpix;
+        float* ls = ws.layer_state + (int64_t)kk * lsr * P + gpix;
         float C[SS_NCH];
 #pragma unroll
         for (int c = 0; c < SS_NCH; ++c) C[c] = ls[c * P];
@@ -114,9 +172,33 @@ __global__ void __launch_bounds__(256) layer_coeff_kernel(ss_ws_view ws, ss_bwd_
         G[8] = (dn0 - hat[8] * nd) * inl;
         G[9] = (dn1 - hat[9] * nd) * inl;
         G[10] = (dn2 - hat[10] * nd) * inl;
+        float S = sG - dW_alpha;
+        if (CONS) {
+            float gDz = 0.f, gDz2 = 0.f;
+            if (gC != 0.f) {
+                const float wk = tw, zk = hat[11];
+                const float Dz = ls[13 * P], Dz2 = ls[14 * P];
+                const float mdz = Dz * invW, var = fmaf(Dz2, invW, -mdz * mdz);
+                const float Sa = Wt - Sb - wk, Ma = WZt - Mb - wk * zk;
+                const float ek = fmaf(zk, Sb - Sa, Ma - Mb) + 2.f * wk * var;
+                Pew = fmaf(ek, wk, Pew);
+                const float dz = wk * (Sb - Sa);                  // dL/dz_k
+                const float w2 = wk * wk;
+                G[11] = fmaf(gC * dz, invW, G[11]);
+                gDz = gC * w2 * (-2.f * mdz * invW);
+                gDz2 = gC * w2 * invW;
+                const float dW = gC * (-dz * zk * invW + w2 * invW * fmaf(2.f * mdz, mdz, -Dz2 * invW) +
+                                       kw * (Tb * e * ek - (Et - Pew)));
+                S -= dW;
+                Sb += wk;
+                Mb = fmaf(wk, zk, Mb);
+            }
+            ls[13 * P] = gDz;
+            ls[14 * P] = gDz2;
+        }
 #pragma unroll
         for (int c = 0; c < SS_NCH; ++c) ls[c * P] = G[c];
-        ls[12 * P] = sG - dW_alpha;
+        ls[12 * P] = S;
         Tb *= e;
     }
 }
@@ -244,13 +326,15 @@ struct ss_wjac {
 // of the record) are differentiated and summed.
 // The kernel is persistent, like the forward one: warps take (tile, block)
 // items from a queue.
-template <bool AOV, bool SSG, int RWPB_BWD>
+template <bool AOV, bool SSG, bool CONS, int RWPB_BWD>
 __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_bwd_args& a, const int gw,
                                                  unsigned char* bwd_smem) {
     constexpr int NV = AOV ? G_N : G_CH + 3;   // gradient values per fragment
     constexpr int NVT = NV + (SSG ? 2 : 0);    // + |(g_x, g_y)| and a count of 1 (Eq. ss_grad)
     constexpr int NC = AOV ? SS_NCH : 3;       // channels with a coefficient
-    using bwarp = ss_bwarp_t<SSG ? G_N + 2 : G_N>;
+    constexpr int GTR = CONS ? GT + 3 : GT;    // layer coefficients per lane (+ dL/dDz, dL/dDz2, z_r)
+    using bwarp = ss_bwarp_t<SSG ? G_N + 2 : G_N, GTR>;
+    const int lsr = ws.ls_rows;
     ss_wstage* Wst = reinterpret_cast<ss_wstage*>(bwd_smem);
     bwarp* Bws = reinterpret_cast<bwarp*>(bwd_smem + RWPB_BWD * sizeof(ss_wstage));
     ss_wjac* Wjs = reinterpret_cast<ss_wjac*>(bwd_smem + RWPB_BWD * (sizeof(ss_wstage) + sizeof(bwarp)));
@@ -290,9 +374,9 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
     int npend = 0;   // warp-uniform: fragments recorded, not yet differentiated
 
     auto enter_layer = [&](int kk) {   // this lane's layer coefficients -> B.gtab
-        const float* ls = ws.layer_state + (int64_t)kk * 13 * P + gpix;
+        const float* ls = ws.layer_state + (int64_t)kk * lsr * P + gpix;
 #pragma unroll
-        for (int c = 0; c < 13; ++c) B.gtab[lane * GT + c] = ls[c * P];
+        for (int c = 0; c < GTR; ++c) B.gtab[lane * GTR + c] = ls[c * P];
     };
 
     const int64_t cap = ws.max_instances;
@@ -324,7 +408,7 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
                 const float rho2 = __fdividef(h.q, h.t);
                 const float ex = __expf(-0.5f * rho2);
                 const float w = nf * ex;   // the forward kernel's weight, same operations
-                const float* gt = B.gtab + pl * GT;
+                const float* gt = B.gtab + pl * GTR;
                 const float4 c0v = Wc->c0[s], c1v = Wc->c1[s], c2v = Wc->c2[s];
                 const float ch[SS_NCH] = {c0v.x, c0v.y, c0v.z, c1v.x, c1v.y, c1v.z,
                                           c1v.w, c2v.x, c2v.y, c2v.z, c2v.w, 0.5f * (h2.x + h2.y)};
@@ -337,7 +421,12 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
                     dl[c % 3] = fmaf(G, ch[c], dl[c % 3]);
                     gr[G_CH + c] = G * w;
                 }
-                const float dLdw = dl[0] + (dl[1] + dl[2]);
+                float dLdw = dl[0] + (dl[1] + dl[2]);
+                if (CONS) {   // the consolidation term's shifted depth sums of the layer
+                    const float dz = ch[11] - gt[15];
+                    dLdw = fmaf(gt[13], dz, fmaf(gt[14] * dz, dz, dLdw));
+                    gr[G_CH + 11] = w * fmaf(2.f * gt[14], dz, gt[11] + gt[13]);
+                }
                 // w = n_f exp(-rho2 / 2), rho2 = q / s2^2 (Eq. mip_weight)
                 gr[G_NF] = dLdw * ex;
                 const float grho = -0.5f * w * dLdw;
@@ -468,7 +557,7 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
     }
 }
 
-template <bool AOV, bool SSG, int RWPB_BWD>
+template <bool AOV, bool SSG, bool CONS, int RWPB_BWD>
 __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kernel(ss_ws_view ws, ss_bwd_args a,
                                                                                   int n_items) {
     extern __shared__ __align__(16) unsigned char bwd_smem[];
@@ -478,34 +567,35 @@ __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kerne
         if (lane == 0) item = (int)atomicAdd(ws.work + 1, 1u);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
-        raster_bwd_block<AOV, SSG, RWPB_BWD>(ws, a, item, bwd_smem);
+        raster_bwd_block<AOV, SSG, CONS, RWPB_BWD>(ws, a, item, bwd_smem);
         __syncwarp();
     }
 }
 
-template <bool AOV, bool SSG, int W>
+template <bool AOV, bool SSG, bool CONS, int W>
 static void launch_raster_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st) {
-    const int smem =
-        W * (int)(sizeof(ss_wstage) + sizeof(ss_bwarp_t<SSG ? G_N + 2 : G_N>) + (SSG ? sizeof(ss_wjac) : 0));
+    const int smem = W * (int)(sizeof(ss_wstage) + sizeof(ss_bwarp_t<SSG ? G_N + 2 : G_N, CONS ? GT + 3 : GT>) +
+                               (SSG ? sizeof(ss_wjac) : 0));
     static std::atomic<unsigned long long> optin{0}, resident{0};
-    ss_smem_optin(raster_bwd_kernel<AOV, SSG, W>, smem, optin);
+    ss_smem_optin(raster_bwd_kernel<AOV, SSG, CONS, W>, smem, optin);
     const int n_items = (int)(L.total_tiles * 8);
-    const int ctas = ss_resident_ctas(raster_bwd_kernel<AOV, SSG, W>, 32 * W, smem, resident);
+    const int ctas = ss_resident_ctas(raster_bwd_kernel<AOV, SSG, CONS, W>, 32 * W, smem, resident);
     const int grid = max(1, min(ctas > 0 ? ctas : 1, (n_items + W - 1) / W));
-    raster_bwd_kernel<AOV, SSG, W><<<grid, 32 * W, smem, st>>>(ws, a, n_items);
+    raster_bwd_kernel<AOV, SSG, CONS, W><<<grid, 32 * W, smem, st>>>(ws, a, n_items);
 }
 
-template <bool AOV, bool SSG>
+template <bool AOV, bool SSG, bool CONS>
 static void launch_raster_bwd_w(int w, const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a,
                                 cudaStream_t st) {
-    if (w == 2) launch_raster_bwd<AOV, SSG, 2>(ws, L, a, st);
-    else if (w == 4) launch_raster_bwd<AOV, SSG, 4>(ws, L, a, st);
-    else launch_raster_bwd<AOV, SSG, 8>(ws, L, a, st);
+    if (w == 2) launch_raster_bwd<AOV, SSG, CONS, 2>(ws, L, a, st);
+    else if (w == 4) launch_raster_bwd<AOV, SSG, CONS, 4>(ws, L, a, st);
+    else launch_raster_bwd<AOV, SSG, CONS, 8>(ws, L, a, st);
 }
 
 void ss_launch_raster_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st) {
     if (L.total_tiles <= 0) return;
     const bool ssg = ws.ssg_jac && (a.g.screen_grad_norm || a.g.screen_grad_views);
+    const bool cons = a.f.p.cons != 0;   // (the host requires d_aov then)
     if (ssg) {
         const int64_t n = L.scene_begin[L.n_scenes];
         if (n > 0) {
@@ -514,15 +604,19 @@ void ss_launch_raster_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd
         }
     }
     ss_note_launch();
-    layer_coeff_kernel<<<(unsigned)((L.total_pixels + 255) / 256), 256, 0, st>>>(ws, a);
+    if (cons) layer_coeff_kernel<true><<<(unsigned)((L.total_pixels + 255) / 256), 256, 0, st>>>(ws, a);
+    else layer_coeff_kernel<false><<<(unsigned)((L.total_pixels + 255) / 256), 256, 0, st>>>(ws, a);
     const int w = a.f.p.bwd_warps ? a.f.p.bwd_warps : RWPB_BWD_DEFAULT;
     ss_note_launch();
-    if (a.d_aov) {
-        if (ssg) launch_raster_bwd_w<true, true>(w, ws, L, a, st);
-        else launch_raster_bwd_w<true, false>(w, ws, L, a, st);
+    if (cons) {
+        if (ssg) launch_raster_bwd_w<true, true, true>(w, ws, L, a, st);
+        else launch_raster_bwd_w<true, false, true>(w, ws, L, a, st);
+    } else if (a.d_aov) {
+        if (ssg) launch_raster_bwd_w<true, true, false>(w, ws, L, a, st);
+        else launch_raster_bwd_w<true, false, false>(w, ws, L, a, st);
     } else {
-        if (ssg) launch_raster_bwd_w<false, true>(w, ws, L, a, st);
-        else launch_raster_bwd_w<false, false>(w, ws, L, a, st);
+        if (ssg) launch_raster_bwd_w<false, true, false>(w, ws, L, a, st);
+        else launch_raster_bwd_w<false, false, false>(w, ws, L, a, st);
     }
 }
 

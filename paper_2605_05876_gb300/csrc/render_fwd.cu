@@ -626,7 +626,7 @@ void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_a
 // as many warps as fit on the device take (tile, block) items from a queue
 // in item order, so no warp slot idles while items are left.
 
-template <bool STATS, bool PP, int RWPB_FWD>
+template <bool STATS, bool PP, bool CONS, int RWPB_FWD>
 __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_fwd_args& a, const int gw,
                                                  unsigned char* fwd_smem) {
     ss_wstage* Wst = reinterpret_cast<ss_wstage*>(fwd_smem);   // [RWPB_FWD warps][2]
@@ -659,6 +659,15 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
     float Wg = 0.f, zmax = 0.f, Tb = 1.f, Acov = 0.f;
     int K = 0;
     bool done = !inside;
+    // depth-consolidation term (Eq. cons_loss): per open layer its first
+    // fragment's depth z_r and the shifted sums sum w (z - z_r), sum w (z - z_r)^2
+    // (a well-conditioned variance); per pixel the running sums of the
+    // composited layers' w_i and w_i z_i and the term itself.  Layer means
+    // increase with the layer index (layers are separated by depth gaps and a
+    // fragment's depth lies in its interval), so sum_{i<j} w_i w_j |z_i - z_j|
+    // = sum_j w_j (z_j S_j - M_j) with S_j, M_j those sums over i < j.
+    float zr = 0.f, Dz = 0.f, Dz2 = 0.f, Sb = 0.f, Mb = 0.f, Lp = 0.f;
+    const int lsr = ws.ls_rows;
 
     auto flush = [&]() {
         const float invW = 1.f / Wg;
@@ -672,11 +681,24 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
         const float tw = Tb * al;
 #pragma unroll
         for (int c = 0; c < SS_NCH; ++c) out[c] = fmaf(tw, hat[c], out[c]);  // Eq. compositing
+        if (CONS) {
+            const float zk = C[11] * invW, mdz = Dz * invW;
+            const float var = fmaf(Dz2, invW, -mdz * mdz);
+            Lp = fmaf(tw, fmaf(zk, Sb, -Mb), Lp);
+            Lp = fmaf(tw * tw, var, Lp);
+            Sb += tw;
+            Mb = fmaf(tw, zk, Mb);
+        }
         if (a.with_backward) {
-            float* ls = ws.layer_state + (int64_t)K * 13 * P + gpix;
+            float* ls = ws.layer_state + (int64_t)K * lsr * P + gpix;
 #pragma unroll
             for (int c = 0; c < SS_NCH; ++c) ls[c * P] = C[c];
             ls[12 * P] = Wg;
+            if (CONS) {
+                ls[13 * P] = Dz;
+                ls[14 * P] = Dz2;
+                ls[15 * P] = zr;
+            }
         }
         Acov = fmaf(Tb, al, Acov);
         Tb *= expf(-kw * Wg);
@@ -685,6 +707,7 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
         for (int c = 0; c < SS_NCH; ++c) C[c] = 0.f;
         Wg = 0.f;
         zmax = 0.f;
+        Dz = Dz2 = 0.f;
         if (K >= kmax) done = true;
     };
 
@@ -774,7 +797,14 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
                     C[3] = fmaf(w, c1v.x, C[3]); C[4] = fmaf(w, c1v.y, C[4]); C[5] = fmaf(w, c1v.z, C[5]);
                     C[6] = fmaf(w, c1v.w, C[6]); C[7] = fmaf(w, c2v.x, C[7]); C[8] = fmaf(w, c2v.y, C[8]);
                     C[9] = fmaf(w, c2v.z, C[9]); C[10] = fmaf(w, c2v.w, C[10]);
-                    C[11] = fmaf(w, 0.5f * (h2.x + h2.y), C[11]);
+                    const float zc = 0.5f * (h2.x + h2.y);
+                    C[11] = fmaf(w, zc, C[11]);
+                    if (CONS) {
+                        if (Wg == 0.f) zr = zc;   // the layer's first fragment
+                        const float dz = zc - zr;
+                        Dz = fmaf(w, dz, Dz);
+                        Dz2 = fmaf(w * dz, dz, Dz2);
+                    }
                     Wg += w;
                 }
             }
@@ -815,6 +845,7 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
     if (a.out_aov) {
 #pragma unroll
         for (int c = 0; c < SS_N_AOV; ++c) a.out_aov[c * P + gpix] = out[3 + c];
+        if (CONS) a.out_aov[SS_N_AOV * P + gpix] = Lp;
     }
     if (a.with_backward) {
         ws.pix_state[gpix] = __int_as_float(K);
@@ -822,7 +853,7 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
     }
 }
 
-template <bool STATS, bool PP, int RWPB_FWD>
+template <bool STATS, bool PP, bool CONS, int RWPB_FWD>
 __global__ void __launch_bounds__(32 * RWPB_FWD, 24 / RWPB_FWD) raster_fwd_kernel(ss_ws_view ws, ss_fwd_args a,
                                                                                   int n_items) {
     extern __shared__ __align__(16) unsigned char fwd_smem[];
@@ -832,42 +863,44 @@ __global__ void __launch_bounds__(32 * RWPB_FWD, 24 / RWPB_FWD) raster_fwd_kerne
         if (lane == 0) item = (int)atomicAdd(ws.work + 0, 1u);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
-        raster_fwd_block<STATS, PP, RWPB_FWD>(ws, a, item, fwd_smem);
+        raster_fwd_block<STATS, PP, CONS, RWPB_FWD>(ws, a, item, fwd_smem);
         __syncwarp();
     }
 }
 
-template <bool STATS, bool PP, int W>
+template <bool STATS, bool PP, bool CONS, int W>
 static void launch_raster_fwd(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st) {
     const int smem = 2 * W * (int)sizeof(ss_wstage);
     static std::atomic<unsigned long long> optin{0}, resident{0};
-    ss_smem_optin(raster_fwd_kernel<STATS, PP, W>, smem, optin);
+    ss_smem_optin(raster_fwd_kernel<STATS, PP, CONS, W>, smem, optin);
     const int n_items = (int)(L.total_tiles * 8);
-    const int ctas = ss_resident_ctas(raster_fwd_kernel<STATS, PP, W>, 32 * W, smem, resident);
+    const int ctas = ss_resident_ctas(raster_fwd_kernel<STATS, PP, CONS, W>, 32 * W, smem, resident);
     const int grid = max(1, min(ctas > 0 ? ctas : 1, (n_items + W - 1) / W));
-    raster_fwd_kernel<STATS, PP, W><<<grid, 32 * W, smem, st>>>(ws, a, n_items);
+    raster_fwd_kernel<STATS, PP, CONS, W><<<grid, 32 * W, smem, st>>>(ws, a, n_items);
 }
 
-template <bool STATS, bool PP>
+template <bool STATS, bool PP, bool CONS>
 static void launch_raster_fwd_w(int w, const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a,
                                 cudaStream_t st) {
-    if (w == 1) launch_raster_fwd<STATS, PP, 1>(ws, L, a, st);
-    else if (w == 2) launch_raster_fwd<STATS, PP, 2>(ws, L, a, st);
-    else launch_raster_fwd<STATS, PP, 4>(ws, L, a, st);
+    if (w == 1) launch_raster_fwd<STATS, PP, CONS, 1>(ws, L, a, st);
+    else if (w == 2) launch_raster_fwd<STATS, PP, CONS, 2>(ws, L, a, st);
+    else launch_raster_fwd<STATS, PP, CONS, 4>(ws, L, a, st);
+}
+
+template <bool STATS>
+static void launch_raster_fwd_mode(int w, const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a,
+                                   cudaStream_t st) {
+    if (a.p.mip_mode == 2) launch_raster_fwd_w<STATS, true, false>(w, ws, L, a, st);   // (no cons with mode 2)
+    else if (a.p.cons) launch_raster_fwd_w<STATS, false, true>(w, ws, L, a, st);
+    else launch_raster_fwd_w<STATS, false, false>(w, ws, L, a, st);
 }
 
 void ss_launch_raster_fwd(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st) {
     if (L.total_tiles <= 0) return;
     ss_note_launch();
     const int w = a.p.fwd_warps ? a.p.fwd_warps : RWPB_FWD_DEFAULT;
-    const bool pp = a.p.mip_mode == 2;
-    if (a.p.collect_stats) {
-        if (pp) launch_raster_fwd_w<true, true>(w, ws, L, a, st);
-        else launch_raster_fwd_w<true, false>(w, ws, L, a, st);
-    } else {
-        if (pp) launch_raster_fwd_w<false, true>(w, ws, L, a, st);
-        else launch_raster_fwd_w<false, false>(w, ws, L, a, st);
-    }
+    if (a.p.collect_stats) launch_raster_fwd_mode<true>(w, ws, L, a, st);
+    else launch_raster_fwd_mode<false>(w, ws, L, a, st);
 }
 
 // ------------------------------------------------------------------------

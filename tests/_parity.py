@@ -15,7 +15,7 @@ MIP_MODES = {0: "centre", 1: "none", 2: "pixel"}
 def oracle_params(prm) -> M.Params:
     return M.Params(r_cut=float(prm.r_cut), sigma_f=float(prm.sigma_f), gamma=float(prm.gamma),
                     k_max=int(prm.k_max), z_near=float(prm.z_near), bg=tuple(float(b) for b in prm.bg),
-                    lut_n=int(prm.lut_n), mip_mode=MIP_MODES[int(prm.mip_mode)])
+                    lut_n=int(prm.lut_n), mip_mode=MIP_MODES[int(prm.mip_mode)], cons=bool(prm.cons))
 
 
 def oracle_view(scene, v, prm, env_levels=6, pix=None, G=None, env_cache=None):
@@ -49,7 +49,8 @@ MAX_FLIP_FRACTION = 1e-4
 
 
 # columns of the composited normal in a [.., 13] row (rgba, then the AOVs:
-# albedo 3, roughness, metallic, normal 3, depth)
+# albedo 3, roughness, metallic, normal 3, depth; a 14th column holds the
+# depth-consolidation term when it is on)
 NORMAL_COLS = slice(9, 12)
 
 
@@ -60,7 +61,7 @@ def scale_of(r):
     its FP32 rounding scales with the composited normal's length, and all
     three components are measured against that length."""
     sc = np.abs(r).astype(np.float64, copy=True)
-    if r.shape[-1] == 13:
+    if r.shape[-1] >= 13:
         sc[..., NORMAL_COLS] = np.linalg.norm(r[..., NORMAL_COLS], axis=-1, keepdims=True)
     return sc
 

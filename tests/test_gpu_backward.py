@@ -35,7 +35,7 @@ def _run(scene, seed=0, params=None, env_levels=6, aov_grad=True):
     torch.cuda.synchronize()
     rng = np.random.default_rng(seed)
     P = r.n_pixels
-    G = rng.normal(size=(P, 13))
+    G = rng.normal(size=(P, 13 + int(r.prm.cons)))   # rgba, 9 AOVs (+ the consolidation term)
     if not aov_grad:
         G[:, 4:] = 0.0            # RGBA-only upstream gradient (d_aov = NULL on the GPU side)
     refs, cache = [], {}
