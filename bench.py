@@ -36,6 +36,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fwd+bwd views/s at 1M surfels 16x800² (batched vs per-view); % HBM roofline"
 FP32_LANES_PER_SM = 128
+# the speed-only knobs the autotuner sets (copied to the renderers of the other forms)
+KNOBS = ("tile_w", "tile_h", "stage_depth", "fwd_warps", "bwd_warps", "pbwd_block")
 # algorithmic FP32 work per unit (counted from the kernels' arithmetic):
 FLOP_TEST = 17        # one (pixel, surfel) test inside the support rectangle
 FLOP_FRAG_FWD = 30    # one covering fragment: weight + 12-channel accumulation
@@ -507,8 +509,9 @@ def run_ours(args):
         for v in range(V):
             sc1 = scenes.Scene(scene.surfels, scene.scene_offsets, scene.envs, [scene.cameras[v]], scene.name)
             rv = Renderer(sc1, share_from=r)
-            for k in ("fwd_warps", "bwd_warps", "pbwd_block"):
+            for k in KNOBS:
                 setattr(rv.prm, k, getattr(r.prm, k))
+            rv.plan_capacity()
             rv.zero_grads(share_from=r)
             singles.append((rv, d_rgba[r.view_slice(v)].contiguous(), d_aov[:, r.view_slice(v)].contiguous()))
 
@@ -530,8 +533,9 @@ def run_ours(args):
     screen_grad = None
     if not args.no_screen_grad:
         rs = Renderer(scene, share_from=r, screen_grad=True)
-        for k in ("fwd_warps", "bwd_warps", "pbwd_block"):
+        for k in KNOBS:
             setattr(rs.prm, k, getattr(r.prm, k))
+        rs.plan_capacity()
         rs.zero_grads()
 
         def step_ssg():

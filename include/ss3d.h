@@ -153,6 +153,12 @@ typedef struct ss_render_params {
                                 (write_aov must be 1); the backward then requires d_aov [10][P]
                                 whose tenth plane is the upstream gradient of that term.  Not with
                                 mip_mode 2.  The workspace keeps 3 more floats per pixel layer */
+    /* tiling and staging (0 = default); they change speed, never results */
+    int32_t tile_w, tile_h;  /* screen tile of the binning and the rasterisers: tile_w in {8, 16, 32},
+                                tile_h in {4, 8, 16, 32}, at most 8 blocks of 8 x 4 pixels per tile
+                                (default 16 x 16, App. A) */
+    int32_t stage_depth;     /* forward rasteriser: chunks of 32 candidate records in flight per warp
+                                (1 = none ahead, 2 default, 3) */
     int32_t pad_;
 } ss_render_params;
 
@@ -298,7 +304,8 @@ ss_status ss_count_instances(const ss_batch_desc* b, const ss_surfels* s, const 
 /* Forward render (Sec. 3, Fig. 2 stages 1-5 without tone mapping):
  * per surfel and view the T-matrix (Sec. 3.1), depth interval, centre-
  * precomputed MIP filter (Eq. mip_weight) and forward split-sum shading
- * (Eq. ibl); binning into 16 x 16 tiles sorted by z_start (Sec. 3.2.1);
+ * (Eq. ibl); binning into screen tiles (16 x 16 by default, App. A) sorted by
+ * z_start (Sec. 3.2.1);
  * per pixel Algorithm 1 with Eq. alpha coverage and Eq. compositing, at most
  * K_max layers.  Surfel i covers pixel x iff x lies in its support rectangle
  * (the projected r_cut disc of App. A united with the r_cut bounds of the

@@ -54,7 +54,8 @@ class ss_render_params(ctypes.Structure):
     _fields_ = [("r_cut", c_f), ("sigma_f", c_f), ("gamma", c_f), ("k_max", c_i32), ("z_near", c_f),
                 ("bg", c_f * 3), ("write_aov", c_i32), ("lut_n", c_i32), ("max_instances", c_i64),
                 ("collect_stats", c_i32), ("fwd_warps", c_i32), ("bwd_warps", c_i32), ("pbwd_block", c_i32),
-                ("screen_grad", c_i32), ("mip_mode", c_i32), ("cons", c_i32), ("pad_", c_i32)]
+                ("screen_grad", c_i32), ("mip_mode", c_i32), ("cons", c_i32), ("tile_w", c_i32), ("tile_h", c_i32),
+                ("stage_depth", c_i32), ("pad_", c_i32)]
 
 
 class ss_stats(ctypes.Structure):

@@ -206,15 +206,25 @@ class Renderer:
         return self.grads
 
 
-    TUNE_SPACE = {"fwd_warps": (1, 2, 4), "bwd_warps": (2, 4, 8), "pbwd_block": (64, 128, 256)}
+    # screen tiles made of 8 x 4 warp blocks (at most 8 per tile), forward
+    # staging depth, launch shapes; searched in this order
+    TUNE_SPACE = {"tile": ((16, 16), (16, 8), (32, 8), (8, 16), (8, 8)), "stage_depth": (1, 2, 3),
+                  "fwd_warps": (1, 2, 4), "bwd_warps": (2, 4, 8), "pbwd_block": (64, 128, 256)}
+
+    def set_tile(self, tile):
+        """Change the screen tile (width, height); the instance capacity and
+        the workspace are planned again for it."""
+        self.prm.tile_w, self.prm.tile_h = int(tile[0]), int(tile[1])
+        self.ws = None
+        self.plan_capacity()
 
     def autotune(self, d_rgba, d_aov=None, reps: int = 3, space: dict | None = None) -> dict:
-        """Choose the launch shapes of ss_render_params (fwd_warps, bwd_warps,
-        pbwd_block) that render and differentiate this batch fastest, one
-        knob at a time in the order given, each candidate timed with CUDA
-        events over `reps` forward+backward passes after one untimed pass.
-        The shapes change speed only, never results.  Returns
-        {knob: (chosen value, {value: ms per pass})}."""
+        """Choose the tile shape, the forward staging depth and the launch
+        shapes of ss_render_params that render and differentiate this batch
+        fastest, one knob at a time in the order given, each candidate timed
+        with CUDA events over `reps` forward+backward passes after one
+        untimed pass.  These knobs change speed only, never results.
+        Returns {knob: (chosen value, {value: ms per pass})}."""
         torch = self.torch
         space = space or self.TUNE_SPACE
 
@@ -238,10 +248,19 @@ class Renderer:
         for knob, values in space.items():
             times = {}
             for v in values:
-                setattr(self.prm, knob, int(v))
-                times[int(v)] = timed()
+                if knob == "tile":
+                    self.set_tile(v)
+                    key = f"{v[0]}x{v[1]}"
+                else:
+                    setattr(self.prm, knob, int(v))
+                    key = int(v)
+                times[key] = timed()
             best = min(times, key=times.get)
-            setattr(self.prm, knob, best)
+            if knob == "tile":
+                w, h = (int(x) for x in best.split("x"))
+                self.set_tile((w, h))
+            else:
+                setattr(self.prm, knob, best)
             chosen[knob] = (best, times)
         return chosen
 

@@ -100,6 +100,11 @@ static ss_status check_knobs(const ss_render_params* p) {
     if (p->mip_mode < 0 || p->mip_mode > 2) return SS_ERR_INVALID_ARG;
     if (p->cons != 0 && p->cons != 1) return SS_ERR_INVALID_ARG;
     if (p->cons && (p->mip_mode == 2 || !p->write_aov)) return SS_ERR_INVALID_ARG;
+    // a tile is a whole number of 8 x 4 blocks, at most 8 of them
+    const int tw = p->tile_w ? p->tile_w : SS_TILE, th = p->tile_h ? p->tile_h : SS_TILE;
+    if (!(tw == 8 || tw == 16 || tw == 32) || !(th == 4 || th == 8 || th == 16 || th == 32)) return SS_ERR_INVALID_ARG;
+    if ((tw / 8) * (th / 4) > 8) return SS_ERR_INVALID_ARG;
+    if (p->stage_depth < 0 || p->stage_depth > 3) return SS_ERR_INVALID_ARG;
     return SS_OK;
 }
 
@@ -132,6 +137,7 @@ extern "C" const char* ss_error_string(ss_status s) {
 
 static ss_status build_layout(const ss_batch_desc* b, const ss_render_params* p, ss_layout* L) {
     if (!b || !p || !L) return SS_ERR_INVALID_ARG;
+    if (check_knobs(p)) return SS_ERR_INVALID_ARG;
     if (b->n_scenes < 1 || b->n_scenes > SS_MAX_SCENES) return SS_ERR_INVALID_ARG;
     if (b->n_views < 1 || b->n_views > SS_MAX_VIEWS) return SS_ERR_INVALID_ARG;
     if (!b->scene_offsets_host || !b->cams_host) return SS_ERR_INVALID_ARG;
@@ -141,6 +147,13 @@ static ss_status build_layout(const ss_batch_desc* b, const ss_render_params* p,
     L->n_views = b->n_views;
     L->n_scenes = b->n_scenes;
     L->k_max = p->k_max;
+    {
+        const int tw = p->tile_w ? p->tile_w : SS_TILE, th = p->tile_h ? p->tile_h : SS_TILE;
+        L->tw_log2 = 31 - __builtin_clz((unsigned)tw);
+        L->th_log2 = 31 - __builtin_clz((unsigned)th);
+        L->bx = tw / 8;
+        L->bpt = (tw / 8) * (th / 4);
+    }
     for (int s = 0; s <= b->n_scenes; ++s) {
         L->scene_begin[s] = b->scene_offsets_host[s];
         if (s > 0 && L->scene_begin[s] < L->scene_begin[s - 1]) return SS_ERR_INVALID_ARG;
@@ -161,8 +174,8 @@ static ss_status build_layout(const ss_batch_desc* b, const ss_render_params* p,
         vl.scene = c.scene;
         vl.width = c.width;
         vl.height = c.height;
-        vl.tiles_x = (c.width + SS_TILE - 1) / SS_TILE;
-        vl.tiles_y = (c.height + SS_TILE - 1) / SS_TILE;
+        vl.tiles_x = (c.width + (1 << L->tw_log2) - 1) >> L->tw_log2;
+        vl.tiles_y = (c.height + (1 << L->th_log2) - 1) >> L->th_log2;
         vl.tile_off = tiles;
         vl.pixel_off = pix;
         vl.rec_off = rec;

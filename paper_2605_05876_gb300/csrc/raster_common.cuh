@@ -83,11 +83,20 @@ __device__ __forceinline__ void stage_ids(ss_wstage& W, const ss_rec* recs, uint
     cp_async_commit();
 }
 
-// Wait for the copies of the n staged slots of W and rewrite them in place:
-// the centre relative to the tile origin (tx0, ty0) from its double-float
-// value, and (z_start, z_end, +-n_f).
-__device__ __forceinline__ void stage_finish(ss_wstage& W, int n, int lane, float tx0, float ty0) {
-    cp_async_wait0();
+// Wait until at most `pending` (0..2) of this thread's copy groups are still
+// in flight.
+__device__ __forceinline__ void cp_async_wait_pending(int pending) {
+    if (pending <= 0) asm volatile("cp.async.wait_group 0;\n" ::);
+    else if (pending == 1) asm volatile("cp.async.wait_group 1;\n" ::);
+    else asm volatile("cp.async.wait_group 2;\n" ::);
+}
+
+// Wait for the copies of the n staged slots of W (allowing `pending` later
+// groups to stay in flight) and rewrite them in place: the centre relative to
+// the tile origin (tx0, ty0) from its double-float value, and
+// (z_start, z_end, +-n_f).
+__device__ __forceinline__ void stage_finish(ss_wstage& W, int n, int lane, float tx0, float ty0, int pending = 0) {
+    cp_async_wait_pending(pending);
     __syncwarp();
     if (lane < n) {
         const float4 r1 = W.h1[lane], r2 = W.h2[lane];

@@ -340,15 +340,15 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
     ss_wjac* Wjs = reinterpret_cast<ss_wjac*>(bwd_smem + RWPB_BWD * (sizeof(ss_wstage) + sizeof(bwarp)));
     const ss_layout* L = ws.layout;
     const int lw = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = gw >> 3, warp = gw & 7;          // 8 blocks per tile
+    const int tile = gw / L->bpt, warp = gw - tile * L->bpt;        // bpt blocks per tile
     const int view = find_view_tile(L, tile);
     const ss_view_layout& vl = L->v[view];
     const int lt = tile - vl.tile_off;
     const int tx = lt % vl.tiles_x, ty = lt / vl.tiles_x;
-    const int x0 = tx * SS_TILE, y0 = ty * SS_TILE;
+    const int x0 = tx << L->tw_log2, y0 = ty << L->th_log2;
     ss_wstage* Wc = Wst + lw;         // staging buffer
     bwarp& B = Bws[lw];
-    const int wx0 = 8 * (warp & 1), wy0 = 4 * (warp >> 1);
+    const int wx0 = 8 * (warp % L->bx), wy0 = 4 * (warp / L->bx);
     const int lx = wx0 + (lane & 7), ly = wy0 + (lane >> 3);
     const int px = x0 + lx, py = y0 + ly;
     const bool inside = px < vl.width && py < vl.height;
@@ -578,7 +578,7 @@ static void launch_raster_bwd(const ss_ws_view& ws, const ss_layout& L, const ss
                                (SSG ? sizeof(ss_wjac) : 0));
     static std::atomic<unsigned long long> optin{0}, resident{0};
     ss_smem_optin(raster_bwd_kernel<AOV, SSG, CONS, W>, smem, optin);
-    const int n_items = (int)(L.total_tiles * 8);
+    const int n_items = (int)(L.total_tiles * L.bpt);
     const int ctas = ss_resident_ctas(raster_bwd_kernel<AOV, SSG, CONS, W>, 32 * W, smem, resident);
     const int grid = max(1, min(ctas > 0 ? ctas : 1, (n_items + W - 1) / W));
     raster_bwd_kernel<AOV, SSG, CONS, W><<<grid, 32 * W, smem, st>>>(ws, a, n_items);

@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(256, 4) project_kernel(ss_ws_view ws, ss_fwd_a
             // bin counts: the record's rank in the bins of its first four tiles
             // (kept for the scatter, which then needs no atomics for them),
             // plain counts for the rest
-            const int tx0 = i0 / SS_TILE, tx1 = i1 / SS_TILE, ty0 = j0 / SS_TILE, ty1 = j1 / SS_TILE;
+            const int tx0 = i0 >> L->tw_log2, tx1 = i1 >> L->tw_log2, ty0 = j0 >> L->th_log2, ty1 = j1 >> L->th_log2;
             const int ntx = tx1 - tx0 + 1, nt = ntx * (ty1 - ty0 + 1);
             uint32_t rk[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
@@ -335,40 +335,43 @@ __global__ void __launch_bounds__(1024) scan_kernel(const uint32_t* cnt, const u
 // the records, computes the masks of each record's first four tiles; the sort
 // kernel reads them back for the sorted instances (instances past a record's
 // fourth tile keep the rectangle test alone).
-__device__ __forceinline__ uint32_t rect_block_bits(uint32_t rx, uint32_t ry, int x0, int y0) {
+// (block b of a tile of bx blocks across sits at (8 (b % bx), 4 (b / bx)))
+__device__ __forceinline__ uint32_t rect_block_bits(uint32_t rx, uint32_t ry, int x0, int y0, int bx, int bpt) {
     const int i0 = (int)(rx & 0xffff), i1 = (int)(rx >> 16), j0 = (int)(ry & 0xffff), j1 = (int)(ry >> 16);
     uint32_t m = 0;
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
-        const int gx0 = x0 + 8 * (b & 1), gy0 = y0 + 4 * (b >> 1);
+        if (b >= bpt) break;
+        const int gx0 = x0 + 8 * (b % bx), gy0 = y0 + 4 * (b / bx);
         if (i0 <= gx0 + 7 && i1 >= gx0 && j0 <= gy0 + 3 && j1 >= gy0) m |= 1u << b;
     }
     return m;
 }
 
 __device__ __forceinline__ uint32_t exact_block_bits(uint32_t m, float4 P, float4 r1, float4 r2, int x0, int y0,
-                                                     float rc2) {
+                                                     float rc2, int bx) {
     const float prx = __fadd_rn(__fsub_rn(r2.x, (float)x0), r2.z);
     const float pry = __fadd_rn(__fsub_rn(r2.y, (float)y0), r2.w);
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
         if (!((m >> b) & 1u)) continue;
-        const float bx = (float)(8 * (b & 1)) - prx, by = (float)(4 * (b >> 1)) - pry;
-        if (!ss_box_may_cover(P, r1.x, r1.y, rc2, bx + 0.5f, bx + 7.5f, by + 0.5f, by + 3.5f)) m &= ~(1u << b);
+        const float dxb = (float)(8 * (b % bx)) - prx, dyb = (float)(4 * (b / bx)) - pry;
+        if (!ss_box_may_cover(P, r1.x, r1.y, rc2, dxb + 0.5f, dxb + 7.5f, dyb + 0.5f, dyb + 3.5f)) m &= ~(1u << b);
     }
     return m;
 }
 
 // the block mask of a sorted instance (key) in tile (x0, y0): from the
 // scatter's per-record masks, or the rectangle test past the fourth tile
-__device__ __forceinline__ uint32_t block_mask_of(const ss_ws_view& ws, unsigned long long key, int x0, int y0) {
+__device__ __forceinline__ uint32_t block_mask_of(const ss_ws_view& ws, const ss_layout* L, unsigned long long key,
+                                                  int x0, int y0) {
     const uint32_t r = (uint32_t)(key & 0xffffffffull);
     const uint2 bm = __ldg(ws.rec_bmask + r);
     const int tx0 = (int)(bm.y & 0xfff), ty0 = (int)((bm.y >> 12) & 0xfff), ntx = (int)(bm.y >> 24);
-    const int q = (y0 / SS_TILE - ty0) * ntx + (x0 / SS_TILE - tx0);
+    const int q = ((y0 >> L->th_log2) - ty0) * ntx + ((x0 >> L->tw_log2) - tx0);
     if (q < 4) return (bm.x >> (8 * q)) & 0xffu;
     const float4 r3 = __ldg(&ws.rec[r].r3);
-    return rect_block_bits(__float_as_uint(r3.z), __float_as_uint(r3.w), x0, y0);
+    return rect_block_bits(__float_as_uint(r3.z), __float_as_uint(r3.w), x0, y0, L->bx, L->bpt);
 }
 
 // One thread per record: its keys go to the bins of the tiles its support
@@ -396,8 +399,9 @@ __global__ void __launch_bounds__(256) scatter_kernel(ss_ws_view ws, int64_t tot
     }
     const ss_view_layout& vl = L->v[v];
     const uint32_t rx = __float_as_uint(r3.z), ry = __float_as_uint(r3.w);
-    const int tx0 = (int)(rx & 0xffff) / SS_TILE, tx1 = (int)(rx >> 16) / SS_TILE;
-    const int ty0 = (int)(ry & 0xffff) / SS_TILE, ty1 = (int)(ry >> 16) / SS_TILE;
+    const int tx0 = (int)(rx & 0xffff) >> L->tw_log2, tx1 = (int)(rx >> 16) >> L->tw_log2;
+    const int ty0 = (int)(ry & 0xffff) >> L->th_log2, ty1 = (int)(ry >> 16) >> L->th_log2;
+    const int bxn = L->bx, bpt = L->bpt;
     const int ntx = tx1 - tx0 + 1, nt = ntx * (ty1 - ty0 + 1);
     // low half: the batch-wide record index (ties of z_start in one tile, which
     // belongs to one view, are broken by surfel index all the same)
@@ -411,8 +415,9 @@ __global__ void __launch_bounds__(256) scatter_kernel(ss_ws_view ws, int64_t tot
             const int t = vl.tile_off + ty * vl.tiles_x + tx;
             const uint64_t p = (uint64_t)ws.tile_start[t] + rks[q];
             if ((int64_t)p < ws.max_instances) ws.keys[p] = key;
-            uint32_t m = rect_block_bits(rx, ry, tx * SS_TILE, ty * SS_TILE);
-            if (exact && m) m = exact_block_bits(m, P, r1, r2, tx * SS_TILE, ty * SS_TILE, rc2);
+            const int ox = tx << L->tw_log2, oy = ty << L->th_log2;
+            uint32_t m = rect_block_bits(rx, ry, ox, oy, bxn, bpt);
+            if (exact && m) m = exact_block_bits(m, P, r1, r2, ox, oy, rc2, bxn);
             masks |= m << (8 * q);
         }
     ws.rec_bmask[r] = make_uint2(masks, (uint32_t)tx0 | ((uint32_t)ty0 << 12) | ((uint32_t)min(ntx, 255) << 24));
@@ -532,7 +537,7 @@ __device__ __noinline__ void sort_chunk(const ss_ws_view& ws, unsigned long long
             uint32_t mm[G];
 #pragma unroll
             for (int k = 0; k < G; ++k)
-                if (base + k0 + k < m) mm[k] = block_mask_of(ws, x[k0 + k], x0, y0);
+                if (base + k0 + k < m) mm[k] = block_mask_of(ws, ws.layout, x[k0 + k], x0, y0);
 #pragma unroll
             for (int k = 0; k < G; ++k)
                 if (base + k0 + k < m) BM[base + k0 + k] = (uint8_t)mm[k];
@@ -556,11 +561,11 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view w
         const ss_layout* L = ws.layout;
         const ss_view_layout& vl = L->v[find_view_tile(L, t)];
         const int lt = t - vl.tile_off;
-        x0 = (lt % vl.tiles_x) * SS_TILE;
-        y0 = (lt / vl.tiles_x) * SS_TILE;
+        x0 = (lt % vl.tiles_x) << L->tw_log2;
+        y0 = (lt / vl.tiles_x) << L->th_log2;
     }
     if (n == 1) {
-        if (threadIdx.x == 0) BM[0] = (uint8_t)block_mask_of(ws, K[0], x0, y0);
+        if (threadIdx.x == 0) BM[0] = (uint8_t)block_mask_of(ws, ws.layout, K[0], x0, y0);
         return;
     }
     unsigned long long* Alt = ws.keys_alt + b;
@@ -596,7 +601,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view w
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const unsigned long long k = src[i];
         if (src != K) K[i] = k;
-        BM[i] = (uint8_t)block_mask_of(ws, k, x0, y0);
+        BM[i] = (uint8_t)block_mask_of(ws, ws.layout, k, x0, y0);
     }
 }
 
@@ -629,16 +634,16 @@ void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_a
 template <bool STATS, bool PP, bool CONS, int RWPB_FWD>
 __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_fwd_args& a, const int gw,
                                                  unsigned char* fwd_smem) {
-    ss_wstage* Wst = reinterpret_cast<ss_wstage*>(fwd_smem);   // [RWPB_FWD warps][2]
+    ss_wstage* Wst = reinterpret_cast<ss_wstage*>(fwd_smem);   // [RWPB_FWD warps][stage depth]
     const ss_layout* L = ws.layout;
     const int lw = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = gw >> 3, warp = gw & 7;          // 8 blocks per tile
+    const int tile = gw / L->bpt, warp = gw - tile * L->bpt;        // bpt blocks per tile
     const int view = find_view_tile(L, tile);
     const ss_view_layout& vl = L->v[view];
     const int lt = tile - vl.tile_off;
     const int tx = lt % vl.tiles_x, ty = lt / vl.tiles_x;
-    const int x0 = tx * SS_TILE, y0 = ty * SS_TILE;
-    const int wx0 = 8 * (warp & 1), wy0 = 4 * (warp >> 1);         // 8 x 4 pixel block per warp
+    const int x0 = tx << L->tw_log2, y0 = ty << L->th_log2;
+    const int wx0 = 8 * (warp % L->bx), wy0 = 4 * (warp / L->bx);  // 8 x 4 pixel block per warp
     const int lx = wx0 + (lane & 7), ly = wy0 + (lane >> 3);
     const int px = x0 + lx, py = y0 + ly;
     const bool inside = px < vl.width && py < vl.height;
@@ -721,7 +726,7 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
     // warp's own region of 8 x the tile's list
     uint2* clist = ws.cover_list ? ws.cover_list + 8 * beg + (int64_t)warp * (end - beg) : nullptr;
     uint32_t n_list = 0;
-    ss_wstage* Wb = Wst + 2 * lw;
+    ss_wstage* Wb = Wst + (a.p.stage_depth ? a.p.stage_depth : 2) * lw;
     // pass 1: the records whose support rectangle meets the block, in list
     // order, into the warp's candidate list (four chunks of keys in flight)
     uint32_t* cand = ws.cand_list + 8 * beg + (int64_t)warp * (end - beg);
@@ -739,24 +744,30 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
         }
     }
     __syncwarp();
-    // pass 2: the candidates 32 at a time, two-deep staging pipeline
+    // pass 2: the candidates 32 at a time through a ring of D staging buffers
+    // (chunks c+1 .. c+D-1 in flight while chunk c is processed)
+    const int D = a.p.stage_depth ? a.p.stage_depth : 2;
+    for (int j = 0; j + 1 < D; ++j) {   // prologue: the first D - 1 chunks
+        const bool act = 32 * j + lane < n_cand;
+        stage_ids(Wb[j], recs, act ? cand[32 * j + lane] : 0u, lane, act);
+    }
     int buf = 0;
-    uint32_t idn = lane < n_cand ? cand[lane] : 0u;
-    if (n_cand > 0) stage_ids(Wb[0], recs, idn, lane, lane < n_cand);
-    idn = 32 + lane < n_cand ? cand[32 + lane] : 0u;
     for (int b0 = 0; b0 < n_cand; b0 += 32) {
         if (__all_sync(0xffffffffu, done)) break;   // every pixel of the block has K_max layers
-        ss_wstage& W = Wb[buf];
-        const int n = min(32, n_cand - b0);
-        stage_finish(W, n, lane, (float)x0, (float)y0);
-        const int n2 = min(32, n_cand - b0 - 32);
-        if (n2 > 0) stage_ids(Wb[buf ^ 1], recs, idn, lane, lane < n2);
-        idn = b0 + 64 + lane < n_cand ? cand[b0 + 64 + lane] : 0u;
-        if (b0 + 64 + lane < n_cand) {   // ask L2 for the records two chunks ahead
-            const char* pr = reinterpret_cast<const char*>(recs + idn);
+        {   // chunk b0 + 32 (D - 1) into the buffer processed last (one copy group, maybe empty)
+            const int c0 = b0 + 32 * (D - 1);
+            const int ib = buf + D - 1 >= D ? buf - 1 : buf + D - 1;
+            const bool act = c0 + lane < n_cand;
+            stage_ids(Wb[ib], recs, act ? cand[c0 + lane] : 0u, lane, act);
+        }
+        if (b0 + 32 * D + lane < n_cand) {   // ask L2 for the records a chunk beyond the ring
+            const char* pr = reinterpret_cast<const char*>(recs + cand[b0 + 32 * D + lane]);
             asm volatile("prefetch.global.L2 [%0];\n" ::"l"(pr));
             asm volatile("prefetch.global.L2 [%0];\n" ::"l"(pr + sizeof(ss_rec) - 1));
         }
+        ss_wstage& W = Wb[buf];
+        const int n = min(32, n_cand - b0);
+        stage_finish(W, n, lane, (float)x0, (float)y0, D - 1);
         uint32_t my_mask = 0;
         // (every candidate may reach a pixel centre of the block: its block bit is set)
         for (uint32_t live = n >= 32 ? 0xffffffffu : ((1u << n) - 1u); live; live &= live - 1) {
@@ -819,10 +830,10 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
             if (keep) clist[n_list + __popc(km & ((1u << lane) - 1u))] = make_uint2(W.id[lane], my_mask);
             n_list += __popc(km);
         }
-        buf ^= 1;
+        buf = buf + 1 == D ? 0 : buf + 1;
         __syncwarp();
     }
-    cp_async_wait0();   // copies of a chunk an early exit left unread
+    cp_async_wait0();   // copies of chunks an early exit left unread
     if (clist && lane == 0) ws.cover_count[(int64_t)tile * 8 + warp] = n_list;
     if (!done && Wg > 0.f) flush();
     if (STATS) {
@@ -870,11 +881,13 @@ __global__ void __launch_bounds__(32 * RWPB_FWD, 24 / RWPB_FWD) raster_fwd_kerne
 
 template <bool STATS, bool PP, bool CONS, int W>
 static void launch_raster_fwd(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st) {
-    const int smem = 2 * W * (int)sizeof(ss_wstage);
-    static std::atomic<unsigned long long> optin{0}, resident{0};
-    ss_smem_optin(raster_fwd_kernel<STATS, PP, CONS, W>, smem, optin);
-    const int n_items = (int)(L.total_tiles * 8);
-    const int ctas = ss_resident_ctas(raster_fwd_kernel<STATS, PP, CONS, W>, 32 * W, smem, resident);
+    const int D = a.p.stage_depth ? a.p.stage_depth : 2;
+    const int smem = D * W * (int)sizeof(ss_wstage);
+    // opt in once for the deepest ring; resident CTAs depend on the depth
+    static std::atomic<unsigned long long> optin{0}, resident[4];
+    ss_smem_optin(raster_fwd_kernel<STATS, PP, CONS, W>, 3 * W * (int)sizeof(ss_wstage), optin);
+    const int n_items = (int)(L.total_tiles * L.bpt);
+    const int ctas = ss_resident_ctas(raster_fwd_kernel<STATS, PP, CONS, W>, 32 * W, smem, resident[D]);
     const int grid = max(1, min(ctas > 0 ? ctas : 1, (n_items + W - 1) / W));
     raster_fwd_kernel<STATS, PP, CONS, W><<<grid, 32 * W, smem, st>>>(ws, a, n_items);
 }

@@ -8,8 +8,7 @@
 
 #include "ss3d.h"
 
-#define SS_TILE 16                 // 16 x 16 pixel tiles (App. A)
-#define SS_TILE_PIX (SS_TILE * SS_TILE)
+#define SS_TILE 16                 // default 16 x 16 pixel tiles (App. A); the batch's tile shape is in ss_layout
 #define SS_NCH 12                  // averaged channels: rgb, albedo 3, rough, metal, normal 3, depth
 // Tile counters and cursors take the atomics of every tile instance; one per
 // SS_CNT_STRIDE words spreads them over the L2 slices instead of a few.
@@ -39,6 +38,9 @@ struct ss_layout {
     int32_t n_views, n_scenes;
     int32_t total_tiles;
     int32_t k_max;
+    // screen tile: (1 << tw_log2) x (1 << th_log2) pixels, made of bx x by
+    // blocks of 8 x 4 pixels (one warp each), bpt = bx by <= 8 blocks per tile
+    int32_t tw_log2, th_log2, bx, bpt;
     int64_t total_pixels;
     int64_t total_records;
     int64_t scene_begin[SS_MAX_SCENES + 1];

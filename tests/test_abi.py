@@ -32,7 +32,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_struct_sizes_match_header():
     assert ctypes.sizeof(_lib.ss_camera) == 80
-    assert ctypes.sizeof(_lib.ss_render_params) == 80
+    assert ctypes.sizeof(_lib.ss_render_params) == 96
     assert ctypes.sizeof(_lib.ss_surfel_grads) == 64
     assert ctypes.sizeof(_lib.ss_stats) == 72
 
@@ -95,7 +95,8 @@ def test_launch_shape_knobs_are_validated_on_the_host():
     nb = ctypes.c_size_t()
     assert lib.ss_workspace_size(ctypes.byref(d), ctypes.byref(p), ctypes.byref(ed), 1, ctypes.byref(nb)) == 0
     for knob, bad, good in (("fwd_warps", 3, 4), ("bwd_warps", 1, 8), ("pbwd_block", 16, 32),
-                            ("pbwd_block", 4096, 1024)):
+                            ("pbwd_block", 4096, 1024), ("tile_w", 12, 8), ("tile_h", 2, 4),
+                            ("stage_depth", 4, 3), ("mip_mode", 3, 2), ("screen_grad", 2, 1)):
         q = _lib.ss_render_params()
         ctypes.memmove(ctypes.byref(q), ctypes.byref(p), ctypes.sizeof(q))
         setattr(q, knob, bad)
@@ -130,3 +131,22 @@ def test_render_calls_reject_null_device_pointers():
     assert st == _lib.SS_ERR_INVALID_ARG
     assert lib.ss_env_prefilter(ctypes.byref(ed), 1, None, None, None, None, None) == _lib.SS_ERR_INVALID_ARG
     assert lib.ss_env_prefilter_noalloc(ctypes.byref(ed), 1, None, None, None, None) == _lib.SS_ERR_INVALID_ARG
+
+
+def test_tile_shapes_validated_on_the_host():
+    """Tiles are unions of 8 x 4 blocks, at most 8 per tile: 32 x 16 (16 blocks)
+    is refused, 8 x 32 and 32 x 8 (8 blocks) are accepted."""
+    lib = _lib.lib()
+    p = _lib.ss_render_params()
+    lib.ss_default_params(ctypes.byref(p))
+    p.max_instances = 1000
+    cams = (_lib.ss_camera * 1)()
+    cams[0].width = cams[0].height = 40
+    cams[0].fx = cams[0].fy = 10.0
+    off = (ctypes.c_int64 * 2)(0, 10)
+    d = _lib.ss_batch_desc(1, 1, off, cams, None)
+    nb = ctypes.c_size_t()
+    for (w, h, ok) in ((32, 16, False), (32, 32, False), (8, 32, True), (32, 8, True), (8, 4, True), (16, 16, True)):
+        p.tile_w, p.tile_h = w, h
+        st = lib.ss_workspace_size(ctypes.byref(d), ctypes.byref(p), None, 0, ctypes.byref(nb))
+        assert (st == 0) == ok, (w, h)
