@@ -152,6 +152,7 @@ static ss_status build_layout(const ss_batch_desc* b, const ss_render_params* p,
         L->tw_log2 = 31 - __builtin_clz((unsigned)tw);
         L->th_log2 = 31 - __builtin_clz((unsigned)th);
         L->bx = tw / 8;
+        L->bx_log2 = L->tw_log2 - 3;
         L->bpt = (tw / 8) * (th / 4);
     }
     for (int s = 0; s <= b->n_scenes; ++s) {

@@ -348,7 +348,7 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
     const int x0 = tx << L->tw_log2, y0 = ty << L->th_log2;
     ss_wstage* Wc = Wst + lw;         // staging buffer
     bwarp& B = Bws[lw];
-    const int wx0 = 8 * (warp % L->bx), wy0 = 4 * (warp / L->bx);
+    const int wx0 = 8 * (warp & (L->bx - 1)), wy0 = 4 * (warp >> L->bx_log2);
     const int lx = wx0 + (lane & 7), ly = wy0 + (lane >> 3);
     const int px = x0 + lx, py = y0 + ly;
     const bool inside = px < vl.width && py < vl.height;

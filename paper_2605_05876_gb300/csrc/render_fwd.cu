@@ -335,27 +335,27 @@ __global__ void __launch_bounds__(1024) scan_kernel(const uint32_t* cnt, const u
 // the records, computes the masks of each record's first four tiles; the sort
 // kernel reads them back for the sorted instances (instances past a record's
 // fourth tile keep the rectangle test alone).
-// (block b of a tile of bx blocks across sits at (8 (b % bx), 4 (b / bx)))
-__device__ __forceinline__ uint32_t rect_block_bits(uint32_t rx, uint32_t ry, int x0, int y0, int bx, int bpt) {
+// (block b of a tile of 2^bxl blocks across sits at (8 (b mod 2^bxl), 4 (b >> bxl)))
+__device__ __forceinline__ uint32_t rect_block_bits(uint32_t rx, uint32_t ry, int x0, int y0, int bxl, int bpt) {
     const int i0 = (int)(rx & 0xffff), i1 = (int)(rx >> 16), j0 = (int)(ry & 0xffff), j1 = (int)(ry >> 16);
     uint32_t m = 0;
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
         if (b >= bpt) break;
-        const int gx0 = x0 + 8 * (b % bx), gy0 = y0 + 4 * (b / bx);
+        const int gx0 = x0 + 8 * (b & ((1 << bxl) - 1)), gy0 = y0 + 4 * (b >> bxl);
         if (i0 <= gx0 + 7 && i1 >= gx0 && j0 <= gy0 + 3 && j1 >= gy0) m |= 1u << b;
     }
     return m;
 }
 
 __device__ __forceinline__ uint32_t exact_block_bits(uint32_t m, float4 P, float4 r1, float4 r2, int x0, int y0,
-                                                     float rc2, int bx) {
+                                                     float rc2, int bxl) {
     const float prx = __fadd_rn(__fsub_rn(r2.x, (float)x0), r2.z);
     const float pry = __fadd_rn(__fsub_rn(r2.y, (float)y0), r2.w);
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
         if (!((m >> b) & 1u)) continue;
-        const float dxb = (float)(8 * (b % bx)) - prx, dyb = (float)(4 * (b / bx)) - pry;
+        const float dxb = (float)(8 * (b & ((1 << bxl) - 1))) - prx, dyb = (float)(4 * (b >> bxl)) - pry;
         if (!ss_box_may_cover(P, r1.x, r1.y, rc2, dxb + 0.5f, dxb + 7.5f, dyb + 0.5f, dyb + 3.5f)) m &= ~(1u << b);
     }
     return m;
@@ -371,7 +371,7 @@ __device__ __forceinline__ uint32_t block_mask_of(const ss_ws_view& ws, const ss
     const int q = ((y0 >> L->th_log2) - ty0) * ntx + ((x0 >> L->tw_log2) - tx0);
     if (q < 4) return (bm.x >> (8 * q)) & 0xffu;
     const float4 r3 = __ldg(&ws.rec[r].r3);
-    return rect_block_bits(__float_as_uint(r3.z), __float_as_uint(r3.w), x0, y0, L->bx, L->bpt);
+    return rect_block_bits(__float_as_uint(r3.z), __float_as_uint(r3.w), x0, y0, L->bx_log2, L->bpt);
 }
 
 // One thread per record: its keys go to the bins of the tiles its support
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(ss_ws_view ws, int64_t tot
     const uint32_t rx = __float_as_uint(r3.z), ry = __float_as_uint(r3.w);
     const int tx0 = (int)(rx & 0xffff) >> L->tw_log2, tx1 = (int)(rx >> 16) >> L->tw_log2;
     const int ty0 = (int)(ry & 0xffff) >> L->th_log2, ty1 = (int)(ry >> 16) >> L->th_log2;
-    const int bxn = L->bx, bpt = L->bpt;
+    const int bxl = L->bx_log2, bpt = L->bpt;
     const int ntx = tx1 - tx0 + 1, nt = ntx * (ty1 - ty0 + 1);
     // low half: the batch-wide record index (ties of z_start in one tile, which
     // belongs to one view, are broken by surfel index all the same)
@@ -416,8 +416,8 @@ __global__ void __launch_bounds__(256) scatter_kernel(ss_ws_view ws, int64_t tot
             const uint64_t p = (uint64_t)ws.tile_start[t] + rks[q];
             if ((int64_t)p < ws.max_instances) ws.keys[p] = key;
             const int ox = tx << L->tw_log2, oy = ty << L->th_log2;
-            uint32_t m = rect_block_bits(rx, ry, ox, oy, bxn, bpt);
-            if (exact && m) m = exact_block_bits(m, P, r1, r2, ox, oy, rc2, bxn);
+            uint32_t m = rect_block_bits(rx, ry, ox, oy, bxl, bpt);
+            if (exact && m) m = exact_block_bits(m, P, r1, r2, ox, oy, rc2, bxl);
             masks |= m << (8 * q);
         }
     ws.rec_bmask[r] = make_uint2(masks, (uint32_t)tx0 | ((uint32_t)ty0 << 12) | ((uint32_t)min(ntx, 255) << 24));
@@ -643,7 +643,7 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
     const int lt = tile - vl.tile_off;
     const int tx = lt % vl.tiles_x, ty = lt / vl.tiles_x;
     const int x0 = tx << L->tw_log2, y0 = ty << L->th_log2;
-    const int wx0 = 8 * (warp % L->bx), wy0 = 4 * (warp / L->bx);  // 8 x 4 pixel block per warp
+    const int wx0 = 8 * (warp & (L->bx - 1)), wy0 = 4 * (warp >> L->bx_log2);   // 8 x 4 pixel block per warp
     const int lx = wx0 + (lane & 7), ly = wy0 + (lane >> 3);
     const int px = x0 + lx, py = y0 + ly;
     const bool inside = px < vl.width && py < vl.height;

@@ -40,7 +40,7 @@ struct ss_layout {
     int32_t k_max;
     // screen tile: (1 << tw_log2) x (1 << th_log2) pixels, made of bx x by
     // blocks of 8 x 4 pixels (one warp each), bpt = bx by <= 8 blocks per tile
-    int32_t tw_log2, th_log2, bx, bpt;
+    int32_t tw_log2, th_log2, bx, bpt, bx_log2, pad_;
     int64_t total_pixels;
     int64_t total_records;
     int64_t scene_begin[SS_MAX_SCENES + 1];
