@@ -398,6 +398,7 @@ static ss_status forward_core(const ss_batch_desc* b, const ss_surfels* s, const
     ss_fwd_args a;
     a.s = *s;
     a.p = *p;
+    a.ts = {L.tw_log2, L.th_log2, L.bx_log2, L.bpt};
     if (p->mip_mode == 1) a.p.sigma_f = 0.f;   // no MIP filter: Sigma_mip = I, n_f = 1
     a.ed = *ed;
     a.env = *env;
@@ -490,6 +491,7 @@ extern "C" ss_status ss_render_backward(const ss_batch_desc* b, const ss_surfels
     ss_bwd_args a;
     a.f.s = *s;
     a.f.p = *p;
+    a.f.ts = {L.tw_log2, L.th_log2, L.bx_log2, L.bpt};
     if (p->mip_mode == 1) a.f.p.sigma_f = 0.f;
     a.f.ed = *ed;
     a.f.env = *env;

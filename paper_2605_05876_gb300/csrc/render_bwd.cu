@@ -340,15 +340,15 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
     ss_wjac* Wjs = reinterpret_cast<ss_wjac*>(bwd_smem + RWPB_BWD * (sizeof(ss_wstage) + sizeof(bwarp)));
     const ss_layout* L = ws.layout;
     const int lw = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = gw / L->bpt, warp = gw - tile * L->bpt;        // bpt blocks per tile
+    const int tile = gw / a.f.ts.bpt, warp = gw - tile * a.f.ts.bpt;   // bpt blocks per tile
     const int view = find_view_tile(L, tile);
     const ss_view_layout& vl = L->v[view];
     const int lt = tile - vl.tile_off;
     const int tx = lt % vl.tiles_x, ty = lt / vl.tiles_x;
-    const int x0 = tx << L->tw_log2, y0 = ty << L->th_log2;
+    const int x0 = tx << a.f.ts.tw_log2, y0 = ty << a.f.ts.th_log2;
     ss_wstage* Wc = Wst + lw;         // staging buffer
     bwarp& B = Bws[lw];
-    const int wx0 = 8 * (warp & (L->bx - 1)), wy0 = 4 * (warp >> L->bx_log2);
+    const int wx0 = 8 * (warp & ((1 << a.f.ts.bx_log2) - 1)), wy0 = 4 * (warp >> a.f.ts.bx_log2);
     const int lx = wx0 + (lane & 7), ly = wy0 + (lane >> 3);
     const int px = x0 + lx, py = y0 + ly;
     const bool inside = px < vl.width && py < vl.height;

@@ -250,7 +250,8 @@ __global__ void __launch_bounds__(256, 4) project_kernel(ss_ws_view ws, ss_fwd_a
             // bin counts: the record's rank in the bins of its first four tiles
             // (kept for the scatter, which then needs no atomics for them),
             // plain counts for the rest
-            const int tx0 = i0 >> L->tw_log2, tx1 = i1 >> L->tw_log2, ty0 = j0 >> L->th_log2, ty1 = j1 >> L->th_log2;
+            const int tx0 = i0 >> a.ts.tw_log2, tx1 = i1 >> a.ts.tw_log2, ty0 = j0 >> a.ts.th_log2,
+                      ty1 = j1 >> a.ts.th_log2;
             const int ntx = tx1 - tx0 + 1, nt = ntx * (ty1 - ty0 + 1);
             uint32_t rk[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
@@ -363,22 +364,23 @@ __device__ __forceinline__ uint32_t exact_block_bits(uint32_t m, float4 P, float
 
 // the block mask of a sorted instance (key) in tile (x0, y0): from the
 // scatter's per-record masks, or the rectangle test past the fourth tile
-__device__ __forceinline__ uint32_t block_mask_of(const ss_ws_view& ws, const ss_layout* L, unsigned long long key,
-                                                  int x0, int y0) {
+__device__ __forceinline__ uint32_t block_mask_of(const ss_ws_view& ws, const ss_tile_shape& ts,
+                                                  unsigned long long key, int x0, int y0) {
     const uint32_t r = (uint32_t)(key & 0xffffffffull);
     const uint2 bm = __ldg(ws.rec_bmask + r);
     const int tx0 = (int)(bm.y & 0xfff), ty0 = (int)((bm.y >> 12) & 0xfff), ntx = (int)(bm.y >> 24);
-    const int q = ((y0 >> L->th_log2) - ty0) * ntx + ((x0 >> L->tw_log2) - tx0);
+    const int q = ((y0 >> ts.th_log2) - ty0) * ntx + ((x0 >> ts.tw_log2) - tx0);
     if (q < 4) return (bm.x >> (8 * q)) & 0xffu;
     const float4 r3 = __ldg(&ws.rec[r].r3);
-    return rect_block_bits(__float_as_uint(r3.z), __float_as_uint(r3.w), x0, y0, L->bx_log2, L->bpt);
+    return rect_block_bits(__float_as_uint(r3.z), __float_as_uint(r3.w), x0, y0, ts.bx_log2, ts.bpt);
 }
 
 // One thread per record: its keys go to the bins of the tiles its support
 // rectangle covers, at the ranks the projection took in the bins of its
 // first four tiles; instances past those take positions behind the first-
 // four instances of their bin by counting the bin's cursor down.
-__global__ void __launch_bounds__(256) scatter_kernel(ss_ws_view ws, int64_t total_records, float rc2, int exact) {
+__global__ void __launch_bounds__(256) scatter_kernel(ss_ws_view ws, int64_t total_records, float rc2, int exact,
+                                                      ss_tile_shape ts) {
     const ss_layout* L = ws.layout;
     int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= total_records) return;
@@ -399,9 +401,9 @@ __global__ void __launch_bounds__(256) scatter_kernel(ss_ws_view ws, int64_t tot
     }
     const ss_view_layout& vl = L->v[v];
     const uint32_t rx = __float_as_uint(r3.z), ry = __float_as_uint(r3.w);
-    const int tx0 = (int)(rx & 0xffff) >> L->tw_log2, tx1 = (int)(rx >> 16) >> L->tw_log2;
-    const int ty0 = (int)(ry & 0xffff) >> L->th_log2, ty1 = (int)(ry >> 16) >> L->th_log2;
-    const int bxl = L->bx_log2, bpt = L->bpt;
+    const int tx0 = (int)(rx & 0xffff) >> ts.tw_log2, tx1 = (int)(rx >> 16) >> ts.tw_log2;
+    const int ty0 = (int)(ry & 0xffff) >> ts.th_log2, ty1 = (int)(ry >> 16) >> ts.th_log2;
+    const int bxl = ts.bx_log2, bpt = ts.bpt;
     const int ntx = tx1 - tx0 + 1, nt = ntx * (ty1 - ty0 + 1);
     // low half: the batch-wide record index (ties of z_start in one tile, which
     // belongs to one view, are broken by surfel index all the same)
@@ -415,7 +417,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(ss_ws_view ws, int64_t tot
             const int t = vl.tile_off + ty * vl.tiles_x + tx;
             const uint64_t p = (uint64_t)ws.tile_start[t] + rks[q];
             if ((int64_t)p < ws.max_instances) ws.keys[p] = key;
-            const int ox = tx << L->tw_log2, oy = ty << L->th_log2;
+            const int ox = tx << ts.tw_log2, oy = ty << ts.th_log2;
             uint32_t m = rect_block_bits(rx, ry, ox, oy, bxl, bpt);
             if (exact && m) m = exact_block_bits(m, P, r1, r2, ox, oy, rc2, bxl);
             masks |= m << (8 * q);
@@ -520,7 +522,8 @@ __device__ void merge_runs(const unsigned long long* A, int na, const unsigned l
 // block masks of the sorted keys.
 template <int KPL>
 __device__ __noinline__ void sort_chunk(const ss_ws_view& ws, unsigned long long* K, uint8_t* BM, int m, int N,
-                                           bool gather, int x0, int y0, unsigned long long* xs) {
+                                           bool gather, const ss_tile_shape& ts, int x0, int y0,
+                                           unsigned long long* xs) {
     const int base = threadIdx.x * KPL;
     unsigned long long x[KPL];
 #pragma unroll
@@ -537,7 +540,7 @@ __device__ __noinline__ void sort_chunk(const ss_ws_view& ws, unsigned long long
             uint32_t mm[G];
 #pragma unroll
             for (int k = 0; k < G; ++k)
-                if (base + k0 + k < m) mm[k] = block_mask_of(ws, ws.layout, x[k0 + k], x0, y0);
+                if (base + k0 + k < m) mm[k] = block_mask_of(ws, ts, x[k0 + k], x0, y0);
 #pragma unroll
             for (int k = 0; k < G; ++k)
                 if (base + k0 + k < m) BM[base + k0 + k] = (uint8_t)mm[k];
@@ -546,7 +549,7 @@ __device__ __noinline__ void sort_chunk(const ss_ws_view& ws, unsigned long long
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view ws, int total_tiles) {
+__global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view ws, int total_tiles, ss_tile_shape ts) {
     extern __shared__ unsigned long long xs[];
     const int t = blockIdx.x;
     const int64_t cap = ws.max_instances;
@@ -561,11 +564,11 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view w
         const ss_layout* L = ws.layout;
         const ss_view_layout& vl = L->v[find_view_tile(L, t)];
         const int lt = t - vl.tile_off;
-        x0 = (lt % vl.tiles_x) << L->tw_log2;
-        y0 = (lt / vl.tiles_x) << L->th_log2;
+        x0 = (lt % vl.tiles_x) << ts.tw_log2;
+        y0 = (lt / vl.tiles_x) << ts.th_log2;
     }
     if (n == 1) {
-        if (threadIdx.x == 0) BM[0] = (uint8_t)block_mask_of(ws, ws.layout, K[0], x0, y0);
+        if (threadIdx.x == 0) BM[0] = (uint8_t)block_mask_of(ws, ts, K[0], x0, y0);
         return;
     }
     unsigned long long* Alt = ws.keys_alt + b;
@@ -576,10 +579,10 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view w
         int N = 2;
         while (N < m) N <<= 1;
         const bool gather = n <= SORT_CAP;
-        if (N <= SORT_THREADS * 4) sort_chunk<4>(ws, K + c0, BM + c0, m, N, gather, x0, y0, xs);
-        else if (N <= SORT_THREADS * 8) sort_chunk<8>(ws, K + c0, BM + c0, m, N, gather, x0, y0, xs);
-        else if (N <= SORT_THREADS * 16) sort_chunk<16>(ws, K + c0, BM + c0, m, N, gather, x0, y0, xs);
-        else sort_chunk<SORT_KPL>(ws, K + c0, BM + c0, m, N, gather, x0, y0, xs);
+        if (N <= SORT_THREADS * 4) sort_chunk<4>(ws, K + c0, BM + c0, m, N, gather, ts, x0, y0, xs);
+        else if (N <= SORT_THREADS * 8) sort_chunk<8>(ws, K + c0, BM + c0, m, N, gather, ts, x0, y0, xs);
+        else if (N <= SORT_THREADS * 16) sort_chunk<16>(ws, K + c0, BM + c0, m, N, gather, ts, x0, y0, xs);
+        else sort_chunk<SORT_KPL>(ws, K + c0, BM + c0, m, N, gather, ts, x0, y0, xs);
     }
     if (n <= SORT_CAP) return;
     // pairwise merges in global memory, ping-pong between K and Alt
@@ -601,7 +604,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view w
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const unsigned long long k = src[i];
         if (src != K) K[i] = k;
-        BM[i] = (uint8_t)block_mask_of(ws, ws.layout, k, x0, y0);
+        BM[i] = (uint8_t)block_mask_of(ws, ts, k, x0, y0);
     }
 }
 
@@ -613,12 +616,13 @@ void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_a
     if (L.total_records > 0) {
         ss_note_launch();
         scatter_kernel<<<(unsigned)((L.total_records + 255) / 256), 256, 0, st>>>(
-            ws, L.total_records, a.p.r_cut * a.p.r_cut, a.p.mip_mode == 2 ? 0 : 1);
+            ws, L.total_records, a.p.r_cut * a.p.r_cut, a.p.mip_mode == 2 ? 0 : 1, a.ts);
     }
     static std::atomic<unsigned long long> optin{0};
     ss_smem_optin(tile_sort_kernel, SORT_CAP * (int)sizeof(unsigned long long), optin);
     ss_note_launch();
-    tile_sort_kernel<<<L.total_tiles, SORT_THREADS, SORT_CAP * sizeof(unsigned long long), st>>>(ws, L.total_tiles);
+    tile_sort_kernel<<<L.total_tiles, SORT_THREADS, SORT_CAP * sizeof(unsigned long long), st>>>(ws, L.total_tiles,
+                                                                                                 a.ts);
 }
 
 // ------------------------------------------------------------------------
@@ -637,13 +641,13 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
     ss_wstage* Wst = reinterpret_cast<ss_wstage*>(fwd_smem);   // [RWPB_FWD warps][stage depth]
     const ss_layout* L = ws.layout;
     const int lw = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = gw / L->bpt, warp = gw - tile * L->bpt;        // bpt blocks per tile
+    const int tile = gw / a.ts.bpt, warp = gw - tile * a.ts.bpt;    // bpt blocks per tile
     const int view = find_view_tile(L, tile);
     const ss_view_layout& vl = L->v[view];
     const int lt = tile - vl.tile_off;
     const int tx = lt % vl.tiles_x, ty = lt / vl.tiles_x;
-    const int x0 = tx << L->tw_log2, y0 = ty << L->th_log2;
-    const int wx0 = 8 * (warp & (L->bx - 1)), wy0 = 4 * (warp >> L->bx_log2);   // 8 x 4 pixel block per warp
+    const int x0 = tx << a.ts.tw_log2, y0 = ty << a.ts.th_log2;
+    const int wx0 = 8 * (warp & ((1 << a.ts.bx_log2) - 1)), wy0 = 4 * (warp >> a.ts.bx_log2);   // 8 x 4 block
     const int lx = wx0 + (lane & 7), ly = wy0 + (lane >> 3);
     const int px = x0 + lx, py = y0 + ly;
     const bool inside = px < vl.width && py < vl.height;
@@ -752,13 +756,15 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
         stage_ids(Wb[j], recs, act ? cand[32 * j + lane] : 0u, lane, act);
     }
     int buf = 0;
+    // record indices of the next chunk to issue, read one iteration ahead
+    uint32_t idn = 32 * (D - 1) + lane < n_cand ? cand[32 * (D - 1) + lane] : 0u;
     for (int b0 = 0; b0 < n_cand; b0 += 32) {
         if (__all_sync(0xffffffffu, done)) break;   // every pixel of the block has K_max layers
         {   // chunk b0 + 32 (D - 1) into the buffer processed last (one copy group, maybe empty)
             const int c0 = b0 + 32 * (D - 1);
             const int ib = buf + D - 1 >= D ? buf - 1 : buf + D - 1;
-            const bool act = c0 + lane < n_cand;
-            stage_ids(Wb[ib], recs, act ? cand[c0 + lane] : 0u, lane, act);
+            stage_ids(Wb[ib], recs, idn, lane, c0 + lane < n_cand);
+            idn = c0 + 32 + lane < n_cand ? cand[c0 + 32 + lane] : 0u;
         }
         if (b0 + 32 * D + lane < n_cand) {   // ask L2 for the records a chunk beyond the ring
             const char* pr = reinterpret_cast<const char*>(recs + cand[b0 + 32 * D + lane]);

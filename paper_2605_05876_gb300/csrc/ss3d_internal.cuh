@@ -373,9 +373,15 @@ int64_t ss_env_spec_floats(const ss_env_desc* d);
 int64_t ss_env_aux_floats(const ss_env_desc* d);
 void ss_env_level_size(const ss_env_desc* d, int i, int* W, int* H);
 
+// the batch's screen tile (copied from ss_layout into kernel arguments)
+struct ss_tile_shape {
+    int tw_log2, th_log2, bx_log2, bpt;
+};
+
 struct ss_fwd_args {
     ss_surfels s;
     ss_render_params p;
+    ss_tile_shape ts;
     ss_env_desc ed;
     ss_env_maps env;
     const ss_camera* cams;

@@ -31,7 +31,8 @@ def _check_view(r, scene, v, pix=None, env_cache=None):
     amb = _parity.ambiguous(ref["margin"])
     refv = np.concatenate([ref["rgba"], ref["aov"]], 1)
     n_bad, msg = _parity.compare(gpu, refv, amb, f"view {v}")
-    assert amb.mean() < _parity.MAX_AMBIGUOUS_FRACTION, f"too many ambiguous pixels: {amb.sum()}"
+    # (a sanity bound; small samples of covered pixels may hold a few more)
+    assert amb.sum() <= max(_parity.MAX_AMBIGUOUS_FRACTION * amb.size, 5), f"too many ambiguous pixels: {amb.sum()}"
     assert n_bad == 0, msg
     n_amb, n_flip = _parity.check_variants(gpu, ref, amb, pix=pix, prm=r.prm)
     print(f"view {v}: {n_amb} of {amb.size} pixels with a decision within rounding (fraction {amb.mean():.2e}), "
