@@ -518,12 +518,9 @@ __device__ void merge_runs(const unsigned long long* A, int na, const unsigned l
 }
 
 // Sort one chunk of m keys (N = the power of two >= m, N <= SORT_THREADS * KPL)
-// in registers, KPL per thread, and store it; with `gather`, also write the
-// block masks of the sorted keys.
+// in registers, KPL per thread, and store it.
 template <int KPL>
-__device__ __noinline__ void sort_chunk(const ss_ws_view& ws, unsigned long long* K, uint8_t* BM, int m, int N,
-                                           bool gather, const ss_tile_shape& ts, int x0, int y0,
-                                           unsigned long long* xs) {
+__device__ __noinline__ void sort_chunk(unsigned long long* K, int m, int N, unsigned long long* xs) {
     const int base = threadIdx.x * KPL;
     unsigned long long x[KPL];
 #pragma unroll
@@ -533,20 +530,13 @@ __device__ __noinline__ void sort_chunk(const ss_ws_view& ws, unsigned long long
 #pragma unroll
     for (int k = 0; k < KPL; ++k)
         if (base + k < m) K[base + k] = x[k];
-    if (gather) {
-        constexpr int G = KPL < 8 ? KPL : 8;   // gathers in flight
-#pragma unroll
-        for (int k0 = 0; k0 < KPL; k0 += G) {
-            uint32_t mm[G];
-#pragma unroll
-            for (int k = 0; k < G; ++k)
-                if (base + k0 + k < m) mm[k] = block_mask_of(ws, ts, x[k0 + k], x0, y0);
-#pragma unroll
-            for (int k = 0; k < G; ++k)
-                if (base + k0 + k < m) BM[base + k0 + k] = (uint8_t)mm[k];
-        }
-    }
     __syncthreads();
+}
+
+// block masks of n sorted keys, all threads of the CTA (coalesced key reads)
+__device__ __forceinline__ void gather_masks(const ss_ws_view& ws, const ss_tile_shape& ts, const unsigned long long* K,
+                                             uint8_t* BM, int n, int x0, int y0) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) BM[i] = (uint8_t)block_mask_of(ws, ts, K[i], x0, y0);
 }
 
 __global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view ws, int total_tiles, ss_tile_shape ts) {
@@ -578,13 +568,15 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view w
         const int m = min(SORT_CAP, n - c0);
         int N = 2;
         while (N < m) N <<= 1;
-        const bool gather = n <= SORT_CAP;
-        if (N <= SORT_THREADS * 4) sort_chunk<4>(ws, K + c0, BM + c0, m, N, gather, ts, x0, y0, xs);
-        else if (N <= SORT_THREADS * 8) sort_chunk<8>(ws, K + c0, BM + c0, m, N, gather, ts, x0, y0, xs);
-        else if (N <= SORT_THREADS * 16) sort_chunk<16>(ws, K + c0, BM + c0, m, N, gather, ts, x0, y0, xs);
-        else sort_chunk<SORT_KPL>(ws, K + c0, BM + c0, m, N, gather, ts, x0, y0, xs);
+        if (N <= SORT_THREADS * 4) sort_chunk<4>(K + c0, m, N, xs);
+        else if (N <= SORT_THREADS * 8) sort_chunk<8>(K + c0, m, N, xs);
+        else if (N <= SORT_THREADS * 16) sort_chunk<16>(K + c0, m, N, xs);
+        else sort_chunk<SORT_KPL>(K + c0, m, N, xs);
     }
-    if (n <= SORT_CAP) return;
+    if (n <= SORT_CAP) {
+        gather_masks(ws, ts, K, BM, n, x0, y0);
+        return;
+    }
     // pairwise merges in global memory, ping-pong between K and Alt
     unsigned long long *src = K, *dst = Alt;
     for (int w = SORT_CAP; w < n; w <<= 1) {
