@@ -622,10 +622,12 @@ def lookup_margins(S: dict, cam: dict, env_shape, prm: Params) -> np.ndarray:
     """Per surfel: the smallest distance (in texels) of any bilinear or level
     coordinate used by the shading (irradiance at n, the two specular levels
     at r, the BRDF table at (n.v, r), the level coordinate r (L-1)) to a
-    cell boundary.  The interpolation cell is a discrete choice; where this
-    margin is within rounding, implementations in different precisions may
-    pick neighbouring cells and differ in the derivative w.r.t. the lookup
-    direction (the value itself is continuous)."""
+    cell boundary, and the distances of n.w_o from 0 and of |n.w_o| from 1
+    (the two-sided flip of the normal and the clamp of n.w_o to [0, 1]).
+    Each is a discrete choice; where this margin is within rounding,
+    implementations in different precisions may take the other branch and
+    differ in the derivative (and, for the flip, in the sign of the normal's
+    contribution), though the shaded value itself is continuous."""
     with torch.no_grad():
         R = quat_to_rot(S["quat"])
         n = R[:, :, 2]
@@ -653,6 +655,8 @@ def lookup_margins(S: dict, cam: dict, env_shape, prm: Params) -> np.ndarray:
             m = torch.minimum(m, torch.minimum(frac(u * Ws - 0.5), frac(v * Hs - 0.5)))
         m = torch.minimum(m, torch.minimum(frac(mu * prm.lut_n - 0.5), frac(r * prm.lut_n - 0.5)))
         m = torch.minimum(m, frac(lc))
+        fa = torch.abs(facing[:, 0])
+        m = torch.minimum(m, torch.minimum(fa, 1.0 - fa))
     return m.numpy()
 
 
