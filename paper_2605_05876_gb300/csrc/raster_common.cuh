@@ -110,35 +110,65 @@ __device__ __forceinline__ void stage_finish(ss_wstage& W, int n, int lane, floa
     __syncwarp();
 }
 
-// Can a staged surfel cover a pixel whose centre offset d from the surfel
-// centre lies in the box [dx0, dx1] x [dy0, dy1]?  Coverage (ss_pixel_test)
-// needs f(d) = |P d|^2 - r^2 s2(d)^2 < 0 with s2 = 1 + A2 dx + B2 dy; f is the
+// Can a surfel cover a pixel whose centre offset d from the surfel centre
+// lies in the box [dx0, dx1] x [dy0, dy1]?  Coverage (ss_pixel_test) needs
+// f(d) = |P d|^2 - r^2 s2(d)^2 < 0 with s2 = 1 + A2 dx + B2 dy; f is the
 // quadratic d^T Q2 d - 2 r^2 g.d - r^2 with Q2 = P^T P - r^2 g g^T, g = (A2, B2).
 // When Q2 is positive definite the minimum of f over the box is at the free
-// minimiser (if inside; f < 0 there) or on an edge (a clamped 1-D minimum per
-// edge).  Returns false only when that minimum exceeds a margin far above the
+// minimiser d_s (if inside; f < 0 there) or on an edge (a clamped 1-D minimum
+// per edge), and {f < t} is the ellipse (d - d_s)^T Q2 (d - d_s) < kappa + t,
+// kappa = -f(d_s), whose bounding box has half-widths sqrt((kappa + t) (Q2^-1)_aa).
+// A box is rejected only when that minimum exceeds a margin far above the
 // rounding of the per-pixel test (f is checked in FP32 against r^2 s2^2,
 // whose size over the box is at most r^2 (1 + |A2| max|dx| + |B2| max|dy|)^2),
-// so a surfel it rejects covers no pixel of the box.
-__device__ __forceinline__ bool ss_box_may_cover(float4 P, float A2, float B2, float rc2, float dx0, float dx1,
-                                                 float dy0, float dy1) {
-    const float a = P.x * P.x + P.z * P.z - rc2 * A2 * A2;
-    const float b = P.x * P.y + P.z * P.w - rc2 * A2 * B2;
-    const float c = P.y * P.y + P.w * P.w - rc2 * B2 * B2;
-    const float det = a * c - b * b;
-    if (!(a > 0.f) || !(c > 0.f) || !(det > 0.f)) return true;
-    const float ga = rc2 * A2, gb = rc2 * B2;
-    const float idet = 1.f / det;
-    const float xs = (c * ga - b * gb) * idet, ys = (a * gb - b * ga) * idet;
-    if (xs >= dx0 && xs <= dx1 && ys >= dy0 && ys <= dy1) return true;
+// so a surfel it rejects covers no pixel of the box.  The per-surfel part is
+// taken once (ss_conic), the per-box part for each box.
+struct ss_conic {
+    float a, b, c, ga, gb, xs, ys, ia, ic, idet, rc2, A2, B2;
+    bool pd;   // Q2 positive definite (else every box may be covered)
+};
+__device__ __forceinline__ ss_conic ss_conic_of(float4 P, float A2, float B2, float rc2) {
+    ss_conic q;
+    q.rc2 = rc2;
+    q.A2 = A2;
+    q.B2 = B2;
+    q.a = P.x * P.x + P.z * P.z - rc2 * A2 * A2;
+    q.b = P.x * P.y + P.z * P.w - rc2 * A2 * B2;
+    q.c = P.y * P.y + P.w * P.w - rc2 * B2 * B2;
+    const float det = q.a * q.c - q.b * q.b;
+    q.pd = (q.a > 0.f) && (q.c > 0.f) && (det > 0.f);
+    q.ga = rc2 * A2;
+    q.gb = rc2 * B2;
+    q.idet = 1.f / det;
+    q.xs = (q.c * q.ga - q.b * q.gb) * q.idet;
+    q.ys = (q.a * q.gb - q.b * q.ga) * q.idet;
+    q.ia = 1.f / q.a;
+    q.ic = 1.f / q.c;
+    return q;
+}
+// the test's margin for a box whose offsets reach |dx| <= ex, |dy| <= ey
+__device__ __forceinline__ float ss_box_margin(const ss_conic& q, float ex, float ey) {
+    const float sc = 1.f + fabsf(q.A2) * ex + fabsf(q.B2) * ey;
+    return 1e-5f * q.rc2 * sc * sc;
+}
+// bounding box of {f < t}: false when it misses [dx0, dx1] x [dy0, dy1]
+__device__ __forceinline__ bool ss_conic_aabb_meets(const ss_conic& q, float t, float dx0, float dx1, float dy0,
+                                                    float dy1) {
+    const float kap = q.ga * q.xs + q.gb * q.ys + q.rc2 + t;   // -f(d_s) + t
+    const float hx = sqrtf(fmaxf(kap * q.c * q.idet, 0.f)) * 1.0001f + 1e-4f;
+    const float hy = sqrtf(fmaxf(kap * q.a * q.idet, 0.f)) * 1.0001f + 1e-4f;
+    return !(q.xs + hx < dx0 || q.xs - hx > dx1 || q.ys + hy < dy0 || q.ys - hy > dy1);
+}
+__device__ __forceinline__ bool ss_conic_box_may_cover(const ss_conic& q, float dx0, float dx1, float dy0, float dy1) {
+    if (!q.pd) return true;
+    if (q.xs >= dx0 && q.xs <= dx1 && q.ys >= dy0 && q.ys <= dy1) return true;
+    const float a = q.a, b = q.b, c = q.c, ga = q.ga, gb = q.gb, rc2 = q.rc2;
     auto f = [&](float x, float y) { return x * (a * x + 2.f * b * y - 2.f * ga) + y * (c * y - 2.f * gb) - rc2; };
-    const float ia = 1.f / a, ic = 1.f / c;
-    float m = f(dx0, fminf(fmaxf((gb - b * dx0) * ic, dy0), dy1));
-    m = fminf(m, f(dx1, fminf(fmaxf((gb - b * dx1) * ic, dy0), dy1)));
-    m = fminf(m, f(fminf(fmaxf((ga - b * dy0) * ia, dx0), dx1), dy0));
-    m = fminf(m, f(fminf(fmaxf((ga - b * dy1) * ia, dx0), dx1), dy1));
-    const float sc = 1.f + fabsf(A2) * fmaxf(fabsf(dx0), fabsf(dx1)) + fabsf(B2) * fmaxf(fabsf(dy0), fabsf(dy1));
-    return !(m > 1e-5f * rc2 * sc * sc);   // NaN keeps the surfel
+    float m = f(dx0, fminf(fmaxf((gb - b * dx0) * q.ic, dy0), dy1));
+    m = fminf(m, f(dx1, fminf(fmaxf((gb - b * dx1) * q.ic, dy0), dy1)));
+    m = fminf(m, f(fminf(fmaxf((ga - b * dy0) * q.ia, dx0), dx1), dy0));
+    m = fminf(m, f(fminf(fmaxf((ga - b * dy1) * q.ia, dx0), dx1), dy1));
+    return !(m > ss_box_margin(q, fmaxf(fabsf(dx0), fabsf(dx1)), fmaxf(fabsf(dy0), fabsf(dy1))));   // NaN keeps it
 }
 
 __device__ __forceinline__ bool in_rect(uint32_t rx, uint32_t ry, int px, int py) {

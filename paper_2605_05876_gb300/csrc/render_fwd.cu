@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const uint32_t* cnt, const u
 // b = (b & 1, b >> 1) of the 16 x 16 tile) is set when the record's support
 // rectangle overlaps the block and -- except for the per-pixel MIP filter,
 // whose support is not the centre quadratic's -- the exact support can reach
-// one of the block's pixel centres (ss_box_may_cover, with the centre relative
+// one of the block's pixel centres (ss_conic_box_may_cover, with the centre relative
 // to the tile formed exactly as the rasteriser's staging forms it).  The
 // rasterisers stage a record for a block only when its bit is set, so the
 // per-pixel tests they run are unchanged.  The scatter kernel, which streams
@@ -349,15 +349,19 @@ __device__ __forceinline__ uint32_t rect_block_bits(uint32_t rx, uint32_t ry, in
     return m;
 }
 
-__device__ __forceinline__ uint32_t exact_block_bits(uint32_t m, float4 P, float4 r1, float4 r2, int x0, int y0,
-                                                     float rc2, int bxl) {
+// t_pre: a margin at least the exact test's for any block of the record, so
+// that the bounding-box pre-test rejects only blocks the exact test rejects
+__device__ __forceinline__ uint32_t exact_block_bits(uint32_t m, const ss_conic& q, float t_pre, float4 r2, int x0,
+                                                     int y0, int bxl) {
     const float prx = __fadd_rn(__fsub_rn(r2.x, (float)x0), r2.z);
     const float pry = __fadd_rn(__fsub_rn(r2.y, (float)y0), r2.w);
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
         if (!((m >> b) & 1u)) continue;
         const float dxb = (float)(8 * (b & ((1 << bxl) - 1))) - prx, dyb = (float)(4 * (b >> bxl)) - pry;
-        if (!ss_box_may_cover(P, r1.x, r1.y, rc2, dxb + 0.5f, dxb + 7.5f, dyb + 0.5f, dyb + 3.5f)) m &= ~(1u << b);
+        const float x0b = dxb + 0.5f, x1b = dxb + 7.5f, y0b = dyb + 0.5f, y1b = dyb + 3.5f;
+        if (q.pd && !ss_conic_aabb_meets(q, t_pre, x0b, x1b, y0b, y1b)) m &= ~(1u << b);
+        else if (!ss_conic_box_may_cover(q, x0b, x1b, y0b, y1b)) m &= ~(1u << b);
     }
     return m;
 }
@@ -410,6 +414,16 @@ __global__ void __launch_bounds__(256) scatter_kernel(ss_ws_view ws, int64_t tot
     const unsigned long long key = ((unsigned long long)__float_as_uint(r3.x) << 32) | (uint32_t)r;
     const uint32_t rks[4] = {rk.x, rk.y, rk.z, rk.w};
     uint32_t masks = 0;
+    // per-record part of the exact-support test, and a margin bound over every
+    // pixel-centre offset the record's rectangle allows
+    const ss_conic cq = ss_conic_of(P, r1.x, r1.y, rc2);
+    float t_pre = 0.f;
+    {
+        const float cx = r2.x + r2.z, cy = r2.y + r2.w;   // centre (pixels)
+        const float ex = fmaxf(fabsf((float)(rx & 0xffff) - 8.f - cx), fabsf((float)(rx >> 16) + 9.f - cx));
+        const float ey = fmaxf(fabsf((float)(ry & 0xffff) - 4.f - cy), fabsf((float)(ry >> 16) + 5.f - cy));
+        t_pre = 2.f * ss_box_margin(cq, ex, ey);
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q)
         if (q < nt) {
@@ -419,7 +433,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(ss_ws_view ws, int64_t tot
             if ((int64_t)p < ws.max_instances) ws.keys[p] = key;
             const int ox = tx << ts.tw_log2, oy = ty << ts.th_log2;
             uint32_t m = rect_block_bits(rx, ry, ox, oy, bxl, bpt);
-            if (exact && m) m = exact_block_bits(m, P, r1, r2, ox, oy, rc2, bxl);
+            if (exact && m) m = exact_block_bits(m, cq, t_pre, r2, ox, oy, bxl);
             masks |= m << (8 * q);
         }
     ws.rec_bmask[r] = make_uint2(masks, (uint32_t)tx0 | ((uint32_t)ty0 << 12) | ((uint32_t)min(ntx, 255) << 24));
