@@ -349,19 +349,20 @@ __device__ __forceinline__ uint32_t rect_block_bits(uint32_t rx, uint32_t ry, in
     return m;
 }
 
-// t_pre: a margin at least the exact test's for any block of the record, so
-// that the bounding-box pre-test rejects only blocks the exact test rejects
+// Blocks whose pixel-centre box misses the bounding box of the surfel's
+// exact support {f < t} are cleared (t_pre: a margin at least the per-pixel
+// test's rounding bound for any block of the record, so that only blocks
+// without a covering pixel are cleared).
 __device__ __forceinline__ uint32_t exact_block_bits(uint32_t m, const ss_conic& q, float t_pre, float4 r2, int x0,
                                                      int y0, int bxl) {
+    if (!q.pd) return m;
     const float prx = __fadd_rn(__fsub_rn(r2.x, (float)x0), r2.z);
     const float pry = __fadd_rn(__fsub_rn(r2.y, (float)y0), r2.w);
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
         if (!((m >> b) & 1u)) continue;
         const float dxb = (float)(8 * (b & ((1 << bxl) - 1))) - prx, dyb = (float)(4 * (b >> bxl)) - pry;
-        const float x0b = dxb + 0.5f, x1b = dxb + 7.5f, y0b = dyb + 0.5f, y1b = dyb + 3.5f;
-        if (q.pd && !ss_conic_aabb_meets(q, t_pre, x0b, x1b, y0b, y1b)) m &= ~(1u << b);
-        else if (!ss_conic_box_may_cover(q, x0b, x1b, y0b, y1b)) m &= ~(1u << b);
+        if (!ss_conic_aabb_meets(q, t_pre, dxb + 0.5f, dxb + 7.5f, dyb + 0.5f, dyb + 3.5f)) m &= ~(1u << b);
     }
     return m;
 }
