@@ -782,8 +782,17 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
         const int n = min(32, n_cand - b0);
         stage_finish(W, n, lane, (float)x0, (float)y0, D - 1);
         uint32_t my_mask = 0;
-        // (every candidate may reach a pixel centre of the block: its block bit is set)
-        for (uint32_t live = n >= 32 ? 0xffffffffu : ((1u << n) - 1u); live; live &= live - 1) {
+        // staged surfels whose exact support can reach a pixel centre of the block
+        // (the block bit only says that the support's bounding box does; the
+        // per-pixel filter's support is not the centre quadratic's: no test)
+        bool may = false;
+        if (lane < n) {
+            const float4 g1 = W.h1[lane];
+            const float bx = (float)wx0 - g1.z, by = (float)wy0 - g1.w;
+            may = PP || ss_conic_box_may_cover(ss_conic_of(W.h0[lane], g1.x, g1.y, rc2), bx + 0.5f, bx + 7.5f,
+                                                by + 0.5f, by + 3.5f);
+        }
+        for (uint32_t live = __ballot_sync(0xffffffffu, may); live; live &= live - 1) {
             const int s = __ffs(live) - 1;
             const float4 h0 = W.h0[s], h1 = W.h1[s], h2 = W.h2[s];
             float rho2, nf;
