@@ -422,6 +422,21 @@ ss_status ss_adam_step(const ss_adam_group* groups_host, int32_t n_groups, const
 ss_status ss_loss_l1(const float* out_dev, const float* target_dev, int64_t n, float scale, float* d_out_dev,
                      float* loss_dev, void* stream);
 
+/* Silhouette loss of Eq. sil_loss (Sec. 3.7.1): the soft intersection-over-
+ * union loss between the rendered coverage A = 1 - T_{K+1} (the alpha
+ * channel of ss_render_forward's RGBA output) and a mask M in [0, 1], per
+ * view v with pixels [view_offsets[v], view_offsets[v+1]):
+ *   I = sum A M,  U = sum (A + M - A M),  loss_dev[v] = scale (1 - I / U)
+ * (0 where U = 0), and its gradient -scale (M U - I (1 - M)) / U^2 ADDED to
+ * the alpha channel of d_rgba_dev [P][4] (so that it combines with other
+ * terms of the loss).  rgba_dev [P][4] (16-byte aligned), mask_dev [P],
+ * view_offsets_dev [n_views + 1] int64 (device), loss_dev [n_views].  The
+ * sums are FP64 in a fixed order: deterministic.  Errors:
+ * SS_ERR_INVALID_ARG for NULL or misaligned pointers or n_views outside
+ * [1, 65535]. */
+ss_status ss_loss_sil_iou(const float* rgba_dev, const float* mask_dev, const int64_t* view_offsets_dev,
+                          int32_t n_views, float scale, float* d_rgba_dev, float* loss_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

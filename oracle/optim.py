@@ -14,6 +14,10 @@ of ``bench.py`` may import this module.  It shares no code with the CUDA path.
   cannot be negative).
 * ``loss_l1``: the l1 term of Eq. photo_loss on linear values,
   scale * sum |out - target|, and its gradient scale * sign(out - target).
+* ``loss_sil_iou``: the silhouette term of Eq. sil_loss, the soft
+  intersection-over-union loss between the rendered coverage 1 - T_{K+1}
+  and a mask, per image: 1 - I / U with I = sum A M and
+  U = sum (A + M - A M), and its gradient with respect to A.
 """
 from __future__ import annotations
 
@@ -58,3 +62,18 @@ def loss_l1(out, target, scale=1.0):
     """(loss, d loss / d out) of scale * sum |out - target|."""
     d = np.asarray(out, np.float64) - np.asarray(target, np.float64)
     return scale * float(np.abs(d).sum()), scale * np.sign(d)
+
+
+def loss_sil_iou(coverage, mask, scale=1.0):
+    """Soft IoU loss of one image (Eq. sil_loss): A = coverage, M = mask in
+    [0, 1]; I = sum A M is the soft intersection, U = sum (A + M - A M) the
+    soft union (the probabilistic 'or'); loss = scale (1 - I / U) and
+    dloss/dA = -scale (M U - I (1 - M)) / U^2 (quotient rule, dI/dA = M,
+    dU/dA = 1 - M).  Returns (loss, gradient)."""
+    A = np.asarray(coverage, np.float64)
+    M = np.asarray(mask, np.float64)
+    inter = float((A * M).sum())
+    union = float((A + M - A * M).sum())
+    loss = scale * (1.0 - inter / union)
+    grad = -scale * (M * union - inter * (1.0 - M)) / union ** 2
+    return loss, grad

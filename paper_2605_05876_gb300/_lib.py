@@ -133,6 +133,7 @@ EXPORTS = {
     "ss_default_adam": (None, [ctypes.POINTER(ss_adam_params)]),
     "ss_adam_step": (c_i32, [ctypes.POINTER(ss_adam_group), c_i32, ctypes.POINTER(ss_adam_params), c_vp]),
     "ss_loss_l1": (c_i32, [c_vp, c_vp, c_i64, c_f, c_vp, c_vp, c_vp]),
+    "ss_loss_sil_iou": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_f, c_vp, c_vp, c_vp]),
 }
 
 

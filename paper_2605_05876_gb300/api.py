@@ -350,6 +350,14 @@ class Adam:
         check(lib().ss_adam_step(self._arr, len(self.groups), ctypes.byref(self.p), _stream()), "ss_adam_step")
 
 
+def loss_sil_iou(rgba, mask, view_offsets, d_rgba, loss, scale: float = 1.0):
+    """Silhouette soft-IoU loss (Eq. sil_loss) per view on the coverage
+    channel of rgba [P,4] against mask [P]; view_offsets: int64 device tensor
+    [V+1]; loss [V] written, its gradient added into d_rgba[:, 3]."""
+    check(lib().ss_loss_sil_iou(_ptr(rgba), _ptr(mask), _ptr(view_offsets), int(view_offsets.numel() - 1),
+                                float(scale), _ptr(d_rgba), _ptr(loss), _stream()), "ss_loss_sil_iou")
+
+
 def loss_l1(out, target, d_out, loss, scale: float = 1.0):
     """loss[0] = scale * sum|out - target|, d_out = scale * sign(out - target) (device tensors)."""
     check(lib().ss_loss_l1(_ptr(out), _ptr(target), out.numel(), float(scale), _ptr(d_out), _ptr(loss), _stream()),

@@ -186,3 +186,71 @@ extern "C" ss_status ss_loss_l1(const float* out_dev, const float* target_dev, i
     if (cudaGetLastError() != cudaSuccess) return SS_ERR_CUDA;
     return SS_OK;
 }
+
+// ------------------------------------------------------------------------
+// Silhouette loss (Eq. sil_loss): the soft intersection-over-union loss
+// between the rendered coverage A = 1 - T_{K+1} (the alpha channel of the
+// RGBA output) and a mask M in [0, 1], per view:
+//   I = sum A M,  U = sum (A + M - A M),  loss_v = scale (1 - I / U),
+//   dloss_v/dA = -scale (M U - I (1 - M)) / U^2   (added to d_rgba's alpha).
+// One CTA per view: the two sums in FP64 in a fixed order (each thread its
+// strided pixels, then the warps and the CTA in order), so the loss is
+// deterministic; no scratch memory.
+
+#define SIL_THREADS 1024
+
+__global__ void __launch_bounds__(SIL_THREADS) sil_iou_kernel(const float4* __restrict__ rgba,
+                                                             const float* __restrict__ mask,
+                                                             const int64_t* __restrict__ offsets, float scale,
+                                                             float* d_rgba, float* loss) {
+    __shared__ double red_i[SIL_THREADS / 32], red_u[SIL_THREADS / 32];
+    __shared__ double tot[2];
+    const int v = blockIdx.x;
+    const int64_t b = offsets[v], e = offsets[v + 1];
+    double si = 0.0, su = 0.0;
+    for (int64_t p = b + threadIdx.x; p < e; p += SIL_THREADS) {
+        const double A = rgba[p].w, M = mask[p];
+        si += A * M;
+        su += A + M - A * M;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        si += __shfl_xor_sync(0xffffffffu, si, o);
+        su += __shfl_xor_sync(0xffffffffu, su, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red_i[threadIdx.x >> 5] = si;
+        red_u[threadIdx.x >> 5] = su;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double I = 0.0, U = 0.0;
+        for (int w = 0; w < SIL_THREADS / 32; ++w) {
+            I += red_i[w];
+            U += red_u[w];
+        }
+        tot[0] = I;
+        tot[1] = U;
+        loss[v] = U > 0.0 ? (float)(scale * (1.0 - I / U)) : 0.f;
+    }
+    __syncthreads();
+    const double I = tot[0], U = tot[1];
+    if (!(U > 0.0)) return;   // empty coverage and mask: no gradient
+    const double k = -(double)scale / (U * U);
+    for (int64_t p = b + threadIdx.x; p < e; p += SIL_THREADS) {
+        const double M = mask[p];
+        d_rgba[p * 4 + 3] += (float)(k * (M * U - I * (1.0 - M)));
+    }
+}
+
+extern "C" ss_status ss_loss_sil_iou(const float* rgba_dev, const float* mask_dev, const int64_t* view_offsets_dev,
+                                     int32_t n_views, float scale, float* d_rgba_dev, float* loss_dev, void* stream) {
+    if (!rgba_dev || !mask_dev || !view_offsets_dev || !d_rgba_dev || !loss_dev || n_views < 1 ||
+        n_views > 65535)
+        return SS_ERR_INVALID_ARG;
+    if (((uintptr_t)rgba_dev & 15) || ((uintptr_t)view_offsets_dev & 7)) return SS_ERR_INVALID_ARG;
+    ss_note_launch();
+    sil_iou_kernel<<<(unsigned)n_views, SIL_THREADS, 0, (cudaStream_t)stream>>>(
+        reinterpret_cast<const float4*>(rgba_dev), mask_dev, view_offsets_dev, scale, d_rgba_dev, loss_dev);
+    if (cudaGetLastError() != cudaSuccess) return SS_ERR_CUDA;
+    return SS_OK;
+}

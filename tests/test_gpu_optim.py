@@ -78,3 +78,32 @@ def test_l1_loss_matches_oracle():
         ref_L, ref_d = O.loss_l1(out.astype(np.float64), tgt.astype(np.float64), 1.0 / n)
         assert abs(L.item() - ref_L) <= 1e-6 * abs(ref_L) + 1e-12
         assert np.array_equal(d.cpu().numpy(), ref_d.astype(np.float32))
+
+
+def test_sil_iou_matches_oracle():
+    """Silhouette soft-IoU loss (Eq. sil_loss) per view against the oracle,
+    three views of different sizes, on top of an existing d_rgba (the
+    gradient is added to the alpha channel only)."""
+    import torch
+    from oracle import optim as O
+    from paper_2605_05876_gb300.api import loss_sil_iou
+    rng = np.random.default_rng(11)
+    sizes = [37 * 29, 64 * 64, 5]
+    P = sum(sizes)
+    A = rng.uniform(0, 1, P) * (rng.uniform(size=P) < 0.7)
+    M = (rng.uniform(size=P) < 0.5).astype(np.float64) * rng.uniform(0.5, 1.0, P)
+    rgba = np.concatenate([rng.normal(size=(P, 3)), A[:, None]], 1).astype(np.float32)
+    base = rng.normal(size=(P, 4)).astype(np.float32)
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    d = torch.from_numpy(base.copy()).cuda()
+    loss = torch.zeros(3, device="cuda")
+    loss_sil_iou(torch.from_numpy(rgba).cuda(), torch.from_numpy(M.astype(np.float32)).cuda(),
+                 torch.from_numpy(offs).cuda(), d, loss, scale=0.5)
+    torch.cuda.synchronize()
+    dg = d.cpu().numpy()
+    assert np.array_equal(dg[:, :3], base[:, :3])          # colour channels untouched
+    for v in range(3):
+        sl = slice(offs[v], offs[v + 1])
+        ref_l, ref_g = O.loss_sil_iou(rgba[sl, 3].astype(np.float64), M[sl].astype(np.float32), 0.5)
+        assert abs(loss[v].item() - ref_l) <= 1e-6 * max(1.0, abs(ref_l))
+        np.testing.assert_allclose(dg[sl, 3] - base[sl, 3], ref_g, rtol=1e-5, atol=3e-7)

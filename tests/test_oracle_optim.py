@@ -62,3 +62,35 @@ def test_l1_loss_and_gradient():
         fd = (O.loss_l1(out + e, tgt, 0.5)[0] - O.loss_l1(out - e, tgt, 0.5)[0]) / (2 * h)
         assert np.isclose(d[i], fd, rtol=1e-6)
     assert np.all(d[:10] == 0)
+
+
+# --------------------------------------------------------------------------
+# silhouette IoU loss (Eq. sil_loss)
+
+
+def test_sil_iou_exact_and_disjoint():
+    """Coverage equal to a binary mask: IoU 1, loss 0; coverage disjoint from
+    it: IoU 0, loss 1; a two-pixel example by hand."""
+    rng = np.random.default_rng(3)
+    M = (rng.uniform(size=500) < 0.4).astype(np.float64)
+    assert abs(O.loss_sil_iou(M, M)[0]) < 1e-15
+    assert abs(O.loss_sil_iou(1.0 - M, M)[0] - 1.0) < 1e-15
+    # A = (0.5, 1), M = (1, 0): I = 0.5, U = (0.5 + 1 - 0.5) + 1 = 2, loss 0.75
+    loss, g = O.loss_sil_iou([0.5, 1.0], [1.0, 0.0], scale=2.0)
+    assert abs(loss - 1.5) < 1e-15
+    # dL/dA_0 = -2 (1 * 2 - 0.5 * 0) / 4 = -1;  dL/dA_1 = -2 (0 - 0.5 * 1) / 4 = 0.25
+    np.testing.assert_allclose(g, [-1.0, 0.25], rtol=1e-15)
+
+
+def test_sil_iou_gradient_matches_finite_differences():
+    rng = np.random.default_rng(4)
+    A = rng.uniform(0, 1, 64)
+    M = rng.uniform(0, 1, 64)
+    loss, g = O.loss_sil_iou(A, M, scale=0.7)
+    for i in rng.choice(64, 10, replace=False):
+        h = 1e-6
+        Ap, Am = A.copy(), A.copy()
+        Ap[i] += h
+        Am[i] -= h
+        fd = (O.loss_sil_iou(Ap, M, 0.7)[0] - O.loss_sil_iou(Am, M, 0.7)[0]) / (2 * h)
+        assert abs(fd - g[i]) < 1e-8
