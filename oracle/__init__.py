@@ -4,4 +4,4 @@ Only tests/, ``__graft_entry__.smoke()`` and the cpu_baseline / reference arm
 of ``bench.py`` may import this package.  It shares no code with the CUDA
 path and never imports it.
 """
-from . import model, optim  # noqa: F401
+from . import density, model, optim  # noqa: F401
