@@ -19,6 +19,7 @@ collective); value = views of all ranks / max time over ranks.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import math
@@ -398,6 +399,46 @@ def run_reference(args):
 # our arm
 
 
+def density_pass(rs, torch, reps: int = 5) -> dict:
+    """Adaptive density control (Sec. 3.6.2) over the batch's surfels with the
+    statistic of the last step: the neighbour statistics, the plan and the
+    compaction into new arrays, each timed with CUDA events (mean of reps);
+    tau_g is the 90th percentile of g_bar so that about a tenth qualify."""
+    from paper_2605_05876_gb300 import _lib as C
+    from paper_2605_05876_gb300.api import SURFEL_FIELDS, _ptr, _stream
+    gbar = (rs.screen_grad_norm / rs.screen_grad_views.clamp(min=1)).cpu().numpy()
+    tau = float(np.quantile(gbar[gbar > 0], 0.9)) if (gbar > 0).any() else 1.0
+    dp = rs.density_params(tau_g=tau)
+    st = torch.cuda.current_stream()
+
+    def timed(fn):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            out = fn()
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    ms_nb, (mean, nn, flags) = timed(lambda: rs.density_neighbours(dp))
+    ms_plan, (action, off) = timed(lambda: rs.density_plan(dp, mean, nn, flags))
+    n_new = int(off[-1].item())
+    new = {k: torch.empty((n_new,) + tuple(v.shape[1:]), device=rs.dev) for k, v in rs.params_t.items()}
+    sin, sout = rs.surfels_struct(), C.ss_surfels(*(_ptr(new[k]) for k in SURFEL_FIELDS))
+
+    def apply():
+        C.check(C.lib().ss_density_apply(ctypes.byref(sin), rs.n_surfels, _ptr(action), _ptr(off),
+                                         float(dp.split_scale), ctypes.byref(sout), _stream()), "ss_density_apply")
+    ms_apply, _ = timed(apply)
+    counts = torch.bincount(action.long(), minlength=3).cpu().tolist()
+    fl = flags.cpu().numpy()
+    return {"ms_neighbours": ms_nb, "ms_plan": ms_plan, "ms_apply": ms_apply, "tau_g": tau,
+            "k": int(dp.k), "cos_min": float(dp.cos_min), "cell": float(dp.cell),
+            "before": rs.n_surfels, "after": n_new, "pruned": counts[0], "split": counts[2],
+            "mean_bound_frac": float((fl & 1).mean()), "nn_bound_frac": float(((fl & 2) != 0).mean())}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -531,6 +572,7 @@ def run_ours(args):
 
     # --- the same step with the densification statistic (Eq. ss_grad) accumulated
     screen_grad = None
+    density = None
     if not args.no_screen_grad:
         rs = Renderer(scene, share_from=r, screen_grad=True)
         for k in KNOBS:
@@ -545,9 +587,13 @@ def run_ours(args):
             rs.backward(d_rgba, d_aov)
         for _ in range(args.warmup):
             step_ssg()
+        profile_begin()
         ms_s = timed(step_ssg, args.steps)
+        st_s = profile_end()
         screen_grad = {"value": job_rate(V, args.steps, world, ms_s), "unit": "views/s",
-                       "ms_per_step": ms_s / args.steps, "cost_vs_step": ms_s / ms - 1.0}
+                       "ms_per_step": ms_s / args.steps, "cost_vs_step": ms_s / ms - 1.0,
+                       "stage_ms": {k: round(v[0] / args.steps, 4) for k, v in st_s.items() if v[1]}}
+        density = density_pass(rs, torch)
         del rs
         torch.cuda.empty_cache()
 
@@ -627,7 +673,7 @@ def run_ours(args):
                            "inputs_vs_l2": "inputs and intermediates > 129 MB L2 (no flush)",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "launch_shapes": tuned or "defaults"},
-                "per_view": per_view, "graph": graph, "screen_grad": screen_grad, "e2e": e2e,
+                "per_view": per_view, "graph": graph, "screen_grad": screen_grad, "density": density, "e2e": e2e,
                 "roofline": roofline, "hbm": hbm_line,
                 "cpu_baseline": cpu,
                 "clocks": clocks,

@@ -179,8 +179,9 @@ typedef struct ss_stats {
  * stage of every call made between ss_profile_begin and ss_profile_end
  * (host-side state, one profile at a time; not for use inside stream
  * capture).  Stages: 0 project, 1 bin+sort, 2 raster_fwd, 3 raster_bwd,
- * 4 project_bwd, 5 env_prefilter, 6 env_prefilter_backward. */
-#define SS_N_STAGES 7
+ * 4 project_bwd, 5 env_prefilter, 6 env_prefilter_backward, 7 density
+ * control (ss_density_*). */
+#define SS_N_STAGES 8
 typedef struct ss_stage_times {
     float ms[SS_N_STAGES];       /* summed event durations */
     int32_t launches[SS_N_STAGES];
@@ -436,6 +437,113 @@ ss_status ss_loss_l1(const float* out_dev, const float* target_dev, int64_t n, f
  * [1, 65535]. */
 ss_status ss_loss_sil_iou(const float* rgba_dev, const float* mask_dev, const int64_t* view_offsets_dev,
                           int32_t n_views, float scale, float* d_rgba_dev, float* loss_dev, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Adaptive density control (Sec. 3.6.2 and the appendix on splitting and
+ * pruning surfels).
+ *
+ * A spatial index over the surfel centres gives each surfel the mean
+ * distance d_bar to its k nearest same-orientation neighbours (other surfels
+ * of the same scene whose unit normals satisfy n_i . n_j >= cos_min; the
+ * paper names neither k nor the test) and the distance to its nearest
+ * neighbour of any orientation.  With the screen-space statistic of
+ * Eq. ss_grad (ss_surfel_grads.screen_grad_norm / screen_grad_views) these
+ * decide, per surfel:
+ *   prune  (SS_DENSITY_PRUNE_VISIBLE)   its summed statistic is zero: no
+ *          backward pass ever reached it;
+ *   prune  (SS_DENSITY_PRUNE_ISOLATED)  no neighbour within its kernel
+ *          support r_cut * max(s_u, s_v);
+ *   split  (SS_DENSITY_SPLIT)  g_bar = norm / views >= tau_g and
+ *          max(s_u, s_v) > d_bar: two children at c +- (s_max/2) t_max
+ *          (t_max the unit tangent of the larger scale, u on a tie), the
+ *          scale along t_max times split_scale (0.7), everything else
+ *          inherited;
+ *   keep   otherwise.  A pruning rule wins over splitting.
+ * The new surfel arrays hold, in the parents' order, each kept surfel once
+ * and each split one as its two children (the + child first).
+ *
+ * Index: a hashed uniform grid of cell size `cell` (world units).  A query
+ * visits rings of cells around its own, nearest first, skipping cells
+ * farther than its current k-th distance, until the k nearest
+ * same-orientation neighbours are certain (the k-th lies within the radius
+ * the visited cells cover) or the ring of radius max_rings is done.  Results are
+ * exact where certain; elsewhere flags say which value is only a lower
+ * bound. */
+#define SS_DENSITY_SPLIT 1
+#define SS_DENSITY_PRUNE_VISIBLE 2
+#define SS_DENSITY_PRUNE_ISOLATED 4
+#define SS_DENSITY_KMAX 16
+#define SS_DENSITY_MAX_RINGS 32
+/* flags of ss_density_neighbours */
+#define SS_NB_MEAN_BOUND 1   /* fewer than k same-orientation neighbours were
+                                certain: mean_dist is a lower bound of d_bar
+                                (each missing one counted at the covered
+                                radius); the surfel is not split */
+#define SS_NB_NN_BOUND 2     /* no neighbour within the covered radius:
+                                nn_dist is that radius, a lower bound */
+#define SS_NB_NONFINITE 4    /* non-finite centre: not indexed, results NaN */
+/* actions of ss_density_plan */
+#define SS_ACTION_PRUNE 0
+#define SS_ACTION_KEEP 1
+#define SS_ACTION_SPLIT 2
+
+typedef struct ss_density_params {
+    int32_t k;            /* neighbours averaged for d_bar, 1 .. SS_DENSITY_KMAX (default 8) */
+    float cos_min;        /* same orientation: n_i . n_j >= cos_min (default 0.5) */
+    float cell;           /* grid cell size, world units, > 0; queries cost
+                             least near the typical k-th neighbour distance.
+                             ss_default_density leaves it 0: the caller
+                             chooses from its scene's scale */
+    int32_t max_rings;    /* largest ring radius in cells, 1 .. SS_DENSITY_MAX_RINGS (default 4) */
+    float tau_g;          /* split threshold on g_bar (default 2e-4) */
+    float r_cut;          /* kernel support in units of the scale (default 3) */
+    float split_scale;    /* factor on the split axis' scale, (0, 1] (default 0.7) */
+    int32_t ops;          /* OR of SS_DENSITY_* (default all three) */
+} ss_density_params;
+
+void ss_default_density(ss_density_params* p);
+
+/* Bytes of device workspace ss_density_neighbours and ss_density_plan need
+ * for n surfels.  Errors: SS_ERR_INVALID_ARG for n < 0 or a null out. */
+ss_status ss_density_workspace_size(int64_t n, size_t* bytes);
+
+/* Neighbour statistics of the n = scene_offsets_host[n_scenes] surfels s
+ * (scenes 0 .. n_scenes-1 own [scene_offsets_host[i], scene_offsets_host[i+1]),
+ * neighbours only within a scene).  Writes mean_dist_dev [n] (d_bar),
+ * nn_dist_dev [n] and flags_dev [n] (int32, SS_NB_*).  Uses pos and quat
+ * only.  Deterministic: the k distances are summed in ascending order.
+ * Errors: SS_ERR_INVALID_ARG for null pointers, bad offsets or parameters;
+ * SS_ERR_WORKSPACE for a workspace below ss_density_workspace_size. */
+ss_status ss_density_neighbours(const ss_surfels* s, const int64_t* scene_offsets_host, int32_t n_scenes,
+                                const ss_density_params* p, float* mean_dist_dev, float* nn_dist_dev,
+                                int32_t* flags_dev, void* ws, size_t ws_bytes, void* stream);
+
+/* Decide every surfel's action (SS_ACTION_*) from its log-scales, the
+ * screen-space statistic (norm and view count, as accumulated by
+ * ss_render_backward with screen_grad = 1) and the outputs of
+ * ss_density_neighbours.  action_dev [n] int32; out_offset_dev [n + 1] int64:
+ * the first output row of each surfel, the new surfel count last.  g_bar is
+ * norm / views in binary32.  Errors: SS_ERR_INVALID_ARG for null pointers
+ * (any input may be NULL only when n = 0), bad parameters; SS_ERR_WORKSPACE. */
+ss_status ss_density_plan(const float* log_scale_dev, const float* screen_grad_norm_dev,
+                          const float* screen_grad_views_dev, const float* mean_dist_dev, const float* nn_dist_dev,
+                          const int32_t* flags_dev, int64_t n, const ss_density_params* p, int32_t* action_dev,
+                          int64_t* out_offset_dev, void* ws, size_t ws_bytes, void* stream);
+
+/* Write the new surfels: `out` arrays hold out_offset[n] rows (read it back
+ * first) and must not overlap `in`.  Children's positions and log-scales
+ * follow the split rule above; the rotation, albedo, roughness and
+ * metallic are copied.  Errors: SS_ERR_INVALID_ARG for null pointers or
+ * split_scale outside (0, 1]. */
+ss_status ss_density_apply(const ss_surfels* in, int64_t n, const int32_t* action_dev, const int64_t* out_offset_dev,
+                           float split_scale, const ss_surfels* out, void* stream);
+
+/* Carry another per-surfel array of `width` floats per row (an optimiser's
+ * raw values or moments) through the same step: kept rows once, split rows
+ * twice, or as two rows of zeros when zero_children is 1.  Errors:
+ * SS_ERR_INVALID_ARG for null pointers or width outside [1, 64]. */
+ss_status ss_density_compact(const float* in_dev, int32_t width, int64_t n, const int32_t* action_dev,
+                             const int64_t* out_offset_dev, int32_t zero_children, float* out_dev, void* stream);
 
 #ifdef __cplusplus
 }

@@ -93,6 +93,31 @@ def neighbours(pos, quat, scene_offsets, k=8, cos_min=0.5, chunk=256):
     return mean, cnt, nn
 
 
+def neighbours_of(pos, quat, scene_offsets, idx, k=8, cos_min=0.5):
+    """``neighbours`` for the surfels idx only (each against every surfel of
+    its scene): (mean_dist, n_same, nn_dist, orientation margin) per query,
+    the margin as in ``orientation_margins``."""
+    pos = np.asarray(pos, np.float64)
+    nrm = normals(quat)
+    offs = np.asarray([int(v) for v in scene_offsets])
+    out = np.zeros((len(idx), 4))
+    for a, i in enumerate(idx):
+        s = int(np.searchsorted(offs, i, side="right") - 1)
+        b, e = offs[s], offs[s + 1]
+        P, Nn, ni = pos[b:e], nrm[b:e], nrm[i]
+        d = np.sqrt(((P - pos[i]) ** 2).sum(1))
+        d[i - b] = np.inf
+        dot = Nn @ ni
+        ds = np.sort(np.where(dot >= cos_min, d, np.inf))[:k]
+        fin = ds[np.isfinite(ds)]
+        mean = fin.mean() if fin.size else np.nan
+        reach = fin[-1] if fin.size == k else np.inf
+        near = d <= reach * (1 + 1e-5)
+        margin = np.abs(dot[near] - cos_min).min() if near.any() else np.inf
+        out[a] = (mean, fin.size, d.min() if e - b > 1 else np.inf, margin)
+    return out
+
+
 def orientation_margins(pos, quat, scene_offsets, k, cos_min, mean_slack=1e-5):
     """Per surfel, the smallest |n_i . n_j - cos_min| over the surfels j within
     (1 + slack) times its k-th same-orientation distance, or within its nearest

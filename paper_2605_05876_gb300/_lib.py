@@ -64,8 +64,9 @@ class ss_stats(ctypes.Structure):
                 ("bwd_batches", c_i64)]
 
 
-SS_N_STAGES = 7
-STAGES = ("project", "bin_sort", "raster_fwd", "raster_bwd", "project_bwd", "env_prefilter", "env_prefilter_bwd")
+SS_N_STAGES = 8
+STAGES = ("project", "bin_sort", "raster_fwd", "raster_bwd", "project_bwd", "env_prefilter", "env_prefilter_bwd",
+          "density")
 
 
 class ss_stage_times(ctypes.Structure):
@@ -94,6 +95,17 @@ SS_MAX_ADAM_GROUPS = 16
 class ss_adam_group(ctypes.Structure):
     _fields_ = [("param", c_vp), ("grad", c_vp), ("m", c_vp), ("v", c_vp), ("act", c_vp), ("n", c_i64),
                 ("lr", c_f), ("activation", c_i32)]
+
+
+class ss_density_params(ctypes.Structure):
+    _fields_ = [("k", c_i32), ("cos_min", c_f), ("cell", c_f), ("max_rings", c_i32), ("tau_g", c_f), ("r_cut", c_f),
+                ("split_scale", c_f), ("ops", c_i32)]
+
+
+SS_DENSITY_SPLIT, SS_DENSITY_PRUNE_VISIBLE, SS_DENSITY_PRUNE_ISOLATED = 1, 2, 4
+SS_DENSITY_KMAX, SS_DENSITY_MAX_RINGS = 16, 32
+SS_NB_MEAN_BOUND, SS_NB_NN_BOUND, SS_NB_NONFINITE = 1, 2, 4
+SS_ACTION_PRUNE, SS_ACTION_KEEP, SS_ACTION_SPLIT = 0, 1, 2
 
 
 class ss_adam_params(ctypes.Structure):
@@ -134,6 +146,16 @@ EXPORTS = {
     "ss_adam_step": (c_i32, [ctypes.POINTER(ss_adam_group), c_i32, ctypes.POINTER(ss_adam_params), c_vp]),
     "ss_loss_l1": (c_i32, [c_vp, c_vp, c_i64, c_f, c_vp, c_vp, c_vp]),
     "ss_loss_sil_iou": (c_i32, [c_vp, c_vp, c_vp, c_i32, c_f, c_vp, c_vp, c_vp]),
+    "ss_default_density": (None, [ctypes.POINTER(ss_density_params)]),
+    "ss_density_workspace_size": (c_i32, [c_i64, ctypes.POINTER(ctypes.c_size_t)]),
+    "ss_density_neighbours": (c_i32, [ctypes.POINTER(ss_surfels), ctypes.POINTER(c_i64), c_i32,
+                                      ctypes.POINTER(ss_density_params), c_vp, c_vp, c_vp, c_vp, ctypes.c_size_t,
+                                      c_vp]),
+    "ss_density_plan": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_i64, ctypes.POINTER(ss_density_params),
+                                c_vp, c_vp, c_vp, ctypes.c_size_t, c_vp]),
+    "ss_density_apply": (c_i32, [ctypes.POINTER(ss_surfels), c_i64, c_vp, c_vp, c_f, ctypes.POINTER(ss_surfels),
+                                 c_vp]),
+    "ss_density_compact": (c_i32, [c_vp, c_i32, c_i64, c_vp, c_vp, c_i32, c_vp, c_vp]),
 }
 
 

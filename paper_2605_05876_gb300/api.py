@@ -264,6 +264,115 @@ class Renderer:
             chosen[knob] = (best, times)
         return chosen
 
+    # -- adaptive density control (Sec. 3.6.2)
+    def density_params(self, **overrides) -> C.ss_density_params:
+        """ss_density_params with the library's defaults, the grid cell set
+        from this batch's surfel scales (twice the median of max(s_u, s_v)
+        over a sample) unless given, and the given overrides."""
+        p = C.ss_density_params()
+        lib().ss_default_density(ctypes.byref(p))
+        if "cell" not in overrides:
+            ls = self.params_t["log_scale"]
+            step = max(1, self.n_surfels // 65536)
+            sample = ls[::step].max(dim=1).values.float().cpu().numpy()
+            overrides["cell"] = float(2.0 * np.exp(np.median(sample))) if sample.size else 1.0
+        for k, v in overrides.items():
+            setattr(p, k, v)
+        return p
+
+    def _density_ws(self, n: int):
+        nb = ctypes.c_size_t()
+        check(lib().ss_density_workspace_size(int(n), ctypes.byref(nb)), "ss_density_workspace_size")
+        if getattr(self, "_dws", None) is None or self._dws.numel() < nb.value:
+            self._dws = self.torch.empty(max(nb.value, 1), dtype=self.torch.uint8, device=self.dev)
+        return self._dws, nb.value
+
+    def density_neighbours(self, dp: C.ss_density_params):
+        """(mean_dist, nn_dist, flags) device tensors of ss_density_neighbours."""
+        torch = self.torch
+        n = self.n_surfels
+        mean = torch.empty(n, device=self.dev)
+        nn = torch.empty(n, device=self.dev)
+        flags = torch.empty(n, dtype=torch.int32, device=self.dev)
+        ws, nb = self._density_ws(n)
+        check(lib().ss_density_neighbours(ctypes.byref(self.surfels_struct()), self._offsets, self.n_scenes,
+                                          ctypes.byref(dp), _ptr(mean), _ptr(nn), _ptr(flags), _ptr(ws), nb,
+                                          _stream()), "ss_density_neighbours")
+        return mean, nn, flags
+
+    def density_plan(self, dp: C.ss_density_params, mean, nn, flags, g_norm=None, g_views=None):
+        """(action int32 [N], out_offset int64 [N+1]) of ss_density_plan, by
+        default from the accumulated screen-space statistic."""
+        torch = self.torch
+        n = self.n_surfels
+        g_norm = self.screen_grad_norm if g_norm is None else g_norm
+        g_views = self.screen_grad_views if g_views is None else g_views
+        action = torch.empty(n, dtype=torch.int32, device=self.dev)
+        off = torch.empty(n + 1, dtype=torch.int64, device=self.dev)
+        ws, nb = self._density_ws(n)
+        check(lib().ss_density_plan(_ptr(self.params_t["log_scale"]), _ptr(g_norm), _ptr(g_views), _ptr(mean),
+                                    _ptr(nn), _ptr(flags), n, ctypes.byref(dp), _ptr(action), _ptr(off), _ptr(ws),
+                                    nb, _stream()), "ss_density_plan")
+        return action, off
+
+    def densify(self, dp: C.ss_density_params | None = None, adam: "Adam | None" = None) -> dict:
+        """One pass of adaptive density control over the batch: neighbour
+        statistics, the split / prune plan from the screen-space statistic
+        accumulated since the last zero_grads (screen_grad=True), and the new
+        surfel arrays.  The renderer is re-planned for the new count and its
+        gradients and statistic are zeroed.  With `adam`, its surfel groups
+        follow: raw values of kept and split surfels are carried over,
+        moments of children start at zero.  Returns the counts."""
+        torch = self.torch
+        if not self.prm.screen_grad:
+            raise ValueError("density control reads the screen-space statistic: Renderer(screen_grad=True)")
+        dp = dp or self.density_params()
+        n = self.n_surfels
+        mean, nn, flags = self.density_neighbours(dp)
+        action, off = self.density_plan(dp, mean, nn, flags)
+        bounds = off[torch.tensor([int(v) for v in self._offsets], device=self.dev)].cpu().tolist()
+        n_new = int(bounds[-1])
+        new = {k: torch.empty((n_new,) + tuple(v.shape[1:]), device=self.dev) for k, v in self.params_t.items()}
+        sin, sout = self.surfels_struct(), C.ss_surfels(*(_ptr(new[k]) for k in SURFEL_FIELDS))
+        check(lib().ss_density_apply(ctypes.byref(sin), n, _ptr(action), _ptr(off), float(dp.split_scale),
+                                     ctypes.byref(sout), _stream()), "ss_density_apply")
+        counts = torch.bincount(action.long(), minlength=3).cpu().tolist()
+        old = self.params_t
+        self.params_t = new
+        self.n_surfels = n_new
+        self._offsets = (ctypes.c_int64 * (self.n_scenes + 1))(*bounds)
+        self.desc.scene_offsets_host = self._offsets
+        if hasattr(self, "grads"):
+            del self.grads
+        self.zero_grads()
+        self.ws = None
+        self.plan_capacity()
+        if adam is not None:
+            groups, moments = {}, {}
+            for k, (raw, grad, act, lr, activation) in adam.groups.items():
+                if k not in SURFEL_FIELDS:
+                    groups[k], moments[k] = (raw, grad, act, lr, activation), adam.moments[k]
+                    continue
+                if raw.data_ptr() == old[k].data_ptr():
+                    nraw = new[k]
+                else:
+                    nraw = self.compact_rows(raw, action, off, n_new, zero_children=False)
+                m, v = adam.moments[k]
+                moments[k] = (self.compact_rows(m, action, off, n_new, zero_children=True),
+                              self.compact_rows(v, action, off, n_new, zero_children=True))
+                groups[k] = (nraw, self.grads[k], None if act is None else new[k], lr, activation)
+            adam.replace(groups, moments)
+        return {"before": n, "after": n_new, "pruned": counts[0], "kept": counts[1], "split": counts[2]}
+
+    def compact_rows(self, t, action, off, n_new: int, zero_children: bool):
+        """ss_density_compact of a per-surfel tensor [N, ...] into a new one."""
+        n = action.numel()
+        width = t.numel() // max(n, 1)
+        out = self.torch.empty((n_new,) + tuple(t.shape[1:]), device=self.dev)
+        check(lib().ss_density_compact(_ptr(t.contiguous()), width, n, _ptr(action), _ptr(off), int(zero_children),
+                                       _ptr(out), _stream()), "ss_density_compact")
+        return out
+
     def read_status(self) -> int:
         return int(lib().ss_read_status(_ptr(self.ws), _stream()))
 
@@ -327,12 +436,18 @@ class Adam:
         import torch
         if not 1 <= len(groups) <= C.SS_MAX_ADAM_GROUPS:
             raise ValueError("1 .. 16 groups")
-        self.groups = groups
-        self.moments = {k: (torch.zeros_like(g[0]), torch.zeros_like(g[0])) for k, g in groups.items()}
         self.p = C.ss_adam_params()
         lib().ss_default_adam(ctypes.byref(self.p))
         self.p.beta1, self.p.beta2, self.p.eps = beta1, beta2, eps
         self.t = 0
+        self.replace(groups, {k: (torch.zeros_like(g[0]), torch.zeros_like(g[0])) for k, g in groups.items()})
+
+    def replace(self, groups: dict, moments: dict):
+        """Point the optimiser at new tensors (same group names), e.g. after
+        density control changed the surfel count; the step count is kept."""
+        import torch
+        self.groups = groups
+        self.moments = moments
         arr = (C.ss_adam_group * len(groups))()
         for i, (k, (raw, grad, act, lr, activation)) in enumerate(groups.items()):
             m, v = self.moments[k]

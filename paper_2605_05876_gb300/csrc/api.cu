@@ -197,7 +197,7 @@ static ss_status build_layout(const ss_batch_desc* b, const ss_render_params* p,
 
 struct ws_plan {
     size_t status, layout, vgeo, rec, rank, rbm, tc, ts, tcur, keys, keys_alt, bmask, cand, layer, pix, grad, masks,
-        mcount, env_acc, jac, total;
+        madv, mcount, env_acc, jac, total;
     int64_t env_texels;   // irradiance + specular texels of one scene (0: no env-gradient scratch)
 };
 
@@ -228,11 +228,12 @@ static ws_plan plan_ws(const ss_layout& L, const ss_render_params& p, int with_b
         w.pix = take(sizeof(float) * 2 * (size_t)L.total_pixels);
         w.grad = take(sizeof(float) * SS_NGRAD * (size_t)L.total_records);
         w.masks = take(sizeof(uint2) * 8 * (size_t)p.max_instances);
+        w.madv = take(sizeof(uint32_t) * 8 * (size_t)p.max_instances);
         w.mcount = take(sizeof(uint32_t) * 8 * (size_t)L.total_tiles);
         w.env_acc = take(sizeof(float4) * SS_ACC_STRIDE * (size_t)w.env_texels * (size_t)L.n_scenes);
         w.jac = p.screen_grad ? take(sizeof(float4) * 4 * (size_t)L.total_records) : 0;
     } else {
-        w.layer = w.pix = w.grad = w.masks = w.mcount = w.env_acc = w.jac = 0;
+        w.layer = w.pix = w.grad = w.masks = w.madv = w.mcount = w.env_acc = w.jac = 0;
     }
     w.total = o;
     return w;
@@ -261,6 +262,7 @@ static ss_ws_view carve(void* ws, const ws_plan& w, const ss_render_params& p, i
     v.pix_state = with_bwd ? (float*)(b + w.pix) : nullptr;
     v.grad_rec = with_bwd ? (float*)(b + w.grad) : nullptr;
     v.cover_list = with_bwd ? (uint2*)(b + w.masks) : nullptr;
+    v.cover_adv = with_bwd ? (uint32_t*)(b + w.madv) : nullptr;
     v.cover_count = with_bwd ? (uint32_t*)(b + w.mcount) : nullptr;
     v.env_acc = (with_bwd && w.env_texels) ? (float4*)(b + w.env_acc) : nullptr;
     v.ssg_jac = (with_bwd && p.screen_grad) ? (float4*)(b + w.jac) : nullptr;

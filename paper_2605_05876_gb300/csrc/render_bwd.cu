@@ -7,8 +7,10 @@
 // surfel parameters and the prefiltered environment texels.
 //
 // Every discrete decision (support, cutoff, grouping, K_max, normal flip) is
-// held fixed; the replay uses the same ss_pixel_test and weight expression as
-// the forward kernel, so both take identical decisions.
+// held fixed: the forward pass writes, per (warp, staged surfel), the pixels
+// it covers and the pixels where it opens a new layer, and the backward
+// re-evaluates each fragment's weight with the same ss_pixel_test and weight
+// expression as the forward kernel.
 #include <math.h>
 
 #include "ss3d_internal.cuh"
@@ -26,9 +28,10 @@
 #define G_SSN 21   // densification statistic: sum of the fragments' |(g_x, g_y)| (Eq. ss_grad)
 #define G_SSC 22   // ... and their number
 
-// Backward rasteriser, per warp (8 x 4 pixels): the forward pass left one
-// coverage word per (warp, staged surfel); the replay of each pixel's
-// grouping only reads those words, and every fragment it accepts is
+// Backward rasteriser, per warp (8 x 4 pixels): the forward pass left a
+// coverage word and a layer-opening word per (warp, staged surfel); the
+// replay of each pixel's grouping only reads those words, and every fragment
+// it accepts is
 // recorded (slot, pixel lane).  The recorded fragments are then
 // differentiated 32 at a time, one per lane: lane f writes its 22 values to
 // column f of a 22 x 32 table; lane q loads row q into registers and sums it
@@ -364,13 +367,11 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
     bool done = !inside || K == 0;
     unsigned n_frag = 0, n_batch = 0;
 
-    // replay state (Algorithm 1): layer index, whether the open layer holds a
-    // fragment of positive weight (w = n_f exp(-rho^2/2) > 0 exactly when
-    // n_f > 0: exp(-rho^2/2) >= e^-4.5 on the support and n_f, when not 0,
-    // is far above the FP32 underflow range), its largest z_end
-    int k = -1;
-    bool have_w = false, pend = false;
-    float zmax = 0.f;
+    // replay state (Algorithm 1): the layer index; the forward pass marked
+    // in cover_adv the fragments that open a new layer (its gap test), so
+    // the replay only counts them
+    int k = 0;
+    bool pend = false;
     int npend = 0;   // warp-uniform: fragments recorded, not yet differentiated
 
     auto enter_layer = [&](int kk) {   // this lane's layer coefficients -> B.gtab
@@ -378,6 +379,7 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
 #pragma unroll
         for (int c = 0; c < GTR; ++c) B.gtab[lane * GTR + c] = ls[c * P];
     };
+    if (!done) enter_layer(0);
 
     const int64_t cap = ws.max_instances;
     int64_t beg = ws.tile_start[tile], end = ws.tile_start[tile + 1];
@@ -387,6 +389,7 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
     float* grad = ws.grad_rec;
     // the forward pass's list of covering staged surfels of this warp
     const uint2* clist = ws.cover_list + 8 * beg + (int64_t)warp * (end - beg);
+    const uint32_t* alist = ws.cover_adv + 8 * beg + (int64_t)warp * (end - beg);
     const int64_t n_list = ws.cover_count[(int64_t)tile * 8 + warp];
 
     // Differentiate every recorded fragment, 32 at a time (one per lane), then
@@ -492,10 +495,12 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
 
     // one staging buffer; the records of the next chunk are prefetched into L2
     uint2 nxt = lane < n_list ? __ldg(clist + lane) : make_uint2(0u, 0u);
+    uint32_t nxa = lane < n_list ? __ldg(alist + lane) : 0u;
     for (int64_t base = 0; base < n_list; base += 32) {
         if (__all_sync(0xffffffffu, done)) break;
         const int n = (int)min((int64_t)32, n_list - base);
         const uint2 cur = nxt;
+        const uint32_t ca = lane < n ? nxa : 0u;   // layer-opening lanes of slot `lane`
         if (SSG && lane < n) {   // the record's densification derivatives, with the record
             const float4* J = ws.ssg_jac + (int64_t)cur.x * 4;
 #pragma unroll
@@ -503,6 +508,7 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
         }
         stage_ids(*Wc, recs, cur.x, lane, lane < n);
         nxt = base + 32 + lane < n_list ? __ldg(clist + base + 32 + lane) : make_uint2(0u, 0u);
+        nxa = base + 32 + lane < n_list ? __ldg(alist + base + 32 + lane) : 0u;
         if (base + 32 + lane < n_list) {
             const char* pr = reinterpret_cast<const char*>(recs + nxt.x);
             asm volatile("prefetch.global.L2 [%0];\n" ::"l"(pr));
@@ -515,27 +521,17 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
             const int s = __ffs(nz) - 1;
             nz &= nz - 1;
             const uint32_t m = __shfl_sync(0xffffffffu, cm, s);
+            const uint32_t av = __shfl_sync(0xffffffffu, ca, s);
             const bool my = ((m >> lane) & 1u) && !done;
-            const float4 h2 = Wc->h2[s];
             // replay of Algorithm 1: the forward kernel's grouping decisions
-            const bool first = my && k < 0;
-            const bool adv = my && k >= 0 && have_w && h2.x > zmax;
+            const bool adv = my && ((av >> lane) & 1u);
             if (__any_sync(0xffffffffu, adv && pend)) run_batches();   // pending fragments use the open layer
-            if (first) {
-                k = 0;
-                enter_layer(0);
-            } else if (adv) {
+            if (adv) {
                 ++k;
-                have_w = false;
-                zmax = 0.f;
                 if (k >= K) done = true;
                 else enter_layer(k);
             }
             const bool app = my && !done;
-            if (app) {
-                zmax = fmaxf(zmax, h2.y);
-                have_w = have_w || h2.z != 0.f;
-            }
             const uint32_t am = __ballot_sync(0xffffffffu, app);
             if (npend + __popc(am) > BW_CAP) run_batches();
             if (app) {

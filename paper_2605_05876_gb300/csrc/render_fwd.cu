@@ -736,6 +736,7 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
     // staged surfel that covers a pixel of this block, in list order, in the
     // warp's own region of 8 x the tile's list
     uint2* clist = ws.cover_list ? ws.cover_list + 8 * beg + (int64_t)warp * (end - beg) : nullptr;
+    uint32_t* alist = clist ? ws.cover_adv + 8 * beg + (int64_t)warp * (end - beg) : nullptr;
     uint32_t n_list = 0;
     ss_wstage* Wb = Wst + (a.p.stage_depth ? a.p.stage_depth : 2) * lw;
     // pass 1: the records whose support rectangle meets the block, in list
@@ -781,7 +782,7 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
         ss_wstage& W = Wb[buf];
         const int n = min(32, n_cand - b0);
         stage_finish(W, n, lane, (float)x0, (float)y0, D - 1);
-        uint32_t my_mask = 0;
+        uint32_t my_mask = 0, my_adv = 0;
         // staged surfels whose exact support can reach a pixel centre of the block
         // (the block bit only says that the support's bounding box does; the
         // per-pixel filter's support is not the centre quadratic's: no test)
@@ -819,6 +820,10 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
             }
             const uint32_t cm = __ballot_sync(0xffffffffu, cg);
             my_mask = lane == s ? cm : my_mask;
+            if (clist) {   // the gap test below, kept for the backward's replay of the grouping
+                const uint32_t am = __ballot_sync(0xffffffffu, cg && !done && Wg > 0.f && h2.x > zmax);
+                my_adv = lane == s ? am : my_adv;
+            }
             if (cg && !done) {
                 if (STATS) ++n_frag;
                 const float w = nf * __expf(-0.5f * rho2);   // Eq. mip_weight (Eq. mip_eval per pixel)
@@ -849,7 +854,11 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
         if (clist) {
             const bool keep = lane < n && my_mask != 0u;
             const uint32_t km = __ballot_sync(0xffffffffu, keep);
-            if (keep) clist[n_list + __popc(km & ((1u << lane) - 1u))] = make_uint2(W.id[lane], my_mask);
+            if (keep) {
+                const uint32_t e = n_list + __popc(km & ((1u << lane) - 1u));
+                clist[e] = make_uint2(W.id[lane], my_mask);
+                alist[e] = my_adv;
+            }
             n_list += __popc(km);
         }
         buf = buf + 1 == D ? 0 : buf + 1;

@@ -112,6 +112,10 @@ struct ss_ws_view {
     float* grad_rec;        // [total_records][SS_NGRAD]
     uint2* cover_list;      // [8 * max_instances]: per warp, (record, 32-pixel coverage word) of every staged
                             // surfel that covers a pixel of the warp's block, in list order (forward -> backward)
+    uint32_t* cover_adv;    // [8 * max_instances]: per cover_list entry, the pixel lanes where that
+                            // surfel's fragment opens a new layer (Algorithm 1's gap test as the
+                            // forward decided it; the first fragment of a pixel opens layer 0 and
+                            // is not marked)
     uint32_t* cover_count;  // [8 * tiles]: entries of each warp's list
     float4* env_acc;        // [scenes][env_texels][SS_ACC_STRIDE] RGBA accumulators of the env-map gradients (backward)
     float4* ssg_jac;        // [total_records][4] (screen_grad only): per record, the derivatives of

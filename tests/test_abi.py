@@ -150,3 +150,56 @@ def test_tile_shapes_validated_on_the_host():
         p.tile_w, p.tile_h = w, h
         st = lib.ss_workspace_size(ctypes.byref(d), ctypes.byref(p), None, 0, ctypes.byref(nb))
         assert (st == 0) == ok, (w, h)
+
+
+def test_density_calls_validate_on_the_host():
+    """Adaptive density control: struct layout, workspace sizing and the
+    host-side rejections (NULL pointers, bad parameters); empty inputs are a
+    no-op that launches nothing."""
+    lib = _lib.lib()
+    assert ctypes.sizeof(_lib.ss_density_params) == 32
+    assert ctypes.sizeof(_lib.ss_stage_times) == 8 * _lib.SS_N_STAGES == 64
+    p = _lib.ss_density_params()
+    lib.ss_default_density(ctypes.byref(p))
+    assert (p.k, p.max_rings, p.ops) == (8, 4, 7) and abs(p.split_scale - 0.7) < 1e-7 and p.cell == 0.0
+    nb = ctypes.c_size_t()
+    assert lib.ss_density_workspace_size(-1, ctypes.byref(nb)) == _lib.SS_ERR_INVALID_ARG
+    assert lib.ss_density_workspace_size(10, None) == _lib.SS_ERR_INVALID_ARG
+    assert lib.ss_density_workspace_size(0, ctypes.byref(nb)) == 0 and nb.value > 0
+    small = nb.value
+    assert lib.ss_density_workspace_size(1_000_000, ctypes.byref(nb)) == 0 and nb.value > 40 * 1_000_000 > small
+    s = _lib.ss_surfels(None, None, None, None, None, None)
+    off = (ctypes.c_int64 * 2)(0, 10)
+    p.cell = 0.1
+    # NULL pointers with surfels to process
+    assert lib.ss_density_neighbours(ctypes.byref(s), off, 1, ctypes.byref(p), None, None, None, None, 0,
+                                     None) == _lib.SS_ERR_INVALID_ARG
+    # bad parameters, bad offsets
+    for field, bad in (("cell", 0.0), ("k", 17), ("max_rings", 0), ("ops", 9)):
+        q = _lib.ss_density_params()
+        ctypes.memmove(ctypes.byref(q), ctypes.byref(p), ctypes.sizeof(q))
+        setattr(q, field, bad)
+        assert lib.ss_density_plan(None, None, None, None, None, None, 0, ctypes.byref(q), None, None, None, 0,
+                                   None) == _lib.SS_ERR_INVALID_ARG, field
+    bad_off = (ctypes.c_int64 * 3)(0, 10, 5)
+    assert lib.ss_density_neighbours(ctypes.byref(s), bad_off, 2, ctypes.byref(p), None, None, None, None, 0,
+                                     None) == _lib.SS_ERR_INVALID_ARG
+    assert lib.ss_density_plan(None, None, None, None, None, None, 5, ctypes.byref(p), None, None, None, 0,
+                               None) == _lib.SS_ERR_INVALID_ARG
+    assert lib.ss_density_apply(ctypes.byref(s), 5, None, None, ctypes.c_float(0.7), ctypes.byref(s),
+                                None) == _lib.SS_ERR_INVALID_ARG
+    assert lib.ss_density_apply(ctypes.byref(s), 0, None, None, ctypes.c_float(1.5), ctypes.byref(s),
+                                None) == _lib.SS_ERR_INVALID_ARG
+    assert lib.ss_density_compact(None, 0, 5, None, None, 0, None, None) == _lib.SS_ERR_INVALID_ARG
+    assert lib.ss_density_compact(None, 3, 5, None, None, 0, None, None) == _lib.SS_ERR_INVALID_ARG
+    # nothing to do: no launch
+    before = ctypes.c_int64()
+    lib.ss_launch_count(ctypes.byref(before))
+    zero = (ctypes.c_int64 * 2)(0, 0)
+    assert lib.ss_density_neighbours(ctypes.byref(s), zero, 1, ctypes.byref(p), None, None, None, None, 0,
+                                     None) == 0
+    assert lib.ss_density_apply(ctypes.byref(s), 0, None, None, ctypes.c_float(0.7), ctypes.byref(s), None) == 0
+    assert lib.ss_density_compact(None, 3, 0, None, None, 1, None, None) == 0
+    after = ctypes.c_int64()
+    lib.ss_launch_count(ctypes.byref(after))
+    assert after.value == before.value
