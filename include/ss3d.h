@@ -180,8 +180,9 @@ typedef struct ss_stats {
  * (host-side state, one profile at a time; not for use inside stream
  * capture).  Stages: 0 project, 1 bin+sort, 2 raster_fwd, 3 raster_bwd,
  * 4 project_bwd, 5 env_prefilter, 6 env_prefilter_backward, 7 density
- * control (ss_density_*). */
-#define SS_N_STAGES 8
+ * control (ss_density_*), 8 the densification statistic's per-record
+ * derivatives (ss_render_backward with screen_grad = 1). */
+#define SS_N_STAGES 9
 typedef struct ss_stage_times {
     float ms[SS_N_STAGES];       /* summed event durations */
     int32_t launches[SS_N_STAGES];

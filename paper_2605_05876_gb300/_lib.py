@@ -64,9 +64,9 @@ class ss_stats(ctypes.Structure):
                 ("bwd_batches", c_i64)]
 
 
-SS_N_STAGES = 8
+SS_N_STAGES = 9
 STAGES = ("project", "bin_sort", "raster_fwd", "raster_bwd", "project_bwd", "env_prefilter", "env_prefilter_bwd",
-          "density")
+          "density", "screen_grad_jac")
 
 
 class ss_stage_times(ctypes.Structure):

@@ -514,6 +514,10 @@ extern "C" ss_status ss_render_backward(const ss_batch_desc* b, const ss_surfels
                            st));
     CK(cudaMemsetAsync(W.work + 1, 0, sizeof(unsigned int), st));   // backward work-queue head
     {
+        ss_stage_scope sc(8, st);
+        ss_launch_screen_grad_jac(W, L, a, st);
+    }
+    {
         ss_stage_scope sc(3, st);
         ss_launch_raster_bwd(W, L, a, st);
     }

@@ -230,13 +230,15 @@ __device__ __forceinline__ d3 operator*(d3 a, d3 b) {
     return {a.v * b.v, a.x * b.v + a.v * b.x, a.y * b.v + a.v * b.y};
 }
 __device__ __forceinline__ d3 operator*(float k, d3 a) { return {k * a.v, k * a.x, k * a.y}; }
+// (the values only carry the partials, which the statistic needs to a few
+// ulp: approximate reciprocals and square roots serve)
 __device__ __forceinline__ d3 operator/(d3 a, d3 b) {
-    const float q = a.v / b.v, ib = 1.f / b.v;
+    const float ib = __fdividef(1.f, b.v), q = a.v * ib;
     return {q, (a.x - q * b.x) * ib, (a.y - q * b.y) * ib};
 }
 __device__ __forceinline__ d3 dsqrt(d3 a) {
-    const float r = sqrtf(a.v), h = 0.5f / r;
-    return {r, a.x * h, a.y * h};
+    const float ir = rsqrtf(a.v), h = 0.5f * ir;
+    return {a.v * ir, a.x * h, a.y * h};
 }
 __device__ __forceinline__ d3 dabs(d3 a) { return a.v < 0.f ? -a : a; }
 
@@ -319,11 +321,6 @@ __global__ void __launch_bounds__(256) ssg_jac_kernel(ss_ws_view ws, ss_fwd_args
     }
 }
 
-// per warp: the staged records' densification derivatives (screen_grad only)
-struct ss_wjac {
-    float4 j[WSLOTS][4];
-};
-
 // AOV = false when no AOV gradient is given: the AOV channels' coefficients
 // are zero, so only P, A2, B2, the centre, n_f and RGB (the first 12 values
 // of the record) are differentiated and summed.
@@ -340,7 +337,6 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
     const int lsr = ws.ls_rows;
     ss_wstage* Wst = reinterpret_cast<ss_wstage*>(bwd_smem);
     bwarp* Bws = reinterpret_cast<bwarp*>(bwd_smem + RWPB_BWD * sizeof(ss_wstage));
-    ss_wjac* Wjs = reinterpret_cast<ss_wjac*>(bwd_smem + RWPB_BWD * (sizeof(ss_wstage) + sizeof(bwarp)));
     const ss_layout* L = ws.layout;
     const int lw = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile = gw / a.f.ts.bpt, warp = gw - tile * a.f.ts.bpt;   // bpt blocks per tile
@@ -444,8 +440,9 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
 #pragma unroll
                 for (int q = 0; q < NV; ++q) B.tab[q * GCOL + lane] = gr[q];
                 if (SSG) {   // Eq. ss_grad: g = dL/dp + sum_k dL/dval_k jac[k]
-                    const float4* J = Wjs[lw].j[s];
-                    const float4 j0 = J[0], j1 = J[1], j2 = J[2], j3 = J[3];
+                    // the record's row (64 B, read by the ~8 lanes of its run: L1 hits after the first)
+                    const float4* J = ws.ssg_jac + (int64_t)Wc->id[s] * 4;
+                    const float4 j0 = __ldg(J), j1 = __ldg(J + 1), j2 = __ldg(J + 2), j3 = __ldg(J + 3);
                     const float gxs = gr[G_PX] + gr[G_P + 0] * j0.x + gr[G_P + 1] * j0.y + gr[G_P + 2] * j0.z +
                                       gr[G_P + 3] * j0.w + gr[G_A2] * j1.x + gr[G_B2] * j1.y + gr[G_NF] * j1.z;
                     const float gys = gr[G_PY] + gr[G_P + 0] * j2.x + gr[G_P + 1] * j2.y + gr[G_P + 2] * j2.z +
@@ -501,10 +498,9 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
         const int n = (int)min((int64_t)32, n_list - base);
         const uint2 cur = nxt;
         const uint32_t ca = lane < n ? nxa : 0u;   // layer-opening lanes of slot `lane`
-        if (SSG && lane < n) {   // the record's densification derivatives, with the record
-            const float4* J = ws.ssg_jac + (int64_t)cur.x * 4;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) cp_async16(&Wjs[lw].j[lane][k], J + k);
+        if (SSG && lane < n) {   // the record's densification derivatives into L2 ahead of their use
+            const char* pj = reinterpret_cast<const char*>(ws.ssg_jac + (int64_t)cur.x * 4);
+            asm volatile("prefetch.global.L2 [%0];\n" ::"l"(pj));
         }
         stage_ids(*Wc, recs, cur.x, lane, lane < n);
         nxt = base + 32 + lane < n_list ? __ldg(clist + base + 32 + lane) : make_uint2(0u, 0u);
@@ -570,8 +566,7 @@ __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kerne
 
 template <bool AOV, bool SSG, bool CONS, int W>
 static void launch_raster_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st) {
-    const int smem = W * (int)(sizeof(ss_wstage) + sizeof(ss_bwarp_t<SSG ? G_N + 2 : G_N, CONS ? GT + 3 : GT>) +
-                               (SSG ? sizeof(ss_wjac) : 0));
+    const int smem = W * (int)(sizeof(ss_wstage) + sizeof(ss_bwarp_t<SSG ? G_N + 2 : G_N, CONS ? GT + 3 : GT>));
     static std::atomic<unsigned long long> optin{0}, resident{0};
     ss_smem_optin(raster_bwd_kernel<AOV, SSG, CONS, W>, smem, optin);
     const int n_items = (int)(L.total_tiles * L.bpt);
@@ -588,17 +583,18 @@ static void launch_raster_bwd_w(int w, const ss_ws_view& ws, const ss_layout& L,
     else launch_raster_bwd<AOV, SSG, CONS, 8>(ws, L, a, st);
 }
 
+void ss_launch_screen_grad_jac(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st) {
+    if (L.total_tiles <= 0 || !ws.ssg_jac || !(a.g.screen_grad_norm || a.g.screen_grad_views)) return;
+    const int64_t n = L.scene_begin[L.n_scenes];
+    if (n <= 0) return;
+    ss_note_launch();
+    ssg_jac_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ws, a.f, n);
+}
+
 void ss_launch_raster_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st) {
     if (L.total_tiles <= 0) return;
     const bool ssg = ws.ssg_jac && (a.g.screen_grad_norm || a.g.screen_grad_views);
     const bool cons = a.f.p.cons != 0;   // (the host requires d_aov then)
-    if (ssg) {
-        const int64_t n = L.scene_begin[L.n_scenes];
-        if (n > 0) {
-            ss_note_launch();
-            ssg_jac_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ws, a.f, n);
-        }
-    }
     ss_note_launch();
     if (cons) layer_coeff_kernel<true><<<(unsigned)((L.total_pixels + 255) / 256), 256, 0, st>>>(ws, a);
     else layer_coeff_kernel<false><<<(unsigned)((L.total_pixels + 255) / 256), 256, 0, st>>>(ws, a);

@@ -407,5 +407,7 @@ struct ss_bwd_args {
     ss_surfel_grads g;
     ss_env_map_grads genv;
 };
+// the densification statistic's per-record derivatives (nothing unless requested)
+void ss_launch_screen_grad_jac(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st);
 void ss_launch_raster_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st);
 void ss_launch_project_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st);

@@ -158,7 +158,7 @@ def test_density_calls_validate_on_the_host():
     no-op that launches nothing."""
     lib = _lib.lib()
     assert ctypes.sizeof(_lib.ss_density_params) == 32
-    assert ctypes.sizeof(_lib.ss_stage_times) == 8 * _lib.SS_N_STAGES == 64
+    assert ctypes.sizeof(_lib.ss_stage_times) == 8 * _lib.SS_N_STAGES == 72
     p = _lib.ss_density_params()
     lib.ss_default_density(ctypes.byref(p))
     assert (p.k, p.max_rings, p.ops) == (8, 4, 7) and abs(p.split_scale - 0.7) < 1e-7 and p.cell == 0.0
