@@ -29,26 +29,46 @@
 #define G_SSC 22   // ... and their number
 
 // Backward rasteriser, per warp (8 x 4 pixels): the forward pass left a
-// coverage word and a layer-opening word per (warp, staged surfel); the
-// replay of each pixel's grouping only reads those words, and every fragment
-// it accepts is
-// recorded (slot, pixel lane).  The recorded fragments are then
-// differentiated 32 at a time, one per lane: lane f writes its 22 values to
-// column f of a 22 x 32 table; lane q loads row q into registers and sums it
-// over each run of columns of the same surfel (records are in surfel order),
-// with one atomic add per value and run.
+// coverage word and a layer-opening word per (warp, staged surfel).  A chunk
+// of 32 staged surfels is cut at the surfels that open a new layer at a live
+// pixel; between two cuts every pixel stays in its layer, so the fragments of
+// the slots in between are numbered in list order (a prefix sum of the slots'
+// live coverage counts) and differentiated 32 at a time, one per lane: lane f
+// finds its slot by a binary search over the prefix sums and its pixel as the
+// j-th set bit of that slot's word, writes its 22 values to column f of a
+// 22 x 32 table; lane q then loads row q into registers and sums it over each
+// run of columns of the same surfel (runs are contiguous), with one atomic add
+// per value and run.  At a cut the opening pixels enter their next layer.
 #define GCOL 36     // table row stride: 16-byte aligned rows, conflict-free column writes
 #define GT 13       // floats per pixel lane in the layer-coefficient table: G_k (12), S_k
-#define BW_CAP 128  // recorded fragments per warp before they are differentiated
+
+// Row stride of the per-pixel layer-coefficient table: GTR rounded up to an
+// even count whose half is odd, so that the 8-byte loads of 16 lanes at
+// distinct pixels fall in distinct bank pairs.
+__host__ __device__ constexpr int ss_gt_stride(int gtr) { return ((gtr + 1) / 2) % 2 ? 2 * ((gtr + 1) / 2) : 2 * ((gtr + 1) / 2) + 2; }
 
 // ROWS table rows: G_N, or G_N + 2 with the densification statistic; GTR
 // layer coefficients per pixel lane: GT, or GT + 3 with the consolidation term
 template <int ROWS, int GTR>
 struct ss_bwarp_t {
     float tab[ROWS * GCOL];
-    float gtab[32 * GTR];
-    uint32_t rec[BW_CAP];
+    float gtab[32 * ss_gt_stride(GTR)];
 };
+
+// Position of the j-th (0-based) set bit of m, for j < popc(m): halving
+// search on population counts.
+__device__ __forceinline__ int ss_nth_bit(uint32_t m, int j) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const int c = __popc((m >> pos) & ((1u << w) - 1u));
+        if (j >= c) {
+            j -= c;
+            pos += w;
+        }
+    }
+    return pos;
+}
 
 // Per pixel, per composited layer k (front to back), from the upstream
 // gradient g and the layer totals (C_k, W_k) kept by the forward pass:
@@ -354,7 +374,6 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
     const float rc2 = a.f.p.r_cut * a.f.p.r_cut;
     const int64_t P = L->total_pixels;
     const int64_t gpix = vl.pixel_off + (int64_t)(inside ? py : 0) * vl.width + (inside ? px : 0);
-    const unsigned lanes_below = (1u << lane) - 1u;
 
     // per-pixel state: layer count from the forward pass; the per-layer
     // gradient coefficients (G_k, S_k) were written over the layer totals by
@@ -367,13 +386,12 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
     // in cover_adv the fragments that open a new layer (its gap test), so
     // the replay only counts them
     int k = 0;
-    bool pend = false;
-    int npend = 0;   // warp-uniform: fragments recorded, not yet differentiated
+    constexpr int GTS = ss_gt_stride(GTR);
 
     auto enter_layer = [&](int kk) {   // this lane's layer coefficients -> B.gtab
         const float* ls = ws.layer_state + (int64_t)kk * lsr * P + gpix;
 #pragma unroll
-        for (int c = 0; c < GTR; ++c) B.gtab[lane * GTR + c] = ls[c * P];
+        for (int c = 0; c < GTR; ++c) B.gtab[lane * GTS + c] = ls[c * P];
     };
     if (!done) enter_layer(0);
 
@@ -388,16 +406,37 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
     const uint32_t* alist = ws.cover_adv + 8 * beg + (int64_t)warp * (end - beg);
     const int64_t n_list = ws.cover_count[(int64_t)tile * 8 + warp];
 
-    // Differentiate every recorded fragment, 32 at a time (one per lane), then
-    // sum the gradient rows of each run of equal surfels and add the sums.
-    auto run_batches = [&]() {
-        __syncwarp();   // records and layer tables written by other lanes
-        for (int b0 = 0; b0 < npend; b0 += 32) {
+    // Differentiate the fragments of staged slots [sa, sb) at the live pixels
+    // (dmask: pixels past their last layer), 32 at a time in list order (one
+    // per lane), then sum the gradient rows of each run of equal surfels and
+    // add the sums.  Every pixel stays in its layer within [sa, sb).
+    auto run_slots = [&](int sa, int sb, uint32_t cmw, uint32_t dmask) {
+        const uint32_t eff = (lane >= sa && lane < sb) ? (cmw & ~dmask) : 0u;
+        const int cnt = __popc(eff);
+        int incl = cnt;   // inclusive prefix sum of the slots' fragment counts
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int excl = incl - cnt;
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        n_frag += lane == 0 ? (unsigned)total : 0u;
+        __syncwarp();   // layer tables written by other lanes
+        for (int b0 = 0; b0 < total; b0 += 32) {
             ++n_batch;
-            const int nb = min(32, npend - b0);
+            const int nb = min(32, total - b0);
             const bool valid = lane < nb;
-            const uint32_t rc = valid ? B.rec[b0 + lane] : 0u;
-            const int s = rc & 31, pl = (rc >> 5) & 31;
+            const int F = b0 + lane;
+            int s = 0;   // the slot of fragment F: the first with incl > F
+#pragma unroll
+            for (int st = 16; st >= 1; st >>= 1) {
+                const int v = __shfl_sync(0xffffffffu, incl, s + st - 1);
+                if (v <= F) s += st;
+            }
+            const uint32_t es = __shfl_sync(0xffffffffu, eff, s);
+            const int first = __shfl_sync(0xffffffffu, excl, s);
+            const int pl = valid ? ss_nth_bit(es, F - first) : 0;   // its pixel lane
             if (valid) {
                 const float4 h0 = Wc->h0[s], h1 = Wc->h1[s], h2 = Wc->h2[s];
                 const float dx = (float)(wx0 + (pl & 7)) + 0.5f - h1.z;
@@ -407,7 +446,16 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
                 const float rho2 = __fdividef(h.q, h.t);
                 const float ex = __expf(-0.5f * rho2);
                 const float w = nf * ex;   // the forward kernel's weight, same operations
-                const float* gt = B.gtab + pl * GTR;
+                float gt[GTS];   // the pixel's layer coefficients, 8 bytes at a time
+                {
+                    const float2* g2 = reinterpret_cast<const float2*>(B.gtab + pl * GTS);
+#pragma unroll
+                    for (int c = 0; c < GTS / 2; ++c) {
+                        const float2 t = g2[c];
+                        gt[2 * c] = t.x;
+                        gt[2 * c + 1] = t.y;
+                    }
+                }
                 const float4 c0v = Wc->c0[s], c1v = Wc->c1[s], c2v = Wc->c2[s];
                 const float ch[SS_NCH] = {c0v.x, c0v.y, c0v.z, c1v.x, c1v.y, c1v.z,
                                           c1v.w, c2v.x, c2v.y, c2v.z, c2v.w, 0.5f * (h2.x + h2.y)};
@@ -486,8 +534,6 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
             }
             __syncwarp();
         }
-        npend = 0;
-        pend = false;
     };
 
     // one staging buffer; the records of the next chunk are prefetched into L2
@@ -512,34 +558,28 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
         }
         stage_finish(*Wc, n, lane, (float)x0, (float)y0);
         const uint32_t cm = lane < n ? cur.y : 0u;   // forward coverage of slot `lane`
-        uint32_t nz = __ballot_sync(0xffffffffu, cm != 0u);
-        while (nz) {
-            const int s = __ffs(nz) - 1;
-            nz &= nz - 1;
-            const uint32_t m = __shfl_sync(0xffffffffu, cm, s);
-            const uint32_t av = __shfl_sync(0xffffffffu, ca, s);
-            const bool my = ((m >> lane) & 1u) && !done;
-            // replay of Algorithm 1: the forward kernel's grouping decisions
-            const bool adv = my && ((av >> lane) & 1u);
-            if (__any_sync(0xffffffffu, adv && pend)) run_batches();   // pending fragments use the open layer
-            if (adv) {
+        // replay of Algorithm 1: cut the chunk at each slot that opens a new
+        // layer at a live pixel (the forward kernel's gap decisions); the
+        // opening slot's own fragments belong to the new layers
+        int sa = 0, applied = -1;
+        for (;;) {
+            const uint32_t dmask = __ballot_sync(0xffffffffu, done);
+            if (dmask == 0xffffffffu) break;
+            const uint32_t am = __ballot_sync(0xffffffffu, lane > applied && (ca & ~dmask) != 0u);
+            const int sb = am ? __ffs(am) - 1 : n;
+            run_slots(sa, sb, cm, dmask);
+            if (sb >= n) break;
+            const uint32_t av = __shfl_sync(0xffffffffu, ca, sb);
+            if (!done && ((av >> lane) & 1u)) {
                 ++k;
                 if (k >= K) done = true;
                 else enter_layer(k);
             }
-            const bool app = my && !done;
-            const uint32_t am = __ballot_sync(0xffffffffu, app);
-            if (npend + __popc(am) > BW_CAP) run_batches();
-            if (app) {
-                B.rec[npend + __popc(am & lanes_below)] = (uint32_t)s | ((uint32_t)lane << 5);
-                pend = true;
-                ++n_frag;
-            }
-            npend += __popc(am);
+            sa = sb;
+            applied = sb;
             __syncwarp();
         }
-        if (npend) run_batches();   // the next chunk rewrites the staged slots
-        __syncwarp();
+        __syncwarp();   // the next chunk rewrites the staged slots
     }
     if (a.f.p.collect_stats) {
         unsigned long long x = n_frag;

@@ -132,6 +132,21 @@ def test_backward_multi_view_multi_scene():
     _compare(gpu, ref)
 
 
+@pytest.mark.parametrize("k_max", [1, 2, 3, 16])
+def test_backward_layer_cap(k_max):
+    """Four planes in depth (four layers at the covered pixels) under K_max
+    below, at and above that count: the replay cuts each chunk of staged
+    surfels at the ones that open a layer and stops a pixel at its last
+    composited layer."""
+    rng = np.random.default_rng(7)
+    planes = [_tiny.grid_plane(24, 0.03, z=0.05 * k, scale=0.025, albedo=tuple(rng.uniform(0, 1, 3)))
+              for k in range(4)]
+    surf = S.Surfels.concat(planes)
+    sc = S.Scene(surf, np.array([0, surf.n]), [_tiny.lognormal_env(rng, 32, 16)], [_tiny.front_camera(res=40)], "cap")
+    gpu, ref = _run(sc, 20 + k_max, params=dict(k_max=k_max))
+    _compare(gpu, ref)
+
+
 @pytest.mark.slow
 def test_backward_torus_sphere_100k():
     gpu, ref = _run(S.torus_sphere_100k(), 9)
