@@ -34,39 +34,39 @@
 // pixel; between two cuts every pixel stays in its layer, so the fragments of
 // the slots in between are numbered in list order (a prefix sum of the slots'
 // live coverage counts) and differentiated 32 at a time, one per lane: lane f
-// finds its slot by a binary search over the prefix sums and its pixel as the
-// j-th set bit of that slot's word, writes its 22 values to column f of a
+// finds its slot from the slot starts that fall inside its batch (a binary
+// search over the prefix sums when an empty slot lies in between) and its
+// pixel as the j-th set bit of that slot's word, writes its 22 values to column f of a
 // 22 x 32 table; lane q then loads row q into registers and sums it over each
 // run of columns of the same surfel (runs are contiguous), with one atomic add
 // per value and run.  At a cut the opening pixels enter their next layer.
 #define GCOL 36     // table row stride: 16-byte aligned rows, conflict-free column writes
 #define GT 13       // floats per pixel lane in the layer-coefficient table: G_k (12), S_k
 
-// Row stride of the per-pixel layer-coefficient table: GTR rounded up to an
-// even count whose half is odd, so that the 8-byte loads of 16 lanes at
-// distinct pixels fall in distinct bank pairs.
-__host__ __device__ constexpr int ss_gt_stride(int gtr) { return ((gtr + 1) / 2) % 2 ? 2 * ((gtr + 1) / 2) : 2 * ((gtr + 1) / 2) + 2; }
-
 // ROWS table rows: G_N, or G_N + 2 with the densification statistic; GTR
 // layer coefficients per pixel lane: GT, or GT + 3 with the consolidation term
 template <int ROWS, int GTR>
 struct ss_bwarp_t {
     float tab[ROWS * GCOL];
-    float gtab[32 * ss_gt_stride(GTR)];
+    float gtab[32 * GTR];
 };
 
-// Position of the j-th (0-based) set bit of m, for j < popc(m): halving
-// search on population counts.
+// Position of the j-th (0-based) set bit of m, for j < popc(m): the byte
+// from the population counts of the low bytes, then a halving search inside
+// the byte.
 __device__ __forceinline__ int ss_nth_bit(uint32_t m, int j) {
-    int pos = 0;
-#pragma unroll
-    for (int w = 16; w >= 1; w >>= 1) {
-        const int c = __popc((m >> pos) & ((1u << w) - 1u));
-        if (j >= c) {
-            j -= c;
-            pos += w;
-        }
-    }
+    const int c1 = __popc(m & 0xffu), c2 = __popc(m & 0xffffu), c3 = __popc(m & 0xffffffu);
+    int pos = 0, below = 0;
+    if (j >= c1) { pos = 8; below = c1; }
+    if (j >= c2) { pos = 16; below = c2; }
+    if (j >= c3) { pos = 24; below = c3; }
+    j -= below;
+    uint32_t b = (m >> pos) & 0xffu;
+    int c = __popc(b & 0xfu);
+    if (j >= c) { j -= c; pos += 4; b >>= 4; }
+    c = __popc(b & 3u);
+    if (j >= c) { j -= c; pos += 2; b >>= 2; }
+    if (j >= (int)(b & 1u)) pos += 1;
     return pos;
 }
 
@@ -386,12 +386,11 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
     // in cover_adv the fragments that open a new layer (its gap test), so
     // the replay only counts them
     int k = 0;
-    constexpr int GTS = ss_gt_stride(GTR);
 
     auto enter_layer = [&](int kk) {   // this lane's layer coefficients -> B.gtab
         const float* ls = ws.layer_state + (int64_t)kk * lsr * P + gpix;
 #pragma unroll
-        for (int c = 0; c < GTR; ++c) B.gtab[lane * GTS + c] = ls[c * P];
+        for (int c = 0; c < GTR; ++c) B.gtab[lane * GTR + c] = ls[c * P];
     };
     if (!done) enter_layer(0);
 
@@ -421,7 +420,13 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
         }
         const int excl = incl - cnt;
         const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total == 0) return;
         n_frag += lane == 0 ? (unsigned)total : 0u;
+        // nonempty slots; when they are consecutive, a fragment's slot is the
+        // one holding the batch's first fragment plus the slot starts between
+        const uint32_t ne = __ballot_sync(0xffffffffu, cnt > 0);
+        const bool contig = ((ne + (ne & (0u - ne))) & ne) == 0u;
+        const int ne0 = __ffs(ne) - 1;
         __syncwarp();   // layer tables written by other lanes
         for (int b0 = 0; b0 < total; b0 += 32) {
             ++n_batch;
@@ -429,10 +434,17 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
             const bool valid = lane < nb;
             const int F = b0 + lane;
             int s = 0;   // the slot of fragment F: the first with incl > F
+            if (contig) {
+                const uint32_t starts = __reduce_or_sync(
+                    0xffffffffu, (cnt > 0 && excl > b0 && excl < b0 + 32) ? 1u << (excl - b0) : 0u);
+                const int c0 = __popc(__ballot_sync(0xffffffffu, cnt > 0 && excl <= b0));
+                s = min(31, ne0 + c0 - 1 + __popc(starts & ((2u << lane) - 1u)));
+            } else {
 #pragma unroll
-            for (int st = 16; st >= 1; st >>= 1) {
-                const int v = __shfl_sync(0xffffffffu, incl, s + st - 1);
-                if (v <= F) s += st;
+                for (int st = 16; st >= 1; st >>= 1) {
+                    const int v = __shfl_sync(0xffffffffu, incl, s + st - 1);
+                    if (v <= F) s += st;
+                }
             }
             const uint32_t es = __shfl_sync(0xffffffffu, eff, s);
             const int first = __shfl_sync(0xffffffffu, excl, s);
@@ -446,16 +458,9 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
                 const float rho2 = __fdividef(h.q, h.t);
                 const float ex = __expf(-0.5f * rho2);
                 const float w = nf * ex;   // the forward kernel's weight, same operations
-                float gt[GTS];   // the pixel's layer coefficients, 8 bytes at a time
-                {
-                    const float2* g2 = reinterpret_cast<const float2*>(B.gtab + pl * GTS);
-#pragma unroll
-                    for (int c = 0; c < GTS / 2; ++c) {
-                        const float2 t = g2[c];
-                        gt[2 * c] = t.x;
-                        gt[2 * c + 1] = t.y;
-                    }
-                }
+                // the pixel's layer coefficients (row stride 13 or 16 floats: 4-byte loads of distinct
+                // pixels fall in distinct banks for the odd stride)
+                const float* gt = B.gtab + pl * GTR;
                 const float4 c0v = Wc->c0[s], c1v = Wc->c1[s], c2v = Wc->c2[s];
                 const float ch[SS_NCH] = {c0v.x, c0v.y, c0v.z, c1v.x, c1v.y, c1v.z,
                                           c1v.w, c2v.x, c2v.y, c2v.z, c2v.w, 0.5f * (h2.x + h2.y)};
@@ -508,7 +513,7 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
                 const float4* t4 = reinterpret_cast<const float4*>(B.tab + (lane < NVT ? lane : 0) * GCOL);
 #pragma unroll
                 for (int m = 0; m < 8; ++m) {
-                    const float4 x = t4[m];
+                    const float4 x = lane < NVT ? t4[m] : make_float4(0.f, 0.f, 0.f, 0.f);
                     v[4 * m] = x.x; v[4 * m + 1] = x.y; v[4 * m + 2] = x.z; v[4 * m + 3] = x.w;
                 }
             }
