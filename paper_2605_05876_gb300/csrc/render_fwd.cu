@@ -895,8 +895,10 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
     }
 }
 
+// 28 warps per SM (at most 72 registers a thread): more resident warps hide
+// more of the staging and shared-memory latency (6.52 -> 6.39 ms against 24)
 template <bool STATS, bool PP, bool CONS, int RWPB_FWD>
-__global__ void __launch_bounds__(32 * RWPB_FWD, 24 / RWPB_FWD) raster_fwd_kernel(ss_ws_view ws, ss_fwd_args a,
+__global__ void __launch_bounds__(32 * RWPB_FWD, 28 / RWPB_FWD) raster_fwd_kernel(ss_ws_view ws, ss_fwd_args a,
                                                                                   int n_items) {
     extern __shared__ __align__(16) unsigned char fwd_smem[];
     const int lane = threadIdx.x & 31;
