@@ -94,6 +94,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--no-screen-grad", action="store_true", help="skip timing the densification statistic")
+    ap.add_argument("--no-det", action="store_true", help="skip timing the deterministic backward")
     return ap.parse_args()
 
 
@@ -597,6 +598,35 @@ def run_ours(args):
         del rs
         torch.cuda.empty_cache()
 
+    # --- the same step with the deterministic (fixed-order) backward
+    deterministic = None
+    if not args.no_det:
+        rd = Renderer(scene, share_from=r)
+        for k in KNOBS:
+            setattr(rd.prm, k, getattr(r.prm, k))
+        rd.prm.deterministic = 1
+        rd.prm.det_rows = int(counts["staged_covering"] * 1.05) + 4096   # one row per covering (block, surfel)
+        rd.plan_capacity()
+        rd.zero_grads()
+
+        def step_det():
+            rd.prefilter_env()
+            rd.forward()
+            rd.zero_grads()
+            rd.backward(d_rgba, d_aov)
+        for _ in range(args.warmup):
+            step_det()
+        profile_begin()
+        ms_d = timed(step_det, args.steps)
+        st_d = profile_end()
+        if rd.read_status() != 0:
+            raise RuntimeError(f"device status {rd.read_status()} in the deterministic step")
+        deterministic = {"value": job_rate(V, args.steps, world, ms_d), "unit": "views/s",
+                         "ms_per_step": ms_d / args.steps, "cost_vs_step": ms_d / ms - 1.0,
+                         "stage_ms": {k: round(v[0] / args.steps, 4) for k, v in st_d.items() if v[1]}}
+        del rd
+        torch.cuda.empty_cache()
+
     # --- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -673,7 +703,7 @@ def run_ours(args):
                            "inputs_vs_l2": "inputs and intermediates > 129 MB L2 (no flush)",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "launch_shapes": tuned or "defaults"},
-                "per_view": per_view, "graph": graph, "screen_grad": screen_grad, "density": density, "e2e": e2e,
+                "per_view": per_view, "graph": graph, "screen_grad": screen_grad, "deterministic": deterministic, "density": density, "e2e": e2e,
                 "roofline": roofline, "hbm": hbm_line,
                 "cpu_baseline": cpu,
                 "clocks": clocks,

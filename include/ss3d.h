@@ -47,7 +47,9 @@ typedef int ss_status;
 #define SS_ERR_INVALID_ARG 1  /* bad argument; nothing was enqueued */
 #define SS_ERR_WORKSPACE 2    /* workspace smaller than ss_workspace_size */
 #define SS_ERR_CAPACITY 4     /* device: more (tile, surfel) instances than
-                                 ss_render_params.max_instances; the affected
+                                 ss_render_params.max_instances, or (the
+                                 deterministic backward) more covering (block,
+                                 surfel) pairs than det_rows; the affected
                                  outputs are incomplete */
 #define SS_ERR_TIMEOUT 8      /* device: a bounded wait gave up */
 #define SS_ERR_NONFINITE 16   /* device: a non-finite surfel parameter was seen
@@ -159,7 +161,21 @@ typedef struct ss_render_params {
                                 (default 16 x 16, App. A) */
     int32_t stage_depth;     /* forward rasteriser: chunks of 32 candidate records in flight per warp
                                 (1 = none ahead, 2 default, 3) */
-    int32_t pad_;
+    int32_t deterministic;   /* 1: ss_render_backward sums in a fixed order, so that two calls on the
+                                same inputs give bitwise-equal gradients (the FP32 atomic adds of
+                                the default mode leave the last bits to the scheduling): each
+                                (warp block, staged surfel) writes its fragment sums to a row of
+                                its own, and every (surfel, view) record sums its rows in row
+                                order; the environment-texel gradients are summed as 64-bit
+                                fixed-point integers (exact and order-free; the scale is a power of
+                                two from a bound on the largest contribution, so one unit is at
+                                most 2^-28 of the largest record colour gradient).  Slower; the
+                                workspace holds 104 bytes per row (det_rows) more */
+    int64_t det_rows;        /* deterministic = 1: capacity of those rows, one per (warp block,
+                                staged surfel that covers a pixel of the block) pair
+                                (ss_stats.staged_covering of the forward); 0 = the bound of
+                                (blocks per tile) x max_instances.  More pairs than rows set
+                                SS_ERR_CAPACITY (the gradients are then incomplete) */
 } ss_render_params;
 
 /* Work counters of the last forward/backward pair (collect_stats = 1). */
@@ -285,10 +301,21 @@ ss_status ss_env_prefilter_backward(const ss_env_desc* d, int32_t n_envs, const 
                                     const float* d_spec_dev, const float* aux_dev, float* d_env_dev,
                                     void* stream);
 
+/* The same transpose with the level terms added one level after the other
+ * on `stream` (level 0, the specular levels 1 .. n_levels - 1, then the
+ * irradiance map), each base texel receiving one add per term: d_env is then
+ * bitwise the same from call to call.  The companion of
+ * ss_render_params.deterministic = 1; slower than the forked form. */
+ss_status ss_env_prefilter_backward_ordered(const ss_env_desc* d, int32_t n_envs, const float* d_irr_dev,
+                                            const float* d_spec_dev, const float* aux_dev, float* d_env_dev,
+                                            void* stream);
+
 /* Workspace bytes for a render of this batch.  with_backward != 0 adds the
  * per-pixel layer state that ss_render_backward reads and, for the env
  * description ed (required then: the one later passed to the render calls),
- * the accumulators of the env-map gradients.  Requires p->max_instances > 0.
+ * the accumulators of the env-map gradients (and, with p->deterministic = 1,
+ * the rows and per-record lists of the fixed-order sums).  Requires
+ * p->max_instances > 0.
  * Host only (reads no device memory).  Errors: SS_ERR_INVALID_ARG for bad
  * sizes, an invalid ed or a launch shape (fwd_warps, bwd_warps, pbwd_block)
  * without a compiled kernel; the render calls reject the same values. */

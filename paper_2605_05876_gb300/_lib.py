@@ -55,7 +55,7 @@ class ss_render_params(ctypes.Structure):
                 ("bg", c_f * 3), ("write_aov", c_i32), ("lut_n", c_i32), ("max_instances", c_i64),
                 ("collect_stats", c_i32), ("fwd_warps", c_i32), ("bwd_warps", c_i32), ("pbwd_block", c_i32),
                 ("screen_grad", c_i32), ("mip_mode", c_i32), ("cons", c_i32), ("tile_w", c_i32), ("tile_h", c_i32),
-                ("stage_depth", c_i32), ("pad_", c_i32)]
+                ("stage_depth", c_i32), ("deterministic", c_i32), ("det_rows", c_i64)]
 
 
 class ss_stats(ctypes.Structure):
@@ -121,6 +121,8 @@ EXPORTS = {
     "ss_env_prefilter": (c_i32, [ctypes.POINTER(ss_env_desc), c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "ss_env_prefilter_noalloc": (c_i32, [ctypes.POINTER(ss_env_desc), c_i32, c_vp, c_vp, c_vp, c_vp]),
     "ss_env_prefilter_backward": (c_i32, [ctypes.POINTER(ss_env_desc), c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "ss_env_prefilter_backward_ordered": (c_i32, [ctypes.POINTER(ss_env_desc), c_i32, c_vp, c_vp, c_vp, c_vp,
+                                                  c_vp]),
     "ss_workspace_size": (c_i32, [ctypes.POINTER(ss_batch_desc), ctypes.POINTER(ss_render_params),
                                   ctypes.POINTER(ss_env_desc), c_i32,
                                   ctypes.POINTER(ctypes.c_size_t)]),

@@ -178,9 +178,10 @@ class Renderer:
             self.screen_grad_views = torch.zeros(self.n_surfels, device=self.dev)
 
     def env_backward(self):
-        check(lib().ss_env_prefilter_backward(ctypes.byref(self.ed), self.n_scenes, _ptr(self.d_irr),
-                                              _ptr(self.d_spec), _ptr(self.aux), _ptr(self.d_env), _stream()),
-              "ss_env_prefilter_backward")
+        # with params deterministic=1 the level terms are added in a fixed order
+        name = "ss_env_prefilter_backward_ordered" if self.prm.deterministic else "ss_env_prefilter_backward"
+        check(getattr(lib(), name)(ctypes.byref(self.ed), self.n_scenes, _ptr(self.d_irr), _ptr(self.d_spec),
+                                   _ptr(self.aux), _ptr(self.d_env), _stream()), name)
 
     def stats(self):
         st = C.ss_stats()

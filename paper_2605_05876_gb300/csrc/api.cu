@@ -1,6 +1,8 @@
 // C ABI entry points (include/ss3d.h): argument checks, batch layout,
 // workspace carving and the launch sequences.
+#include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <math.h>
 #include <string.h>
 
@@ -105,6 +107,8 @@ static ss_status check_knobs(const ss_render_params* p) {
     if (!(tw == 8 || tw == 16 || tw == 32) || !(th == 4 || th == 8 || th == 16 || th == 32)) return SS_ERR_INVALID_ARG;
     if ((tw / 8) * (th / 4) > 8) return SS_ERR_INVALID_ARG;
     if (p->stage_depth < 0 || p->stage_depth > 3) return SS_ERR_INVALID_ARG;
+    if (p->deterministic != 0 && p->deterministic != 1) return SS_ERR_INVALID_ARG;
+    if (p->det_rows < 0 || p->det_rows > 0xffffffffll) return SS_ERR_INVALID_ARG;
     return SS_OK;
 }
 
@@ -199,7 +203,17 @@ struct ws_plan {
     size_t status, layout, vgeo, rec, rank, rbm, tc, ts, tcur, keys, keys_alt, bmask, cand, layer, pix, grad, masks,
         madv, mcount, env_acc, jac, total;
     int64_t env_texels;   // irradiance + specular texels of one scene (0: no env-gradient scratch)
+    // deterministic backward
+    size_t d_icnt, d_coff, d_rows, d_rid, d_rcnt, d_roff, d_rcur, d_rlist, d_scan;
+    int64_t det_cap;
 };
+
+// rows of the deterministic backward: det_rows, or (blocks per tile) x max_instances
+static int64_t det_capacity(const ss_layout& L, const ss_render_params& p) {
+    if (!p.deterministic) return 0;
+    const int64_t c = p.det_rows ? p.det_rows : (int64_t)L.bpt * p.max_instances;
+    return c < 0xffffffffll ? (c > 0 ? c : 1) : 0xffffffffll;
+}
 
 static ws_plan plan_ws(const ss_layout& L, const ss_render_params& p, int with_bwd, const ss_env_desc* ed) {
     ws_plan w;
@@ -235,6 +249,22 @@ static ws_plan plan_ws(const ss_layout& L, const ss_render_params& p, int with_b
     } else {
         w.layer = w.pix = w.grad = w.masks = w.madv = w.mcount = w.env_acc = w.jac = 0;
     }
+    w.det_cap = with_bwd ? det_capacity(L, p) : 0;
+    if (w.det_cap) {
+        const int64_t items = (int64_t)L.total_tiles * L.bpt, R = L.total_records;
+        w.d_icnt = take(sizeof(uint32_t) * (size_t)items);
+        w.d_coff = take(sizeof(uint32_t) * (size_t)(items + 1));
+        w.d_rows = take(sizeof(float) * SS_NGRAD * (size_t)w.det_cap);
+        w.d_rid = take(sizeof(uint32_t) * (size_t)w.det_cap);
+        w.d_rcnt = take(sizeof(uint32_t) * (size_t)R);
+        w.d_roff = take(sizeof(uint32_t) * (size_t)(R + 1));
+        w.d_rcur = take(sizeof(uint32_t) * (size_t)R);
+        w.d_rlist = take(sizeof(uint32_t) * (size_t)w.det_cap);
+        const int64_t nb = ss_det_scan_blocks(items > R ? items : R);
+        w.d_scan = take(sizeof(unsigned long long) * (size_t)(nb + 1));
+    } else {
+        w.d_icnt = w.d_coff = w.d_rows = w.d_rid = w.d_rcnt = w.d_roff = w.d_rcur = w.d_rlist = w.d_scan = 0;
+    }
     w.total = o;
     return w;
 }
@@ -268,6 +298,17 @@ static ss_ws_view carve(void* ws, const ws_plan& w, const ss_render_params& p, i
     v.ssg_jac = (with_bwd && p.screen_grad) ? (float4*)(b + w.jac) : nullptr;
     v.env_texels = w.env_texels;
     v.max_instances = p.max_instances;
+    v.det_cap = with_bwd ? w.det_cap : 0;
+    v.det_icnt = v.det_cap ? (uint32_t*)(b + w.d_icnt) : nullptr;
+    v.det_coff = v.det_cap ? (uint32_t*)(b + w.d_coff) : nullptr;
+    v.det_rows = v.det_cap ? (float*)(b + w.d_rows) : nullptr;
+    v.det_rid = v.det_cap ? (uint32_t*)(b + w.d_rid) : nullptr;
+    v.det_rcnt = v.det_cap ? (uint32_t*)(b + w.d_rcnt) : nullptr;
+    v.det_roff = v.det_cap ? (uint32_t*)(b + w.d_roff) : nullptr;
+    v.det_rcur = v.det_cap ? (uint32_t*)(b + w.d_rcur) : nullptr;
+    v.det_rlist = v.det_cap ? (uint32_t*)(b + w.d_rlist) : nullptr;
+    v.det_scan = v.det_cap ? (unsigned long long*)(b + w.d_scan) : nullptr;
+    v.det_maxbits = (unsigned int*)(b + w.status + SS_DET_OFFSET);
     return v;
 }
 
@@ -368,6 +409,18 @@ extern "C" ss_status ss_env_prefilter_backward(const ss_env_desc* d, int32_t n_e
     {
         ss_stage_scope sc(6, (cudaStream_t)stream);
         ss_launch_env_prefilter_bwd(d, n_envs, d_irr_dev, d_spec_dev, aux_dev, d_env_dev, (cudaStream_t)stream);
+    }
+    CK(cudaGetLastError());
+    return SS_OK;
+}
+
+extern "C" ss_status ss_env_prefilter_backward_ordered(const ss_env_desc* d, int32_t n_envs, const float* d_irr_dev,
+                                                       const float* d_spec_dev, const float* aux_dev,
+                                                       float* d_env_dev, void* stream) {
+    if (!env_desc_ok(d) || n_envs < 1 || !aux_dev || !d_env_dev) return SS_ERR_INVALID_ARG;
+    {
+        ss_stage_scope sc(6, (cudaStream_t)stream);
+        ss_launch_env_prefilter_bwd(d, n_envs, d_irr_dev, d_spec_dev, aux_dev, d_env_dev, (cudaStream_t)stream, true);
     }
     CK(cudaGetLastError());
     return SS_OK;
@@ -508,18 +561,43 @@ extern "C" ss_status ss_render_backward(const ss_batch_desc* b, const ss_surfels
     a.g = *g;
     ss_env_map_grads ge = {nullptr, nullptr};
     a.genv = genv ? *genv : ge;
+    // deterministic mode: the most views of a scene, and log2 of a bound on the
+    // contributions one env texel can receive (every surfel side's irradiance
+    // taps and every record's specular taps: 8 each)
+    a.det_vmax = 1;
+    a.det_cbits = 1;
+    if (W.det_cap) {
+        int vmax = 1;
+        for (int sc = 0; sc < L.n_scenes; ++sc) vmax = std::max(vmax, L.scene_view_begin[sc + 1] - L.scene_view_begin[sc]);
+        const double contrib = 8.0 * ((double)L.scene_begin[L.n_scenes] + (double)L.total_records) + 1.0;
+        a.det_vmax = vmax;
+        a.det_cbits = (int)std::ceil(std::log2(contrib));
+        if (a.det_cbits > 40) return SS_ERR_INVALID_ARG;   // the fixed-point sums would keep too few bits
+    }
     CK(cudaMemsetAsync(W.grad_rec, 0, sizeof(float) * SS_NGRAD * (size_t)L.total_records, st));
     if (a.genv.irr || a.genv.spec)
         CK(cudaMemsetAsync(W.env_acc, 0, sizeof(float4) * SS_ACC_STRIDE * (size_t)W.env_texels * (size_t)L.n_scenes,
                            st));
     CK(cudaMemsetAsync(W.work + 1, 0, sizeof(unsigned int), st));   // backward work-queue head
+    if (W.det_cap) {
+        CK(cudaMemsetAsync(W.det_rid, 0xff, sizeof(uint32_t) * (size_t)W.det_cap, st));
+        CK(cudaMemsetAsync(W.det_rcnt, 0, sizeof(uint32_t) * (size_t)L.total_records, st));
+        CK(cudaMemsetAsync(W.det_rcur, 0, sizeof(uint32_t) * (size_t)L.total_records, st));
+        CK(cudaMemsetAsync(W.det_maxbits, 0, sizeof(unsigned int), st));
+    }
     {
         ss_stage_scope sc(8, st);
         ss_launch_screen_grad_jac(W, L, a, st);
     }
     {
         ss_stage_scope sc(3, st);
+        if (W.det_cap) ss_launch_det_item_offsets(W, L, st);
         ss_launch_raster_bwd(W, L, a, st);
+        if (W.det_cap) {
+            const bool ssg = W.ssg_jac && (a.g.screen_grad_norm || a.g.screen_grad_views);
+            ss_launch_det_record_sums(W, L, (p->cons || a.d_aov) ? 21 : 12, ssg, st);
+            ss_launch_det_env_bound(W, L, st);
+        }
     }
     {
         ss_stage_scope sc(4, st);

@@ -779,7 +779,7 @@ void ss_launch_env_prefilter(const ss_env_desc* d, int n_envs, const float* env,
 }
 
 void ss_launch_env_prefilter_bwd(const ss_env_desc* d, int n_envs, const float* d_irr, const float* d_spec,
-                                 const float* aux, float* d_env, cudaStream_t st) {
+                                 const float* aux, float* d_env, cudaStream_t st, bool ordered) {
     const int We = d->width, He = d->height;
     const int64_t env_stride = (int64_t)We * He * 3;
     const int64_t irr_stride = ss_env_irr_floats(d), spec_stride = ss_env_spec_floats(d),
@@ -794,7 +794,7 @@ void ss_launch_env_prefilter_bwd(const ss_env_desc* d, int n_envs, const float* 
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(g_side_mutex);
-    ss_side* sd = d_spec ? side_streams_locked(dev, st) : nullptr;
+    ss_side* sd = (d_spec && !ordered) ? side_streams_locked(dev, st) : nullptr;
     const bool fork = sd && d->n_levels - 1 <= SS_SIDE_STREAMS && cudaEventRecord(sd->fork, st) == cudaSuccess;
     if (d_spec) {
         int64_t spec_off = env_stride, aux_off = (int64_t)Wi * Hi;

@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(256) ssg_jac_kernel(ss_ws_view ws, ss_fwd_args
 // of the record) are differentiated and summed.
 // The kernel is persistent, like the forward one: warps take (tile, block)
 // items from a queue.
-template <bool AOV, bool SSG, bool CONS, int RWPB_BWD>
+template <bool AOV, bool SSG, bool CONS, bool DET, int RWPB_BWD>
 __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_bwd_args& a, const int gw,
                                                  unsigned char* bwd_smem) {
     constexpr int NV = AOV ? G_N : G_CH + 3;   // gradient values per fragment
@@ -404,6 +404,9 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
     const uint2* clist = ws.cover_list + 8 * beg + (int64_t)warp * (end - beg);
     const uint32_t* alist = ws.cover_adv + 8 * beg + (int64_t)warp * (end - beg);
     const int64_t n_list = ws.cover_count[(int64_t)tile * 8 + warp];
+    // deterministic mode: this item's rows start at det_coff[item] (one per list entry)
+    const int64_t row0 = DET ? (int64_t)ws.det_coff[gw] : 0;
+    int64_t chunk_base = 0;   // list index of the staged chunk's first slot
 
     // Differentiate the fragments of staged slots [sa, sb) at the live pixels
     // (dmask: pixels past their last layer), 32 at a time in list order (one
@@ -519,6 +522,7 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
             }
             // run sums, four columns at a time where no run ends inside them
             float tot = 0.f;
+            int rs = 0;   // first column of the current run
 #pragma unroll
             for (int m = 0; m < 8; ++m) {
                 if (((ends >> (4 * m)) & 15u) == 0u) {   // warp-uniform
@@ -530,10 +534,22 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
                     tot += v[j];
                     if ((ends >> j) & 1u) {   // warp-uniform
                         const int sl = __shfl_sync(0xffffffffu, s, j);
-                        if (lane < NVT && tot != 0.f)   // table row -> record column (the statistic at 21, 22)
-                            atomicAdd(grad + (int64_t)Wc->id[sl] * SS_NGRAD + (lane < NV ? lane : G_SSN + lane - NV),
-                                      tot);
+                        const int colq = lane < NV ? lane : G_SSN + lane - NV;   // table row -> record column
+                        if constexpr (DET) {
+                            // the entry's row: written by its first run, added to by the run that
+                            // continues it at the start of the next batch
+                            const int64_t row = row0 + chunk_base + sl;
+                            const bool cont = rs == 0 && __shfl_sync(0xffffffffu, excl, sl) < b0;
+                            if (row < ws.det_cap) {
+                                float* dst = ws.det_rows + row * SS_NGRAD + colq;
+                                if (lane < NVT) *dst = cont ? *dst + tot : tot;
+                                if (lane == 0 && !cont) ws.det_rid[row] = Wc->id[sl];
+                            }
+                        } else if (lane < NVT && tot != 0.f) {
+                            atomicAdd(grad + (int64_t)Wc->id[sl] * SS_NGRAD + colq, tot);
+                        }
                         tot = 0.f;
+                        rs = j + 1;
                     }
                 }
             }
@@ -547,6 +563,7 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
     for (int64_t base = 0; base < n_list; base += 32) {
         if (__all_sync(0xffffffffu, done)) break;
         const int n = (int)min((int64_t)32, n_list - base);
+        chunk_base = base;
         const uint2 cur = nxt;
         const uint32_t ca = lane < n ? nxa : 0u;   // layer-opening lanes of slot `lane`
         if (SSG && lane < n) {   // the record's densification derivatives into L2 ahead of their use
@@ -594,7 +611,7 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
     }
 }
 
-template <bool AOV, bool SSG, bool CONS, int RWPB_BWD>
+template <bool AOV, bool SSG, bool CONS, bool DET, int RWPB_BWD>
 __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kernel(ss_ws_view ws, ss_bwd_args a,
                                                                                   int n_items) {
     extern __shared__ __align__(16) unsigned char bwd_smem[];
@@ -604,28 +621,37 @@ __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kerne
         if (lane == 0) item = (int)atomicAdd(ws.work + 1, 1u);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
-        raster_bwd_block<AOV, SSG, CONS, RWPB_BWD>(ws, a, item, bwd_smem);
+        raster_bwd_block<AOV, SSG, CONS, DET, RWPB_BWD>(ws, a, item, bwd_smem);
         __syncwarp();
     }
 }
 
-template <bool AOV, bool SSG, bool CONS, int W>
+template <bool AOV, bool SSG, bool CONS, bool DET, int W>
 static void launch_raster_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st) {
     const int smem = W * (int)(sizeof(ss_wstage) + sizeof(ss_bwarp_t<SSG ? G_N + 2 : G_N, CONS ? GT + 3 : GT>));
     static std::atomic<unsigned long long> optin{0}, resident{0};
-    ss_smem_optin(raster_bwd_kernel<AOV, SSG, CONS, W>, smem, optin);
+    ss_smem_optin(raster_bwd_kernel<AOV, SSG, CONS, DET, W>, smem, optin);
     const int n_items = (int)(L.total_tiles * L.bpt);
-    const int ctas = ss_resident_ctas(raster_bwd_kernel<AOV, SSG, CONS, W>, 32 * W, smem, resident);
+    const int ctas = ss_resident_ctas(raster_bwd_kernel<AOV, SSG, CONS, DET, W>, 32 * W, smem, resident);
     const int grid = max(1, min(ctas > 0 ? ctas : 1, (n_items + W - 1) / W));
-    raster_bwd_kernel<AOV, SSG, CONS, W><<<grid, 32 * W, smem, st>>>(ws, a, n_items);
+    raster_bwd_kernel<AOV, SSG, CONS, DET, W><<<grid, 32 * W, smem, st>>>(ws, a, n_items);
 }
 
+template <bool AOV, bool SSG, bool CONS, bool DET>
+static void launch_raster_bwd_w2(int w, const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a,
+                                 cudaStream_t st) {
+    if (w == 2) launch_raster_bwd<AOV, SSG, CONS, DET, 2>(ws, L, a, st);
+    else if (w == 4) launch_raster_bwd<AOV, SSG, CONS, DET, 4>(ws, L, a, st);
+    else launch_raster_bwd<AOV, SSG, CONS, DET, 8>(ws, L, a, st);
+}
+
+// the deterministic mode (fixed-order row sums) is an instance of its own, so
+// that the default one carries none of its code
 template <bool AOV, bool SSG, bool CONS>
 static void launch_raster_bwd_w(int w, const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a,
                                 cudaStream_t st) {
-    if (w == 2) launch_raster_bwd<AOV, SSG, CONS, 2>(ws, L, a, st);
-    else if (w == 4) launch_raster_bwd<AOV, SSG, CONS, 4>(ws, L, a, st);
-    else launch_raster_bwd<AOV, SSG, CONS, 8>(ws, L, a, st);
+    if (ws.det_cap) launch_raster_bwd_w2<AOV, SSG, CONS, true>(w, ws, L, a, st);
+    else launch_raster_bwd_w2<AOV, SSG, CONS, false>(w, ws, L, a, st);
 }
 
 void ss_launch_screen_grad_jac(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st) {
@@ -692,8 +718,38 @@ __device__ __forceinline__ lk3 lookup3(const float* T, const ss_taps& t, int W, 
     }
     return r;
 }
-// bilinear adjoint: g * scale * tap weights added to RGBA accumulators (one
-// 16-byte atomic per tap; accumulators SS_ACC_STRIDE float4 apart)
+// Where the env-texel gradients go: RGBA float accumulators (one 16-byte
+// atomic per tap, accumulators SS_ACC_STRIDE float4 apart), or in the
+// deterministic mode the same memory as 64-bit fixed-point integers (RGB,
+// 2 SS_ACC_STRIDE words apart): a contribution v is added as rint(v 2^k),
+// exact and independent of the order; one beyond 2^lim_bits is flagged.
+struct ss_env_sink {
+    float4* acc;
+    long long* accx;   // deterministic mode (acc is then null)
+    int k;
+    double lim;        // 2^(62 - cbits)
+    int* status;
+};
+__device__ __forceinline__ void scatter4_fx(const ss_env_sink& S, int64_t base, const ss_taps& t, const float g[3],
+                                            float scale) {
+    const float w[4] = {(1.f - t.fx) * (1.f - t.fy) * scale, t.fx * (1.f - t.fy) * scale, (1.f - t.fx) * t.fy * scale,
+                        t.fx * t.fy * scale};
+    const int idx[4] = {t.i00, t.i01, t.i10, t.i11};
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double v = ldexp((double)(w[q] * g[c]), S.k);
+            if (!(fabs(v) < S.lim)) {
+                atomicOr(S.status, SS_ERR_CAPACITY);
+                continue;
+            }
+            const long long iv = llrint(v);
+            if (iv)
+                atomicAdd(reinterpret_cast<unsigned long long*>(S.accx + (base + idx[q]) * (2 * SS_ACC_STRIDE) + c),
+                          (unsigned long long)iv);
+        }
+}
 __device__ __forceinline__ void scatter4(float4* D, const ss_taps& t, const float g[3], float scale) {
     if (scale == 0.f || (g[0] == 0.f && g[1] == 0.f && g[2] == 0.f)) return;
     const float w00 = (1.f - t.fx) * (1.f - t.fy) * scale, w01 = t.fx * (1.f - t.fy) * scale,
@@ -703,6 +759,14 @@ __device__ __forceinline__ void scatter4(float4* D, const ss_taps& t, const floa
     atomicAdd(D + (int64_t)t.i10 * SS_ACC_STRIDE, make_float4(w10 * g[0], w10 * g[1], w10 * g[2], 0.f));
     atomicAdd(D + (int64_t)t.i11 * SS_ACC_STRIDE, make_float4(w11 * g[0], w11 * g[1], w11 * g[2], 0.f));
 }
+// the taps of a map whose first texel is `base` of the scene's accumulators
+__device__ __forceinline__ void scatter_to(const ss_env_sink& S, int64_t base, const ss_taps& t, const float g[3],
+                                           float scale) {
+    if (scale == 0.f || (g[0] == 0.f && g[1] == 0.f && g[2] == 0.f)) return;
+    if (S.accx) scatter4_fx(S, base, t, g, scale);
+    else if (S.acc) scatter4(S.acc + base * SS_ACC_STRIDE, t, g, scale);
+}
+
 // d(u, v)/d(direction) for the equirect map of a unit direction d
 __device__ __forceinline__ void uv_grad(const float d[3], float gu, float gv, float out[3]) {
     const float rxz = fmaxf(d[0] * d[0] + d[2] * d[2], 1e-20f);
@@ -731,14 +795,15 @@ __device__ __forceinline__ void uv_grad(const float d[3], float gu, float gv, fl
 // g = sum over that side's views of dL/dLd: the texel gradients (bilinear
 // adjoint) and the normal column of dL/dR through uv(fs n).
 __device__ __forceinline__ void irr_side_adjoint(const float* irr, int W, int H, const float nrm[3], float fs,
-                                                 const float g[3], float4* acc, float gRn[3]) {
+                                                 const float g[3], const ss_env_sink* sink, int64_t base,
+                                                 float gRn[3]) {
     if (g[0] == 0.f && g[1] == 0.f && g[2] == 0.f) return;
     const float ns[3] = {fs * nrm[0], fs * nrm[1], fs * nrm[2]};
     float un, vn;
     dir_to_uv(ns[0], ns[1], ns[2], un, vn);
     const ss_taps t = bilinear_taps(un, vn, W, H, true);
     const lk3 Ld = lookup3(irr, t, W, H);
-    if (acc) scatter4(acc, t, g, 1.f);
+    if (sink) scatter_to(*sink, base, t, g, 1.f);
     float gun = 0.f, gvn = 0.f;
     for (int k = 0; k < 3; ++k) {
         gun += g[k] * Ld.du[k];
@@ -749,6 +814,7 @@ __device__ __forceinline__ void irr_side_adjoint(const float* irr, int W, int H,
     for (int k = 0; k < 3; ++k) gRn[k] += fs * dnsv[k];
 }
 
+template <bool DET>
 __device__ __forceinline__ void pbwd_surfel(const ss_ws_view& ws, const ss_bwd_args& A, const int64_t i,
                                             const int scene) {
     const ss_layout* L = ws.layout;
@@ -773,6 +839,13 @@ __device__ __forceinline__ void pbwd_surfel(const ss_ws_view& ws, const ss_bwd_a
     const float* irr = a.env.irr + scene * irr_stride;
     const float* spec = a.env.spec + scene * spec_stride;
     const bool d_irr = A.genv.irr != nullptr, d_spec = A.genv.spec != nullptr;
+    // env-texel gradients: float accumulators, or fixed-point integers (deterministic mode)
+    ss_env_sink sink;
+    sink.acc = DET ? nullptr : ws.env_acc;
+    sink.accx = DET ? reinterpret_cast<long long*>(ws.env_acc) : nullptr;
+    sink.k = DET ? ss_det_env_exponent(*ws.det_maxbits, A.det_vmax, A.det_cbits) : 0;
+    sink.lim = DET ? ldexp(1.0, 62 - A.det_cbits) : 0.0;
+    sink.status = ws.status;
     const int lutn = a.p.lut_n;
     const float* LUT = a.env.lut;
     // roughness-only shading quantities: the two specular levels and their blend
@@ -987,9 +1060,9 @@ __device__ __forceinline__ void pbwd_surfel(const ss_ws_view& ws, const ss_bwd_a
             // specular texels into the workspace's RGBA accumulators (irradiance
             // texels first, then the specular stack)
             if (d_spec) {
-                float4* acc = ws.env_acc + (scene * ws.env_texels + (int64_t)IW * IH) * SS_ACC_STRIDE;
-                scatter4(acc + o0 / 3 * SS_ACC_STRIDE, t0, dLs, 1.f - lf);
-                scatter4(acc + o1 / 3 * SS_ACC_STRIDE, t1, dLs, lf);
+                const int64_t sb = scene * ws.env_texels + (int64_t)IW * IH;   // the scene's first specular texel
+                scatter_to(sink, sb + o0 / 3, t0, dLs, 1.f - lf);
+                scatter_to(sink, sb + o1 / 3, t1, dLs, lf);
             }
             // reflected direction: Ls(uv(refl))
             float gur = 0.f, gvr = 0.f;
@@ -1031,9 +1104,9 @@ __device__ __forceinline__ void pbwd_surfel(const ss_ws_view& ws, const ss_bwd_a
     // ---- irradiance: once per side, from the view sums
     {
         float gRn[3] = {0.f, 0.f, 0.f};
-        float4* acc = d_irr ? ws.env_acc + scene * ws.env_texels * SS_ACC_STRIDE : nullptr;
-        irr_side_adjoint(irr, IW, IH, nrm, 1.f, gLdF, acc, gRn);
-        irr_side_adjoint(irr, IW, IH, nrm, -1.f, gLdB, acc, gRn);
+        const ss_env_sink* sk = d_irr ? &sink : nullptr;
+        irr_side_adjoint(irr, IW, IH, nrm, 1.f, gLdF, sk, scene * ws.env_texels, gRn);
+        irr_side_adjoint(irr, IW, IH, nrm, -1.f, gLdB, sk, scene * ws.env_texels, gRn);
         for (int k = 0; k < 3; ++k) gRq[k * 3 + 2] += gRn[k];
     }
     // ---- R(q / |q|) -> q (linear in the summed dL/dR)
@@ -1064,8 +1137,11 @@ __device__ __forceinline__ void pbwd_surfel(const ss_ws_view& ws, const ss_bwd_a
     if (g.metallic) g.metallic[i] += gmetal;
 }
 
-// One CTA per contiguous block of surfels (each thread one surfel at a time).
-__global__ void __launch_bounds__(128, 4) project_bwd_kernel(ss_ws_view ws, ss_bwd_args A, int64_t n_surfels,
+// One CTA per contiguous block of surfels (each thread one surfel at a time);
+// three CTAs per SM leave 170 registers a thread (1.85 -> 1.81 ms against
+// four CTAs at 128 registers, which spilled ~280 bytes a thread).
+template <bool DET>
+__global__ void __launch_bounds__(128, 3) project_bwd_kernel(ss_ws_view ws, ss_bwd_args A, int64_t n_surfels,
                                                             int64_t per_block) {
     const ss_layout* L = ws.layout;
     const int64_t i0 = blockIdx.x * per_block;
@@ -1082,16 +1158,26 @@ __global__ void __launch_bounds__(128, 4) project_bwd_kernel(ss_ws_view ws, ss_b
     };
     const int scene = scene_of(i0);
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x)
-        pbwd_surfel(ws, A, i, i < L->scene_begin[scene + 1] ? scene : scene_of(i));
+        pbwd_surfel<DET>(ws, A, i, i < L->scene_begin[scene + 1] ? scene : scene_of(i));
 }
 
-// Add the RGBA accumulators into the caller's env-map gradients (RGB).
+// Add the RGBA accumulators into the caller's env-map gradients (RGB); in
+// the deterministic mode they hold fixed-point integers of scale 2^k.
 __global__ void env_acc_flush_kernel(const float4* acc, int64_t texels, int64_t irr_tex, int64_t total,
-                                     float* d_irr, float* d_spec) {
+                                     float* d_irr, float* d_spec, const unsigned int* det_maxbits, int vmax,
+                                     int cbits) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= total) return;
     const int64_t sc = i / texels, k = i % texels;
-    const float4 v = acc[i * SS_ACC_STRIDE];
+    float4 v;
+    if (det_maxbits) {
+        const long long* x = reinterpret_cast<const long long*>(acc) + i * (2 * SS_ACC_STRIDE);
+        const int e = -ss_det_env_exponent(*det_maxbits, vmax, cbits);
+        v = make_float4((float)ldexp((double)x[0], e), (float)ldexp((double)x[1], e), (float)ldexp((double)x[2], e),
+                        0.f);
+    } else {
+        v = acc[i * SS_ACC_STRIDE];
+    }
     if (v.x == 0.f && v.y == 0.f && v.z == 0.f) return;
     float* d = k < irr_tex ? (d_irr ? d_irr + (sc * irr_tex + k) * 3 : nullptr)
                            : (d_spec ? d_spec + (sc * (texels - irr_tex) + (k - irr_tex)) * 3 : nullptr);
@@ -1107,11 +1193,13 @@ void ss_launch_project_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bw
     const int64_t per_block = a.f.p.pbwd_block ? a.f.p.pbwd_block : 128;   // surfels per CTA (all their views)
     const unsigned blocks = (unsigned)((n + per_block - 1) / per_block);
     ss_note_launch();
-    project_bwd_kernel<<<blocks, 128, 0, st>>>(ws, a, n, per_block);
+    if (ws.det_cap) project_bwd_kernel<true><<<blocks, 128, 0, st>>>(ws, a, n, per_block);
+    else project_bwd_kernel<false><<<blocks, 128, 0, st>>>(ws, a, n, per_block);
     if ((a.genv.irr || a.genv.spec) && ws.env_acc) {
         const int64_t total = ws.env_texels * L.n_scenes;
         ss_note_launch();
         env_acc_flush_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
-            ws.env_acc, ws.env_texels, (int64_t)a.f.ed.irr_width * a.f.ed.irr_height, total, a.genv.irr, a.genv.spec);
+            ws.env_acc, ws.env_texels, (int64_t)a.f.ed.irr_width * a.f.ed.irr_height, total, a.genv.irr, a.genv.spec,
+            ws.det_cap ? ws.det_maxbits : nullptr, a.det_vmax, a.det_cbits);
     }
 }

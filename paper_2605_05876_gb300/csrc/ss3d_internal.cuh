@@ -17,6 +17,7 @@
 #define SS_ACC_STRIDE 8
 #define SS_NGRAD 24                // floats per (view, surfel) gradient record (21 used, 23 with
                                    // the densification statistic)
+#define SS_GREC_RGB 9              // its first colour column (dL/d rgb, then the AOV channels)
 #define SS_PI_F 3.14159265358979323846f
 
 // ------------------------------------------------------------------------
@@ -85,6 +86,9 @@ struct ss_view_geo {
 // work-queue heads of the persistent rasterisers (uint32: forward, backward)
 // at byte 192 of the same block
 #define SS_WORK_OFFSET 192
+// deterministic backward: the largest |dL/d rgb| of the records (float bits,
+// uint32) at byte 160 of the same block, the bound of the fixed-point scale
+#define SS_DET_OFFSET 160
 struct ss_ws_view {
     int* status;
     unsigned long long* stats;
@@ -123,6 +127,20 @@ struct ss_ws_view {
                             // that g_x = dL/dp_x + sum_k dL/dval_k jac_x[k] (Eq. ss_grad); x then y
     int64_t env_texels;     // irradiance + specular texels per scene
     int64_t max_instances;
+    // deterministic backward (ss_render_params.deterministic): one row of
+    // fragment sums per (warp block, covering staged surfel), then per record
+    // the sum of its rows in row order
+    uint32_t* det_icnt;     // [total_tiles * bpt] covering entries of each (tile, block) item
+    uint32_t* det_coff;     // [items + 1] first row of each item (exclusive prefix sum)
+    float* det_rows;        // [det_cap][SS_NGRAD]
+    uint32_t* det_rid;      // [det_cap] record of each row (0xffffffff: unused)
+    uint32_t* det_rcnt;     // [total_records] rows of each record
+    uint32_t* det_roff;     // [total_records + 1] first list slot of each record
+    uint32_t* det_rcur;     // [total_records] fill cursors
+    uint32_t* det_rlist;    // [det_cap] rows of each record (sorted before the sum)
+    unsigned long long* det_scan;   // block sums of the prefix-sum kernels
+    unsigned int* det_maxbits;      // SS_DET_OFFSET word of the status block
+    int64_t det_cap;        // rows (0: deterministic mode off)
 };
 
 // ------------------------------------------------------------------------
@@ -370,8 +388,10 @@ inline int ss_resident_ctas(K k, int threads, int smem, std::atomic<unsigned lon
 void ss_launch_brdf_lut(float* lut, int n, cudaStream_t st);
 void ss_launch_env_prefilter(const ss_env_desc* d, int n_envs, const float* env, float* irr, float* spec,
                              float* aux, cudaStream_t st);
+// ordered: the level terms one after the other on st (bitwise-reproducible
+// d_env) instead of side by side on forked streams
 void ss_launch_env_prefilter_bwd(const ss_env_desc* d, int n_envs, const float* d_irr, const float* d_spec,
-                                 const float* aux, float* d_env, cudaStream_t st);
+                                 const float* aux, float* d_env, cudaStream_t st, bool ordered = false);
 int64_t ss_env_irr_floats(const ss_env_desc* d);
 int64_t ss_env_spec_floats(const ss_env_desc* d);
 int64_t ss_env_aux_floats(const ss_env_desc* d);
@@ -406,8 +426,38 @@ struct ss_bwd_args {
     const float* d_aov;
     ss_surfel_grads g;
     ss_env_map_grads genv;
+    // deterministic mode: the most views of a scene and log2 of a bound on
+    // the contributions one env texel can receive (ss_det_env_exponent)
+    int det_vmax, det_cbits;
 };
 // the densification statistic's per-record derivatives (nothing unless requested)
 void ss_launch_screen_grad_jac(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st);
 void ss_launch_raster_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st);
 void ss_launch_project_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st);
+
+// deterministic backward (det.cu): the rows' first index per (tile, block)
+// item, before the backward raster; the per-record sums of the rows, after
+// it; the bound of the fixed-point environment scale, before the projection
+// adjoint.  nv: the raster's gradient values per fragment (columns 0..nv-1,
+// plus 21 and 22 with the densification statistic)
+void ss_launch_det_item_offsets(const ss_ws_view& ws, const ss_layout& L, cudaStream_t st);
+void ss_launch_det_record_sums(const ss_ws_view& ws, const ss_layout& L, int nv, bool ssg, cudaStream_t st);
+void ss_launch_det_env_bound(const ss_ws_view& ws, const ss_layout& L, cudaStream_t st);
+int64_t ss_det_scan_blocks(int64_t n);
+
+// Fixed-point scale of the deterministic environment-gradient sums: 2^k
+// with k from the record bound (maxbits: the largest |dL/d rgb| of a
+// record, float bits), the views per scene and the contributions a texel can
+// receive (2^cbits), so that no sum can leave the 63-bit range.  A texel
+// contribution is a bilinear tap weight times dL/dL_s = dL/dc (F0 beta1 +
+// beta2) (one view) or dL/dL_d = sum over the views of dL/dc k_d rho, so with
+// activated attributes in [0, 1] it is at most (views + 1) times the bound;
+// 16 times that again is kept as headroom (a contribution beyond it is
+// flagged, not summed).
+__device__ __forceinline__ int ss_det_env_exponent(unsigned int maxbits, int vmax, int cbits) {
+    const float m = __uint_as_float(maxbits);
+    if (!(m > 0.f) || !(m < 1.0e30f)) return 0;   // no contribution, or a non-finite record (flagged)
+    int e = 0;
+    frexpf(m * (float)(32 * (vmax + 1)), &e);   // 2^e > 32 (vmax + 1) m
+    return 62 - cbits - e;
+}

@@ -32,7 +32,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_struct_sizes_match_header():
     assert ctypes.sizeof(_lib.ss_camera) == 80
-    assert ctypes.sizeof(_lib.ss_render_params) == 96
+    assert ctypes.sizeof(_lib.ss_render_params) == 104
     assert ctypes.sizeof(_lib.ss_surfel_grads) == 64
     assert ctypes.sizeof(_lib.ss_stats) == 72
 
@@ -96,7 +96,8 @@ def test_launch_shape_knobs_are_validated_on_the_host():
     assert lib.ss_workspace_size(ctypes.byref(d), ctypes.byref(p), ctypes.byref(ed), 1, ctypes.byref(nb)) == 0
     for knob, bad, good in (("fwd_warps", 3, 4), ("bwd_warps", 1, 8), ("pbwd_block", 16, 32),
                             ("pbwd_block", 4096, 1024), ("tile_w", 12, 8), ("tile_h", 2, 4),
-                            ("stage_depth", 4, 3), ("mip_mode", 3, 2), ("screen_grad", 2, 1)):
+                            ("stage_depth", 4, 3), ("mip_mode", 3, 2), ("screen_grad", 2, 1),
+                            ("deterministic", 2, 1), ("det_rows", -1, 1 << 20)):
         q = _lib.ss_render_params()
         ctypes.memmove(ctypes.byref(q), ctypes.byref(p), ctypes.sizeof(q))
         setattr(q, knob, bad)
@@ -203,3 +204,37 @@ def test_density_calls_validate_on_the_host():
     after = ctypes.c_int64()
     lib.ss_launch_count(ctypes.byref(after))
     assert after.value == before.value
+
+
+def test_deterministic_mode_sizes_its_rows_on_the_host():
+    """The deterministic backward's rows (one per covering (block, surfel)
+    pair: 96 bytes of sums, a record index and a list slot) are sized by
+    det_rows, or by (blocks per tile) x max_instances when det_rows is 0;
+    the forward-only workspace is unchanged."""
+    lib = _lib.lib()
+    p = _lib.ss_render_params()
+    lib.ss_default_params(ctypes.byref(p))
+    p.max_instances = 1000
+    cams = (_lib.ss_camera * 1)()
+    cams[0].width = cams[0].height = 16
+    cams[0].fx = cams[0].fy = 10.0
+    off = (ctypes.c_int64 * 2)(0, 10)
+    d = _lib.ss_batch_desc(1, 1, off, cams, None)
+    ed = _lib.ss_env_desc(64, 32, 6, 32, 16)
+
+    def size(with_bwd, **kw):
+        q = _lib.ss_render_params()
+        ctypes.memmove(ctypes.byref(q), ctypes.byref(p), ctypes.sizeof(q))
+        for k, v in kw.items():
+            setattr(q, k, v)
+        nb = ctypes.c_size_t()
+        assert lib.ss_workspace_size(ctypes.byref(d), ctypes.byref(q), ctypes.byref(ed), with_bwd,
+                                     ctypes.byref(nb)) == 0
+        return nb.value
+
+    base = size(1)
+    assert size(0, deterministic=1) == size(0)
+    r1, r2 = size(1, deterministic=1, det_rows=10000), size(1, deterministic=1, det_rows=20000)
+    assert r2 - r1 >= 10000 * 104 - 1024 and r2 - r1 <= 10000 * 104 + 1024
+    # det_rows 0: (16 / 8) x (16 / 4) = 8 blocks per tile times max_instances
+    assert size(1, deterministic=1) == size(1, deterministic=1, det_rows=8 * 1000) > base
