@@ -95,6 +95,10 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--no-screen-grad", action="store_true", help="skip timing the densification statistic")
     ap.add_argument("--no-det", action="store_true", help="skip timing the deterministic backward")
+    ap.add_argument("--dense-layers", type=int, default=0,
+                    help="headline step: layers per pixel in dense planes, deeper ones in a pool sized by the "
+                         "work (0: all k_max layers dense)")
+    ap.add_argument("--no-layer-pool", action="store_true", help="skip timing the step with pooled layer state")
     return ap.parse_args()
 
 
@@ -497,6 +501,12 @@ def run_ours(args):
     tuned = None
     if not args.no_autotune:
         tuned = {k: v[0] for k, v in r.autotune(d_rgba, d_aov).items()}
+    # layer state sized by the work: dense planes for the first layers, a pool for the rest
+    layers_cfg = {"dense_layers": "all", "workspace_bytes": int(r.ws_bytes)}
+    if args.dense_layers > 0:
+        pool, wsb = r.compact_layers(args.dense_layers)
+        layers_cfg = {"dense_layers": args.dense_layers, "layer_pool": pool, "workspace_bytes": int(wsb),
+                      "workspace_bytes_all_dense": layers_cfg["workspace_bytes"]}
 
     for _ in range(args.warmup):
         step()
@@ -627,6 +637,32 @@ def run_ours(args):
         del rd
         torch.cuda.empty_cache()
 
+    # --- the same step with the layer state sized by the work (2 dense layers + a pool)
+    layer_pool = None
+    if not args.no_layer_pool and args.dense_layers == 0:
+        rp = Renderer(scene, share_from=r)
+        for k in KNOBS:
+            setattr(rp.prm, k, getattr(r.prm, k))
+        rp.plan_capacity()
+        pool, wsb = rp.compact_layers(2)
+        rp.zero_grads()
+
+        def step_pool():
+            rp.prefilter_env()
+            rp.forward()
+            rp.zero_grads()
+            rp.backward(d_rgba, d_aov)
+        for _ in range(args.warmup):
+            step_pool()
+        ms_p = timed(step_pool, args.steps)
+        if rp.read_status() != 0:
+            raise RuntimeError(f"device status {rp.read_status()} in the pooled-layer step")
+        layer_pool = {"value": job_rate(V, args.steps, world, ms_p), "unit": "views/s", "ms_per_step": ms_p / args.steps,
+                      "dense_layers": 2, "layer_pool": pool, "pool_layers_used": rp.stats()["pool_layers"],
+                      "workspace_bytes": int(wsb), "workspace_bytes_all_dense": int(r.ws_bytes)}
+        del rp
+        torch.cuda.empty_cache()
+
     # --- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
@@ -702,8 +738,8 @@ def run_ours(args):
                 "config": {"workload": describe(scene, args.config) + ", batched in one launch per stage",
                            "inputs_vs_l2": "inputs and intermediates > 129 MB L2 (no flush)",
                            "parallelism": "replicas" if world > 1 else "single GPU",
-                           "launch_shapes": tuned or "defaults"},
-                "per_view": per_view, "graph": graph, "screen_grad": screen_grad, "deterministic": deterministic, "density": density, "e2e": e2e,
+                           "launch_shapes": tuned or "defaults", "layer_state": layers_cfg},
+                "per_view": per_view, "graph": graph, "screen_grad": screen_grad, "deterministic": deterministic, "layer_pool": layer_pool, "density": density, "e2e": e2e,
                 "roofline": roofline, "hbm": hbm_line,
                 "cpu_baseline": cpu,
                 "clocks": clocks,

@@ -176,6 +176,14 @@ typedef struct ss_render_params {
                                 (ss_stats.staged_covering of the forward); 0 = the bound of
                                 (blocks per tile) x max_instances.  More pairs than rows set
                                 SS_ERR_CAPACITY (the gradients are then incomplete) */
+    /* layer state kept by the forward for the backward (with_backward workspaces) */
+    int32_t dense_layers;    /* layers per pixel held in planes of every pixel (0 = k_max: all of
+                                them, no pool); the layers past it go to layer_pool */
+    int32_t pad_;
+    int64_t layer_pool;      /* dense_layers < k_max: slots for the (pixel, layer) pairs past
+                                dense_layers, 64 bytes each (80 with cons); ss_stats.pool_layers
+                                of a forward is the number it needed.  More pairs than slots
+                                set SS_ERR_CAPACITY (the backward then drops those layers' terms) */
 } ss_render_params;
 
 /* Work counters of the last forward/backward pair (collect_stats = 1). */
@@ -189,6 +197,9 @@ typedef struct ss_stats {
     int64_t staged;          /* (warp block, surfel) pairs the forward raster staged */
     int64_t staged_covering; /* ... of which cover at least one pixel of the block */
     int64_t bwd_batches;     /* groups of up to 32 fragments the backward raster differentiated together */
+    int64_t pool_layers;     /* (pixel, layer) pairs past dense_layers that the forward stored in
+                                layer_pool slots (counted whether or not collect_stats is set, and
+                                beyond the capacity, so it sizes layer_pool) */
 } ss_stats;
 
 /* Stage timing: CUDA events recorded on the launching stream around each

@@ -212,6 +212,20 @@ class Renderer:
     TUNE_SPACE = {"tile": ((16, 16), (16, 8), (32, 8), (8, 16), (8, 8)), "stage_depth": (1, 2, 3),
                   "fwd_warps": (1, 2, 4), "bwd_warps": (2, 4, 8), "pbwd_block": (64, 128, 256)}
 
+    def compact_layers(self, dense: int = 2, slack: float = 1.25):
+        """Keep `dense` layers per pixel in planes of every pixel and the
+        deeper ones in a pool sized by this batch's work: one forward with
+        an empty pool counts the (pixel, layer) pairs past `dense`
+        (ss_stats.pool_layers), then the pool is sized with `slack` and the
+        workspace planned again.  Returns (pool slots, workspace bytes)."""
+        self.prm.dense_layers, self.prm.layer_pool = int(dense), 0
+        self.plan_capacity(self.prm.max_instances)
+        self.forward()
+        need = self.stats()["pool_layers"]
+        self.prm.layer_pool = int(math.ceil(need * slack)) + 1024
+        self.plan_capacity(self.prm.max_instances)
+        return self.prm.layer_pool, self.ws_bytes
+
     def set_tile(self, tile):
         """Change the screen tile (width, height); the instance capacity and
         the workspace are planned again for it."""

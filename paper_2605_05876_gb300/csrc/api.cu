@@ -109,6 +109,8 @@ static ss_status check_knobs(const ss_render_params* p) {
     if (p->stage_depth < 0 || p->stage_depth > 3) return SS_ERR_INVALID_ARG;
     if (p->deterministic != 0 && p->deterministic != 1) return SS_ERR_INVALID_ARG;
     if (p->det_rows < 0 || p->det_rows > 0xffffffffll) return SS_ERR_INVALID_ARG;
+    if (p->dense_layers < 0 || p->dense_layers > p->k_max) return SS_ERR_INVALID_ARG;
+    if (p->layer_pool < 0 || p->layer_pool > 0xffffffffll) return SS_ERR_INVALID_ARG;
     return SS_OK;
 }
 
@@ -200,13 +202,16 @@ static ss_status build_layout(const ss_batch_desc* b, const ss_render_params* p,
 }
 
 struct ws_plan {
-    size_t status, layout, vgeo, rec, rank, rbm, tc, ts, tcur, keys, keys_alt, bmask, cand, layer, pix, grad, masks,
+    size_t status, layout, vgeo, rec, rank, rbm, tc, ts, tcur, keys, keys_alt, bmask, cand, layer, pool, pix, grad, masks,
         madv, mcount, env_acc, jac, total;
     int64_t env_texels;   // irradiance + specular texels of one scene (0: no env-gradient scratch)
     // deterministic backward
     size_t d_icnt, d_coff, d_rows, d_rid, d_rcnt, d_roff, d_rcur, d_rlist, d_scan;
     int64_t det_cap;
 };
+
+// layers per pixel in the dense planes (dense_layers; 0 = all k_max)
+static int dense_layers(const ss_render_params& p) { return p.dense_layers > 0 ? p.dense_layers : p.k_max; }
 
 // rows of the deterministic backward: det_rows, or (blocks per tile) x max_instances
 static int64_t det_capacity(const ss_layout& L, const ss_render_params& p) {
@@ -238,8 +243,9 @@ static ws_plan plan_ws(const ss_layout& L, const ss_render_params& p, int with_b
     w.bmask = take(sizeof(uint8_t) * (size_t)p.max_instances);
     w.cand = take(sizeof(uint32_t) * 8 * (size_t)p.max_instances);
     if (with_bwd) {
-        w.layer = take(sizeof(float) * (size_t)p.k_max * (p.cons ? 16 : 13) * (size_t)L.total_pixels);
-        w.pix = take(sizeof(float) * 2 * (size_t)L.total_pixels);
+        w.layer = take(sizeof(float) * (size_t)dense_layers(p) * (p.cons ? 16 : 13) * (size_t)L.total_pixels);
+        w.pool = dense_layers(p) < p.k_max ? take(sizeof(float) * (p.cons ? 20 : 16) * (size_t)p.layer_pool) : 0;
+        w.pix = take(sizeof(float) * 3 * (size_t)L.total_pixels);
         w.grad = take(sizeof(float) * SS_NGRAD * (size_t)L.total_records);
         w.masks = take(sizeof(uint2) * 8 * (size_t)p.max_instances);
         w.madv = take(sizeof(uint32_t) * 8 * (size_t)p.max_instances);
@@ -247,7 +253,7 @@ static ws_plan plan_ws(const ss_layout& L, const ss_render_params& p, int with_b
         w.env_acc = take(sizeof(float4) * SS_ACC_STRIDE * (size_t)w.env_texels * (size_t)L.n_scenes);
         w.jac = p.screen_grad ? take(sizeof(float4) * 4 * (size_t)L.total_records) : 0;
     } else {
-        w.layer = w.pix = w.grad = w.masks = w.madv = w.mcount = w.env_acc = w.jac = 0;
+        w.layer = w.pool = w.pix = w.grad = w.masks = w.madv = w.mcount = w.env_acc = w.jac = 0;
     }
     w.det_cap = with_bwd ? det_capacity(L, p) : 0;
     if (w.det_cap) {
@@ -289,6 +295,10 @@ static ss_ws_view carve(void* ws, const ws_plan& w, const ss_render_params& p, i
     v.cand_list = (uint32_t*)(b + w.cand);
     v.layer_state = with_bwd ? (float*)(b + w.layer) : nullptr;
     v.ls_rows = p.cons ? 16 : 13;
+    v.dense_layers = dense_layers(p);
+    v.pool_stride = p.cons ? 20 : 16;
+    v.pool_cap = (with_bwd && v.dense_layers < p.k_max) ? p.layer_pool : 0;
+    v.layer_pool = (with_bwd && w.pool) ? (float*)(b + w.pool) : nullptr;
     v.pix_state = with_bwd ? (float*)(b + w.pix) : nullptr;
     v.grad_rec = with_bwd ? (float*)(b + w.grad) : nullptr;
     v.cover_list = with_bwd ? (uint2*)(b + w.masks) : nullptr;

@@ -107,7 +107,6 @@ __global__ void __launch_bounds__(256) layer_coeff_kernel(ss_ws_view ws, ss_bwd_
     if (gpix >= P) return;
     const int K = __float_as_int(ws.pix_state[gpix]);
     if (K <= 0) return;
-    const int lsr = ws.ls_rows;
     const float kw = a.f.p.gamma * (0.5f / SS_PI_F);
     const float Tend = ws.pix_state[P + gpix];
     float g[SS_NCH], rem[SS_NCH];   // rem_c = out_c - sum_{j<=k} T_j alpha_j C_hat_j
@@ -124,30 +123,39 @@ __global__ void __launch_bounds__(256) layer_coeff_kernel(ss_ws_view ws, ss_bwd_
     // consolidation: upstream gradient and the totals of two pre-passes
     const float gC = CONS ? a.d_aov[SS_N_AOV * P + gpix] : 0.f;
     float Wt = 0.f, WZt = 0.f, Et = 0.f;
-    auto cons_layer = [&](int kk, float Tk, float& wk, float& zk, float& var, float& alk, float& ek_e) {
-        const float* ls = ws.layer_state + (int64_t)kk * lsr * P + gpix;
-        const float W = ls[12 * P], iW = 1.f / W;
-        zk = ls[11 * P] * iW;
-        const float mdz = ls[13 * P] * iW;
-        var = fmaf(ls[14 * P], iW, -mdz * mdz);
+    auto cons_layer = [&](int kk, uint32_t& slot, float Tk, float& wk, float& zk, float& var, float& alk,
+                          float& ek_e) {
+        int64_t rs;
+        const float* ls = ss_layer_rows(ws, P, gpix, kk, slot, rs);
+        if (!ls) {   // a layer the forward could not store (pool capacity): no term
+            wk = zk = var = alk = 0.f;
+            ek_e = 1.f;
+            return;
+        }
+        const float W = ls[12 * rs], iW = 1.f / W;
+        zk = ls[11 * rs] * iW;
+        const float mdz = ls[13 * rs] * iW;
+        var = fmaf(ls[14 * rs], iW, -mdz * mdz);
         ek_e = expf(-kw * W);
         alk = -expm1f(-kw * W);
         wk = Tk * alk;
     };
     if (CONS && gC != 0.f) {
         float Tk = 1.f;
+        uint32_t slot = SS_NO_SLOT;
         for (int kk = 0; kk < K; ++kk) {
             float wk, zk, var, al, e;
-            cons_layer(kk, Tk, wk, zk, var, al, e);
+            cons_layer(kk, slot, Tk, wk, zk, var, al, e);
             Wt += wk;
             WZt = fmaf(wk, zk, WZt);
             Tk *= e;
         }
         Tk = 1.f;
+        slot = SS_NO_SLOT;
         float Sb = 0.f, Mb = 0.f;
         for (int kk = 0; kk < K; ++kk) {
             float wk, zk, var, al, e;
-            cons_layer(kk, Tk, wk, zk, var, al, e);
+            cons_layer(kk, slot, Tk, wk, zk, var, al, e);
             const float Sa = Wt - Sb - wk, Ma = WZt - Mb - wk * zk;
             const float ek = fmaf(zk, Sb - Sa, Ma - Mb) + 2.f * wk * var;
             Et = fmaf(ek, wk, Et);
@@ -158,12 +166,15 @@ __global__ void __launch_bounds__(256) layer_coeff_kernel(ss_ws_view ws, ss_bwd_
     }
     float Tb = 1.f;
     float Sb = 0.f, Mb = 0.f, Pew = 0.f;   // consolidation: running sums over the layers in front
+    uint32_t slot = SS_NO_SLOT;
     for (int kk = 0; kk < K; ++kk) {
-        float* ls = ws.layer_state + (int64_t)kk * lsr * P + gpix;
+        int64_t rs;
+        float* ls = ss_layer_rows(ws, P, gpix, kk, slot, rs);
+        if (!ls) break;   // the forward ran out of pool slots (SS_ERR_CAPACITY): no deeper terms
         float C[SS_NCH];
 #pragma unroll
-        for (int c = 0; c < SS_NCH; ++c) C[c] = ls[c * P];
-        const float W = ls[12 * P];
+        for (int c = 0; c < SS_NCH; ++c) C[c] = ls[c * rs];
+        const float W = ls[12 * rs];
         const float invW = 1.f / W;
         float hat[SS_NCH];
 #pragma unroll
@@ -200,7 +211,7 @@ __global__ void __launch_bounds__(256) layer_coeff_kernel(ss_ws_view ws, ss_bwd_
             float gDz = 0.f, gDz2 = 0.f;
             if (gC != 0.f) {
                 const float wk = tw, zk = hat[11];
-                const float Dz = ls[13 * P], Dz2 = ls[14 * P];
+                const float Dz = ls[13 * rs], Dz2 = ls[14 * rs];
                 const float mdz = Dz * invW, var = fmaf(Dz2, invW, -mdz * mdz);
                 const float Sa = Wt - Sb - wk, Ma = WZt - Mb - wk * zk;
                 const float ek = fmaf(zk, Sb - Sa, Ma - Mb) + 2.f * wk * var;
@@ -216,12 +227,12 @@ __global__ void __launch_bounds__(256) layer_coeff_kernel(ss_ws_view ws, ss_bwd_
                 Sb += wk;
                 Mb = fmaf(wk, zk, Mb);
             }
-            ls[13 * P] = gDz;
-            ls[14 * P] = gDz2;
+            ls[13 * rs] = gDz;
+            ls[14 * rs] = gDz2;
         }
 #pragma unroll
-        for (int c = 0; c < SS_NCH; ++c) ls[c * P] = G[c];
-        ls[12 * P] = S;
+        for (int c = 0; c < SS_NCH; ++c) ls[c * rs] = G[c];
+        ls[12 * rs] = S;
         Tb *= e;
     }
 }
@@ -346,7 +357,7 @@ __global__ void __launch_bounds__(256) ssg_jac_kernel(ss_ws_view ws, ss_fwd_args
 // of the record) are differentiated and summed.
 // The kernel is persistent, like the forward one: warps take (tile, block)
 // items from a queue.
-template <bool AOV, bool SSG, bool CONS, bool DET, int RWPB_BWD>
+template <bool AOV, bool SSG, bool CONS, bool DET, bool POOL, int RWPB_BWD>
 __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_bwd_args& a, const int gw,
                                                  unsigned char* bwd_smem) {
     constexpr int NV = AOV ? G_N : G_CH + 3;   // gradient values per fragment
@@ -354,7 +365,6 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
     constexpr int NC = AOV ? SS_NCH : 3;       // channels with a coefficient
     constexpr int GTR = CONS ? GT + 3 : GT;    // layer coefficients per lane (+ dL/dDz, dL/dDz2, z_r)
     using bwarp = ss_bwarp_t<SSG ? G_N + 2 : G_N, GTR>;
-    const int lsr = ws.ls_rows;
     ss_wstage* Wst = reinterpret_cast<ss_wstage*>(bwd_smem);
     bwarp* Bws = reinterpret_cast<bwarp*>(bwd_smem + RWPB_BWD * sizeof(ss_wstage));
     const ss_layout* L = ws.layout;
@@ -387,10 +397,18 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
     // the replay only counts them
     int k = 0;
 
-    auto enter_layer = [&](int kk) {   // this lane's layer coefficients -> B.gtab
-        const float* ls = ws.layer_state + (int64_t)kk * lsr * P + gpix;
+    uint32_t slot = SS_NO_SLOT;   // pool slot of the current layer (layers past dense_layers)
+    auto enter_layer = [&](int kk) {   // this lane's layer coefficients -> B.gtab (layers entered in order)
+        if (!POOL || kk < ws.dense_layers) {
+            const float* ls = ws.layer_state + (int64_t)kk * ws.ls_rows * P + gpix;
 #pragma unroll
-        for (int c = 0; c < GTR; ++c) B.gtab[lane * GTR + c] = ls[c * P];
+            for (int c = 0; c < GTR; ++c) B.gtab[lane * GTR + c] = ls[c * P];
+        } else {
+            int64_t rs;
+            const float* ls = ss_layer_rows(ws, P, gpix, kk, slot, rs);
+#pragma unroll
+            for (int c = 0; c < GTR; ++c) B.gtab[lane * GTR + c] = ls ? ls[c] : 0.f;
+        }
     };
     if (!done) enter_layer(0);
 
@@ -611,7 +629,7 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
     }
 }
 
-template <bool AOV, bool SSG, bool CONS, bool DET, int RWPB_BWD>
+template <bool AOV, bool SSG, bool CONS, bool DET, bool POOL, int RWPB_BWD>
 __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kernel(ss_ws_view ws, ss_bwd_args a,
                                                                                   int n_items) {
     extern __shared__ __align__(16) unsigned char bwd_smem[];
@@ -621,32 +639,39 @@ __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kerne
         if (lane == 0) item = (int)atomicAdd(ws.work + 1, 1u);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
-        raster_bwd_block<AOV, SSG, CONS, DET, RWPB_BWD>(ws, a, item, bwd_smem);
+        raster_bwd_block<AOV, SSG, CONS, DET, POOL, RWPB_BWD>(ws, a, item, bwd_smem);
         __syncwarp();
     }
 }
 
-template <bool AOV, bool SSG, bool CONS, bool DET, int W>
+template <bool AOV, bool SSG, bool CONS, bool DET, bool POOL, int W>
 static void launch_raster_bwd(const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a, cudaStream_t st) {
     const int smem = W * (int)(sizeof(ss_wstage) + sizeof(ss_bwarp_t<SSG ? G_N + 2 : G_N, CONS ? GT + 3 : GT>));
     static std::atomic<unsigned long long> optin{0}, resident{0};
-    ss_smem_optin(raster_bwd_kernel<AOV, SSG, CONS, DET, W>, smem, optin);
+    ss_smem_optin(raster_bwd_kernel<AOV, SSG, CONS, DET, POOL, W>, smem, optin);
     const int n_items = (int)(L.total_tiles * L.bpt);
-    const int ctas = ss_resident_ctas(raster_bwd_kernel<AOV, SSG, CONS, DET, W>, 32 * W, smem, resident);
+    const int ctas = ss_resident_ctas(raster_bwd_kernel<AOV, SSG, CONS, DET, POOL, W>, 32 * W, smem, resident);
     const int grid = max(1, min(ctas > 0 ? ctas : 1, (n_items + W - 1) / W));
-    raster_bwd_kernel<AOV, SSG, CONS, DET, W><<<grid, 32 * W, smem, st>>>(ws, a, n_items);
+    raster_bwd_kernel<AOV, SSG, CONS, DET, POOL, W><<<grid, 32 * W, smem, st>>>(ws, a, n_items);
+}
+
+template <bool AOV, bool SSG, bool CONS, bool DET, bool POOL>
+static void launch_raster_bwd_w3(int w, const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a,
+                                 cudaStream_t st) {
+    if (w == 2) launch_raster_bwd<AOV, SSG, CONS, DET, POOL, 2>(ws, L, a, st);
+    else if (w == 4) launch_raster_bwd<AOV, SSG, CONS, DET, POOL, 4>(ws, L, a, st);
+    else launch_raster_bwd<AOV, SSG, CONS, DET, POOL, 8>(ws, L, a, st);
 }
 
 template <bool AOV, bool SSG, bool CONS, bool DET>
 static void launch_raster_bwd_w2(int w, const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a,
                                  cudaStream_t st) {
-    if (w == 2) launch_raster_bwd<AOV, SSG, CONS, DET, 2>(ws, L, a, st);
-    else if (w == 4) launch_raster_bwd<AOV, SSG, CONS, DET, 4>(ws, L, a, st);
-    else launch_raster_bwd<AOV, SSG, CONS, DET, 8>(ws, L, a, st);
+    if (ws.dense_layers < a.f.p.k_max) launch_raster_bwd_w3<AOV, SSG, CONS, DET, true>(w, ws, L, a, st);
+    else launch_raster_bwd_w3<AOV, SSG, CONS, DET, false>(w, ws, L, a, st);
 }
 
-// the deterministic mode (fixed-order row sums) is an instance of its own, so
-// that the default one carries none of its code
+// the deterministic mode (fixed-order row sums) and the pooled layer state
+// are instances of their own, so that the default one carries none of their code
 template <bool AOV, bool SSG, bool CONS>
 static void launch_raster_bwd_w(int w, const ss_ws_view& ws, const ss_layout& L, const ss_bwd_args& a,
                                 cudaStream_t st) {

@@ -642,7 +642,9 @@ void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_a
 // as many warps as fit on the device take (tile, block) items from a queue
 // in item order, so no warp slot idles while items are left.
 
-template <bool STATS, bool PP, bool CONS, int RWPB_FWD>
+// POOL: layers past dense_layers go to pool slots (an instance of its own, so
+// that the all-dense one carries none of that code)
+template <bool STATS, bool PP, bool CONS, bool POOL, int RWPB_FWD>
 __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_fwd_args& a, const int gw,
                                                  unsigned char* fwd_smem) {
     ss_wstage* Wst = reinterpret_cast<ss_wstage*>(fwd_smem);   // [RWPB_FWD warps][stage depth]
@@ -684,6 +686,8 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
     // = sum_j w_j (z_j S_j - M_j) with S_j, M_j those sums over i < j.
     float zr = 0.f, Dz = 0.f, Dz2 = 0.f, Sb = 0.f, Mb = 0.f, Lp = 0.f;
     const int lsr = ws.ls_rows;
+    // layers past dense_layers: the pixel's first pool slot and the last one taken
+    uint32_t first_slot = SS_NO_SLOT, last_slot = SS_NO_SLOT;
 
     auto flush = [&]() {
         const float invW = 1.f / Wg;
@@ -706,14 +710,37 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
             Mb = fmaf(tw, zk, Mb);
         }
         if (a.with_backward) {
-            float* ls = ws.layer_state + (int64_t)K * lsr * P + gpix;
+            if (!POOL || K < ws.dense_layers) {   // the dense planes (every pixel has a place)
+                float* ls = ws.layer_state + (int64_t)K * lsr * P + gpix;
 #pragma unroll
-            for (int c = 0; c < SS_NCH; ++c) ls[c * P] = C[c];
-            ls[12 * P] = Wg;
-            if (CONS) {
-                ls[13 * P] = Dz;
-                ls[14 * P] = Dz2;
-                ls[15 * P] = zr;
+                for (int c = 0; c < SS_NCH; ++c) ls[c * P] = C[c];
+                ls[12 * P] = Wg;
+                if (CONS) {
+                    ls[13 * P] = Dz;
+                    ls[14 * P] = Dz2;
+                    ls[15 * P] = zr;
+                }
+            } else {   // a pool slot, linked from the previous layer's slot or the pixel's first-slot word
+                const unsigned long long t = atomicAdd(ws.stats + 9, 1ull);   // (ss_stats.pool_layers)
+                const uint32_t slot = t < (unsigned long long)ws.pool_cap ? (uint32_t)t : SS_NO_SLOT;
+                if (slot == SS_NO_SLOT) atomicOr(ws.status, SS_ERR_CAPACITY);
+                if (K == ws.dense_layers) first_slot = slot;
+                else if (last_slot != SS_NO_SLOT)
+                    ws.layer_pool[(int64_t)last_slot * ws.pool_stride + lsr] = __uint_as_float(slot);
+                last_slot = slot;
+                if (slot != SS_NO_SLOT) {
+                    float4* q = reinterpret_cast<float4*>(ws.layer_pool + (int64_t)slot * ws.pool_stride);
+                    const float nx = __uint_as_float(SS_NO_SLOT);   // the chain ends here until a next layer
+                    q[0] = make_float4(C[0], C[1], C[2], C[3]);
+                    q[1] = make_float4(C[4], C[5], C[6], C[7]);
+                    q[2] = make_float4(C[8], C[9], C[10], C[11]);
+                    if (CONS) {
+                        q[3] = make_float4(Wg, Dz, Dz2, zr);
+                        q[4] = make_float4(nx, 0.f, 0.f, 0.f);
+                    } else {
+                        q[3] = make_float4(Wg, nx, 0.f, 0.f);
+                    }
+                }
             }
         }
         Acov = fmaf(Tb, al, Acov);
@@ -892,12 +919,13 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
     if (a.with_backward) {
         ws.pix_state[gpix] = __int_as_float(K);
         ws.pix_state[P + gpix] = Tb;
+        ws.pix_state[2 * P + gpix] = __uint_as_float(first_slot);
     }
 }
 
 // 28 warps per SM (at most 72 registers a thread): more resident warps hide
 // more of the staging and shared-memory latency (6.52 -> 6.39 ms against 24)
-template <bool STATS, bool PP, bool CONS, int RWPB_FWD>
+template <bool STATS, bool PP, bool CONS, bool POOL, int RWPB_FWD>
 __global__ void __launch_bounds__(32 * RWPB_FWD, 28 / RWPB_FWD) raster_fwd_kernel(ss_ws_view ws, ss_fwd_args a,
                                                                                   int n_items) {
     extern __shared__ __align__(16) unsigned char fwd_smem[];
@@ -907,30 +935,37 @@ __global__ void __launch_bounds__(32 * RWPB_FWD, 28 / RWPB_FWD) raster_fwd_kerne
         if (lane == 0) item = (int)atomicAdd(ws.work + 0, 1u);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
-        raster_fwd_block<STATS, PP, CONS, RWPB_FWD>(ws, a, item, fwd_smem);
+        raster_fwd_block<STATS, PP, CONS, POOL, RWPB_FWD>(ws, a, item, fwd_smem);
         __syncwarp();
     }
 }
 
-template <bool STATS, bool PP, bool CONS, int W>
+template <bool STATS, bool PP, bool CONS, bool POOL, int W>
 static void launch_raster_fwd(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st) {
     const int D = a.p.stage_depth ? a.p.stage_depth : 2;
     const int smem = D * W * (int)sizeof(ss_wstage);
     // opt in once for the deepest ring; resident CTAs depend on the depth
     static std::atomic<unsigned long long> optin{0}, resident[4];
-    ss_smem_optin(raster_fwd_kernel<STATS, PP, CONS, W>, 3 * W * (int)sizeof(ss_wstage), optin);
+    ss_smem_optin(raster_fwd_kernel<STATS, PP, CONS, POOL, W>, 3 * W * (int)sizeof(ss_wstage), optin);
     const int n_items = (int)(L.total_tiles * L.bpt);
-    const int ctas = ss_resident_ctas(raster_fwd_kernel<STATS, PP, CONS, W>, 32 * W, smem, resident[D]);
+    const int ctas = ss_resident_ctas(raster_fwd_kernel<STATS, PP, CONS, POOL, W>, 32 * W, smem, resident[D]);
     const int grid = max(1, min(ctas > 0 ? ctas : 1, (n_items + W - 1) / W));
-    raster_fwd_kernel<STATS, PP, CONS, W><<<grid, 32 * W, smem, st>>>(ws, a, n_items);
+    raster_fwd_kernel<STATS, PP, CONS, POOL, W><<<grid, 32 * W, smem, st>>>(ws, a, n_items);
+}
+
+template <bool STATS, bool PP, bool CONS, bool POOL>
+static void launch_raster_fwd_w2(int w, const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a,
+                                 cudaStream_t st) {
+    if (w == 1) launch_raster_fwd<STATS, PP, CONS, POOL, 1>(ws, L, a, st);
+    else if (w == 2) launch_raster_fwd<STATS, PP, CONS, POOL, 2>(ws, L, a, st);
+    else launch_raster_fwd<STATS, PP, CONS, POOL, 4>(ws, L, a, st);
 }
 
 template <bool STATS, bool PP, bool CONS>
 static void launch_raster_fwd_w(int w, const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a,
                                 cudaStream_t st) {
-    if (w == 1) launch_raster_fwd<STATS, PP, CONS, 1>(ws, L, a, st);
-    else if (w == 2) launch_raster_fwd<STATS, PP, CONS, 2>(ws, L, a, st);
-    else launch_raster_fwd<STATS, PP, CONS, 4>(ws, L, a, st);
+    if (a.with_backward && ws.dense_layers < a.p.k_max) launch_raster_fwd_w2<STATS, PP, CONS, true>(w, ws, L, a, st);
+    else launch_raster_fwd_w2<STATS, PP, CONS, false>(w, ws, L, a, st);
 }
 
 template <bool STATS>

@@ -81,7 +81,8 @@ struct ss_view_geo {
 };
 
 // device status bits live in the first word of the workspace; the work
-// counters (ss_stats, int64 x 8) at byte 64 of the same 256-byte block
+// counters (ss_stats, int64 x 10) at byte 64 of the same 256-byte block (the
+// last, the layer-pool slots taken, is the pool's allocation counter)
 #define SS_STATS_OFFSET 64
 // work-queue heads of the persistent rasterisers (uint32: forward, backward)
 // at byte 192 of the same block
@@ -109,10 +110,15 @@ struct ss_ws_view {
                             // centre of 8 x 4 block b of its tile (support rectangle overlaps the block and
                             // the exact support's minimum over the block's pixel centres is below the cutoff)
     uint32_t* cand_list;    // [8 x max_instances] per (tile, block): records whose rectangle meets the block
-    float* layer_state;     // [k_max][ls_rows][total_pixels]: raw C (12), W; with the depth-consolidation
+    float* layer_state;     // [dense_layers][ls_rows][total_pixels]: raw C (12), W; with the depth-consolidation
                             // term also (sum w (z - z_r), sum w (z - z_r)^2, z_r), z_r the layer's first depth
     int32_t ls_rows;        // 13, or 16 with the depth-consolidation term
-    float* pix_state;       // [2][total_pixels]  (K as float bits, T_end)
+    int32_t dense_layers;   // layers per pixel in the dense planes (k_max: no pool)
+    float* layer_pool;      // [pool_cap][pool_stride]: the layers past dense_layers, one slot each (ls_rows
+                            // values, then the next layer's slot as uint32 bits; 0xffffffff: none)
+    int32_t pool_stride;    // 16 floats, or 20 with the depth-consolidation term (16-byte aligned slots)
+    int64_t pool_cap;       // slots (0: no pool)
+    float* pix_state;       // [3][total_pixels]  (K as float bits, T_end, first pool slot as uint32 bits)
     float* grad_rec;        // [total_records][SS_NGRAD]
     uint2* cover_list;      // [8 * max_instances]: per warp, (record, 32-pixel coverage word) of every staged
                             // surfel that covers a pixel of the warp's block, in list order (forward -> backward)
@@ -142,6 +148,24 @@ struct ss_ws_view {
     unsigned int* det_maxbits;      // SS_DET_OFFSET word of the status block
     int64_t det_cap;        // rows (0: deterministic mode off)
 };
+
+// The rows of layer kk of pixel gpix (P pixels), for kk = 0, 1, 2, ... in
+// turn: a dense plane (row stride P) below dense_layers, else the pool slot
+// that the previous layer's slot (or the pixel's first-slot word) links to
+// (row stride 1); `slot` carries the chain from one call to the next.  Null
+// when the forward ran out of pool slots (SS_ERR_CAPACITY).
+#define SS_NO_SLOT 0xffffffffu
+__device__ __forceinline__ float* ss_layer_rows(const ss_ws_view& ws, int64_t P, int64_t gpix, int kk, uint32_t& slot,
+                                                int64_t& stride) {
+    if (kk < ws.dense_layers) {
+        stride = P;
+        return ws.layer_state + (int64_t)kk * ws.ls_rows * P + gpix;
+    }
+    stride = 1;
+    if (kk == ws.dense_layers) slot = __float_as_uint(ws.pix_state[2 * P + gpix]);
+    else if (slot != SS_NO_SLOT) slot = __float_as_uint(ws.layer_pool[(int64_t)slot * ws.pool_stride + ws.ls_rows]);
+    return slot == SS_NO_SLOT ? nullptr : ws.layer_pool + (int64_t)slot * ws.pool_stride;
+}
 
 // ------------------------------------------------------------------------
 // double-float helpers (error-free transforms; Dekker / Knuth)

@@ -32,9 +32,9 @@ def test_library_exports_every_declared_symbol():
 
 def test_struct_sizes_match_header():
     assert ctypes.sizeof(_lib.ss_camera) == 80
-    assert ctypes.sizeof(_lib.ss_render_params) == 104
+    assert ctypes.sizeof(_lib.ss_render_params) == 120
     assert ctypes.sizeof(_lib.ss_surfel_grads) == 64
-    assert ctypes.sizeof(_lib.ss_stats) == 72
+    assert ctypes.sizeof(_lib.ss_stats) == 80
 
 
 def test_host_side_argument_errors():
@@ -97,7 +97,8 @@ def test_launch_shape_knobs_are_validated_on_the_host():
     for knob, bad, good in (("fwd_warps", 3, 4), ("bwd_warps", 1, 8), ("pbwd_block", 16, 32),
                             ("pbwd_block", 4096, 1024), ("tile_w", 12, 8), ("tile_h", 2, 4),
                             ("stage_depth", 4, 3), ("mip_mode", 3, 2), ("screen_grad", 2, 1),
-                            ("deterministic", 2, 1), ("det_rows", -1, 1 << 20)):
+                            ("deterministic", 2, 1), ("det_rows", -1, 1 << 20), ("dense_layers", 17, 2),
+                            ("layer_pool", -1, 1000)):
         q = _lib.ss_render_params()
         ctypes.memmove(ctypes.byref(q), ctypes.byref(p), ctypes.sizeof(q))
         setattr(q, knob, bad)
@@ -238,3 +239,35 @@ def test_deterministic_mode_sizes_its_rows_on_the_host():
     assert r2 - r1 >= 10000 * 104 - 1024 and r2 - r1 <= 10000 * 104 + 1024
     # det_rows 0: (16 / 8) x (16 / 4) = 8 blocks per tile times max_instances
     assert size(1, deterministic=1) == size(1, deterministic=1, det_rows=8 * 1000) > base
+
+
+def test_layer_pool_sizes_the_layer_state_on_the_host():
+    """dense_layers keeps that many layers per pixel in planes of every pixel
+    (13 floats each) and the deeper ones in layer_pool slots of 64 bytes: the
+    workspace shrinks by (k_max - dense) planes and grows by the pool."""
+    lib = _lib.lib()
+    p = _lib.ss_render_params()
+    lib.ss_default_params(ctypes.byref(p))
+    p.max_instances = 1000
+    cams = (_lib.ss_camera * 1)()
+    cams[0].width, cams[0].height = 64, 32
+    cams[0].fx = cams[0].fy = 10.0
+    off = (ctypes.c_int64 * 2)(0, 10)
+    d = _lib.ss_batch_desc(1, 1, off, cams, None)
+    ed = _lib.ss_env_desc(64, 32, 6, 32, 16)
+
+    def size(**kw):
+        q = _lib.ss_render_params()
+        ctypes.memmove(ctypes.byref(q), ctypes.byref(p), ctypes.sizeof(q))
+        for k, v in kw.items():
+            setattr(q, k, v)
+        nb = ctypes.c_size_t()
+        assert lib.ss_workspace_size(ctypes.byref(d), ctypes.byref(q), ctypes.byref(ed), 1, ctypes.byref(nb)) == 0
+        return nb.value
+
+    P = 64 * 32
+    full = size()
+    assert size(dense_layers=16) == full
+    two = size(dense_layers=2, layer_pool=0)
+    assert abs((full - two) - 14 * 13 * 4 * P) <= 512
+    assert abs((size(dense_layers=2, layer_pool=5000) - two) - 5000 * 64) <= 512
