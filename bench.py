@@ -504,9 +504,9 @@ def run_ours(args):
     # layer state sized by the work: dense planes for the first layers, a pool for the rest
     layers_cfg = {"dense_layers": "all", "workspace_bytes": int(r.ws_bytes)}
     if args.dense_layers > 0:
-        pool, wsb = r.compact_layers(args.dense_layers)
-        layers_cfg = {"dense_layers": args.dense_layers, "layer_pool": pool, "workspace_bytes": int(wsb),
-                      "workspace_bytes_all_dense": layers_cfg["workspace_bytes"]}
+        cands, pool, wsb = r.compact_workspace(args.dense_layers)
+        layers_cfg = {"dense_layers": args.dense_layers, "layer_pool": pool, "max_candidates": cands,
+                      "workspace_bytes": int(wsb), "workspace_bytes_bounds": layers_cfg["workspace_bytes"]}
 
     for _ in range(args.warmup):
         step()
@@ -637,14 +637,15 @@ def run_ours(args):
         del rd
         torch.cuda.empty_cache()
 
-    # --- the same step with the layer state sized by the work (2 dense layers + a pool)
+    # --- the same step with the workspace sized by the work (block lists by their candidates,
+    #     2 dense layers + a pool for the deeper ones)
     layer_pool = None
     if not args.no_layer_pool and args.dense_layers == 0:
         rp = Renderer(scene, share_from=r)
         for k in KNOBS:
             setattr(rp.prm, k, getattr(r.prm, k))
         rp.plan_capacity()
-        pool, wsb = rp.compact_layers(2)
+        cands, pool, wsb = rp.compact_workspace(2)
         rp.zero_grads()
 
         def step_pool():
@@ -657,9 +658,11 @@ def run_ours(args):
         ms_p = timed(step_pool, args.steps)
         if rp.read_status() != 0:
             raise RuntimeError(f"device status {rp.read_status()} in the pooled-layer step")
+        used = rp.stats()
         layer_pool = {"value": job_rate(V, args.steps, world, ms_p), "unit": "views/s", "ms_per_step": ms_p / args.steps,
-                      "dense_layers": 2, "layer_pool": pool, "pool_layers_used": rp.stats()["pool_layers"],
-                      "workspace_bytes": int(wsb), "workspace_bytes_all_dense": int(r.ws_bytes)}
+                      "dense_layers": 2, "layer_pool": pool, "pool_layers_used": used["pool_layers"],
+                      "max_candidates": cands, "candidates_used": used["candidates"],
+                      "workspace_bytes": int(wsb), "workspace_bytes_bounds": int(r.ws_bytes)}
         del rp
         torch.cuda.empty_cache()
 

@@ -47,10 +47,12 @@ typedef int ss_status;
 #define SS_ERR_INVALID_ARG 1  /* bad argument; nothing was enqueued */
 #define SS_ERR_WORKSPACE 2    /* workspace smaller than ss_workspace_size */
 #define SS_ERR_CAPACITY 4     /* device: more (tile, surfel) instances than
-                                 ss_render_params.max_instances, or (the
-                                 deterministic backward) more covering (block,
-                                 surfel) pairs than det_rows; the affected
-                                 outputs are incomplete */
+                                 ss_render_params.max_instances, more block
+                                 candidates than max_candidates, more deep
+                                 layers than layer_pool, or (the deterministic
+                                 backward) more covering (block, surfel) pairs
+                                 than det_rows; the affected outputs are
+                                 incomplete */
 #define SS_ERR_TIMEOUT 8      /* device: a bounded wait gave up */
 #define SS_ERR_NONFINITE 16   /* device: a non-finite surfel parameter was seen
                                  (that surfel is skipped) */
@@ -184,6 +186,12 @@ typedef struct ss_render_params {
                                 dense_layers, 64 bytes each (80 with cons); ss_stats.pool_layers
                                 of a forward is the number it needed.  More pairs than slots
                                 set SS_ERR_CAPACITY (the backward then drops those layers' terms) */
+    int64_t max_candidates;  /* capacity of the per-(tile, 8 x 4 block) candidate lists of the
+                                rasterisers: the (tile, surfel) instances whose support can reach a
+                                block, once per block (ss_stats.candidates of a forward; 4 bytes each,
+                                16 with with_backward); 0 = the bound of (blocks per tile) x
+                                max_instances.  A block whose list would pass the capacity is not
+                                rendered and sets SS_ERR_CAPACITY */
 } ss_render_params;
 
 /* Work counters of the last forward/backward pair (collect_stats = 1). */
@@ -200,6 +208,9 @@ typedef struct ss_stats {
     int64_t pool_layers;     /* (pixel, layer) pairs past dense_layers that the forward stored in
                                 layer_pool slots (counted whether or not collect_stats is set, and
                                 beyond the capacity, so it sizes layer_pool) */
+    int64_t candidates;      /* (tile, block, surfel) candidates of the rasterisers' block lists
+                                (counted whether or not collect_stats is set; it sizes
+                                max_candidates) */
 } ss_stats;
 
 /* Stage timing: CUDA events recorded on the launching stream around each

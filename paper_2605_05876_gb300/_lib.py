@@ -56,13 +56,13 @@ class ss_render_params(ctypes.Structure):
                 ("collect_stats", c_i32), ("fwd_warps", c_i32), ("bwd_warps", c_i32), ("pbwd_block", c_i32),
                 ("screen_grad", c_i32), ("mip_mode", c_i32), ("cons", c_i32), ("tile_w", c_i32), ("tile_h", c_i32),
                 ("stage_depth", c_i32), ("deterministic", c_i32), ("det_rows", c_i64), ("dense_layers", c_i32),
-                ("pad_", c_i32), ("layer_pool", c_i64)]
+                ("pad_", c_i32), ("layer_pool", c_i64), ("max_candidates", c_i64)]
 
 
 class ss_stats(ctypes.Structure):
     _fields_ = [("instances", c_i64), ("rect_tests", c_i64), ("lane_tests", c_i64), ("fragments", c_i64),
                 ("layers", c_i64), ("bwd_fragments", c_i64), ("staged", c_i64), ("staged_covering", c_i64),
-                ("bwd_batches", c_i64), ("pool_layers", c_i64)]
+                ("bwd_batches", c_i64), ("pool_layers", c_i64), ("candidates", c_i64)]
 
 
 SS_N_STAGES = 9

@@ -212,19 +212,24 @@ class Renderer:
     TUNE_SPACE = {"tile": ((16, 16), (16, 8), (32, 8), (8, 16), (8, 8)), "stage_depth": (1, 2, 3),
                   "fwd_warps": (1, 2, 4), "bwd_warps": (2, 4, 8), "pbwd_block": (64, 128, 256)}
 
-    def compact_layers(self, dense: int = 2, slack: float = 1.25):
-        """Keep `dense` layers per pixel in planes of every pixel and the
-        deeper ones in a pool sized by this batch's work: one forward with
-        an empty pool counts the (pixel, layer) pairs past `dense`
-        (ss_stats.pool_layers), then the pool is sized with `slack` and the
-        workspace planned again.  Returns (pool slots, workspace bytes)."""
-        self.prm.dense_layers, self.prm.layer_pool = int(dense), 0
+    def compact_workspace(self, dense: int = 2, slack: float = 1.25):
+        """Size the workspace by this batch's work instead of its bounds: the
+        rasterisers' block lists by the candidates a forward counts
+        (ss_stats.candidates; the first forward runs with no room, which the
+        binning counts all the same), then `dense` layers per pixel in planes
+        of every pixel and the deeper ones in a pool sized by the (pixel,
+        layer) pairs past `dense` that a second forward counts
+        (ss_stats.pool_layers); each with `slack`.  Returns (candidates
+        capacity, pool slots, workspace bytes)."""
+        self.prm.dense_layers, self.prm.layer_pool, self.prm.max_candidates = int(dense), 0, 1
         self.plan_capacity(self.prm.max_instances)
         self.forward()
-        need = self.stats()["pool_layers"]
-        self.prm.layer_pool = int(math.ceil(need * slack)) + 1024
+        self.prm.max_candidates = int(math.ceil(self.stats()["candidates"] * slack)) + 4096
         self.plan_capacity(self.prm.max_instances)
-        return self.prm.layer_pool, self.ws_bytes
+        self.forward()
+        self.prm.layer_pool = int(math.ceil(self.stats()["pool_layers"] * slack)) + 1024
+        self.plan_capacity(self.prm.max_instances)
+        return self.prm.max_candidates, self.prm.layer_pool, self.ws_bytes
 
     def set_tile(self, tile):
         """Change the screen tile (width, height); the instance capacity and

@@ -111,6 +111,7 @@ static ss_status check_knobs(const ss_render_params* p) {
     if (p->det_rows < 0 || p->det_rows > 0xffffffffll) return SS_ERR_INVALID_ARG;
     if (p->dense_layers < 0 || p->dense_layers > p->k_max) return SS_ERR_INVALID_ARG;
     if (p->layer_pool < 0 || p->layer_pool > 0xffffffffll) return SS_ERR_INVALID_ARG;
+    if (p->max_candidates < 0 || p->max_candidates > 0xffffffffll) return SS_ERR_INVALID_ARG;
     return SS_OK;
 }
 
@@ -202,13 +203,21 @@ static ss_status build_layout(const ss_batch_desc* b, const ss_render_params* p,
 }
 
 struct ws_plan {
-    size_t status, layout, vgeo, rec, rank, rbm, tc, ts, tcur, keys, keys_alt, bmask, cand, layer, pool, pix, grad, masks,
-        madv, mcount, env_acc, jac, total;
+    size_t status, layout, vgeo, rec, rank, rbm, tc, ts, tcur, keys, keys_alt, bmask, cand, ccnt, coff, stmp, layer,
+        pool, pix, grad, masks, madv, mcount, env_acc, jac, total;
+    int64_t cand_cap;
     int64_t env_texels;   // irradiance + specular texels of one scene (0: no env-gradient scratch)
     // deterministic backward
     size_t d_icnt, d_coff, d_rows, d_rid, d_rcnt, d_roff, d_rcur, d_rlist, d_scan;
     int64_t det_cap;
 };
+
+// entries of the per-(tile, block) candidate and cover lists: max_candidates,
+// or (blocks per tile) x max_instances
+static int64_t cand_capacity(const ss_layout& L, const ss_render_params& p) {
+    const int64_t c = p.max_candidates ? p.max_candidates : (int64_t)L.bpt * p.max_instances;
+    return c < 0xffffffffll ? c : 0xffffffffll;
+}
 
 // layers per pixel in the dense planes (dense_layers; 0 = all k_max)
 static int dense_layers(const ss_render_params& p) { return p.dense_layers > 0 ? p.dense_layers : p.k_max; }
@@ -241,14 +250,18 @@ static ws_plan plan_ws(const ss_layout& L, const ss_render_params& p, int with_b
     w.keys = take(sizeof(unsigned long long) * (size_t)p.max_instances);
     w.keys_alt = take(sizeof(unsigned long long) * (size_t)p.max_instances);
     w.bmask = take(sizeof(uint8_t) * (size_t)p.max_instances);
-    w.cand = take(sizeof(uint32_t) * 8 * (size_t)p.max_instances);
+    w.cand_cap = cand_capacity(L, p);
+    w.cand = take(sizeof(uint32_t) * (size_t)w.cand_cap);
+    w.ccnt = take(sizeof(uint32_t) * 8 * (size_t)L.total_tiles);
+    w.coff = take(sizeof(uint32_t) * (8 * (size_t)L.total_tiles + 1));
+    w.stmp = take(sizeof(unsigned long long) * (size_t)(ss_det_scan_blocks(8 * (int64_t)L.total_tiles) + 1));
     if (with_bwd) {
         w.layer = take(sizeof(float) * (size_t)dense_layers(p) * (p.cons ? 16 : 13) * (size_t)L.total_pixels);
         w.pool = dense_layers(p) < p.k_max ? take(sizeof(float) * (p.cons ? 20 : 16) * (size_t)p.layer_pool) : 0;
         w.pix = take(sizeof(float) * 3 * (size_t)L.total_pixels);
         w.grad = take(sizeof(float) * SS_NGRAD * (size_t)L.total_records);
-        w.masks = take(sizeof(uint2) * 8 * (size_t)p.max_instances);
-        w.madv = take(sizeof(uint32_t) * 8 * (size_t)p.max_instances);
+        w.masks = take(sizeof(uint2) * (size_t)w.cand_cap);
+        w.madv = take(sizeof(uint32_t) * (size_t)w.cand_cap);
         w.mcount = take(sizeof(uint32_t) * 8 * (size_t)L.total_tiles);
         w.env_acc = take(sizeof(float4) * SS_ACC_STRIDE * (size_t)w.env_texels * (size_t)L.n_scenes);
         w.jac = p.screen_grad ? take(sizeof(float4) * 4 * (size_t)L.total_records) : 0;
@@ -293,6 +306,10 @@ static ss_ws_view carve(void* ws, const ws_plan& w, const ss_render_params& p, i
     v.keys_alt = (unsigned long long*)(b + w.keys_alt);
     v.bmask = (uint8_t*)(b + w.bmask);
     v.cand_list = (uint32_t*)(b + w.cand);
+    v.cand_cnt = (uint32_t*)(b + w.ccnt);
+    v.cand_off = (uint32_t*)(b + w.coff);
+    v.scan_tmp = (unsigned long long*)(b + w.stmp);
+    v.cand_cap = w.cand_cap;
     v.layer_state = with_bwd ? (float*)(b + w.layer) : nullptr;
     v.ls_rows = p.cons ? 16 : 13;
     v.dense_layers = dense_layers(p);

@@ -1,4 +1,5 @@
-// Deterministic backward (ss_render_params.deterministic = 1).
+// Deterministic backward (ss_render_params.deterministic = 1), and the
+// multi-block prefix sum it shares with the rasterisers' block lists.
 //
 // The default backward adds every run of fragment gradients into its
 // (surfel, view) record with FP32 atomics, whose order -- and so the last
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(DSCAN_T) scan_bsum_kernel(unsigned long long* 
 __global__ void __launch_bounds__(DSCAN_T) scan_apply_kernel(const uint32_t* __restrict__ in, int64_t n,
                                                              const unsigned long long* __restrict__ bsum, int64_t nb,
                                                              uint32_t* __restrict__ out, unsigned long long cap,
-                                                             int* status) {
+                                                             int* status, unsigned long long* total_out) {
     __shared__ unsigned long long wsum[32];
     const int64_t i0 = (int64_t)blockIdx.x * DSCAN_B + (int64_t)threadIdx.x * DSCAN_PER;
     uint32_t x[DSCAN_PER];
@@ -105,11 +106,12 @@ __global__ void __launch_bounds__(DSCAN_T) scan_apply_kernel(const uint32_t* __r
         const unsigned long long t = bsum[nb];
         out[n] = (uint32_t)(t < 0xffffffffull ? t : 0xffffffffull);
         if (t > cap) atomicOr(status, SS_ERR_CAPACITY);
+        if (total_out) *total_out = t;
     }
 }
 
-static void launch_scan(const uint32_t* in, int64_t n, uint32_t* out, unsigned long long* bsum, unsigned long long cap,
-                        int* status, cudaStream_t st) {
+void ss_launch_scan_u32(const uint32_t* in, int64_t n, uint32_t* out, unsigned long long* bsum, unsigned long long cap,
+                        int* status, unsigned long long* total_out, cudaStream_t st) {
     const int64_t nb = ss_det_scan_blocks(n);
     if (nb > 0) {
         ss_note_launch();
@@ -118,7 +120,7 @@ static void launch_scan(const uint32_t* in, int64_t n, uint32_t* out, unsigned l
     ss_note_launch();
     scan_bsum_kernel<<<1, DSCAN_T, 0, st>>>(bsum, nb);
     ss_note_launch();
-    scan_apply_kernel<<<(unsigned)(nb > 0 ? nb : 1), DSCAN_T, 0, st>>>(in, n, bsum, nb, out, cap, status);
+    scan_apply_kernel<<<(unsigned)(nb > 0 ? nb : 1), DSCAN_T, 0, st>>>(in, n, bsum, nb, out, cap, status, total_out);
 }
 
 // covering entries of each (tile, block) item, as the forward left them
@@ -137,7 +139,8 @@ void ss_launch_det_item_offsets(const ss_ws_view& ws, const ss_layout& L, cudaSt
         det_item_count_kernel<<<(unsigned)((items + 255) / 256), 256, 0, st>>>(ws.cover_count, items, L.bpt,
                                                                                 ws.det_icnt);
     }
-    launch_scan(ws.det_icnt, items, ws.det_coff, ws.det_scan, (unsigned long long)ws.det_cap, ws.status, st);
+    ss_launch_scan_u32(ws.det_icnt, items, ws.det_coff, ws.det_scan, (unsigned long long)ws.det_cap, ws.status, nullptr,
+                       st);
 }
 
 // the rows in use: rows [0, min(total, cap)), total = det_coff[items]
@@ -211,7 +214,7 @@ void ss_launch_det_record_sums(const ss_ws_view& ws, const ss_layout& L, int nv,
     const unsigned grid = (unsigned)(sms > 0 ? 8 * sms : 1024);
     ss_note_launch();
     det_count_kernel<<<grid, 256, 0, st>>>(ws, items);
-    launch_scan(ws.det_rcnt, R, ws.det_roff, ws.det_scan, 0xffffffffull, ws.status, st);
+    ss_launch_scan_u32(ws.det_rcnt, R, ws.det_roff, ws.det_scan, 0xffffffffull, ws.status, nullptr, st);
     ss_note_launch();
     det_fill_kernel<<<grid, 256, 0, st>>>(ws, items);
     ss_note_launch();

@@ -412,15 +412,12 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
     };
     if (!done) enter_layer(0);
 
-    const int64_t cap = ws.max_instances;
-    int64_t beg = ws.tile_start[tile], end = ws.tile_start[tile + 1];
-    if (end > cap) end = cap;
-    if (beg > end) beg = end;
     const ss_rec* recs = ws.rec;   // keys hold batch-wide record indices
     float* grad = ws.grad_rec;
     // the forward pass's list of covering staged surfels of this warp
-    const uint2* clist = ws.cover_list + 8 * beg + (int64_t)warp * (end - beg);
-    const uint32_t* alist = ws.cover_adv + 8 * beg + (int64_t)warp * (end - beg);
+    const int64_t loff = ws.cand_off[(int64_t)tile * 8 + warp];   // the block's list (the forward's offsets)
+    const uint2* clist = ws.cover_list + loff;
+    const uint32_t* alist = ws.cover_adv + loff;
     const int64_t n_list = ws.cover_count[(int64_t)tile * 8 + warp];
     // deterministic mode: this item's rows start at det_coff[item] (one per list entry)
     const int64_t row0 = DET ? (int64_t)ws.det_coff[gw] : 0;

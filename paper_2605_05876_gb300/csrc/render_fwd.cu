@@ -548,10 +548,30 @@ __device__ __noinline__ void sort_chunk(unsigned long long* K, int m, int N, uns
     __syncthreads();
 }
 
-// block masks of n sorted keys, all threads of the CTA (coalesced key reads)
+// block masks of n sorted keys, all threads of the CTA (coalesced key reads);
+// each thread counts the bits of the masks it wrote (candidates per block)
 __device__ __forceinline__ void gather_masks(const ss_ws_view& ws, const ss_tile_shape& ts, const unsigned long long* K,
-                                             uint8_t* BM, int n, int x0, int y0) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) BM[i] = (uint8_t)block_mask_of(ws, ts, K[i], x0, y0);
+                                             uint8_t* BM, int n, int x0, int y0, uint32_t (&cnt)[8]) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const uint32_t m = block_mask_of(ws, ts, K[i], x0, y0);
+        BM[i] = (uint8_t)m;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) cnt[b] += (m >> b) & 1u;
+    }
+}
+
+// the tile's candidates per block (the threads' counts summed) -> cand_cnt
+__device__ __forceinline__ void store_block_counts(const ss_ws_view& ws, int t, const uint32_t (&cnt)[8]) {
+    __shared__ uint32_t tot[8];
+    if (threadIdx.x < 8) tot[threadIdx.x] = 0u;
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const uint32_t v = __reduce_add_sync(0xffffffffu, cnt[b]);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&tot[b], v);
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) ws.cand_cnt[(int64_t)t * 8 + threadIdx.x] = tot[threadIdx.x];
 }
 
 __global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view ws, int total_tiles, ss_tile_shape ts) {
@@ -560,7 +580,11 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view w
     const int64_t cap = ws.max_instances;
     int64_t b = ws.tile_start[t], e = ws.tile_start[t + 1];
     if (e > cap) e = cap;
-    if (b >= e) return;
+    uint32_t cnt[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};   // candidates per block (the mask bits)
+    if (b >= e) {
+        if (threadIdx.x < 8) ws.cand_cnt[(int64_t)t * 8 + threadIdx.x] = 0u;
+        return;
+    }
     const int n = (int)(e - b);
     unsigned long long* K = ws.keys + b;
     uint8_t* BM = ws.bmask + b;
@@ -573,7 +597,8 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view w
         y0 = (lt / vl.tiles_x) << ts.th_log2;
     }
     if (n == 1) {
-        if (threadIdx.x == 0) BM[0] = (uint8_t)block_mask_of(ws, ts, K[0], x0, y0);
+        gather_masks(ws, ts, K, BM, 1, x0, y0, cnt);
+        store_block_counts(ws, t, cnt);
         return;
     }
     unsigned long long* Alt = ws.keys_alt + b;
@@ -589,7 +614,8 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view w
         else sort_chunk<SORT_KPL>(K + c0, m, N, xs);
     }
     if (n <= SORT_CAP) {
-        gather_masks(ws, ts, K, BM, n, x0, y0);
+        gather_masks(ws, ts, K, BM, n, x0, y0, cnt);
+        store_block_counts(ws, t, cnt);
         return;
     }
     // pairwise merges in global memory, ping-pong between K and Alt
@@ -611,8 +637,12 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view w
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const unsigned long long k = src[i];
         if (src != K) K[i] = k;
-        BM[i] = (uint8_t)block_mask_of(ws, ts, k, x0, y0);
+        const uint32_t m = block_mask_of(ws, ts, k, x0, y0);
+        BM[i] = (uint8_t)m;
+#pragma unroll
+        for (int bb = 0; bb < 8; ++bb) cnt[bb] += (m >> bb) & 1u;
     }
+    store_block_counts(ws, t, cnt);
 }
 
 void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st) {
@@ -630,6 +660,9 @@ void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_a
     ss_note_launch();
     tile_sort_kernel<<<L.total_tiles, SORT_THREADS, SORT_CAP * sizeof(unsigned long long), st>>>(ws, L.total_tiles,
                                                                                                  a.ts);
+    // each (tile, block)'s list starts at the prefix sum of the candidate counts
+    ss_launch_scan_u32(ws.cand_cnt, (int64_t)L.total_tiles * 8, ws.cand_off, ws.scan_tmp,
+                       (unsigned long long)ws.cand_cap, ws.status, ws.stats + 10, st);
 }
 
 // ------------------------------------------------------------------------
@@ -760,15 +793,20 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
     if (beg > end) beg = end;
     const ss_rec* recs = ws.rec;   // keys hold batch-wide record indices
     // the backward pass's fragment list: (record, coverage word) of every
-    // staged surfel that covers a pixel of this block, in list order, in the
-    // warp's own region of 8 x the tile's list
-    uint2* clist = ws.cover_list ? ws.cover_list + 8 * beg + (int64_t)warp * (end - beg) : nullptr;
-    uint32_t* alist = clist ? ws.cover_adv + 8 * beg + (int64_t)warp * (end - beg) : nullptr;
+    // staged surfel that covers a pixel of this block, in list order;
+    // the block's lists (candidates, covering entries) start at cand_off[tile * 8 + block]; a block
+    // whose lists would pass the capacity is not rendered (the scan flagged SS_ERR_CAPACITY)
+    const int64_t loff = ws.cand_off[(int64_t)tile * 8 + warp];
+    const bool fits = (int64_t)ws.cand_off[(int64_t)tile * 8 + warp + 1] <= ws.cand_cap &&
+                      ws.cand_off[(int64_t)tile * 8 + warp + 1] != 0xffffffffu;
+    if (!fits) end = beg;
+    uint2* clist = ws.cover_list ? ws.cover_list + loff : nullptr;
+    uint32_t* alist = clist ? ws.cover_adv + loff : nullptr;
     uint32_t n_list = 0;
     ss_wstage* Wb = Wst + (a.p.stage_depth ? a.p.stage_depth : 2) * lw;
     // pass 1: the records whose support rectangle meets the block, in list
     // order, into the warp's candidate list (four chunks of keys in flight)
-    uint32_t* cand = ws.cand_list + 8 * beg + (int64_t)warp * (end - beg);
+    uint32_t* cand = ws.cand_list + loff;
     int n_cand = 0;
     for (int64_t j0 = beg; j0 < end; j0 += 128) {
         ss_chunk c[4];

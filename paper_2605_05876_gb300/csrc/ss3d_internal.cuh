@@ -81,8 +81,9 @@ struct ss_view_geo {
 };
 
 // device status bits live in the first word of the workspace; the work
-// counters (ss_stats, int64 x 10) at byte 64 of the same 256-byte block (the
-// last, the layer-pool slots taken, is the pool's allocation counter)
+// counters (ss_stats, int64 x 11) at byte 64 of the same 256-byte block (the
+// layer-pool slots taken is the pool's allocation counter; the candidates are
+// written by the prefix sum of the block lists)
 #define SS_STATS_OFFSET 64
 // work-queue heads of the persistent rasterisers (uint32: forward, backward)
 // at byte 192 of the same block
@@ -109,7 +110,12 @@ struct ss_ws_view {
     uint8_t* bmask;         // [max_instances] per sorted instance: bit b set iff the instance may cover a pixel
                             // centre of 8 x 4 block b of its tile (support rectangle overlaps the block and
                             // the exact support's minimum over the block's pixel centres is below the cutoff)
-    uint32_t* cand_list;    // [8 x max_instances] per (tile, block): records whose rectangle meets the block
+    uint32_t* cand_list;    // [cand_cap] per (tile, block) from cand_off[tile * 8 + block]: the records of the
+                            // tile's list whose block bit is set, in list order
+    uint32_t* cand_cnt;     // [total_tiles * 8] candidates of each (tile, block) (the tile sort's block bits)
+    uint32_t* cand_off;     // [total_tiles * 8 + 1] their exclusive prefix sum (clamped to 32 bits)
+    unsigned long long* scan_tmp;   // block sums of the prefix-sum kernels
+    int64_t cand_cap;
     float* layer_state;     // [dense_layers][ls_rows][total_pixels]: raw C (12), W; with the depth-consolidation
                             // term also (sum w (z - z_r), sum w (z - z_r)^2, z_r), z_r the layer's first depth
     int32_t ls_rows;        // 13, or 16 with the depth-consolidation term
@@ -120,9 +126,9 @@ struct ss_ws_view {
     int64_t pool_cap;       // slots (0: no pool)
     float* pix_state;       // [3][total_pixels]  (K as float bits, T_end, first pool slot as uint32 bits)
     float* grad_rec;        // [total_records][SS_NGRAD]
-    uint2* cover_list;      // [8 * max_instances]: per warp, (record, 32-pixel coverage word) of every staged
-                            // surfel that covers a pixel of the warp's block, in list order (forward -> backward)
-    uint32_t* cover_adv;    // [8 * max_instances]: per cover_list entry, the pixel lanes where that
+    uint2* cover_list;      // [cand_cap] per (tile, block) from cand_off: (record, 32-pixel coverage word) of every
+                            // staged surfel that covers a pixel of the block, in list order (forward -> backward)
+    uint32_t* cover_adv;    // [cand_cap]: per cover_list entry, the pixel lanes where that
                             // surfel's fragment opens a new layer (Algorithm 1's gap test as the
                             // forward decided it; the first fragment of a pixel opens layer 0 and
                             // is not marked)
@@ -468,6 +474,11 @@ void ss_launch_det_item_offsets(const ss_ws_view& ws, const ss_layout& L, cudaSt
 void ss_launch_det_record_sums(const ss_ws_view& ws, const ss_layout& L, int nv, bool ssg, cudaStream_t st);
 void ss_launch_det_env_bound(const ss_ws_view& ws, const ss_layout& L, cudaStream_t st);
 int64_t ss_det_scan_blocks(int64_t n);
+// exclusive prefix sum of n uint32 counts into out[0 .. n] (out[n] = total,
+// clamped to 32 bits; a total above cap sets SS_ERR_CAPACITY in *status; the
+// total also into *total_out when given); bsum: ss_det_scan_blocks(n) + 1 words
+void ss_launch_scan_u32(const uint32_t* in, int64_t n, uint32_t* out, unsigned long long* bsum, unsigned long long cap,
+                        int* status, unsigned long long* total_out, cudaStream_t st);
 
 // Fixed-point scale of the deterministic environment-gradient sums: 2^k
 // with k from the record bound (maxbits: the largest |dL/d rgb| of a

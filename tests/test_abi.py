@@ -32,9 +32,9 @@ def test_library_exports_every_declared_symbol():
 
 def test_struct_sizes_match_header():
     assert ctypes.sizeof(_lib.ss_camera) == 80
-    assert ctypes.sizeof(_lib.ss_render_params) == 120
+    assert ctypes.sizeof(_lib.ss_render_params) == 128
     assert ctypes.sizeof(_lib.ss_surfel_grads) == 64
-    assert ctypes.sizeof(_lib.ss_stats) == 80
+    assert ctypes.sizeof(_lib.ss_stats) == 88
 
 
 def test_host_side_argument_errors():
@@ -98,7 +98,7 @@ def test_launch_shape_knobs_are_validated_on_the_host():
                             ("pbwd_block", 4096, 1024), ("tile_w", 12, 8), ("tile_h", 2, 4),
                             ("stage_depth", 4, 3), ("mip_mode", 3, 2), ("screen_grad", 2, 1),
                             ("deterministic", 2, 1), ("det_rows", -1, 1 << 20), ("dense_layers", 17, 2),
-                            ("layer_pool", -1, 1000)):
+                            ("layer_pool", -1, 1000), ("max_candidates", -1, 1000)):
         q = _lib.ss_render_params()
         ctypes.memmove(ctypes.byref(q), ctypes.byref(p), ctypes.sizeof(q))
         setattr(q, knob, bad)
@@ -271,3 +271,33 @@ def test_layer_pool_sizes_the_layer_state_on_the_host():
     two = size(dense_layers=2, layer_pool=0)
     assert abs((full - two) - 14 * 13 * 4 * P) <= 512
     assert abs((size(dense_layers=2, layer_pool=5000) - two) - 5000 * 64) <= 512
+
+
+def test_candidate_lists_size_the_workspace_on_the_host():
+    """The rasterisers' per-block candidate and cover lists take max_candidates
+    entries (4 + 8 + 4 bytes with the backward's lists), by default (blocks per
+    tile) x max_instances."""
+    lib = _lib.lib()
+    p = _lib.ss_render_params()
+    lib.ss_default_params(ctypes.byref(p))
+    p.max_instances = 1000
+    cams = (_lib.ss_camera * 1)()
+    cams[0].width = cams[0].height = 16
+    cams[0].fx = cams[0].fy = 10.0
+    off = (ctypes.c_int64 * 2)(0, 10)
+    d = _lib.ss_batch_desc(1, 1, off, cams, None)
+    ed = _lib.ss_env_desc(64, 32, 6, 32, 16)
+
+    def size(with_bwd, **kw):
+        q = _lib.ss_render_params()
+        ctypes.memmove(ctypes.byref(q), ctypes.byref(p), ctypes.sizeof(q))
+        for k, v in kw.items():
+            setattr(q, k, v)
+        nb = ctypes.c_size_t()
+        assert lib.ss_workspace_size(ctypes.byref(d), ctypes.byref(q), ctypes.byref(ed), with_bwd,
+                                     ctypes.byref(nb)) == 0
+        return nb.value
+
+    assert size(1) == size(1, max_candidates=8 * 1000)
+    assert abs((size(1, max_candidates=20000) - size(1, max_candidates=10000)) - 10000 * 16) <= 1024
+    assert abs((size(0, max_candidates=20000) - size(0, max_candidates=10000)) - 10000 * 4) <= 512

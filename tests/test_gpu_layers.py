@@ -81,3 +81,38 @@ def test_crowded_tile_with_pooled_layers_matches_oracle():
     assert r.read_status() == 0 and r.stats()["pool_layers"] > 0
     ref, gpu = _check_view(r, sc, 0)
     assert ref["n_layers"].max() == 16
+
+
+def test_block_lists_sized_by_their_candidates():
+    """max_candidates = the count a forward reports gives bitwise the images
+    and gradients of the bound-sized lists; one less is reported."""
+    from paper_2605_05876_gb300 import _lib
+    sc = _planes()
+    ref, st0, s0 = _render(sc)
+    need = s0["candidates"]
+    assert st0 == 0 and need > 0
+    got, st, s = _render(sc, max_candidates=need)
+    assert st == 0 and s["candidates"] == need
+    for k in ref:
+        assert np.array_equal(ref[k].view(np.uint32), got[k].view(np.uint32)), k
+    _, st, s = _render(sc, max_candidates=need - 1)
+    assert st & _lib.SS_ERR_CAPACITY and s["candidates"] == need
+
+
+def test_compact_workspace_renders_as_the_bounds():
+    """Renderer.compact_workspace (block lists and deep layers sized by two
+    counting forwards) renders the torus-and-sphere batch bitwise as the
+    bound-sized workspace, in less memory."""
+    import torch
+    from paper_2605_05876_gb300.api import Renderer
+    b = S.torus_sphere_100k(n=20000, res=96)
+    a = Renderer(b)
+    a.forward()
+    ref = a.rgba.cpu().numpy().copy()
+    c = Renderer(b)
+    cands, pool, ws = c.compact_workspace(1)
+    assert ws < a.ws_bytes
+    c.forward()
+    torch.cuda.synchronize()
+    assert c.read_status() == 0
+    assert np.array_equal(ref.view(np.uint32), c.rgba.cpu().numpy().view(np.uint32))
