@@ -38,12 +38,16 @@ __device__ __forceinline__ int64_t spec_level_off(const ss_env_desc& ed, int i, 
     return off;
 }
 
+// One thread per (surfel, view) record: blockIdx.y is the view, blockIdx.x
+// runs over its scene's surfels (blocks past the scene's count return).
 __global__ void __launch_bounds__(256, 4) project_kernel(ss_ws_view ws, ss_fwd_args a, int64_t n_total) {
     const ss_layout* L = ws.layout;
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n_total) return;
-    int scene = 0;
-    while (scene + 1 < L->n_scenes && i >= L->scene_begin[scene + 1]) ++scene;
+    const int vthis = blockIdx.y;
+    const ss_view_layout& vl0 = L->v[vthis];
+    const int64_t li = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (li >= vl0.n_surfels) return;
+    const int64_t i = vl0.surfel_begin + li;
+    const int scene = vl0.scene;
     const float* P = a.s.pos + i * 3;
     float c0 = P[0], c1 = P[1], c2 = P[2];
     float4 q = *reinterpret_cast<const float4*>(a.s.quat + i * 4);
@@ -73,8 +77,9 @@ __global__ void __launch_bounds__(256, 4) project_kernel(ss_ws_view ws, ss_fwd_a
     const float* spec = a.env.spec + scene * spec_stride;
     const int lutn = a.p.lut_n;
 
-    for (int v = L->scene_view_begin[scene]; v < L->scene_view_begin[scene + 1]; ++v) {
-        const ss_view_layout& vl = L->v[v];
+    {
+        const int v = vthis;
+        const ss_view_layout& vl = vl0;
         const ss_camera& cam = a.cams[v];
         const int64_t local = i - vl.surfel_begin;
         ss_rec rec;
@@ -272,8 +277,11 @@ __global__ void __launch_bounds__(256, 4) project_kernel(ss_ws_view ws, ss_fwd_a
 void ss_launch_project(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_args& a, cudaStream_t st) {
     int64_t n = L.scene_begin[L.n_scenes];
     if (n <= 0) return;
+    int64_t nmax = 0;   // the largest scene's surfels: the grid's x extent
+    for (int v = 0; v < L.n_views; ++v) nmax = nmax > L.v[v].n_surfels ? nmax : L.v[v].n_surfels;
+    if (nmax <= 0) return;
     ss_note_launch();
-    project_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ws, a, n);
+    project_kernel<<<dim3((unsigned)((nmax + 255) / 256), (unsigned)L.n_views), 256, 0, st>>>(ws, a, n);
 }
 
 // ------------------------------------------------------------------------
@@ -848,6 +856,7 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
         const int n = min(32, n_cand - b0);
         stage_finish(W, n, lane, (float)x0, (float)y0, D - 1);
         uint32_t my_mask = 0, my_adv = 0;
+        uint32_t advc = 0;   // the slots whose fragment opened a layer at this lane's pixel
         // staged surfels whose exact support can reach a pixel centre of the block
         // (the block bit only says that the support's bounding box does; the
         // per-pixel filter's support is not the centre quadratic's: no test)
@@ -885,14 +894,13 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
             }
             const uint32_t cm = __ballot_sync(0xffffffffu, cg);
             my_mask = lane == s ? cm : my_mask;
-            if (clist) {   // the gap test below, kept for the backward's replay of the grouping
-                const uint32_t am = __ballot_sync(0xffffffffu, cg && !done && Wg > 0.f && h2.x > zmax);
-                my_adv = lane == s ? am : my_adv;
-            }
             if (cg && !done) {
                 if (STATS) ++n_frag;
                 const float w = nf * __expf(-0.5f * rho2);   // Eq. mip_weight (Eq. mip_eval per pixel)
-                if (Wg > 0.f && h2.x > zmax) flush();                          // gap: new layer
+                if (Wg > 0.f && h2.x > zmax) {   // gap: new layer (kept for the backward's replay)
+                    advc |= 1u << s;
+                    flush();
+                }
                 if (!done) {
                     zmax = fmaxf(zmax, h2.y);
                     const float4 c0v = W.c0[s], c1v = W.c1[s], c2v = W.c2[s];
@@ -910,6 +918,13 @@ __device__ __forceinline__ void raster_fwd_block(const ss_ws_view& ws, const ss_
                     }
                     Wg += w;
                 }
+            }
+        }
+        if (clist) {   // slot s's layer-opening word: bit p of pixel p's advc, for the slots with one
+            for (uint32_t any = __reduce_or_sync(0xffffffffu, advc); any; any &= any - 1) {
+                const int s = __ffs(any) - 1;
+                const uint32_t am = __ballot_sync(0xffffffffu, (advc >> s) & 1u);
+                my_adv = lane == s ? am : my_adv;
             }
         }
         if (STATS) {   // warp-uniform counts, kept by lane 0
