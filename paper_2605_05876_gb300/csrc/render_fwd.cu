@@ -582,12 +582,19 @@ __device__ __forceinline__ void store_block_counts(const ss_ws_view& ws, int t, 
     if (threadIdx.x < 8) ws.cand_cnt[(int64_t)t * 8 + threadIdx.x] = tot[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view ws, int total_tiles, ss_tile_shape ts) {
+// SMALL: the tiles of at most SORT_SMALL keys (4 or 8 per thread: 16 KB of
+// shared memory, so 4 CTAs share an SM); the others in a launch of their own
+// with room for SORT_CAP keys.  Each launch skips the other's tiles.
+#define SORT_SMALL (SORT_THREADS * 8)
+template <bool SMALL>
+__global__ void __launch_bounds__(SORT_THREADS, SMALL ? 4 : 2) tile_sort_kernel(ss_ws_view ws, int total_tiles,
+                                                                              ss_tile_shape ts) {
     extern __shared__ unsigned long long xs[];
     const int t = blockIdx.x;
     const int64_t cap = ws.max_instances;
     int64_t b = ws.tile_start[t], e = ws.tile_start[t + 1];
     if (e > cap) e = cap;
+    if ((e - b <= SORT_SMALL) != SMALL) return;   // the other launch's tile
     uint32_t cnt[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};   // candidates per block (the mask bits)
     if (b >= e) {
         if (threadIdx.x < 8) ws.cand_cnt[(int64_t)t * 8 + threadIdx.x] = 0u;
@@ -617,7 +624,7 @@ __global__ void __launch_bounds__(SORT_THREADS, 2) tile_sort_kernel(ss_ws_view w
         int N = 2;
         while (N < m) N <<= 1;
         if (N <= SORT_THREADS * 4) sort_chunk<4>(K + c0, m, N, xs);
-        else if (N <= SORT_THREADS * 8) sort_chunk<8>(K + c0, m, N, xs);
+        else if (SMALL || N <= SORT_THREADS * 8) sort_chunk<8>(K + c0, m, N, xs);
         else if (N <= SORT_THREADS * 16) sort_chunk<16>(K + c0, m, N, xs);
         else sort_chunk<SORT_KPL>(K + c0, m, N, xs);
     }
@@ -664,10 +671,13 @@ void ss_launch_bin_sort(const ss_ws_view& ws, const ss_layout& L, const ss_fwd_a
             ws, L.total_records, a.p.r_cut * a.p.r_cut, a.p.mip_mode == 2 ? 0 : 1, a.ts);
     }
     static std::atomic<unsigned long long> optin{0};
-    ss_smem_optin(tile_sort_kernel, SORT_CAP * (int)sizeof(unsigned long long), optin);
+    ss_smem_optin(tile_sort_kernel<false>, SORT_CAP * (int)sizeof(unsigned long long), optin);
     ss_note_launch();
-    tile_sort_kernel<<<L.total_tiles, SORT_THREADS, SORT_CAP * sizeof(unsigned long long), st>>>(ws, L.total_tiles,
-                                                                                                 a.ts);
+    tile_sort_kernel<true><<<L.total_tiles, SORT_THREADS, SORT_SMALL * sizeof(unsigned long long), st>>>(
+        ws, L.total_tiles, a.ts);
+    ss_note_launch();
+    tile_sort_kernel<false><<<L.total_tiles, SORT_THREADS, SORT_CAP * sizeof(unsigned long long), st>>>(
+        ws, L.total_tiles, a.ts);
     // each (tile, block)'s list starts at the prefix sum of the candidate counts
     ss_launch_scan_u32(ws.cand_cnt, (int64_t)L.total_tiles * 8, ws.cand_off, ws.scan_tmp,
                        (unsigned long long)ws.cand_cap, ws.status, ws.stats + 10, st);
