@@ -522,6 +522,7 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
                     B.tab[(NV + 1) * GCOL + lane] = 1.f;
                 }
             }
+            const uint32_t rid = Wc->id[s];   // this lane's record (run ends shuffle it to the row lanes)
             const int snext = __shfl_down_sync(0xffffffffu, s, 1);
             // run ends: the last valid column and every column followed by another surfel
             const uint32_t ends = __ballot_sync(0xffffffffu, valid && (lane == nb - 1 || snext != s));
@@ -548,11 +549,11 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
                 for (int j = 4 * m; j < 4 * m + 4; ++j) {
                     tot += v[j];
                     if ((ends >> j) & 1u) {   // warp-uniform
-                        const int sl = __shfl_sync(0xffffffffu, s, j);
                         const int colq = lane < NV ? lane : G_SSN + lane - NV;   // table row -> record column
                         if constexpr (DET) {
                             // the entry's row: written by its first run, added to by the run that
                             // continues it at the start of the next batch
+                            const int sl = __shfl_sync(0xffffffffu, s, j);
                             const int64_t row = row0 + chunk_base + sl;
                             const bool cont = rs == 0 && __shfl_sync(0xffffffffu, excl, sl) < b0;
                             if (row < ws.det_cap) {
@@ -560,8 +561,9 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
                                 if (lane < NVT) *dst = cont ? *dst + tot : tot;
                                 if (lane == 0 && !cont) ws.det_rid[row] = Wc->id[sl];
                             }
-                        } else if (lane < NVT && tot != 0.f) {
-                            atomicAdd(grad + (int64_t)Wc->id[sl] * SS_NGRAD + colq, tot);
+                        } else {
+                            const uint32_t rj = __shfl_sync(0xffffffffu, rid, j);
+                            if (lane < NVT && tot != 0.f) atomicAdd(grad + (int64_t)rj * SS_NGRAD + colq, tot);
                         }
                         tot = 0.f;
                         rs = j + 1;
