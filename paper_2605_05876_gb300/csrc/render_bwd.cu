@@ -52,22 +52,15 @@ struct ss_bwarp_t {
 };
 
 // Position of the j-th (0-based) set bit of m, for j < popc(m): the byte
-// from the population counts of the low bytes, then a halving search inside
-// the byte.
-__device__ __forceinline__ int ss_nth_bit(uint32_t m, int j) {
+// from the population counts of the low bytes, then the table of set-bit
+// positions within a byte (nth8[byte * 8 + k], in shared memory).
+__device__ __forceinline__ int ss_nth_bit(uint32_t m, int j, const uint8_t* nth8) {
     const int c1 = __popc(m & 0xffu), c2 = __popc(m & 0xffffu), c3 = __popc(m & 0xffffffu);
     int pos = 0, below = 0;
     if (j >= c1) { pos = 8; below = c1; }
     if (j >= c2) { pos = 16; below = c2; }
     if (j >= c3) { pos = 24; below = c3; }
-    j -= below;
-    uint32_t b = (m >> pos) & 0xffu;
-    int c = __popc(b & 0xfu);
-    if (j >= c) { j -= c; pos += 4; b >>= 4; }
-    c = __popc(b & 3u);
-    if (j >= c) { j -= c; pos += 2; b >>= 2; }
-    if (j >= (int)(b & 1u)) pos += 1;
-    return pos;
+    return pos + nth8[((m >> pos) & 0xffu) * 8 + (j - below)];
 }
 
 // Per pixel, per composited layer k (front to back), from the upstream
@@ -359,7 +352,7 @@ __global__ void __launch_bounds__(256) ssg_jac_kernel(ss_ws_view ws, ss_fwd_args
 // items from a queue.
 template <bool AOV, bool SSG, bool CONS, bool DET, bool POOL, int RWPB_BWD>
 __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_bwd_args& a, const int gw,
-                                                 unsigned char* bwd_smem) {
+                                                 unsigned char* bwd_smem, const uint8_t* nth8) {
     constexpr int NV = AOV ? G_N : G_CH + 3;   // gradient values per fragment
     constexpr int NVT = NV + (SSG ? 2 : 0);    // + |(g_x, g_y)| and a count of 1 (Eq. ss_grad)
     constexpr int NC = AOV ? SS_NCH : 3;       // channels with a coefficient
@@ -466,7 +459,7 @@ __device__ __forceinline__ void raster_bwd_block(const ss_ws_view& ws, const ss_
             }
             const uint32_t es = __shfl_sync(0xffffffffu, eff, s);
             const int first = __shfl_sync(0xffffffffu, excl, s);
-            const int pl = valid ? ss_nth_bit(es, F - first) : 0;   // its pixel lane
+            const int pl = valid ? ss_nth_bit(es, F - first, nth8) : 0;   // its pixel lane
             if (valid) {
                 const float4 h0 = Wc->h0[s], h1 = Wc->h1[s], h2 = Wc->h2[s];
                 const float dx = (float)(wx0 + (pl & 7)) + 0.5f - h1.z;
@@ -632,13 +625,23 @@ template <bool AOV, bool SSG, bool CONS, bool DET, bool POOL, int RWPB_BWD>
 __global__ void __launch_bounds__(32 * RWPB_BWD, 24 / RWPB_BWD) raster_bwd_kernel(ss_ws_view ws, ss_bwd_args a,
                                                                                   int n_items) {
     extern __shared__ __align__(16) unsigned char bwd_smem[];
+    __shared__ uint8_t nth8[256 * 8];   // set-bit positions within a byte
+    for (int e = threadIdx.x; e < 256 * 8; e += blockDim.x) {
+        const uint32_t v = (uint32_t)e >> 3;
+        const int k = e & 7;
+        int p = 0;
+        for (int c = -1; p < 8; ++p)
+            if (((v >> p) & 1u) && ++c == k) break;
+        nth8[e] = (uint8_t)(p & 7);
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     for (;;) {
         int item = 0;
         if (lane == 0) item = (int)atomicAdd(ws.work + 1, 1u);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= n_items) break;
-        raster_bwd_block<AOV, SSG, CONS, DET, POOL, RWPB_BWD>(ws, a, item, bwd_smem);
+        raster_bwd_block<AOV, SSG, CONS, DET, POOL, RWPB_BWD>(ws, a, item, bwd_smem, nth8);
         __syncwarp();
     }
 }
