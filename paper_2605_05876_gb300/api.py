@@ -212,6 +212,20 @@ class Renderer:
     TUNE_SPACE = {"tile": ((16, 16), (16, 8), (32, 8), (8, 16), (8, 8)), "stage_depth": (1, 2, 3),
                   "fwd_warps": (1, 2, 4), "bwd_warps": (2, 4, 8), "pbwd_block": (64, 128, 256)}
 
+    def state_dict(self) -> dict:
+        """The surfel parameters the renderer reads and the base env map
+        (copies), for torch.save: with Adam.state_dict, a checkpoint of the
+        inverse-rendering loop."""
+        return {"params": {k: v.detach().clone() for k, v in self.params_t.items()}, "env": self.env.detach().clone()}
+
+    def load_state_dict(self, st: dict):
+        """Restore a state_dict into this renderer's tensors (same surfel
+        count and env shape); the prefiltered maps are recomputed by the next
+        prefilter_env."""
+        for k, v in self.params_t.items():
+            v.copy_(st["params"][k])
+        self.env.copy_(st["env"])
+
     def compact_workspace(self, dense: int = 2, slack: float = 1.25):
         """Size the workspace by this batch's work instead of its bounds: the
         rasterisers' block lists by the candidates a forward counts
@@ -483,6 +497,22 @@ class Adam:
         self.t += 1
         self.p.step = self.t
         check(lib().ss_adam_step(self._arr, len(self.groups), ctypes.byref(self.p), _stream()), "ss_adam_step")
+
+    def state_dict(self) -> dict:
+        """Step count, raw values and moments of every group (copies), for
+        torch.save; the activated copies belong to the renderer's state."""
+        return {"t": self.t,
+                "raw": {k: g[0].detach().clone() for k, g in self.groups.items()},
+                "m": {k: m.detach().clone() for k, (m, _) in self.moments.items()},
+                "v": {k: v.detach().clone() for k, (_, v) in self.moments.items()}}
+
+    def load_state_dict(self, st: dict):
+        """Restore a state_dict into this optimiser's tensors (same groups and sizes)."""
+        self.t = int(st["t"])
+        for k, g in self.groups.items():
+            g[0].copy_(st["raw"][k])
+            self.moments[k][0].copy_(st["m"][k])
+            self.moments[k][1].copy_(st["v"][k])
 
 
 def loss_sil_iou(rgba, mask, view_offsets, d_rgba, loss, scale: float = 1.0):
