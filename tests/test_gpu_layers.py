@@ -116,3 +116,31 @@ def test_compact_workspace_renders_as_the_bounds():
     torch.cuda.synchronize()
     assert c.read_status() == 0
     assert np.array_equal(ref.view(np.uint32), c.rgba.cpu().numpy().view(np.uint32))
+
+
+def test_instance_capacity_overflow_is_reported_and_replanned():
+    """Too small an instance list (max_instances): the forward completes,
+    reports SS_ERR_CAPACITY and the real count (ss_stats.instances); planned
+    again with that count, the batch renders as with the default plan."""
+    import torch
+    from paper_2605_05876_gb300 import _lib
+    from paper_2605_05876_gb300.api import Renderer
+    b = S.torus_sphere_100k(n=20000, res=96)
+    ref = Renderer(b)
+    ref.forward()
+    torch.cuda.synchronize()
+    assert ref.read_status() == 0
+    r = Renderer(b)
+    r.plan_capacity(max_instances=ref.counted_instances // 3)
+    r.prm.collect_stats = 1
+    r.forward()
+    torch.cuda.synchronize()
+    assert r.read_status() & _lib.SS_ERR_CAPACITY
+    need = r.stats()["instances"]
+    assert need == ref.counted_instances
+    r.prm.collect_stats = 0
+    r.plan_capacity(max_instances=need)
+    r.forward()
+    torch.cuda.synchronize()
+    assert r.read_status() == 0
+    assert torch.equal(r.rgba, ref.rgba)
