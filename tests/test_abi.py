@@ -133,6 +133,8 @@ def test_render_calls_reject_null_device_pointers():
     assert st == _lib.SS_ERR_INVALID_ARG
     assert lib.ss_env_prefilter(ctypes.byref(ed), 1, None, None, None, None, None) == _lib.SS_ERR_INVALID_ARG
     assert lib.ss_env_prefilter_noalloc(ctypes.byref(ed), 1, None, None, None, None) == _lib.SS_ERR_INVALID_ARG
+    for f in (lib.ss_env_prefilter_backward, lib.ss_env_prefilter_backward_ordered):
+        assert f(ctypes.byref(ed), 1, None, None, None, None, None) == _lib.SS_ERR_INVALID_ARG
 
 
 def test_tile_shapes_validated_on_the_host():
