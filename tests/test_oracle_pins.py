@@ -597,3 +597,83 @@ def test_no_mip_is_the_unfiltered_unit_kernel():
     cov = out["rgba"][:, 3]
     inside = (U ** 2 + V ** 2).ravel() < 9.0 * (1 - 1e-6)
     np.testing.assert_allclose(cov[inside], 1 - np.exp(-w[inside]), rtol=1e-9, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# compositing identities with gamma != 2 pi
+
+
+def _stack_at_pixel(res=33):
+    """Fronto-parallel surfels stacked on the optical axis at four depths
+    (four layers at the centre pixel) plus a second surfel in the nearest
+    layer, one pixel to the side.  Returns the surfels, the camera, and for
+    each surfel its layer and closed-form weight at the centre pixel:
+    n_f exp(-rho^2 / 2) with a = z / (f s) the tangent-frame units per pixel,
+    n_f = 1 / (1 + sigma_f a^2) and rho^2 = a^2 d^2 / (1 + sigma_f a^2)
+    for a centre offset of d pixels (Sec. 3.3.2, Eq. mip_cov, mip_eval)."""
+    cam = _tiny.front_camera(dist=3.0, res=res)
+    f = float(np.float32(cam.fx))
+    zw = np.array([0.3, 0.1, -0.1, -0.3])            # world z; camera depth 3 - z
+    a_want = np.array([0.7, 1.1, 0.5, 0.9])
+    scale = (3.0 - zw) / (f * a_want)
+    dx = (3.0 - zw[0]) / f                           # one pixel at the nearest depth
+    pos = np.concatenate([np.stack([np.zeros(4), np.zeros(4), zw], 1), [[dx, 0.0, zw[0]]]])
+    surf = _tiny.surfels(pos, scale=np.concatenate([scale, scale[:1]]))
+    layer = np.array([0, 1, 2, 3, 0])
+    return surf, cam, layer
+
+
+def _closed_form_weights(surf, cam, sigma_f):
+    f = float(np.float32(cam.fx))
+    zc = 3.0 - surf.pos[:, 2].astype(np.float64)
+    s = np.exp(surf.log_scale[:, 0].astype(np.float64))
+    a = zc / (f * s)
+    d = surf.pos[:, 0].astype(np.float64) * f / zc    # centre offset in pixels
+    nf = 1.0 / (1.0 + sigma_f * a * a)
+    return nf * np.exp(-0.5 * a * a * d * d * nf), np.exp(-0.5 * a * a * d * d * nf)
+
+
+@pytest.mark.parametrize("k_max", [2, 3, 4])
+def test_coverage_is_exp_of_kept_weight_sum(k_max):
+    """The pixel's coverage is 1 - exp(-gamma / 2 pi * sum of W_k over the
+    kept layers): the product of the per-layer 1 - alpha_k of Eq. alpha
+    telescopes (Sec. 3.5.1, 3.5.2), and layers past K_max add nothing
+    (Algorithm 1).  gamma is taken away from 2 pi so that a dropped or
+    inverted gamma / 2 pi factor fails."""
+    gamma = 3.7
+    prm = M.Params(gamma=gamma, k_max=k_max)
+    surf, cam, layer = _stack_at_pixel()
+    env = env_state(_tiny.const_env(), prm)
+    pid = 16 * 33 + 16
+    out = _render(surf, cam, env, prm, pix=[pid])
+    assert out["n_layers"][0] == k_max
+    w, _ = _closed_form_weights(surf, cam, prm.sigma_f)
+    kept = layer < k_max
+    expect = 1.0 - math.exp(-gamma / (2 * math.pi) * w[kept].sum())
+    assert abs(out["rgba"][0, 3] - expect) < 1e-12
+    # and not the sum over every covering fragment
+    if k_max < 4:
+        assert abs(out["rgba"][0, 3] - (1.0 - math.exp(-gamma / (2 * math.pi) * w.sum()))) > 1e-3
+
+
+@pytest.mark.parametrize("k_max", [2, 4])
+def test_coverage_gradient_is_gamma_over_2pi_transmittance(k_max):
+    """dA/dw_i = gamma / 2 pi * T_{K+1} for every kept fragment, whatever its
+    layer (A = 1 - exp(-gamma / 2 pi * sum W)), and 0 for a fragment of a
+    dropped layer.  Back-propagated through w = n_f exp(-rho^2 / 2), the
+    gradient reaching each record's n_f is that times exp(-rho^2 / 2)."""
+    gamma = 3.7
+    prm = M.Params(gamma=gamma, k_max=k_max)
+    surf, cam, layer = _stack_at_pixel()
+    env = env_state(_tiny.const_env(), prm)
+    pid = 16 * 33 + 16
+    vs = M.prepare_view(surf, cam, env, prm, need_grad=True)
+    G = np.zeros((1, 13))
+    G[0, 3] = 1.0                                      # d/d(alpha channel)
+    out = M.render_pixels(vs, np.array([pid], np.int32), G)
+    T_end = 1.0 - out["rgba"][0, 3]
+    _, gauss = _closed_form_weights(surf, cam, prm.sigma_f)
+    expect = np.where(layer < k_max, gamma / (2 * math.pi) * T_end * gauss, 0.0)
+    got = vs.leaf["n_f"].grad.numpy()
+    np.testing.assert_allclose(got, expect, rtol=1e-10, atol=1e-15)
+    assert np.all(got[layer < k_max] > 0)
