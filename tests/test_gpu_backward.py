@@ -147,6 +147,29 @@ def test_backward_layer_cap(k_max):
     _compare(gpu, ref)
 
 
+@pytest.mark.parametrize("cons", [False, True])
+def test_gamma_away_from_2pi(cons):
+    """gamma = 3.7 (the coverage gain of Eq. alpha, 2 pi by default) on four
+    planes with K_max = 3: images and gradients (through alpha, the
+    transmittance and, with the consolidation term, its layer weights) match
+    the oracle, so the gain reaches every place the kernels use it."""
+    from paper_2605_05876_gb300.api import Renderer
+    from tests.test_gpu_forward import _check_view
+    rng = np.random.default_rng(9)
+    planes = [_tiny.grid_plane(24, 0.03, z=0.05 * k, scale=0.025, albedo=tuple(rng.uniform(0, 1, 3)))
+              for k in range(4)]
+    surf = S.Surfels.concat(planes)
+    sc = S.Scene(surf, np.array([0, surf.n]), [_tiny.lognormal_env(rng, 32, 16)], [_tiny.front_camera(res=40)],
+                 "gamma")
+    params = dict(gamma=3.7, k_max=3, cons=int(cons))
+    r = Renderer(sc, params=params)
+    r.forward()
+    ref, _ = _check_view(r, sc, 0)
+    assert ref["n_layers"].max() == 3
+    gpu, ref = _run(sc, 31 + int(cons), params=params)
+    _compare(gpu, ref)
+
+
 @pytest.mark.slow
 def test_backward_torus_sphere_100k():
     gpu, ref = _run(S.torus_sphere_100k(), 9)
