@@ -181,7 +181,16 @@ typedef struct ss_render_params {
     /* layer state kept by the forward for the backward (with_backward workspaces) */
     int32_t dense_layers;    /* layers per pixel held in planes of every pixel (0 = k_max: all of
                                 them, no pool); the layers past it go to layer_pool */
-    int32_t pad_;
+    int32_t zero_grad_in_forward;   /* 1: a forward that keeps backward state also clears the
+                                per-record gradient rows of the workspace (one 96-byte row per
+                                (view, surfel) record, written by the projection pass, where the
+                                stores cost little), and a backward called with it set adds into
+                                those rows without clearing them first.  Valid only for the
+                                backward that follows such a forward on the same workspace, in
+                                stream order, with nothing in between that could write the rows
+                                (inside CUDA graphs: both captured in the same graph); otherwise
+                                call the backward with 0.  0 (default): the backward clears the
+                                rows itself */
     int64_t layer_pool;      /* dense_layers < k_max: slots for the (pixel, layer) pairs past
                                 dense_layers, 64 bytes each (80 with cons); ss_stats.pool_layers
                                 of a forward is the number it needed.  More pairs than slots
@@ -377,7 +386,9 @@ ss_status ss_render_forward(const ss_batch_desc* b, const ss_surfels* s, const s
  * sum(d_aov * aov) w.r.t. the surfel parameters and the prefiltered maps.
  * All discrete decisions (support, cutoff, grouping, K_max) are held fixed.
  * d_aov may be NULL.  out_rgba/out_aov are the forward outputs.  Must follow
- * a ss_render_forward with with_backward workspace and the same inputs. */
+ * a ss_render_forward with with_backward workspace and the same inputs, one
+ * backward per forward: the backward turns the forward's per-pixel layer
+ * state into its own coefficients in place. */
 ss_status ss_render_backward(const ss_batch_desc* b, const ss_surfels* s, const ss_render_params* p,
                              const ss_env_desc* ed, const ss_env_maps* env, const float* out_rgba_dev,
                              const float* out_aov_dev, const float* d_rgba_dev, const float* d_aov_dev,
@@ -406,6 +417,14 @@ ss_status ss_read_stats(void* ws, ss_stats* out, void* stream);
  * the GPU work of a region (read before and after).  out: host int64.
  * Errors: SS_ERR_INVALID_ARG for a null out. */
 ss_status ss_launch_count(int64_t* out);
+
+/* Which CUDA graph capture, if any, the stream is recording into: *id = the
+ * capture's id (unique in the process), or 0 when the stream is not
+ * capturing.  A host query with no counterpart in the paper; it lets a
+ * caller pair a forward and a backward recorded in the same graph (see
+ * ss_render_params.zero_grad_in_forward).  out: host uint64.  Errors:
+ * SS_ERR_INVALID_ARG for a null id; SS_ERR_CUDA if the query fails. */
+ss_status ss_stream_capture_id(void* stream, uint64_t* id);
 
 /* Synchronise the stream and return (and clear) the device status word in
  * ws: SS_OK or an OR of SS_ERR_CAPACITY / SS_ERR_TIMEOUT / SS_ERR_NONFINITE. */

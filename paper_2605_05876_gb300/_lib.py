@@ -56,7 +56,7 @@ class ss_render_params(ctypes.Structure):
                 ("collect_stats", c_i32), ("fwd_warps", c_i32), ("bwd_warps", c_i32), ("pbwd_block", c_i32),
                 ("screen_grad", c_i32), ("mip_mode", c_i32), ("cons", c_i32), ("tile_w", c_i32), ("tile_h", c_i32),
                 ("stage_depth", c_i32), ("deterministic", c_i32), ("det_rows", c_i64), ("dense_layers", c_i32),
-                ("pad_", c_i32), ("layer_pool", c_i64), ("max_candidates", c_i64)]
+                ("zero_grad_in_forward", c_i32), ("layer_pool", c_i64), ("max_candidates", c_i64)]
 
 
 class ss_stats(ctypes.Structure):
@@ -143,6 +143,7 @@ EXPORTS = {
     "ss_box_downsample": (c_i32, [c_vp, c_i32, c_i32, c_i32, c_vp, c_vp]),
     "ss_read_stats": (c_i32, [c_vp, ctypes.c_void_p, c_vp]),
     "ss_launch_count": (c_i32, [ctypes.POINTER(ctypes.c_int64)]),
+    "ss_stream_capture_id": (c_i32, [c_vp, ctypes.POINTER(ctypes.c_uint64)]),
     "ss_profile_begin": (c_i32, []),
     "ss_profile_end": (c_i32, [ctypes.c_void_p]),
     "ss_default_adam": (None, [ctypes.POINTER(ss_adam_params)]),

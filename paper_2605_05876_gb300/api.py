@@ -143,12 +143,28 @@ class Renderer:
                                       int(self.with_backward), ctypes.byref(nb)), "ss_workspace_size")
         self.ws_bytes = nb.value
         self.ws = torch.empty(nb.value, dtype=torch.uint8, device=self.dev)
+        self._rows_clear = None   # a new workspace: its gradient rows hold nothing yet
+
+    def _capture_id(self) -> int:
+        cid = ctypes.c_uint64()
+        check(lib().ss_stream_capture_id(_stream(), ctypes.byref(cid)), "ss_stream_capture_id")
+        return int(cid.value)
 
     def forward(self):
-        check(lib().ss_render_forward(ctypes.byref(self.desc), ctypes.byref(self.surfels_struct()),
-                                      ctypes.byref(self.prm), ctypes.byref(self.ed), ctypes.byref(self.maps),
-                                      _ptr(self.rgba), _ptr(self.aov), _ptr(self.ws), self.ws_bytes, _stream()),
-              "ss_render_forward")
+        # with backward state, the forward also clears the per-record gradient
+        # rows (params zero_grad_in_forward); the first backward after it, in
+        # the same graph capture or none, then skips that clearing
+        self._rows_clear = None
+        self.prm.zero_grad_in_forward = int(self.with_backward)
+        try:
+            check(lib().ss_render_forward(ctypes.byref(self.desc), ctypes.byref(self.surfels_struct()),
+                                          ctypes.byref(self.prm), ctypes.byref(self.ed), ctypes.byref(self.maps),
+                                          _ptr(self.rgba), _ptr(self.aov), _ptr(self.ws), self.ws_bytes, _stream()),
+                  "ss_render_forward")
+        finally:
+            self.prm.zero_grad_in_forward = 0
+        if self.with_backward:
+            self._rows_clear = self._capture_id()
         return self.rgba, self.aov
 
     def zero_grads(self, share_from: "Renderer | None" = None):
@@ -190,18 +206,25 @@ class Renderer:
 
     def backward(self, d_rgba, d_aov=None, env_grad: bool = True):
         """Accumulate gradients of sum(d_rgba * rgba) + sum(d_aov * aov) into
-        self.grads (surfel params) and self.d_env (base env texels)."""
+        self.grads (surfel params) and self.d_env (base env texels).  One
+        backward per forward: it consumes the forward's layer state."""
         if not hasattr(self, "grads"):
             self.zero_grads()
         ssg = (_ptr(self.screen_grad_norm), _ptr(self.screen_grad_views)) if self.prm.screen_grad else (None, None)
         g = C.ss_surfel_grads(*(ctypes.c_void_p(self.grads[k].data_ptr()) for k in SURFEL_FIELDS), *ssg)
         ge = C.ss_env_map_grads(_ptr(self.d_irr), _ptr(self.d_spec))
-        check(lib().ss_render_backward(ctypes.byref(self.desc), ctypes.byref(self.surfels_struct()),
-                                       ctypes.byref(self.prm), ctypes.byref(self.ed), ctypes.byref(self.maps),
-                                       _ptr(self.rgba), _ptr(self.aov), _ptr(d_rgba.contiguous()),
-                                       _ptr(d_aov.contiguous() if d_aov is not None else None), ctypes.byref(g),
-                                       ctypes.byref(ge), _ptr(self.ws), self.ws_bytes, _stream()),
-              "ss_render_backward")
+        rows_clear = self._rows_clear is not None and self._rows_clear == self._capture_id()
+        self._rows_clear = None
+        self.prm.zero_grad_in_forward = int(rows_clear)
+        try:
+            check(lib().ss_render_backward(ctypes.byref(self.desc), ctypes.byref(self.surfels_struct()),
+                                           ctypes.byref(self.prm), ctypes.byref(self.ed), ctypes.byref(self.maps),
+                                           _ptr(self.rgba), _ptr(self.aov), _ptr(d_rgba.contiguous()),
+                                           _ptr(d_aov.contiguous() if d_aov is not None else None), ctypes.byref(g),
+                                           ctypes.byref(ge), _ptr(self.ws), self.ws_bytes, _stream()),
+                  "ss_render_backward")
+        finally:
+            self.prm.zero_grad_in_forward = 0
         if env_grad:
             self.env_backward()
         return self.grads

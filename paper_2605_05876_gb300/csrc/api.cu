@@ -58,6 +58,15 @@ extern "C" ss_status ss_launch_count(int64_t* out) {
     return SS_OK;
 }
 
+extern "C" ss_status ss_stream_capture_id(void* stream, uint64_t* id) {
+    if (!id) return SS_ERR_INVALID_ARG;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    unsigned long long cid = 0;
+    if (cudaStreamGetCaptureInfo((cudaStream_t)stream, &cs, &cid) != cudaSuccess) return SS_ERR_CUDA;
+    *id = cs == cudaStreamCaptureStatusActive ? (uint64_t)cid : 0;
+    return SS_OK;
+}
+
 extern "C" ss_status ss_profile_begin(void) {
     g_prof.on = true;
     for (auto& r : g_prof.recs) {
@@ -112,6 +121,7 @@ static ss_status check_knobs(const ss_render_params* p) {
     if (p->dense_layers < 0 || p->dense_layers > p->k_max) return SS_ERR_INVALID_ARG;
     if (p->layer_pool < 0 || p->layer_pool > 0xffffffffll) return SS_ERR_INVALID_ARG;
     if (p->max_candidates < 0 || p->max_candidates > 0xffffffffll) return SS_ERR_INVALID_ARG;
+    if (p->zero_grad_in_forward != 0 && p->zero_grad_in_forward != 1) return SS_ERR_INVALID_ARG;
     return SS_OK;
 }
 
@@ -601,7 +611,10 @@ extern "C" ss_status ss_render_backward(const ss_batch_desc* b, const ss_surfels
         a.det_cbits = (int)std::ceil(std::log2(contrib));
         if (a.det_cbits > 40) return SS_ERR_INVALID_ARG;   // the fixed-point sums would keep too few bits
     }
-    CK(cudaMemsetAsync(W.grad_rec, 0, sizeof(float) * SS_NGRAD * (size_t)L.total_records, st));
+    // the per-record gradient rows start at zero: cleared here, or by the
+    // projection pass of the forward that preceded this call
+    if (!p->zero_grad_in_forward)
+        CK(cudaMemsetAsync(W.grad_rec, 0, sizeof(float) * SS_NGRAD * (size_t)L.total_records, st));
     if (a.genv.irr || a.genv.spec)
         CK(cudaMemsetAsync(W.env_acc, 0, sizeof(float4) * SS_ACC_STRIDE * (size_t)W.env_texels * (size_t)L.n_scenes,
                            st));

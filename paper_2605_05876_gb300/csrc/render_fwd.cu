@@ -45,6 +45,20 @@ __global__ void __launch_bounds__(256, 4) project_kernel(ss_ws_view ws, ss_fwd_a
     const int vthis = blockIdx.y;
     const ss_view_layout& vl0 = L->v[vthis];
     const int64_t li = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (ws.grad_rec && a.with_backward && a.p.zero_grad_in_forward) {
+        // clear this block's gradient rows for the backward: the block's
+        // records are consecutive, so its rows are one span of float4s
+        // (rows of SS_NGRAD floats, 256-byte aligned base); evict-first
+        // stores, so the rows do not push the surfels and the prefiltered
+        // maps, which every view's blocks read again, out of L2
+        const int64_t b0 = blockIdx.x * (int64_t)blockDim.x;
+        const int64_t nrow = min((int64_t)blockDim.x, (int64_t)vl0.n_surfels - b0);
+        if (nrow > 0) {
+            float4* g = reinterpret_cast<float4*>(ws.grad_rec + (vl0.rec_off + b0) * SS_NGRAD);
+            const int n4 = (int)nrow * (SS_NGRAD / 4);
+            for (int k = threadIdx.x; k < n4; k += blockDim.x) __stcs(&g[k], make_float4(0.f, 0.f, 0.f, 0.f));
+        }
+    }
     if (li >= vl0.n_surfels) return;
     const int64_t i = vl0.surfel_begin + li;
     const int scene = vl0.scene;

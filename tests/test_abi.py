@@ -76,6 +76,8 @@ def test_host_side_argument_errors():
     n = ctypes.c_int64(-1)
     assert lib.ss_launch_count(ctypes.byref(n)) == 0 and n.value >= 0
     assert lib.ss_launch_count(None) == _lib.SS_ERR_INVALID_ARG
+    # the capture query rejects a null out before any CUDA call
+    assert lib.ss_stream_capture_id(None, None) == _lib.SS_ERR_INVALID_ARG
 
 
 def test_launch_shape_knobs_are_validated_on_the_host():
@@ -98,7 +100,8 @@ def test_launch_shape_knobs_are_validated_on_the_host():
                             ("pbwd_block", 4096, 1024), ("tile_w", 12, 8), ("tile_h", 2, 4),
                             ("stage_depth", 4, 3), ("mip_mode", 3, 2), ("screen_grad", 2, 1),
                             ("deterministic", 2, 1), ("det_rows", -1, 1 << 20), ("dense_layers", 17, 2),
-                            ("layer_pool", -1, 1000), ("max_candidates", -1, 1000)):
+                            ("layer_pool", -1, 1000), ("max_candidates", -1, 1000),
+                            ("zero_grad_in_forward", 2, 1)):
         q = _lib.ss_render_params()
         ctypes.memmove(ctypes.byref(q), ctypes.byref(p), ctypes.sizeof(q))
         setattr(q, knob, bad)
