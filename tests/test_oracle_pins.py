@@ -677,3 +677,42 @@ def test_coverage_gradient_is_gamma_over_2pi_transmittance(k_max):
     got = vs.leaf["n_f"].grad.numpy()
     np.testing.assert_allclose(got, expect, rtol=1e-10, atol=1e-15)
     assert np.all(got[layer < k_max] > 0)
+
+
+def test_background_enters_through_the_residual_transmittance():
+    """rgb = sum_k T_k alpha_k C_hat_k + T_{K+1} bg (Sec. 3.5.2): two
+    backgrounds differ by exactly (1 - A) * (bg' - bg) at every pixel,
+    covered or not, and leave the coverage and the AOVs alone (every other
+    pin renders on black, where a dropped background term is invisible)."""
+    rng = np.random.default_rng(5)
+    surf = _tiny.random_scene(rng, n=40, spread=0.3, scale=(0.03, 0.08))
+    cam = _tiny.front_camera(res=24)
+    env = env_state(_tiny.lognormal_env(rng), M.Params())
+    bg = np.array([0.3, 0.5, 0.7])
+    o0 = _render(surf, cam, env, M.Params())
+    o1 = _render(surf, cam, env, M.Params(bg=tuple(bg)))
+    A = o0["rgba"][:, 3]
+    assert (A == 0).sum() > 20 and ((A > 0.05) & (A < 0.95)).sum() > 20
+    np.testing.assert_allclose(o1["rgba"][:, :3] - o0["rgba"][:, :3], (1 - A)[:, None] * bg, rtol=0, atol=1e-14)
+    assert np.array_equal(o1["rgba"][:, 3], A) and np.array_equal(o1["aov"], o0["aov"])
+
+
+def test_lone_surfel_reconstructs_its_depth_and_materials():
+    """A lone fronto-parallel surfel's layer carries its own roughness,
+    metallic, normal and camera-space centre depth (Sec. 3.5.3: the Shepard
+    mean of one fragment is its value): the AOVs divided by the coverage
+    give them back at every covered pixel."""
+    z_w, rough, metal = 0.3, 0.37, 0.61
+    surf = _tiny.surfels([[0.02, -0.01, z_w]], scale=0.15, rough=rough, metal=metal)
+    cam = _tiny.front_camera(dist=3.0, res=32)
+    env = env_state(_tiny.const_env(), M.Params())
+    out = _render(surf, cam, env, M.Params())
+    A = out["rgba"][:, 3]
+    cov = A > 1e-3
+    assert cov.sum() > 50
+    f32 = lambda v: float(np.float32(v))
+    got = out["aov"][cov] / A[cov, None]
+    np.testing.assert_allclose(got[:, 3], f32(rough), rtol=1e-12)
+    np.testing.assert_allclose(got[:, 4], f32(metal), rtol=1e-12)
+    np.testing.assert_allclose(got[:, 5:8], np.broadcast_to([0.0, 0.0, 1.0], got[:, 5:8].shape), atol=1e-12)
+    np.testing.assert_allclose(got[:, 8], 3.0 - f32(z_w), rtol=1e-12)
