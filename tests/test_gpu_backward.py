@@ -115,6 +115,13 @@ def test_backward_tiny(seed, sigma_f):
     _compare(gpu, ref)
 
 
+def test_backward_unequal_focal_lengths():
+    """f_y = 1.3 f_x: the projection adjoint's f_x and f_y terms apart."""
+    from tests.test_gpu_forward import _aniso_scene
+    gpu, ref = _run(_aniso_scene(2), 4, params=dict(sigma_f=0.5))
+    _compare(gpu, ref)
+
+
 def test_backward_sphere_4k():
     gpu, ref = _run(S.sphere_4k(), 5)
     _compare(gpu, ref)

@@ -124,6 +124,24 @@ def test_forward_tiny_random(seed, sigma_f, res):
     _check_view(r, sc, 0)
 
 
+def _aniso_scene(seed):
+    """A camera with f_y = 1.3 f_x and a wider than high image (every other
+    case has square pixels), over a random scene."""
+    rng = np.random.default_rng(300 + seed)
+    surf = _tiny.random_scene(rng, n=300, spread=0.5, scale=(0.01, 0.08))
+    c = _tiny.front_camera(res=36, width=44)
+    cam = S.Camera(c.R, c.t, c.fx, 1.3 * c.fy, c.cx, c.cy, c.width, c.height, c.scene)
+    return S.Scene(surf, np.array([0, surf.n]), [_tiny.lognormal_env(rng, 64, 32)], [cam], "aniso")
+
+
+def test_forward_unequal_focal_lengths():
+    sc = _aniso_scene(1)
+    r = _renderer(sc, params=dict(sigma_f=0.5))
+    r.forward()
+    assert r.read_status() == 0
+    _check_view(r, sc, 0)
+
+
 @pytest.mark.parametrize("k_max", [1, 2, 16])
 def test_forward_layer_cap(k_max):
     rng = np.random.default_rng(7)

@@ -482,16 +482,23 @@ def brute_force(surf, cam, prm, ch, cons=False):
     return rgba, aov, unsure
 
 
-@pytest.mark.parametrize("seed,mip", [(21, "centre"), (22, "centre"), (23, "pixel"), (24, "pixel"), (25, "none")])
-def test_oracle_matches_brute_force(seed, mip):
+@pytest.mark.parametrize("seed,mip,aniso", [(21, "centre", False), (22, "centre", False), (23, "pixel", False),
+                                             (24, "pixel", False), (25, "none", False), (26, "centre", True),
+                                             (27, "pixel", True)])
+def test_oracle_matches_brute_force(seed, mip, aniso):
     """The oracle against the independent brute-force renderer, for the
     centre-precomputed MIP filter (the method), the per-pixel Jacobian of
     the Sec. 4.4.2 ablation (J by finite differences of the 3x3 solve at
-    every pixel) and no filter."""
+    every pixel) and no filter; `aniso`: a camera with f_y = 1.3 f_x and a
+    wider than high image, so that a swap of the focal lengths or of the
+    principal point's coordinates fails."""
     rng = np.random.default_rng(seed)
     prm = M.Params(sigma_f=0.5 if seed in (21, 23) else 1.5, mip_mode=mip)
     surf = _tiny.random_scene(rng, n=40, spread=0.35, scale=(0.08, 0.2))
     cam = _tiny.front_camera(res=28)
+    if aniso:
+        cam = _tiny.front_camera(res=24, width=34)
+        cam = S.Camera(cam.R, cam.t, cam.fx, 1.3 * cam.fy, cam.cx, cam.cy, cam.width, cam.height, cam.scene)
     env = env_state(_tiny.lognormal_env(rng), prm)
     out = _render(surf, cam, env, prm)
     Sd = M.to_torch_surfels(surf)
