@@ -18,7 +18,10 @@ special cases of Eq. ibl that the paper's definitions fix: F0 = 0.04 and
 k_d = 0.96 for a dielectric (m = 0), F0 = albedo and k_d = 0 for a metal
 (m = 1).  A transposed table lookup, swapped Fresnel terms, a reflected
 vector of the wrong sign, another azimuth convention, a wrong level
-coordinate or a diffuse lookup along another direction each fail one case.
+coordinate, a diffuse lookup along another direction, a lookup clamped
+instead of wrapped at the azimuth seam, the irradiance of a back-facing
+surfel read at its unflipped normal, or near-plane culling by the centre
+depth instead of z_start each fail one case.
 Nothing here uses the CUDA path.
 """
 import math
@@ -221,3 +224,76 @@ def test_dielectric_diffuse_reads_the_irradiance_along_the_normal():
     np.testing.assert_allclose(got, 0.96 * ALBEDO * Ld + Ls * (0.04 * b1 + b2), rtol=1e-9, atol=0)
     # neighbouring irradiance rows differ, so a lookup along another direction shows
     assert np.abs(irr[4, 0] - irr[5, 0]).min() > 1e-3 and np.abs(irr[6, 0] - irr[5, 0]).min() > 1e-3
+
+
+def _rows_map(values, W=32):
+    """A map whose row k holds values[k] everywhere (rows constant)."""
+    v = np.asarray(values, np.float64)
+    return np.broadcast_to(v[:, None, :], (v.shape[0], W, 3)).copy()
+
+
+def _dark_levels():
+    return [np.zeros((32 >> i, 64 >> i, 3)) for i in range(6)]
+
+
+def test_irradiance_lookup_wraps_across_the_azimuth_seam():
+    """The equirect maps wrap in azimuth: a normal at phi = pi (u = 1, the
+    seam) reads half the last column and half the first, and a quarter
+    texel to either side three quarters of the nearer one.  A dielectric in a
+    dark specular environment shows c = 0.96 rho L_d, with L_d = (A + B) / 2
+    for last column A and first column B (a clamped lookup reads A alone)."""
+    Hi, Wi, k = 16, 32, 7
+    irr = _rows_map(np.full((Hi, 3), 0.3), Wi)
+    A, B = np.array([1.0, 2.0, 3.0]), np.array([3.0, 0.5, 0.25])
+    irr[:, -1] = A
+    irr[:, 0] = B
+    th = (k + 0.5) / Hi * math.pi                     # a row centre: no blend between rows
+    n = np.array([0.0, math.cos(th), math.sin(th)])   # phi = atan2(0, -sin th) = pi
+    w_o = rotate_towards(n, 0.6)
+    got = shade(n, w_o, ALBEDO, 0.4, 0.0, irr, _dark_levels(), None)[:3]
+    np.testing.assert_allclose(got, 0.96 * ALBEDO * 0.5 * (A + B), rtol=1e-9, atol=0)
+    # a quarter texel to either side of the seam: 3/4 of the nearer column
+    for u, wA in ((1.0 - 0.25 / Wi, 0.75), (0.25 / Wi, 0.25)):
+        n = texel_dir(u, (k + 0.5) / Hi)
+        got = shade(n, rotate_towards(n, 0.6), ALBEDO, 0.4, 0.0, irr, _dark_levels(), None)[:3]
+        np.testing.assert_allclose(got, 0.96 * ALBEDO * (wA * A + (1 - wA) * B), rtol=1e-9, atol=0)
+
+
+def test_back_facing_dielectric_reads_the_irradiance_at_the_flipped_normal():
+    """The diffuse term of a back-facing surfel is looked up along the
+    normal turned toward the viewer (two-sided surfels): with every
+    irradiance row distinct, c = 0.96 rho L_d(n_s), not L_d(-n_s)."""
+    Hi = 16
+    vals = np.stack([0.2 + 0.1 * np.arange(Hi), 1.0 + 0.05 * np.arange(Hi) ** 2, 3.0 - 0.15 * np.arange(Hi)], 1)
+    irr = _rows_map(vals)
+    k = 4
+    n_s = polar_dir((k + 0.5) / Hi * math.pi, 0.9)     # row k; -n_s lies in row Hi - 1 - k
+    w_o = rotate_towards(n_s, 0.5)
+    got = shade(-n_s, w_o, ALBEDO, 0.3, 0.0, irr, _dark_levels(), None)
+    np.testing.assert_allclose(got[:3], 0.96 * ALBEDO * vals[k], rtol=1e-9, atol=0)
+    np.testing.assert_allclose(got[8:11], n_s, atol=1e-12)
+    assert np.abs(vals[k] - vals[Hi - 1 - k]).min() > 0.1
+
+
+def test_surfel_reaching_in_front_of_the_near_plane_is_culled():
+    """z_near (0.01; not given by the paper) culls a surfel whose depth
+    interval [z_c - eps, z_c + eps], eps = r_cut sqrt(t_uz^2 + t_vz^2),
+    starts at or before it, although its centre lies beyond: a surfel tilted
+    60 degrees with scale 0.05 has eps = 0.13, so at z_c = 0.1 it is culled
+    and at z_c = 0.2 it is kept."""
+    q = quat_for_normal([0.0, math.sin(math.pi / 3), math.cos(math.pi / 3)])
+    cam = {"R": torch.eye(3, dtype=F64), "t": torch.zeros(3, dtype=F64),
+           "fx": 100.0, "fy": 100.0, "cx": 32.0, "cy": 32.0, "width": 64, "height": 64}
+    prm = M.Params(lut_n=LUT_N)
+    irr, levels = M.env_prefilter(np.ones((32, 64, 3)), 6, 32, 16)
+    S = {"pos": torch.tensor([[0.0, 0.0, 0.1], [0.0, 0.0, 0.2]], dtype=F64),
+         "quat": torch.tensor(np.stack([q, q]), dtype=F64),
+         "log_scale": torch.full((2, 2), math.log(0.05), dtype=F64),
+         "albedo": torch.full((2, 3), 0.5, dtype=F64), "roughness": torch.full((2,), 0.5, dtype=F64),
+         "metallic": torch.zeros(2, dtype=F64)}
+    rec = M.records(S, cam, torch.from_numpy(irr), [torch.from_numpy(l) for l in levels],
+                    torch.from_numpy(M.brdf_lut(LUT_N, 16)), prm)
+    eps = 3.0 * 0.05 * math.sin(math.pi / 3)
+    np.testing.assert_allclose(rec["zs"].numpy(), [0.1 - eps, 0.2 - eps], rtol=1e-12)
+    assert rec["zs"][0] < prm.z_near < 0.1 and rec["zs"][1] > prm.z_near
+    assert rec["valid"].tolist() == [False, True]
