@@ -78,6 +78,24 @@ SLIPS = {
     "level_roughness": ("c", "double r = (double)i / (L - 1);", "double r = (double)i / L;"),
     "box_norm": ("c", "out[(b * W + a) * 3 + c] = s / (bw * bh);", "out[(b * W + a) * 3 + c] = s / bw;"),
     "adjoint_norm": ("c", "acc[c] += w / norm[t] * d_out[t * 3 + c];", "acc[c] += w * d_out[t * 3 + c];"),
+    # depth consolidation (Eq. cons_loss) and the densification statistic (Eq. ss_grad) (model.py)
+    "cons_signed_gap": ("model", "torch.abs(zbar[:, :, None] - zbar[:, None, :])", "(zbar[:, :, None] - zbar[:, None, :])"),
+    "cons_intra_weight": ("model", "intra = (wl ** 2 * torch.where(present, var, torch.zeros_like(var))).sum(1)",
+                          "intra = (wl * torch.where(present, var, torch.zeros_like(var))).sum(1)"),
+    "cons_unweighted_var": ("model", "dev2 = w * (z_f - zbar[row_t, layer]) ** 2", "dev2 = (z_f - zbar[row_t, layer]) ** 2"),
+    "ssg_unscaled": ("model", "g[name] = (dLdT * T[sid, 2, 2]).numpy()", "g[name] = dLdT.numpy()"),
+    "ssg_no_nf_term": ("model", "(pf[\"Sinv\"].grad * dS[sid]).sum((1, 2)) + pf[\"n_f\"].grad * dn[sid])",
+                       "(pf[\"Sinv\"].grad * dS[sid]).sum((1, 2)))"),
+    "ssg_signed_sum": ("model", "norm = np.sqrt(g[\"gx\"] ** 2 + g[\"gy\"] ** 2)", "norm = g[\"gx\"] + g[\"gy\"]"),
+    # density control (density.py)
+    "split_scale_test": ("density", "(s_max > np.asarray(mean_dist, np.float64))", "(s_max < np.asarray(mean_dist, np.float64))"),
+    "prune_no_rcut": ("density", "act[np.asarray(nn_dist, np.float64) > r_cut * s_max] = PRUNE",
+                      "act[np.asarray(nn_dist, np.float64) > s_max] = PRUNE"),
+    "prune_visible": ("density", "act[~(gn > 0)] = PRUNE", "act[gn < 0] = PRUNE"),
+    "split_full_offset": ("density", "half = 0.5 * s_max[:, None] * t", "half = s_max[:, None] * t"),
+    "split_minor_axis": ("density", "use_u = ls[:, 0] >= ls[:, 1]", "use_u = ls[:, 0] < ls[:, 1]"),
+    "split_over_prune": ("density", "    rows = act.copy()", "    act[split] = SPLIT\n    rows = act.copy()"),
+    "neighbours_unoriented": ("density", "same = (Nn[r0:r1] @ Nn.T) >= cos_min", "same = np.abs(Nn[r0:r1] @ Nn.T) >= cos_min"),
     # Adam (optim.py)
     "adam_bias1": ("optim", "m_hat = m / (1.0 - beta1 ** step)", "m_hat = m"),
     "adam_bias2": ("optim", "v_hat = v / (1.0 - beta2 ** step)", "v_hat = v"),

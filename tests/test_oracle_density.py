@@ -85,21 +85,22 @@ def test_plan_rules():
     0 zero gradient -> prune;  1 nearest neighbour beyond 0.3 -> prune;
     2 g_bar = tau_g and s_max > d_bar -> split;  3 s_max < d_bar -> keep;
     4 g_bar < tau_g -> keep;  5 as 2 but d_bar only a lower bound -> keep;
-    6 nearest distance a lower bound above the support -> prune.
+    6 nearest distance a lower bound above the support -> prune;
+    7 nearest neighbour beyond s_max but within the support 0.3 -> keep.
     With pruning disabled, 1 and 6 (which also meet the split rule) split."""
-    ls = np.log(np.array([[0.1, 0.05]] * 7))
-    g_norm = np.array([0.0, 3.0, 3.0, 3.0, 2.9, 3.0, 3.0])
-    g_views = np.array([0.0, 3.0, 3.0, 3.0, 3.0, 3.0, 3.0])
-    mean = np.array([0.05, 0.05, 0.08, 0.12, 0.05, 0.05, 0.05])
-    nn = np.array([0.01, 0.31, 0.02, 0.02, 0.02, 0.02, 0.35])
-    flags = np.array([0, 0, 0, 0, 0, 1, 2])
+    ls = np.log(np.array([[0.1, 0.05]] * 8))
+    g_norm = np.array([0.0, 3.0, 3.0, 3.0, 2.9, 3.0, 3.0, 3.0])
+    g_views = np.array([0.0, 3.0, 3.0, 3.0, 3.0, 3.0, 3.0, 3.0])
+    mean = np.array([0.05, 0.05, 0.08, 0.12, 0.05, 0.05, 0.05, 0.12])
+    nn = np.array([0.01, 0.31, 0.02, 0.02, 0.02, 0.02, 0.35, 0.2])
+    flags = np.array([0, 0, 0, 0, 0, 1, 2, 0])
     act, off = D.plan(ls, g_norm, g_views, mean, nn, flags, tau_g=1.0, r_cut=3.0)
-    np.testing.assert_array_equal(act, [D.PRUNE, D.PRUNE, D.SPLIT, D.KEEP, D.KEEP, D.KEEP, D.PRUNE])
-    np.testing.assert_array_equal(off, [0, 0, 0, 2, 3, 4, 5, 5])
+    np.testing.assert_array_equal(act, [D.PRUNE, D.PRUNE, D.SPLIT, D.KEEP, D.KEEP, D.KEEP, D.PRUNE, D.KEEP])
+    np.testing.assert_array_equal(off, [0, 0, 0, 2, 3, 4, 5, 5, 6])
     act, _ = D.plan(ls, g_norm, g_views, mean, nn, flags, tau_g=1.0, ops=D.OP_PRUNE_VISIBLE)
-    np.testing.assert_array_equal(act, [D.PRUNE] + [D.KEEP] * 6)
+    np.testing.assert_array_equal(act, [D.PRUNE] + [D.KEEP] * 7)
     act, _ = D.plan(ls, g_norm, g_views, mean, nn, flags, tau_g=1.0, ops=D.OP_SPLIT)
-    np.testing.assert_array_equal(act, [D.KEEP, D.SPLIT, D.SPLIT, D.KEEP, D.KEEP, D.KEEP, D.SPLIT])
+    np.testing.assert_array_equal(act, [D.KEEP, D.SPLIT, D.SPLIT, D.KEEP, D.KEEP, D.KEEP, D.SPLIT, D.KEEP])
 
 
 def test_split_children_closed_form():
