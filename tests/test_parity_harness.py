@@ -86,3 +86,68 @@ def test_ambiguous_pixel_accepts_either_outcome_and_nothing_else(view, monkeypat
     _parity.check_flip_fraction(2, 20000)
     with pytest.raises(AssertionError):
         _parity.check_flip_fraction(3, 20000)
+
+
+def _grad_blocks(rng, n=500, env_shape=(1, 32, 64, 3)):
+    ref = {"pos": rng.normal(size=(n, 3)), "quat": rng.normal(size=(n, 4)), "log_scale": rng.normal(size=(n, 2)),
+           "albedo": rng.normal(size=(n, 3)), "roughness": rng.normal(size=n), "metallic": rng.normal(size=n),
+           "env": rng.normal(size=env_shape)}
+    gpu = {k: v.astype(np.float32).astype(np.float64) for k, v in ref.items()}
+    gpu["_near"] = np.zeros(n, bool)
+    return gpu, ref
+
+
+def test_gradient_comparison_flags_block_and_element_deviations():
+    """The gradient bound of the backward parity tests (per block
+    |g - g_ref| / |g_ref| <= 1e-4, per element 1e-3 |g_ref| + 1e-5 max|g_ref|):
+    FP32 rounding passes; one element at 1.5x its bound, or a whole block
+    scaled by 1 + 2e-4, fails; 0.5x and 1 + 5e-5 pass; a surfel set aside near
+    a lookup boundary is not compared, but more than 1% of them fail."""
+    from tests import test_gpu_backward as B
+    rng = np.random.default_rng(62)
+    gpu, ref = _grad_blocks(rng)
+    B._compare(gpu, ref)
+    amax = np.abs(ref["albedo"]).max()
+    i = 7
+    bound = B.ELEM_RTOL * abs(ref["albedo"][i, 1]) + B.ELEM_ATOL * amax
+    for factor, fails in ((1.5, True), (0.5, False)):
+        g = dict(gpu, albedo=gpu["albedo"].copy())
+        g["albedo"][i, 1] = ref["albedo"][i, 1] + factor * bound
+        if fails:
+            with pytest.raises(AssertionError, match="albedo"):
+                B._compare(g, ref)
+        else:
+            B._compare(g, ref)
+    for factor, fails in ((1 + 2e-4, True), (1 + 5e-5, False)):
+        g = dict(gpu, metallic=ref["metallic"] * factor)
+        if fails:
+            with pytest.raises(AssertionError, match="metallic"):
+                B._compare(g, ref)
+        else:
+            B._compare(g, ref)
+    # a position compares against the surfel's vector norm, not the component:
+    # a small component may move by half the norm-relative bound, far more
+    # than a component-relative bound would allow
+    r2 = dict(ref, pos=ref["pos"].copy())
+    r2["pos"][3] = [1e-4, 1.0, 1.0]
+    g = dict(gpu, pos=r2["pos"].copy())
+    dev = 0.5 * B.ELEM_RTOL * np.linalg.norm(r2["pos"][3])
+    assert dev > B.ELEM_RTOL * 1e-4 + B.ELEM_ATOL * np.abs(r2["pos"]).max()
+    g["pos"][3, 0] += dev
+    B._compare(g, r2)
+    # near a lookup boundary: set aside, up to 1% of the surfels
+    g = dict(gpu, roughness=gpu["roughness"].copy(), _near=gpu["_near"].copy())
+    g["roughness"][11] += 1.0
+    g["_near"][11] = True
+    B._compare(g, ref)
+    g["_near"][:10] = True
+    with pytest.raises(AssertionError, match="near a lookup"):
+        B._compare(g, ref)
+    # a block the oracle says is zero must be zero
+    z = dict(ref, metallic=np.zeros_like(ref["metallic"]))
+    g = dict(gpu, metallic=np.zeros_like(ref["metallic"]))
+    B._compare(g, z)
+    g["metallic"] = g["metallic"].copy()
+    g["metallic"][0] = 1e-30
+    with pytest.raises(AssertionError):
+        B._compare(g, z)
