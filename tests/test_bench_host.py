@@ -3,25 +3,38 @@ recorded DRAM traffic is used only while the kernel sources it was taken on
 are unchanged, and the algorithmic bytes of the batched and per-view forms
 differ only in the once-per-batch terms."""
 import os
+import pathlib
 import shutil
+
+import pytest
 
 import bench
 
 
-def _tree(tmp_path):
-    csrc = tmp_path / "paper_2605_05876_gb300" / "csrc"
+@pytest.fixture
+def scratch(request):
+    """A fresh directory under the repository's git-ignored _build/."""
+    d = pathlib.Path(bench.ROOT) / "_build" / "test_bench_host" / request.node.name
+    shutil.rmtree(d, ignore_errors=True)
+    d.mkdir(parents=True)
+    yield d
+    shutil.rmtree(d, ignore_errors=True)
+
+
+def _tree(root):
+    csrc = root / "paper_2605_05876_gb300" / "csrc"
     csrc.mkdir(parents=True)
     for f in bench.RASTER_SOURCES:
         shutil.copy(os.path.join(bench.ROOT, "paper_2605_05876_gb300", "csrc", f), csrc / f)
-    (tmp_path / "profiles").mkdir()
+    (root / "profiles").mkdir()
     return csrc
 
 
-def test_recorded_traffic_follows_the_source_hash(tmp_path, monkeypatch):
-    csrc = _tree(tmp_path)
-    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+def test_recorded_traffic_follows_the_source_hash(scratch, monkeypatch):
+    csrc = _tree(scratch)
+    monkeypatch.setattr(bench, "ROOT", str(scratch))
     h = bench.source_hash()
-    (tmp_path / "profiles" / "traffic.txt").write_text(
+    (scratch / "profiles" / "traffic.txt").write_text(
         "# kernel workload bytes hash\n"
         f"raster_bwd some_workload 12345 {h}\n"
         "raster_fwd some_workload 999 0123456789ab\n")
@@ -34,9 +47,9 @@ def test_recorded_traffic_follows_the_source_hash(tmp_path, monkeypatch):
     assert bench.recorded_traffic("raster_bwd", "some_workload") is None
 
 
-def test_missing_traffic_file_reads_as_unmeasured(tmp_path, monkeypatch):
-    _tree(tmp_path)
-    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+def test_missing_traffic_file_reads_as_unmeasured(scratch, monkeypatch):
+    _tree(scratch)
+    monkeypatch.setattr(bench, "ROOT", str(scratch))
     assert bench.recorded_traffic("raster_bwd", "some_workload") is None
 
 
