@@ -94,8 +94,8 @@ SS_MAX_ADAM_GROUPS = 16
 
 
 class ss_adam_group(ctypes.Structure):
-    _fields_ = [("param", c_vp), ("grad", c_vp), ("m", c_vp), ("v", c_vp), ("act", c_vp), ("n", c_i64),
-                ("lr", c_f), ("activation", c_i32)]
+    _fields_ = [("param_dev", c_vp), ("grad_dev", c_vp), ("m_dev", c_vp), ("v_dev", c_vp), ("act_dev", c_vp),
+                ("n", c_i64), ("lr", c_f), ("activation", c_i32)]
 
 
 class ss_density_params(ctypes.Structure):

@@ -6,7 +6,8 @@ import re
 
 from paper_2605_05876_gb300 import _lib, build
 
-HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "ss3d.h")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ss3d.h")
 
 
 def declared_functions():
@@ -35,6 +36,40 @@ def test_struct_sizes_match_header():
     assert ctypes.sizeof(_lib.ss_render_params) == 128
     assert ctypes.sizeof(_lib.ss_surfel_grads) == 64
     assert ctypes.sizeof(_lib.ss_stats) == 88
+
+
+def test_struct_layouts_match_the_header_field_by_field():
+    """Every struct the binding mirrors has the header's size and, field by
+    field, the header's names and offsets: a C program generated from the
+    ctypes definitions prints sizeof and offsetof of each (gcc, the plain C
+    view of include/ss3d.h), so a field renamed, reordered or retyped on
+    either side fails here."""
+    import subprocess
+    structs = [v for v in vars(_lib).values()
+               if isinstance(v, type) and issubclass(v, ctypes.Structure) and hasattr(v, "_fields_")]
+    assert len(structs) >= 12
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ss3d.h"', "int main(void) {"]
+    for st in structs:
+        n = st.__name__
+        lines.append(f'    printf("{n} sizeof %zu\\n", sizeof({n}));')
+        for f in st._fields_:
+            lines.append(f'    printf("{n} {f[0]} %zu\\n", offsetof({n}, {f[0]}));')
+    lines += ["    return 0;", "}"]
+    out_dir = os.path.join(ROOT, "_build", "abi_layout")
+    os.makedirs(out_dir, exist_ok=True)
+    src, exe = os.path.join(out_dir, "layout.c"), os.path.join(out_dir, "layout")
+    with open(src, "w") as fh:
+        fh.write("\n".join(lines) + "\n")
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", exe, src])
+    got = {}
+    for line in subprocess.check_output([exe], text=True).splitlines():
+        n, f, v = line.split()
+        got[(n, f)] = int(v)
+    for st in structs:
+        n = st.__name__
+        assert got[(n, "sizeof")] == ctypes.sizeof(st), n
+        for f in st._fields_:
+            assert got[(n, f[0])] == getattr(st, f[0]).offset, (n, f[0])
 
 
 def test_host_side_argument_errors():
