@@ -72,6 +72,41 @@ def test_struct_layouts_match_the_header_field_by_field():
             assert got[(n, f[0])] == getattr(st, f[0]).offset, (n, f[0])
 
 
+def _c_kind(decl: str) -> str:
+    """Kind of a C parameter declaration: ptr, i32, i64, u32 or u64 (size_t
+    is 64-bit unsigned on every target here), f32, f64."""
+    decl = " ".join(decl.split())
+    if "*" in decl:
+        return "ptr"
+    words = decl.replace("const ", "").split()
+    t = words[0]
+    return {"int32_t": "i32", "int": "i32", "ss_status": "i32", "int64_t": "i64", "uint32_t": "u32",
+            "uint64_t": "u64", "size_t": "u64", "float": "f32", "double": "f64"}[t]
+
+
+def _ctypes_kind(a) -> str:
+    if a in (ctypes.c_void_p, ctypes.c_char_p) or (isinstance(a, type) and issubclass(a, ctypes._Pointer)):
+        return "ptr"
+    return {ctypes.c_int32: "i32", ctypes.c_int64: "i64", ctypes.c_uint32: "u32", ctypes.c_uint64: "u64",
+            ctypes.c_float: "f32", ctypes.c_double: "f64"}[a]
+
+
+def test_binding_signatures_match_the_header():
+    """Each declared function's parameters, in order, have the kinds of the
+    binding's argtypes (pointer, 32/64-bit integer, float), and its return
+    type the binding's restype: an int32 passed for an int64 or a swapped
+    pair of arguments fails here."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    protos = re.findall(r"^\s*(ss_status|void|const char\*)\s+(ss_\w+)\s*\(([^;]*?)\)\s*;", src, flags=re.M | re.S)
+    assert {n for _, n, _ in protos} == set(_lib.EXPORTS)
+    for ret, name, args in protos:
+        args = args.strip()
+        want = [] if args in ("", "void") else [_c_kind(x) for x in args.split(",")]
+        restype, argtypes = _lib.EXPORTS[name]
+        assert [_ctypes_kind(t) for t in argtypes] == want, name
+        assert restype == {"ss_status": ctypes.c_int32, "void": None, "const char*": ctypes.c_char_p}[ret], name
+
+
 def test_host_side_argument_errors():
     """Host-detectable errors return SS_ERR_INVALID_ARG without touching a GPU."""
     lib = _lib.lib()
