@@ -62,6 +62,9 @@ typedef int ss_status;
 #define SS_MAX_SCENES 64
 #define SS_KMAX_LIMIT 16      /* App. A: at most 16 composited layers */
 #define SS_N_AOV 9            /* albedo(3), roughness, metallic, normal(3), depth */
+#define SS_MIP_CENTRE 0       /* values of ss_render_params.mip_mode (see there) */
+#define SS_MIP_NONE 1
+#define SS_MIP_PIXEL 2
 
 /* One view.  80 bytes; arrays of it are read by both host and device. */
 typedef struct ss_camera {

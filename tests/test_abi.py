@@ -107,6 +107,17 @@ def test_binding_signatures_match_the_header():
         assert restype == {"ss_status": ctypes.c_int32, "void": None, "const char*": ctypes.c_char_p}[ret], name
 
 
+def test_constants_match_the_header():
+    """Every integer #define SS_* of the header is a constant of the binding
+    with the same value, and the binding has no SS_* constant the header
+    lacks."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    defs = {n: eval(v.strip()) for n, v in re.findall(r"^#define (SS_[A-Z0-9_]+) ([^\n]+)$", src, flags=re.M)}
+    ours = {n: v for n, v in vars(_lib).items() if n.startswith("SS_") and isinstance(v, int)}
+    assert len(defs) >= 30
+    assert defs == ours
+
+
 def test_host_side_argument_errors():
     """Host-detectable errors return SS_ERR_INVALID_ARG without touching a GPU."""
     lib = _lib.lib()
