@@ -60,6 +60,9 @@ typedef int ss_status;
 
 #define SS_MAX_VIEWS 256
 #define SS_MAX_SCENES 64
+#define SS_MAX_RECORDS 0xfffffffell   /* (view, surfel) records of a batch: sum over the views of
+                                         their scene's surfels (32-bit record indices) */
+#define SS_MAX_TILES (1ll << 28)       /* screen tiles of a batch, over all views */
 #define SS_KMAX_LIMIT 16      /* App. A: at most 16 composited layers */
 #define SS_N_AOV 9            /* albedo(3), roughness, metallic, normal(3), depth */
 #define SS_MIP_CENTRE 0       /* values of ss_render_params.mip_mode (see there) */
@@ -351,7 +354,8 @@ ss_status ss_env_prefilter_backward_ordered(const ss_env_desc* d, int32_t n_envs
  * the rows and per-record lists of the fixed-order sums).  Requires
  * p->max_instances > 0.
  * Host only (reads no device memory).  Errors: SS_ERR_INVALID_ARG for bad
- * sizes, an invalid ed or a launch shape (fwd_warps, bwd_warps, pbwd_block)
+ * sizes (among them a batch past SS_MAX_RECORDS records or SS_MAX_TILES
+ * tiles), an invalid ed or a launch shape (fwd_warps, bwd_warps, pbwd_block)
  * without a compiled kernel; the render calls reject the same values. */
 ss_status ss_workspace_size(const ss_batch_desc* b, const ss_render_params* p, const ss_env_desc* ed,
                             int32_t with_backward, size_t* bytes);

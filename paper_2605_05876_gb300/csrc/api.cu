@@ -194,6 +194,8 @@ static ss_status build_layout(const ss_batch_desc* b, const ss_render_params* p,
         vl.height = c.height;
         vl.tiles_x = (c.width + (1 << L->tw_log2) - 1) >> L->tw_log2;
         vl.tiles_y = (c.height + (1 << L->th_log2) - 1) >> L->th_log2;
+        // (tile, block) items are numbered tile * 8 + block in 32 bits
+        if ((int64_t)tiles + (int64_t)vl.tiles_x * vl.tiles_y > SS_MAX_TILES) return SS_ERR_INVALID_ARG;
         vl.tile_off = tiles;
         vl.pixel_off = pix;
         vl.rec_off = rec;
@@ -206,6 +208,9 @@ static ss_status build_layout(const ss_batch_desc* b, const ss_render_params* p,
         rec += ns;
     }
     for (int s = prev_scene + 1; s <= SS_MAX_SCENES; ++s) L->scene_view_begin[s] = b->n_views;
+    // record indices are 32-bit in the instance keys and the block lists, and
+    // 0xffffffff marks an unused row
+    if (rec > SS_MAX_RECORDS) return SS_ERR_INVALID_ARG;
     L->total_tiles = tiles;
     L->total_pixels = pix;
     L->total_records = rec;

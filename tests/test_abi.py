@@ -112,10 +112,42 @@ def test_constants_match_the_header():
     with the same value, and the binding has no SS_* constant the header
     lacks."""
     src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
-    defs = {n: eval(v.strip()) for n, v in re.findall(r"^#define (SS_[A-Z0-9_]+) ([^\n]+)$", src, flags=re.M)}
+    lits = re.findall(r"^#define (SS_[A-Z0-9_]+) ([^\n]+)$", src, flags=re.M)
+    # C integer literals: drop the suffixes (1ll, 0xfffffffell, 8u)
+    defs = {n: eval(re.sub(r"(?<=[0-9a-fA-F])(?:ull|ULL|ll|LL|u|U|l|L)\b", "", v.strip())) for n, v in lits}
     ours = {n: v for n, v in vars(_lib).items() if n.startswith("SS_") and isinstance(v, int)}
     assert len(defs) >= 30
     assert defs == ours
+
+
+def test_batch_limits_are_checked_on_the_host():
+    """Record indices are 32-bit (SS_MAX_RECORDS) and (tile, block) items are
+    numbered in 32 bits (SS_MAX_TILES): a batch past either is refused by the
+    workspace query, one at the limit is planned."""
+    lib = _lib.lib()
+    p = _lib.ss_render_params()
+    lib.ss_default_params(ctypes.byref(p))
+    p.max_instances = 1000
+    nb = ctypes.c_size_t()
+
+    def query(n_views, n_surfels, w=16, h=16, tile=(8, 4)):
+        p.tile_w, p.tile_h = tile
+        cams = (_lib.ss_camera * n_views)()
+        for c in cams:
+            c.width, c.height, c.fx, c.fy = w, h, 10.0, 10.0
+        off = (ctypes.c_int64 * 2)(0, n_surfels)
+        d = _lib.ss_batch_desc(1, n_views, off, cams, None)
+        return lib.ss_workspace_size(ctypes.byref(d), ctypes.byref(p), None, 0, ctypes.byref(nb))
+
+    # records: views x the scene's surfels
+    assert query(255, 1 << 24) == 0                              # 4.28e9 records
+    assert query(256, 1 << 24) == _lib.SS_ERR_INVALID_ARG         # 2^32 records
+    assert query(2, _lib.SS_MAX_RECORDS // 2) == 0                # exactly SS_MAX_RECORDS
+    assert query(3, 0x55555555) == _lib.SS_ERR_INVALID_ARG        # 0xffffffff, scenes within their limit
+    assert query(3, 0x55555554) == 0
+    # tiles: 8 x 4 tiles of a 32768^2 view = 2^25 each
+    assert query(8, 10, 32768, 32768) == 0                        # 2^28 tiles
+    assert query(9, 10, 32768, 32768) == _lib.SS_ERR_INVALID_ARG
 
 
 def test_host_side_argument_errors():
