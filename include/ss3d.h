@@ -62,7 +62,7 @@ typedef int ss_status;
 #define SS_MAX_SCENES 64
 #define SS_MAX_RECORDS 0xfffffffell   /* (view, surfel) records of a batch: sum over the views of
                                          their scene's surfels (32-bit record indices) */
-#define SS_MAX_TILES (1ll << 28)       /* screen tiles of a batch, over all views */
+#define SS_MAX_TILES (1ll << 27)       /* screen tiles of a batch, over all views */
 #define SS_KMAX_LIMIT 16      /* App. A: at most 16 composited layers */
 #define SS_N_AOV 9            /* albedo(3), roughness, metallic, normal(3), depth */
 #define SS_MIP_CENTRE 0       /* values of ss_render_params.mip_mode (see there) */

@@ -26,7 +26,7 @@ SS_ERR_CUDA = 32
 SS_MAX_VIEWS = 256
 SS_MAX_SCENES = 64
 SS_MAX_RECORDS = 0xfffffffe
-SS_MAX_TILES = 1 << 28
+SS_MAX_TILES = 1 << 27
 SS_KMAX_LIMIT = 16
 SS_N_AOV = 9
 SS_NOALLOC_AUX_FLOATS = 1 << 20

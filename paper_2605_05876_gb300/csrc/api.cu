@@ -194,7 +194,7 @@ static ss_status build_layout(const ss_batch_desc* b, const ss_render_params* p,
         vl.height = c.height;
         vl.tiles_x = (c.width + (1 << L->tw_log2) - 1) >> L->tw_log2;
         vl.tiles_y = (c.height + (1 << L->th_log2) - 1) >> L->th_log2;
-        // (tile, block) items are numbered tile * 8 + block in 32 bits
+        // (tile, block) items are numbered tile * 8 + block in 32-bit integers
         if ((int64_t)tiles + (int64_t)vl.tiles_x * vl.tiles_y > SS_MAX_TILES) return SS_ERR_INVALID_ARG;
         vl.tile_off = tiles;
         vl.pixel_off = pix;

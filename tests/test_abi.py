@@ -146,8 +146,8 @@ def test_batch_limits_are_checked_on_the_host():
     assert query(3, 0x55555555) == _lib.SS_ERR_INVALID_ARG        # 0xffffffff, scenes within their limit
     assert query(3, 0x55555554) == 0
     # tiles: 8 x 4 tiles of a 32768^2 view = 2^25 each
-    assert query(8, 10, 32768, 32768) == 0                        # 2^28 tiles
-    assert query(9, 10, 32768, 32768) == _lib.SS_ERR_INVALID_ARG
+    assert query(4, 10, 32768, 32768) == 0                        # 2^27 tiles
+    assert query(5, 10, 32768, 32768) == _lib.SS_ERR_INVALID_ARG
 
 
 def test_host_side_argument_errors():
