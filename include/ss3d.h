@@ -140,7 +140,7 @@ typedef struct ss_render_params {
     float bg[3];             /* background radiance behind the last layer */
     int32_t write_aov;       /* 1: also write the 9 AOV channels */
     int32_t lut_n;           /* BRDF table resolution (n x n) */
-    int64_t max_instances;   /* capacity of the (tile, surfel) instance list */
+    int64_t max_instances;   /* capacity of the (tile, surfel) instance list: 1 .. 2^32 - 1 */
     int32_t collect_stats;   /* 1: count work (see ss_read_stats); off by default */
     /* launch shapes (0 = default); they change speed, never results */
     int32_t fwd_warps;       /* warps per CTA of the forward rasteriser: 1 (default), 2 or 4 */
