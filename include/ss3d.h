@@ -176,8 +176,10 @@ typedef struct ss_render_params {
                                 its own, and every (surfel, view) record sums its rows in row
                                 order; the environment-texel gradients are summed as 64-bit
                                 fixed-point integers (exact and order-free; the scale is a power of
-                                two from a bound on the largest contribution, so one unit is at
-                                most 2^-28 of the largest record colour gradient).  Slower; the
+                                two from a bound on the largest contribution: one unit is at most
+                                2^(c - 56) (V + 1) of the largest record colour gradient, with 2^c
+                                >= 8 (surfels + records) + 1 and V the most views of a scene, about
+                                2^-24 for 1M surfels x 16 views; c <= 40 is required).  Slower; the
                                 workspace holds 104 bytes per row (det_rows) more */
     int64_t det_rows;        /* deterministic = 1: capacity of those rows, one per (warp block,
                                 staged surfel that covers a pixel of the block) pair
