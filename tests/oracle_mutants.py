@@ -62,6 +62,14 @@ SLIPS = {
     "theta_sign": ("model", "th = torch.acos(torch.clamp(d[..., 1], -1.0, 1.0))",
                    "th = torch.acos(torch.clamp(-d[..., 1], -1.0, 1.0))"),
     "seam_clamped": ("model", "xa = torch.remainder(x0, W)", "xa = torch.clamp(x0, 0, W - 1)"),
+    # support rectangle (model.py)
+    "rect_unpadded": ("model", "lo = np.minimum(np.minimum(r0, r1), p[:, a] - ext) - 1.0",
+                      "lo = np.minimum(np.minimum(r0, r1), p[:, a] - ext)"),
+    "rect_no_ewa": ("model", "lo = np.minimum(np.minimum(r0, r1), p[:, a] - ext) - 1.0",
+                    "lo = np.minimum(r0, r1) - 1.0"),
+    "rect_no_disc": ("model", "hi = np.maximum(np.maximum(r0, r1), p[:, a] + ext) + 1.0",
+                     "hi = p[:, a] + ext + 1.0"),
+    "rect_dual_conic": ("model", "Q = np.diag([1.0, 1.0, -1.0 / prm.r_cut ** 2])", "Q = np.diag([1.0, 1.0, -1.0 / prm.r_cut])"),
     # per-pixel decisions and the environment prefilter (ss3d_oracle.c)
     "cut_radius": ("c", "if (!(rho2 < rcut2)) continue;", "if (!(rho2 < sqrt(rcut2))) continue;"),
     "gap_ge": ("c", "if (layer < 0 || fr[f].zs > zmax) {", "if (layer < 0 || fr[f].zs >= zmax) {"),

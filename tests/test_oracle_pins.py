@@ -723,3 +723,52 @@ def test_lone_surfel_reconstructs_its_depth_and_materials():
     np.testing.assert_allclose(got[:, 4], f32(metal), rtol=1e-12)
     np.testing.assert_allclose(got[:, 5:8], np.broadcast_to([0.0, 0.0, 1.0], got[:, 5:8].shape), atol=1e-12)
     np.testing.assert_allclose(got[:, 8], 3.0 - f32(z_w), rtol=1e-12)
+
+
+@pytest.mark.parametrize("angle", [1.2, -1.2])
+def test_support_of_a_tilted_surfel_near_the_camera_is_its_projected_disc(angle):
+    """Without the MIP filter (n_f = 1, Sigma = I) the support is the disc of
+    radius r_cut in the surfel plane.  A large surfel tilted about 70 degrees
+    close to the camera projects that disc far from its affine image at the
+    centre (its near half is wider), so the support rectangle must take the
+    disc's exact projected bounds (App. A), not only the EWA ellipse's: the
+    covered pixels are exactly those whose ray meets the plane inside the
+    disc (ray-plane intersection in FP64), and some lie beyond the affine
+    bounds."""
+    prm = M.Params(mip_mode="none")
+    cam = _tiny.front_camera(dist=0.9, res=48)
+    surf = _tilt(_tiny.surfels([[0.0, 0.05, 0.0]], scale=0.12), angle)
+    env = env_state(_tiny.const_env(), prm)
+    out = _render(surf, cam, env, prm)
+    got = out["rgba"][:, 3] > 0
+    # direct intersection: camera at (0, 0, 0.9) looking down -z, pixel rays through centres
+    cd = M.cam_dict(cam)
+    R, t = cd["R"].numpy(), cd["t"].numpy()
+    q = surf.quat[0].astype(np.float64)
+    Rs = M.quat_to_rot(torch.from_numpy(q[None])).numpy()[0]
+    sc = np.exp(surf.log_scale[0].astype(np.float64))
+    c = R @ surf.pos[0].astype(np.float64) + t
+    tu, tv = R @ (sc[0] * Rs[:, 0]), R @ (sc[1] * Rs[:, 1])
+    n = np.cross(tu, tv)
+    W = H = 48
+    xs, ys = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
+    d = np.stack([(xs - cd["cx"]) / cd["fx"], (ys - cd["cy"]) / cd["fy"], np.ones_like(xs)], -1).reshape(-1, 3)
+    lam = (n @ c) / (d @ n)
+    X = lam[:, None] * d - c
+    A = np.stack([tu, tv], 1)
+    uv = np.linalg.lstsq(A, X.T, rcond=None)[0].T
+    r2 = (uv ** 2).sum(1)
+    want = (lam > 0) & (r2 < prm.r_cut ** 2)
+    near_edge = np.abs(r2 - prm.r_cut ** 2) < 1e-6
+    assert want.sum() > 100
+    assert np.array_equal(got[~near_edge], want[~near_edge])
+    # the disc reaches past the affine (EWA) bounds at the centre
+    Mm = out["records"]["T"]
+    T = Mm.numpy()[0]
+    px, py = T[0, 2] / T[2, 2], T[1, 2] / T[2, 2]
+    Mx = np.array([[T[0, 0] - px * T[2, 0], T[0, 1] - px * T[2, 1]],
+                   [T[1, 0] - py * T[2, 0], T[1, 1] - py * T[2, 1]]]) / T[2, 2]
+    ext = prm.r_cut * np.sqrt(np.diag(Mx @ Mx.T))
+    cx_, cy_ = xs.ravel()[want], ys.ravel()[want]
+    beyond = (np.abs(cx_ - px) > ext[0] + 1) | (np.abs(cy_ - py) > ext[1] + 1)
+    assert beyond.sum() > 20     # (tilted one way or the other: the far side differs)
