@@ -31,7 +31,12 @@ SLIPS = {
     "no_background": ("model", "rgb = out[:, :3] + T_end[:, None] * bg", "rgb = out[:, :3]"),
     "pixel_corner": ("model", "x = torch.from_numpy((fr.pix % W).astype(np.float64)) + 0.5",
                      "x = torch.from_numpy((fr.pix % W).astype(np.float64)) + 0.0"),
+    "no_shepard": ("model", "Chat = Ck / Wsafe[..., None]", "Chat = Ck"),
+    "one_layer": ("model", "key = row_t * Kq + layer", "key = row_t * Kq"),
+    "T_end_early": ("model", "T_end = Tbar[:, Kq]", "T_end = Tbar[:, Kq - 1]"),
+    "uv_swapped": ("model", "u = s[:, 0] / s[:, 2]\n    v = s[:, 1] / s[:, 2]", "u = s[:, 1] / s[:, 2]\n    v = s[:, 0] / s[:, 2]"),
     # records: projection, MIP filter, depth interval, channels (model.py)
+    "centre_undivided": ("model", "px = T1[:, 2] / T4[:, 2]", "px = T1[:, 2]"),
     "swap_f": ("model", 'fx, fy, cx, cy = cam["fx"], cam["fy"], cam["cx"], cam["cy"]',
                'fy, fx, cx, cy = cam["fx"], cam["fy"], cam["cx"], cam["cy"]'),
     "swap_c": ("model", 'fx, fy, cx, cy = cam["fx"], cam["fy"], cam["cx"], cam["cy"]',
